@@ -1,0 +1,175 @@
+/*
+ * edt.h - C ABI of the GB300 (sm_103a) extended-diffraction-tomography library.
+ *
+ * The library solves the linear (first-order Born) seismic inverse problem of
+ * R. B. Schlottmann, "Extended diffraction tomography": surface data D(omega, xs, xr)
+ * over a laterally invariant reference c0(z) are mapped to the scattering potential
+ * V(x, z) = 1/c^2 - 1/c0^2 (Section "Two dimensions", eq. Born and the definition of V
+ * after it).  The 2D problem decouples into one independent 1D depth problem per
+ * midpoint wavenumber k_m (eqs. DMV and M); each is split into real systems for
+ * Re Vhat and Im Vhat (eq. Split) and solved by damped least squares; the negative
+ * wavenumbers follow from Vhat(-k_m) = conj Vhat(k_m) (eq. VSym).
+ *
+ * Discrete model (shared by every entry point):
+ *   - lateral grid x_i = i dx, i < nx, periodic with L = nx dx; one source and one
+ *     receiver at every grid point on z = 0; k_n = 2 pi n'/L, n' = n (n <= nx/2) or n - nx;
+ *   - depths z_j = z0 + (j + 1/2) dz, j < nz;
+ *   - complex frequency omega~_f = 2 pi freq_hz[f] + i eps (the paper's omega -> omega + i eps);
+ *   - g(k, z) solves g'' + (omega~^2/c0(z)^2 - k^2) g = -delta(z) (the reference
+ *     Green's-function equation after a lateral Fourier transform), radiating away from
+ *     the surface source, with the top layer continued above z = 0 (no free surface);
+ *   - kernel rows M[(f, p), j] = (omega~_f^2 dz/dx) g(k_p, z_j) g(k_{p-m}, z_j)
+ *     (eq. M with every offset recorded, so the aperture sinc is a delta);
+ *   - data transform D2(p, q) = sum_is sum_ir D(is, ir) exp(-i k_p x_ir) exp(+i k_q x_is);
+ *   - per 0 <= m <= nx/2: minimise ||Ahat x - dhat||^2 + lam ||x||^2 with
+ *     Ahat = [Re M; Im M], lam = alpha * trace(Ahat^T Ahat), dhat from d_+ and d_- of
+ *     eq. Split; Vhat(k_m) = x_+ + i x_- (x_- = 0 at m = 0 and m = nx/2);
+ *   - V(x, z) = (1/nx) sum_m Vhat(k_m, z) exp(+i k_m x).
+ *   Rows with a leg evanescent in the slowest layer are dropped when cutoff > 0:
+ *   row (f, p) of m is kept iff |p'| c_min < (cutoff f) L and |q'| c_min < (cutoff f) L,
+ *   q = (p - m) mod nx, evaluated in IEEE double exactly in that order.
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are CUDA device pointers of the current device; *_host are
+ *     host pointers (pinned memory recommended).  Complex data are interleaved (re, im).
+ *   - Layouts are row-major: D is [nfreq][nx (source)][nx (receiver)], V is [nx][nz],
+ *     Vhat is [nx/2 + 1][nz], g is [nfreq][nx/2 + 1][nz].
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Every
+ *     device call is asynchronous on that stream; results are valid after it syncs.
+ *   - The caller owns every input/output buffer and the device workspace; nothing is
+ *     allocated on the device after edt_create (edt_invert is safe to capture in a graph
+ *     once edt_set_workspace has run).  edt_create allocates host memory only.
+ *   - Errors are negative return codes (below); no exception crosses the ABI.  A context
+ *     must not be used by two threads at once.
+ */
+#ifndef EDT_H
+#define EDT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define EDT_OK            0
+#define EDT_EINVAL       -1   /* invalid argument or configuration                        */
+#define EDT_ENOMEM_WS    -2   /* workspace not set or smaller than edt_create reported     */
+#define EDT_ENOTPD       -3   /* a damped normal matrix was not positive definite          */
+#define EDT_ETIMEOUT     -4   /* a bounded device-side wait expired                        */
+#define EDT_ENONFINITE   -5   /* non-finite value met in the data or a factorisation       */
+#define EDT_ECUDA        -6   /* a CUDA runtime call failed (see edt_last_cuda_error)      */
+#define EDT_EUNSUPPORTED -7   /* valid request outside what this build implements          */
+
+/* ---- enumerations ---------------------------------------------------------------- */
+#define EDT_FP64   0   /* every stage in IEEE double                                          */
+#define EDT_MIXED  1   /* FP32 transforms, BF16 tensor-core Gram with FP32 accumulation,
+                          FP64 Cholesky and FP64-accumulated iterative refinement          */
+
+#define EDT_C64    0   /* complex64 data (interleaved float)   */
+#define EDT_C128   1   /* complex128 data (interleaved double) */
+#define EDT_F32    2   /* real float32 model                   */
+#define EDT_F64    3   /* real float64 model                   */
+
+typedef struct edt_ctx edt_ctx;   /* opaque; owned by the library */
+
+/* Problem description.  Lengths in metres, velocities in m/s, frequencies in Hz.
+ * Arrays are read during edt_create only and may be freed afterwards. */
+typedef struct {
+  int nx;                       /* lateral samples (power of two, 4..1024)               */
+  double dx;                    /* lateral spacing (> 0)                                 */
+  int nz;                       /* depth unknowns (1..512; the mixed path: 1..256)       */
+  double dz;                    /* depth spacing (> 0)                                   */
+  double z0;                    /* depth of the top of the first depth cell (>= 0)       */
+  int nfreq;                    /* number of frequencies (1..32767)                      */
+  const double* freq_hz;        /* [nfreq], > 0                                          */
+  double eps;                   /* imaginary part of the complex frequency (1/s, >= 0)    */
+  int nlayer;                   /* layers of the reference c0(z) (1..4096)               */
+  const double* layer_top_m;    /* [nlayer], layer_top_m[0] == 0, strictly increasing    */
+  const double* layer_vel_mps;  /* [nlayer], > 0; the last layer is a half-space         */
+  int precision;                /* EDT_FP64 or EDT_MIXED                                 */
+  int passes;                   /* mixed: 1 = BF16 Gram, 3 = split BF16x3 Gram           */
+  int refine;                   /* mixed: refinement steps (0..4, default 1)             */
+  double alpha;                 /* damping: lam = alpha * trace(Gram) (>= 0)             */
+  double cutoff;                /* evanescent cut factor; <= 0 keeps every row           */
+  int fold;                     /* 1: merge the identical reciprocal rows (p,q),(-q,-p)
+                                   into one row of weight 2 (same normal equations);
+                                   0: keep every row as the paper writes them           */
+} edt_config;
+
+/* Host-side statistics of a context; the device-side fields are refreshed by
+ * edt_get_stats, which synchronises the context's last stream. */
+typedef struct {
+  int n_sub;                    /* subproblems solved: nx/2 + 1                          */
+  long long rows_total;         /* complex rows over all subproblems after the cut       */
+  long long rows_solved;        /* rows actually processed (after folding)               */
+  int rows_min, rows_max;       /* per-subproblem complex rows after the cut             */
+  size_t workspace_bytes;       /* device workspace required                             */
+  double gram_flop;             /* algorithmic Gram flops per invert (2 * rows_solved'
+                                   * 2 * nz * (nz + 2), real rows, full square)          */
+  int n_notpd;                  /* subproblems whose factorisation failed (last invert)  */
+  int n_nonfinite;              /* subproblems with a non-finite solution (last invert)  */
+  int last_status;              /* status of the last device call                        */
+} edt_stats;
+
+/* Create a context for `cfg` and report the device workspace it needs.
+ * Returns EDT_OK, EDT_EINVAL or EDT_EUNSUPPORTED.  *out is NULL on failure. */
+int edt_create(edt_ctx** out, const edt_config* cfg, size_t* workspace_bytes);
+
+/* Attach a caller-owned device workspace of at least the reported size (256-byte
+ * aligned) and upload the context's constant tables into it (synchronous copies on the
+ * legacy stream).  The workspace must stay valid until edt_destroy or the next call. */
+int edt_set_workspace(edt_ctx* ctx, void* ws_dev, size_t bytes);
+
+/* Invert data D -> model V (the whole method above).  D_dtype is EDT_C64 or EDT_C128,
+ * V_dtype EDT_F32 or EDT_F64.  Per-subproblem failures (EDT_ENOTPD) zero that
+ * subproblem and are counted in edt_get_stats; they do not fail the call. */
+int edt_invert(edt_ctx* ctx, const void* D_dev, int D_dtype, void* V_dev, int V_dtype,
+               void* stream);
+
+/* edt_invert from host buffers: copies D to the device, inverts, copies V back, all on
+ * `stream` (asynchronous; the host buffers must stay valid until the stream syncs).
+ * Uses the staging areas inside the workspace. */
+int edt_invert_host(edt_ctx* ctx, const void* D_host, int D_dtype, void* V_host,
+                    int V_dtype, void* stream);
+
+/* Born forward model V -> D in the same discrete model (eq. Born with omega~^2):
+ * D(is, ir) = omega~^2 dx dz sum_x sum_j G(x_ir - x, z_j) V(x, z_j) G(x - x_is, z_j),
+ * evaluated spectrally.  Precision follows cfg.precision (FP32 for EDT_MIXED). */
+int edt_forward(edt_ctx* ctx, const void* V_dev, int V_dtype, void* D_dev, int D_dtype,
+                void* stream);
+
+/* Reference Green's function table g(k_n, z_j; omega~_f), n = 0..nx/2, as complex128
+ * [nfreq][nx/2+1][nz] (computed in FP64 by the depth march). */
+int edt_green(edt_ctx* ctx, void* g_dev, void* stream);
+
+/* Copy Vhat(k_m, z_j) of the last edt_invert on this context, m = 0..nx/2, as
+ * complex128 [nx/2+1][nz], into g_dev-like caller memory. */
+int edt_get_vhat(edt_ctx* ctx, void* vhat_dev, void* stream);
+
+/* Per-subproblem complex row counts after the cut (before folding): counts[nx/2+1]. */
+int edt_row_counts(const edt_ctx* ctx, long long* counts);
+
+/* Fill *out; synchronises the stream of the last device call on this context. */
+int edt_get_stats(edt_ctx* ctx, edt_stats* out);
+
+/* Per-stage device timing.  With profiling on, every edt_invert records CUDA events
+ * around its stages; edt_read_profile synchronises and returns the summed milliseconds
+ * per stage since the last reset (names[i] static strings), then resets.
+ * Returns the number of stages written (<= max_stages), or a negative code. */
+int edt_set_profiling(edt_ctx* ctx, int on);
+int edt_read_profile(edt_ctx* ctx, double* ms, const char** names, int max_stages,
+                     int* n_calls);
+
+/* Message for a status code; message of the last CUDA error seen by the library. */
+const char* edt_strerror(int code);
+const char* edt_last_cuda_error(void);
+
+/* Release the context (does not free the caller's workspace). */
+void edt_destroy(edt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EDT_H */

@@ -1,0 +1,274 @@
+// Damped normal-equation solves, FP64: (G + lam I) x_+- = b_+-, lam = alpha * trace(G).
+//
+// Zeroth-order Tikhonov damping is the regularisation the paper's Discussion proposes in
+// place of its truncated SVD.  One block per midpoint wavenumber m: blocked right-looking
+// Cholesky (32-column panels; the diagonal block is factored by one warp, the panel by a
+// row-per-thread triangular solve, the trailing lower triangle by 4x4 register tiles),
+// in place on the L2-resident matrix, then blocked forward and backward substitution for
+// the two right-hand sides.  A non-positive or non-finite pivot marks the subproblem
+// EDT_ENOTPD and zeroes its solution.
+//
+// refine_update: x += (L L^T)^{-1} (r - lam x), where r = Ahat^T (dhat - Ahat x) was
+// accumulated over all rows by the refinement kernel (one step of iterative refinement on
+// the normal equations).
+#include "edt_internal.h"
+#include "cplx.cuh"
+
+namespace edt {
+
+namespace {
+
+constexpr int NB = 32, LDP = NB + 1;
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int(blockDim.x) + 31) / 32; ++w) t += red[w];
+    red[32] = t;
+  }
+  __syncthreads();
+  t = red[32];
+  __syncthreads();
+  return t;
+}
+
+// Solve L L^T x = sb in place (two right-hand sides, sb[i][0..1]); L lower in A (ld n).
+__device__ void chol_solve_2rhs(const double* A, int n, double* sb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // forward: L y = b
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    if (warp == 0) {
+      for (int j = 0; j < kb; ++j) {
+        const double ljj = A[size_t(k0 + j) * n + k0 + j];
+        const double y0 = sb[(k0 + j) * 2 + 0] / ljj, y1 = sb[(k0 + j) * 2 + 1] / ljj;
+        __syncwarp();
+        if (lane == 0) { sb[(k0 + j) * 2 + 0] = y0; sb[(k0 + j) * 2 + 1] = y1; }
+        if (lane > j && lane < kb) {
+          const double l = A[size_t(k0 + lane) * n + k0 + j];
+          sb[(k0 + lane) * 2 + 0] -= l * y0;
+          sb[(k0 + lane) * 2 + 1] -= l * y1;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {
+      double s0 = sb[i * 2 + 0], s1 = sb[i * 2 + 1];
+      const double* Ai = A + size_t(i) * n + k0;
+      for (int l = 0; l < kb; ++l) {
+        s0 -= Ai[l] * sb[(k0 + l) * 2 + 0];
+        s1 -= Ai[l] * sb[(k0 + l) * 2 + 1];
+      }
+      sb[i * 2 + 0] = s0; sb[i * 2 + 1] = s1;
+    }
+    __syncthreads();
+  }
+  // backward: L^T x = y
+  const int nblk = (n + NB - 1) / NB;
+  for (int bk = nblk - 1; bk >= 0; --bk) {
+    const int k0 = bk * NB, kb = min(NB, n - k0);
+    if (warp == 0) {
+      for (int j = kb - 1; j >= 0; --j) {
+        const double ljj = A[size_t(k0 + j) * n + k0 + j];
+        const double x0 = sb[(k0 + j) * 2 + 0] / ljj, x1 = sb[(k0 + j) * 2 + 1] / ljj;
+        __syncwarp();
+        if (lane == 0) { sb[(k0 + j) * 2 + 0] = x0; sb[(k0 + j) * 2 + 1] = x1; }
+        if (lane < j) {
+          const double l = A[size_t(k0 + j) * n + k0 + lane];
+          sb[(k0 + lane) * 2 + 0] -= l * x0;
+          sb[(k0 + lane) * 2 + 1] -= l * x1;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k0; i += blockDim.x) {
+      double s0 = sb[i * 2 + 0], s1 = sb[i * 2 + 1];
+      for (int l = 0; l < kb; ++l) {
+        const double a = A[size_t(k0 + l) * n + i];
+        s0 -= a * sb[(k0 + l) * 2 + 0];
+        s1 -= a * sb[(k0 + l) * 2 + 1];
+      }
+      sb[i * 2 + 0] = s0; sb[i * 2 + 1] = s1;
+    }
+    __syncthreads();
+  }
+}
+
+// trace_mode 0: trace from the diagonal of G; 1: from d.trace (accumulated by the producer).
+__global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
+  extern __shared__ __align__(16) double sm[];
+  const int n = d.nz;
+  double* sP = sm;                          // [n][LDP] panel
+  double* sD = sP + size_t(n) * LDP;        // [NB][LDP] diagonal block
+  double* sb = sD + NB * LDP;               // [n][2] right-hand sides
+  double* red = sb + 2 * n;                 // [33] reduction scratch
+  __shared__ int fail;
+  const int m = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* A = d.G + size_t(m) * n * n;
+  const long long nr = d.row_off[m + 1] - d.row_off[m];
+  double* xo = d.x + size_t(m) * n * 2;
+  if (threadIdx.x == 0) fail = 0;
+  if (nr == 0) {
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    if (threadIdx.x == 0) { d.status[m] = EDT_OK; d.trace[m] = 0.0; }
+    return;
+  }
+  double tr;
+  if (trace_mode == 0) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += A[size_t(i) * n + i];
+    tr = block_sum(t, red);
+  } else {
+    tr = d.trace[m];
+  }
+  const double lam = d.alpha * tr;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    A[size_t(i) * n + i] += lam;
+    sb[2 * i + 0] = d.b[(size_t(m) * n + i) * 2 + 0];
+    sb[2 * i + 1] = d.b[(size_t(m) * n + i) * 2 + 1];
+  }
+  if (threadIdx.x == 0) d.trace[m] = lam;     // from here on the slot holds lam
+  __syncthreads();
+
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, j = e - i * kb;
+      if (j <= i) sD[i * LDP + j] = A[size_t(k0 + i) * n + k0 + j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int j = 0; j < kb; ++j) {
+        const double djj = sD[j * LDP + j];
+        if (!(djj > 0.0) || !isfinite(djj)) { if (lane == 0) fail = 1; break; }
+        const double ljj = sqrt(djj);
+        __syncwarp();
+        if (lane == j) sD[j * LDP + j] = ljj;
+        if (lane > j && lane < kb) sD[lane * LDP + j] /= ljj;
+        __syncwarp();
+        if (lane > j && lane < kb) {
+          const double lij = sD[lane * LDP + j];
+          for (int l = j + 1; l <= lane; ++l) sD[lane * LDP + l] -= lij * sD[l * LDP + j];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (fail) break;
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, j = e - i * kb;
+      if (j <= i) A[size_t(k0 + i) * n + k0 + j] = sD[i * LDP + j];
+    }
+    const int t0 = k0 + kb, t = n - t0;
+    // panel: row i of the block column solves x L_kk^T = a
+    for (int i = threadIdx.x; i < t; i += blockDim.x) {
+      double x[NB];
+      double* Ai = A + size_t(t0 + i) * n + k0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) x[j] = j < kb ? Ai[j] : 0.0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (j < kb) {
+          double s = x[j];
+#pragma unroll
+          for (int l = 0; l < j; ++l) s -= x[l] * sD[j * LDP + l];
+          x[j] = s / sD[j * LDP + j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        if (j < kb) { Ai[j] = x[j]; sP[i * LDP + j] = x[j]; }
+    }
+    __syncthreads();
+    // trailing lower triangle: A[i][j] -= sum_l P[i][l] P[j][l], 4x4 tiles
+    const int nbt = (t + 3) / 4;
+    const int npair = nbt * (nbt + 1) / 2;
+    for (int pt = threadIdx.x; pt < npair; pt += blockDim.x) {
+      int bi = int((sqrtf(8.0f * pt + 1.0f) - 1.0f) * 0.5f);
+      while (bi * (bi + 1) / 2 > pt) --bi;
+      while ((bi + 1) * (bi + 2) / 2 <= pt) ++bi;
+      const int bj = pt - bi * (bi + 1) / 2;
+      double acc[4][4] = {};
+      for (int l = 0; l < kb; ++l) {
+        double pi[4], pj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int ii = bi * 4 + u, jj = bj * 4 + u;
+          pi[u] = ii < t ? sP[ii * LDP + l] : 0.0;
+          pj[u] = jj < t ? sP[jj * LDP + l] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fma(pi[u], pj[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          int ii = bi * 4 + u, jj = bj * 4 + v;
+          if (ii < t && jj <= ii) A[size_t(t0 + ii) * n + t0 + jj] -= acc[u][v];
+        }
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
+    return;
+  }
+  chol_solve_2rhs(A, n, sb);
+  bool bad = false;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+    xo[i] = sb[i];
+    if (!isfinite(sb[i])) bad = true;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) d.status[m] = bad ? EDT_ENONFINITE : EDT_OK;
+}
+
+__global__ void __launch_bounds__(256) refine_update_kernel(Dev d) {
+  extern __shared__ __align__(16) double sm[];
+  const int n = d.nz, m = blockIdx.x;
+  double* sb = sm;
+  if (d.status[m] != EDT_OK) return;
+  if (d.row_off[m + 1] == d.row_off[m]) return;
+  const double lam = d.trace[m];
+  double* xo = d.x + size_t(m) * n * 2;
+  const double* r = d.r + size_t(m) * n * 2;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) sb[i] = r[i] - lam * xo[i];
+  __syncthreads();
+  chol_solve_2rhs(d.G + size_t(m) * n * n, n, sb);
+  bool bad = false;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+    double v = xo[i] + sb[i];
+    xo[i] = v;
+    if (!isfinite(v)) bad = true;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0 && bad) d.status[m] = EDT_ENONFINITE;
+}
+
+}  // namespace
+
+cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
+  size_t smem = (size_t(d.nz) * LDP + NB * LDP + 2 * d.nz + 40) * sizeof(double);
+  cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  chol_kernel<<<d.nsub, 256, smem, s>>>(d, trace_mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_update(const Dev& d, cudaStream_t s) {
+  size_t smem = size_t(2 * d.nz) * sizeof(double);
+  refine_update_kernel<<<d.nsub, 256, smem, s>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace edt

@@ -1,0 +1,65 @@
+// Small complex-arithmetic helpers on CUDA vector types (device and host).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace edt {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cplx_t = typename cplx_of<T>::type;
+
+__host__ __device__ __forceinline__ double2 cmk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, b); }
+
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator*(double2 a, double2 b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return cmk(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float2 b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return cmk(s * a.x, s * a.y); }
+
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return cmk(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return cmk(a.x, -a.y); }
+
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  // Smith's algorithm (scaled division, avoids overflow in |b|^2)
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, den = b.x + b.y * r;
+    return cmk((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+  } else {
+    double r = b.x / b.y, den = b.x * r + b.y;
+    return cmk((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+  }
+}
+
+__host__ __device__ __forceinline__ double2 cexp(double2 a) {
+  double e = exp(a.x), s, c;
+  sincos(a.y, &s, &c);
+  return cmk(e * c, e * s);
+}
+
+// Principal square root, then the branch with non-negative imaginary part.
+__host__ __device__ __forceinline__ double2 csqrt_upper(double2 w) {
+  double r = hypot(w.x, w.y);
+  double2 z;
+  if (r == 0.0) return cmk(0.0, 0.0);
+  if (w.x >= 0.0) {
+    double t = sqrt(0.5 * (r + w.x));
+    z = cmk(t, w.y / (2.0 * t));
+  } else {
+    double t = sqrt(0.5 * (r - w.x));
+    z = cmk(fabs(w.y) / (2.0 * t), copysign(t, w.y));
+  }
+  if (z.y < 0.0) z = cmk(-z.x, -z.y);
+  return z;
+}
+
+}  // namespace edt

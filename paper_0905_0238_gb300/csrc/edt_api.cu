@@ -1,0 +1,555 @@
+// C ABI: context creation, host-side planning (row lists, tables, workspace layout) and
+// the orchestration of the device stages.  See include/edt.h for the contract.
+#include "edt_internal.h"
+#include "cplx.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+namespace edt {
+
+namespace {
+
+thread_local std::string g_last_cuda;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda = cudaGetErrorString(e);
+  return EDT_ECUDA;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+struct Region { size_t off = 0, bytes = 0; };
+
+}  // namespace
+
+}  // namespace edt
+
+using namespace edt;
+
+struct edt_ctx {
+  edt_config cfg{};
+  std::vector<double> freq, tops, vel;
+  // plan
+  int N = 0, nk = 0, nz = 0, nf = 0, nsub = 0, nlayer = 0;
+  std::vector<FreqConst> fc;
+  std::vector<int> z_layer;
+  std::vector<double> z_off;
+  std::vector<uint32_t> rows;
+  std::vector<long long> row_off;
+  std::vector<long long> counts_cut;
+  std::vector<double2> tw64;
+  std::vector<float2> tw32;
+  // tensor-core Gram schedule
+  std::vector<int> seg_m, cta_seg0, m_slot0;
+  std::vector<long long> seg_row0, seg_nrow;
+  int ncta_gram = 0, nslot = 0;
+  // workspace
+  size_t ws_bytes = 0;
+  void* ws = nullptr;
+  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_tw64, r_tw32, r_segm, r_segr0,
+      r_segn, r_ctas, r_mslot, r_coef, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gpart, r_G,
+      r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
+  Dev dev{};
+  cudaStream_t last_stream = nullptr;
+  int last_status = EDT_OK;
+  // profiling
+  bool prof = false;
+  static constexpr int NSTAGE = 8;
+  std::vector<cudaEvent_t> ev;   // [calls][NSTAGE + 1]
+  int prof_calls = 0;
+  int prof_used[NSTAGE] = {};
+};
+
+namespace {
+
+const char* kStageNames[edt_ctx::NSTAGE] = {"green", "transform", "rhs", "gram",
+                                            "cholesky", "refine", "inverse", "unused"};
+
+int validate(const edt_config* c) {
+  if (!c) return EDT_EINVAL;
+  if (!is_pow2(c->nx) || c->nx < 16 || c->nx > 1024) return EDT_EUNSUPPORTED;
+  if (!(c->dx > 0) || !(c->dz > 0) || !(c->z0 >= 0) || !(c->eps >= 0)) return EDT_EINVAL;
+  if (c->nz < 1 || c->nz > 512) return EDT_EUNSUPPORTED;
+  if (c->nfreq < 1 || c->nfreq > 32767 || !c->freq_hz) return EDT_EINVAL;
+  if (c->nlayer < 1 || c->nlayer > 4096 || !c->layer_top_m || !c->layer_vel_mps) return EDT_EINVAL;
+  if (c->layer_top_m[0] != 0.0) return EDT_EINVAL;
+  for (int j = 0; j < c->nlayer; ++j) {
+    if (!(c->layer_vel_mps[j] > 0) || !std::isfinite(c->layer_vel_mps[j])) return EDT_EINVAL;
+    if (j > 0 && !(c->layer_top_m[j] > c->layer_top_m[j - 1])) return EDT_EINVAL;
+  }
+  for (int f = 0; f < c->nfreq; ++f)
+    if (!(c->freq_hz[f] > 0) || !std::isfinite(c->freq_hz[f])) return EDT_EINVAL;
+  if (c->precision != EDT_FP64 && c->precision != EDT_MIXED) return EDT_EINVAL;
+  if (c->precision == EDT_MIXED) {
+    if (c->passes != 1 && c->passes != 3) return EDT_EINVAL;
+    if (c->refine < 0 || c->refine > 4) return EDT_EINVAL;
+    if (c->nz > 256) return EDT_EUNSUPPORTED;
+  }
+  if (!(c->alpha >= 0) || !std::isfinite(c->alpha)) return EDT_EINVAL;
+  if (!std::isfinite(c->cutoff)) return EDT_EINVAL;
+  if (c->fold != 0 && c->fold != 1) return EDT_EINVAL;
+  return EDT_OK;
+}
+
+void plan(edt_ctx* c) {
+  const edt_config& g = c->cfg;
+  c->N = g.nx; c->nk = g.nx / 2 + 1; c->nz = g.nz; c->nf = g.nfreq; c->nsub = g.nx / 2 + 1;
+  c->nlayer = g.nlayer;
+  const int N = c->N;
+  const double L = double(N) * g.dx;
+  // frequencies
+  c->fc.resize(c->nf);
+  for (int f = 0; f < c->nf; ++f) {
+    FreqConst& q = c->fc[f];
+    q.om_re = 2.0 * M_PI * c->freq[f];
+    q.om_im = g.eps;
+    double2 om = make_double2(q.om_re, q.om_im);
+    double2 s = om * om;
+    s = make_double2(s.x * g.dz / g.dx, s.y * g.dz / g.dx);
+    q.s_abs = std::hypot(s.x, s.y);
+    q.rot_re = s.x / q.s_abs;
+    q.rot_im = -s.y / q.s_abs;
+    q.lim = (g.cutoff * c->freq[f]) * L;
+  }
+  // depth samples -> layer and offset below its top (an interface belongs to the layer below)
+  c->z_layer.resize(c->nz);
+  c->z_off.resize(c->nz);
+  for (int j = 0; j < c->nz; ++j) {
+    double z = g.z0 + (j + 0.5) * g.dz;
+    int l = int(std::upper_bound(c->tops.begin(), c->tops.end(), z) - c->tops.begin()) - 1;
+    l = std::max(0, std::min(l, c->nlayer - 1));
+    c->z_layer[j] = l;
+    c->z_off[j] = z - c->tops[l];
+  }
+  // rows of every subproblem, in (f, p) order, evanescent cut and optional folding
+  const double cmin = *std::min_element(c->vel.begin(), c->vel.end());
+  c->rows.clear();
+  c->row_off.assign(c->nsub + 1, 0);
+  c->counts_cut.assign(c->nsub, 0);
+  auto sidx = [N](int n) { return n <= N / 2 ? n : n - N; };
+  for (int m = 0; m < c->nsub; ++m) {
+    c->row_off[m] = (long long)c->rows.size();
+    for (int f = 0; f < c->nf; ++f) {
+      const double lim = c->fc[f].lim;
+      for (int p = 0; p < N; ++p) {
+        const int q = (p - m + N) % N;
+        bool keep = true;
+        if (g.cutoff > 0) {
+          keep = double(std::abs(sidx(p))) * cmin < lim && double(std::abs(sidx(q))) * cmin < lim;
+        }
+        if (!keep) continue;
+        c->counts_cut[m] += 1;
+        if (g.fold) {
+          const int pp = (N - q) % N;          // first index of the reciprocal partner (-q, -p)
+          if (pp == p) c->rows.push_back(row_pack(f, p, 0));
+          else if (p < pp) c->rows.push_back(row_pack(f, p, 1));
+        } else {
+          c->rows.push_back(row_pack(f, p, 0));
+        }
+      }
+    }
+  }
+  c->row_off[c->nsub] = (long long)c->rows.size();
+  // twiddles e^{-2 pi i k / N}
+  c->tw64.resize(N / 2);
+  c->tw32.resize(N / 2);
+  for (int k = 0; k < N / 2; ++k) {
+    double a = 2.0 * M_PI * double(k) / double(N);
+    c->tw64[k] = make_double2(std::cos(a), -std::sin(a));
+    c->tw32[k] = make_float2(float(std::cos(a)), float(-std::sin(a)));
+  }
+  // tensor-core Gram: split the concatenated rows evenly over the CTAs; a segment is the
+  // part of one subproblem's rows that one CTA covers, each with its own partial slot
+  c->seg_m.clear(); c->seg_row0.clear(); c->seg_nrow.clear(); c->cta_seg0.clear();
+  c->m_slot0.assign(c->nsub + 1, 0);
+  if (g.precision == EDT_MIXED) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long total = c->row_off[c->nsub];
+    int ncta = int(std::max<long long>(1, std::min<long long>(sms, (total + TC_KC - 1) / TC_KC)));
+    c->ncta_gram = ncta;
+    // segments per CTA, slots ordered by m so each m's slots are contiguous
+    std::vector<std::vector<std::pair<int, std::pair<long long, long long>>>> per_m(c->nsub);
+    std::vector<std::vector<int>> cta_segs(ncta);
+    struct Seg { int m, cta; long long r0, n; };
+    std::vector<Seg> segs;
+    for (int k = 0; k < ncta; ++k) {
+      long long a = total * k / ncta, b = total * (k + 1) / ncta;
+      long long r = a;
+      while (r < b) {
+        int m = int(std::upper_bound(c->row_off.begin(), c->row_off.end(), r) - c->row_off.begin()) - 1;
+        long long e = std::min(b, c->row_off[m + 1]);
+        segs.push_back({m, k, r, e - r});
+        r = e;
+      }
+    }
+    // slot of a segment = its index when segments are sorted by (m, cta)
+    std::vector<int> order(segs.size());
+    for (size_t i = 0; i < segs.size(); ++i) order[i] = int(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return segs[x].m < segs[y].m; });
+    std::vector<int> slot_of(segs.size());
+    for (size_t i = 0; i < order.size(); ++i) slot_of[order[i]] = int(i);
+    std::vector<int> cnt(c->nsub, 0);
+    for (auto& s : segs) cnt[s.m]++;
+    for (int m = 0; m < c->nsub; ++m) c->m_slot0[m + 1] = c->m_slot0[m] + cnt[m];
+    // per-CTA segment lists in row order; seg_m/row0/nrow indexed by slot
+    c->seg_m.resize(segs.size()); c->seg_row0.resize(segs.size()); c->seg_nrow.resize(segs.size());
+    for (size_t i = 0; i < segs.size(); ++i) {
+      int sl = slot_of[i];
+      c->seg_m[sl] = segs[i].m; c->seg_row0[sl] = segs[i].r0; c->seg_nrow[sl] = segs[i].n;
+    }
+    // cta_seg0 points into a per-CTA list of slots stored after the slot tables
+    c->cta_seg0.assign(ncta + 1, 0);
+    std::vector<int> cta_slots;
+    for (int k = 0; k < ncta; ++k) {
+      c->cta_seg0[k] = int(cta_slots.size());
+      for (size_t i = 0; i < segs.size(); ++i) if (segs[i].cta == k) cta_slots.push_back(slot_of[i]);
+    }
+    c->cta_seg0[ncta] = int(cta_slots.size());
+    c->cta_seg0.insert(c->cta_seg0.end(), cta_slots.begin(), cta_slots.end());
+    c->nslot = int(segs.size());
+  }
+}
+
+void layout(edt_ctx* c) {
+  size_t off = 0;
+  auto take = [&](Region& r, size_t bytes) {
+    off = align_up(off, 256);
+    r.off = off; r.bytes = bytes;
+    off += bytes;
+  };
+  const size_t nf = c->nf, N = c->N, nk = c->nk, nz = c->nz, ns = c->nsub;
+  const bool mixed = c->cfg.precision == EDT_MIXED;
+  const size_t R = c->rows.size();
+  take(c->r_fc, nf * sizeof(FreqConst));
+  take(c->r_ltop, c->nlayer * sizeof(double));
+  take(c->r_lvel, c->nlayer * sizeof(double));
+  take(c->r_zl, nz * sizeof(int));
+  take(c->r_zo, nz * sizeof(double));
+  take(c->r_rows, std::max<size_t>(R, 1) * sizeof(uint32_t));
+  take(c->r_roff, (ns + 1) * sizeof(long long));
+  take(c->r_tw64, (N / 2) * sizeof(double2));
+  take(c->r_tw32, (N / 2) * sizeof(float2));
+  take(c->r_segm, std::max<size_t>(c->seg_m.size(), 1) * sizeof(int));
+  take(c->r_segr0, std::max<size_t>(c->seg_row0.size(), 1) * sizeof(long long));
+  take(c->r_segn, std::max<size_t>(c->seg_nrow.size(), 1) * sizeof(long long));
+  take(c->r_ctas, std::max<size_t>(c->cta_seg0.size(), 1) * sizeof(int));
+  take(c->r_mslot, (ns + 1) * sizeof(int));
+  take(c->r_coef, nf * nk * c->nlayer * 5 * sizeof(double2));
+  take(c->r_g64, nf * nk * nz * sizeof(double2));
+  take(c->r_g32, mixed ? nf * nk * nz * sizeof(float2) : 0);
+  take(c->r_X, nf * N * N * (mixed ? sizeof(float2) : sizeof(double2)));
+  take(c->r_Dst, nf * N * N * sizeof(double2));
+  take(c->r_Vst, N * nz * sizeof(double));
+  take(c->r_rhs, std::max<size_t>(R, 1) * 2 * (mixed ? sizeof(float2) : sizeof(double2)));
+  take(c->r_gpart, mixed ? size_t(c->nslot) * TC_M * tc_cols(c->nz) * (nz > TC_M ? 2 : 1) * sizeof(float) : 0);
+  take(c->r_G, ns * nz * nz * sizeof(double));
+  take(c->r_b, ns * nz * 2 * sizeof(double));
+  take(c->r_tr, ns * sizeof(double));
+  take(c->r_x, ns * nz * 2 * sizeof(double));
+  take(c->r_r, ns * nz * 2 * sizeof(double));
+  take(c->r_vhat, ns * nz * sizeof(double2));
+  take(c->r_vfull, N * nz * sizeof(double2));
+  take(c->r_status, ns * sizeof(int));
+  take(c->r_flags, 8 * sizeof(unsigned));
+  c->ws_bytes = align_up(off, 256);
+}
+
+template <typename P> P at(edt_ctx* c, const Region& r) {
+  return reinterpret_cast<P>(static_cast<char*>(c->ws) + r.off);
+}
+
+void bind(edt_ctx* c) {
+  Dev& d = c->dev;
+  d.N = c->N; d.nk = c->nk; d.nz = c->nz; d.nf = c->nf; d.nsub = c->nsub; d.nlayer = c->nlayer;
+  d.precision = c->cfg.precision; d.passes = c->cfg.passes; d.fold = c->cfg.fold;
+  d.alpha = c->cfg.alpha; d.dx = c->cfg.dx; d.dz = c->cfg.dz;
+  d.fc = at<const FreqConst*>(c, c->r_fc);
+  d.layer_top = at<const double*>(c, c->r_ltop);
+  d.layer_vel = at<const double*>(c, c->r_lvel);
+  d.z_layer = at<const int*>(c, c->r_zl);
+  d.z_off = at<const double*>(c, c->r_zo);
+  d.rows = at<const uint32_t*>(c, c->r_rows);
+  d.row_off = at<const long long*>(c, c->r_roff);
+  d.tw64 = at<const double2*>(c, c->r_tw64);
+  d.tw32 = at<const float2*>(c, c->r_tw32);
+  d.seg_m = at<const int*>(c, c->r_segm);
+  d.seg_row0 = at<const long long*>(c, c->r_segr0);
+  d.seg_nrow = at<const long long*>(c, c->r_segn);
+  d.cta_seg0 = at<const int*>(c, c->r_ctas);
+  d.m_slot0 = at<const int*>(c, c->r_mslot);
+  d.nseg = c->nslot; d.ncta_gram = c->ncta_gram;
+  d.coef = at<double2*>(c, c->r_coef);
+  d.g64 = at<double2*>(c, c->r_g64);
+  d.g32 = c->r_g32.bytes ? at<float2*>(c, c->r_g32) : nullptr;
+  d.X = at<void*>(c, c->r_X);
+  d.Dstage = at<void*>(c, c->r_Dst);
+  d.Vstage = at<void*>(c, c->r_Vst);
+  d.rhs = at<void*>(c, c->r_rhs);
+  d.gpart = c->r_gpart.bytes ? at<float*>(c, c->r_gpart) : nullptr;
+  d.G = at<double*>(c, c->r_G);
+  d.b = at<double*>(c, c->r_b);
+  d.trace = at<double*>(c, c->r_tr);
+  d.x = at<double*>(c, c->r_x);
+  d.r = at<double*>(c, c->r_r);
+  d.vhat = at<double2*>(c, c->r_vhat);
+  d.vfull = at<double2*>(c, c->r_vfull);
+  d.status = at<int*>(c, c->r_status);
+  d.flags = at<unsigned*>(c, c->r_flags);
+}
+
+template <typename T>
+int upload(edt_ctx* c, const Region& r, const std::vector<T>& v) {
+  if (v.empty()) return EDT_OK;
+  cudaError_t e = cudaMemcpy(at<void*>(c, r), v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? EDT_OK : cuda_fail(e);
+}
+
+#define EDT_TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return cuda_fail(_e); } while (0)
+#define EDT_TRYI(x) do { int _r = (x); if (_r != EDT_OK) return _r; } while (0)
+
+void prof_mark(edt_ctx* c, int stage, cudaStream_t s) {
+  if (!c->prof || c->prof_calls >= 64) return;
+  cudaEventRecord(c->ev[size_t(c->prof_calls) * (edt_ctx::NSTAGE + 1) + stage], s);
+  c->prof_used[stage] = 1;
+}
+
+int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cudaStream_t s) {
+  const Dev& d = c->dev;
+  const bool mixed = c->cfg.precision == EDT_MIXED;
+  c->last_stream = s;
+  prof_mark(c, 0, s);
+  EDT_TRY(launch_green(d, s));
+  prof_mark(c, 1, s);
+  if (mixed) { EDT_TRY(launch_transform<float>(d, D, D_dtype, s)); }
+  else { EDT_TRY(launch_transform<double>(d, D, D_dtype, s)); }
+  prof_mark(c, 2, s);
+  if (mixed) { EDT_TRY(launch_rhs<float>(d, s)); }
+  else { EDT_TRY(launch_rhs<double>(d, s)); }
+  prof_mark(c, 3, s);
+  if (mixed) {
+    EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
+    EDT_TRY(launch_gram_tc(d, s));
+  } else {
+    EDT_TRY(launch_gram_f64(d, s));
+  }
+  prof_mark(c, 4, s);
+  EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
+  prof_mark(c, 5, s);
+  if (mixed) {
+    for (int it = 0; it < c->cfg.refine; ++it) {
+      EDT_TRY(cudaMemsetAsync(d.r, 0, sizeof(double) * d.nsub * d.nz * 2, s));
+      EDT_TRY(launch_refine(d, s));
+      EDT_TRY(launch_refine_update(d, s));
+    }
+  }
+  prof_mark(c, 6, s);
+  EDT_TRY(launch_inverse(d, V, V_dtype, s));
+  prof_mark(c, 7, s);
+  if (c->prof && c->prof_calls < 64) c->prof_calls++;
+  return EDT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int edt_create(edt_ctx** out, const edt_config* cfg, size_t* workspace_bytes) {
+  if (!out) return EDT_EINVAL;
+  *out = nullptr;
+  int v = validate(cfg);
+  if (v != EDT_OK) return v;
+  edt_ctx* c = new (std::nothrow) edt_ctx();
+  if (!c) return EDT_EINVAL;
+  c->cfg = *cfg;
+  c->freq.assign(cfg->freq_hz, cfg->freq_hz + cfg->nfreq);
+  c->tops.assign(cfg->layer_top_m, cfg->layer_top_m + cfg->nlayer);
+  c->vel.assign(cfg->layer_vel_mps, cfg->layer_vel_mps + cfg->nlayer);
+  c->cfg.freq_hz = c->freq.data();
+  c->cfg.layer_top_m = c->tops.data();
+  c->cfg.layer_vel_mps = c->vel.data();
+  if (c->cfg.precision == EDT_FP64) { c->cfg.passes = 0; c->cfg.refine = 0; }
+  plan(c);
+  layout(c);
+  if (workspace_bytes) *workspace_bytes = c->ws_bytes;
+  *out = c;
+  return EDT_OK;
+}
+
+int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
+  if (!c || !ws) return EDT_EINVAL;
+  if (bytes < c->ws_bytes) return EDT_ENOMEM_WS;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return EDT_EINVAL;
+  c->ws = ws;
+  bind(c);
+  std::vector<double> zo(c->z_off);
+  EDT_TRYI(upload(c, c->r_fc, c->fc));
+  EDT_TRYI(upload(c, c->r_ltop, c->tops));
+  EDT_TRYI(upload(c, c->r_lvel, c->vel));
+  EDT_TRYI(upload(c, c->r_zl, c->z_layer));
+  EDT_TRYI(upload(c, c->r_zo, zo));
+  EDT_TRYI(upload(c, c->r_rows, c->rows));
+  EDT_TRYI(upload(c, c->r_roff, c->row_off));
+  EDT_TRYI(upload(c, c->r_tw64, c->tw64));
+  EDT_TRYI(upload(c, c->r_tw32, c->tw32));
+  EDT_TRYI(upload(c, c->r_segm, c->seg_m));
+  EDT_TRYI(upload(c, c->r_segr0, c->seg_row0));
+  EDT_TRYI(upload(c, c->r_segn, c->seg_nrow));
+  EDT_TRYI(upload(c, c->r_ctas, c->cta_seg0));
+  EDT_TRYI(upload(c, c->r_mslot, c->m_slot0));
+  EDT_TRY(cudaMemset(at<void*>(c, c->r_status), 0, c->r_status.bytes));
+  EDT_TRY(cudaMemset(at<void*>(c, c->r_flags), 0, c->r_flags.bytes));
+  EDT_TRY(cudaMemset(at<void*>(c, c->r_x), 0, c->r_x.bytes));
+  EDT_TRY(cudaDeviceSynchronize());
+  return EDT_OK;
+}
+
+int edt_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, void* stream) {
+  if (!c || !D || !V) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
+  if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
+  int r = run_invert(c, D, D_dtype, V, V_dtype, static_cast<cudaStream_t>(stream));
+  c->last_status = r;
+  return r;
+}
+
+int edt_invert_host(edt_ctx* c, const void* D_host, int D_dtype, void* V_host, int V_dtype,
+                    void* stream) {
+  if (!c || !D_host || !V_host) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
+  if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t dbytes = size_t(c->nf) * c->N * c->N * (D_dtype == EDT_C64 ? 8 : 16);
+  const size_t vbytes = size_t(c->N) * c->nz * (V_dtype == EDT_F32 ? 4 : 8);
+  EDT_TRY(cudaMemcpyAsync(c->dev.Dstage, D_host, dbytes, cudaMemcpyHostToDevice, s));
+  int r = run_invert(c, c->dev.Dstage, D_dtype, c->dev.Vstage, V_dtype, s);
+  if (r != EDT_OK) return r;
+  EDT_TRY(cudaMemcpyAsync(V_host, c->dev.Vstage, vbytes, cudaMemcpyDeviceToHost, s));
+  return EDT_OK;
+}
+
+int edt_forward(edt_ctx* c, const void* V, int V_dtype, void* D, int D_dtype, void* stream) {
+  if (!c || !D || !V) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
+  if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  EDT_TRY(launch_green(c->dev, s));
+  EDT_TRY(launch_forward(c->dev, V, V_dtype, D, D_dtype, s));
+  return EDT_OK;
+}
+
+int edt_green(edt_ctx* c, void* g_dev, void* stream) {
+  if (!c || !g_dev) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  EDT_TRY(launch_green(c->dev, s));
+  EDT_TRY(cudaMemcpyAsync(g_dev, c->dev.g64, c->r_g64.bytes, cudaMemcpyDeviceToDevice, s));
+  return EDT_OK;
+}
+
+int edt_get_vhat(edt_ctx* c, void* vhat_dev, void* stream) {
+  if (!c || !vhat_dev) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EDT_TRY(cudaMemcpyAsync(vhat_dev, c->dev.vhat, c->r_vhat.bytes, cudaMemcpyDeviceToDevice, s));
+  return EDT_OK;
+}
+
+int edt_row_counts(const edt_ctx* c, long long* counts) {
+  if (!c || !counts) return EDT_EINVAL;
+  for (int m = 0; m < c->nsub; ++m) counts[m] = c->counts_cut[m];
+  return EDT_OK;
+}
+
+int edt_get_stats(edt_ctx* c, edt_stats* o) {
+  if (!c || !o) return EDT_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->n_sub = c->nsub;
+  long long tot = 0;
+  int mn = 0x7fffffff, mx = 0;
+  for (long long v : c->counts_cut) { tot += v; mn = std::min<long long>(mn, v); mx = std::max<long long>(mx, v); }
+  o->rows_total = tot;
+  o->rows_solved = (long long)c->rows.size();
+  o->rows_min = mn; o->rows_max = mx;
+  o->workspace_bytes = c->ws_bytes;
+  o->gram_flop = 2.0 * 2.0 * double(o->rows_solved) * double(c->nz) * double(c->nz + 2);
+  o->last_status = c->last_status;
+  if (c->ws) {
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::vector<int> st(c->nsub);
+    e = cudaMemcpy(st.data(), c->dev.status, sizeof(int) * c->nsub, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int v : st) {
+      if (v == EDT_ENOTPD) o->n_notpd++;
+      if (v == EDT_ENONFINITE) o->n_nonfinite++;
+    }
+  }
+  return EDT_OK;
+}
+
+int edt_set_profiling(edt_ctx* c, int on) {
+  if (!c) return EDT_EINVAL;
+  if (on && c->ev.empty()) {
+    c->ev.resize(64 * (edt_ctx::NSTAGE + 1));
+    for (auto& e : c->ev) EDT_TRY(cudaEventCreate(&e));
+  }
+  c->prof = on != 0;
+  c->prof_calls = 0;
+  std::memset(c->prof_used, 0, sizeof(c->prof_used));
+  return EDT_OK;
+}
+
+int edt_read_profile(edt_ctx* c, double* ms, const char** names, int max_stages, int* n_calls) {
+  if (!c || !ms) return EDT_EINVAL;
+  const int ns = std::min(max_stages, edt_ctx::NSTAGE - 1);
+  for (int i = 0; i < ns; ++i) { ms[i] = 0.0; if (names) names[i] = kStageNames[i]; }
+  if (n_calls) *n_calls = c->prof_calls;
+  if (c->prof_calls > 0) {
+    const int K = edt_ctx::NSTAGE + 1;
+    EDT_TRY(cudaEventSynchronize(c->ev[size_t(c->prof_calls - 1) * K + 7]));
+    for (int call = 0; call < c->prof_calls; ++call)
+      for (int i = 0; i < ns; ++i) {
+        float t = 0.f;
+        EDT_TRY(cudaEventElapsedTime(&t, c->ev[size_t(call) * K + i], c->ev[size_t(call) * K + i + 1]));
+        ms[i] += t;
+      }
+  }
+  c->prof_calls = 0;
+  return ns;
+}
+
+const char* edt_strerror(int code) {
+  switch (code) {
+    case EDT_OK: return "ok";
+    case EDT_EINVAL: return "invalid argument";
+    case EDT_ENOMEM_WS: return "workspace missing or too small";
+    case EDT_ENOTPD: return "damped normal matrix not positive definite";
+    case EDT_ETIMEOUT: return "bounded device wait expired";
+    case EDT_ENONFINITE: return "non-finite value";
+    case EDT_ECUDA: return "CUDA runtime error";
+    case EDT_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+const char* edt_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+void edt_destroy(edt_ctx* c) {
+  if (!c) return;
+  for (auto& e : c->ev) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

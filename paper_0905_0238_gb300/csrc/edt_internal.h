@@ -1,0 +1,98 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include <string>
+
+#include "../../include/edt.h"
+
+namespace edt {
+
+// Packed row of a midpoint-wavenumber system: (frequency index f, receiver wavenumber
+// index p, weight flag).  Weight 2 marks a row that stands for itself and its reciprocal
+// partner (-q, -p), which carries the same kernel row.
+__host__ __device__ inline uint32_t row_pack(int f, int p, int w2) {
+  return (uint32_t(f) << 16) | (uint32_t(w2 & 1) << 15) | uint32_t(p);
+}
+__host__ __device__ inline int row_f(uint32_t r) { return int(r >> 16); }
+__host__ __device__ inline int row_p(uint32_t r) { return int(r & 0x7fffu); }
+__host__ __device__ inline int row_w2(uint32_t r) { return int((r >> 15) & 1u); }
+
+// Per-frequency constants: omega~ = omega + i eps, |s_f| with s_f = omega~^2 dz/dx, and
+// the unit phase conj(s_f)/|s_f| that moves the complex prefactor onto the data.
+struct FreqConst {
+  double om_re, om_im;
+  double s_abs;
+  double rot_re, rot_im;
+  double lim;        // (cutoff * f) * L
+};
+
+// Device-side view of the workspace and constant tables of one context.
+struct Dev {
+  int N, nk, nz, nf, nsub, nlayer;
+  int precision, passes, fold;
+  double alpha, dx, dz;
+  // constant tables
+  const FreqConst* fc;          // [nf]
+  const double* layer_top;      // [nlayer]
+  const double* layer_vel;      // [nlayer]
+  const int* z_layer;           // [nz] layer of each sample depth
+  const double* z_off;          // [nz] depth below that layer's top
+  const uint32_t* rows;         // [rows_solved], grouped by m
+  const long long* row_off;     // [nsub + 1]
+  const double2* tw64;          // [N/2] exp(-2 pi i k / N)
+  const float2* tw32;           // [N/2]
+  const int* seg_m;             // tensor-core Gram: per segment its m      [nseg]
+  const long long* seg_row0;    //                   first row, row count    [nseg], [nseg]
+  const long long* seg_nrow;
+  const int* cta_seg0;          //                   per CTA first segment   [ncta + 1]
+  const int* m_slot0;           //                   per m first partial slot [nsub + 1]
+  int nseg, ncta_gram;
+  // scratch
+  double2* coef;                // [nf][nk][nlayer][3] kappa, rho, amp
+  double2* g64;                 // [nf][nk][nz]
+  float2* g32;                  // [nf][nk][nz]  sqrt|s_f| g, mixed path
+  void* X;                      // [nf][N][N] complex, path precision
+  void* Dstage;                 // host-call staging of D (complex128-sized)
+  void* Vstage;                 // host-call staging of V (double-sized)
+  void* rhs;                    // [rows_solved][2] complex, path precision
+  float* gpart;                 // tensor-core Gram partial tiles [nslot][TM_COLS * 128]
+  double* G;                    // [nsub][nz][nz]  Gram, then its Cholesky factor
+  double* b;                    // [nsub][nz][2]
+  double* trace;                // [nsub]
+  double* x;                    // [nsub][nz][2]
+  double* r;                    // [nsub][nz][2]
+  double2* vhat;                // [nsub][nz]
+  double2* vfull;               // [N][nz] scratch for the forward model
+  int* status;                  // [nsub]
+  unsigned int* flags;          // [8] device-side error flags
+};
+
+// ---- launchers (each returns cudaGetLastError()) ---------------------------------------
+cudaError_t launch_green(const Dev& d, cudaStream_t s);
+cudaError_t launch_green_export(const Dev& d, double2* out, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rhs(const Dev& d, cudaStream_t s);
+
+cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
+cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);
+cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s);
+cudaError_t launch_refine(const Dev& d, cudaStream_t s);          // r += Ahat^T (dhat - Ahat x)
+cudaError_t launch_refine_update(const Dev& d, cudaStream_t s);   // x += (LL^T)^-1 (r - lam x)
+cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s);
+cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
+                           cudaStream_t s);
+
+// Tensor-core Gram tiling (shared by host planning and the kernel).
+constexpr int TC_M = 128;              // MMA rows (depth unknowns per M tile)
+constexpr int TC_KC = 32;              // complex rows per pipeline stage (K = 64 real rows)
+int tc_cols(int nz);                   // TMEM columns of one subproblem's accumulator
+int tc_smem_bytes(int nz, int passes); // dynamic shared memory of the Gram kernel
+
+}  // namespace edt

@@ -1,0 +1,277 @@
+// Lateral transforms: the shot/receiver data transform, the inverse transform back to
+// (x, z), and the spectral Born forward model.
+//
+// Data transform (the discrete form of the Fourier transform over midpoint and offset in
+// Section "Two dimensions"):  D2(p, q) = sum_is sum_ir D(is, ir) e^{-i k_p x_ir} e^{+i k_q x_is}.
+// Pass 1 transforms every receiver line (contiguous rows, sign -), pass 2 every source
+// column (stride N, sign +), leaving X[f][q][p] = D2(p, q).  Both passes are radix-2
+// decimation-in-time FFTs in shared memory with twiddles from a host-computed table.
+//
+// Inverse transform: Vhat(k_m) for 0 <= m <= N/2 from the split solutions x_+/x_-,
+// completed by Vhat(-k_m) = conj Vhat(k_m) (eq. VSym), then
+// V(x, z) = (1/N) sum_m Vhat(k_m, z) e^{+i k_m x}, real part.
+//
+// Forward model (eqs. DMV/M read forward): D2(p, q) = s_f sum_j g(k_p,z_j) g(k_q,z_j)
+// Vhat(k_p - k_q, z_j), then the inverse of the data transform.
+#include "edt_internal.h"
+#include "cplx.cuh"
+
+namespace edt {
+
+namespace {
+
+__device__ __forceinline__ int bitrev(int i, int logn) { return int(__brev(unsigned(i)) >> (32 - logn)); }
+__host__ __device__ __forceinline__ int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+template <typename T> __device__ __forceinline__ const cplx_t<T>* twid(const Dev& d);
+template <> __device__ __forceinline__ const float2* twid<float>(const Dev& d) { return d.tw32; }
+template <> __device__ __forceinline__ const double2* twid<double>(const Dev& d) { return d.tw64; }
+
+template <typename T2> __device__ __forceinline__ T2 load_c(const void* p, int dtype, size_t i);
+template <> __device__ __forceinline__ float2 load_c<float2>(const void* p, int dtype, size_t i) {
+  if (dtype == EDT_C64) return reinterpret_cast<const float2*>(p)[i];
+  double2 v = reinterpret_cast<const double2*>(p)[i];
+  return make_float2(float(v.x), float(v.y));
+}
+template <> __device__ __forceinline__ double2 load_c<double2>(const void* p, int dtype, size_t i) {
+  if (dtype == EDT_C128) return reinterpret_cast<const double2*>(p)[i];
+  float2 v = reinterpret_cast<const float2*>(p)[i];
+  return make_double2(double(v.x), double(v.y));
+}
+template <typename T2> __device__ __forceinline__ void store_c(void* p, int dtype, size_t i, T2 v) {
+  if (dtype == EDT_C64) reinterpret_cast<float2*>(p)[i] = make_float2(float(v.x), float(v.y));
+  else reinterpret_cast<double2*>(p)[i] = make_double2(double(v.x), double(v.y));
+}
+
+// In-place radix-2 DIT butterflies over `batch` sequences of length N held in shared
+// memory in bit-reversed order; sequence b starts at s + b * bstride.  sign = -1 uses
+// e^{-2 pi i k/N}, sign = +1 its conjugate.  All threads of the block participate.
+template <typename T, typename T2>
+__device__ void block_fft(T2* s, int N, int batch, int bstride, const T2* tw, int sign) {
+  const int half = N >> 1;
+  const int total = half * batch;
+  for (int h = 1; h < N; h <<= 1) {
+    const int step = N / (2 * h);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      int b = t / half, j = t - b * half;
+      int grp = j / h, jj = j - grp * h;
+      int i0 = grp * 2 * h + jj, i1 = i0 + h;
+      T2 w = tw[jj * step];
+      if (sign > 0) w.y = -w.y;
+      T2* base = s + b * bstride;
+      T2 u = base[i0], v = base[i1] * w;
+      base[i0] = u + v;
+      base[i1] = u - v;
+    }
+    __syncthreads();
+  }
+}
+
+// Row FFTs: rows of length N at stride N; each block handles `rpb` consecutive rows.
+template <typename T>
+__global__ void fft_rows_kernel(Dev d, const void* in, int in_dtype, void* out, int out_dtype,
+                                long long nrows, int rpb, int sign, T scale) {
+  using T2 = cplx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* s = reinterpret_cast<T2*>(smem_raw);
+  const int N = d.N, logn = ilog2(N);
+  const long long r0 = (long long)blockIdx.x * rpb;
+  const int nr = int(min((long long)rpb, nrows - r0));
+  for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
+    int r = e / N, i = e - r * N;
+    s[r * N + bitrev(i, logn)] = load_c<T2>(in, in_dtype, size_t(r0) * N + e);
+  }
+  __syncthreads();
+  block_fft<T, T2>(s, N, nr, N, twid<T>(d), sign);
+  for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
+    T2 v = s[e];
+    store_c<T2>(out, out_dtype, size_t(r0) * N + e, cmk(v.x * scale, v.y * scale));
+  }
+}
+
+// Column FFTs of [planes][N][N] (transform along the first index), in place; each block
+// takes `cpb` adjacent columns of one plane (a 128-byte row segment).
+template <typename T>
+__global__ void fft_cols_kernel(Dev d, cplx_t<T>* X, int cpb, int sign, T scale) {
+  using T2 = cplx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* s = reinterpret_cast<T2*>(smem_raw);
+  const int N = d.N, logn = ilog2(N), ld = N + 1;
+  const int c0 = blockIdx.x * cpb;
+  T2* P = X + size_t(blockIdx.y) * N * N;
+  for (int e = threadIdx.x; e < N * cpb; e += blockDim.x) {
+    int r = e / cpb, c = e - r * cpb;
+    s[c * ld + bitrev(r, logn)] = P[size_t(r) * N + c0 + c];
+  }
+  __syncthreads();
+  block_fft<T, T2>(s, N, cpb, ld, twid<T>(d), sign);
+  for (int e = threadIdx.x; e < N * cpb; e += blockDim.x) {
+    int r = e / cpb, c = e - r * cpb;
+    T2 v = s[c * ld + r];
+    P[size_t(r) * N + c0 + c] = cmk(v.x * scale, v.y * scale);
+  }
+}
+
+template <typename T>
+cudaError_t rows_fft(const Dev& d, const void* in, int in_dtype, void* out, int out_dtype,
+                     long long nrows, int sign, T scale, cudaStream_t st) {
+  using T2 = cplx_t<T>;
+  int rpb = (int(sizeof(T)) == 4 ? 4096 : 2048) / d.N;
+  if (rpb < 1) rpb = 1;
+  size_t smem = size_t(rpb) * d.N * sizeof(T2);
+  cudaFuncSetAttribute(fft_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  long long nb = (nrows + rpb - 1) / rpb;
+  fft_rows_kernel<T><<<unsigned(nb), 256, smem, st>>>(d, in, in_dtype, out, out_dtype, nrows, rpb,
+                                                      sign, scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cols_fft(const Dev& d, cplx_t<T>* X, int planes, int sign, T scale, cudaStream_t st) {
+  using T2 = cplx_t<T>;
+  int cpb = 128 / int(sizeof(T2));
+  if (cpb > d.N) cpb = d.N;
+  size_t smem = size_t(cpb) * (d.N + 1) * sizeof(T2);
+  cudaFuncSetAttribute(fft_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  dim3 g(d.N / cpb, planes);
+  fft_cols_kernel<T><<<g, 256, smem, st>>>(d, X, cpb, sign, scale);
+  return cudaGetLastError();
+}
+
+// ---- inverse transform ------------------------------------------------------------------
+constexpr int INV_ZT = 8;
+
+__global__ void inverse_kernel(Dev d, void* V, int V_dtype) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* s = reinterpret_cast<double2*>(smem_raw);
+  const int N = d.N, logn = ilog2(N), ld = N + 1, half = N / 2;
+  const int z0 = blockIdx.x * INV_ZT;
+  const int nzt = min(INV_ZT, d.nz - z0);
+  for (int e = threadIdx.x; e < (half + 1) * nzt; e += blockDim.x) {
+    int m = e / nzt, t = e - m * nzt;
+    int z = z0 + t;
+    const double* xm = d.x + (size_t(m) * d.nz + z) * 2;
+    double re = xm[0];
+    double im = (m == 0 || m == half) ? 0.0 : xm[1];
+    if (d.status[m] != EDT_OK) { re = 0.0; im = 0.0; }
+    d.vhat[size_t(m) * d.nz + z] = make_double2(re, im);
+    s[t * ld + bitrev(m, logn)] = make_double2(re, im);
+    if (m > 0 && m < half) s[t * ld + bitrev(N - m, logn)] = make_double2(re, -im);
+  }
+  __syncthreads();
+  block_fft<double, double2>(s, N, nzt, ld, d.tw64, +1);
+  const double inv = 1.0 / double(N);
+  for (int e = threadIdx.x; e < N * nzt; e += blockDim.x) {
+    int xi = e / nzt, t = e - xi * nzt;
+    double v = s[t * ld + xi].x * inv;
+    size_t o = size_t(xi) * d.nz + z0 + t;
+    if (V_dtype == EDT_F64) reinterpret_cast<double*>(V)[o] = v;
+    else reinterpret_cast<float*>(V)[o] = float(v);
+  }
+}
+
+// ---- forward model -------------------------------------------------------------------------
+// Vhat(k_m, z) = sum_x V(x, z) e^{-i k_m x} for all m: one block per z tile.
+__global__ void lateral_dft_kernel(Dev d, const void* V, int V_dtype) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* s = reinterpret_cast<double2*>(smem_raw);
+  const int N = d.N, logn = ilog2(N), ld = N + 1;
+  const int z0 = blockIdx.x * INV_ZT;
+  const int nzt = min(INV_ZT, d.nz - z0);
+  for (int e = threadIdx.x; e < N * nzt; e += blockDim.x) {
+    int xi = e / nzt, t = e - xi * nzt;
+    size_t o = size_t(xi) * d.nz + z0 + t;
+    double v = V_dtype == EDT_F64 ? reinterpret_cast<const double*>(V)[o]
+                                  : double(reinterpret_cast<const float*>(V)[o]);
+    s[t * ld + bitrev(xi, logn)] = make_double2(v, 0.0);
+  }
+  __syncthreads();
+  block_fft<double, double2>(s, N, nzt, ld, d.tw64, -1);
+  for (int e = threadIdx.x; e < N * nzt; e += blockDim.x) {
+    int m = e / nzt, t = e - m * nzt;
+    d.vfull[size_t(m) * d.nz + z0 + t] = s[t * ld + m];
+  }
+}
+
+// D2[f][q][p] = s_f sum_j g(|p'|, j) g(|q'|, j) Vhat((p - q) mod N, j): 16 x 16 (p, q) tile
+// per block, depth in chunks of 32 staged in shared memory.
+template <typename T>
+__global__ void born_spectral_kernel(Dev d, cplx_t<T>* X) {
+  using T2 = cplx_t<T>;
+  constexpr int TP = 16, ZC = 32;
+  __shared__ double2 gp[TP][ZC], gq[TP][ZC], vh[2 * TP][ZC];
+  const int N = d.N, f = blockIdx.z;
+  const int p0 = blockIdx.x * TP, q0 = blockIdx.y * TP;
+  const int tp = threadIdx.x & (TP - 1), tq = threadIdx.x / TP;
+  double2 acc = make_double2(0.0, 0.0);
+  const double2* g = d.g64 + size_t(f) * d.nk * d.nz;
+  for (int zc = 0; zc < d.nz; zc += ZC) {
+    for (int e = threadIdx.x; e < TP * ZC; e += blockDim.x) {
+      int i = e / ZC, j = e - i * ZC, z = zc + j;
+      int pa = p0 + i, qa = q0 + i;
+      int np = pa <= N / 2 ? pa : N - pa, nq = qa <= N / 2 ? qa : N - qa;
+      gp[i][j] = z < d.nz ? g[size_t(np) * d.nz + z] : make_double2(0.0, 0.0);
+      gq[i][j] = z < d.nz ? g[size_t(nq) * d.nz + z] : make_double2(0.0, 0.0);
+    }
+    for (int e = threadIdx.x; e < 2 * TP * ZC; e += blockDim.x) {
+      int i = e / ZC, j = e - i * ZC, z = zc + j;
+      int m = (p0 - q0 - (TP - 1) + i) & (N - 1);     // m = p - q covers [p0-q0-15, p0-q0+15]
+      vh[i][j] = z < d.nz ? d.vfull[size_t(m) * d.nz + z] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const int mi = tp - tq + (TP - 1);
+#pragma unroll 4
+    for (int j = 0; j < ZC; ++j) acc = acc + gp[tp][j] * gq[tq][j] * vh[mi][j];
+    __syncthreads();
+  }
+  const FreqConst fc = d.fc[f];
+  double2 om = make_double2(fc.om_re, fc.om_im);
+  double2 sf = (d.dz / d.dx) * (om * om);
+  acc = sf * acc;
+  X[size_t(f) * N * N + size_t(q0 + tq) * N + p0 + tp] = cmk(T(acc.x), T(acc.y));
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, cudaStream_t s) {
+  using T2 = cplx_t<T>;
+  const int out_dtype = sizeof(T) == 4 ? EDT_C64 : EDT_C128;
+  cudaError_t e = rows_fft<T>(d, D, D_dtype, d.X, out_dtype, (long long)d.nf * d.N, -1, T(1), s);
+  if (e != cudaSuccess) return e;
+  return cols_fft<T>(d, reinterpret_cast<T2*>(d.X), d.nf, +1, T(1), s);
+}
+template cudaError_t launch_transform<float>(const Dev&, const void*, int, cudaStream_t);
+template cudaError_t launch_transform<double>(const Dev&, const void*, int, cudaStream_t);
+
+cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s) {
+  size_t smem = size_t(INV_ZT) * (d.N + 1) * sizeof(double2);
+  cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  inverse_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
+                           cudaStream_t s) {
+  size_t smem = size_t(INV_ZT) * (d.N + 1) * sizeof(double2);
+  cudaFuncSetAttribute(lateral_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  lateral_dft_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 g(d.N / 16, d.N / 16, d.nf);
+  if (d.precision == EDT_FP64) {
+    born_spectral_kernel<double><<<g, 256, 0, s>>>(d, reinterpret_cast<double2*>(d.X));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // inverse of the data transform: undo pass 2 (sign -, 1/N), then pass 1 (sign +, 1/N)
+    if ((e = cols_fft<double>(d, reinterpret_cast<double2*>(d.X), d.nf, -1, 1.0 / d.N, s)) != cudaSuccess)
+      return e;
+    return rows_fft<double>(d, d.X, EDT_C128, D, D_dtype, (long long)d.nf * d.N, +1, 1.0 / d.N, s);
+  }
+  born_spectral_kernel<float><<<g, 256, 0, s>>>(d, reinterpret_cast<float2*>(d.X));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cols_fft<float>(d, reinterpret_cast<float2*>(d.X), d.nf, -1, 1.0f / d.N, s)) != cudaSuccess)
+    return e;
+  return rows_fft<float>(d, d.X, EDT_C64, D, D_dtype, (long long)d.nf * d.N, +1, 1.0f / d.N, s);
+}
+
+}  // namespace edt

@@ -1,0 +1,283 @@
+"""Thin ctypes binding of the C ABI in ``include/edt.h`` (argument marshalling only).
+
+Every computation runs in ``_lib/libedt.so``; torch is used here only to own device
+memory (the workspace and the caller's tensors) and to supply CUDA streams.  Loading
+fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libedt.so")
+
+EDT_OK, EDT_EINVAL, EDT_ENOMEM_WS, EDT_ENOTPD = 0, -1, -2, -3
+EDT_ETIMEOUT, EDT_ENONFINITE, EDT_ECUDA, EDT_EUNSUPPORTED = -4, -5, -6, -7
+EDT_FP64, EDT_MIXED = 0, 1
+EDT_C64, EDT_C128, EDT_F32, EDT_F64 = 0, 1, 2, 3
+
+
+class edt_config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("dx", C.c_double),
+        ("nz", C.c_int), ("dz", C.c_double), ("z0", C.c_double),
+        ("nfreq", C.c_int), ("freq_hz", C.POINTER(C.c_double)), ("eps", C.c_double),
+        ("nlayer", C.c_int), ("layer_top_m", C.POINTER(C.c_double)),
+        ("layer_vel_mps", C.POINTER(C.c_double)),
+        ("precision", C.c_int), ("passes", C.c_int), ("refine", C.c_int),
+        ("alpha", C.c_double), ("cutoff", C.c_double), ("fold", C.c_int),
+    ]
+
+
+class edt_stats(C.Structure):
+    _fields_ = [
+        ("n_sub", C.c_int), ("rows_total", C.c_longlong), ("rows_solved", C.c_longlong),
+        ("rows_min", C.c_int), ("rows_max", C.c_int), ("workspace_bytes", C.c_size_t),
+        ("gram_flop", C.c_double), ("n_notpd", C.c_int), ("n_nonfinite", C.c_int),
+        ("last_status", C.c_int),
+    ]
+
+
+class EdtError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib().edt_strerror(code).decode()
+        if code == EDT_ECUDA:
+            msg += ": " + _lib().edt_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+_LIB: Optional[C.CDLL] = None
+
+
+def _lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_0905_0238_gb300.build.build() (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        vp, i, sz = C.c_void_p, C.c_int, C.c_size_t
+        L.edt_create.argtypes = [C.POINTER(vp), C.POINTER(edt_config), C.POINTER(sz)]
+        L.edt_set_workspace.argtypes = [vp, vp, sz]
+        L.edt_invert.argtypes = [vp, vp, i, vp, i, vp]
+        L.edt_invert_host.argtypes = [vp, vp, i, vp, i, vp]
+        L.edt_forward.argtypes = [vp, vp, i, vp, i, vp]
+        L.edt_green.argtypes = [vp, vp, vp]
+        L.edt_get_vhat.argtypes = [vp, vp, vp]
+        L.edt_row_counts.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.edt_get_stats.argtypes = [vp, C.POINTER(edt_stats)]
+        L.edt_set_profiling.argtypes = [vp, i]
+        L.edt_read_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_char_p), i,
+                                       C.POINTER(i)]
+        L.edt_strerror.argtypes = [i]
+        L.edt_strerror.restype = C.c_char_p
+        L.edt_last_cuda_error.restype = C.c_char_p
+        L.edt_destroy.argtypes = [vp]
+        L.edt_destroy.restype = None
+        for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
+                     "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts",
+                     "edt_get_stats", "edt_set_profiling", "edt_read_profile"):
+            getattr(L, name).restype = i
+        _LIB = L
+    return _LIB
+
+
+def _check(code: int, where: str) -> int:
+    if code < 0:
+        raise EdtError(code, where)
+    return code
+
+
+# ---- raw C-ABI calls with the same names -------------------------------------------------
+def edt_create(cfg: edt_config):
+    ctx, ws = C.c_void_p(), C.c_size_t()
+    _check(_lib().edt_create(C.byref(ctx), C.byref(cfg), C.byref(ws)), "edt_create")
+    return ctx, ws.value
+
+
+def edt_set_workspace(ctx, ptr: int, nbytes: int):
+    _check(_lib().edt_set_workspace(ctx, C.c_void_p(ptr), nbytes), "edt_set_workspace")
+
+
+def edt_invert(ctx, D_ptr: int, D_dtype: int, V_ptr: int, V_dtype: int, stream: int):
+    _check(_lib().edt_invert(ctx, C.c_void_p(D_ptr), D_dtype, C.c_void_p(V_ptr), V_dtype,
+                             C.c_void_p(stream)), "edt_invert")
+
+
+def edt_invert_host(ctx, D_ptr: int, D_dtype: int, V_ptr: int, V_dtype: int, stream: int):
+    _check(_lib().edt_invert_host(ctx, C.c_void_p(D_ptr), D_dtype, C.c_void_p(V_ptr), V_dtype,
+                                  C.c_void_p(stream)), "edt_invert_host")
+
+
+def edt_forward(ctx, V_ptr: int, V_dtype: int, D_ptr: int, D_dtype: int, stream: int):
+    _check(_lib().edt_forward(ctx, C.c_void_p(V_ptr), V_dtype, C.c_void_p(D_ptr), D_dtype,
+                              C.c_void_p(stream)), "edt_forward")
+
+
+def edt_green(ctx, g_ptr: int, stream: int):
+    _check(_lib().edt_green(ctx, C.c_void_p(g_ptr), C.c_void_p(stream)), "edt_green")
+
+
+def edt_get_vhat(ctx, ptr: int, stream: int):
+    _check(_lib().edt_get_vhat(ctx, C.c_void_p(ptr), C.c_void_p(stream)), "edt_get_vhat")
+
+
+def edt_row_counts(ctx, nsub: int) -> np.ndarray:
+    out = (C.c_longlong * nsub)()
+    _check(_lib().edt_row_counts(ctx, out), "edt_row_counts")
+    return np.array(out[:], dtype=np.int64)
+
+
+def edt_get_stats(ctx) -> edt_stats:
+    st = edt_stats()
+    _check(_lib().edt_get_stats(ctx, C.byref(st)), "edt_get_stats")
+    return st
+
+
+def edt_set_profiling(ctx, on: bool):
+    _check(_lib().edt_set_profiling(ctx, int(bool(on))), "edt_set_profiling")
+
+
+def edt_read_profile(ctx, max_stages: int = 8):
+    ms = (C.c_double * max_stages)()
+    names = (C.c_char_p * max_stages)()
+    ncalls = C.c_int()
+    n = _check(_lib().edt_read_profile(ctx, ms, names, max_stages, C.byref(ncalls)),
+               "edt_read_profile")
+    return {names[i].decode(): ms[i] for i in range(n)}, ncalls.value
+
+
+def edt_destroy(ctx):
+    if ctx:
+        _lib().edt_destroy(ctx)
+
+
+# ---- convenience wrapper owning the workspace ---------------------------------------------
+@dataclass
+class Config:
+    nx: int
+    dx: float
+    nz: int
+    dz: float
+    z0: float
+    freq_hz: Sequence[float]
+    eps: float
+    layer_top: Sequence[float]
+    layer_vel: Sequence[float]
+    precision: int = EDT_FP64
+    passes: int = 1
+    refine: int = 1
+    alpha: float = 1e-2
+    cutoff: float = 1.0
+    fold: int = 1
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        base = dict(nx=wl.nx, dx=wl.dx, nz=wl.nz, dz=wl.dz, z0=wl.z0, freq_hz=wl.freq_hz,
+                    eps=wl.eps, layer_top=wl.layer_top, layer_vel=wl.layer_vel,
+                    alpha=wl.alpha, cutoff=wl.cutoff)
+        base.update(kw)
+        return cls(**base)
+
+
+class Solver:
+    """A context plus a torch-owned workspace on the current CUDA device."""
+
+    def __init__(self, cfg: Config, device=None):
+        import torch
+        self._torch = torch
+        self.cfg = cfg
+        self._freq = np.ascontiguousarray(cfg.freq_hz, dtype=np.float64)
+        self._top = np.ascontiguousarray(cfg.layer_top, dtype=np.float64)
+        self._vel = np.ascontiguousarray(cfg.layer_vel, dtype=np.float64)
+        dp = C.POINTER(C.c_double)
+        c = edt_config(
+            nx=cfg.nx, dx=cfg.dx, nz=cfg.nz, dz=cfg.dz, z0=cfg.z0,
+            nfreq=len(self._freq), freq_hz=self._freq.ctypes.data_as(dp), eps=cfg.eps,
+            nlayer=len(self._top), layer_top_m=self._top.ctypes.data_as(dp),
+            layer_vel_mps=self._vel.ctypes.data_as(dp), precision=cfg.precision,
+            passes=cfg.passes, refine=cfg.refine, alpha=cfg.alpha, cutoff=cfg.cutoff,
+            fold=cfg.fold)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.ctx = None
+        self.ctx, self.ws_bytes = edt_create(c)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        edt_set_workspace(self.ctx, self.workspace.data_ptr(), self.ws_bytes)
+        self.nsub = cfg.nx // 2 + 1
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            edt_destroy(self.ctx)
+            self.ctx = None
+
+    def _stream(self):
+        return self._torch.cuda.current_stream(self.device).cuda_stream
+
+    @staticmethod
+    def _cdtype(t):
+        import torch
+        return {torch.complex64: EDT_C64, torch.complex128: EDT_C128}[t.dtype]
+
+    @staticmethod
+    def _rdtype(t):
+        import torch
+        return {torch.float32: EDT_F32, torch.float64: EDT_F64}[t.dtype]
+
+    def invert(self, D, out=None, out_dtype=None):
+        torch = self._torch
+        assert D.is_cuda and D.is_contiguous()
+        nf = len(self._freq)
+        assert tuple(D.shape) == (nf, self.cfg.nx, self.cfg.nx)
+        if out is None:
+            out = torch.empty((self.cfg.nx, self.cfg.nz), device=self.device,
+                              dtype=out_dtype or torch.float64)
+        edt_invert(self.ctx, D.data_ptr(), self._cdtype(D), out.data_ptr(), self._rdtype(out),
+                   self._stream())
+        return out
+
+    def invert_host(self, D_host, V_host):
+        """Host-buffer entry point: copies in, inverts, copies out on the current stream."""
+        edt_invert_host(self.ctx, D_host.data_ptr(), self._cdtype(D_host), V_host.data_ptr(),
+                        self._rdtype(V_host), self._stream())
+        return V_host
+
+    def forward(self, V, out_dtype=None):
+        torch = self._torch
+        nf = len(self._freq)
+        D = torch.empty((nf, self.cfg.nx, self.cfg.nx), device=self.device,
+                        dtype=out_dtype or torch.complex128)
+        edt_forward(self.ctx, V.data_ptr(), self._rdtype(V), D.data_ptr(), self._cdtype(D),
+                    self._stream())
+        return D
+
+    def green(self):
+        torch = self._torch
+        nf = len(self._freq)
+        g = torch.empty((nf, self.cfg.nx // 2 + 1, self.cfg.nz), device=self.device,
+                        dtype=torch.complex128)
+        edt_green(self.ctx, g.data_ptr(), self._stream())
+        return g
+
+    def vhat(self):
+        torch = self._torch
+        v = torch.empty((self.nsub, self.cfg.nz), device=self.device, dtype=torch.complex128)
+        edt_get_vhat(self.ctx, v.data_ptr(), self._stream())
+        return v
+
+    def row_counts(self):
+        return edt_row_counts(self.ctx, self.nsub)
+
+    def stats(self):
+        return edt_get_stats(self.ctx)
+
+    def set_profiling(self, on=True):
+        edt_set_profiling(self.ctx, on)
+
+    def read_profile(self):
+        return edt_read_profile(self.ctx)
