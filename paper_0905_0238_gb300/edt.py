@@ -231,9 +231,9 @@ class Solver:
 
     def invert(self, D, out=None, out_dtype=None):
         torch = self._torch
-        assert D.is_cuda and D.is_contiguous()
         nf = len(self._freq)
-        assert tuple(D.shape) == (nf, self.cfg.nx, self.cfg.nx)
+        if not (D.is_cuda and D.is_contiguous()) or tuple(D.shape) != (nf, self.cfg.nx, self.cfg.nx):
+            raise ValueError("D must be a contiguous CUDA tensor of shape (nfreq, nx, nx)")
         if out is None:
             out = torch.empty((self.cfg.nx, self.cfg.nz), device=self.device,
                               dtype=out_dtype or torch.float64)

@@ -23,3 +23,9 @@ def blobs(wl, salt=0):
     rng = synth.rng_for(0, salt=salt)
     return synth.perturbation_blobs(rng, wl.nx, wl.dx, wl.nz, wl.dz, wl.z0, wl.layer_top,
                                     wl.layer_vel, nblob=3, sigma=30.0, amp=0.05)
+
+
+def dev(a):
+    """A contiguous CUDA tensor copy of a numpy array."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()

@@ -10,7 +10,7 @@ import pytest
 
 import synth
 from oracle import edt2d
-from tests.gpu_helpers import rel_l2, small_workload, blobs
+from tests.gpu_helpers import rel_l2, small_workload, blobs, dev
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -58,7 +58,7 @@ def test_invert_small_2d_matches_oracle(fold):
     D = edt2d.forward(wl, V)
     V_or, vh_or = edt2d.invert(wl, D)
     s = solver(wl, fold=fold)
-    V_gpu = s.invert(torch.from_numpy(D).cuda()).cpu().numpy()
+    V_gpu = s.invert(dev(D)).cpu().numpy()
     vh_gpu = s.vhat().cpu().numpy()
     st = s.stats()
     assert st.n_notpd == 0 and st.n_nonfinite == 0
@@ -74,7 +74,7 @@ def test_invert_ragged_matches_oracle(nx, nz, nf, cutoff):
     D = synth.random_data(rng, (nf, nx, nx))
     V_or, vh_or = edt2d.invert(wl, D)
     s = solver(wl)
-    V_gpu = s.invert(torch.from_numpy(D).cuda()).cpu().numpy()
+    V_gpu = s.invert(dev(D)).cpu().numpy()
     assert rel_l2(s.vhat().cpu().numpy(), vh_or) < 1e-10
     assert rel_l2(V_gpu, V_or) < 1e-10
 
@@ -84,7 +84,7 @@ def test_invert_complex64_input_and_float32_output():
     D = synth.random_data(synth.rng_for(0, salt=6), (4, 32, 32), np.complex64)
     V_or, _ = edt2d.invert(wl, D.astype(np.complex128))
     s = solver(wl)
-    V32 = s.invert(torch.from_numpy(D).cuda(), out_dtype=torch.float32).cpu().numpy()
+    V32 = s.invert(dev(D), out_dtype=torch.float32).cpu().numpy()
     assert V32.dtype == np.float32
     assert rel_l2(V32, V_or) < 1e-6
 
@@ -110,7 +110,7 @@ def test_empty_subproblems_are_zero():
     assert (counts == 0).any()
     D = synth.random_data(synth.rng_for(0, salt=8), (2, 64, 64))
     _, vh_or = edt2d.invert(wl, D)
-    s.invert(torch.from_numpy(D).cuda())
+    s.invert(dev(D))
     vh = s.vhat().cpu().numpy()
     assert np.all(vh[counts == 0] == 0)
     assert rel_l2(vh, vh_or) < 1e-10
