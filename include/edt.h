@@ -145,8 +145,16 @@ int edt_forward(edt_ctx* ctx, const void* V_dev, int V_dtype, void* D_dev, int D
 int edt_green(edt_ctx* ctx, void* g_dev, void* stream);
 
 /* Copy Vhat(k_m, z_j) of the last edt_invert on this context, m = 0..nx/2, as
- * complex128 [nx/2+1][nz], into g_dev-like caller memory. */
+ * complex128 [nx/2+1][nz], into caller device memory. */
 int edt_get_vhat(edt_ctx* ctx, void* vhat_dev, void* stream);
+
+/* Stages up to the normal matrices only (depth march, data transform, split right-hand
+ * sides, Gram): writes G = Ahat^T W Ahat as double [nx/2+1][nz][nz], b = Ahat^T W dhat as
+ * double [nx/2+1][nz][2] (columns d_+, d_-) and trace(G) as double [nx/2+1], where W holds
+ * the row weights (2 for merged reciprocal rows).  For EDT_MIXED these are the tensor-core
+ * results (BF16 operands, FP32 accumulation) and the FP64 trace used for the damping. */
+int edt_gram(edt_ctx* ctx, const void* D_dev, int D_dtype, void* G_dev, void* b_dev,
+             void* trace_dev, void* stream);
 
 /* Per-subproblem complex row counts after the cut (before folding): counts[nx/2+1]. */
 int edt_row_counts(const edt_ctx* ctx, long long* counts);

@@ -256,7 +256,21 @@ __global__ void __launch_bounds__(256) refine_update_kernel(Dev d) {
   if (threadIdx.x == 0 && bad) d.status[m] = EDT_ENONFINITE;
 }
 
+__global__ void trace_diag_kernel(Dev d) {
+  __shared__ double red[40];
+  const int m = blockIdx.x, n = d.nz;
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += d.G[size_t(m) * n * n + size_t(i) * n + i];
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) d.trace[m] = t;
+}
+
 }  // namespace
+
+cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s) {
+  trace_diag_kernel<<<d.nsub, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
   size_t smem = (size_t(d.nz) * LDP + NB * LDP + 2 * d.nz + 40) * sizeof(double);

@@ -90,6 +90,8 @@ int validate(const edt_config* c) {
     if (c->passes != 1 && c->passes != 3) return EDT_EINVAL;
     if (c->refine < 0 || c->refine > 4) return EDT_EINVAL;
     if (c->nz > 256) return EDT_EUNSUPPORTED;
+    // the tensor-core producer addresses the FP32 table with 32-bit element offsets
+    if (double(c->nfreq) * (c->nx / 2 + 1) * c->nz >= 4294967295.0) return EDT_EUNSUPPORTED;
   }
   if (!(c->alpha >= 0) || !std::isfinite(c->alpha)) return EDT_EINVAL;
   if (!std::isfinite(c->cutoff)) return EDT_EINVAL;
@@ -463,6 +465,30 @@ int edt_get_vhat(edt_ctx* c, void* vhat_dev, void* stream) {
   if (!c->ws) return EDT_ENOMEM_WS;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   EDT_TRY(cudaMemcpyAsync(vhat_dev, c->dev.vhat, c->r_vhat.bytes, cudaMemcpyDeviceToDevice, s));
+  return EDT_OK;
+}
+
+int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr, void* stream) {
+  if (!c || !D || !G || !b || !tr) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Dev& d = c->dev;
+  const bool mixed = c->cfg.precision == EDT_MIXED;
+  c->last_stream = s;
+  EDT_TRY(launch_green(d, s));
+  if (mixed) { EDT_TRY(launch_transform<float>(d, D, D_dtype, s)); EDT_TRY(launch_rhs<float>(d, s)); }
+  else { EDT_TRY(launch_transform<double>(d, D, D_dtype, s)); EDT_TRY(launch_rhs<double>(d, s)); }
+  if (mixed) {
+    EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
+    EDT_TRY(launch_gram_tc(d, s));
+  } else {
+    EDT_TRY(launch_gram_f64(d, s));
+    EDT_TRY(launch_trace_diag(d, s));
+  }
+  EDT_TRY(cudaMemcpyAsync(G, d.G, c->r_G.bytes, cudaMemcpyDeviceToDevice, s));
+  EDT_TRY(cudaMemcpyAsync(b, d.b, c->r_b.bytes, cudaMemcpyDeviceToDevice, s));
+  EDT_TRY(cudaMemcpyAsync(tr, d.trace, c->r_tr.bytes, cudaMemcpyDeviceToDevice, s));
   return EDT_OK;
 }
 

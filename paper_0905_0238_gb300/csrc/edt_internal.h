@@ -82,6 +82,7 @@ cudaError_t launch_rhs(const Dev& d, cudaStream_t s);
 
 cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);
+cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s);   // trace[m] = sum_z G[m][z][z]
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s);
 cudaError_t launch_refine(const Dev& d, cudaStream_t s);          // r += Ahat^T (dhat - Ahat x)
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s);   // x += (LL^T)^-1 (r - lam x)

@@ -1,7 +1,453 @@
-// placeholder until the tensor-core Gram lands
+// Tensor-core (tcgen05, sm_103a) augmented Gram of the split systems, mixed precision.
+//
+// For every midpoint index m the split least-squares problem of eq. Split has the
+// real-stacked matrix Ahat = [Re A; Im A] (rows: frequencies x receiver wavenumbers, one
+// complex row giving two real rows) and right-hand sides dhat_+-.  This kernel forms
+//     [Ahat | dhat_+ | dhat_-]^T [Ahat | dhat_+ | dhat_-]  restricted to the rows z < nz,
+// i.e. G = Ahat^T W Ahat and b_+- = Ahat^T W dhat_+-, with BF16 operands (optionally the
+// split hi + lo pair, three MMAs per product) and FP32 accumulation in tensor memory.
+//
+// Structure (one persistent CTA per SM, all subproblems in one launch):
+//   * rows of all subproblems are concatenated and split evenly over the CTAs; a CTA's
+//     range falls into 1..few "segments" (its part of one subproblem), each accumulated
+//     in TMEM and written out as an FP32 partial tile, summed per subproblem afterwards;
+//   * warps 0-3 are producers: for 32 complex rows per pipeline stage they rebuild the
+//     kernel rows a(z) = |s_f| g(k_p, z) g(k_q, z) from the L2-resident FP32 table of
+//     sqrt|s_f| g, scale weight-2 rows by sqrt 2, split into BF16 hi (and lo), and store
+//     them K-major with the 128-byte swizzle; (Re a, Im a) of one complex row are two
+//     adjacent K elements.  The data rows d_+, d_- occupy two extra operand rows;
+//   * warp 4 issues tcgen05.mma (M = 128, K = 16) from one thread: both operands are
+//     views of the same stage tile (A = depth rows of one 128-row half, B = all depth rows
+//     plus the data rows), so one generated tile feeds the whole upper block row;
+//   * after the last stage of a segment the producers read the accumulator with
+//     tcgen05.ld and write the partial tile; they also accumulate trace(G) in FP64 from the
+//     unrounded FP32 rows (the damping lam = alpha * trace(G) must not inherit BF16 error).
+// Every wait is bounded; on expiry the CTA raises a device flag and leaves cleanly.
 #include "edt_internal.h"
+#include "cplx.cuh"
+#include <cuda_bf16.h>
+
 namespace edt {
-int tc_cols(int nz) { return nz; }
-int tc_smem_bytes(int nz, int passes) { return 0; }
-cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s) { return cudaErrorNotSupported; }
+
+namespace {
+
+constexpr int PRODUCER_WARPS = 4;
+constexpr int NTHREADS = (PRODUCER_WARPS + 1) * 32;
+constexpr int ROWB = 128;                       // bytes per operand row per stage (64 bf16)
+constexpr long long WAIT_CYCLES = 4000000000ll; // ~2 s at 2 GHz: a wait longer than this gives up
+
+__host__ __device__ inline int nzp_of(int nz) { return (nz + 31) / 32 * 32; }
+__host__ __device__ inline int zrows_of(int nzp) {
+  int need = nzp + 16;
+  int mrows = nzp > TC_M ? 2 * TC_M : TC_M;
+  return need > mrows ? need : mrows;
 }
+__host__ __device__ inline int cols_of(int nzp) { return (nzp + 16) + (nzp > TC_M ? nzp - TC_M + 16 : 0); }
+__host__ __device__ inline int stages_of(int passes) { return passes == 1 ? 4 : 3; }
+
+struct RowEnt {
+  unsigned offp, offq;   // element offsets of the g rows (f, |p|) and (f, |q|)
+  float sw;              // sqrt(weight), 0 for padding rows
+  float pad;
+  float2 dp, dm;         // data rows times sqrt(weight)
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: returns false (and raises the abort flag) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) { *abort_flag = 1; return false; }
+  }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 inputs, FP32 accumulate)
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups of
+// 1024 bytes (stride byte offset), start address in 16-byte units.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFFu);
+  d |= uint64_t(1) << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;         // stride byte offset
+  d |= uint64_t(1) << 46;                 // descriptor version
+  d |= uint64_t(2) << 61;                 // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);   // .x -> lower address (smaller K)
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// byte offset of (operand row, 16-byte chunk) in a 128B-swizzled K-major stage tile
+__device__ __forceinline__ uint32_t sw_off(int row, int chunk) {
+  return uint32_t((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+template <int PASSES>
+__global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
+  constexpr int STAGES = PASSES == 1 ? 4 : 3;
+  constexpr int NCOMP = PASSES == 1 ? 1 : 2;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int nz = d.nz, nzp = nzp_of(nz), zr = zrows_of(nzp), ncols = cols_of(nzp);
+  const uint32_t stage_bytes = uint32_t(zr) * ROWB;
+
+  // carve shared memory: operand stages (1024-aligned), row tables, barriers
+  uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
+  unsigned char* ops = reinterpret_cast<unsigned char*>(base);
+  RowEnt* rowtab = reinterpret_cast<RowEnt*>(ops + size_t(STAGES) * NCOMP * stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rowtab + STAGES * TC_KC);
+  uint64_t* full = bars;                   // [STAGES] producers -> MMA
+  uint64_t* empty = bars + STAGES;         // [STAGES] MMA commit -> producers
+  uint64_t* acc_full = bars + 2 * STAGES;  // MMA commit -> epilogue
+  uint64_t* acc_empty = acc_full + 1;      // epilogue -> MMA
+  uint64_t* drain = acc_empty + 1;         // final commit: every issued MMA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cta = blockIdx.x;
+  const int s0 = d.cta_seg0[cta], s1 = d.cta_seg0[cta + 1];
+  const int* slots = d.cta_seg0 + d.ncta_gram + 1;
+
+  // zero every operand stage once: padding rows stay zero for the whole kernel
+  {
+    uint4* z4 = reinterpret_cast<uint4*>(ops);
+    const size_t n16 = size_t(STAGES) * NCOMP * stage_bytes / 16;
+    for (size_t i = threadIdx.x; i < n16; i += NTHREADS) z4[i] = make_uint4(0, 0, 0, 0);
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], PRODUCER_WARPS * 32); mbar_init(&empty[s], 1); }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, PRODUCER_WARPS * 32);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  uint32_t alloc_cols = 32;
+  while (alloc_cols < uint32_t(ncols)) alloc_cols <<= 1;
+  if (warp == PRODUCER_WARPS) tmem_alloc(tmem_slot, alloc_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == PRODUCER_WARPS) {
+    // ------------------------------------------------------------ MMA issuer
+    // instruction list: (A first row, B first row, N, TMEM column)
+    int ia[3], ib[3], in_[3], ic[3], ni = 0;
+    {
+      int n0 = nzp + 16;
+      ia[ni] = 0; ib[ni] = 0; in_[ni] = n0 > 256 ? 256 : n0; ic[ni] = 0; ++ni;
+      if (n0 > 256) { ia[ni] = 0; ib[ni] = 256; in_[ni] = n0 - 256; ic[ni] = 256; ++ni; }
+      if (nzp > TC_M) { ia[ni] = TC_M; ib[ni] = TC_M; in_[ni] = nzp - TC_M + 16; ic[ni] = n0; ++ni; }
+    }
+    const uint32_t ops_s = smem_u32(ops);
+    long long it = 0;
+    bool ok = true;
+    for (int si = s0; si < s1 && ok; ++si) {
+      const int slot = slots[si];
+      const long long nrow = d.seg_nrow[slot];
+      const long long nst = (nrow + TC_KC - 1) / TC_KC;
+      const int k = si - s0;
+      if (k > 0) {
+        if (!mbar_wait(acc_empty, unsigned((k - 1) & 1), abort_flag)) { ok = false; break; }
+        tc_fence_after();
+      }
+      for (long long st = 0; st < nst; ++st, ++it) {
+        const int s = int(it % STAGES);
+        if (!mbar_wait(&full[s], unsigned((it / STAGES) & 1), abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t hi = ops_s + uint32_t(s) * NCOMP * stage_bytes;
+          const uint32_t lo = hi + stage_bytes;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            for (int i = 0; i < ni; ++i) {
+              const uint32_t ao = uint32_t(ia[i]) * ROWB + kk * 32, bo = uint32_t(ib[i]) * ROWB + kk * 32;
+              const uint32_t idesc = idesc_bf16(TC_M, in_[i]);
+              const uint32_t dt = tmem + uint32_t(ic[i]);
+              const uint32_t acc0 = (st > 0 || kk > 0) ? 1u : 0u;
+              mma_bf16(dt, sw128_desc(hi + ao), sw128_desc(hi + bo), idesc, acc0);
+              if (PASSES == 3) {
+                mma_bf16(dt, sw128_desc(hi + ao), sw128_desc(lo + bo), idesc, 1u);
+                mma_bf16(dt, sw128_desc(lo + ao), sw128_desc(hi + bo), idesc, 1u);
+              }
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(acc_full);
+      __syncwarp();
+    }
+    // drain: wait (bounded, independent of the abort flag) until every issued MMA is done
+    if (lane == 0) {
+      mma_commit(drain);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(drain, 0u) && clock64() - t0 < WAIT_CYCLES) {
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ producers + epilogue
+    const int ptid = threadIdx.x;                 // 0..127
+    const int nunits = (nzp / 32) * 8;            // (32-depth group, 16-byte K chunk)
+    const int N = d.N, msk = N - 1;
+    const float2* g32 = d.g32;
+    long long it = 0;
+    bool ok = true;
+    for (int si = s0; si < s1 && ok; ++si) {
+      const int slot = slots[si];
+      const int m = d.seg_m[slot];
+      const long long row0 = d.seg_row0[slot], nrow = d.seg_nrow[slot];
+      const long long nst = (nrow + TC_KC - 1) / TC_KC;
+      double tr = 0.0;
+      for (long long st = 0; st < nst; ++st, ++it) {
+        const int s = int(it % STAGES);
+        if (it >= STAGES) {
+          if (!mbar_wait(&empty[s], unsigned(((it / STAGES) - 1) & 1), abort_flag)) { ok = false; break; }
+        }
+        RowEnt* rt = rowtab + s * TC_KC;
+        if (ptid < TC_KC) {
+          const long long r = st * TC_KC + ptid;
+          RowEnt e;
+          if (r < nrow) {
+            const uint32_t row = d.rows[row0 + r];
+            const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
+            const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
+            e.offp = unsigned((size_t(f) * d.nk + np) * nz);
+            e.offq = unsigned((size_t(f) * d.nk + nq) * nz);
+            e.sw = row_w2(row) ? 1.41421356237309515f : 1.0f;
+            const float2* rh = reinterpret_cast<const float2*>(d.rhs) + 2 * (row0 + r);
+            const float2 a = rh[0], b = rh[1];
+            e.dp = make_float2(e.sw * a.x, e.sw * a.y);
+            e.dm = make_float2(e.sw * b.x, e.sw * b.y);
+          } else {
+            e.offp = e.offq = 0; e.sw = 0.f; e.dp = e.dm = make_float2(0.f, 0.f);
+          }
+          e.pad = 0.f;
+          rt[ptid] = e;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(PRODUCER_WARPS * 32) : "memory");
+        unsigned char* hi = ops + size_t(s) * NCOMP * stage_bytes;
+        unsigned char* lo = hi + stage_bytes;
+        float trs = 0.f;
+        for (int u = warp; u < nunits; u += PRODUCER_WARPS) {
+          const int zg = u >> 3, c = u & 7;
+          const int z = zg * 32 + lane;
+          float2 a[4];
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            const RowEnt e = rt[c * 4 + rr];
+            if (z < nz && e.sw != 0.f) {
+              const float2 gp = g32[e.offp + z], gq = g32[e.offq + z];
+              const float2 v = gp * gq;
+              a[rr] = make_float2(e.sw * v.x, e.sw * v.y);
+            } else {
+              a[rr] = make_float2(0.f, 0.f);
+            }
+            trs = fmaf(a[rr].x, a[rr].x, fmaf(a[rr].y, a[rr].y, trs));
+          }
+          uint4 h;
+          h.x = pack_bf16(a[0].x, a[0].y); h.y = pack_bf16(a[1].x, a[1].y);
+          h.z = pack_bf16(a[2].x, a[2].y); h.w = pack_bf16(a[3].x, a[3].y);
+          const uint32_t off = sw_off(z, c);
+          *reinterpret_cast<uint4*>(hi + off) = h;
+          if (PASSES == 3) {
+            uint4 l;
+            const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
+            float2 h0 = __bfloat1622float2(hb[0]), h1 = __bfloat1622float2(hb[1]);
+            float2 h2 = __bfloat1622float2(hb[2]), h3 = __bfloat1622float2(hb[3]);
+            l.x = pack_bf16(a[0].x - h0.x, a[0].y - h0.y); l.y = pack_bf16(a[1].x - h1.x, a[1].y - h1.y);
+            l.z = pack_bf16(a[2].x - h2.x, a[2].y - h2.y); l.w = pack_bf16(a[3].x - h3.x, a[3].y - h3.y);
+            *reinterpret_cast<uint4*>(lo + off) = l;
+          }
+        }
+        // data rows: operand rows nzp (d_+) and nzp + 1 (d_-), 8 chunks each
+        if (warp == PRODUCER_WARPS - 1 && lane < 16) {
+          const int which = lane >> 3, c = lane & 7;
+          float2 v[4];
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) v[rr] = which ? rt[c * 4 + rr].dm : rt[c * 4 + rr].dp;
+          uint4 h;
+          h.x = pack_bf16(v[0].x, v[0].y); h.y = pack_bf16(v[1].x, v[1].y);
+          h.z = pack_bf16(v[2].x, v[2].y); h.w = pack_bf16(v[3].x, v[3].y);
+          const uint32_t off = sw_off(nzp + which, c);
+          *reinterpret_cast<uint4*>(hi + off) = h;
+          if (PASSES == 3) {
+            uint4 l;
+            const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
+            float2 h0 = __bfloat1622float2(hb[0]), h1 = __bfloat1622float2(hb[1]);
+            float2 h2 = __bfloat1622float2(hb[2]), h3 = __bfloat1622float2(hb[3]);
+            l.x = pack_bf16(v[0].x - h0.x, v[0].y - h0.y); l.y = pack_bf16(v[1].x - h1.x, v[1].y - h1.y);
+            l.z = pack_bf16(v[2].x - h2.x, v[2].y - h2.y); l.w = pack_bf16(v[3].x - h3.x, v[3].y - h3.y);
+            *reinterpret_cast<uint4*>(lo + off) = l;
+          }
+        }
+        tr += double(trs);
+        fence_proxy_async();
+        mbar_arrive(&full[s]);
+      }
+      if (!ok) break;
+      // epilogue: accumulator -> FP32 partial tile [col][128 lanes]
+      if (!mbar_wait(acc_full, unsigned((si - s0) & 1), abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      float* out = d.gpart + size_t(slot) * size_t(ncols) * TC_M;
+      const uint32_t lane_base = uint32_t(warp * 32) << 16;
+      for (int c0 = 0; c0 < ncols; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + uint32_t(c0), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) out[size_t(c0 + j) * TC_M + warp * 32 + lane] = v[j];
+      }
+      tc_fence_before();
+      mbar_arrive(acc_empty);
+      // trace(G) of this segment, FP64
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      if (lane == 0) atomicAdd(&d.trace[m], tr);
+    }
+  }
+
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(&d.flags[0], 1u);
+  if (warp == PRODUCER_WARPS) {
+    tc_fence_after();
+    tmem_dealloc(tmem, alloc_cols);
+  }
+}
+
+// Sum the partial tiles of each subproblem into the FP64 Gram (both triangles) and b.
+__global__ void gram_reduce_kernel(Dev d) {
+  const int m = blockIdx.y;
+  const int nz = d.nz, nzp = nzp_of(nz), ncols = cols_of(nzp);
+  const int c1 = nzp + 16;
+  const int sl0 = d.m_slot0[m], sl1 = d.m_slot0[m + 1];
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nG = (long long)nz * nz;
+  if (e < nG) {
+    const int zi = int(e / nz), zj = int(e - (long long)zi * nz);
+    int a = zi, b = zj;
+    if (a >= TC_M && b < TC_M) { a = zj; b = zi; }     // lower-left block from its transpose
+    int lanei, col;
+    if (a < TC_M) { lanei = a; col = b; }
+    else { lanei = a - TC_M; col = c1 + (b - TC_M); }
+    double s = 0.0;
+    for (int sl = sl0; sl < sl1; ++sl) s += double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
+    d.G[size_t(m) * nG + e] = s;
+  } else if (e < nG + 2 * nz) {
+    const int zi = int((e - nG) >> 1), k = int((e - nG) & 1);
+    int lanei, col;
+    if (zi < TC_M) { lanei = zi; col = nzp + k; }
+    else { lanei = zi - TC_M; col = c1 + (nzp - TC_M) + k; }
+    double s = 0.0;
+    for (int sl = sl0; sl < sl1; ++sl) s += double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
+    d.b[(size_t(m) * nz + zi) * 2 + k] = s;
+  }
+}
+
+}  // namespace
+
+int tc_cols(int nz) { return cols_of(nzp_of(nz)); }
+
+int tc_smem_bytes(int nz, int passes) {
+  const int zr = zrows_of(nzp_of(nz));
+  const int stages = stages_of(passes), ncomp = passes == 1 ? 1 : 2;
+  return 1024 + stages * ncomp * zr * ROWB + stages * TC_KC * int(sizeof(RowEnt)) + (2 * stages + 3) * 8 + 16;
+}
+
+cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s) {
+  const int smem = tc_smem_bytes(d.nz, d.passes);
+  cudaError_t e;
+  if (d.ncta_gram > 0) {
+    if (d.passes == 3) {
+      cudaFuncSetAttribute(gram_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      gram_tc_kernel<3><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
+    } else {
+      cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      gram_tc_kernel<1><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const long long n = (long long)d.nz * d.nz + 2 * d.nz;
+  dim3 g(unsigned((n + 255) / 256), d.nsub);
+  gram_reduce_kernel<<<g, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace edt

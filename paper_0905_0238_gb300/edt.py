@@ -71,6 +71,7 @@ def _lib() -> C.CDLL:
         L.edt_green.argtypes = [vp, vp, vp]
         L.edt_get_vhat.argtypes = [vp, vp, vp]
         L.edt_row_counts.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.edt_gram.argtypes = [vp, vp, i, vp, vp, vp, vp]
         L.edt_get_stats.argtypes = [vp, C.POINTER(edt_stats)]
         L.edt_set_profiling.argtypes = [vp, i]
         L.edt_read_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_char_p), i,
@@ -81,7 +82,7 @@ def _lib() -> C.CDLL:
         L.edt_destroy.argtypes = [vp]
         L.edt_destroy.restype = None
         for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
-                     "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts",
+                     "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile"):
             getattr(L, name).restype = i
         _LIB = L
@@ -128,6 +129,11 @@ def edt_get_vhat(ctx, ptr: int, stream: int):
     _check(_lib().edt_get_vhat(ctx, C.c_void_p(ptr), C.c_void_p(stream)), "edt_get_vhat")
 
 
+def edt_gram(ctx, D_ptr: int, D_dtype: int, G_ptr: int, b_ptr: int, tr_ptr: int, stream: int):
+    _check(_lib().edt_gram(ctx, C.c_void_p(D_ptr), D_dtype, C.c_void_p(G_ptr), C.c_void_p(b_ptr),
+                           C.c_void_p(tr_ptr), C.c_void_p(stream)), "edt_gram")
+
+
 def edt_row_counts(ctx, nsub: int) -> np.ndarray:
     out = (C.c_longlong * nsub)()
     _check(_lib().edt_row_counts(ctx, out), "edt_row_counts")
@@ -171,7 +177,7 @@ class Config:
     layer_top: Sequence[float]
     layer_vel: Sequence[float]
     precision: int = EDT_FP64
-    passes: int = 1
+    passes: int = 3
     refine: int = 1
     alpha: float = 1e-2
     cutoff: float = 1.0
@@ -269,6 +275,17 @@ class Solver:
         v = torch.empty((self.nsub, self.cfg.nz), device=self.device, dtype=torch.complex128)
         edt_get_vhat(self.ctx, v.data_ptr(), self._stream())
         return v
+
+    def gram(self, D):
+        """(G [nsub][nz][nz], b [nsub][nz][2], trace [nsub]) of the split systems for data D."""
+        torch = self._torch
+        nz = self.cfg.nz
+        G = torch.empty((self.nsub, nz, nz), device=self.device, dtype=torch.float64)
+        b = torch.empty((self.nsub, nz, 2), device=self.device, dtype=torch.float64)
+        tr = torch.empty((self.nsub,), device=self.device, dtype=torch.float64)
+        edt_gram(self.ctx, D.data_ptr(), self._cdtype(D), G.data_ptr(), b.data_ptr(),
+                 tr.data_ptr(), self._stream())
+        return G, b, tr
 
     def row_counts(self):
         return edt_row_counts(self.ctx, self.nsub)

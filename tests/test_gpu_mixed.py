@@ -1,0 +1,90 @@
+"""GPU parity of the mixed-precision path (tcgen05 Gram + FP64 Cholesky + refinement).
+
+The tensor-core normal matrices are compared with Ahat^T Ahat formed in FP64 from the
+oracle's own kernel rows (a matmul in the test; the oracle itself never forms a Gram);
+the end-to-end inversion with the oracle's QR solution.  Tolerances: Gram relative
+Frobenius 5e-3 with BF16 operands, 2e-5 with the split BF16x3 operands; trace(G) 1e-7;
+V and Vhat 1e-5 relative L2 after one refinement step.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import edt2d
+from tests.gpu_helpers import rel_l2, small_workload, blobs, dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def solver(wl, passes=3, refine=1, fold=1):
+    from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED
+    return Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=passes, refine=refine,
+                                       fold=fold))
+
+
+def born_data(wl, salt=0, snr_db=20.0):
+    V = blobs(wl, salt=salt)
+    D = edt2d.forward(wl, V)
+    if snr_db is not None:
+        D = D + synth.noise_snr(synth.rng_for(0, salt=salt + 100), D, snr_db)
+    return np.ascontiguousarray(D.astype(np.complex64))
+
+
+@pytest.mark.parametrize("passes", [1, 3])
+@pytest.mark.parametrize("nz", [40, 130, 256])
+def test_gram_tc_matches_fp64_normal_matrix(passes, nz):
+    wl = small_workload(nx=32, nz=nz, nf=4, alpha=1e-2, dz=8.0)
+    D = born_data(wl, salt=1)
+    G, b, tr = solver(wl, passes=passes).gram(dev(D))
+    G, b, tr = G.cpu().numpy(), b.cpu().numpy(), tr.cpu().numpy()
+    D2 = edt2d.data_transform(D.astype(np.complex128))
+    tolG = 5e-3 if passes == 1 else 2e-5
+    for m in range(wl.nx // 2 + 1):
+        _, sysd = edt2d.solve_wavenumber(wl, D2, m, return_system=True)
+        if len(sysd["rows"]) == 0:
+            assert np.all(G[m] == 0) and tr[m] == 0
+            continue
+        Ah, dh = sysd["Ahat"], sysd["dhat"]
+        Gr = Ah.T @ Ah
+        br = Ah.T @ dh
+        assert rel_l2(G[m], Gr) < tolG, (m, rel_l2(G[m], Gr))
+        assert rel_l2(b[m][:, : br.shape[1]], br) < 5 * tolG
+        assert abs(tr[m] - np.trace(Gr)) <= 1e-7 * np.trace(Gr)
+
+
+@pytest.mark.parametrize("passes,refine", [(3, 1), (1, 2)])
+@pytest.mark.parametrize("nx,nz,nf", [(32, 40, 6), (64, 130, 4), (32, 256, 3)])
+def test_invert_mixed_matches_oracle(passes, refine, nx, nz, nf):
+    """Split BF16x3 Gram + one refinement step (or BF16 Gram + two steps) reach 1e-5."""
+    wl = small_workload(nx=nx, nz=nz, nf=nf, alpha=1e-2, dz=8.0)
+    D = born_data(wl, salt=2)
+    V_or, vh_or = edt2d.invert(wl, D.astype(np.complex128))
+    s = solver(wl, passes=passes, refine=refine)
+    V = s.invert(dev(D)).cpu().numpy()
+    vh = s.vhat().cpu().numpy()
+    st = s.stats()
+    assert st.n_notpd == 0 and st.n_nonfinite == 0
+    assert rel_l2(vh, vh_or) < 1e-5
+    assert rel_l2(V, V_or) < 1e-5
+
+
+def test_refinement_is_what_reaches_the_tolerance():
+    """Without refinement the BF16 Gram leaves a visible error; one step removes it."""
+    wl = small_workload(nx=32, nz=64, nf=6, alpha=1e-4, dz=8.0)
+    D = born_data(wl, salt=3)
+    V_or, _ = edt2d.invert(wl, D.astype(np.complex128))
+    e0 = rel_l2(solver(wl, passes=1, refine=0).invert(dev(D)).cpu().numpy(), V_or)
+    e1 = rel_l2(solver(wl, passes=1, refine=1).invert(dev(D)).cpu().numpy(), V_or)
+    e2 = rel_l2(solver(wl, passes=1, refine=2).invert(dev(D)).cpu().numpy(), V_or)
+    assert e0 > 1e-5
+    assert e1 < e0 / 10 and e2 <= e1 * 1.01 + 1e-9
+
+
+def test_mixed_without_folding_and_without_cut():
+    wl = small_workload(nx=32, nz=48, nf=4, alpha=1e-2, cutoff=0.0, dz=8.0)
+    D = born_data(wl, salt=4)
+    V_or, _ = edt2d.invert(wl, D.astype(np.complex128))
+    for fold in (0, 1):
+        V = solver(wl, fold=fold).invert(dev(D)).cpu().numpy()
+        assert rel_l2(V, V_or) < 1e-5
