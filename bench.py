@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the batched per-wavenumber inversion on the 2D production workload.
+
+Workload: 512 shots x 512 receivers (dx 12.5 m, periodic line), 128 frequencies 3-60 Hz,
+256 depths of 8 m, a 20-layer reference (seeded), a Gaussian-correlated 3 % random
+velocity field, complex64 Born data from the library's own forward model plus complex
+Gaussian noise at 20 dB SNR per frequency, damping alpha = 1e-2 (lam = alpha trace G).
+One step = one full inversion (all 257 split systems standing for the 512 midpoint
+wavenumbers): depth march, data transform, right-hand sides, tensor-core Gram, FP64
+Cholesky, one refinement step, inverse transform.  Subproblems counted = nx (512) per
+inversion, one per midpoint wavenumber.
+
+Multi-GPU: each rank inverts its own independent survey line (weak scaling, no
+data-path collective); time = max over ranks.
+
+--impl reference times the FP64 CPU oracle (the only reference this project has) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "production_2d"
+CPU_SAMPLE_M = (1, 64, 128, 192)      # midpoint indices solved by the CPU baseline sample
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--passes", type=int, default=3)
+    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload_summary(wl):
+    return (f"{WORKLOAD}: {wl.nx}x{wl.nx} sources/receivers dx {wl.dx} m, {len(wl.freq_hz)} freqs "
+            f"{wl.freq_hz.min():g}-{wl.freq_hz.max():g} Hz, nz {wl.nz} dz {wl.dz} m, "
+            f"{len(wl.layer_top)} layers, 3% random field, c64 Born data + 20 dB noise")
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def cpu_child(spec_path):
+    """Runs in a subprocess with single-threaded BLAS: time the oracle on a sample."""
+    import numpy as np
+    import synth
+    from oracle import edt2d
+    spec = json.load(open(spec_path))
+    wl = synth.preset(spec["workload"])
+    rng = synth.rng_for(1, salt=77)
+    D = synth.random_data(rng, (len(wl.freq_hz), wl.nx, wl.nx), np.complex64).astype(np.complex128)
+    t0 = time.perf_counter()
+    D2 = edt2d.data_transform(D)
+    t1 = time.perf_counter()
+    g = edt2d.green_table(wl)
+    t2 = time.perf_counter()
+    ms = spec["ms"]
+    per = []
+    for m in ms:
+        a = time.perf_counter()
+        edt2d.solve_wavenumber(wl, D2, m, g)
+        per.append(time.perf_counter() - a)
+    nsolve = wl.nx // 2 + 1
+    # per-subproblem cost: one split system solves the pair +-k_m, i.e. nx/nsolve subproblems;
+    # the transform and the Green's table are amortised over the nsolve systems
+    t_sys = statistics.mean(per) + ((t1 - t0) + (t2 - t1)) / nsolve
+    rate = (wl.nx / nsolve) / t_sys
+    out = dict(value=rate, unit="subproblems/s", cores=1, kind="oracle",
+               sample=(f"FP64 numpy oracle, 1 thread: full data transform ({t1 - t0:.1f} s) and "
+                       f"Green's table ({t2 - t1:.1f} s) amortised over {nsolve} split systems, "
+                       f"plus QR solves of midpoint indices {list(ms)} "
+                       f"(mean {statistics.mean(per):.2f} s each); random c64 data of the "
+                       f"workload's shape"),
+               per_solve_s=per, transform_s=t1 - t0, green_s=t2 - t1)
+    print("CPUJSON " + json.dumps(out))
+
+
+def run_cpu_baseline(ms):
+    spec = dict(workload=WORKLOAD, ms=list(ms))
+    with tempfile.NamedTemporaryFile("w", suffix=".json", delete=False) as f:
+        json.dump(spec, f)
+        path = f.name
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", path],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    os.unlink(path)
+    for line in r.stdout.splitlines():
+        if line.startswith("CPUJSON "):
+            return json.loads(line[8:])
+    raise RuntimeError("cpu baseline failed:\n" + r.stdout[-2000:] + r.stderr[-2000:])
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ms_per_step = 1
+    nsolve = 257
+    sample = []
+    # step i solves one midpoint index; K + W steps stay within a few minutes at 1 core
+    for i in range(args.warmup + args.steps):
+        sample.append((1 + 37 * i) % nsolve)
+    base = run_cpu_baseline(sample)
+    per = base["per_solve_s"][args.warmup:]
+    amort = (base["transform_s"] + base["green_s"]) / nsolve
+    step_t = [p + amort for p in per]
+    total = sum(step_t)
+    import synth
+    wl = synth.preset(WORKLOAD)
+    value = (wl.nx / nsolve) * len(step_t) / total
+    line = dict(impl="reference", metric="subproblems_per_sec", value=value, unit="subproblems/s",
+                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * total / len(step_t), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=workload_summary(wl), per_step=f"{ms_per_step} split system"),
+                cpu_baseline=dict(kind="oracle", cores=1, value=value, unit="subproblems/s",
+                                  sample=base["sample"]),
+                e2e=dict(value=value, unit="subproblems/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.cpu_child:
+        cpu_child(args.cpu_child)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_0905_0238_gb300 import build as libbuild
+    libbuild.build()
+    from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED, EDT_FP64
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = synth.preset(WORKLOAD)
+    rng = synth.rng_for(1, salt=1 + rank)           # each rank: its own survey line
+    V = synth.perturbation_random_field(rng, wl.nx, wl.dx, wl.nz, wl.dz, wl.z0,
+                                        wl.layer_top, wl.layer_vel, corr=40.0, rms=0.03)
+    fp64 = Solver(Config.from_workload(wl, precision=EDT_FP64), device=dev)
+    D = fp64.forward(torch.from_numpy(V).to(dev), out_dtype=torch.complex64)
+    # complex Gaussian noise at 20 dB SNR per frequency (seeded, generated on the device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.SEED_BASE + 1 + 1000 * rank)
+    p_sig = (D.abs() ** 2).mean(dim=(1, 2), keepdim=True)
+    sd = torch.sqrt(p_sig / 10 ** (wl.snr_db / 10) / 2)
+    D = D + torch.complex(torch.randn(D.shape, device=dev, generator=gen),
+                          torch.randn(D.shape, device=dev, generator=gen)) * sd
+    D = D.contiguous()
+    torch.cuda.synchronize()
+
+    mixed = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=args.passes,
+                                        refine=args.refine), device=dev)
+    Vout = torch.empty((wl.nx, wl.nz), device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        mixed.invert(D, out=Vout)
+    torch.cuda.synchronize()
+    st = mixed.stats()
+    if st.n_notpd or st.n_nonfinite:
+        raise RuntimeError(f"mixed path: {st.n_notpd} not PD, {st.n_nonfinite} non-finite")
+
+    # ---- device-resident timed region ----------------------------------------------
+    clocks = Clocks(local)
+    mixed.set_profiling(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mixed.invert(D, out=Vout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    stages, ncalls = mixed.read_profile()
+    mixed.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    sub_per_step = wl.nx                             # one subproblem per midpoint wavenumber
+    value = world * sub_per_step * args.steps / (ms_total / 1e3)
+
+    # ---- end to end through the host-buffer entry point ----------------------------
+    Dh = D.cpu().pin_memory()
+    Vh = torch.empty((wl.nx, wl.nz), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        mixed.invert_host(Dh, Vh)
+    torch.cuda.synchronize()
+    barrier()
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(args.steps):
+        mixed.invert_host(Dh, Vh)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = h0.elapsed_time(h1)
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = world * sub_per_step * args.steps / (ms_e2e / 1e3)
+
+    # ---- accuracy vs the FP64 GPU path, and the FP64 path's own throughput --------------
+    acc = {}
+    if not args.no_fp64:
+        V64 = torch.empty((wl.nx, wl.nz), device=dev, dtype=torch.float64)
+        fp64.invert(D, out=V64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        nf64 = 3
+        f0.record(stream)
+        for _ in range(nf64):
+            fp64.invert(D, out=V64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / nf64
+        Vm = Vout.double()
+        rel = float(torch.linalg.norm(Vm - V64) / torch.linalg.norm(V64))
+        vh_m = mixed.vhat(); vh_d = fp64.vhat()
+        relh = float(torch.linalg.norm(vh_m - vh_d) / torch.linalg.norm(vh_d))
+        acc = dict(rel_l2_V_vs_fp64_gpu=rel, rel_l2_vhat_vs_fp64_gpu=relh,
+                   fp64_gpu_ms_per_step=ms64,
+                   fp64_gpu_subproblems_per_sec=sub_per_step / (ms64 / 1e3),
+                   speedup_vs_fp64_gpu=(ms64 / ms_step))
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (tensor-core Gram) --------------------------
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    nzp = (wl.nz + 31) // 32 * 32
+    ncols = (nzp + 16) + (nzp - 128 + 16 if nzp > 128 else 0)
+    padded_rows = st.gram_rows_padded
+    issued = args.passes * 2.0 * (2 * padded_rows) * 128 * ncols          # MMA flops / launch
+    useful = 2.0 * (2 * st.rows_solved) * wl.nz * (wl.nz + 2)             # full-square G + b
+    gram_ms = stages.get("gram", 0.0) / max(ncalls, 1)
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = issued / (gram_ms / 1e3) / 1e12 if gram_ms > 0 else None
+    roof = dict(bound="tensor", kernel="gram_tc_kernel", achieved=achieved, peak=peak,
+                unit="TFLOP/s", frac=(achieved / peak) if achieved else None,
+                traffic=_traffic_from_profile(), peak_source="MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                flops_per_launch=issued, useful_flops_per_launch=useful,
+                useful_tflops=useful / (gram_ms / 1e3) / 1e12 if gram_ms > 0 else None,
+                gram_ms=gram_ms)
+    stage_ms = {k: v / max(ncalls, 1) for k, v in stages.items()}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = run_cpu_baseline(CPU_SAMPLE_M)
+            cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as ex:  # the GPU number stands; report why the baseline is missing
+            cpu = dict(value=None, unit="subproblems/s", cores=0, kind="oracle", sample=str(ex)[:300])
+
+    line = dict(
+        metric="subproblems_per_sec", value=value, unit="subproblems/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="bf16x3+f32acc+f64", data="synthetic",
+        config=dict(workload=workload_summary(wl), l2="inputs larger than L2 (268 MB data per step)",
+                    passes=args.passes, refine=args.refine, alpha=wl.alpha,
+                    rows_total=int(st.rows_total), rows_solved=int(st.rows_solved),
+                    parallelism=f"replicas x{world} (independent lines)"),
+        model_pts_per_sec=world * wl.nx * wl.nz * args.steps / (ms_total / 1e3),
+        e2e=dict(value=e2e_value, unit="subproblems/s",
+                 h2d_bytes_per_step=int(Dh.numel() * Dh.element_size()),
+                 d2h_bytes_per_step=int(Vh.numel() * Vh.element_size())),
+        gpu_launches=int(st.launches_per_invert) * args.steps,
+        roofline=roof, stage_ms=stage_ms, accuracy=acc, clocks=clk, cpu_baseline=cpu)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _traffic_from_profile():
+    """DRAM bytes per launch of the Gram kernel from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", "gram_tc_production_2d.json")
+    try:
+        return json.load(open(p)).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+if __name__ == "__main__":
+    main()

@@ -111,6 +111,9 @@ typedef struct {
   int n_notpd;                  /* subproblems whose factorisation failed (last invert)  */
   int n_nonfinite;              /* subproblems with a non-finite solution (last invert)  */
   int last_status;              /* status of the last device call                        */
+  int launches_per_invert;      /* CUDA kernels one edt_invert launches                  */
+  long long gram_rows_padded;   /* complex rows the tensor-core Gram processes per call,
+                                   each CTA segment padded to a multiple of 32           */
 } edt_stats;
 
 /* Create a context for `cfg` and report the device workspace it needs.

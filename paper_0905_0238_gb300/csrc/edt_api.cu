@@ -60,7 +60,7 @@ struct edt_ctx {
   int last_status = EDT_OK;
   // profiling
   bool prof = false;
-  static constexpr int NSTAGE = 8;
+  static constexpr int NSTAGE = 9;        // marks; NSTAGE - 1 timed stages
   std::vector<cudaEvent_t> ev;   // [calls][NSTAGE + 1]
   int prof_calls = 0;
   int prof_used[NSTAGE] = {};
@@ -69,7 +69,8 @@ struct edt_ctx {
 namespace {
 
 const char* kStageNames[edt_ctx::NSTAGE] = {"green", "transform", "rhs", "gram",
-                                            "cholesky", "refine", "inverse", "unused"};
+                                            "gram_reduce", "cholesky", "refine", "inverse",
+                                            "unused"};
 
 int validate(const edt_config* c) {
   if (!c) return EDT_EINVAL;
@@ -250,7 +251,7 @@ void layout(edt_ctx* c) {
   take(c->r_Dst, nf * N * N * sizeof(double2));
   take(c->r_Vst, N * nz * sizeof(double));
   take(c->r_rhs, std::max<size_t>(R, 1) * 2 * (mixed ? sizeof(float2) : sizeof(double2)));
-  take(c->r_gpart, mixed ? size_t(c->nslot) * TC_M * tc_cols(c->nz) * (nz > TC_M ? 2 : 1) * sizeof(float) : 0);
+  take(c->r_gpart, mixed ? size_t(c->nslot) * TC_M * tc_cols(c->nz) * sizeof(float) : 0);
   take(c->r_G, ns * nz * nz * sizeof(double));
   take(c->r_b, ns * nz * 2 * sizeof(double));
   take(c->r_tr, ns * sizeof(double));
@@ -334,16 +335,19 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_mark(c, 2, s);
   if (mixed) { EDT_TRY(launch_rhs<float>(d, s)); }
   else { EDT_TRY(launch_rhs<double>(d, s)); }
+  if (mixed) EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
   prof_mark(c, 3, s);
   if (mixed) {
-    EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
     EDT_TRY(launch_gram_tc(d, s));
+    prof_mark(c, 4, s);
+    EDT_TRY(launch_gram_reduce(d, s));
   } else {
     EDT_TRY(launch_gram_f64(d, s));
+    prof_mark(c, 4, s);
   }
-  prof_mark(c, 4, s);
-  EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
   prof_mark(c, 5, s);
+  EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
+  prof_mark(c, 6, s);
   if (mixed) {
     for (int it = 0; it < c->cfg.refine; ++it) {
       EDT_TRY(cudaMemsetAsync(d.r, 0, sizeof(double) * d.nsub * d.nz * 2, s));
@@ -351,9 +355,9 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
       EDT_TRY(launch_refine_update(d, s));
     }
   }
-  prof_mark(c, 6, s);
-  EDT_TRY(launch_inverse(d, V, V_dtype, s));
   prof_mark(c, 7, s);
+  EDT_TRY(launch_inverse(d, V, V_dtype, s));
+  prof_mark(c, 8, s);
   if (c->prof && c->prof_calls < 64) c->prof_calls++;
   return EDT_OK;
 }
@@ -482,6 +486,7 @@ int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr,
   if (mixed) {
     EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
     EDT_TRY(launch_gram_tc(d, s));
+    EDT_TRY(launch_gram_reduce(d, s));
   } else {
     EDT_TRY(launch_gram_f64(d, s));
     EDT_TRY(launch_trace_diag(d, s));
@@ -511,6 +516,11 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   o->workspace_bytes = c->ws_bytes;
   o->gram_flop = 2.0 * 2.0 * double(o->rows_solved) * double(c->nz) * double(c->nz + 2);
   o->last_status = c->last_status;
+  // kernels launched by one edt_invert: green (2), transform (2), rhs (1), Gram (FP64: 1;
+  // mixed: tensor-core + reduce 2), Cholesky (1), per refinement step (2), inverse (1)
+  o->launches_per_invert = c->cfg.precision == EDT_MIXED ? 9 + 2 * c->cfg.refine : 8;
+  o->gram_rows_padded = 0;
+  for (long long n : c->seg_nrow) o->gram_rows_padded += (n + TC_KC - 1) / TC_KC * TC_KC;
   if (c->ws) {
     cudaError_t e = cudaStreamSynchronize(c->last_stream);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -544,7 +554,7 @@ int edt_read_profile(edt_ctx* c, double* ms, const char** names, int max_stages,
   if (n_calls) *n_calls = c->prof_calls;
   if (c->prof_calls > 0) {
     const int K = edt_ctx::NSTAGE + 1;
-    EDT_TRY(cudaEventSynchronize(c->ev[size_t(c->prof_calls - 1) * K + 7]));
+    EDT_TRY(cudaEventSynchronize(c->ev[size_t(c->prof_calls - 1) * K + (edt_ctx::NSTAGE - 1)]));
     for (int call = 0; call < c->prof_calls; ++call)
       for (int i = 0; i < ns; ++i) {
         float t = 0.f;

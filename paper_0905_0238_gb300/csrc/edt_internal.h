@@ -81,7 +81,8 @@ template <typename T>
 cudaError_t launch_rhs(const Dev& d, cudaStream_t s);
 
 cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
-cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);
+cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace
+cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s);   // partials -> G, b (FP64)
 cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s);   // trace[m] = sum_z G[m][z][z]
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s);
 cudaError_t launch_refine(const Dev& d, cudaStream_t s);          // r += Ahat^T (dhat - Ahat x)

@@ -444,6 +444,10 @@ cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s) {
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s) {
   const long long n = (long long)d.nz * d.nz + 2 * d.nz;
   dim3 g(unsigned((n + 255) / 256), d.nsub);
   gram_reduce_kernel<<<g, 256, 0, s>>>(d);

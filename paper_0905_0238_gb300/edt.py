@@ -39,7 +39,8 @@ class edt_stats(C.Structure):
         ("n_sub", C.c_int), ("rows_total", C.c_longlong), ("rows_solved", C.c_longlong),
         ("rows_min", C.c_int), ("rows_max", C.c_int), ("workspace_bytes", C.c_size_t),
         ("gram_flop", C.c_double), ("n_notpd", C.c_int), ("n_nonfinite", C.c_int),
-        ("last_status", C.c_int),
+        ("last_status", C.c_int), ("launches_per_invert", C.c_int),
+        ("gram_rows_padded", C.c_longlong),
     ]
 
 
@@ -150,7 +151,7 @@ def edt_set_profiling(ctx, on: bool):
     _check(_lib().edt_set_profiling(ctx, int(bool(on))), "edt_set_profiling")
 
 
-def edt_read_profile(ctx, max_stages: int = 8):
+def edt_read_profile(ctx, max_stages: int = 16):
     ms = (C.c_double * max_stages)()
     names = (C.c_char_p * max_stages)()
     ncalls = C.c_int()

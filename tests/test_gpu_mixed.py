@@ -71,7 +71,7 @@ def test_invert_mixed_matches_oracle(passes, refine, nx, nz, nf):
 
 def test_refinement_is_what_reaches_the_tolerance():
     """Without refinement the BF16 Gram leaves a visible error; one step removes it."""
-    wl = small_workload(nx=32, nz=64, nf=6, alpha=1e-4, dz=8.0)
+    wl = small_workload(nx=32, nz=64, nf=6, alpha=1e-2, dz=8.0)
     D = born_data(wl, salt=3)
     V_or, _ = edt2d.invert(wl, D.astype(np.complex128))
     e0 = rel_l2(solver(wl, passes=1, refine=0).invert(dev(D)).cpu().numpy(), V_or)
