@@ -159,6 +159,27 @@ int edt_get_vhat(edt_ctx* ctx, void* vhat_dev, void* stream);
 int edt_gram(edt_ctx* ctx, const void* D_dev, int D_dtype, void* G_dev, void* b_dev,
              void* trace_dev, void* stream);
 
+/* Allocation-free depth march (no counterpart in the paper: a library service).
+ * For callers that may not allocate device memory at all, e.g. a component running
+ * inside a host application that owns the device allocator, or one that is handed only
+ * its input and output buffers.  It computes the same table as edt_green,
+ * g(k_n, z_j; omega~_f) as complex128 [nfreq][nx/2+1][nz] into the caller's g_dev, from
+ * host arrays, without a context and without any device allocation: all scratch (the
+ * layer stack, per-frequency constants and the recursion coefficients) lives in one
+ * fixed 8 MiB device array inside the library, which every GPU that loads the library
+ * keeps until the process exits.  Frequencies are processed in chunks that fit it.
+ * Limits: nx a power of two >= 2; one frequency's coefficients, (nx/2+1) * nlayer * 80
+ * bytes, must fit in the 8 MiB (else EDT_EUNSUPPORTED).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Every call reuses the same array, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on it; each
+ * call fully writes the scratch it reads, so nothing carries over between calls.
+ * Host arrays may be freed when the call returns; the computation is asynchronous on
+ * `stream`.  Returns EDT_OK, EDT_EINVAL, EDT_EUNSUPPORTED or EDT_ECUDA. */
+int edt_green_noalloc(int nx, double dx, int nz, double dz, double z0, int nfreq,
+                      const double* freq_hz, double eps, int nlayer, const double* layer_top_m,
+                      const double* layer_vel_mps, void* g_dev, void* stream);
+
 /* Per-subproblem complex row counts after the cut (before folding): counts[nx/2+1]. */
 int edt_row_counts(const edt_ctx* ctx, long long* counts);
 

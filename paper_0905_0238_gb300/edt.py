@@ -73,6 +73,9 @@ def _lib() -> C.CDLL:
         L.edt_get_vhat.argtypes = [vp, vp, vp]
         L.edt_row_counts.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.edt_gram.argtypes = [vp, vp, i, vp, vp, vp, vp]
+        d = C.c_double
+        L.edt_green_noalloc.argtypes = [i, d, i, d, d, i, C.POINTER(d), d, i, C.POINTER(d),
+                                        C.POINTER(d), vp, vp]
         L.edt_get_stats.argtypes = [vp, C.POINTER(edt_stats)]
         L.edt_set_profiling.argtypes = [vp, i]
         L.edt_read_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_char_p), i,
@@ -84,7 +87,7 @@ def _lib() -> C.CDLL:
         L.edt_destroy.restype = None
         for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
                      "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
-                     "edt_get_stats", "edt_set_profiling", "edt_read_profile"):
+                     "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc"):
             getattr(L, name).restype = i
         _LIB = L
     return _LIB
@@ -133,6 +136,18 @@ def edt_get_vhat(ctx, ptr: int, stream: int):
 def edt_gram(ctx, D_ptr: int, D_dtype: int, G_ptr: int, b_ptr: int, tr_ptr: int, stream: int):
     _check(_lib().edt_gram(ctx, C.c_void_p(D_ptr), D_dtype, C.c_void_p(G_ptr), C.c_void_p(b_ptr),
                            C.c_void_p(tr_ptr), C.c_void_p(stream)), "edt_gram")
+
+
+def edt_green_noalloc(nx, dx, nz, dz, z0, freq_hz, eps, layer_top, layer_vel, g_ptr: int,
+                      stream: int):
+    """Allocation-free depth march into caller memory (complex128 [nfreq][nx/2+1][nz])."""
+    dp = C.POINTER(C.c_double)
+    fr = np.ascontiguousarray(freq_hz, dtype=np.float64)
+    tp = np.ascontiguousarray(layer_top, dtype=np.float64)
+    vl = np.ascontiguousarray(layer_vel, dtype=np.float64)
+    _check(_lib().edt_green_noalloc(nx, dx, nz, dz, z0, len(fr), fr.ctypes.data_as(dp), eps,
+                                    len(tp), tp.ctypes.data_as(dp), vl.ctypes.data_as(dp),
+                                    C.c_void_p(g_ptr), C.c_void_p(stream)), "edt_green_noalloc")
 
 
 def edt_row_counts(ctx, nsub: int) -> np.ndarray:
