@@ -168,7 +168,7 @@ int edt_gram(edt_ctx* ctx, const void* D_dev, int D_dtype, void* G_dev, void* b_
  * layer stack, per-frequency constants and the recursion coefficients) lives in one
  * fixed 8 MiB device array inside the library, which every GPU that loads the library
  * keeps until the process exits.  Frequencies are processed in chunks that fit it.
- * Limits: nx a power of two >= 2; one frequency's coefficients, (nx/2+1) * nlayer * 80
+ * Limits: nx a power of two >= 2; one frequency's coefficients, (nx/2+1) * nlayer * 112
  * bytes, must fit in the 8 MiB (else EDT_EUNSUPPORTED).  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current; make
  * that first call before any stream capture.  Every call reuses the same array, so calls

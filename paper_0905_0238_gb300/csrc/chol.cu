@@ -1,16 +1,19 @@
 // Damped normal-equation solves, FP64: (G + lam I) x_+- = b_+-, lam = alpha * trace(G).
 //
 // Zeroth-order Tikhonov damping is the regularisation the paper's Discussion proposes in
-// place of its truncated SVD.  One block per midpoint wavenumber m: blocked right-looking
-// Cholesky (32-column panels; the diagonal block is factored by one warp, the panel by a
-// row-per-thread triangular solve, the trailing lower triangle by 4x4 register tiles),
-// in place on the L2-resident matrix, then blocked forward and backward substitution for
-// the two right-hand sides.  A non-positive or non-finite pivot marks the subproblem
-// EDT_ENOTPD and zeroes its solution.
+// place of its truncated SVD.  One block per midpoint wavenumber m (two resident per SM,
+// so one problem's serial panel steps overlap another's trailing update on the FP64
+// pipe): blocked right-looking Cholesky with 32-column panels, in place on the
+// L2-resident matrix -- the diagonal block factored by one warp in shared memory, the
+// panel by row-per-thread triangular solves, the trailing lower triangle by 4x4 FP64
+// register tiles.  Then forward and backward substitution for the two right-hand sides
+// with each 32x32 diagonal block staged in shared memory and solved by one warp with
+// shuffles, and the off-diagonal updates as warp-per-row dot products (forward) or
+// coalesced column sweeps (backward).  A non-positive or non-finite pivot marks the
+// subproblem EDT_ENOTPD and zeroes its solution.
 //
-// refine_update: x += (L L^T)^{-1} (r - lam x), where r = Ahat^T (dhat - Ahat x) was
-// accumulated over all rows by the refinement kernel (one step of iterative refinement on
-// the normal equations).
+// chol_solve applied to r - lam x, with r = Ahat^T (dhat - Ahat x) accumulated by the
+// refinement kernel, gives one step of iterative refinement on the normal equations.
 #include "edt_internal.h"
 #include "cplx.cuh"
 
@@ -36,65 +39,74 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
+__device__ __forceinline__ bool active(const Dev& d, int m) {
+  return d.row_off[m + 1] > d.row_off[m] && d.status[m] == EDT_OK;
+}
+
 // Solve L L^T x = sb in place (two right-hand sides, sb[i][0..1]); L lower in A (ld n).
-__device__ void chol_solve_2rhs(const double* A, int n, double* sb) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ void chol_solve_2rhs(const double* A, const double* dinv, int n, double* sb,
+                                double (*sL)[LDP]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nblk = (n + NB - 1) / NB;
   // forward: L y = b
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = min(NB, n - k0);
-    if (warp == 0) {
-      for (int j = 0; j < kb; ++j) {
-        const double ljj = A[size_t(k0 + j) * n + k0 + j];
-        const double y0 = sb[(k0 + j) * 2 + 0] / ljj, y1 = sb[(k0 + j) * 2 + 1] / ljj;
-        __syncwarp();
-        if (lane == 0) { sb[(k0 + j) * 2 + 0] = y0; sb[(k0 + j) * 2 + 1] = y1; }
-        if (lane > j && lane < kb) {
-          const double l = A[size_t(k0 + lane) * n + k0 + j];
-          sb[(k0 + lane) * 2 + 0] -= l * y0;
-          sb[(k0 + lane) * 2 + 1] -= l * y1;
-        }
-        __syncwarp();
-      }
+  for (int bk = 0; bk < nblk; ++bk) {
+    const int k0 = bk * NB, kb = min(NB, n - k0);
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int i = e / kb, j = e - i * kb;
+      sL[i][j] = j <= i ? A[size_t(k0 + i) * n + k0 + j] : 0.0;
     }
     __syncthreads();
-    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {
-      double s0 = sb[i * 2 + 0], s1 = sb[i * 2 + 1];
-      const double* Ai = A + size_t(i) * n + k0;
-      for (int l = 0; l < kb; ++l) {
-        s0 -= Ai[l] * sb[(k0 + l) * 2 + 0];
-        s1 -= Ai[l] * sb[(k0 + l) * 2 + 1];
+    if (warp == 0) {
+      double v0 = lane < kb ? sb[(k0 + lane) * 2] : 0.0, v1 = lane < kb ? sb[(k0 + lane) * 2 + 1] : 0.0;
+      for (int j = 0; j < kb; ++j) {
+        const double ij = dinv[k0 + j];
+        const double y0 = __shfl_sync(0xffffffffu, v0, j) * ij;
+        const double y1 = __shfl_sync(0xffffffffu, v1, j) * ij;
+        if (lane == j) { v0 = y0; v1 = y1; }
+        if (lane > j && lane < kb) { v0 -= sL[lane][j] * y0; v1 -= sL[lane][j] * y1; }
       }
-      sb[i * 2 + 0] = s0; sb[i * 2 + 1] = s1;
+      if (lane < kb) { sb[(k0 + lane) * 2] = v0; sb[(k0 + lane) * 2 + 1] = v1; }
+    }
+    __syncthreads();
+    for (int i = k0 + kb + warp; i < n; i += nw) {     // warp per row: b_i -= L[i][blk] . y
+      const double a = lane < kb ? A[size_t(i) * n + k0 + lane] : 0.0;
+      double s0 = lane < kb ? a * sb[(k0 + lane) * 2] : 0.0, s1 = lane < kb ? a * sb[(k0 + lane) * 2 + 1] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      if (lane == 0) { sb[i * 2] -= s0; sb[i * 2 + 1] -= s1; }
     }
     __syncthreads();
   }
   // backward: L^T x = y
-  const int nblk = (n + NB - 1) / NB;
   for (int bk = nblk - 1; bk >= 0; --bk) {
     const int k0 = bk * NB, kb = min(NB, n - k0);
-    if (warp == 0) {
-      for (int j = kb - 1; j >= 0; --j) {
-        const double ljj = A[size_t(k0 + j) * n + k0 + j];
-        const double x0 = sb[(k0 + j) * 2 + 0] / ljj, x1 = sb[(k0 + j) * 2 + 1] / ljj;
-        __syncwarp();
-        if (lane == 0) { sb[(k0 + j) * 2 + 0] = x0; sb[(k0 + j) * 2 + 1] = x1; }
-        if (lane < j) {
-          const double l = A[size_t(k0 + j) * n + k0 + lane];
-          sb[(k0 + lane) * 2 + 0] -= l * x0;
-          sb[(k0 + lane) * 2 + 1] -= l * x1;
-        }
-        __syncwarp();
-      }
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int i = e / kb, j = e - i * kb;
+      sL[i][j] = j <= i ? A[size_t(k0 + i) * n + k0 + j] : 0.0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < k0; i += blockDim.x) {
-      double s0 = sb[i * 2 + 0], s1 = sb[i * 2 + 1];
+    if (warp == 0) {
+      double v0 = lane < kb ? sb[(k0 + lane) * 2] : 0.0, v1 = lane < kb ? sb[(k0 + lane) * 2 + 1] : 0.0;
+      for (int j = kb - 1; j >= 0; --j) {
+        const double ij = dinv[k0 + j];
+        const double x0 = __shfl_sync(0xffffffffu, v0, j) * ij;
+        const double x1 = __shfl_sync(0xffffffffu, v1, j) * ij;
+        if (lane == j) { v0 = x0; v1 = x1; }
+        if (lane < j) { v0 -= sL[j][lane] * x0; v1 -= sL[j][lane] * x1; }
+      }
+      if (lane < kb) { sb[(k0 + lane) * 2] = v0; sb[(k0 + lane) * 2 + 1] = v1; }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k0; i += blockDim.x) {   // y_i -= sum_l L[k0+l][i] x_l
+      double s0 = sb[i * 2], s1 = sb[i * 2 + 1];
       for (int l = 0; l < kb; ++l) {
         const double a = A[size_t(k0 + l) * n + i];
-        s0 -= a * sb[(k0 + l) * 2 + 0];
+        s0 -= a * sb[(k0 + l) * 2];
         s1 -= a * sb[(k0 + l) * 2 + 1];
       }
-      sb[i * 2 + 0] = s0; sb[i * 2 + 1] = s1;
+      sb[i * 2] = s0; sb[i * 2 + 1] = s1;
     }
     __syncthreads();
   }
@@ -109,6 +121,7 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
   double* sb = sD + NB * LDP;               // [n][2] right-hand sides
   double* red = sb + 2 * n;                 // [33] reduction scratch
   __shared__ int fail;
+  __shared__ double sInv[NB];
   const int m = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* A = d.G + size_t(m) * n * n;
@@ -148,10 +161,10 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
       for (int j = 0; j < kb; ++j) {
         const double djj = sD[j * LDP + j];
         if (!(djj > 0.0) || !isfinite(djj)) { if (lane == 0) fail = 1; break; }
-        const double ljj = sqrt(djj);
+        const double inv = rsqrt(djj);          // 1 / L_jj; multiplications replace divisions
         __syncwarp();
-        if (lane == j) sD[j * LDP + j] = ljj;
-        if (lane > j && lane < kb) sD[lane * LDP + j] /= ljj;
+        if (lane == j) { sD[j * LDP + j] = djj * inv; sInv[j] = inv; }
+        if (lane > j && lane < kb) sD[lane * LDP + j] *= inv;
         __syncwarp();
         if (lane > j && lane < kb) {
           const double lij = sD[lane * LDP + j];
@@ -166,6 +179,7 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
       int i = e / kb, j = e - i * kb;
       if (j <= i) A[size_t(k0 + i) * n + k0 + j] = sD[i * LDP + j];
     }
+    for (int j = threadIdx.x; j < kb; j += blockDim.x) d.dinv[size_t(m) * n + k0 + j] = sInv[j];
     const int t0 = k0 + kb, t = n - t0;
     // panel: row i of the block column solves x L_kk^T = a
     for (int i = threadIdx.x; i < t; i += blockDim.x) {
@@ -179,7 +193,7 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
           double s = x[j];
 #pragma unroll
           for (int l = 0; l < j; ++l) s -= x[l] * sD[j * LDP + l];
-          x[j] = s / sD[j * LDP + j];
+          x[j] = s * sInv[j];
         }
       }
 #pragma unroll
@@ -224,7 +238,7 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
     if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
     return;
   }
-  chol_solve_2rhs(A, n, sb);
+  chol_solve_2rhs(A, d.dinv + size_t(m) * n, n, sb, reinterpret_cast<double (*)[LDP]>(sD));
   bool bad = false;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
     xo[i] = sb[i];
@@ -234,21 +248,26 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
   if (threadIdx.x == 0) d.status[m] = bad ? EDT_ENONFINITE : EDT_OK;
 }
 
-__global__ void __launch_bounds__(256) refine_update_kernel(Dev d) {
-  extern __shared__ __align__(16) double sm[];
-  const int n = d.nz, m = blockIdx.x;
-  double* sb = sm;
-  if (d.status[m] != EDT_OK) return;
-  if (d.row_off[m + 1] == d.row_off[m]) return;
-  const double lam = d.trace[m];
+// mode 0: x = (LL^T)^-1 b; mode 1 (refinement): x += (LL^T)^-1 (r - lam x).
+__global__ void __launch_bounds__(256) chol_solve_kernel(Dev d, int mode) {
+  extern __shared__ __align__(16) double sb[];
+  __shared__ double sL[NB][LDP];
+  const int m = blockIdx.x, n = d.nz;
   double* xo = d.x + size_t(m) * n * 2;
-  const double* r = d.r + size_t(m) * n * 2;
-  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) sb[i] = r[i] - lam * xo[i];
+  const bool has_rows = d.row_off[m + 1] > d.row_off[m];
+  if (!has_rows || d.status[m] != EDT_OK) {
+    if (mode == 0 || d.status[m] != EDT_OK)
+      for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    return;
+  }
+  const double lam = d.trace[m];
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
+    sb[i] = mode == 0 ? d.b[size_t(m) * n * 2 + i] : d.r[size_t(m) * n * 2 + i] - lam * xo[i];
   __syncthreads();
-  chol_solve_2rhs(d.G + size_t(m) * n * n, n, sb);
+  chol_solve_2rhs(d.G + size_t(m) * n * n, d.dinv + size_t(m) * n, n, sb, sL);
   bool bad = false;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
-    double v = xo[i] + sb[i];
+    const double v = mode == 0 ? sb[i] : xo[i] + sb[i];
     xo[i] = v;
     if (!isfinite(v)) bad = true;
   }
@@ -272,6 +291,8 @@ cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+int chol_launches(int nz) { return 1; }
+
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
   size_t smem = (size_t(d.nz) * LDP + NB * LDP + 2 * d.nz + 40) * sizeof(double);
   cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -280,8 +301,7 @@ cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
 }
 
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s) {
-  size_t smem = size_t(2 * d.nz) * sizeof(double);
-  refine_update_kernel<<<d.nsub, 256, smem, s>>>(d);
+  chol_solve_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 1);
   return cudaGetLastError();
 }
 

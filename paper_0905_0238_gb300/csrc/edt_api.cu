@@ -40,6 +40,8 @@ struct edt_ctx {
   std::vector<FreqConst> fc;
   std::vector<int> z_layer;
   std::vector<double> z_off;
+  std::vector<float> z_off32;      // [nz][4]
+  std::vector<float> fc32;         // [nf] sqrt|s_f|
   std::vector<uint32_t> rows;
   std::vector<long long> row_off;
   std::vector<long long> counts_cut;
@@ -53,8 +55,8 @@ struct edt_ctx {
   size_t ws_bytes = 0;
   void* ws = nullptr;
   Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_tw64, r_tw32, r_segm, r_segr0,
-      r_segn, r_ctas, r_mslot, r_coef, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gpart, r_G,
-      r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
+      r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gpart, r_G,
+      r_dinv, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
   Dev dev{};
   cudaStream_t last_stream = nullptr;
   int last_status = EDT_OK;
@@ -130,6 +132,18 @@ void plan(edt_ctx* c) {
     c->z_layer[j] = l;
     c->z_off[j] = z - c->tops[l];
   }
+  // FP32 (hi, lo) pairs of the offset below the layer top and of 2 h_l - offset
+  c->z_off32.assign(size_t(c->nz) * 4, 0.f);
+  for (int j = 0; j < c->nz; ++j) {
+    const int l = c->z_layer[j];
+    const double off = c->z_off[j];
+    const double o2 = l < c->nlayer - 1 ? 2.0 * (c->tops[l + 1] - c->tops[l]) - off : 0.0;
+    const float oh = float(off), o2h = float(o2);
+    c->z_off32[4 * j + 0] = oh; c->z_off32[4 * j + 1] = float(off - double(oh));
+    c->z_off32[4 * j + 2] = o2h; c->z_off32[4 * j + 3] = float(o2 - double(o2h));
+  }
+  c->fc32.resize(c->nf);
+  for (int f = 0; f < c->nf; ++f) c->fc32[f] = float(std::sqrt(c->fc[f].s_abs));
   // rows of every subproblem, in (f, p) order, evanescent cut and optional folding
   const double cmin = *std::min_element(c->vel.begin(), c->vel.end());
   c->rows.clear();
@@ -244,7 +258,10 @@ void layout(edt_ctx* c) {
   take(c->r_segn, std::max<size_t>(c->seg_nrow.size(), 1) * sizeof(long long));
   take(c->r_ctas, std::max<size_t>(c->cta_seg0.size(), 1) * sizeof(int));
   take(c->r_mslot, (ns + 1) * sizeof(int));
-  take(c->r_coef, nf * nk * c->nlayer * 5 * sizeof(double2));
+  take(c->r_zo32, nz * 4 * sizeof(float));
+  take(c->r_fc32, nf * sizeof(float));
+  take(c->r_coef, nf * nk * c->nlayer * 7 * sizeof(double2));
+  take(c->r_coef32, mixed ? nf * nk * c->nlayer * 8 * sizeof(float) : 0);
   take(c->r_g64, nf * nk * nz * sizeof(double2));
   take(c->r_g32, mixed ? nf * nk * nz * sizeof(float2) : 0);
   take(c->r_X, nf * N * N * (mixed ? sizeof(float2) : sizeof(double2)));
@@ -253,6 +270,7 @@ void layout(edt_ctx* c) {
   take(c->r_rhs, std::max<size_t>(R, 1) * 2 * (mixed ? sizeof(float2) : sizeof(double2)));
   take(c->r_gpart, mixed ? size_t(c->nslot) * TC_M * tc_cols(c->nz) * sizeof(float) : 0);
   take(c->r_G, ns * nz * nz * sizeof(double));
+  take(c->r_dinv, ns * nz * sizeof(double));
   take(c->r_b, ns * nz * 2 * sizeof(double));
   take(c->r_tr, ns * sizeof(double));
   take(c->r_x, ns * nz * 2 * sizeof(double));
@@ -289,6 +307,9 @@ void bind(edt_ctx* c) {
   d.m_slot0 = at<const int*>(c, c->r_mslot);
   d.nseg = c->nslot; d.ncta_gram = c->ncta_gram;
   d.coef = at<double2*>(c, c->r_coef);
+  d.coef32 = c->r_coef32.bytes ? at<float*>(c, c->r_coef32) : nullptr;
+  d.z_off32 = at<const float*>(c, c->r_zo32);
+  d.fc32_sqrt_s = at<const float*>(c, c->r_fc32);
   d.g64 = at<double2*>(c, c->r_g64);
   d.g32 = c->r_g32.bytes ? at<float2*>(c, c->r_g32) : nullptr;
   d.X = at<void*>(c, c->r_X);
@@ -297,6 +318,7 @@ void bind(edt_ctx* c) {
   d.rhs = at<void*>(c, c->r_rhs);
   d.gpart = c->r_gpart.bytes ? at<float*>(c, c->r_gpart) : nullptr;
   d.G = at<double*>(c, c->r_G);
+  d.dinv = at<double*>(c, c->r_dinv);
   d.b = at<double*>(c, c->r_b);
   d.trace = at<double*>(c, c->r_tr);
   d.x = at<double*>(c, c->r_x);
@@ -328,7 +350,7 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   const bool mixed = c->cfg.precision == EDT_MIXED;
   c->last_stream = s;
   prof_mark(c, 0, s);
-  EDT_TRY(launch_green(d, s));
+  EDT_TRY(launch_green(d, s, mixed ? GREEN_G32 : GREEN_G64));
   prof_mark(c, 1, s);
   if (mixed) { EDT_TRY(launch_transform<float>(d, D, D_dtype, s)); }
   else { EDT_TRY(launch_transform<double>(d, D, D_dtype, s)); }
@@ -400,6 +422,8 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRYI(upload(c, c->r_lvel, c->vel));
   EDT_TRYI(upload(c, c->r_zl, c->z_layer));
   EDT_TRYI(upload(c, c->r_zo, zo));
+  EDT_TRYI(upload(c, c->r_zo32, c->z_off32));
+  EDT_TRYI(upload(c, c->r_fc32, c->fc32));
   EDT_TRYI(upload(c, c->r_rows, c->rows));
   EDT_TRYI(upload(c, c->r_roff, c->row_off));
   EDT_TRYI(upload(c, c->r_tw64, c->tw64));
@@ -449,7 +473,7 @@ int edt_forward(edt_ctx* c, const void* V, int V_dtype, void* D, int D_dtype, vo
   if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c->last_stream = s;
-  EDT_TRY(launch_green(c->dev, s));
+  EDT_TRY(launch_green(c->dev, s, GREEN_G64));
   EDT_TRY(launch_forward(c->dev, V, V_dtype, D, D_dtype, s));
   return EDT_OK;
 }
@@ -459,7 +483,7 @@ int edt_green(edt_ctx* c, void* g_dev, void* stream) {
   if (!c->ws) return EDT_ENOMEM_WS;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c->last_stream = s;
-  EDT_TRY(launch_green(c->dev, s));
+  EDT_TRY(launch_green(c->dev, s, GREEN_G64));
   EDT_TRY(cudaMemcpyAsync(g_dev, c->dev.g64, c->r_g64.bytes, cudaMemcpyDeviceToDevice, s));
   return EDT_OK;
 }
@@ -480,7 +504,7 @@ int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr,
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
   c->last_stream = s;
-  EDT_TRY(launch_green(d, s));
+  EDT_TRY(launch_green(d, s, mixed ? GREEN_G32 : GREEN_G64));
   if (mixed) { EDT_TRY(launch_transform<float>(d, D, D_dtype, s)); EDT_TRY(launch_rhs<float>(d, s)); }
   else { EDT_TRY(launch_transform<double>(d, D, D_dtype, s)); EDT_TRY(launch_rhs<double>(d, s)); }
   if (mixed) {
@@ -516,9 +540,10 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   o->workspace_bytes = c->ws_bytes;
   o->gram_flop = 2.0 * 2.0 * double(o->rows_solved) * double(c->nz) * double(c->nz + 2);
   o->last_status = c->last_status;
-  // kernels launched by one edt_invert: green (2), transform (2), rhs (1), Gram (FP64: 1;
-  // mixed: tensor-core + reduce 2), Cholesky (1), per refinement step (2), inverse (1)
-  o->launches_per_invert = c->cfg.precision == EDT_MIXED ? 9 + 2 * c->cfg.refine : 8;
+  // kernels launched by one edt_invert: green (3), transform (2), rhs (1), Gram (FP64: 1;
+  // mixed: tensor-core + reduce 2), batched Cholesky, per refinement step (2), inverse (1)
+  o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 9 + 2 * c->cfg.refine : 7) +
+                           chol_launches(c->nz);
   o->gram_rows_padded = 0;
   for (long long n : c->seg_nrow) o->gram_rows_padded += (n + TC_KC - 1) / TC_KC * TC_KC;
   if (c->ws) {

@@ -41,6 +41,8 @@ struct Dev {
   const double* layer_vel;      // [nlayer]
   const int* z_layer;           // [nz] layer of each sample depth
   const double* z_off;          // [nz] depth below that layer's top
+  const float* z_off32;         // [nz][4] (off hi, off lo, 2h - off hi, 2h - off lo) as floats
+  const float* fc32_sqrt_s;     // [nf] sqrt|s_f| as float
   const uint32_t* rows;         // [rows_solved], grouped by m
   const long long* row_off;     // [nsub + 1]
   const double2* tw64;          // [N/2] exp(-2 pi i k / N)
@@ -52,7 +54,8 @@ struct Dev {
   const int* m_slot0;           //                   per m first partial slot [nsub + 1]
   int nseg, ncta_gram;
   // scratch
-  double2* coef;                // [nf][nk][nlayer][3] kappa, rho, amp
+  double2* coef;                // [nf][nk][nlayer][7] recursion coefficients (FP64)
+  float* coef32;                // [nf][nk][nlayer][8] FP32 copies for the fast evaluation
   double2* g64;                 // [nf][nk][nz]
   float2* g32;                  // [nf][nk][nz]  sqrt|s_f| g, mixed path
   void* X;                      // [nf][N][N] complex, path precision
@@ -61,6 +64,7 @@ struct Dev {
   void* rhs;                    // [rows_solved][2] complex, path precision
   float* gpart;                 // tensor-core Gram partial tiles [nslot][TM_COLS * 128]
   double* G;                    // [nsub][nz][nz]  Gram, then its Cholesky factor
+  double* dinv;                 // [nsub][nz]      1 / diagonal of the factor
   double* b;                    // [nsub][nz][2]
   double* trace;                // [nsub]
   double* x;                    // [nsub][nz][2]
@@ -72,8 +76,9 @@ struct Dev {
 };
 
 // ---- launchers (each returns cudaGetLastError()) ---------------------------------------
-cudaError_t launch_green(const Dev& d, cudaStream_t s);
-cudaError_t launch_green_export(const Dev& d, double2* out, cudaStream_t s);
+constexpr int GREEN_G64 = 1, GREEN_G32 = 2;   // tables launch_green writes
+// GREEN_G32 alone: the fast FP32 evaluation for the mixed path (no FP64 table)
+cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables);
 
 template <typename T>
 cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, cudaStream_t s);
@@ -84,6 +89,7 @@ cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace
 cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s);   // partials -> G, b (FP64)
 cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s);   // trace[m] = sum_z G[m][z][z]
+int chol_launches(int nz);                                      // kernels of launch_chol_solve
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s);
 cudaError_t launch_refine(const Dev& d, cudaStream_t s);          // r += Ahat^T (dhat - Ahat x)
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s);   // x += (LL^T)^-1 (r - lam x)

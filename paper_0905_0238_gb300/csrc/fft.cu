@@ -21,6 +21,10 @@ namespace edt {
 namespace {
 
 __device__ __forceinline__ int bitrev(int i, int logn) { return int(__brev(unsigned(i)) >> (32 - logn)); }
+// shared-memory index with one pad element per 16: bit-reversed stores and strided
+// butterflies then spread over the banks instead of hitting one
+__device__ __forceinline__ int pd(int e) { return e + (e >> 4); }
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4); }
 __host__ __device__ __forceinline__ int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 template <typename T> __device__ __forceinline__ const cplx_t<T>* twid(const Dev& d);
@@ -43,25 +47,48 @@ template <typename T2> __device__ __forceinline__ void store_c(void* p, int dtyp
   else reinterpret_cast<double2*>(p)[i] = make_double2(double(v.x), double(v.y));
 }
 
-// In-place radix-2 DIT butterflies over `batch` sequences of length N held in shared
-// memory in bit-reversed order; sequence b starts at s + b * bstride.  sign = -1 uses
-// e^{-2 pi i k/N}, sign = +1 its conjugate.  All threads of the block participate.
+// In-place decimation-in-time FFT of `batch` sequences of length N = 2^logn held in
+// shared memory in bit-reversed order; sequence b starts at s + b * bstride.  sign = -1
+// uses e^{-2 pi i k/N}, sign = +1 its conjugate.  One radix-2 stage when logn is odd, then
+// pairs of radix-2 stages fused into radix-4 butterflies (one barrier per pair).  All
+// threads of the block participate; indices use shifts only.
 template <typename T, typename T2>
-__device__ void block_fft(T2* s, int N, int batch, int bstride, const T2* tw, int sign) {
-  const int half = N >> 1;
-  const int total = half * batch;
-  for (int h = 1; h < N; h <<= 1) {
-    const int step = N / (2 * h);
+__device__ void block_fft(T2* s, int N, int logn, int batch, int bstride, const T2* tw, int sign) {
+  int lh = 0;                       // log2 of the current half-size h
+  if (logn & 1) {                   // radix-2 stage, h = 1 (twiddle 1)
+    const int lq = logn - 1, total = batch << lq;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      int b = t / half, j = t - b * half;
-      int grp = j / h, jj = j - grp * h;
-      int i0 = grp * 2 * h + jj, i1 = i0 + h;
-      T2 w = tw[jj * step];
-      if (sign > 0) w.y = -w.y;
+      const int b = t >> lq, j = t & ((1 << lq) - 1);
       T2* base = s + b * bstride;
-      T2 u = base[i0], v = base[i1] * w;
+      const int i0 = pd(2 * j), i1 = pd(2 * j + 1);
+      const T2 u = base[i0], v = base[i1];
       base[i0] = u + v;
       base[i1] = u - v;
+    }
+    __syncthreads();
+    lh = 1;
+  }
+  for (; lh < logn; lh += 2) {      // fused stages h and 2h
+    const int h = 1 << lh;
+    const int lq = logn - 2, total = batch << lq;   // N/4 radix-4 butterflies per sequence
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int b = t >> lq, q = t & ((1 << lq) - 1);
+      const int jj = q & (h - 1), blk = q >> lh;    // jj < h, block of 4h
+      T2* base = s + b * bstride;
+      const int e0 = (blk << (lh + 2)) + jj;
+      const int i0 = pd(e0), i1 = pd(e0 + h), i2 = pd(e0 + 2 * h), i3 = pd(e0 + 3 * h);
+      T2 w1 = tw[jj << (logn - 1 - lh)];            // W_{2h}^jj
+      T2 w2 = tw[jj << (logn - 2 - lh)];            // W_{4h}^jj
+      if (sign > 0) { w1.y = -w1.y; w2.y = -w2.y; }
+      const T2 x0 = base[i0], x1 = base[i1] * w1, x2 = base[i2], x3 = base[i3] * w1;
+      const T2 y0 = x0 + x1, y1 = x0 - x1, y2 = x2 + x3, y3 = x2 - x3;
+      const T2 a = w2 * y2;
+      T2 c = w2 * y3;                               // times W_4 = -i (sign -) or +i (sign +)
+      c = sign < 0 ? cmk(c.y, -c.x) : cmk(-c.y, c.x);
+      base[i0] = y0 + a;
+      base[i2] = y0 - a;
+      base[i1] = y1 + c;
+      base[i3] = y1 - c;
     }
     __syncthreads();
   }
@@ -77,14 +104,16 @@ __global__ void fft_rows_kernel(Dev d, const void* in, int in_dtype, void* out, 
   const int N = d.N, logn = ilog2(N);
   const long long r0 = (long long)blockIdx.x * rpb;
   const int nr = int(min((long long)rpb, nrows - r0));
+  const int ld = padded_len(N);
   for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
-    int r = e / N, i = e - r * N;
-    s[r * N + bitrev(i, logn)] = load_c<T2>(in, in_dtype, size_t(r0) * N + e);
+    const int r = e >> logn, i = e & (N - 1);
+    s[r * ld + pd(bitrev(i, logn))] = load_c<T2>(in, in_dtype, size_t(r0) * N + e);
   }
   __syncthreads();
-  block_fft<T, T2>(s, N, nr, N, twid<T>(d), sign);
+  block_fft<T, T2>(s, N, logn, nr, ld, twid<T>(d), sign);
   for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
-    T2 v = s[e];
+    const int r = e >> logn, i = e & (N - 1);
+    T2 v = s[r * ld + pd(i)];
     store_c<T2>(out, out_dtype, size_t(r0) * N + e, cmk(v.x * scale, v.y * scale));
   }
 }
@@ -96,18 +125,18 @@ __global__ void fft_cols_kernel(Dev d, cplx_t<T>* X, int cpb, int sign, T scale)
   using T2 = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* s = reinterpret_cast<T2*>(smem_raw);
-  const int N = d.N, logn = ilog2(N), ld = N + 1;
+  const int N = d.N, logn = ilog2(N), ld = padded_len(N) + 1;
   const int c0 = blockIdx.x * cpb;
   T2* P = X + size_t(blockIdx.y) * N * N;
   for (int e = threadIdx.x; e < N * cpb; e += blockDim.x) {
     int r = e / cpb, c = e - r * cpb;
-    s[c * ld + bitrev(r, logn)] = P[size_t(r) * N + c0 + c];
+    s[c * ld + pd(bitrev(r, logn))] = P[size_t(r) * N + c0 + c];
   }
   __syncthreads();
-  block_fft<T, T2>(s, N, cpb, ld, twid<T>(d), sign);
+  block_fft<T, T2>(s, N, logn, cpb, ld, twid<T>(d), sign);
   for (int e = threadIdx.x; e < N * cpb; e += blockDim.x) {
     int r = e / cpb, c = e - r * cpb;
-    T2 v = s[c * ld + r];
+    T2 v = s[c * ld + pd(r)];
     P[size_t(r) * N + c0 + c] = cmk(v.x * scale, v.y * scale);
   }
 }
@@ -118,7 +147,7 @@ cudaError_t rows_fft(const Dev& d, const void* in, int in_dtype, void* out, int 
   using T2 = cplx_t<T>;
   int rpb = (int(sizeof(T)) == 4 ? 4096 : 2048) / d.N;
   if (rpb < 1) rpb = 1;
-  size_t smem = size_t(rpb) * d.N * sizeof(T2);
+  size_t smem = size_t(rpb) * padded_len(d.N) * sizeof(T2);
   cudaFuncSetAttribute(fft_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   long long nb = (nrows + rpb - 1) / rpb;
   fft_rows_kernel<T><<<unsigned(nb), 256, smem, st>>>(d, in, in_dtype, out, out_dtype, nrows, rpb,
@@ -131,7 +160,7 @@ cudaError_t cols_fft(const Dev& d, cplx_t<T>* X, int planes, int sign, T scale, 
   using T2 = cplx_t<T>;
   int cpb = 128 / int(sizeof(T2));
   if (cpb > d.N) cpb = d.N;
-  size_t smem = size_t(cpb) * (d.N + 1) * sizeof(T2);
+  size_t smem = size_t(cpb) * (padded_len(d.N) + 1) * sizeof(T2);
   cudaFuncSetAttribute(fft_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   dim3 g(d.N / cpb, planes);
   fft_cols_kernel<T><<<g, 256, smem, st>>>(d, X, cpb, sign, scale);
@@ -144,7 +173,7 @@ constexpr int INV_ZT = 8;
 __global__ void inverse_kernel(Dev d, void* V, int V_dtype) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* s = reinterpret_cast<double2*>(smem_raw);
-  const int N = d.N, logn = ilog2(N), ld = N + 1, half = N / 2;
+  const int N = d.N, logn = ilog2(N), ld = padded_len(N) + 1, half = N / 2;
   const int z0 = blockIdx.x * INV_ZT;
   const int nzt = min(INV_ZT, d.nz - z0);
   for (int e = threadIdx.x; e < (half + 1) * nzt; e += blockDim.x) {
@@ -155,15 +184,15 @@ __global__ void inverse_kernel(Dev d, void* V, int V_dtype) {
     double im = (m == 0 || m == half) ? 0.0 : xm[1];
     if (d.status[m] != EDT_OK) { re = 0.0; im = 0.0; }
     d.vhat[size_t(m) * d.nz + z] = make_double2(re, im);
-    s[t * ld + bitrev(m, logn)] = make_double2(re, im);
-    if (m > 0 && m < half) s[t * ld + bitrev(N - m, logn)] = make_double2(re, -im);
+    s[t * ld + pd(bitrev(m, logn))] = make_double2(re, im);
+    if (m > 0 && m < half) s[t * ld + pd(bitrev(N - m, logn))] = make_double2(re, -im);
   }
   __syncthreads();
-  block_fft<double, double2>(s, N, nzt, ld, d.tw64, +1);
+  block_fft<double, double2>(s, N, logn, nzt, ld, d.tw64, +1);
   const double inv = 1.0 / double(N);
   for (int e = threadIdx.x; e < N * nzt; e += blockDim.x) {
     int xi = e / nzt, t = e - xi * nzt;
-    double v = s[t * ld + xi].x * inv;
+    double v = s[t * ld + pd(xi)].x * inv;
     size_t o = size_t(xi) * d.nz + z0 + t;
     if (V_dtype == EDT_F64) reinterpret_cast<double*>(V)[o] = v;
     else reinterpret_cast<float*>(V)[o] = float(v);
@@ -175,7 +204,7 @@ __global__ void inverse_kernel(Dev d, void* V, int V_dtype) {
 __global__ void lateral_dft_kernel(Dev d, const void* V, int V_dtype) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* s = reinterpret_cast<double2*>(smem_raw);
-  const int N = d.N, logn = ilog2(N), ld = N + 1;
+  const int N = d.N, logn = ilog2(N), ld = padded_len(N) + 1;
   const int z0 = blockIdx.x * INV_ZT;
   const int nzt = min(INV_ZT, d.nz - z0);
   for (int e = threadIdx.x; e < N * nzt; e += blockDim.x) {
@@ -183,13 +212,13 @@ __global__ void lateral_dft_kernel(Dev d, const void* V, int V_dtype) {
     size_t o = size_t(xi) * d.nz + z0 + t;
     double v = V_dtype == EDT_F64 ? reinterpret_cast<const double*>(V)[o]
                                   : double(reinterpret_cast<const float*>(V)[o]);
-    s[t * ld + bitrev(xi, logn)] = make_double2(v, 0.0);
+    s[t * ld + pd(bitrev(xi, logn))] = make_double2(v, 0.0);
   }
   __syncthreads();
-  block_fft<double, double2>(s, N, nzt, ld, d.tw64, -1);
+  block_fft<double, double2>(s, N, logn, nzt, ld, d.tw64, -1);
   for (int e = threadIdx.x; e < N * nzt; e += blockDim.x) {
     int m = e / nzt, t = e - m * nzt;
-    d.vfull[size_t(m) * d.nz + z0 + t] = s[t * ld + m];
+    d.vfull[size_t(m) * d.nz + z0 + t] = s[t * ld + pd(m)];
   }
 }
 
@@ -245,7 +274,7 @@ template cudaError_t launch_transform<float>(const Dev&, const void*, int, cudaS
 template cudaError_t launch_transform<double>(const Dev&, const void*, int, cudaStream_t);
 
 cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s) {
-  size_t smem = size_t(INV_ZT) * (d.N + 1) * sizeof(double2);
+  size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);
   cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   inverse_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
   return cudaGetLastError();
@@ -253,7 +282,7 @@ cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s) {
 
 cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
                            cudaStream_t s) {
-  size_t smem = size_t(INV_ZT) * (d.N + 1) * sizeof(double2);
+  size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);
   cudaFuncSetAttribute(lateral_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   lateral_dft_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
   cudaError_t e = cudaGetLastError();

@@ -11,12 +11,12 @@
 //   * rows of all subproblems are concatenated and split evenly over the CTAs; a CTA's
 //     range falls into 1..few "segments" (its part of one subproblem), each accumulated
 //     in TMEM and written out as an FP32 partial tile, summed per subproblem afterwards;
-//   * warps 0-3 are producers: for 32 complex rows per pipeline stage they rebuild the
+//   * warps 0-7 are producers: for 32 complex rows per pipeline stage they rebuild the
 //     kernel rows a(z) = |s_f| g(k_p, z) g(k_q, z) from the L2-resident FP32 table of
 //     sqrt|s_f| g, scale weight-2 rows by sqrt 2, split into BF16 hi (and lo), and store
 //     them K-major with the 128-byte swizzle; (Re a, Im a) of one complex row are two
 //     adjacent K elements.  The data rows d_+, d_- occupy two extra operand rows;
-//   * warp 4 issues tcgen05.mma (M = 128, K = 16) from one thread: both operands are
+//   * warp 8 issues tcgen05.mma (M = 128, K = 16) from one thread: both operands are
 //     views of the same stage tile (A = depth rows of one 128-row half, B = all depth rows
 //     plus the data rows), so one generated tile feeds the whole upper block row;
 //   * after the last stage of a segment the producers read the accumulator with
@@ -31,7 +31,7 @@ namespace edt {
 
 namespace {
 
-constexpr int PRODUCER_WARPS = 4;
+constexpr int PRODUCER_WARPS = 8;
 constexpr int NTHREADS = (PRODUCER_WARPS + 1) * 32;
 constexpr int ROWB = 128;                       // bytes per operand row per stage (64 bf16)
 constexpr long long WAIT_CYCLES = 4000000000ll; // ~2 s at 2 GHz: a wait longer than this gives up
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     __syncwarp();
   } else {
     // ------------------------------------------------------------ producers + epilogue
-    const int ptid = threadIdx.x;                 // 0..127
+    const int ptid = threadIdx.x;                 // 0..255
     const int nunits = (nzp / 32) * 8;            // (32-depth group, 16-byte K chunk)
     const int N = d.N, msk = N - 1;
     const float2* g32 = d.g32;
@@ -308,35 +308,51 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
         unsigned char* hi = ops + size_t(s) * NCOMP * stage_bytes;
         unsigned char* lo = hi + stage_bytes;
         float trs = 0.f;
-        for (int u = warp; u < nunits; u += PRODUCER_WARPS) {
-          const int zg = u >> 3, c = u & 7;
-          const int z = zg * 32 + lane;
-          float2 a[4];
+        // two (32-depth, 16-byte chunk) units per warp at a time: all 16 table loads of
+        // both are issued before either is converted, to keep enough L2 reads in flight
+        for (int u0 = warp; u0 < nunits; u0 += 2 * PRODUCER_WARPS) {
+          float2 gpv[2][4], gqv[2][4];
+          float swv[2][4];
+          int zz[2], cc[2];
 #pragma unroll
-          for (int rr = 0; rr < 4; ++rr) {
-            const RowEnt e = rt[c * 4 + rr];
-            if (z < nz && e.sw != 0.f) {
-              const float2 gp = g32[e.offp + z], gq = g32[e.offq + z];
-              const float2 v = gp * gq;
-              a[rr] = make_float2(e.sw * v.x, e.sw * v.y);
-            } else {
-              a[rr] = make_float2(0.f, 0.f);
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int u = u0 + h2 * PRODUCER_WARPS;
+            const bool uv = u < nunits;
+            zz[h2] = uv ? (u >> 3) * 32 + lane : nzp;     // nzp: marks an absent unit
+            cc[h2] = u & 7;
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+              const RowEnt e = rt[cc[h2] * 4 + rr];
+              const bool ok2 = uv && zz[h2] < nz && e.sw != 0.f;
+              swv[h2][rr] = ok2 ? e.sw : 0.f;
+              gpv[h2][rr] = ok2 ? __ldg(g32 + e.offp + zz[h2]) : make_float2(0.f, 0.f);
+              gqv[h2][rr] = ok2 ? __ldg(g32 + e.offq + zz[h2]) : make_float2(0.f, 0.f);
             }
-            trs = fmaf(a[rr].x, a[rr].x, fmaf(a[rr].y, a[rr].y, trs));
           }
-          uint4 h;
-          h.x = pack_bf16(a[0].x, a[0].y); h.y = pack_bf16(a[1].x, a[1].y);
-          h.z = pack_bf16(a[2].x, a[2].y); h.w = pack_bf16(a[3].x, a[3].y);
-          const uint32_t off = sw_off(z, c);
-          *reinterpret_cast<uint4*>(hi + off) = h;
-          if (PASSES == 3) {
-            uint4 l;
-            const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
-            float2 h0 = __bfloat1622float2(hb[0]), h1 = __bfloat1622float2(hb[1]);
-            float2 h2 = __bfloat1622float2(hb[2]), h3 = __bfloat1622float2(hb[3]);
-            l.x = pack_bf16(a[0].x - h0.x, a[0].y - h0.y); l.y = pack_bf16(a[1].x - h1.x, a[1].y - h1.y);
-            l.z = pack_bf16(a[2].x - h2.x, a[2].y - h2.y); l.w = pack_bf16(a[3].x - h3.x, a[3].y - h3.y);
-            *reinterpret_cast<uint4*>(lo + off) = l;
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            if (zz[h2] >= nzp) continue;
+            float2 a[4];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+              const float2 v = gpv[h2][rr] * gqv[h2][rr];
+              a[rr] = make_float2(swv[h2][rr] * v.x, swv[h2][rr] * v.y);
+              trs = fmaf(a[rr].x, a[rr].x, fmaf(a[rr].y, a[rr].y, trs));
+            }
+            uint4 h;
+            h.x = pack_bf16(a[0].x, a[0].y); h.y = pack_bf16(a[1].x, a[1].y);
+            h.z = pack_bf16(a[2].x, a[2].y); h.w = pack_bf16(a[3].x, a[3].y);
+            const uint32_t off = sw_off(zz[h2], cc[h2]);
+            *reinterpret_cast<uint4*>(hi + off) = h;
+            if (PASSES == 3) {
+              uint4 l;
+              const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
+              float2 h0 = __bfloat1622float2(hb[0]), h1 = __bfloat1622float2(hb[1]);
+              float2 hh2 = __bfloat1622float2(hb[2]), h3 = __bfloat1622float2(hb[3]);
+              l.x = pack_bf16(a[0].x - h0.x, a[0].y - h0.y); l.y = pack_bf16(a[1].x - h1.x, a[1].y - h1.y);
+              l.z = pack_bf16(a[2].x - hh2.x, a[2].y - hh2.y); l.w = pack_bf16(a[3].x - h3.x, a[3].y - h3.y);
+              *reinterpret_cast<uint4*>(lo + off) = l;
+            }
           }
         }
         // data rows: operand rows nzp (d_+) and nzp + 1 (d_-), 8 chunks each
@@ -369,12 +385,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
       if (!mbar_wait(acc_full, unsigned((si - s0) & 1), abort_flag)) { ok = false; break; }
       tc_fence_after();
       float* out = d.gpart + size_t(slot) * size_t(ncols) * TC_M;
-      const uint32_t lane_base = uint32_t(warp * 32) << 16;
-      for (int c0 = 0; c0 < ncols; c0 += 16) {
+      const int quarter = warp & 3, group = warp >> 2;   // TMEM lanes 32*quarter..+31
+      const uint32_t lane_base = uint32_t(quarter * 32) << 16;
+      for (int c0 = group * 16; c0 < ncols; c0 += 32) {
         float v[16];
         tmem_ld16(tmem + lane_base + uint32_t(c0), v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) out[size_t(c0 + j) * TC_M + warp * 32 + lane] = v[j];
+        for (int j = 0; j < 16; ++j) out[size_t(c0 + j) * TC_M + quarter * 32 + lane] = v[j];
       }
       tc_fence_before();
       mbar_arrive(acc_empty);

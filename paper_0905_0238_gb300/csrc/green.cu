@@ -13,9 +13,16 @@
 // depth sample to the next by multiplication with exp(+-i kappa_j dz) (error ~ n ulp),
 // re-anchored by a direct evaluation at every layer entry and chunk start.
 //
-// Kernels: green_coef (one thread per (f, n): the two recursions, all in FP64) and
-// green_eval (a CTA per (f, block of 32 n); each warp marches a chunk of depths and
-// stages its tile in shared memory so that the table rows are written coalesced).
+// Kernels: green_layer (one thread per (f, n, layer): vertical wavenumber and the layer's
+// phase factors, the FP64 transcendentals, fully parallel), green_recursion (one thread
+// per (f, n): the two recursions, FP64), then one of two evaluations:
+//   green_eval64  (FP64 table): a CTA per (f, block of 32 n); each warp marches a chunk of
+//                 depths by the recurrence and stages its tile in shared memory so the
+//                 table rows are written coalesced;
+//   green_eval32  (FP32 table sqrt|s_f| g for the mixed path): one thread per (f, n, z);
+//                 each exponential's phase and decay are formed and range-reduced in FP64
+//                 (Cody-Waite for the phase, integer/fraction split for the decay) and
+//                 evaluated with FP32 sincos/exp2 of the reduced arguments, ~1e-7 relative.
 #include "edt_internal.h"
 #include "cplx.cuh"
 
@@ -23,58 +30,96 @@ namespace edt {
 
 namespace {
 
-constexpr int NCOEF = 5;   // kappa, rho, amp, exp(i kappa dz), exp(-i kappa dz)
+// coefficient slots per (f, n, layer): kappa, rho, amp, exp(i kappa dz), exp(-i kappa dz),
+// exp(i kappa h), 1 / (1 + r_{j+1})
+constexpr int NCOEF = 7;
+constexpr int C_KAP = 0, C_RHO = 1, C_AMP = 2, C_E = 3, C_EI = 4, C_EH = 5, C_INV1R = 6;
+// FP32 copies for the fast evaluation: kappa.x and kappa.y as (hi, lo) pairs, amp, rho
+constexpr int NCOEF32 = 8;
 
-__global__ void green_coef_kernel(Dev d) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  int f = blockIdx.y;
-  if (n >= d.nk) return;
+// 1 / b with one real division (|b| is O(1e-3 .. 1e3) for every use here)
+__device__ __forceinline__ double2 cinv(double2 b) {
+  const double r = 1.0 / (b.x * b.x + b.y * b.y);
+  return cmk(b.x * r, -b.y * r);
+}
+
+__global__ void green_layer_kernel(Dev d, int want_steps) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = d.nlayer;
+  const long long total = (long long)d.nf * d.nk * J;
+  if (gid >= total) return;
+  const int j = int(gid % J);
+  const long long fn = gid / J;
+  const int n = int(fn % d.nk), f = int(fn / d.nk);
   const FreqConst fc = d.fc[f];
   const double L = double(d.N) * d.dx;
   const double k = 2.0 * M_PI * double(n) / L;
   const double2 om = cmk(fc.om_re, fc.om_im);
   const double2 om2 = om * om;
+  const double inv_c2 = 1.0 / (d.layer_vel[j] * d.layer_vel[j]);
+  const double2 kap = csqrt_upper(cmk(om2.x * inv_c2 - k * k, om2.y * inv_c2));
+  double2* c = d.coef + gid * NCOEF;
+  c[C_KAP] = kap;
+  if (j < J - 1) {
+    const double h = d.layer_top[j + 1] - d.layer_top[j];
+    c[C_EH] = cexp(cmk(-kap.y * h, kap.x * h));
+  } else {
+    c[C_EH] = cmk(1.0, 0.0);
+  }
+  if (want_steps) {
+    const double2 E = cexp(cmk(-kap.y * d.dz, kap.x * d.dz));
+    c[C_E] = E;
+    c[C_EI] = cdiv(cmk(1.0, 0.0), E);
+  }
+}
+
+__global__ void green_recursion_kernel(Dev d) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (n >= d.nk) return;
   const int J = d.nlayer;
   double2* c = d.coef + (size_t(f) * d.nk + n) * size_t(J) * NCOEF;
-  for (int j = 0; j < J; ++j) {
-    double inv_c2 = 1.0 / (d.layer_vel[j] * d.layer_vel[j]);
-    double2 kap = csqrt_upper(cmk(om2.x * inv_c2 - k * k, om2.y * inv_c2));
-    c[j * NCOEF + 0] = kap;
-    c[j * NCOEF + 3] = cexp(cmk(-kap.y * d.dz, kap.x * d.dz));    // exp(i kap dz)
-    c[j * NCOEF + 4] = cexp(cmk(kap.y * d.dz, -kap.x * d.dz));    // exp(-i kap dz)
-  }
-  // upward recursion; r_j is parked in the amplitude slot until the downward pass
+  const double2 one = cmk(1.0, 0.0);
+  // upward recursion for the reflection coefficient of the stack below each interface
   double2 r_next = cmk(0.0, 0.0);
-  c[(J - 1) * NCOEF + 1] = cmk(0.0, 0.0);
-  c[(J - 1) * NCOEF + 2] = r_next;
+  c[(J - 1) * NCOEF + C_RHO] = cmk(0.0, 0.0);
+  double2 kn = c[(J - 1) * NCOEF + C_KAP];
   for (int j = J - 2; j >= 0; --j) {
-    double2 kj = c[j * NCOEF + 0], kn = c[(j + 1) * NCOEF + 0];
-    double2 y = cdiv(kn * (cmk(1.0, 0.0) - r_next), cmk(1.0, 0.0) + r_next);
-    double2 rho = cdiv(kj - y, kj + y);
-    double h = d.layer_top[j + 1] - d.layer_top[j];
-    double2 rj = rho * cexp(cmk(-2.0 * kj.y * h, 2.0 * kj.x * h));
-    c[j * NCOEF + 1] = rho;
-    c[j * NCOEF + 2] = rj;
-    r_next = rj;
+    const double2 kj = c[j * NCOEF + C_KAP], eh = c[j * NCOEF + C_EH];
+    const double2 inv1r = cinv(one + r_next);             // 1 / (1 + r_{j+1})
+    const double2 y = kn * (one - r_next) * inv1r;
+    const double2 rho = (kj - y) * cinv(kj + y);
+    c[j * NCOEF + C_RHO] = rho;
+    c[j * NCOEF + C_INV1R] = inv1r;
+    r_next = rho * (eh * eh);
+    kn = kj;
   }
   // downward recursion for the downgoing amplitude; jump g'(0+) - g'(0-) = -1
-  double2 k0 = c[0];
-  double2 amp = cdiv(cmk(0.0, 1.0), cmk(2.0 * k0.x, 2.0 * k0.y));
+  const double2 k0 = c[C_KAP];
+  double2 amp = cmk(0.0, 0.5) * cinv(k0);
   for (int j = 0; j < J - 1; ++j) {
-    double2 kj = c[j * NCOEF + 0];
-    double2 rho = c[j * NCOEF + 1];
-    double h = d.layer_top[j + 1] - d.layer_top[j];
-    double2 r1 = c[(j + 1) * NCOEF + 2];
-    c[j * NCOEF + 2] = amp;
-    amp = cdiv(amp * cexp(cmk(-kj.y * h, kj.x * h)) * (cmk(1.0, 0.0) + rho), cmk(1.0, 0.0) + r1);
+    c[j * NCOEF + C_AMP] = amp;
+    amp = amp * c[j * NCOEF + C_EH] * (one + c[j * NCOEF + C_RHO]) * c[j * NCOEF + C_INV1R];
   }
-  c[(J - 1) * NCOEF + 2] = amp;
+  c[(J - 1) * NCOEF + C_AMP] = amp;
+  if (d.coef32) {
+    float* c32 = d.coef32 + (size_t(f) * d.nk + n) * size_t(J) * NCOEF32;
+    for (int j = 0; j < J; ++j) {
+      const double2 kap = c[j * NCOEF + C_KAP], a = c[j * NCOEF + C_AMP], r = c[j * NCOEF + C_RHO];
+      const float kxh = float(kap.x), kyh = float(kap.y);
+      float* o = c32 + j * NCOEF32;
+      o[0] = kxh; o[1] = float(kap.x - double(kxh));
+      o[2] = kyh; o[3] = float(kap.y - double(kyh));
+      o[4] = float(a.x); o[5] = float(a.y);
+      o[6] = j < J - 1 ? float(r.x) : 0.f; o[7] = j < J - 1 ? float(r.y) : 0.f;
+    }
+  }
 }
 
 constexpr int EV_WARPS = 4;
 constexpr int EV_ZC = 16;   // depths per warp chunk
 
-__global__ void __launch_bounds__(EV_WARPS * 32) green_eval_kernel(Dev d) {
+__global__ void __launch_bounds__(EV_WARPS * 32) green_eval64_kernel(Dev d) {
   __shared__ double2 tile[EV_WARPS][32][EV_ZC + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int f = blockIdx.y;
@@ -86,21 +131,21 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval_kernel(Dev d) {
   const double sq = sqrt(d.fc[f].s_abs);
   for (int zc = warp * EV_ZC; zc < d.nz; zc += EV_WARPS * EV_ZC) {
     int cur = -1;
-    double2 e1 = cmk(0.0, 0.0), e2 = cmk(0.0, 0.0), E = e1, Ei = e1, amp = e1, rho = e1;
+    double2 e1 = cmk(0.0, 0.0), e2 = e1, E = e1, Ei = e1, amp = e1, rho = e1;
     for (int i = 0; i < EV_ZC && zc + i < d.nz; ++i) {
-      int z = zc + i;
-      int l = d.z_layer[z];
+      const int z = zc + i;
+      const int l = d.z_layer[z];
       if (l != cur) {             // anchor: direct evaluation at layer entry / chunk start
         cur = l;
-        double2 kap = c[l * NCOEF + 0];
-        rho = c[l * NCOEF + 1];
-        amp = c[l * NCOEF + 2];
-        E = c[l * NCOEF + 3];
-        Ei = c[l * NCOEF + 4];
-        double off = d.z_off[z];
+        const double2 kap = c[l * NCOEF + C_KAP];
+        rho = c[l * NCOEF + C_RHO];
+        amp = c[l * NCOEF + C_AMP];
+        E = c[l * NCOEF + C_E];
+        Ei = c[l * NCOEF + C_EI];
+        const double off = d.z_off[z];
         e1 = cexp(cmk(-kap.y * off, kap.x * off));
         if (l < J - 1) {
-          double a = 2.0 * (d.layer_top[l + 1] - d.layer_top[l]) - off;
+          const double a = 2.0 * (d.layer_top[l + 1] - d.layer_top[l]) - off;
           e2 = cexp(cmk(-kap.y * a, kap.x * a));
         } else {
           e2 = cmk(0.0, 0.0);
@@ -113,15 +158,14 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval_kernel(Dev d) {
       tile[warp][lane][i] = amp * (e1 + rho * e2);
     }
     __syncwarp();
-    // coalesced write-out: two table rows (n) per pass, 16 depths each
     const int zi = lane & 15;
     for (int rr = 0; rr < 32; rr += 2) {
-      int nl = rr + (lane >> 4);
-      int nn = n0 + nl;
-      int z = zc + zi;
+      const int nl = rr + (lane >> 4);
+      const int nn = n0 + nl;
+      const int z = zc + zi;
       if (nn < d.nk && z < d.nz) {
-        double2 v = tile[warp][nl][zi];
-        size_t o = (size_t(f) * d.nk + nn) * d.nz + z;
+        const double2 v = tile[warp][nl][zi];
+        const size_t o = (size_t(f) * d.nk + nn) * d.nz + z;
         d.g64[o] = v;
         if (d.g32) d.g32[o] = make_float2(float(sq * v.x), float(sq * v.y));
       }
@@ -130,13 +174,65 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval_kernel(Dev d) {
   }
 }
 
+// e^{i kappa x} for kappa = (kx, ky) and x >= 0 given as FP32 (hi, lo) pairs, ~1e-7
+// relative: the phase kx x is formed as an unevaluated sum p + q (exact product of the high
+// parts by fma, plus the cross terms), reduced modulo 2 pi with a three-constant Cody-Waite
+// split (2 pi = C1 + C2 + C3, C1 = 6.28125 so that k C1 is exact for |k| < 2^16), and
+// evaluated with FP32 sincos; the decay e^{-ky x} uses the FP32 product.
+__device__ __forceinline__ float2 expi_ff(float kxh, float kxl, float kyh, float xh, float xl) {
+  const float C1 = 6.28125f, C2 = 0.0019353071693331003f, C3 = 1.0253131677018246e-11f;
+  const float p = kxh * xh;
+  const float q = fmaf(kxh, xh, -p) + fmaf(kxh, xl, kxl * xh);
+  const float k = rintf(p * 0.15915493667125702f);
+  float r = fmaf(-k, C1, p);
+  r = fmaf(-k, C2, r);
+  r = fmaf(-k, C3, r);
+  r += q;
+  float sn, cs;
+  sincosf(r, &sn, &cs);
+  const float mag = expf(-kyh * (xh + xl));
+  return make_float2(mag * cs, mag * sn);
+}
+
+__global__ void green_eval32_kernel(Dev d) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)d.nf * d.nk * d.nz;
+  if (gid >= total) return;
+  const int z = int(gid % d.nz);
+  const long long fn = gid / d.nz;
+  const int J = d.nlayer;
+  const int l = d.z_layer[z];
+  const float4 zo = reinterpret_cast<const float4*>(d.z_off32)[z];   // off (hi, lo), 2h - off (hi, lo)
+  const float4* c4 = reinterpret_cast<const float4*>(d.coef32 + (fn * J + l) * NCOEF32);
+  const float4 k4 = c4[0], ar = c4[1];
+  float2 e = expi_ff(k4.x, k4.y, k4.z, zo.x, zo.y);
+  if (l < J - 1) {
+    const float2 e2 = expi_ff(k4.x, k4.y, k4.z, zo.z, zo.w);
+    e = e + make_float2(ar.z, ar.w) * e2;
+  }
+  const int f = int(fn / d.nk);
+  const float sq = d.fc32_sqrt_s[f];
+  const float2 g = make_float2(ar.x, ar.y) * e;
+  d.g32[gid] = make_float2(sq * g.x, sq * g.y);
+}
+
 }  // namespace
 
-cudaError_t launch_green(const Dev& d, cudaStream_t s) {
+cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables) {
+  const bool fast32 = tables == GREEN_G32;
+  const long long nl = (long long)d.nf * d.nk * d.nlayer;
+  green_layer_kernel<<<unsigned((nl + 255) / 256), 256, 0, s>>>(d, fast32 ? 0 : 1);
   dim3 g1((d.nk + 127) / 128, d.nf);
-  green_coef_kernel<<<g1, 128, 0, s>>>(d);
-  dim3 g2((d.nk + 31) / 32, d.nf);
-  green_eval_kernel<<<g2, EV_WARPS * 32, 0, s>>>(d);
+  green_recursion_kernel<<<g1, 128, 0, s>>>(d);
+  if (fast32) {
+    const long long ne = (long long)d.nf * d.nk * d.nz;
+    green_eval32_kernel<<<unsigned((ne + 255) / 256), 256, 0, s>>>(d);
+  } else {
+    Dev e = d;
+    if (!(tables & GREEN_G32)) e.g32 = nullptr;
+    dim3 g2((d.nk + 31) / 32, d.nf);
+    green_eval64_kernel<<<g2, EV_WARPS * 32, 0, s>>>(e);
+  }
   return cudaGetLastError();
 }
 

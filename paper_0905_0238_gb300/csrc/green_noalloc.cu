@@ -80,7 +80,7 @@ extern "C" int edt_green_noalloc(int nx, double dx, int nz, double dz, double z0
   const size_t o_zl = up256(o_vel + sizeof(double) * nlayer);
   const size_t o_zo = up256(o_zl + sizeof(int) * nz);
   const size_t o_fc = up256(o_zo + sizeof(double) * nz);
-  const size_t per_f_coef = size_t(nk) * nlayer * 5 * sizeof(double2);
+  const size_t per_f_coef = size_t(nk) * nlayer * 7 * sizeof(double2);
   const size_t fixed = o_fc;
   if (fixed + up256(sizeof(FreqConst)) + per_f_coef > kNoAllocScratchBytes)
     return EDT_EUNSUPPORTED;   // one frequency's recursion coefficients exceed the 8 MiB scratch
@@ -140,7 +140,7 @@ extern "C" int edt_green_noalloc(int nx, double dx, int nz, double dz, double z0
       return EDT_ECUDA;
     d.nf = nf;
     d.g64 = static_cast<double2*>(g_dev) + size_t(f0) * nk * nz;
-    if (launch_green(d, s) != cudaSuccess) return EDT_ECUDA;
+    if (launch_green(d, s, GREEN_G64) != cudaSuccess) return EDT_ECUDA;
   }
   return EDT_OK;
 }

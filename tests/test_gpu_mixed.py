@@ -3,7 +3,9 @@
 The tensor-core normal matrices are compared with Ahat^T Ahat formed in FP64 from the
 oracle's own kernel rows (a matmul in the test; the oracle itself never forms a Gram);
 the end-to-end inversion with the oracle's QR solution.  Tolerances: Gram relative
-Frobenius 5e-3 with BF16 operands, 2e-5 with the split BF16x3 operands; trace(G) 1e-7;
+Frobenius 5e-3 with BF16 operands, 2e-5 with the split BF16x3 operands; trace(G) 5e-7
+(the FP32 table sqrt|s_f| g is accurate to ~2e-7 relative: FP64-reduced arguments, FP32
+sincos/exp2, so each |a|^2 carries up to ~5e-7);
 V and Vhat 1e-5 relative L2 after one refinement step.
 """
 import numpy as np
@@ -50,7 +52,7 @@ def test_gram_tc_matches_fp64_normal_matrix(passes, nz):
         br = Ah.T @ dh
         assert rel_l2(G[m], Gr) < tolG, (m, rel_l2(G[m], Gr))
         assert rel_l2(b[m][:, : br.shape[1]], br) < 5 * tolG
-        assert abs(tr[m] - np.trace(Gr)) <= 1e-7 * np.trace(Gr)
+        assert abs(tr[m] - np.trace(Gr)) <= 5e-7 * np.trace(Gr)
 
 
 @pytest.mark.parametrize("passes,refine", [(3, 1), (1, 2)])
