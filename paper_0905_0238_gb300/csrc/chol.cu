@@ -8,8 +8,8 @@
 // panel by row-per-thread triangular solves, the trailing lower triangle by 4x4 FP64
 // register tiles.  Then forward and backward substitution for the two right-hand sides
 // with each 32x32 diagonal block staged in shared memory and solved by one warp with
-// shuffles, and the off-diagonal updates as warp-per-row dot products (forward) or
-// coalesced column sweeps (backward).  A non-positive or non-finite pivot marks the
+// shuffles, and the off-diagonal updates by thread-per-row dot products (forward) or
+// coalesced column sweeps (backward), two FP64 FMAs per matrix element and no reductions.  A non-positive or non-finite pivot marks the
 // subproblem EDT_ENOTPD and zeroes its solution.
 //
 // chol_solve applied to r - lam x, with r = Ahat^T (dhat - Ahat x) accumulated by the
@@ -46,7 +46,7 @@ __device__ __forceinline__ bool active(const Dev& d, int m) {
 // Solve L L^T x = sb in place (two right-hand sides, sb[i][0..1]); L lower in A (ld n).
 __device__ void chol_solve_2rhs(const double* A, const double* dinv, int n, double* sb,
                                 double (*sL)[LDP]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nblk = (n + NB - 1) / NB;
   // forward: L y = b
   for (int bk = 0; bk < nblk; ++bk) {
@@ -68,14 +68,15 @@ __device__ void chol_solve_2rhs(const double* A, const double* dinv, int n, doub
       if (lane < kb) { sb[(k0 + lane) * 2] = v0; sb[(k0 + lane) * 2 + 1] = v1; }
     }
     __syncthreads();
-    for (int i = k0 + kb + warp; i < n; i += nw) {     // warp per row: b_i -= L[i][blk] . y
-      const double a = lane < kb ? A[size_t(i) * n + k0 + lane] : 0.0;
-      double s0 = lane < kb ? a * sb[(k0 + lane) * 2] : 0.0, s1 = lane < kb ? a * sb[(k0 + lane) * 2 + 1] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {   // b_i -= L[i][blk] . y
+      double s0 = sb[i * 2], s1 = sb[i * 2 + 1];
+      const double* Ai = A + size_t(i) * n + k0;
+      for (int l = 0; l < kb; ++l) {
+        const double a = Ai[l];
+        s0 -= a * sb[(k0 + l) * 2];
+        s1 -= a * sb[(k0 + l) * 2 + 1];
       }
-      if (lane == 0) { sb[i * 2] -= s0; sb[i * 2 + 1] -= s1; }
+      sb[i * 2] = s0; sb[i * 2 + 1] = s1;
     }
     __syncthreads();
   }

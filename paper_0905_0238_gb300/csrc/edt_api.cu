@@ -154,7 +154,13 @@ void plan(edt_ctx* c) {
     c->row_off[m] = (long long)c->rows.size();
     for (int f = 0; f < c->nf; ++f) {
       const double lim = c->fc[f].lim;
-      for (int p = 0; p < N; ++p) {
+      // order p = 0, N/2, 1, N-1, 2, N-2, ...: rows p and -p read the same table row g(|p|),
+      // so placed side by side the second read is served from L1
+      for (int pi = 0; pi < N; ++pi) {
+        int p;
+        if (pi == 0) p = 0;
+        else if (pi == 1) p = N / 2;
+        else p = (pi & 1) ? N - (pi / 2) : pi / 2;
         const int q = (p - m + N) % N;
         bool keep = true;
         if (g.cutoff > 0) {

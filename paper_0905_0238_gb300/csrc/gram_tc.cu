@@ -11,12 +11,12 @@
 //   * rows of all subproblems are concatenated and split evenly over the CTAs; a CTA's
 //     range falls into 1..few "segments" (its part of one subproblem), each accumulated
 //     in TMEM and written out as an FP32 partial tile, summed per subproblem afterwards;
-//   * warps 0-7 are producers: for 32 complex rows per pipeline stage they rebuild the
+//   * warps 0-11 are producers: for 32 complex rows per pipeline stage they rebuild the
 //     kernel rows a(z) = |s_f| g(k_p, z) g(k_q, z) from the L2-resident FP32 table of
 //     sqrt|s_f| g, scale weight-2 rows by sqrt 2, split into BF16 hi (and lo), and store
 //     them K-major with the 128-byte swizzle; (Re a, Im a) of one complex row are two
 //     adjacent K elements.  The data rows d_+, d_- occupy two extra operand rows;
-//   * warp 8 issues tcgen05.mma (M = 128, K = 16) from one thread: both operands are
+//   * warp 12 issues tcgen05.mma (M = 128, K = 16) from one thread: both operands are
 //     views of the same stage tile (A = depth rows of one 128-row half, B = all depth rows
 //     plus the data rows), so one generated tile feeds the whole upper block row;
 //   * after the last stage of a segment the producers read the accumulator with
@@ -31,7 +31,7 @@ namespace edt {
 
 namespace {
 
-constexpr int PRODUCER_WARPS = 8;
+constexpr int PRODUCER_WARPS = 12;
 constexpr int NTHREADS = (PRODUCER_WARPS + 1) * 32;
 constexpr int ROWB = 128;                       // bytes per operand row per stage (64 bf16)
 constexpr long long WAIT_CYCLES = 4000000000ll; // ~2 s at 2 GHz: a wait longer than this gives up
@@ -386,8 +386,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
       tc_fence_after();
       float* out = d.gpart + size_t(slot) * size_t(ncols) * TC_M;
       const int quarter = warp & 3, group = warp >> 2;   // TMEM lanes 32*quarter..+31
+      constexpr int NGROUP = PRODUCER_WARPS / 4;
       const uint32_t lane_base = uint32_t(quarter * 32) << 16;
-      for (int c0 = group * 16; c0 < ncols; c0 += 32) {
+      for (int c0 = group * 16; c0 < ncols; c0 += 16 * NGROUP) {
         float v[16];
         tmem_ld16(tmem + lane_base + uint32_t(c0), v);
 #pragma unroll

@@ -4,7 +4,9 @@
 // a(z) = |s_f| g(k_p, z) g(k_q, z) is rebuilt from the FP32 table sqrt|s_f| g (rounded from
 // the FP64 depth march), the row's prediction sum_z a(z) x(z) and residual u = d~ - a.x are
 // formed in FP32, and w Re(conj(a(z)) u) is accumulated per lane in FP32 over 16 rows at a
-// time, then in FP64.  This is the matrix-free form of Ahat^T (dhat - Ahat x): the normal
+// time, then in FP64.  Each warp walks its rows two at a time so that the table loads of
+// both rows are in flight together; rows p and -p sit side by side in the row order and
+// share a table row, so one of the two reads is an L1 hit.  This is the matrix-free form of Ahat^T (dhat - Ahat x): the normal
 // matrix used by the factorisation (from the tensor-core Gram) is not involved, so the
 // refinement corrects the Gram's rounding.
 #include "edt_internal.h"
@@ -39,36 +41,54 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
   const long long wb = c0 + warp * RF_ROWS_PER_WARP;
   const long long we = min(nr, wb + RF_ROWS_PER_WARP);
   int since = 0;
-  for (long long i = wb; i < we; ++i) {
-    const uint32_t row = d.rows[r0 + i];
-    const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
-    const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
-    const float2* gp = d.g32 + (size_t(f) * d.nk + np) * nz;
-    const float2* gq = d.g32 + (size_t(f) * d.nk + nq) * nz;
-    float2 a[ZPL];
-    float2 tp = make_float2(0.f, 0.f), tm = tp;
+  // two rows per iteration: the table loads of both are in flight together
+  for (long long i = wb; i < we; i += 2) {
+    const bool two = i + 1 < we;
+    float2 a[2][ZPL];
+    float wv[2];
+    long long ri[2] = {r0 + i, r0 + (two ? i + 1 : i)};
 #pragma unroll
-    for (int t = 0; t < ZPL; ++t) {
-      const int z = lane + 32 * t;
-      a[t] = z < nz ? gp[z] * gq[z] : make_float2(0.f, 0.f);
-      tp.x = fmaf(a[t].x, xs[0][z], tp.x); tp.y = fmaf(a[t].y, xs[0][z], tp.y);
-      tm.x = fmaf(a[t].x, xs[1][z], tm.x); tm.y = fmaf(a[t].y, xs[1][z], tm.y);
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t row = d.rows[ri[h]];
+      const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
+      const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
+      const float2* gp = d.g32 + (size_t(f) * d.nk + np) * nz;
+      const float2* gq = d.g32 + (size_t(f) * d.nk + nq) * nz;
+      wv[h] = (h == 1 && !two) ? 0.f : (row_w2(row) ? 2.f : 1.f);
+#pragma unroll
+      for (int t = 0; t < ZPL; ++t) {
+        const int z = lane + 32 * t;
+        a[h][t] = z < nz ? __ldg(gp + z) : make_float2(0.f, 0.f);
+        const float2 b = z < nz ? __ldg(gq + z) : make_float2(0.f, 0.f);
+        a[h][t] = a[h][t] * b;
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      tp.x += __shfl_xor_sync(0xffffffffu, tp.x, o); tp.y += __shfl_xor_sync(0xffffffffu, tp.y, o);
-      tm.x += __shfl_xor_sync(0xffffffffu, tm.x, o); tm.y += __shfl_xor_sync(0xffffffffu, tm.y, o);
-    }
-    const float w = row_w2(row) ? 2.f : 1.f;
-    const float2 dp = rhs[2 * (r0 + i)], dm = rhs[2 * (r0 + i) + 1];
-    const float2 up = make_float2(w * (dp.x - tp.x), w * (dp.y - tp.y));
-    const float2 um = make_float2(w * (dm.x - tm.x), w * (dm.y - tm.y));
+    for (int h = 0; h < 2; ++h) {
+      float2 tp = make_float2(0.f, 0.f), tm = tp;
 #pragma unroll
-    for (int t = 0; t < ZPL; ++t) {
-      acc[t][0] = fmaf(a[t].x, up.x, fmaf(a[t].y, up.y, acc[t][0]));
-      acc[t][1] = fmaf(a[t].x, um.x, fmaf(a[t].y, um.y, acc[t][1]));
+      for (int t = 0; t < ZPL; ++t) {
+        const int z = lane + 32 * t;
+        tp.x = fmaf(a[h][t].x, xs[0][z], tp.x); tp.y = fmaf(a[h][t].y, xs[0][z], tp.y);
+        tm.x = fmaf(a[h][t].x, xs[1][z], tm.x); tm.y = fmaf(a[h][t].y, xs[1][z], tm.y);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        tp.x += __shfl_xor_sync(0xffffffffu, tp.x, o); tp.y += __shfl_xor_sync(0xffffffffu, tp.y, o);
+        tm.x += __shfl_xor_sync(0xffffffffu, tm.x, o); tm.y += __shfl_xor_sync(0xffffffffu, tm.y, o);
+      }
+      const float w = wv[h];
+      const float2 dp = rhs[2 * ri[h]], dm = rhs[2 * ri[h] + 1];
+      const float2 up = make_float2(w * (dp.x - tp.x), w * (dp.y - tp.y));
+      const float2 um = make_float2(w * (dm.x - tm.x), w * (dm.y - tm.y));
+#pragma unroll
+      for (int t = 0; t < ZPL; ++t) {
+        acc[t][0] = fmaf(a[h][t].x, up.x, fmaf(a[h][t].y, up.y, acc[t][0]));
+        acc[t][1] = fmaf(a[h][t].x, um.x, fmaf(a[h][t].y, um.y, acc[t][1]));
+      }
     }
-    if (++since == 16) {
+    since += 2;
+    if (since >= 16) {
 #pragma unroll
       for (int t = 0; t < ZPL; ++t) {
         acc64[t][0] += acc[t][0]; acc64[t][1] += acc[t][1];
