@@ -269,7 +269,7 @@ void layout(edt_ctx* c) {
   take(c->r_coef, nf * nk * c->nlayer * 7 * sizeof(double2));
   take(c->r_coef32, mixed ? nf * nk * c->nlayer * 8 * sizeof(float) : 0);
   take(c->r_g64, nf * nk * nz * sizeof(double2));
-  take(c->r_g32, mixed ? nf * nk * nz * sizeof(float2) : 0);
+  take(c->r_g32, mixed ? nf * nk * size_t((c->nz + 1) & ~1) * sizeof(float2) : 0);
   take(c->r_X, nf * N * N * (mixed ? sizeof(float2) : sizeof(double2)));
   take(c->r_Dst, nf * N * N * sizeof(double2));
   take(c->r_Vst, N * nz * sizeof(double));
@@ -295,6 +295,7 @@ template <typename P> P at(edt_ctx* c, const Region& r) {
 void bind(edt_ctx* c) {
   Dev& d = c->dev;
   d.N = c->N; d.nk = c->nk; d.nz = c->nz; d.nf = c->nf; d.nsub = c->nsub; d.nlayer = c->nlayer;
+  d.nzs = (c->nz + 1) & ~1;
   d.precision = c->cfg.precision; d.passes = c->cfg.passes; d.fold = c->cfg.fold;
   d.alpha = c->cfg.alpha; d.dx = c->cfg.dx; d.dz = c->cfg.dz;
   d.fc = at<const FreqConst*>(c, c->r_fc);
@@ -442,6 +443,7 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRY(cudaMemset(at<void*>(c, c->r_status), 0, c->r_status.bytes));
   EDT_TRY(cudaMemset(at<void*>(c, c->r_flags), 0, c->r_flags.bytes));
   EDT_TRY(cudaMemset(at<void*>(c, c->r_x), 0, c->r_x.bytes));
+  if (c->r_g32.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_g32), 0, c->r_g32.bytes));
   EDT_TRY(cudaDeviceSynchronize());
   return EDT_OK;
 }

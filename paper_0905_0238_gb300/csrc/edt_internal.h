@@ -33,6 +33,7 @@ struct FreqConst {
 // Device-side view of the workspace and constant tables of one context.
 struct Dev {
   int N, nk, nz, nf, nsub, nlayer;
+  int nzs;                      // row stride of the FP32 table: nz rounded up to even
   int precision, passes, fold;
   double alpha, dx, dz;
   // constant tables
@@ -57,7 +58,7 @@ struct Dev {
   double2* coef;                // [nf][nk][nlayer][7] recursion coefficients (FP64)
   float* coef32;                // [nf][nk][nlayer][8] FP32 copies for the fast evaluation
   double2* g64;                 // [nf][nk][nz]
-  float2* g32;                  // [nf][nk][nz]  sqrt|s_f| g, mixed path
+  float2* g32;                  // [nf][nk][nzs] sqrt|s_f| g, mixed path (padding zero)
   void* X;                      // [nf][N][N] complex, path precision
   void* Dstage;                 // host-call staging of D (complex128-sized)
   void* Vstage;                 // host-call staging of V (double-sized)

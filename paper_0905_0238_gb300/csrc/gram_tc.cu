@@ -11,12 +11,12 @@
 //   * rows of all subproblems are concatenated and split evenly over the CTAs; a CTA's
 //     range falls into 1..few "segments" (its part of one subproblem), each accumulated
 //     in TMEM and written out as an FP32 partial tile, summed per subproblem afterwards;
-//   * warps 0-11 are producers: for 32 complex rows per pipeline stage they rebuild the
+//   * warps 0-15 are producers: for 32 complex rows per pipeline stage they rebuild the
 //     kernel rows a(z) = |s_f| g(k_p, z) g(k_q, z) from the L2-resident FP32 table of
 //     sqrt|s_f| g, scale weight-2 rows by sqrt 2, split into BF16 hi (and lo), and store
 //     them K-major with the 128-byte swizzle; (Re a, Im a) of one complex row are two
 //     adjacent K elements.  The data rows d_+, d_- occupy two extra operand rows;
-//   * warp 12 issues tcgen05.mma (M = 128, K = 16) from one thread: both operands are
+//   * warp 16 issues tcgen05.mma (M = 128, K = 16) from one thread: both operands are
 //     views of the same stage tile (A = depth rows of one 128-row half, B = all depth rows
 //     plus the data rows), so one generated tile feeds the whole upper block row;
 //   * after the last stage of a segment the producers read the accumulator with
@@ -31,7 +31,7 @@ namespace edt {
 
 namespace {
 
-constexpr int PRODUCER_WARPS = 12;
+constexpr int PRODUCER_WARPS = 16;
 constexpr int NTHREADS = (PRODUCER_WARPS + 1) * 32;
 constexpr int ROWB = 128;                       // bytes per operand row per stage (64 bf16)
 constexpr long long WAIT_CYCLES = 4000000000ll; // ~2 s at 2 GHz: a wait longer than this gives up
@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
             const uint32_t row = d.rows[row0 + r];
             const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
             const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
-            e.offp = unsigned((size_t(f) * d.nk + np) * nz);
-            e.offq = unsigned((size_t(f) * d.nk + nq) * nz);
+            e.offp = unsigned((size_t(f) * d.nk + np) * d.nzs);
+            e.offq = unsigned((size_t(f) * d.nk + nq) * d.nzs);
             e.sw = row_w2(row) ? 1.41421356237309515f : 1.0f;
             const float2* rh = reinterpret_cast<const float2*>(d.rhs) + 2 * (row0 + r);
             const float2 a = rh[0], b = rh[1];

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval64_kernel(Dev d) {
         const double2 v = tile[warp][nl][zi];
         const size_t o = (size_t(f) * d.nk + nn) * d.nz + z;
         d.g64[o] = v;
-        if (d.g32) d.g32[o] = make_float2(float(sq * v.x), float(sq * v.y));
+        if (d.g32) d.g32[(size_t(f) * d.nk + nn) * d.nzs + z] = make_float2(float(sq * v.x), float(sq * v.y));
       }
     }
     __syncwarp();
@@ -213,7 +213,7 @@ __global__ void green_eval32_kernel(Dev d) {
   const int f = int(fn / d.nk);
   const float sq = d.fc32_sqrt_s[f];
   const float2 g = make_float2(ar.x, ar.y) * e;
-  d.g32[gid] = make_float2(sq * g.x, sq * g.y);
+  d.g32[size_t(fn) * d.nzs + z] = make_float2(sq * g.x, sq * g.y);
 }
 
 }  // namespace

@@ -113,7 +113,7 @@ extern "C" int edt_green_noalloc(int nx, double dx, int nz, double dz, double z0
     return EDT_ECUDA;
 
   Dev d{};
-  d.N = nx; d.nk = nk; d.nz = nz; d.nlayer = nlayer; d.dx = dx; d.dz = dz;
+  d.N = nx; d.nk = nk; d.nz = nz; d.nzs = (nz + 1) & ~1; d.nlayer = nlayer; d.dx = dx; d.dz = dz;
   d.layer_top = reinterpret_cast<const double*>(sb + o_top);
   d.layer_vel = reinterpret_cast<const double*>(sb + o_vel);
   d.z_layer = reinterpret_cast<const int*>(sb + o_zl);

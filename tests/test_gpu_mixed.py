@@ -56,7 +56,7 @@ def test_gram_tc_matches_fp64_normal_matrix(passes, nz):
 
 
 @pytest.mark.parametrize("passes,refine", [(3, 1), (1, 2)])
-@pytest.mark.parametrize("nx,nz,nf", [(32, 40, 6), (64, 130, 4), (32, 256, 3)])
+@pytest.mark.parametrize("nx,nz,nf", [(32, 40, 6), (32, 41, 5), (64, 130, 4), (32, 256, 3)])
 def test_invert_mixed_matches_oracle(passes, refine, nx, nz, nf):
     """Split BF16x3 Gram + one refinement step (or BF16 Gram + two steps) reach 1e-5."""
     wl = small_workload(nx=nx, nz=nz, nf=nf, alpha=1e-2, dz=8.0)
