@@ -55,7 +55,7 @@ struct edt_ctx {
   size_t ws_bytes = 0;
   void* ws = nullptr;
   Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_tw64, r_tw32, r_segm, r_segr0,
-      r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gpart, r_G,
+      r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
       r_dinv, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
   Dev dev{};
   cudaStream_t last_stream = nullptr;
@@ -274,6 +274,7 @@ void layout(edt_ctx* c) {
   take(c->r_Dst, nf * N * N * sizeof(double2));
   take(c->r_Vst, N * nz * sizeof(double));
   take(c->r_rhs, std::max<size_t>(R, 1) * 2 * (mixed ? sizeof(float2) : sizeof(double2)));
+  take(c->r_gent, mixed ? (R + 32) * sizeof(GramRow) : 0);
   take(c->r_gpart, mixed ? size_t(c->nslot) * TC_M * tc_cols(c->nz) * sizeof(float) : 0);
   take(c->r_G, ns * nz * nz * sizeof(double));
   take(c->r_dinv, ns * nz * sizeof(double));
@@ -323,6 +324,7 @@ void bind(edt_ctx* c) {
   d.Dstage = at<void*>(c, c->r_Dst);
   d.Vstage = at<void*>(c, c->r_Vst);
   d.rhs = at<void*>(c, c->r_rhs);
+  d.gent = c->r_gent.bytes ? at<GramRow*>(c, c->r_gent) : nullptr;
   d.gpart = c->r_gpart.bytes ? at<float*>(c, c->r_gpart) : nullptr;
   d.G = at<double*>(c, c->r_G);
   d.dinv = at<double*>(c, c->r_dinv);
@@ -444,6 +446,7 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRY(cudaMemset(at<void*>(c, c->r_flags), 0, c->r_flags.bytes));
   EDT_TRY(cudaMemset(at<void*>(c, c->r_x), 0, c->r_x.bytes));
   if (c->r_g32.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_g32), 0, c->r_g32.bytes));
+  if (c->r_gent.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_gent), 0, c->r_gent.bytes));
   EDT_TRY(cudaDeviceSynchronize());
   return EDT_OK;
 }

@@ -21,6 +21,14 @@ __host__ __device__ inline int row_f(uint32_t r) { return int(r >> 16); }
 __host__ __device__ inline int row_p(uint32_t r) { return int(r & 0x7fffu); }
 __host__ __device__ inline int row_w2(uint32_t r) { return int((r >> 15) & 1u); }
 
+// Per-row operand metadata of the tensor-core Gram, written by the right-hand-side kernel:
+// element offsets of the two FP32 table rows, sqrt(weight), data rows times sqrt(weight).
+struct GramRow {
+  unsigned offp, offq;
+  float sw, pad;
+  float2 dp, dm;
+};
+
 // Per-frequency constants: omega~ = omega + i eps, |s_f| with s_f = omega~^2 dz/dx, and
 // the unit phase conj(s_f)/|s_f| that moves the complex prefactor onto the data.
 struct FreqConst {
@@ -63,6 +71,7 @@ struct Dev {
   void* Dstage;                 // host-call staging of D (complex128-sized)
   void* Vstage;                 // host-call staging of V (double-sized)
   void* rhs;                    // [rows_solved][2] complex, path precision
+  GramRow* gent;                // [rows_solved + 32] tensor-core Gram row metadata (mixed)
   float* gpart;                 // tensor-core Gram partial tiles [nslot][TM_COLS * 128]
   double* G;                    // [nsub][nz][nz]  Gram, then its Cholesky factor
   double* dinv;                 // [nsub][nz]      1 / diagonal of the factor

@@ -48,10 +48,11 @@ template <typename T2> __device__ __forceinline__ void store_c(void* p, int dtyp
 }
 
 // In-place decimation-in-time FFT of `batch` sequences of length N = 2^logn held in
-// shared memory in bit-reversed order; sequence b starts at s + b * bstride.  sign = -1
-// uses e^{-2 pi i k/N}, sign = +1 its conjugate.  One radix-2 stage when logn is odd, then
-// pairs of radix-2 stages fused into radix-4 butterflies (one barrier per pair).  All
-// threads of the block participate; indices use shifts only.
+// shared memory in bit-reversed order; sequence b starts at s + b * bstride and element e
+// sits at pd(e).  sign = -1 uses e^{-2 pi i k/N}, sign = +1 its conjugate.  One radix-2
+// stage when logn is odd, then pairs of radix-2 stages fused into radix-4 butterflies (one
+// barrier per pair).  Each thread owns one butterfly position q and walks a share of the
+// sequences, so its two twiddles are loaded once per stage and reused across the batch.
 template <typename T, typename T2>
 __device__ void block_fft(T2* s, int N, int logn, int batch, int bstride, const T2* tw, int sign) {
   int lh = 0;                       // log2 of the current half-size h
@@ -68,27 +69,30 @@ __device__ void block_fft(T2* s, int N, int logn, int batch, int bstride, const 
     __syncthreads();
     lh = 1;
   }
+  const int nq = N >> 2;                                   // radix-4 butterflies per sequence
+  const int ngrp = max(1, int(blockDim.x) / max(nq, 1));   // thread groups over sequences
   for (; lh < logn; lh += 2) {      // fused stages h and 2h
     const int h = 1 << lh;
-    const int lq = logn - 2, total = batch << lq;   // N/4 radix-4 butterflies per sequence
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int b = t >> lq, q = t & ((1 << lq) - 1);
+    for (int t = threadIdx.x; t < nq * ngrp; t += blockDim.x) {
+      const int q = t % nq, g = t / nq;
       const int jj = q & (h - 1), blk = q >> lh;    // jj < h, block of 4h
-      T2* base = s + b * bstride;
       const int e0 = (blk << (lh + 2)) + jj;
       const int i0 = pd(e0), i1 = pd(e0 + h), i2 = pd(e0 + 2 * h), i3 = pd(e0 + 3 * h);
       T2 w1 = tw[jj << (logn - 1 - lh)];            // W_{2h}^jj
       T2 w2 = tw[jj << (logn - 2 - lh)];            // W_{4h}^jj
       if (sign > 0) { w1.y = -w1.y; w2.y = -w2.y; }
-      const T2 x0 = base[i0], x1 = base[i1] * w1, x2 = base[i2], x3 = base[i3] * w1;
-      const T2 y0 = x0 + x1, y1 = x0 - x1, y2 = x2 + x3, y3 = x2 - x3;
-      const T2 a = w2 * y2;
-      T2 c = w2 * y3;                               // times W_4 = -i (sign -) or +i (sign +)
-      c = sign < 0 ? cmk(c.y, -c.x) : cmk(-c.y, c.x);
-      base[i0] = y0 + a;
-      base[i2] = y0 - a;
-      base[i1] = y1 + c;
-      base[i3] = y1 - c;
+      for (int b = g; b < batch; b += ngrp) {
+        T2* base = s + b * bstride;
+        const T2 x0 = base[i0], x1 = base[i1] * w1, x2 = base[i2], x3 = base[i3] * w1;
+        const T2 y0 = x0 + x1, y1 = x0 - x1, y2 = x2 + x3, y3 = x2 - x3;
+        const T2 a = w2 * y2;
+        T2 c = w2 * y3;                             // times W_4 = -i (sign -) or +i (sign +)
+        c = sign < 0 ? cmk(c.y, -c.x) : cmk(-c.y, c.x);
+        base[i0] = y0 + a;
+        base[i2] = y0 - a;
+        base[i1] = y1 + c;
+        base[i3] = y1 - c;
+      }
     }
     __syncthreads();
   }

@@ -45,12 +45,7 @@ __host__ __device__ inline int zrows_of(int nzp) {
 __host__ __device__ inline int cols_of(int nzp) { return (nzp + 16) + (nzp > TC_M ? nzp - TC_M + 16 : 0); }
 __host__ __device__ inline int stages_of(int passes) { return passes == 1 ? 4 : 3; }
 
-struct RowEnt {
-  unsigned offp, offq;   // element offsets of the g rows (f, |p|) and (f, |q|)
-  float sw;              // sqrt(weight), 0 for padding rows
-  float pad;
-  float2 dp, dm;         // data rows times sqrt(weight)
-};
+using RowEnt = GramRow;   // per-row operand metadata, built by the right-hand-side kernel
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -86,6 +81,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volati
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// one-dimensional bulk copy global -> shared, completing on an mbarrier (16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -167,14 +174,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
   // carve shared memory: operand stages (1024-aligned), row tables, barriers
   uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
   unsigned char* ops = reinterpret_cast<unsigned char*>(base);
-  RowEnt* rowtab = reinterpret_cast<RowEnt*>(ops + size_t(STAGES) * NCOMP * stage_bytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(rowtab + STAGES * TC_KC);
+  RowEnt* rowtab = reinterpret_cast<RowEnt*>(ops + size_t(STAGES) * NCOMP * stage_bytes);   // [2][TC_KC]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rowtab + 2 * TC_KC);
   uint64_t* full = bars;                   // [STAGES] producers -> MMA
   uint64_t* empty = bars + STAGES;         // [STAGES] MMA commit -> producers
   uint64_t* acc_full = bars + 2 * STAGES;  // MMA commit -> epilogue
   uint64_t* acc_empty = acc_full + 1;      // epilogue -> MMA
   uint64_t* drain = acc_empty + 1;         // final commit: every issued MMA has completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* tbar = drain + 1;              // [2] row-table bulk copies
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tbar + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,6 +201,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, PRODUCER_WARPS * 32);
     mbar_init(drain, 1);
+    mbar_init(&tbar[0], 1);
+    mbar_init(&tbar[1], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -272,39 +282,46 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     const float2* g32 = d.g32;
     long long it = 0;
     bool ok = true;
+    // The row table of each stage (32 GramRow entries, 1 KB) arrives by a bulk copy issued
+    // one stage ahead into a double buffer, so it is off the producers' critical path.
+    int nsi = s0;                        // (segment, stage) of the next table copy to issue
+    long long nst_next = 0;
+    auto issue_table = [&](long long it_next) {
+      while (nsi < s1) {
+        const int sl = slots[nsi];
+        const long long n = (d.seg_nrow[sl] + TC_KC - 1) / TC_KC;
+        if (nst_next < n) {
+          const int b = int(it_next & 1);
+          mbar_expect_tx(&tbar[b], TC_KC * sizeof(RowEnt));
+          bulk_g2s(rowtab + b * TC_KC, d.gent + d.seg_row0[sl] + nst_next * TC_KC,
+                   TC_KC * sizeof(RowEnt), &tbar[b]);
+          ++nst_next;
+          return;
+        }
+        ++nsi;
+        nst_next = 0;
+      }
+    };
+    if (ptid == 0) issue_table(0);
+    float tr_hi = 0.f, tr_lo = 0.f;      // Kahan-compensated FP32 trace of the segment
     for (int si = s0; si < s1 && ok; ++si) {
       const int slot = slots[si];
       const int m = d.seg_m[slot];
-      const long long row0 = d.seg_row0[slot], nrow = d.seg_nrow[slot];
+      const long long nrow = d.seg_nrow[slot];
       const long long nst = (nrow + TC_KC - 1) / TC_KC;
-      double tr = 0.0;
+      (void)m;
+      tr_hi = 0.f; tr_lo = 0.f;
       for (long long st = 0; st < nst; ++st, ++it) {
         const int s = int(it % STAGES);
         if (it >= STAGES) {
           if (!mbar_wait(&empty[s], unsigned(((it / STAGES) - 1) & 1), abort_flag)) { ok = false; break; }
         }
-        RowEnt* rt = rowtab + s * TC_KC;
-        if (ptid < TC_KC) {
-          const long long r = st * TC_KC + ptid;
-          RowEnt e;
-          if (r < nrow) {
-            const uint32_t row = d.rows[row0 + r];
-            const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
-            const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
-            e.offp = unsigned((size_t(f) * d.nk + np) * d.nzs);
-            e.offq = unsigned((size_t(f) * d.nk + nq) * d.nzs);
-            e.sw = row_w2(row) ? 1.41421356237309515f : 1.0f;
-            const float2* rh = reinterpret_cast<const float2*>(d.rhs) + 2 * (row0 + r);
-            const float2 a = rh[0], b = rh[1];
-            e.dp = make_float2(e.sw * a.x, e.sw * a.y);
-            e.dm = make_float2(e.sw * b.x, e.sw * b.y);
-          } else {
-            e.offp = e.offq = 0; e.sw = 0.f; e.dp = e.dm = make_float2(0.f, 0.f);
-          }
-          e.pad = 0.f;
-          rt[ptid] = e;
-        }
+        if (!mbar_wait(&tbar[it & 1], unsigned((it >> 1) & 1), abort_flag)) { ok = false; break; }
+        RowEnt* rt = rowtab + (it & 1) * TC_KC;
+        const int nvalid = int(min((long long)TC_KC, nrow - st * TC_KC));   // rows past it: padding
         asm volatile("bar.sync 1, %0;" ::"n"(PRODUCER_WARPS * 32) : "memory");
+        asm volatile("bar.sync 1, %0;" ::"n"(PRODUCER_WARPS * 32) : "memory");
+        if (ptid == 0) issue_table(it + 1);
         unsigned char* hi = ops + size_t(s) * NCOMP * stage_bytes;
         unsigned char* lo = hi + stage_bytes;
         float trs = 0.f;
@@ -323,7 +340,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
 #pragma unroll
             for (int rr = 0; rr < 4; ++rr) {
               const RowEnt e = rt[cc[h2] * 4 + rr];
-              const bool ok2 = uv && zz[h2] < nz && e.sw != 0.f;
+              // entries past the segment's last row belong to the next segment: padding here
+              const bool ok2 = uv && zz[h2] < nz && (cc[h2] * 4 + rr) < nvalid;
               swv[h2][rr] = ok2 ? e.sw : 0.f;
               gpv[h2][rr] = ok2 ? __ldg(g32 + e.offp + zz[h2]) : make_float2(0.f, 0.f);
               gqv[h2][rr] = ok2 ? __ldg(g32 + e.offq + zz[h2]) : make_float2(0.f, 0.f);
@@ -360,7 +378,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
           const int which = lane >> 3, c = lane & 7;
           float2 v[4];
 #pragma unroll
-          for (int rr = 0; rr < 4; ++rr) v[rr] = which ? rt[c * 4 + rr].dm : rt[c * 4 + rr].dp;
+          for (int rr = 0; rr < 4; ++rr) {
+            v[rr] = which ? rt[c * 4 + rr].dm : rt[c * 4 + rr].dp;
+            if (c * 4 + rr >= nvalid) v[rr] = make_float2(0.f, 0.f);
+          }
           uint4 h;
           h.x = pack_bf16(v[0].x, v[0].y); h.y = pack_bf16(v[1].x, v[1].y);
           h.z = pack_bf16(v[2].x, v[2].y); h.w = pack_bf16(v[3].x, v[3].y);
@@ -376,7 +397,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
             *reinterpret_cast<uint4*>(lo + off) = l;
           }
         }
-        tr += double(trs);
+        {   // Kahan: tr_hi + tr_lo carries the segment's trace without FP64 arithmetic
+          const float yk = trs - tr_lo, tk = tr_hi + yk;
+          tr_lo = (tk - tr_hi) - yk;
+          tr_hi = tk;
+        }
         fence_proxy_async();
         mbar_arrive(&full[s]);
       }
@@ -396,9 +421,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
       }
       tc_fence_before();
       mbar_arrive(acc_empty);
-      // trace(G) of this segment, FP64
+      // trace(G) of this segment, summed over the warp in FP64
+      double tr = double(tr_hi) - double(tr_lo);
       for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-      if (lane == 0) atomicAdd(&d.trace[m], tr);
+      if (lane == 0) atomicAdd(&d.trace[d.seg_m[slot]], tr);
     }
   }
 
@@ -446,7 +472,7 @@ int tc_cols(int nz) { return cols_of(nzp_of(nz)); }
 int tc_smem_bytes(int nz, int passes) {
   const int zr = zrows_of(nzp_of(nz));
   const int stages = stages_of(passes), ncomp = passes == 1 ? 1 : 2;
-  return 1024 + stages * ncomp * zr * ROWB + stages * TC_KC * int(sizeof(RowEnt)) + (2 * stages + 3) * 8 + 16;
+  return 1024 + stages * ncomp * zr * ROWB + 2 * TC_KC * int(sizeof(RowEnt)) + (2 * stages + 5) * 8 + 16;
 }
 
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s) {

@@ -41,8 +41,21 @@ __global__ void rhs_kernel(Dev d) {
   const FreqConst fc = d.fc[f];
   T2 rot = cmk(T(fc.rot_re), T(fc.rot_im));
   T2* out = reinterpret_cast<T2*>(d.rhs) + 2 * size_t(r0 + i);
-  out[0] = dp * rot;
-  out[1] = dm * rot;
+  const T2 rp = dp * rot, rm = dm * rot;
+  out[0] = rp;
+  out[1] = rm;
+  if (d.gent) {
+    // operand metadata of the tensor-core Gram (weight-2 rows scaled by sqrt 2)
+    const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
+    GramRow g;
+    g.offp = unsigned((size_t(f) * d.nk + np) * d.nzs);
+    g.offq = unsigned((size_t(f) * d.nk + nq) * d.nzs);
+    g.sw = row_w2(row) ? 1.41421356237309515f : 1.0f;
+    g.pad = 0.f;
+    g.dp = make_float2(g.sw * float(rp.x), g.sw * float(rp.y));
+    g.dm = make_float2(g.sw * float(rm.x), g.sw * float(rm.y));
+    d.gent[r0 + i] = g;
+  }
 }
 
 }  // namespace
