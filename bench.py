@@ -38,8 +38,8 @@ CPU_SAMPLE_M = (1, 64, 128, 192)      # midpoint indices solved by the CPU basel
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--passes", type=int, default=3)
     ap.add_argument("--refine", type=int, default=1)
@@ -116,7 +116,7 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -240,6 +240,7 @@ def main():
 
     # ---- device-resident timed region ----------------------------------------------
     clocks = Clocks(local)
+    time.sleep(0.3)                      # let the sampler start before the timed region
     mixed.set_profiling(True)
     barrier()
     torch.cuda.synchronize()

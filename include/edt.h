@@ -186,7 +186,8 @@ int edt_row_counts(const edt_ctx* ctx, long long* counts);
 /* Fill *out; synchronises the stream of the last device call on this context. */
 int edt_get_stats(edt_ctx* ctx, edt_stats* out);
 
-/* Per-stage device timing.  With profiling on, every edt_invert records CUDA events
+/* Per-stage device timing.  With profiling on, every edt_invert (up to 256 calls between
+ * reads) records CUDA events
  * around its stages; edt_read_profile synchronises and returns the summed milliseconds
  * per stage since the last reset (names[i] static strings), then resets.
  * Returns the number of stages written (<= max_stages), or a negative code. */

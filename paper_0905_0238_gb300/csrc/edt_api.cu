@@ -70,6 +70,8 @@ struct edt_ctx {
 
 namespace {
 
+constexpr int kProfCalls = 256;   // calls whose stage events are kept between reads
+
 const char* kStageNames[edt_ctx::NSTAGE] = {"green", "transform", "rhs", "gram",
                                             "gram_reduce", "cholesky", "refine", "inverse",
                                             "unused"};
@@ -349,7 +351,7 @@ int upload(edt_ctx* c, const Region& r, const std::vector<T>& v) {
 #define EDT_TRYI(x) do { int _r = (x); if (_r != EDT_OK) return _r; } while (0)
 
 void prof_mark(edt_ctx* c, int stage, cudaStream_t s) {
-  if (!c->prof || c->prof_calls >= 64) return;
+  if (!c->prof || c->prof_calls >= kProfCalls) return;
   cudaEventRecord(c->ev[size_t(c->prof_calls) * (edt_ctx::NSTAGE + 1) + stage], s);
   c->prof_used[stage] = 1;
 }
@@ -389,7 +391,7 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_mark(c, 7, s);
   EDT_TRY(launch_inverse(d, V, V_dtype, s));
   prof_mark(c, 8, s);
-  if (c->prof && c->prof_calls < 64) c->prof_calls++;
+  if (c->prof && c->prof_calls < kProfCalls) c->prof_calls++;
   return EDT_OK;
 }
 
@@ -574,7 +576,7 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
 int edt_set_profiling(edt_ctx* c, int on) {
   if (!c) return EDT_EINVAL;
   if (on && c->ev.empty()) {
-    c->ev.resize(64 * (edt_ctx::NSTAGE + 1));
+    c->ev.resize(size_t(kProfCalls) * (edt_ctx::NSTAGE + 1));
     for (auto& e : c->ev) EDT_TRY(cudaEventCreate(&e));
   }
   c->prof = on != 0;
