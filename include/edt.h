@@ -131,6 +131,12 @@ int edt_set_workspace(edt_ctx* ctx, void* ws_dev, size_t bytes);
 int edt_invert(edt_ctx* ctx, const void* D_dev, int D_dtype, void* V_dev, int V_dtype,
                void* stream);
 
+/* CUDA-graph mode: with on != 0, edt_invert captures all of its stages into one CUDA graph
+ * on the first call and replays it while the data and model pointers, their dtypes and the
+ * stream stay the same (a change re-captures).  Requires a non-default stream; calls on the
+ * legacy default stream, and calls made while profiling is on, run uncaptured. */
+int edt_set_graph(edt_ctx* ctx, int on);
+
 /* edt_invert from host buffers: copies D to the device, inverts, copies V back, all on
  * `stream` (asynchronous; the host buffers must stay valid until the stream syncs).
  * Uses the staging areas inside the workspace. */

@@ -294,9 +294,14 @@ cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s) {
 
 int chol_launches(int nz) { return 1; }
 
+static size_t chol_smem(int nz) { return (size_t(nz) * LDP + NB * LDP + 2 * nz + 40) * sizeof(double); }
+
+cudaError_t prepare_chol(const Dev& d) {
+  return cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(chol_smem(d.nz)));
+}
+
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
-  size_t smem = (size_t(d.nz) * LDP + NB * LDP + 2 * d.nz + 40) * sizeof(double);
-  cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  size_t smem = chol_smem(d.nz);
   chol_kernel<<<d.nsub, 256, smem, s>>>(d, trace_mode);
   return cudaGetLastError();
 }

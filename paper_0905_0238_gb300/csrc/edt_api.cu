@@ -60,6 +60,13 @@ struct edt_ctx {
   Dev dev{};
   cudaStream_t last_stream = nullptr;
   int last_status = EDT_OK;
+  // CUDA-graph replay of edt_invert (keyed on the call's pointers, dtypes and stream)
+  bool use_graph = false;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_D = nullptr;
+  void* g_V = nullptr;
+  int g_Dt = -1, g_Vt = -1;
+  cudaStream_t g_s = nullptr;
   // profiling
   bool prof = false;
   static constexpr int NSTAGE = 9;        // marks; NSTAGE - 1 timed stages
@@ -449,8 +456,16 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRY(cudaMemset(at<void*>(c, c->r_x), 0, c->r_x.bytes));
   if (c->r_g32.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_g32), 0, c->r_g32.bytes));
   if (c->r_gent.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_gent), 0, c->r_gent.bytes));
+  EDT_TRY(prepare_fft(c->dev));
+  EDT_TRY(prepare_chol(c->dev));
+  if (c->cfg.precision == EDT_MIXED) EDT_TRY(prepare_gram_tc(c->dev));
   EDT_TRY(cudaDeviceSynchronize());
   return EDT_OK;
+}
+
+static void drop_graph(edt_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
 }
 
 int edt_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, void* stream) {
@@ -458,9 +473,38 @@ int edt_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, voi
   if (!c->ws) return EDT_ENOMEM_WS;
   if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
   if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
-  int r = run_invert(c, D, D_dtype, V, V_dtype, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int r;
+  if (c->use_graph && !c->prof && s != nullptr) {
+    // one captured graph of every stage, replayed while the call's arguments stay the same
+    if (!c->gexec || c->g_D != D || c->g_V != V || c->g_Dt != D_dtype || c->g_Vt != V_dtype || c->g_s != s) {
+      drop_graph(c);
+      cudaGraph_t g = nullptr;
+      EDT_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      r = run_invert(c, D, D_dtype, V, V_dtype, s);
+      cudaError_t e = cudaStreamEndCapture(s, &g);
+      if (r != EDT_OK) { if (g) cudaGraphDestroy(g); c->last_status = r; return r; }
+      if (e != cudaSuccess) return cuda_fail(e);
+      e = cudaGraphInstantiate(&c->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { c->gexec = nullptr; return cuda_fail(e); }
+      c->g_D = D; c->g_V = V; c->g_Dt = D_dtype; c->g_Vt = V_dtype; c->g_s = s;
+    }
+    c->last_stream = s;
+    cudaError_t e = cudaGraphLaunch(c->gexec, s);
+    r = e == cudaSuccess ? EDT_OK : cuda_fail(e);
+  } else {
+    r = run_invert(c, D, D_dtype, V, V_dtype, s);
+  }
   c->last_status = r;
   return r;
+}
+
+int edt_set_graph(edt_ctx* c, int on) {
+  if (!c) return EDT_EINVAL;
+  c->use_graph = on != 0;
+  drop_graph(c);
+  return EDT_OK;
 }
 
 int edt_invert_host(edt_ctx* c, const void* D_host, int D_dtype, void* V_host, int V_dtype,
@@ -622,6 +666,7 @@ const char* edt_last_cuda_error(void) { return g_last_cuda.c_str(); }
 
 void edt_destroy(edt_ctx* c) {
   if (!c) return;
+  drop_graph(c);
   for (auto& e : c->ev) cudaEventDestroy(e);
   delete c;
 }

@@ -107,6 +107,11 @@ cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s);
 cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
                            cudaStream_t s);
 
+// One-time kernel attribute setup (opt-in shared memory), done outside any stream capture.
+cudaError_t prepare_fft(const Dev& d);
+cudaError_t prepare_chol(const Dev& d);
+cudaError_t prepare_gram_tc(const Dev& d);
+
 // Tensor-core Gram tiling (shared by host planning and the kernel).
 constexpr int TC_M = 128;              // MMA rows (depth unknowns per M tile)
 constexpr int TC_KC = 32;              // complex rows per pipeline stage (K = 64 real rows)

@@ -16,6 +16,8 @@
 #include "edt_internal.h"
 #include "cplx.cuh"
 
+#include <algorithm>
+
 namespace edt {
 
 namespace {
@@ -152,7 +154,6 @@ cudaError_t rows_fft(const Dev& d, const void* in, int in_dtype, void* out, int 
   int rpb = (int(sizeof(T)) == 4 ? 4096 : 2048) / d.N;
   if (rpb < 1) rpb = 1;
   size_t smem = size_t(rpb) * padded_len(d.N) * sizeof(T2);
-  cudaFuncSetAttribute(fft_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   long long nb = (nrows + rpb - 1) / rpb;
   fft_rows_kernel<T><<<unsigned(nb), 256, smem, st>>>(d, in, in_dtype, out, out_dtype, nrows, rpb,
                                                       sign, scale);
@@ -165,7 +166,6 @@ cudaError_t cols_fft(const Dev& d, cplx_t<T>* X, int planes, int sign, T scale, 
   int cpb = 128 / int(sizeof(T2));
   if (cpb > d.N) cpb = d.N;
   size_t smem = size_t(cpb) * (padded_len(d.N) + 1) * sizeof(T2);
-  cudaFuncSetAttribute(fft_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   dim3 g(d.N / cpb, planes);
   fft_cols_kernel<T><<<g, 256, smem, st>>>(d, X, cpb, sign, scale);
   return cudaGetLastError();
@@ -277,9 +277,29 @@ cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, cudaStrea
 template cudaError_t launch_transform<float>(const Dev&, const void*, int, cudaStream_t);
 template cudaError_t launch_transform<double>(const Dev&, const void*, int, cudaStream_t);
 
+// Opt-in shared-memory sizes of this file's kernels, set once per context (outside any
+// stream capture).
+cudaError_t prepare_fft(const Dev& d) {
+  const int N = d.N;
+  const int rpb32 = std::max(1, 4096 / N), rpb64 = std::max(1, 2048 / N);
+  const int cpb32 = std::min(N, 16), cpb64 = std::min(N, 8);
+  const size_t inv = size_t(INV_ZT) * (padded_len(N) + 1) * sizeof(double2);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(fft_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(size_t(rpb32) * padded_len(N) * sizeof(float2)))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fft_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(size_t(rpb64) * padded_len(N) * sizeof(double2)))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fft_cols_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(size_t(cpb32) * (padded_len(N) + 1) * sizeof(float2)))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fft_cols_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(size_t(cpb64) * (padded_len(N) + 1) * sizeof(double2)))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(inv))) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(lateral_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(inv));
+}
+
 cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s) {
   size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);
-  cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   inverse_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
   return cudaGetLastError();
 }
@@ -287,7 +307,6 @@ cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s) {
 cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
                            cudaStream_t s) {
   size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);
-  cudaFuncSetAttribute(lateral_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   lateral_dft_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -475,17 +475,19 @@ int tc_smem_bytes(int nz, int passes) {
   return 1024 + stages * ncomp * zr * ROWB + 2 * TC_KC * int(sizeof(RowEnt)) + (2 * stages + 5) * 8 + 16;
 }
 
+cudaError_t prepare_gram_tc(const Dev& d) {
+  const int smem = tc_smem_bytes(d.nz, d.passes);
+  return d.passes == 3
+             ? cudaFuncSetAttribute(gram_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+             : cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s) {
   const int smem = tc_smem_bytes(d.nz, d.passes);
   cudaError_t e;
   if (d.ncta_gram > 0) {
-    if (d.passes == 3) {
-      cudaFuncSetAttribute(gram_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      gram_tc_kernel<3><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
-    } else {
-      cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      gram_tc_kernel<1><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
-    }
+    if (d.passes == 3) gram_tc_kernel<3><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
+    else gram_tc_kernel<1><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -78,6 +78,7 @@ def _lib() -> C.CDLL:
                                         C.POINTER(d), vp, vp]
         L.edt_get_stats.argtypes = [vp, C.POINTER(edt_stats)]
         L.edt_set_profiling.argtypes = [vp, i]
+        L.edt_set_graph.argtypes = [vp, i]
         L.edt_read_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_char_p), i,
                                        C.POINTER(i)]
         L.edt_strerror.argtypes = [i]
@@ -87,7 +88,8 @@ def _lib() -> C.CDLL:
         L.edt_destroy.restype = None
         for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
                      "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
-                     "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc"):
+                     "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
+                     "edt_set_graph"):
             getattr(L, name).restype = i
         _LIB = L
     return _LIB
@@ -160,6 +162,10 @@ def edt_get_stats(ctx) -> edt_stats:
     st = edt_stats()
     _check(_lib().edt_get_stats(ctx, C.byref(st)), "edt_get_stats")
     return st
+
+
+def edt_set_graph(ctx, on: bool):
+    _check(_lib().edt_set_graph(ctx, int(bool(on))), "edt_set_graph")
 
 
 def edt_set_profiling(ctx, on: bool):
@@ -308,6 +314,9 @@ class Solver:
 
     def stats(self):
         return edt_get_stats(self.ctx)
+
+    def set_graph(self, on=True):
+        edt_set_graph(self.ctx, on)
 
     def set_profiling(self, on=True):
         edt_set_profiling(self.ctx, on)

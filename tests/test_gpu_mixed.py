@@ -90,3 +90,25 @@ def test_mixed_without_folding_and_without_cut():
     for fold in (0, 1):
         V = solver(wl, fold=fold).invert(dev(D)).cpu().numpy()
         assert rel_l2(V, V_or) < 1e-5
+
+
+def test_graph_replay_matches_direct_calls():
+    """edt_invert captured into a CUDA graph gives the direct call's result, replayed and
+    re-captured when the output buffer changes."""
+    wl = small_workload(nx=32, nz=40, nf=4, alpha=1e-2, dz=8.0)
+    D = born_data(wl, salt=6)
+    s = solver(wl)
+    ref = s.invert(dev(D)).cpu().numpy()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s.set_graph(True)
+        Dd = dev(D)
+        out1 = torch.empty((wl.nx, wl.nz), device="cuda", dtype=torch.float64)
+        out2 = torch.empty_like(out1)
+        for out in (out1, out1, out1, out2, out2):
+            out.fill_(float("nan"))
+            s.invert(Dd, out=out)
+            st.synchronize()
+            # FP64 atomics in the trace and residual sums make the last bits order-dependent
+            assert rel_l2(out.cpu().numpy(), ref) < 1e-10
+        s.set_graph(False)
