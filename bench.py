@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--passes", type=int, default=3)
     ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--chol-df", type=int, default=0,
+                    help="1: Cholesky trailing updates in double-float on the FP32 pipes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
@@ -228,7 +230,7 @@ def main():
     torch.cuda.synchronize()
 
     mixed = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=args.passes,
-                                        refine=args.refine), device=dev)
+                                        refine=args.refine, chol_df=args.chol_df), device=dev)
     Vout = torch.empty((wl.nx, wl.nz), device=dev, dtype=torch.float32)
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(3, args.warmup)):
@@ -350,7 +352,7 @@ def main():
         steps=args.steps, warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="bf16x3+f32acc+f64", data="synthetic",
         config=dict(workload=workload_summary(wl), l2="inputs larger than L2 (268 MB data per step)",
-                    passes=args.passes, refine=args.refine, alpha=wl.alpha,
+                    passes=args.passes, refine=args.refine, chol_df=args.chol_df, alpha=wl.alpha,
                     rows_total=int(st.rows_total), rows_solved=int(st.rows_solved),
                     parallelism=f"replicas x{world} (independent lines)"),
         model_pts_per_sec=world * wl.nx * wl.nz * args.steps / (ms_total / 1e3),

@@ -96,6 +96,9 @@ typedef struct {
   int fold;                     /* 1: merge the identical reciprocal rows (p,q),(-q,-p)
                                    into one row of weight 2 (same normal equations);
                                    0: keep every row as the paper writes them           */
+  int chol_df;                  /* mixed path only: 1 = Cholesky trailing updates in
+                                   double-float (FP32 hi/lo pairs, ~48-bit) on the FP32
+                                   pipes, 0 = native FP64 everywhere (default)          */
 } edt_config;
 
 /* Host-side statistics of a context; the device-side fields are refreshed by

@@ -108,6 +108,7 @@ int validate(const edt_config* c) {
   if (!(c->alpha >= 0) || !std::isfinite(c->alpha)) return EDT_EINVAL;
   if (!std::isfinite(c->cutoff)) return EDT_EINVAL;
   if (c->fold != 0 && c->fold != 1) return EDT_EINVAL;
+  if (c->chol_df != 0 && c->chol_df != 1) return EDT_EINVAL;
   return EDT_OK;
 }
 
@@ -307,6 +308,7 @@ void bind(edt_ctx* c) {
   d.N = c->N; d.nk = c->nk; d.nz = c->nz; d.nf = c->nf; d.nsub = c->nsub; d.nlayer = c->nlayer;
   d.nzs = (c->nz + 1) & ~1;
   d.precision = c->cfg.precision; d.passes = c->cfg.passes; d.fold = c->cfg.fold;
+  d.chol_df = c->cfg.precision == EDT_MIXED ? c->cfg.chol_df : 0;
   d.alpha = c->cfg.alpha; d.dx = c->cfg.dx; d.dz = c->cfg.dz;
   d.fc = at<const FreqConst*>(c, c->r_fc);
   d.layer_top = at<const double*>(c, c->r_ltop);

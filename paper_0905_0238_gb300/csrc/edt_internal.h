@@ -42,7 +42,7 @@ struct FreqConst {
 struct Dev {
   int N, nk, nz, nf, nsub, nlayer;
   int nzs;                      // row stride of the FP32 table: nz rounded up to even
-  int precision, passes, fold;
+  int precision, passes, fold, chol_df;
   double alpha, dx, dz;
   // constant tables
   const FreqConst* fc;          // [nf]

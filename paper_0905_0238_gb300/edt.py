@@ -31,6 +31,7 @@ class edt_config(C.Structure):
         ("layer_vel_mps", C.POINTER(C.c_double)),
         ("precision", C.c_int), ("passes", C.c_int), ("refine", C.c_int),
         ("alpha", C.c_double), ("cutoff", C.c_double), ("fold", C.c_int),
+        ("chol_df", C.c_int),
     ]
 
 
@@ -204,6 +205,7 @@ class Config:
     alpha: float = 1e-2
     cutoff: float = 1.0
     fold: int = 1
+    chol_df: int = 0
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -231,7 +233,7 @@ class Solver:
             nlayer=len(self._top), layer_top_m=self._top.ctypes.data_as(dp),
             layer_vel_mps=self._vel.ctypes.data_as(dp), precision=cfg.precision,
             passes=cfg.passes, refine=cfg.refine, alpha=cfg.alpha, cutoff=cfg.cutoff,
-            fold=cfg.fold)
+            fold=cfg.fold, chol_df=cfg.chol_df)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.ctx = None
         self.ctx, self.ws_bytes = edt_create(c)

@@ -112,3 +112,18 @@ def test_graph_replay_matches_direct_calls():
             # FP64 atomics in the trace and residual sums make the last bits order-dependent
             assert rel_l2(out.cpu().numpy(), ref) < 1e-10
         s.set_graph(False)
+
+
+@pytest.mark.parametrize("nx,nz,nf", [(32, 40, 6), (64, 130, 4), (32, 256, 3)])
+def test_double_float_cholesky_option(nx, nz, nf):
+    """Trailing updates in double-float give the native-FP64 result to ~1e-9 and stay
+    within the 1e-5 target against the oracle."""
+    from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED
+    wl = small_workload(nx=nx, nz=nz, nf=nf, alpha=1e-2, dz=8.0)
+    D = born_data(wl, salt=7)
+    V_or, _ = edt2d.invert(wl, D.astype(np.complex128))
+    V64 = solver(wl).invert(dev(D)).cpu().numpy()
+    s = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=3, refine=1, chol_df=1))
+    Vdf = s.invert(dev(D)).cpu().numpy()
+    assert rel_l2(Vdf, V64) < 1e-9
+    assert rel_l2(Vdf, V_or) < 1e-5
