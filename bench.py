@@ -57,6 +57,29 @@ def workload_summary(wl):
             f"{len(wl.layer_top)} layers, 3% random field, c64 Born data + 20 dB noise")
 
 
+# ------------------------------------------------------------------ multi-rank host logic
+def line_salt(rank: int) -> int:
+    """Seed salt of the survey line a rank inverts: every rank gets its own line."""
+    return 1 + int(rank)
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """The largest of the ranks' values (the job's time); identity on one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_step: int, steps: int, ms_total: float) -> float:
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return world * units_per_step * steps / (ms_total / 1e3)
+
+
 # ------------------------------------------------------------------ CPU oracle timing
 def cpu_child(spec_path):
     """Runs in a subprocess with single-threaded BLAS: time the oracle on a sample."""
@@ -214,7 +237,7 @@ def main():
             dist.barrier()
 
     wl = synth.preset(WORKLOAD)
-    rng = synth.rng_for(1, salt=1 + rank)           # each rank: its own survey line
+    rng = synth.rng_for(1, salt=line_salt(rank))     # each rank: its own survey line
     V = synth.perturbation_random_field(rng, wl.nx, wl.dx, wl.nz, wl.dz, wl.z0,
                                         wl.layer_top, wl.layer_vel, corr=40.0, rms=0.03)
     fp64 = Solver(Config.from_workload(wl, precision=EDT_FP64), device=dev)
@@ -258,13 +281,10 @@ def main():
     ms_total = e0.elapsed_time(e1)
     stages, ncalls = mixed.read_profile()
     mixed.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
     sub_per_step = wl.nx                             # one subproblem per midpoint wavenumber
-    value = world * sub_per_step * args.steps / (ms_total / 1e3)
+    value = job_throughput(world, sub_per_step, args.steps, ms_total)
 
     # ---- end to end through the host-buffer entry point ----------------------------
     Dh = D.cpu().pin_memory()
@@ -281,12 +301,8 @@ def main():
     h1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = h0.elapsed_time(h1)
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * sub_per_step * args.steps / (ms_e2e / 1e3)
+    ms_e2e = max_over_ranks(h0.elapsed_time(h1), world)
+    e2e_value = job_throughput(world, sub_per_step, args.steps, ms_e2e)
 
     # ---- accuracy vs the FP64 GPU path, and the FP64 path's own throughput --------------
     acc = {}
@@ -311,6 +327,32 @@ def main():
                    fp64_gpu_ms_per_step=ms64,
                    fp64_gpu_subproblems_per_sec=sub_per_step / (ms64 / 1e3),
                    speedup_vs_fp64_gpu=(ms64 / ms_step))
+
+    # ---- variant: Cholesky trailing updates in double-float (a library option) ------------
+    variants = {}
+    if args.chol_df == 0:
+        dfs = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=args.passes,
+                                          refine=args.refine, chol_df=1), device=dev)
+        Vdf = torch.empty_like(Vout)
+        for _ in range(3):
+            dfs.invert(D, out=Vdf)
+        torch.cuda.synchronize()
+        barrier()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(args.steps):
+            dfs.invert(D, out=Vdf)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        ms_df = max_over_ranks(v0.elapsed_time(v1), world)
+        variants["chol_df"] = dict(
+            description="Cholesky trailing updates in double-float (FP32 hi/lo) on the FP32 pipes",
+            value=job_throughput(world, sub_per_step, args.steps, ms_df), unit="subproblems/s",
+            ms_per_step=ms_df / args.steps,
+            rel_l2_V_vs_default=float(torch.linalg.norm(Vdf.double() - Vout.double())
+                                      / torch.linalg.norm(Vout.double())))
+        del dfs
 
     if rank != 0:
         if world > 1:
@@ -360,7 +402,8 @@ def main():
                  h2d_bytes_per_step=int(Dh.numel() * Dh.element_size()),
                  d2h_bytes_per_step=int(Vh.numel() * Vh.element_size())),
         gpu_launches=int(st.launches_per_invert) * args.steps,
-        roofline=roof, stage_ms=stage_ms, accuracy=acc, clocks=clk, cpu_baseline=cpu)
+        roofline=roof, stage_ms=stage_ms, accuracy=acc, variants=variants, clocks=clk,
+        cpu_baseline=cpu)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
