@@ -351,7 +351,9 @@ def main():
             value=job_throughput(world, sub_per_step, args.steps, ms_df), unit="subproblems/s",
             ms_per_step=ms_df / args.steps,
             rel_l2_V_vs_default=float(torch.linalg.norm(Vdf.double() - Vout.double())
-                                      / torch.linalg.norm(Vout.double())))
+                                      / torch.linalg.norm(Vout.double())),
+            rel_l2_vhat_vs_default=float(torch.linalg.norm(dfs.vhat() - mixed.vhat())
+                                         / torch.linalg.norm(mixed.vhat())))
         del dfs
 
     if rank != 0:

@@ -99,6 +99,10 @@ typedef struct {
   int chol_df;                  /* mixed path only: 1 = Cholesky trailing updates in
                                    double-float (FP32 hi/lo pairs, ~48-bit) on the FP32
                                    pipes, 0 = native FP64 everywhere (default)          */
+  int freq_chunk;               /* frequency planes per chunk of the data transform and
+                                   the forward model (the spectrum buffer holds one
+                                   chunk); 0 = automatic: as many planes as fit in
+                                   256 MB.  Smaller chunks trade speed for workspace.   */
 } edt_config;
 
 /* Host-side statistics of a context; the device-side fields are refreshed by
@@ -117,6 +121,9 @@ typedef struct {
   int launches_per_invert;      /* CUDA kernels one edt_invert launches                  */
   long long gram_rows_padded;   /* complex rows the tensor-core Gram processes per call,
                                    each CTA segment padded to a multiple of 32           */
+  int freq_chunk;               /* frequency planes the data transform and the
+                                   right-hand-side gather process per chunk (the
+                                   spectrum buffer holds one chunk, about 32 MB)         */
 } edt_stats;
 
 /* Create a context for `cfg` and report the device workspace it needs.

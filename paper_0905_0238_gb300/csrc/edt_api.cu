@@ -44,6 +44,8 @@ struct edt_ctx {
   std::vector<float> fc32;         // [nf] sqrt|s_f|
   std::vector<uint32_t> rows;
   std::vector<long long> row_off;
+  std::vector<long long> row_off_mf;   // [nsub][nf + 1]
+  int fchunk = 1;
   std::vector<long long> counts_cut;
   std::vector<double2> tw64;
   std::vector<float2> tw32;
@@ -54,7 +56,7 @@ struct edt_ctx {
   // workspace
   size_t ws_bytes = 0;
   void* ws = nullptr;
-  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_tw64, r_tw32, r_segm, r_segr0,
+  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
       r_dinv, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
   Dev dev{};
@@ -79,7 +81,7 @@ namespace {
 
 constexpr int kProfCalls = 256;   // calls whose stage events are kept between reads
 
-const char* kStageNames[edt_ctx::NSTAGE] = {"green", "transform", "rhs", "gram",
+const char* kStageNames[edt_ctx::NSTAGE] = {"green", "transform_rhs", "trace_reset", "gram",
                                             "gram_reduce", "cholesky", "refine", "inverse",
                                             "unused"};
 
@@ -109,6 +111,7 @@ int validate(const edt_config* c) {
   if (!std::isfinite(c->cutoff)) return EDT_EINVAL;
   if (c->fold != 0 && c->fold != 1) return EDT_EINVAL;
   if (c->chol_df != 0 && c->chol_df != 1) return EDT_EINVAL;
+  if (c->freq_chunk < 0) return EDT_EINVAL;
   return EDT_OK;
 }
 
@@ -158,11 +161,13 @@ void plan(edt_ctx* c) {
   const double cmin = *std::min_element(c->vel.begin(), c->vel.end());
   c->rows.clear();
   c->row_off.assign(c->nsub + 1, 0);
+  c->row_off_mf.assign(size_t(c->nsub) * (c->nf + 1), 0);
   c->counts_cut.assign(c->nsub, 0);
   auto sidx = [N](int n) { return n <= N / 2 ? n : n - N; };
   for (int m = 0; m < c->nsub; ++m) {
     c->row_off[m] = (long long)c->rows.size();
     for (int f = 0; f < c->nf; ++f) {
+      c->row_off_mf[size_t(m) * (c->nf + 1) + f] = (long long)c->rows.size();
       const double lim = c->fc[f].lim;
       // order p = 0, N/2, 1, N-1, 2, N-2, ...: rows p and -p read the same table row g(|p|),
       // so placed side by side the second read is served from L1
@@ -189,6 +194,14 @@ void plan(edt_ctx* c) {
     }
   }
   c->row_off[c->nsub] = (long long)c->rows.size();
+  for (int m = 0; m < c->nsub; ++m) c->row_off_mf[size_t(m) * (c->nf + 1) + c->nf] = c->row_off[m + 1];
+  // frequency planes per transform chunk: bounds the spectrum buffer (each chunk costs a
+  // few partly filled waves of three launches, so the automatic size is large)
+  {
+    const size_t plane = size_t(N) * N * (g.precision == EDT_MIXED ? sizeof(float2) : sizeof(double2));
+    const size_t want = g.freq_chunk > 0 ? size_t(g.freq_chunk) : (size_t(256) << 20) / plane;
+    c->fchunk = int(std::max<size_t>(1, std::min<size_t>(c->nf, want)));
+  }
   // twiddles e^{-2 pi i k / N}
   c->tw64.resize(N / 2);
   c->tw32.resize(N / 2);
@@ -267,6 +280,7 @@ void layout(edt_ctx* c) {
   take(c->r_zo, nz * sizeof(double));
   take(c->r_rows, std::max<size_t>(R, 1) * sizeof(uint32_t));
   take(c->r_roff, (ns + 1) * sizeof(long long));
+  take(c->r_roffmf, ns * (nf + 1) * sizeof(long long));
   take(c->r_tw64, (N / 2) * sizeof(double2));
   take(c->r_tw32, (N / 2) * sizeof(float2));
   take(c->r_segm, std::max<size_t>(c->seg_m.size(), 1) * sizeof(int));
@@ -280,7 +294,7 @@ void layout(edt_ctx* c) {
   take(c->r_coef32, mixed ? nf * nk * c->nlayer * 8 * sizeof(float) : 0);
   take(c->r_g64, nf * nk * nz * sizeof(double2));
   take(c->r_g32, mixed ? nf * nk * size_t((c->nz + 1) & ~1) * sizeof(float2) : 0);
-  take(c->r_X, nf * N * N * (mixed ? sizeof(float2) : sizeof(double2)));
+  take(c->r_X, size_t(c->fchunk) * N * N * (mixed ? sizeof(float2) : sizeof(double2)));
   take(c->r_Dst, nf * N * N * sizeof(double2));
   take(c->r_Vst, N * nz * sizeof(double));
   take(c->r_rhs, std::max<size_t>(R, 1) * 2 * (mixed ? sizeof(float2) : sizeof(double2)));
@@ -317,6 +331,8 @@ void bind(edt_ctx* c) {
   d.z_off = at<const double*>(c, c->r_zo);
   d.rows = at<const uint32_t*>(c, c->r_rows);
   d.row_off = at<const long long*>(c, c->r_roff);
+  d.row_off_mf = at<const long long*>(c, c->r_roffmf);
+  d.fchunk = c->fchunk;
   d.tw64 = at<const double2*>(c, c->r_tw64);
   d.tw32 = at<const float2*>(c, c->r_tw32);
   d.seg_m = at<const int*>(c, c->r_segm);
@@ -365,6 +381,23 @@ void prof_mark(edt_ctx* c, int stage, cudaStream_t s) {
   c->prof_used[stage] = 1;
 }
 
+// Data transform and right-hand-side gather, chunk by chunk of frequency planes.
+int transform_rhs(edt_ctx* c, const void* D, int D_dtype, cudaStream_t s) {
+  const Dev& d = c->dev;
+  const bool mixed = c->cfg.precision == EDT_MIXED;
+  for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
+    const int nfc = std::min(d.fchunk, d.nf - f0);
+    if (mixed) {
+      EDT_TRY(launch_transform<float>(d, D, D_dtype, f0, nfc, s));
+      EDT_TRY(launch_rhs<float>(d, f0, nfc, s));
+    } else {
+      EDT_TRY(launch_transform<double>(d, D, D_dtype, f0, nfc, s));
+      EDT_TRY(launch_rhs<double>(d, f0, nfc, s));
+    }
+  }
+  return EDT_OK;
+}
+
 int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cudaStream_t s) {
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
@@ -372,11 +405,8 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_mark(c, 0, s);
   EDT_TRY(launch_green(d, s, mixed ? GREEN_G32 : GREEN_G64));
   prof_mark(c, 1, s);
-  if (mixed) { EDT_TRY(launch_transform<float>(d, D, D_dtype, s)); }
-  else { EDT_TRY(launch_transform<double>(d, D, D_dtype, s)); }
+  EDT_TRYI(transform_rhs(c, D, D_dtype, s));
   prof_mark(c, 2, s);
-  if (mixed) { EDT_TRY(launch_rhs<float>(d, s)); }
-  else { EDT_TRY(launch_rhs<double>(d, s)); }
   if (mixed) EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
   prof_mark(c, 3, s);
   if (mixed) {
@@ -446,6 +476,7 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRYI(upload(c, c->r_fc32, c->fc32));
   EDT_TRYI(upload(c, c->r_rows, c->rows));
   EDT_TRYI(upload(c, c->r_roff, c->row_off));
+  EDT_TRYI(upload(c, c->r_roffmf, c->row_off_mf));
   EDT_TRYI(upload(c, c->r_tw64, c->tw64));
   EDT_TRYI(upload(c, c->r_tw32, c->tw32));
   EDT_TRYI(upload(c, c->r_segm, c->seg_m));
@@ -564,8 +595,7 @@ int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr,
   const bool mixed = c->cfg.precision == EDT_MIXED;
   c->last_stream = s;
   EDT_TRY(launch_green(d, s, mixed ? GREEN_G32 : GREEN_G64));
-  if (mixed) { EDT_TRY(launch_transform<float>(d, D, D_dtype, s)); EDT_TRY(launch_rhs<float>(d, s)); }
-  else { EDT_TRY(launch_transform<double>(d, D, D_dtype, s)); EDT_TRY(launch_rhs<double>(d, s)); }
+  EDT_TRYI(transform_rhs(c, D, D_dtype, s));
   if (mixed) {
     EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
     EDT_TRY(launch_gram_tc(d, s));
@@ -599,10 +629,13 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   o->workspace_bytes = c->ws_bytes;
   o->gram_flop = 2.0 * 2.0 * double(o->rows_solved) * double(c->nz) * double(c->nz + 2);
   o->last_status = c->last_status;
-  // kernels launched by one edt_invert: green (3), transform (2), rhs (1), Gram (FP64: 1;
-  // mixed: tensor-core + reduce 2), batched Cholesky, per refinement step (2), inverse (1)
-  o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 9 + 2 * c->cfg.refine : 7) +
+  // kernels launched by one edt_invert: green (3), per frequency chunk transform (2) and
+  // right-hand sides (1), Gram (FP64: 1; mixed: tensor-core + reduce 2), batched Cholesky,
+  // per refinement step (2), inverse (1)
+  const int nchunk = (c->nf + c->fchunk - 1) / c->fchunk;
+  o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + 3 * nchunk +
                            chol_launches(c->nz);
+  o->freq_chunk = c->fchunk;
   o->gram_rows_padded = 0;
   for (long long n : c->seg_nrow) o->gram_rows_padded += (n + TC_KC - 1) / TC_KC * TC_KC;
   if (c->ws) {

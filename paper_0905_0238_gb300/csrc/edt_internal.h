@@ -54,6 +54,8 @@ struct Dev {
   const float* fc32_sqrt_s;     // [nf] sqrt|s_f| as float
   const uint32_t* rows;         // [rows_solved], grouped by m
   const long long* row_off;     // [nsub + 1]
+  const long long* row_off_mf;  // [nsub][nf + 1]: first row of frequency f within subproblem m
+  int fchunk;                   // frequency planes transformed per chunk (L2-sized)
   const double2* tw64;          // [N/2] exp(-2 pi i k / N)
   const float2* tw32;           // [N/2]
   const int* seg_m;             // tensor-core Gram: per segment its m      [nseg]
@@ -67,7 +69,7 @@ struct Dev {
   float* coef32;                // [nf][nk][nlayer][8] FP32 copies for the fast evaluation
   double2* g64;                 // [nf][nk][nz]
   float2* g32;                  // [nf][nk][nzs] sqrt|s_f| g, mixed path (padding zero)
-  void* X;                      // [nf][N][N] complex, path precision
+  void* X;                      // [fchunk][N][N] complex, path precision (one chunk of planes)
   void* Dstage;                 // host-call staging of D (complex128-sized)
   void* Vstage;                 // host-call staging of V (double-sized)
   void* rhs;                    // [rows_solved][2] complex, path precision
@@ -90,10 +92,12 @@ constexpr int GREEN_G64 = 1, GREEN_G32 = 2;   // tables launch_green writes
 // GREEN_G32 alone: the fast FP32 evaluation for the mixed path (no FP64 table)
 cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables);
 
+// Data transform of frequency planes [f0, f0 + nfc) into X, then the split right-hand
+// sides of every subproblem's rows at those frequencies (X holds only the chunk).
 template <typename T>
-cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, cudaStream_t s);
+cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, int f0, int nfc, cudaStream_t s);
 template <typename T>
-cudaError_t launch_rhs(const Dev& d, cudaStream_t s);
+cudaError_t launch_rhs(const Dev& d, int f0, int nfc, cudaStream_t s);
 
 cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace

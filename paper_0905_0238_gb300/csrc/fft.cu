@@ -4,8 +4,9 @@
 // Data transform (the discrete form of the Fourier transform over midpoint and offset in
 // Section "Two dimensions"):  D2(p, q) = sum_is sum_ir D(is, ir) e^{-i k_p x_ir} e^{+i k_q x_is}.
 // Pass 1 transforms every receiver line (contiguous rows, sign -), pass 2 every source
-// column (stride N, sign +), leaving X[f][q][p] = D2(p, q).  Both passes are radix-2
-// decimation-in-time FFTs in shared memory with twiddles from a host-computed table.
+// column (stride N, sign +), leaving X[f][q][p] = D2(p, q).  The FP32 path uses register-
+// resident warp FFTs (one warp per line); the FP64 path and N < 32 use shared-memory
+// radix-4 FFTs.  Twiddles come from a host-computed table.
 //
 // Inverse transform: Vhat(k_m) for 0 <= m <= N/2 from the split solutions x_+/x_-,
 // completed by Vhat(-k_m) = conj Vhat(k_m) (eq. VSym), then
@@ -147,6 +148,173 @@ __global__ void fft_cols_kernel(Dev d, cplx_t<T>* X, int cpb, int sign, T scale)
   }
 }
 
+// ---- register-resident warp FFT (FP32, N = 32 * P) ----------------------------------
+// Four-step split of one length-N transform over a warp: lane b holds x[32 a + b] for
+// a < P; (1) a P-point DFT over a in registers (radix-2 DIT, bit-reversed register order
+// fixed at compile time), (2) the twiddle W_N^{b k1}, (3) a 32-point decimation-in-frequency
+// DFT across the lanes by shuffles.  Lane l then holds X[k1 + P * bitrev5(l)] in register
+// k1.  Each point passes through shared memory once (for the coalesced store) instead of
+// once per radix stage.
+__host__ __device__ constexpr int clog2(int n) { return n <= 1 ? 0 : 1 + clog2(n / 2); }
+__device__ __forceinline__ int rbits(int x, int bits) {     // bit reversal of the low `bits` bits
+  return bits == 0 ? 0 : int(__brev(unsigned(x)) >> (32 - bits));
+}
+
+__device__ __forceinline__ float2 tw_at(const float2* tw, int e, int N) {   // W_N^e, 0 <= e < N
+  if (e < (N >> 1)) return tw[e];
+  const float2 w = tw[e - (N >> 1)];
+  return make_float2(-w.x, -w.y);
+}
+
+template <int P>
+__device__ __forceinline__ void warp_fft(float2 (&r)[P], const float2* tw, int N, int sign, int lane) {
+  constexpr int LP = clog2(P);
+  float2 t[P];
+#pragma unroll
+  for (int a = 0; a < P; ++a) t[rbits(a, LP)] = r[a];
+#pragma unroll
+  for (int st = 0; st < LP; ++st) {                         // half-size h = 2^st
+#pragma unroll
+    for (int b = 0; b < P / 2; ++b) {
+      const int h = 1 << st;
+      const int jj = b & (h - 1), i0 = ((b >> st) << (st + 1)) + jj, i1 = i0 + h;
+      float2 w = tw[jj * (N >> (st + 1))];                  // W_{2h}^jj
+      if (sign > 0) w.y = -w.y;
+      const float2 u = t[i0], v = t[i1] * w;
+      t[i0] = u + v;
+      t[i1] = u - v;
+    }
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < P; ++k1) {                          // W_N^{lane k1}
+    float2 w = tw_at(tw, (lane * k1) & (N - 1), N);
+    if (sign > 0) w.y = -w.y;
+    t[k1] = t[k1] * w;
+  }
+#pragma unroll
+  for (int sh = 4; sh >= 0; --sh) {                         // cross-lane DIF, span 2^sh
+    const int j = lane & ((1 << sh) - 1);
+    float2 w = tw[j * (N >> (sh + 1))];                     // W_{2^(sh+1)}^j
+    if (sign > 0) w.y = -w.y;
+    const bool upper = (lane >> sh) & 1;
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      float2 u;
+      u.x = __shfl_xor_sync(0xffffffffu, t[k1].x, 1 << sh);
+      u.y = __shfl_xor_sync(0xffffffffu, t[k1].y, 1 << sh);
+      t[k1] = upper ? (u - t[k1]) * w : t[k1] + u;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < P; ++a) r[a] = t[a];
+}
+
+constexpr int WR_WARPS = 8;   // rows per block in the row kernel
+
+template <int P>
+__global__ void __launch_bounds__(WR_WARPS * 32) wfft_rows_kernel(Dev d, const void* in, int in_dtype,
+                                                                 float2* out, long long nrows, int sign,
+                                                                 float scale) {
+  constexpr int N = 32 * P;
+  __shared__ float2 sm[WR_WARPS][N + N / 16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long row = (long long)blockIdx.x * WR_WARPS + warp;
+  if (row >= nrows) return;
+  float2 r[P];
+#pragma unroll
+  for (int a = 0; a < P; ++a) r[a] = load_c<float2>(in, in_dtype, size_t(row) * N + 32 * a + lane);
+  warp_fft<P>(r, d.tw32, N, sign, lane);
+  const int brl = rbits(lane, 5) * P;
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) sm[warp][pd(k1 + brl)] = r[k1];
+  __syncwarp();
+  float2* o = out + size_t(row) * N;
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const float2 v = sm[warp][pd(32 * j + lane)];
+    o[32 * j + lane] = make_float2(v.x * scale, v.y * scale);
+  }
+}
+
+// Columns of [planes][N][N] in place, WC columns per block, one warp per column.
+template <int P, int WC>
+__global__ void __launch_bounds__(WC * 32) wfft_cols_kernel(Dev d, float2* X, int sign, float scale) {
+  constexpr int N = 32 * P;
+  constexpr int LD = N + N / 16 + 1;                         // odd stride: columns on distinct banks
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tile = reinterpret_cast<float2*>(smem_raw);        // [WC][LD]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * WC;
+  float2* Pl = X + size_t(blockIdx.y) * N * N;
+  for (int e = threadIdx.x; e < N * WC; e += blockDim.x) {
+    const int rr = e / WC, c = e - rr * WC;
+    tile[c * LD + pd(rr)] = Pl[size_t(rr) * N + c0 + c];
+  }
+  __syncthreads();
+  float2 r[P];
+#pragma unroll
+  for (int a = 0; a < P; ++a) r[a] = tile[warp * LD + pd(32 * a + lane)];
+  warp_fft<P>(r, d.tw32, N, sign, lane);
+  const int brl = rbits(lane, 5) * P;
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) tile[warp * LD + pd(k1 + brl)] = r[k1];
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * WC; e += blockDim.x) {
+    const int rr = e / WC, c = e - rr * WC;
+    const float2 v = tile[c * LD + pd(rr)];
+    Pl[size_t(rr) * N + c0 + c] = make_float2(v.x * scale, v.y * scale);
+  }
+}
+
+template <int P>
+cudaError_t wfft_rows_launch(const Dev& d, const void* in, int in_dtype, float2* out, long long nrows,
+                             int sign, float scale, cudaStream_t st) {
+  const long long nb = (nrows + WR_WARPS - 1) / WR_WARPS;
+  wfft_rows_kernel<P><<<unsigned(nb), WR_WARPS * 32, 0, st>>>(d, in, in_dtype, out, nrows, sign, scale);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t wfft_cols_launch(const Dev& d, float2* X, int planes, int sign, float scale, cudaStream_t st) {
+  constexpr int N = 32 * P, WC = P >= 32 ? 8 : 16;
+  const size_t smem = size_t(WC) * (N + N / 16 + 1) * sizeof(float2);
+  dim3 g(N / WC, planes);
+  wfft_cols_kernel<P, WC><<<g, WC * 32, smem, st>>>(d, X, sign, scale);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t wfft_cols_prepare() {
+  constexpr int N = 32 * P, WC = P >= 32 ? 8 : 16;
+  const size_t smem = size_t(WC) * (N + N / 16 + 1) * sizeof(float2);
+  return cudaFuncSetAttribute(wfft_cols_kernel<P, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+// FP32 row / column transforms for N >= 32 (warp FFT); false if N is outside that range
+bool wfft_rows(const Dev& d, const void* in, int in_dtype, float2* out, long long nrows, int sign,
+               float scale, cudaStream_t st, cudaError_t* e) {
+  switch (d.N) {
+    case 32: *e = wfft_rows_launch<1>(d, in, in_dtype, out, nrows, sign, scale, st); return true;
+    case 64: *e = wfft_rows_launch<2>(d, in, in_dtype, out, nrows, sign, scale, st); return true;
+    case 128: *e = wfft_rows_launch<4>(d, in, in_dtype, out, nrows, sign, scale, st); return true;
+    case 256: *e = wfft_rows_launch<8>(d, in, in_dtype, out, nrows, sign, scale, st); return true;
+    case 512: *e = wfft_rows_launch<16>(d, in, in_dtype, out, nrows, sign, scale, st); return true;
+    case 1024: *e = wfft_rows_launch<32>(d, in, in_dtype, out, nrows, sign, scale, st); return true;
+    default: return false;
+  }
+}
+bool wfft_cols(const Dev& d, float2* X, int planes, int sign, float scale, cudaStream_t st, cudaError_t* e) {
+  switch (d.N) {
+    case 32: *e = wfft_cols_launch<1>(d, X, planes, sign, scale, st); return true;
+    case 64: *e = wfft_cols_launch<2>(d, X, planes, sign, scale, st); return true;
+    case 128: *e = wfft_cols_launch<4>(d, X, planes, sign, scale, st); return true;
+    case 256: *e = wfft_cols_launch<8>(d, X, planes, sign, scale, st); return true;
+    case 512: *e = wfft_cols_launch<16>(d, X, planes, sign, scale, st); return true;
+    case 1024: *e = wfft_cols_launch<32>(d, X, planes, sign, scale, st); return true;
+    default: return false;
+  }
+}
+
 template <typename T>
 cudaError_t rows_fft(const Dev& d, const void* in, int in_dtype, void* out, int out_dtype,
                      long long nrows, int sign, T scale, cudaStream_t st) {
@@ -229,11 +397,11 @@ __global__ void lateral_dft_kernel(Dev d, const void* V, int V_dtype) {
 // D2[f][q][p] = s_f sum_j g(|p'|, j) g(|q'|, j) Vhat((p - q) mod N, j): 16 x 16 (p, q) tile
 // per block, depth in chunks of 32 staged in shared memory.
 template <typename T>
-__global__ void born_spectral_kernel(Dev d, cplx_t<T>* X) {
+__global__ void born_spectral_kernel(Dev d, cplx_t<T>* X, int f0) {
   using T2 = cplx_t<T>;
   constexpr int TP = 16, ZC = 32;
   __shared__ double2 gp[TP][ZC], gq[TP][ZC], vh[2 * TP][ZC];
-  const int N = d.N, f = blockIdx.z;
+  const int N = d.N, f = f0 + blockIdx.z;   // X holds the chunk's planes only
   const int p0 = blockIdx.x * TP, q0 = blockIdx.y * TP;
   const int tp = threadIdx.x & (TP - 1), tq = threadIdx.x / TP;
   double2 acc = make_double2(0.0, 0.0);
@@ -261,21 +429,30 @@ __global__ void born_spectral_kernel(Dev d, cplx_t<T>* X) {
   double2 om = make_double2(fc.om_re, fc.om_im);
   double2 sf = (d.dz / d.dx) * (om * om);
   acc = sf * acc;
-  X[size_t(f) * N * N + size_t(q0 + tq) * N + p0 + tp] = cmk(T(acc.x), T(acc.y));
+  X[size_t(blockIdx.z) * N * N + size_t(q0 + tq) * N + p0 + tp] = cmk(T(acc.x), T(acc.y));
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, cudaStream_t s) {
+cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, int f0, int nfc, cudaStream_t s) {
   using T2 = cplx_t<T>;
   const int out_dtype = sizeof(T) == 4 ? EDT_C64 : EDT_C128;
-  cudaError_t e = rows_fft<T>(d, D, D_dtype, d.X, out_dtype, (long long)d.nf * d.N, -1, T(1), s);
+  const size_t esz = D_dtype == EDT_C64 ? sizeof(float2) : sizeof(double2);
+  const void* Dc = static_cast<const char*>(D) + size_t(f0) * d.N * d.N * esz;
+  const long long nrows = (long long)nfc * d.N;
+  cudaError_t e = cudaSuccess;
+  if (sizeof(T) == 4 && wfft_rows(d, Dc, D_dtype, reinterpret_cast<float2*>(d.X), nrows, -1, 1.f, s, &e)) {
+    if (e != cudaSuccess) return e;
+    wfft_cols(d, reinterpret_cast<float2*>(d.X), nfc, +1, 1.f, s, &e);
+    return e;
+  }
+  e = rows_fft<T>(d, Dc, D_dtype, d.X, out_dtype, nrows, -1, T(1), s);
   if (e != cudaSuccess) return e;
-  return cols_fft<T>(d, reinterpret_cast<T2*>(d.X), d.nf, +1, T(1), s);
+  return cols_fft<T>(d, reinterpret_cast<T2*>(d.X), nfc, +1, T(1), s);
 }
-template cudaError_t launch_transform<float>(const Dev&, const void*, int, cudaStream_t);
-template cudaError_t launch_transform<double>(const Dev&, const void*, int, cudaStream_t);
+template cudaError_t launch_transform<float>(const Dev&, const void*, int, int, int, cudaStream_t);
+template cudaError_t launch_transform<double>(const Dev&, const void*, int, int, int, cudaStream_t);
 
 // Opt-in shared-memory sizes of this file's kernels, set once per context (outside any
 // stream capture).
@@ -295,7 +472,18 @@ cudaError_t prepare_fft(const Dev& d) {
                                 int(size_t(cpb64) * (padded_len(N) + 1) * sizeof(double2)))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(inv))) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(lateral_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(inv));
+  if ((e = cudaFuncSetAttribute(lateral_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(inv))) !=
+      cudaSuccess)
+    return e;
+  switch (N) {
+    case 32: return wfft_cols_prepare<1>();
+    case 64: return wfft_cols_prepare<2>();
+    case 128: return wfft_cols_prepare<4>();
+    case 256: return wfft_cols_prepare<8>();
+    case 512: return wfft_cols_prepare<16>();
+    case 1024: return wfft_cols_prepare<32>();
+    default: return cudaSuccess;
+  }
 }
 
 cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s) {
@@ -304,26 +492,35 @@ cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t forward_chunk(const Dev& d, void* D, int D_dtype, int f0, int nfc, cudaStream_t s) {
+  using T2 = cplx_t<T>;
+  const int xdtype = sizeof(T) == 4 ? EDT_C64 : EDT_C128;
+  const size_t esz = D_dtype == EDT_C64 ? sizeof(float2) : sizeof(double2);
+  void* Dc = static_cast<char*>(D) + size_t(f0) * d.N * d.N * esz;
+  dim3 g(d.N / 16, d.N / 16, nfc);
+  born_spectral_kernel<T><<<g, 256, 0, s>>>(d, reinterpret_cast<T2*>(d.X), f0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // inverse of the data transform: undo pass 2 (sign -, 1/N), then pass 1 (sign +, 1/N)
+  if ((e = cols_fft<T>(d, reinterpret_cast<T2*>(d.X), nfc, -1, T(1) / T(d.N), s)) != cudaSuccess) return e;
+  return rows_fft<T>(d, d.X, xdtype, Dc, D_dtype, (long long)nfc * d.N, +1, T(1) / T(d.N), s);
+}
+
 cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
                            cudaStream_t s) {
   size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);
   lateral_dft_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 g(d.N / 16, d.N / 16, d.nf);
-  if (d.precision == EDT_FP64) {
-    born_spectral_kernel<double><<<g, 256, 0, s>>>(d, reinterpret_cast<double2*>(d.X));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // inverse of the data transform: undo pass 2 (sign -, 1/N), then pass 1 (sign +, 1/N)
-    if ((e = cols_fft<double>(d, reinterpret_cast<double2*>(d.X), d.nf, -1, 1.0 / d.N, s)) != cudaSuccess)
-      return e;
-    return rows_fft<double>(d, d.X, EDT_C128, D, D_dtype, (long long)d.nf * d.N, +1, 1.0 / d.N, s);
+  // the spectrum X holds one chunk of frequency planes at a time
+  for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
+    const int nfc = std::min(d.fchunk, d.nf - f0);
+    e = d.precision == EDT_FP64 ? forward_chunk<double>(d, D, D_dtype, f0, nfc, s)
+                                : forward_chunk<float>(d, D, D_dtype, f0, nfc, s);
+    if (e != cudaSuccess) return e;
   }
-  born_spectral_kernel<float><<<g, 256, 0, s>>>(d, reinterpret_cast<float2*>(d.X));
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cols_fft<float>(d, reinterpret_cast<float2*>(d.X), d.nf, -1, 1.0f / d.N, s)) != cudaSuccess)
-    return e;
-  return rows_fft<float>(d, d.X, EDT_C64, D, D_dtype, (long long)d.nf * d.N, +1, 1.0f / d.N, s);
+  return cudaSuccess;
 }
 
 }  // namespace edt

@@ -7,7 +7,7 @@
 // which leaves the normal equations unchanged.  Finally the complex prefactor of the
 // kernel is moved onto the data: rows are built as |s_f| g_p g_q and the data are rotated
 // by conj(s_f)/|s_f| (a unit-modulus row scaling, which leaves the least-squares problem
-// unchanged).  X holds D2(p, q) at X[f][q][p].
+// unchanged).  X holds D2(p, q) at X[f - f0][q][p] for the current chunk of frequencies.
 #include "edt_internal.h"
 #include "cplx.cuh"
 
@@ -16,17 +16,18 @@ namespace edt {
 namespace {
 
 template <typename T>
-__global__ void rhs_kernel(Dev d) {
+__global__ void rhs_kernel(Dev d, int f0, int f1) {
   using T2 = cplx_t<T>;
   const int m = blockIdx.y;
-  const long long r0 = d.row_off[m], nr = d.row_off[m + 1] - r0;
+  const long long* mo = d.row_off_mf + size_t(m) * (d.nf + 1);
+  const long long r0 = mo[f0], nr = mo[f1] - r0;            // this chunk's rows of subproblem m
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nr) return;
   const int N = d.N, msk = N - 1;
   const uint32_t row = d.rows[r0 + i];
   const int f = row_f(row), p = row_p(row);
   const int q = (p - m) & msk;
-  const T2* X = reinterpret_cast<const T2*>(d.X) + size_t(f) * N * N;
+  const T2* X = reinterpret_cast<const T2*>(d.X) + size_t(f - f0) * N * N;   // chunk-local plane
   T2 a = X[size_t(q) * N + p];           // D2(p, q)
   T2 b = X[size_t(p) * N + q];           // D2(q, p)
   if (row_w2(row)) {
@@ -61,13 +62,13 @@ __global__ void rhs_kernel(Dev d) {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_rhs(const Dev& d, cudaStream_t s) {
-  // a subproblem has at most nf * N rows
-  dim3 g(unsigned((d.nf * (long long)d.N + 255) / 256), d.nsub);
-  rhs_kernel<T><<<g, 256, 0, s>>>(d);
+cudaError_t launch_rhs(const Dev& d, int f0, int nfc, cudaStream_t s) {
+  // a subproblem has at most nfc * N rows at these frequencies
+  dim3 g(unsigned((nfc * (long long)d.N + 255) / 256), d.nsub);
+  rhs_kernel<T><<<g, 256, 0, s>>>(d, f0, f0 + nfc);
   return cudaGetLastError();
 }
-template cudaError_t launch_rhs<float>(const Dev&, cudaStream_t);
-template cudaError_t launch_rhs<double>(const Dev&, cudaStream_t);
+template cudaError_t launch_rhs<float>(const Dev&, int, int, cudaStream_t);
+template cudaError_t launch_rhs<double>(const Dev&, int, int, cudaStream_t);
 
 }  // namespace edt

@@ -31,7 +31,7 @@ class edt_config(C.Structure):
         ("layer_vel_mps", C.POINTER(C.c_double)),
         ("precision", C.c_int), ("passes", C.c_int), ("refine", C.c_int),
         ("alpha", C.c_double), ("cutoff", C.c_double), ("fold", C.c_int),
-        ("chol_df", C.c_int),
+        ("chol_df", C.c_int), ("freq_chunk", C.c_int),
     ]
 
 
@@ -41,7 +41,7 @@ class edt_stats(C.Structure):
         ("rows_min", C.c_int), ("rows_max", C.c_int), ("workspace_bytes", C.c_size_t),
         ("gram_flop", C.c_double), ("n_notpd", C.c_int), ("n_nonfinite", C.c_int),
         ("last_status", C.c_int), ("launches_per_invert", C.c_int),
-        ("gram_rows_padded", C.c_longlong),
+        ("gram_rows_padded", C.c_longlong), ("freq_chunk", C.c_int),
     ]
 
 
@@ -206,6 +206,7 @@ class Config:
     cutoff: float = 1.0
     fold: int = 1
     chol_df: int = 0
+    freq_chunk: int = 0
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -233,7 +234,7 @@ class Solver:
             nlayer=len(self._top), layer_top_m=self._top.ctypes.data_as(dp),
             layer_vel_mps=self._vel.ctypes.data_as(dp), precision=cfg.precision,
             passes=cfg.passes, refine=cfg.refine, alpha=cfg.alpha, cutoff=cfg.cutoff,
-            fold=cfg.fold, chol_df=cfg.chol_df)
+            fold=cfg.fold, chol_df=cfg.chol_df, freq_chunk=cfg.freq_chunk)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.ctx = None
         self.ctx, self.ws_bytes = edt_create(c)

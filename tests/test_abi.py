@@ -46,11 +46,17 @@ def test_host_side_validation_without_gpu():
     st = edt.edt_get_stats(ctx)
     assert st.n_sub == 17 and st.rows_total == counts.sum() and st.rows_solved <= st.rows_total
     edt.edt_destroy(ctx)
+    # the transform chunk: every frequency when they fit, else the requested plane count
+    for req, want in ((0, None), (1, 1), (2, 2), (3, None), (10 ** 6, None)):
+        ctx, ws_req = edt.edt_create(cfg(freq_chunk=req))
+        st = edt.edt_get_stats(ctx)
+        assert st.freq_chunk == (want if want is not None else cfg().nfreq)
+        edt.edt_destroy(ctx)
     for bad, code in ((dict(nx=48), edt.EDT_EUNSUPPORTED), (dict(dx=-1.0), edt.EDT_EINVAL),
                       (dict(precision=7), edt.EDT_EINVAL), (dict(fold=3), edt.EDT_EINVAL),
                       (dict(precision=edt.EDT_MIXED, passes=2), edt.EDT_EINVAL),
                       (dict(precision=edt.EDT_MIXED, nz=300), edt.EDT_EUNSUPPORTED),
-                      (dict(chol_df=2), edt.EDT_EINVAL)):
+                      (dict(chol_df=2), edt.EDT_EINVAL), (dict(freq_chunk=-1), edt.EDT_EINVAL)):
         with pytest.raises(edt.EdtError) as ei:
             edt.edt_create(cfg(**bad))
         assert ei.value.code == code
