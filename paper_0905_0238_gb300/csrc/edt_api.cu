@@ -46,6 +46,14 @@ struct edt_ctx {
   std::vector<long long> row_off;
   std::vector<long long> row_off_mf;   // [nsub][nf + 1]
   int fchunk = 1;
+  // band-limited transform of the mixed path
+  bool band_mode = false;
+  std::vector<BandInfo> band;
+  std::vector<int2> bcol;
+  std::vector<long long> cpre;
+  std::vector<BandChunk> bchunks;
+  size_t band_ymax = 0, band_xmax = 0;   // complex elements of the largest chunk's Y and Xc
+  int band_maxplanes = 0;
   std::vector<long long> counts_cut;
   std::vector<double2> tw64;
   std::vector<float2> tw32;
@@ -56,7 +64,7 @@ struct edt_ctx {
   // workspace
   size_t ws_bytes = 0;
   void* ws = nullptr;
-  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_tw64, r_tw32, r_segm, r_segr0,
+  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
       r_dinv, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
   Dev dev{};
@@ -113,6 +121,65 @@ int validate(const edt_config* c) {
   if (c->chol_df != 0 && c->chol_df != 1) return EDT_EINVAL;
   if (c->freq_chunk < 0) return EDT_EINVAL;
   return EDT_OK;
+}
+
+// Band-limited transform of the mixed path: per frequency the band of signed wavenumber
+// indices that the cut keeps (the same strict test as the row plan), then chunks of planes
+// whose band spectra fit in L2 together (or freq_chunk planes each), the column-pass block
+// table and, per chunk, the prefix counts of its rows over the subproblems.
+void plan_band(edt_ctx* c, double cmin) {
+  const edt_config& g = c->cfg;
+  const int N = c->N, nf = c->nf, ns = c->nsub;
+  c->band_mode = g.precision == EDT_MIXED && band_supported(N);
+  c->band.assign(nf, BandInfo{0, 0, 0, 0});
+  c->bcol.clear(); c->cpre.clear(); c->bchunks.clear();
+  c->band_ymax = c->band_xmax = 0; c->band_maxplanes = 0;
+  if (!c->band_mode) return;
+  for (int f = 0; f < nf; ++f) {
+    BandInfo& b = c->band[f];
+    if (g.cutoff > 0) {
+      const double lim = c->fc[f].lim;
+      if (!(0.0 < lim)) { b.lo = 0; b.w = 0; continue; }       // even n' = 0 is cut
+      int P = 0;
+      while (P < N / 2 && double(P + 1) * cmin < lim) ++P;
+      if (P >= N / 2) { b.lo = -N / 2 + 1; b.w = N; }
+      else { b.lo = -P; b.w = 2 * P + 1; }
+    } else {
+      b.lo = -N / 2 + 1; b.w = N;
+    }
+  }
+  const size_t budget = size_t(48) << 20;                  // bytes of Y + Xc per chunk
+  const int bc = band_cols_per_block();
+  int f0 = 0;
+  while (f0 < nf) {
+    BandChunk ch{f0, f0, int(c->bcol.size()), 0, 0, int(c->bchunks.size())};
+    size_t ysz = 0, xsz = 0;
+    while (ch.f1 < nf) {
+      const BandInfo& b = c->band[ch.f1];
+      const size_t yb = size_t(N) * b.w, xb = size_t(b.w) * b.w;
+      if (g.freq_chunk > 0 ? ch.f1 - f0 >= g.freq_chunk
+                           : (ch.f1 > f0 && (ysz + yb + xsz + xb) * sizeof(float2) > budget))
+        break;
+      c->band[ch.f1].yoff = (long long)ysz;
+      c->band[ch.f1].xoff = (long long)xsz;
+      ysz += yb; xsz += xb;
+      for (int pb = 0; pb < b.w; pb += bc) c->bcol.push_back(make_int2(ch.f1, pb));
+      ch.f1++;
+    }
+    ch.nbcol = int(c->bcol.size()) - ch.bcol0;
+    const size_t base = c->cpre.size();
+    c->cpre.resize(base + ns + 1, 0);
+    for (int m = 0; m < ns; ++m) {
+      const long long* mo = &c->row_off_mf[size_t(m) * (nf + 1)];
+      c->cpre[base + m + 1] = c->cpre[base + m] + (mo[ch.f1] - mo[ch.f0]);
+    }
+    ch.nrow = c->cpre[base + ns];
+    c->band_ymax = std::max(c->band_ymax, ysz);
+    c->band_xmax = std::max(c->band_xmax, xsz);
+    c->band_maxplanes = std::max(c->band_maxplanes, ch.f1 - ch.f0);
+    c->bchunks.push_back(ch);
+    f0 = ch.f1;
+  }
 }
 
 void plan(edt_ctx* c) {
@@ -202,6 +269,7 @@ void plan(edt_ctx* c) {
     const size_t want = g.freq_chunk > 0 ? size_t(g.freq_chunk) : (size_t(256) << 20) / plane;
     c->fchunk = int(std::max<size_t>(1, std::min<size_t>(c->nf, want)));
   }
+  plan_band(c, cmin);
   // twiddles e^{-2 pi i k / N}
   c->tw64.resize(N / 2);
   c->tw32.resize(N / 2);
@@ -281,6 +349,9 @@ void layout(edt_ctx* c) {
   take(c->r_rows, std::max<size_t>(R, 1) * sizeof(uint32_t));
   take(c->r_roff, (ns + 1) * sizeof(long long));
   take(c->r_roffmf, ns * (nf + 1) * sizeof(long long));
+  take(c->r_band, nf * sizeof(BandInfo));
+  take(c->r_bcol, std::max<size_t>(c->bcol.size(), 1) * sizeof(int2));
+  take(c->r_cpre, std::max<size_t>(c->cpre.size(), 1) * sizeof(long long));
   take(c->r_tw64, (N / 2) * sizeof(double2));
   take(c->r_tw32, (N / 2) * sizeof(float2));
   take(c->r_segm, std::max<size_t>(c->seg_m.size(), 1) * sizeof(int));
@@ -294,10 +365,15 @@ void layout(edt_ctx* c) {
   take(c->r_coef32, mixed ? nf * nk * c->nlayer * 8 * sizeof(float) : 0);
   take(c->r_g64, nf * nk * nz * sizeof(double2));
   take(c->r_g32, mixed ? nf * nk * size_t((c->nz + 1) & ~1) * sizeof(float2) : 0);
-  take(c->r_X, size_t(c->fchunk) * N * N * (mixed ? sizeof(float2) : sizeof(double2)));
+  // full planes of the forward model (and of the FP64 transform), or the band spectra of
+  // one chunk (Y, then Xc at a 256-byte boundary); one call uses one of the two
+  take(c->r_X, std::max(size_t(c->fchunk) * N * N * (mixed ? sizeof(float2) : sizeof(double2)),
+                        align_up(c->band_ymax * sizeof(float2), 256) + c->band_xmax * sizeof(float2)));
   take(c->r_Dst, nf * N * N * sizeof(double2));
   take(c->r_Vst, N * nz * sizeof(double));
-  take(c->r_rhs, std::max<size_t>(R, 1) * 2 * (mixed ? sizeof(float2) : sizeof(double2)));
+  // right-hand sides; the mixed path's tensor-core Gram bulk-copies whole stages of 32 rows,
+  // so its array (like the row metadata) carries 32 rows of padding
+  take(c->r_rhs, (mixed ? R + 32 : std::max<size_t>(R, 1)) * 2 * (mixed ? sizeof(float2) : sizeof(double2)));
   take(c->r_gent, mixed ? (R + 32) * sizeof(GramRow) : 0);
   take(c->r_gpart, mixed ? size_t(c->nslot) * TC_M * tc_cols(c->nz) * sizeof(float) : 0);
   take(c->r_G, ns * nz * nz * sizeof(double));
@@ -333,6 +409,12 @@ void bind(edt_ctx* c) {
   d.row_off = at<const long long*>(c, c->r_roff);
   d.row_off_mf = at<const long long*>(c, c->r_roffmf);
   d.fchunk = c->fchunk;
+  d.band = at<const BandInfo*>(c, c->r_band);
+  d.bcol = at<const int2*>(c, c->r_bcol);
+  d.cpre = at<const long long*>(c, c->r_cpre);
+  d.Yc = at<float2*>(c, c->r_X);
+  d.Xc = reinterpret_cast<float2*>(static_cast<char*>(c->ws) + c->r_X.off +
+                                   align_up(c->band_ymax * sizeof(float2), 256));
   d.tw64 = at<const double2*>(c, c->r_tw64);
   d.tw32 = at<const float2*>(c, c->r_tw32);
   d.seg_m = at<const int*>(c, c->r_segm);
@@ -385,6 +467,10 @@ void prof_mark(edt_ctx* c, int stage, cudaStream_t s) {
 int transform_rhs(edt_ctx* c, const void* D, int D_dtype, cudaStream_t s) {
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
+  if (c->band_mode) {
+    for (const BandChunk& ch : c->bchunks) EDT_TRY(launch_band_chunk(d, ch, D, D_dtype, s));
+    return EDT_OK;
+  }
   for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
     const int nfc = std::min(d.fchunk, d.nf - f0);
     if (mixed) {
@@ -477,6 +563,9 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRYI(upload(c, c->r_rows, c->rows));
   EDT_TRYI(upload(c, c->r_roff, c->row_off));
   EDT_TRYI(upload(c, c->r_roffmf, c->row_off_mf));
+  EDT_TRYI(upload(c, c->r_band, c->band));
+  if (!c->bcol.empty()) EDT_TRYI(upload(c, c->r_bcol, c->bcol));
+  if (!c->cpre.empty()) EDT_TRYI(upload(c, c->r_cpre, c->cpre));
   EDT_TRYI(upload(c, c->r_tw64, c->tw64));
   EDT_TRYI(upload(c, c->r_tw32, c->tw32));
   EDT_TRYI(upload(c, c->r_segm, c->seg_m));
@@ -488,10 +577,15 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRY(cudaMemset(at<void*>(c, c->r_flags), 0, c->r_flags.bytes));
   EDT_TRY(cudaMemset(at<void*>(c, c->r_x), 0, c->r_x.bytes));
   if (c->r_g32.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_g32), 0, c->r_g32.bytes));
-  if (c->r_gent.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_gent), 0, c->r_gent.bytes));
+  if (c->r_gent.bytes) {
+    EDT_TRY(cudaMemset(at<void*>(c, c->r_gent), 0, c->r_gent.bytes));
+    EDT_TRY(cudaMemset(at<void*>(c, c->r_rhs), 0, c->r_rhs.bytes));
+    if (!c->rows.empty()) EDT_TRY(launch_gent_static(c->dev, nullptr));
+  }
   EDT_TRY(prepare_fft(c->dev));
   EDT_TRY(prepare_chol(c->dev));
   if (c->cfg.precision == EDT_MIXED) EDT_TRY(prepare_gram_tc(c->dev));
+  if (c->band_mode) EDT_TRY(prepare_band(c->dev));
   EDT_TRY(cudaDeviceSynchronize());
   return EDT_OK;
 }
@@ -632,10 +726,14 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   // kernels launched by one edt_invert: green (3), per frequency chunk transform (2) and
   // right-hand sides (1), Gram (FP64: 1; mixed: tensor-core + reduce 2), batched Cholesky,
   // per refinement step (2), inverse (1)
-  const int nchunk = (c->nf + c->fchunk - 1) / c->fchunk;
-  o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + 3 * nchunk +
+  int tr_launches = 3 * ((c->nf + c->fchunk - 1) / c->fchunk);
+  if (c->band_mode) {
+    tr_launches = 0;
+    for (const BandChunk& ch : c->bchunks) tr_launches += 1 + (ch.nbcol > 0) + (ch.nrow > 0);
+  }
+  o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + tr_launches +
                            chol_launches(c->nz);
-  o->freq_chunk = c->fchunk;
+  o->freq_chunk = c->band_mode ? c->band_maxplanes : c->fchunk;
   o->gram_rows_padded = 0;
   for (long long n : c->seg_nrow) o->gram_rows_padded += (n + TC_KC - 1) / TC_KC * TC_KC;
   if (c->ws) {

@@ -21,12 +21,29 @@ __host__ __device__ inline int row_f(uint32_t r) { return int(r >> 16); }
 __host__ __device__ inline int row_p(uint32_t r) { return int(r & 0x7fffu); }
 __host__ __device__ inline int row_w2(uint32_t r) { return int((r >> 15) & 1u); }
 
-// Per-row operand metadata of the tensor-core Gram, written by the right-hand-side kernel:
-// element offsets of the two FP32 table rows, sqrt(weight), data rows times sqrt(weight).
+// Per-row operand metadata of the tensor-core Gram (fixed by the row plan, written once per
+// workspace): element offsets of the two FP32 table rows and sqrt(weight).  The data of a
+// row, (d_+, d_-) as a float4 in the right-hand-side array, are scaled by sw on use.
 struct GramRow {
   unsigned offp, offq;
   float sw, pad;
-  float2 dp, dm;
+};
+
+// Wavenumber band of one frequency kept by the evanescent cut: signed indices
+// [lo, lo + w), and the offsets (in complex elements, within the chunk buffers) of the
+// band-limited row spectrum Y_f [N][w] and transformed plane Xc_f [w][w].
+struct BandInfo {
+  int lo, w;
+  long long yoff, xoff;
+};
+
+// One chunk of frequency planes of the band-limited transform: planes [f0, f1), column-pass
+// blocks [bcol0, bcol0 + nbcol) of the block table, nrow rows of all subproblems at these
+// frequencies, ci = index of its row-count prefix array.
+struct BandChunk {
+  int f0, f1, bcol0, nbcol;
+  long long nrow;
+  int ci;
 };
 
 // Per-frequency constants: omega~ = omega + i eps, |s_f| with s_f = omega~^2 dz/dx, and
@@ -55,7 +72,13 @@ struct Dev {
   const uint32_t* rows;         // [rows_solved], grouped by m
   const long long* row_off;     // [nsub + 1]
   const long long* row_off_mf;  // [nsub][nf + 1]: first row of frequency f within subproblem m
-  int fchunk;                   // frequency planes transformed per chunk (L2-sized)
+  int fchunk;                   // frequency planes per chunk of the full-plane transform
+  // band-limited transform (mixed path)
+  const BandInfo* band;         // [nf]
+  const int2* bcol;             // column-pass block table: (f, first band column)
+  const long long* cpre;        // [nchunk][nsub + 1] chunk rows of subproblems < m
+  float2* Yc;                   // band row spectra of one chunk
+  float2* Xc;                   // band planes of one chunk
   const double2* tw64;          // [N/2] exp(-2 pi i k / N)
   const float2* tw32;           // [N/2]
   const int* seg_m;             // tensor-core Gram: per segment its m      [nseg]
@@ -98,6 +121,13 @@ template <typename T>
 cudaError_t launch_transform(const Dev& d, const void* D, int D_dtype, int f0, int nfc, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rhs(const Dev& d, int f0, int nfc, cudaStream_t s);
+// Tensor-core Gram row metadata from the row plan (once per workspace, mixed path).
+cudaError_t launch_gent_static(const Dev& d, cudaStream_t s);
+// Band-limited transform and right-hand sides of one chunk (FP32, mixed path, 32 <= N <= 1024).
+bool band_supported(int N);
+int band_cols_per_block();
+cudaError_t launch_band_chunk(const Dev& d, const BandChunk& ch, const void* D, int D_dtype, cudaStream_t s);
+cudaError_t prepare_band(const Dev& d);
 
 cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace

@@ -16,6 +16,7 @@
 // Vhat(k_p - k_q, z_j), then the inverse of the data transform.
 #include "edt_internal.h"
 #include "cplx.cuh"
+#include "wfft.cuh"
 
 #include <algorithm>
 
@@ -146,67 +147,6 @@ __global__ void fft_cols_kernel(Dev d, cplx_t<T>* X, int cpb, int sign, T scale)
     T2 v = s[c * ld + pd(r)];
     P[size_t(r) * N + c0 + c] = cmk(v.x * scale, v.y * scale);
   }
-}
-
-// ---- register-resident warp FFT (FP32, N = 32 * P) ----------------------------------
-// Four-step split of one length-N transform over a warp: lane b holds x[32 a + b] for
-// a < P; (1) a P-point DFT over a in registers (radix-2 DIT, bit-reversed register order
-// fixed at compile time), (2) the twiddle W_N^{b k1}, (3) a 32-point decimation-in-frequency
-// DFT across the lanes by shuffles.  Lane l then holds X[k1 + P * bitrev5(l)] in register
-// k1.  Each point passes through shared memory once (for the coalesced store) instead of
-// once per radix stage.
-__host__ __device__ constexpr int clog2(int n) { return n <= 1 ? 0 : 1 + clog2(n / 2); }
-__device__ __forceinline__ int rbits(int x, int bits) {     // bit reversal of the low `bits` bits
-  return bits == 0 ? 0 : int(__brev(unsigned(x)) >> (32 - bits));
-}
-
-__device__ __forceinline__ float2 tw_at(const float2* tw, int e, int N) {   // W_N^e, 0 <= e < N
-  if (e < (N >> 1)) return tw[e];
-  const float2 w = tw[e - (N >> 1)];
-  return make_float2(-w.x, -w.y);
-}
-
-template <int P>
-__device__ __forceinline__ void warp_fft(float2 (&r)[P], const float2* tw, int N, int sign, int lane) {
-  constexpr int LP = clog2(P);
-  float2 t[P];
-#pragma unroll
-  for (int a = 0; a < P; ++a) t[rbits(a, LP)] = r[a];
-#pragma unroll
-  for (int st = 0; st < LP; ++st) {                         // half-size h = 2^st
-#pragma unroll
-    for (int b = 0; b < P / 2; ++b) {
-      const int h = 1 << st;
-      const int jj = b & (h - 1), i0 = ((b >> st) << (st + 1)) + jj, i1 = i0 + h;
-      float2 w = tw[jj * (N >> (st + 1))];                  // W_{2h}^jj
-      if (sign > 0) w.y = -w.y;
-      const float2 u = t[i0], v = t[i1] * w;
-      t[i0] = u + v;
-      t[i1] = u - v;
-    }
-  }
-#pragma unroll
-  for (int k1 = 1; k1 < P; ++k1) {                          // W_N^{lane k1}
-    float2 w = tw_at(tw, (lane * k1) & (N - 1), N);
-    if (sign > 0) w.y = -w.y;
-    t[k1] = t[k1] * w;
-  }
-#pragma unroll
-  for (int sh = 4; sh >= 0; --sh) {                         // cross-lane DIF, span 2^sh
-    const int j = lane & ((1 << sh) - 1);
-    float2 w = tw[j * (N >> (sh + 1))];                     // W_{2^(sh+1)}^j
-    if (sign > 0) w.y = -w.y;
-    const bool upper = (lane >> sh) & 1;
-#pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) {
-      float2 u;
-      u.x = __shfl_xor_sync(0xffffffffu, t[k1].x, 1 << sh);
-      u.y = __shfl_xor_sync(0xffffffffu, t[k1].y, 1 << sh);
-      t[k1] = upper ? (u - t[k1]) * w : t[k1] + u;
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < P; ++a) r[a] = t[a];
 }
 
 constexpr int WR_WARPS = 8;   // rows per block in the row kernel

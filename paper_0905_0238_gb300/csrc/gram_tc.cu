@@ -45,7 +45,9 @@ __host__ __device__ inline int zrows_of(int nzp) {
 __host__ __device__ inline int cols_of(int nzp) { return (nzp + 16) + (nzp > TC_M ? nzp - TC_M + 16 : 0); }
 __host__ __device__ inline int stages_of(int passes) { return passes == 1 ? 4 : 3; }
 
-using RowEnt = GramRow;   // per-row operand metadata, built by the right-hand-side kernel
+// Row table of one stage in shared memory: TC_KC GramRow entries (offsets, sqrt weight),
+// then the rows' data (d_+, d_-) as TC_KC float4; both arrive by bulk copy.
+constexpr int TAB_BYTES = TC_KC * int(sizeof(GramRow) + sizeof(float4));
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -174,8 +176,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
   // carve shared memory: operand stages (1024-aligned), row tables, barriers
   uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
   unsigned char* ops = reinterpret_cast<unsigned char*>(base);
-  RowEnt* rowtab = reinterpret_cast<RowEnt*>(ops + size_t(STAGES) * NCOMP * stage_bytes);   // [2][TC_KC]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(rowtab + 2 * TC_KC);
+  unsigned char* rowtab = ops + size_t(STAGES) * NCOMP * stage_bytes;   // [2][TAB_BYTES]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rowtab + 2 * TAB_BYTES);
   uint64_t* full = bars;                   // [STAGES] producers -> MMA
   uint64_t* empty = bars + STAGES;         // [STAGES] MMA commit -> producers
   uint64_t* acc_full = bars + 2 * STAGES;  // MMA commit -> epilogue
@@ -292,9 +294,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
         const long long n = (d.seg_nrow[sl] + TC_KC - 1) / TC_KC;
         if (nst_next < n) {
           const int b = int(it_next & 1);
-          mbar_expect_tx(&tbar[b], TC_KC * sizeof(RowEnt));
-          bulk_g2s(rowtab + b * TC_KC, d.gent + d.seg_row0[sl] + nst_next * TC_KC,
-                   TC_KC * sizeof(RowEnt), &tbar[b]);
+          const long long r = d.seg_row0[sl] + nst_next * TC_KC;
+          unsigned char* tb = rowtab + b * TAB_BYTES;
+          mbar_expect_tx(&tbar[b], TAB_BYTES);
+          bulk_g2s(tb, d.gent + r, TC_KC * sizeof(GramRow), &tbar[b]);
+          bulk_g2s(tb + TC_KC * sizeof(GramRow), reinterpret_cast<const float4*>(d.rhs) + r,
+                   TC_KC * sizeof(float4), &tbar[b]);
           ++nst_next;
           return;
         }
@@ -317,7 +322,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
           if (!mbar_wait(&empty[s], unsigned(((it / STAGES) - 1) & 1), abort_flag)) { ok = false; break; }
         }
         if (!mbar_wait(&tbar[it & 1], unsigned((it >> 1) & 1), abort_flag)) { ok = false; break; }
-        RowEnt* rt = rowtab + (it & 1) * TC_KC;
+        const GramRow* rt = reinterpret_cast<const GramRow*>(rowtab + (it & 1) * TAB_BYTES);
+        const float4* rdat = reinterpret_cast<const float4*>(rt + TC_KC);
         const int nvalid = int(min((long long)TC_KC, nrow - st * TC_KC));   // rows past it: padding
         asm volatile("bar.sync 1, %0;" ::"n"(PRODUCER_WARPS * 32) : "memory");
         asm volatile("bar.sync 1, %0;" ::"n"(PRODUCER_WARPS * 32) : "memory");
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
             cc[h2] = u & 7;
 #pragma unroll
             for (int rr = 0; rr < 4; ++rr) {
-              const RowEnt e = rt[cc[h2] * 4 + rr];
+              const GramRow e = rt[cc[h2] * 4 + rr];
               // entries past the segment's last row belong to the next segment: padding here
               const bool ok2 = uv && zz[h2] < nz && (cc[h2] * 4 + rr) < nvalid;
               swv[h2][rr] = ok2 ? e.sw : 0.f;
@@ -379,7 +385,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
           float2 v[4];
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr) {
-            v[rr] = which ? rt[c * 4 + rr].dm : rt[c * 4 + rr].dp;
+            const float4 dd = rdat[c * 4 + rr];
+            const float sw = rt[c * 4 + rr].sw;
+            v[rr] = which ? make_float2(sw * dd.z, sw * dd.w) : make_float2(sw * dd.x, sw * dd.y);
             if (c * 4 + rr >= nvalid) v[rr] = make_float2(0.f, 0.f);
           }
           uint4 h;
@@ -472,7 +480,7 @@ int tc_cols(int nz) { return cols_of(nzp_of(nz)); }
 int tc_smem_bytes(int nz, int passes) {
   const int zr = zrows_of(nzp_of(nz));
   const int stages = stages_of(passes), ncomp = passes == 1 ? 1 : 2;
-  return 1024 + stages * ncomp * zr * ROWB + 2 * TC_KC * int(sizeof(RowEnt)) + (2 * stages + 5) * 8 + 16;
+  return 1024 + stages * ncomp * zr * ROWB + 2 * TAB_BYTES + (2 * stages + 5) * 8 + 16;
 }
 
 cudaError_t prepare_gram_tc(const Dev& d) {
