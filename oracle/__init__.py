@@ -16,6 +16,11 @@ Contents (each function cites the part of the paper it follows):
   (eq. M with the aperture sinc reduced to a delta), the Hermitian split (eq. Split), the
   damped least-squares solve by Householder QR, Hermitian completion (eq. VSym) and the
   inverse transform; plus the spectral Born forward model and its adjoint.
+* :mod:`oracle.edt3d`  the finite-aperture / 3D geometry (Section "A practical 3D
+  geometry" with the aperture sinc of eq. M kept as the window's Dirichlet kernel):
+  midpoint and half-offset-window transforms, the kernel K(k_m, w, z) of every recorded
+  half-offset, the split per pair {k_m, -k_m}, the same damped QR solve, forward model and
+  adjoint.
 * :mod:`oracle.brute`  independent brute-force references used only to pin the above:
   space-domain Born summation (eq. Born) and a finite-difference solve of the 1D
   Green's-function equation.

@@ -5,6 +5,9 @@
   with the Green's function G(x, z) assembled from g(k, z) by an explicit O(N^2) sum over
   wavenumbers.  It shares only g with :mod:`oracle.edt2d`; it does no Fourier transform of
   the data and never forms the decoupled kernel M.
+* :func:`green_periodic_2d` and :func:`born_space_domain_3d`: the same for the finite-
+  aperture / 3D geometry (eq. Born3D): G(y, z) by an explicit sum over the 2D wavenumber
+  grid and the data D(m, w) of every recorded half-offset summed over the whole grid.
 * :func:`green_finite_difference`: the 1D Green's-function equation
   g'' + (omega~^2/c0(z)^2 - k^2) g = -delta(z) solved by second-order finite volumes on a
   fine grid, with exact radiation conditions g' = +- i kappa g at the two ends of the
@@ -43,6 +46,39 @@ def born_space_domain(omega_t, g_kn_z, V, dx, dz):
             Gs = Gp[(i - xs) % N, :]                  # G(x - x_s, z)
             D[xs, xr] = np.sum(Gr * V * Gs)
     return omega_t ** 2 * dx * dz * D
+
+
+def green_periodic_2d(g_grid, nx, ny, dx, dy):
+    """G(y, z) = (1/(L_x L_y)) sum_a exp(i k_a.y) g(|k_a|, z) by direct summation.
+
+    ``g_grid`` is g on the wavenumber grid [ay][ax][...]; returns [yy][yx][...]."""
+    ax = np.arange(nx)
+    ay = np.arange(ny)
+    kx = 2 * np.pi * np.where(ax <= nx // 2, ax, ax - nx) / (nx * dx)
+    ky = 2 * np.pi * np.where(ay <= ny // 2, ay, ay - ny) / (ny * dy)
+    phx = np.exp(1j * np.outer(ax * dx, kx))          # [yx][ax]
+    phy = np.exp(1j * np.outer(ay * dy, ky))          # [yy][ay]
+    G = np.einsum("ya,xb,ab...->yx...", phy, phx, g_grid)
+    return G / (nx * dx * ny * dy)
+
+
+def born_space_domain_3d(omega_t, g_grid, V, nx, ny, dx, dy, dz, wx, wy):
+    """D(m, w) = omega~^2 dx dy dz sum_x sum_j G(m + w - x, z_j) V(x, z_j) G(x - m + w, z_j)
+
+    for every midpoint m = (mx, my) and half-offset w of the window [-wx/2, wx/2) x
+    [-wy/2, wy/2) (source at m - w, receiver at m + w).  ``g_grid`` [ay][ax][j] for one
+    frequency; V [y][x][j].  Returns [my][mx][wy][wx]."""
+    G = green_periodic_2d(g_grid, nx, ny, dx, dy)     # [yy][yx][j]
+    yy, xx = np.arange(ny), np.arange(nx)
+    D = np.zeros((ny, nx, wy, wx), dtype=np.complex128)
+    for my in range(ny):
+        for mx in range(nx):
+            for iy, wyv in enumerate(np.arange(wy) - wy // 2):
+                for ix, wxv in enumerate(np.arange(wx) - wx // 2):
+                    Gr = G[(my + wyv - yy) % ny][:, (mx + wxv - xx) % nx]      # G(m + w - x)
+                    Gs = G[(yy - my + wyv) % ny][:, (xx - mx + wxv) % nx]      # G(x - m + w)
+                    D[my, mx, iy, ix] = np.sum(Gr * V * Gs)
+    return omega_t ** 2 * dx * dy * dz * D
 
 
 def green_finite_difference(omega_t, k, layer_top, layer_vel, z_eval, h, z_above, z_below):

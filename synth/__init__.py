@@ -17,6 +17,10 @@ the surface z = 0, depth-dependent layered references) at the sizes used by this
                       complex Gaussian noise at 20 dB SNR per frequency.
   * ``paper_2d``      the paper's own acquisition (m, h every 50 m, 1-10 Hz) reduced to a
                       periodic line of 256 points, used as an extra paper-shaped size.
+
+Finite-aperture presets (``preset3d``): ``small_3d`` (16 x 16 midpoints, 4 x 4 half-offsets),
+``line_fa`` (a 64-point line with 16 half-offsets) and ``batched_3d`` (128 x 128 midpoints,
+16 x 16 half-offsets, 64 frequencies 4-50 Hz, 200 depths of 10 m, 20 random layers).
 """
 from .generators import *  # noqa: F401,F403
 from .generators import __all__  # noqa: F401

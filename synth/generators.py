@@ -16,7 +16,8 @@ __all__ = [
     "SEED_BASE", "Workload", "preset", "freqs_uniform", "layers_gradient_staircase",
     "layers_random", "layers_two", "velocity_at", "perturbation_blobs",
     "perturbation_random_field", "perturbation_square", "noise_snr", "noise_paper",
-    "random_data", "rng_for",
+    "random_data", "rng_for", "Workload3D", "preset3d", "perturbation_blobs_3d",
+    "perturbation_random_field_3d",
 ]
 
 SEED_BASE = 20260905
@@ -193,4 +194,96 @@ def preset(name: str) -> Workload:
         return Workload(name, nx=256, dx=50.0, freq_hz=freqs_uniform(10, 1.0, 10.0), eps=0.15,
                         nz=65, dz=50.0, z0=775.0, layer_top=tops, layer_vel=vel,
                         alpha=1e-3, cutoff=1.0, snr_db=None)
+    raise KeyError(name)
+
+
+@dataclass
+class Workload3D:
+    """A synthetic finite-aperture problem on an nx x ny periodic midpoint grid.
+
+    Data D[f][my][mx][wy][wx] are recorded at midpoint (mx, my) (grid units) for every
+    half-offset (wx, wy) of a wx_n x wy_n window of signed indices [-n/2, n/2): the source sits
+    at midpoint - half-offset and the receiver at midpoint + half-offset, so the offsets
+    are 2 (wx, wy) grid steps.  ny = 1 and wy_n = 1 give the 2D line survey with a finite
+    aperture.
+    """
+    name: str
+    nx: int
+    ny: int
+    dx: float
+    dy: float
+    wx: int
+    wy: int
+    freq_hz: np.ndarray
+    eps: float
+    nz: int
+    dz: float
+    z0: float
+    layer_top: np.ndarray
+    layer_vel: np.ndarray
+    alpha: float
+    cutoff: float
+    snr_db: Optional[float] = None
+
+    def summary(self) -> dict:
+        d = {k: v for k, v in asdict(self).items() if not isinstance(v, np.ndarray)}
+        d["nfreq"] = int(len(self.freq_hz))
+        d["nlayer"] = int(len(self.layer_top))
+        return d
+
+
+def perturbation_blobs_3d(rng, nx, ny, dx, dy, nz, dz, z0, layer_top, layer_vel, nblob=3,
+                          sigma=30.0, amp=0.05):
+    """V(x, y, z) [ny][nx][nz] for Gaussian blobs of relative velocity change +-amp."""
+    x = np.arange(nx) * dx
+    y = np.arange(ny) * dy
+    z = _depths(nz, dz, z0)
+    c0 = velocity_at(z, layer_top, layer_vel)
+    rel = np.zeros((ny, nx, nz))
+    for b in range(nblob):
+        xc = rng.uniform(0.15, 0.85) * nx * dx
+        yc = rng.uniform(0.15, 0.85) * ny * dy
+        zc = z0 + rng.uniform(0.2, 0.8) * nz * dz
+        sgn = 1.0 if b % 2 == 0 else -1.0
+        rel += sgn * amp * np.exp(-((y[:, None, None] - yc) ** 2 + (x[None, :, None] - xc) ** 2
+                                    + (z[None, None, :] - zc) ** 2) / (2.0 * sigma ** 2))
+    return _v_from_rel(rel, c0[None, None, :])
+
+
+def perturbation_random_field_3d(rng, nx, ny, dx, dy, nz, dz, z0, layer_top, layer_vel,
+                                 corr=40.0, rms=0.03):
+    """V(x, y, z) [ny][nx][nz] for a Gaussian-correlated random relative velocity field."""
+    white = rng.standard_normal((ny, nx, nz))
+    ky = 2 * np.pi * np.fft.fftfreq(ny, dy)
+    kx = 2 * np.pi * np.fft.fftfreq(nx, dx)
+    kz = 2 * np.pi * np.fft.fftfreq(nz, dz)
+    filt = np.exp(-0.25 * corr ** 2 * (ky[:, None, None] ** 2 + kx[None, :, None] ** 2
+                                       + kz[None, None, :] ** 2))
+    rel = np.real(np.fft.ifftn(np.fft.fftn(white) * filt))
+    rel *= rms / max(np.sqrt(np.mean(rel ** 2)), 1e-300)
+    z = _depths(nz, dz, z0)
+    c0 = velocity_at(z, layer_top, layer_vel)
+    return _v_from_rel(rel, c0[None, None, :])
+
+
+def preset3d(name: str) -> Workload3D:
+    """Finite-aperture workloads: ``small_3d`` (tests), ``line_fa`` (a 2D line with a
+    finite aperture) and ``batched_3d`` (128 x 128 midpoints at 12.5 m, 16 x 16 half-offsets
+    at 12.5 m (offsets every 25 m), 64 frequencies 4-50 Hz, 200 depths of 10 m, the 20-layer
+    generator)."""
+    if name == "small_3d":
+        tops, vel = layers_gradient_staircase(1500.0, 3000.0, 120.0, 10.0, sub=2)
+        return Workload3D(name, nx=16, ny=16, dx=10.0, dy=10.0, wx=4, wy=4,
+                          freq_hz=freqs_uniform(4, 10.0, 40.0), eps=0.15, nz=12, dz=10.0,
+                          z0=0.0, layer_top=tops, layer_vel=vel, alpha=1e-4, cutoff=1.0)
+    if name == "line_fa":
+        tops, vel = layers_gradient_staircase(1500.0, 3000.0, 320.0, 10.0, sub=2)
+        return Workload3D(name, nx=64, ny=1, dx=10.0, dy=10.0, wx=16, wy=1,
+                          freq_hz=freqs_uniform(12, 5.0, 40.0), eps=0.15, nz=32, dz=10.0,
+                          z0=0.0, layer_top=tops, layer_vel=vel, alpha=1e-4, cutoff=1.0)
+    if name == "batched_3d":
+        tops, vel = layers_random(rng_for(2), 20, 2048.0)
+        return Workload3D(name, nx=128, ny=128, dx=12.5, dy=12.5, wx=16, wy=16,
+                          freq_hz=freqs_uniform(64, 4.0, 50.0), eps=0.15, nz=200, dz=10.0,
+                          z0=0.0, layer_top=tops, layer_vel=vel, alpha=1e-2, cutoff=1.0)
     raise KeyError(name)
