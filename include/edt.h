@@ -29,6 +29,24 @@
  *   row (f, p) of m is kept iff |p'| c_min < (cutoff f) L and |q'| c_min < (cutoff f) L,
  *   q = (p - m) mod nx, evaluated in IEEE double exactly in that order.
  *
+ * Finite-aperture geometry (geometry = EDT_GEOM_WINDOW; Section "A practical 3D geometry"
+ * with the aperture sinc of eq. M kept): a periodic nx x ny midpoint grid (spacings dx, dy;
+ * ny = 1 is a 2D line), data recorded for every half-offset w of the window
+ * [-wx/2, wx/2) x [-wy/2, wy/2) grid steps, source at m - w and receiver at m + w:
+ *   - G(y, z) = (1/(L_x L_y)) sum_a exp(i k_a.y) g(|k_a|, z), k_a on the 2D grid;
+ *   - Born data D(f, m, w) = omega~^2 dx dy dz sum_j sum_x G(m + w - x, z_j) V(x, z_j) G(x - m + w, z_j);
+ *   - d(k_m; f, j) = sum_w exp(-2 pi i j.w/W) sum_m exp(-i k_m.m) D(f, m, w) (j, w signed);
+ *   - rows M(k_m; f, j, z) = sum_w exp(-2 pi i j.w/W) omega~^2 dx dy dz
+ *                            sum_y exp(i k_m.(y - w)) G(2w - y, z) G(y, z);
+ *   - M(-k_m) = M(k_m) row by row, so one real damped least-squares problem per pair
+ *     {k_m, -k_m} (eq. Split), lam = alpha trace(Gram);
+ *   - cut: row (f, j) of k_m is kept iff c_min^2 ((m_x'/L_x +- j_x/(wx dx))^2 +
+ *     (m_y'/L_y +- j_y/(wy dy))^2) < (2 cutoff f)^2 for both signs (cutoff <= 0: all rows);
+ *   - V(x, z) = (1/(nx ny)) sum_m Vhat(k_m, z) exp(i k_m.x), Vhat(-k_m) = conj Vhat(k_m).
+ *   Pairs are numbered my = 0..ny/2 and, within, mx = 0..nx-1 (mx = 0..nx/2 on the rows
+ *   my = 0 and my = ny/2, whose other half is the conjugate); layouts D
+ *   [nfreq][ny][nx][wy][wx], V [ny][nx][nz].  Mixed precision only.
+ *
  * Conventions for every call:
  *   - Pointers named *_dev are CUDA device pointers of the current device; *_host are
  *     host pointers (pinned memory recommended).  Complex data are interleaved (re, im).
@@ -67,6 +85,9 @@ extern "C" {
 #define EDT_MIXED  1   /* FP32 transforms, BF16 tensor-core Gram with FP32 accumulation,
                           FP64 Cholesky and FP64-accumulated iterative refinement          */
 
+#define EDT_GEOM_LINE    0   /* 2D line, every source/receiver pair recorded (default)  */
+#define EDT_GEOM_WINDOW  1   /* finite half-offset window on an nx x ny midpoint grid   */
+
 #define EDT_C64    0   /* complex64 data (interleaved float)   */
 #define EDT_C128   1   /* complex128 data (interleaved double) */
 #define EDT_F32    2   /* real float32 model                   */
@@ -103,12 +124,20 @@ typedef struct {
                                    the forward model (the spectrum buffer holds one
                                    chunk); 0 = automatic: as many planes as fit in
                                    256 MB.  Smaller chunks trade speed for workspace.   */
+  int geometry;                 /* EDT_GEOM_LINE (0) or EDT_GEOM_WINDOW (1)              */
+  int ny;                       /* window geometry: midpoints along y (1, or == nx with
+                                   nx <= 128); nx in 32..512 (ny == 1) or 32..128       */
+  double dy;                    /* window geometry: y spacing (> 0)                      */
+  int wx, wy;                   /* window geometry: half-offsets per axis (powers of
+                                   two, 1..16; wx <= nx, wy <= ny); the half-offset
+                                   spacing equals the midpoint spacing                  */
 } edt_config;
 
 /* Host-side statistics of a context; the device-side fields are refreshed by
  * edt_get_stats, which synchronises the context's last stream. */
 typedef struct {
-  int n_sub;                    /* subproblems solved: nx/2 + 1                          */
+  int n_sub;                    /* subproblems solved: nx/2 + 1 (line geometry) or the
+                                   number of pairs {k_m, -k_m} (window geometry)        */
   long long rows_total;         /* complex rows over all subproblems after the cut       */
   long long rows_solved;        /* rows actually processed (after folding)               */
   int rows_min, rows_max;       /* per-subproblem complex rows after the cut             */

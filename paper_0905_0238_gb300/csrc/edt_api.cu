@@ -46,6 +46,15 @@ struct edt_ctx {
   std::vector<long long> row_off;
   std::vector<long long> row_off_mf;   // [nsub][nf + 1]
   int fchunk = 1;
+  // window geometry
+  bool win = false;
+  int ny = 1, wx = 1, wy = 1, W = 1, nxy = 0;
+  std::vector<double> kval;            // [nk] |k| of each table row
+  std::vector<int> pair_m;             // [nsub] midpoint index of each pair
+  std::vector<int> fj_off;             // [nf * W + 1]
+  std::vector<int2> fj_ent;            // [rows] (midpoint index, row) grouped by (f, j)
+  std::vector<double2> cf;             // [nf] omega~^2 dx dy dz
+  long long rows_max_sub = 0;
   // band-limited transform of the mixed path
   bool band_mode = false;
   std::vector<BandInfo> band;
@@ -64,7 +73,7 @@ struct edt_ctx {
   // workspace
   size_t ws_bytes = 0;
   void* ws = nullptr;
-  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_tw64, r_tw32, r_segm, r_segr0,
+  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
       r_dinv, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
   Dev dev{};
@@ -79,7 +88,7 @@ struct edt_ctx {
   cudaStream_t g_s = nullptr;
   // profiling
   bool prof = false;
-  static constexpr int NSTAGE = 9;        // marks; NSTAGE - 1 timed stages
+  static constexpr int NSTAGE = 10;       // marks; NSTAGE - 1 timed stages
   std::vector<cudaEvent_t> ev;   // [calls][NSTAGE + 1]
   int prof_calls = 0;
   int prof_used[NSTAGE] = {};
@@ -89,9 +98,9 @@ namespace {
 
 constexpr int kProfCalls = 256;   // calls whose stage events are kept between reads
 
-const char* kStageNames[edt_ctx::NSTAGE] = {"green", "transform_rhs", "trace_reset", "gram",
-                                            "gram_reduce", "cholesky", "refine", "inverse",
-                                            "unused"};
+const char* kStageNames[edt_ctx::NSTAGE] = {"green", "kernel_rows", "transform_rhs", "trace_reset",
+                                            "gram", "gram_reduce", "cholesky", "refine",
+                                            "inverse", "unused"};
 
 int validate(const edt_config* c) {
   if (!c) return EDT_EINVAL;
@@ -120,7 +129,81 @@ int validate(const edt_config* c) {
   if (c->fold != 0 && c->fold != 1) return EDT_EINVAL;
   if (c->chol_df != 0 && c->chol_df != 1) return EDT_EINVAL;
   if (c->freq_chunk < 0) return EDT_EINVAL;
+  if (c->geometry != EDT_GEOM_LINE && c->geometry != EDT_GEOM_WINDOW) return EDT_EINVAL;
+  if (c->geometry == EDT_GEOM_WINDOW) {
+    if (c->ny < 1 || c->wx < 1 || c->wy < 1 || !(c->dy > 0)) return EDT_EINVAL;
+    if (c->precision != EDT_MIXED) return EDT_EUNSUPPORTED;
+    if (!fa_supported(c->nx, c->ny, c->wx, c->wy)) return EDT_EUNSUPPORTED;
+  }
   return EDT_OK;
+}
+
+// Window geometry: pairs {k_m, -k_m}, their rows (f, j) kept by the cut, the (f, j) lists
+// the assembly and data kernels walk, and |k| of every table row (the quadrant
+// |a_x| <= nx/2, |a_y| <= ny/2 of the wavenumber grid).  Same order and same IEEE double
+// cut test as the finite-aperture oracle.
+void plan_window(edt_ctx* c, double cmin) {
+  const edt_config& g = c->cfg;
+  const int nx = c->N, ny = c->ny, wx = c->wx, wy = c->wy, W = c->W, nf = c->nf;
+  const int hx = nx / 2 + 1, hy = ny / 2 + 1;
+  c->kval.resize(size_t(hx) * hy);
+  for (int qy = 0; qy < hy; ++qy)
+    for (int qx = 0; qx < hx; ++qx) {
+      const double kx = 2.0 * M_PI * qx / (nx * g.dx), ky = 2.0 * M_PI * qy / (ny * g.dy);
+      c->kval[size_t(qy) * hx + qx] = std::sqrt(kx * kx + ky * ky);
+    }
+  c->pair_m.clear();
+  for (int my = 0; my <= ny / 2; ++my) {
+    const bool half = my == 0 || 2 * my == ny;
+    for (int mx = 0; mx < (half ? nx / 2 + 1 : nx); ++mx) c->pair_m.push_back(my * nx + mx);
+  }
+  c->nsub = int(c->pair_m.size());
+  auto sgn = [](int n, int N) { return n <= N / 2 ? n : n - N; };
+  std::vector<double> lim(nf);
+  for (int f = 0; f < nf; ++f) lim[f] = (2.0 * g.cutoff * c->freq[f]) * (2.0 * g.cutoff * c->freq[f]);
+  std::vector<std::vector<int2>> lists(size_t(nf) * W);
+  c->rows.clear();
+  c->row_off.assign(c->nsub + 1, 0);
+  c->counts_cut.assign(c->nsub, 0);
+  for (int p = 0; p < c->nsub; ++p) {
+    c->row_off[p] = (long long)c->rows.size();
+    const int m = c->pair_m[p], my = m / nx, mx = m - my * nx;
+    const double mxs = double(sgn(mx, nx)) / (nx * g.dx), mys = double(sgn(my, ny)) / (ny * g.dy);
+    for (int f = 0; f < nf; ++f)
+      for (int jy = 0; jy < wy; ++jy)
+        for (int jx = 0; jx < wx; ++jx) {
+          bool keep = true;
+          if (g.cutoff > 0) {
+            const double jxs = double(jx - wx / 2) / (wx * g.dx), jys = double(jy - wy / 2) / (wy * g.dy);
+            for (int sg = 0; sg < 2 && keep; ++sg) {
+              const double vx = sg == 0 ? mxs + jxs : mxs + (-1.0) * jxs;
+              const double vy = sg == 0 ? mys + jys : mys + (-1.0) * jys;
+              keep = (cmin * cmin) * (vy * vy + vx * vx) < lim[f];
+            }
+          }
+          if (!keep) continue;
+          const int j = jy * wx + jx;
+          lists[size_t(f) * W + j].push_back(make_int2(m, int(c->rows.size())));
+          c->rows.push_back(uint32_t(f) << 16 | uint32_t(j));
+          c->counts_cut[p] += 1;
+        }
+  }
+  c->row_off[c->nsub] = (long long)c->rows.size();
+  c->fj_off.assign(size_t(nf) * W + 1, 0);
+  c->fj_ent.clear();
+  c->fj_ent.reserve(c->rows.size());
+  for (size_t i = 0; i < lists.size(); ++i) {
+    c->fj_off[i] = int(c->fj_ent.size());
+    c->fj_ent.insert(c->fj_ent.end(), lists[i].begin(), lists[i].end());
+  }
+  c->fj_off[lists.size()] = int(c->fj_ent.size());
+  c->cf.resize(nf);
+  for (int f = 0; f < nf; ++f) {
+    const double2 om = make_double2(c->fc[f].om_re, c->fc[f].om_im);
+    const double2 o2 = om * om;
+    const double sc = g.dx * g.dy * g.dz;
+    c->cf[f] = make_double2(o2.x * sc, o2.y * sc);
+  }
 }
 
 // Band-limited transform of the mixed path: per frequency the band of signed wavenumber
@@ -186,6 +269,13 @@ void plan(edt_ctx* c) {
   const edt_config& g = c->cfg;
   c->N = g.nx; c->nk = g.nx / 2 + 1; c->nz = g.nz; c->nf = g.nfreq; c->nsub = g.nx / 2 + 1;
   c->nlayer = g.nlayer;
+  c->win = g.geometry == EDT_GEOM_WINDOW;
+  c->ny = c->win ? g.ny : 1;
+  c->wx = c->win ? g.wx : 1;
+  c->wy = c->win ? g.wy : 1;
+  c->W = c->wx * c->wy;
+  c->nxy = c->N * c->ny;
+  if (c->win) c->nk = (g.nx / 2 + 1) * (c->ny / 2 + 1);
   const int N = c->N;
   const double L = double(N) * g.dx;
   // frequencies
@@ -223,9 +313,17 @@ void plan(edt_ctx* c) {
     c->z_off32[4 * j + 2] = o2h; c->z_off32[4 * j + 3] = float(o2 - double(o2h));
   }
   c->fc32.resize(c->nf);
-  for (int f = 0; f < c->nf; ++f) c->fc32[f] = float(std::sqrt(c->fc[f].s_abs));
-  // rows of every subproblem, in (f, p) order, evanescent cut and optional folding
+  // line geometry: the FP32 table carries sqrt|s_f| (rows are products of two table rows);
+  // window geometry: plain g (the assembly applies the prefactor)
+  for (int f = 0; f < c->nf; ++f) c->fc32[f] = c->win ? 1.f : float(std::sqrt(c->fc[f].s_abs));
   const double cmin = *std::min_element(c->vel.begin(), c->vel.end());
+  if (c->win) {
+    plan_window(c, cmin);
+    c->row_off_mf.assign(size_t(c->nsub) * (c->nf + 1), 0);
+    c->fchunk = 0;
+    c->band_mode = false;
+  } else {
+  // rows of every subproblem, in (f, p) order, evanescent cut and optional folding
   c->rows.clear();
   c->row_off.assign(c->nsub + 1, 0);
   c->row_off_mf.assign(size_t(c->nsub) * (c->nf + 1), 0);
@@ -270,6 +368,9 @@ void plan(edt_ctx* c) {
     c->fchunk = int(std::max<size_t>(1, std::min<size_t>(c->nf, want)));
   }
   plan_band(c, cmin);
+  }
+  c->rows_max_sub = 0;
+  for (int m = 0; m < c->nsub; ++m) c->rows_max_sub = std::max(c->rows_max_sub, c->row_off[m + 1] - c->row_off[m]);
   // twiddles e^{-2 pi i k / N}
   c->tw64.resize(N / 2);
   c->tw32.resize(N / 2);
@@ -352,6 +453,15 @@ void layout(edt_ctx* c) {
   take(c->r_band, nf * sizeof(BandInfo));
   take(c->r_bcol, std::max<size_t>(c->bcol.size(), 1) * sizeof(int2));
   take(c->r_cpre, std::max<size_t>(c->cpre.size(), 1) * sizeof(long long));
+  const size_t nxy = c->nxy, W = c->W, nzs = size_t((c->nz + 1) & ~1);
+  take(c->r_kval, std::max<size_t>(c->kval.size(), 1) * sizeof(double));
+  take(c->r_pairm, std::max<size_t>(c->pair_m.size(), 1) * sizeof(int));
+  take(c->r_fjoff, std::max<size_t>(c->fj_off.size(), 1) * sizeof(int));
+  take(c->r_fjent, std::max<size_t>(c->fj_ent.size(), 1) * sizeof(int2));
+  take(c->r_Gs, c->win ? nz * nxy * sizeof(float2) : 0);
+  take(c->r_U, c->win ? W * nz * nxy * sizeof(float2) : 0);
+  take(c->r_Dw, c->win ? nf * W * nxy * sizeof(float2) : 0);
+  take(c->r_A32, c->win ? (R + 1) * nzs * sizeof(float2) : 0);
   take(c->r_tw64, (N / 2) * sizeof(double2));
   take(c->r_tw32, (N / 2) * sizeof(float2));
   take(c->r_segm, std::max<size_t>(c->seg_m.size(), 1) * sizeof(int));
@@ -369,8 +479,8 @@ void layout(edt_ctx* c) {
   // one chunk (Y, then Xc at a 256-byte boundary); one call uses one of the two
   take(c->r_X, std::max(size_t(c->fchunk) * N * N * (mixed ? sizeof(float2) : sizeof(double2)),
                         align_up(c->band_ymax * sizeof(float2), 256) + c->band_xmax * sizeof(float2)));
-  take(c->r_Dst, nf * N * N * sizeof(double2));
-  take(c->r_Vst, N * nz * sizeof(double));
+  take(c->r_Dst, (c->win ? nf * nxy * W : nf * N * N) * sizeof(double2));
+  take(c->r_Vst, (c->win ? nxy : N) * nz * sizeof(double));
   // right-hand sides; the mixed path's tensor-core Gram bulk-copies whole stages of 32 rows,
   // so its array (like the row metadata) carries 32 rows of padding
   take(c->r_rhs, (mixed ? R + 32 : std::max<size_t>(R, 1)) * 2 * (mixed ? sizeof(float2) : sizeof(double2)));
@@ -383,7 +493,7 @@ void layout(edt_ctx* c) {
   take(c->r_x, ns * nz * 2 * sizeof(double));
   take(c->r_r, ns * nz * 2 * sizeof(double));
   take(c->r_vhat, ns * nz * sizeof(double2));
-  take(c->r_vfull, N * nz * sizeof(double2));
+  take(c->r_vfull, (c->win ? nxy : N) * nz * sizeof(double2));
   take(c->r_status, ns * sizeof(int));
   take(c->r_flags, 8 * sizeof(unsigned));
   c->ws_bytes = align_up(off, 256);
@@ -409,6 +519,18 @@ void bind(edt_ctx* c) {
   d.row_off = at<const long long*>(c, c->r_roff);
   d.row_off_mf = at<const long long*>(c, c->r_roffmf);
   d.fchunk = c->fchunk;
+  d.rows_max_sub = c->rows_max_sub;
+  d.geom = c->win ? EDT_GEOM_WINDOW : EDT_GEOM_LINE;
+  d.ny = c->ny; d.wx = c->wx; d.wy = c->wy; d.W = c->W; d.nxy = c->nxy; d.dy = c->cfg.dy;
+  d.kval = c->win ? at<const double*>(c, c->r_kval) : nullptr;
+  d.pair_m = at<const int*>(c, c->r_pairm);
+  d.fj_off = at<const int*>(c, c->r_fjoff);
+  d.fj_ent = at<const int2*>(c, c->r_fjent);
+  d.Gs = c->r_Gs.bytes ? at<float2*>(c, c->r_Gs) : nullptr;
+  d.U = c->r_U.bytes ? at<float2*>(c, c->r_U) : nullptr;
+  d.Dw = c->r_Dw.bytes ? at<float2*>(c, c->r_Dw) : nullptr;
+  d.A32 = c->r_A32.bytes ? at<float2*>(c, c->r_A32) : nullptr;
+  d.ones_row = (long long)c->rows.size();
   d.band = at<const BandInfo*>(c, c->r_band);
   d.bcol = at<const int2*>(c, c->r_bcol);
   d.cpre = at<const long long*>(c, c->r_cpre);
@@ -429,6 +551,7 @@ void bind(edt_ctx* c) {
   d.fc32_sqrt_s = at<const float*>(c, c->r_fc32);
   d.g64 = at<double2*>(c, c->r_g64);
   d.g32 = c->r_g32.bytes ? at<float2*>(c, c->r_g32) : nullptr;
+  d.rowtab32 = c->win ? d.A32 : d.g32;
   d.X = at<void*>(c, c->r_X);
   d.Dstage = at<void*>(c, c->r_Dst);
   d.Vstage = at<void*>(c, c->r_Vst);
@@ -467,6 +590,10 @@ void prof_mark(edt_ctx* c, int stage, cudaStream_t s) {
 int transform_rhs(edt_ctx* c, const void* D, int D_dtype, cudaStream_t s) {
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
+  if (c->win) {
+    EDT_TRY(launch_fa_data(d, D, D_dtype, s));
+    return EDT_OK;
+  }
   if (c->band_mode) {
     for (const BandChunk& ch : c->bchunks) EDT_TRY(launch_band_chunk(d, ch, D, D_dtype, s));
     return EDT_OK;
@@ -484,6 +611,13 @@ int transform_rhs(edt_ctx* c, const void* D, int D_dtype, cudaStream_t s) {
   return EDT_OK;
 }
 
+// Window geometry: the assembled kernel rows of every frequency into the row table.
+int kernel_rows(edt_ctx* c, cudaStream_t s) {
+  if (!c->win) return EDT_OK;
+  for (int f = 0; f < c->nf; ++f) EDT_TRY(launch_fa_rows(c->dev, f, c->cf[f], s));
+  return EDT_OK;
+}
+
 int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cudaStream_t s) {
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
@@ -491,21 +625,23 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_mark(c, 0, s);
   EDT_TRY(launch_green(d, s, mixed ? GREEN_G32 : GREEN_G64));
   prof_mark(c, 1, s);
-  EDT_TRYI(transform_rhs(c, D, D_dtype, s));
+  EDT_TRYI(kernel_rows(c, s));
   prof_mark(c, 2, s);
-  if (mixed) EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
+  EDT_TRYI(transform_rhs(c, D, D_dtype, s));
   prof_mark(c, 3, s);
+  if (mixed) EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
+  prof_mark(c, 4, s);
   if (mixed) {
     EDT_TRY(launch_gram_tc(d, s));
-    prof_mark(c, 4, s);
+    prof_mark(c, 5, s);
     EDT_TRY(launch_gram_reduce(d, s));
   } else {
     EDT_TRY(launch_gram_f64(d, s));
-    prof_mark(c, 4, s);
+    prof_mark(c, 5, s);
   }
-  prof_mark(c, 5, s);
-  EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
   prof_mark(c, 6, s);
+  EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
+  prof_mark(c, 7, s);
   if (mixed) {
     for (int it = 0; it < c->cfg.refine; ++it) {
       EDT_TRY(cudaMemsetAsync(d.r, 0, sizeof(double) * d.nsub * d.nz * 2, s));
@@ -513,9 +649,10 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
       EDT_TRY(launch_refine_update(d, s));
     }
   }
-  prof_mark(c, 7, s);
-  EDT_TRY(launch_inverse(d, V, V_dtype, s));
   prof_mark(c, 8, s);
+  if (c->win) EDT_TRY(launch_fa_inverse(d, V, V_dtype, s));
+  else EDT_TRY(launch_inverse(d, V, V_dtype, s));
+  prof_mark(c, 9, s);
   if (c->prof && c->prof_calls < kProfCalls) c->prof_calls++;
   return EDT_OK;
 }
@@ -566,6 +703,10 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRYI(upload(c, c->r_band, c->band));
   if (!c->bcol.empty()) EDT_TRYI(upload(c, c->r_bcol, c->bcol));
   if (!c->cpre.empty()) EDT_TRYI(upload(c, c->r_cpre, c->cpre));
+  EDT_TRYI(upload(c, c->r_kval, c->kval));
+  EDT_TRYI(upload(c, c->r_pairm, c->pair_m));
+  EDT_TRYI(upload(c, c->r_fjoff, c->fj_off));
+  EDT_TRYI(upload(c, c->r_fjent, c->fj_ent));
   EDT_TRYI(upload(c, c->r_tw64, c->tw64));
   EDT_TRYI(upload(c, c->r_tw32, c->tw32));
   EDT_TRYI(upload(c, c->r_segm, c->seg_m));
@@ -580,12 +721,18 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   if (c->r_gent.bytes) {
     EDT_TRY(cudaMemset(at<void*>(c, c->r_gent), 0, c->r_gent.bytes));
     EDT_TRY(cudaMemset(at<void*>(c, c->r_rhs), 0, c->r_rhs.bytes));
-    if (!c->rows.empty()) EDT_TRY(launch_gent_static(c->dev, nullptr));
+    if (c->win) {
+      EDT_TRY(cudaMemset(at<void*>(c, c->r_A32), 0, c->r_A32.bytes));
+      EDT_TRY(launch_fa_setup(c->dev, (long long)c->rows.size(), nullptr));
+    } else if (!c->rows.empty()) {
+      EDT_TRY(launch_gent_static(c->dev, nullptr));
+    }
   }
   EDT_TRY(prepare_fft(c->dev));
   EDT_TRY(prepare_chol(c->dev));
   if (c->cfg.precision == EDT_MIXED) EDT_TRY(prepare_gram_tc(c->dev));
   if (c->band_mode) EDT_TRY(prepare_band(c->dev));
+  if (c->win) EDT_TRY(prepare_fa(c->dev));
   EDT_TRY(cudaDeviceSynchronize());
   return EDT_OK;
 }
@@ -641,8 +788,9 @@ int edt_invert_host(edt_ctx* c, const void* D_host, int D_dtype, void* V_host, i
   if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
   if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t dbytes = size_t(c->nf) * c->N * c->N * (D_dtype == EDT_C64 ? 8 : 16);
-  const size_t vbytes = size_t(c->N) * c->nz * (V_dtype == EDT_F32 ? 4 : 8);
+  const size_t dbytes = size_t(c->nf) * (c->win ? size_t(c->nxy) * c->W : size_t(c->N) * c->N) *
+                        (D_dtype == EDT_C64 ? 8 : 16);
+  const size_t vbytes = size_t(c->win ? c->nxy : c->N) * c->nz * (V_dtype == EDT_F32 ? 4 : 8);
   EDT_TRY(cudaMemcpyAsync(c->dev.Dstage, D_host, dbytes, cudaMemcpyHostToDevice, s));
   int r = run_invert(c, c->dev.Dstage, D_dtype, c->dev.Vstage, V_dtype, s);
   if (r != EDT_OK) return r;
@@ -655,6 +803,7 @@ int edt_forward(edt_ctx* c, const void* V, int V_dtype, void* D, int D_dtype, vo
   if (!c->ws) return EDT_ENOMEM_WS;
   if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
   if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
+  if (c->win) return EDT_EUNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c->last_stream = s;
   EDT_TRY(launch_green(c->dev, s, GREEN_G64));
@@ -689,6 +838,7 @@ int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr,
   const bool mixed = c->cfg.precision == EDT_MIXED;
   c->last_stream = s;
   EDT_TRY(launch_green(d, s, mixed ? GREEN_G32 : GREEN_G64));
+  EDT_TRYI(kernel_rows(c, s));
   EDT_TRYI(transform_rhs(c, D, D_dtype, s));
   if (mixed) {
     EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
@@ -726,13 +876,19 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   // kernels launched by one edt_invert: green (3), per frequency chunk transform (2) and
   // right-hand sides (1), Gram (FP64: 1; mixed: tensor-core + reduce 2), batched Cholesky,
   // per refinement step (2), inverse (1)
-  int tr_launches = 3 * ((c->nf + c->fchunk - 1) / c->fchunk);
+  int tr_launches = c->fchunk > 0 ? 3 * ((c->nf + c->fchunk - 1) / c->fchunk) : 0;
   if (c->band_mode) {
     tr_launches = 0;
     for (const BandChunk& ch : c->bchunks) tr_launches += 1 + (ch.nbcol > 0) + (ch.nrow > 0);
   }
   o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + tr_launches +
                            chol_launches(c->nz);
+  if (c->win) {
+    // green (3), per frequency rows (3), data (2), Gram (2), Cholesky, refinement (2 per
+    // step), inverse (completion, FP64 row and column transforms, output: 3 or 4)
+    o->launches_per_invert = 3 + 3 * c->nf + 2 + 2 + chol_launches(c->nz) + 2 * c->cfg.refine +
+                             (c->ny > 1 ? 4 : 3);
+  }
   o->freq_chunk = c->band_mode ? c->band_maxplanes : c->fchunk;
   o->gram_rows_padded = 0;
   for (long long n : c->seg_nrow) o->gram_rows_padded += (n + TC_KC - 1) / TC_KC * TC_KC;

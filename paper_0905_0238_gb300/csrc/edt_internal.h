@@ -22,8 +22,11 @@ __host__ __device__ inline int row_p(uint32_t r) { return int(r & 0x7fffu); }
 __host__ __device__ inline int row_w2(uint32_t r) { return int((r >> 15) & 1u); }
 
 // Per-row operand metadata of the tensor-core Gram (fixed by the row plan, written once per
-// workspace): element offsets of the two FP32 table rows and sqrt(weight).  The data of a
-// row, (d_+, d_-) as a float4 in the right-hand-side array, are scaled by sw on use.
+// workspace): the two rows p, q of the FP32 row table whose elementwise product is the
+// kernel row (row r of the table starts at element r * nzs), and sqrt(weight).  The data
+// of a row, (d_+, d_-) as a float4 in the right-hand-side array, are scaled by sw on use.
+// Line geometry: the table is sqrt|s_f| g and the rows are g(|k_p|), g(|k_q|); window
+// geometry: the table holds the assembled kernel rows and q is a row of ones.
 struct GramRow {
   unsigned offp, offq;
   float sw, pad;
@@ -60,6 +63,10 @@ struct Dev {
   int N, nk, nz, nf, nsub, nlayer;
   int nzs;                      // row stride of the FP32 table: nz rounded up to even
   int precision, passes, fold, chol_df;
+  // window geometry (geom == EDT_GEOM_WINDOW): ny x nx midpoints (nx == N), wy x wx
+  // half-offsets, W = wx * wy, nxy = nx * ny
+  int geom, ny, wx, wy, W, nxy;
+  double dy;
   double alpha, dx, dz;
   // constant tables
   const FreqConst* fc;          // [nf]
@@ -71,6 +78,7 @@ struct Dev {
   const float* fc32_sqrt_s;     // [nf] sqrt|s_f| as float
   const uint32_t* rows;         // [rows_solved], grouped by m
   const long long* row_off;     // [nsub + 1]
+  long long rows_max_sub;       // most rows of any subproblem
   const long long* row_off_mf;  // [nsub][nf + 1]: first row of frequency f within subproblem m
   int fchunk;                   // frequency planes per chunk of the full-plane transform
   // band-limited transform (mixed path)
@@ -81,6 +89,17 @@ struct Dev {
   float2* Xc;                   // band planes of one chunk
   const double2* tw64;          // [N/2] exp(-2 pi i k / N)
   const float2* tw32;           // [N/2]
+  const double* kval;           // [nk] |k| of each table row (window geometry), else null
+  const float2* rowtab32;       // row table the tensor-core Gram and the refinement read
+  // window geometry
+  const int* pair_m;            // [nsub] midpoint index my * nx + mx of each pair's k_m
+  const int* fj_off;            // [nf * W + 1] entry ranges of the (f, j) lists
+  const int2* fj_ent;           // (midpoint index, row) of every row, grouped by (f, j)
+  float2* Gs;                   // [nz][ny][nx] G(y, z) of one frequency
+  float2* U;                    // [W][nz][ny][nx] window products of one frequency
+  float2* Dw;                   // [nf][W][ny][nx] window-transformed data
+  float2* A32;                  // [rows + 1][nzs] kernel rows, then a row of ones
+  long long ones_row;           // index of the ones row in A32
   const int* seg_m;             // tensor-core Gram: per segment its m      [nseg]
   const long long* seg_row0;    //                   first row, row count    [nseg], [nseg]
   const long long* seg_nrow;
@@ -128,6 +147,17 @@ bool band_supported(int N);
 int band_cols_per_block();
 cudaError_t launch_band_chunk(const Dev& d, const BandChunk& ch, const void* D, int D_dtype, cudaStream_t s);
 cudaError_t prepare_band(const Dev& d);
+
+// Window geometry (csrc/fa.cu): kernel rows of frequency f into A32, data transform and
+// right-hand sides, the inverse transform to V[ny][nx][nz]; supported grids and windows.
+bool fa_supported(int nx, int ny, int wx, int wy);
+cudaError_t launch_fa_rows(const Dev& d, int f, double2 cf, cudaStream_t s);
+cudaError_t launch_fa_data(const Dev& d, const void* D, int D_dtype, cudaStream_t s);
+cudaError_t launch_fa_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s);
+cudaError_t launch_fa_setup(const Dev& d, long long nrows, cudaStream_t s);
+cudaError_t prepare_fa(const Dev& d);
+// FP64 2D transform of [planes][ny][N] in place (ny == N or 1), sign +-1, times scale.
+cudaError_t fft2_f64(const Dev& d, double2* X, int planes, int ny, int sign, double scale, cudaStream_t s);
 
 cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace

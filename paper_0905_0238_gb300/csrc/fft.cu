@@ -279,6 +279,16 @@ cudaError_t cols_fft(const Dev& d, cplx_t<T>* X, int planes, int sign, T scale, 
   return cudaGetLastError();
 }
 
+}  // namespace
+
+cudaError_t fft2_f64(const Dev& d, double2* X, int planes, int ny, int sign, double scale, cudaStream_t s) {
+  cudaError_t e = rows_fft<double>(d, X, EDT_C128, X, EDT_C128, (long long)planes * ny, sign, scale, s);
+  if (e != cudaSuccess || ny == 1) return e;
+  return cols_fft<double>(d, X, planes, sign, 1.0, s);
+}
+
+namespace {
+
 // ---- inverse transform ------------------------------------------------------------------
 constexpr int INV_ZT = 8;
 

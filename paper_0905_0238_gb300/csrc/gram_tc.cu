@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     const int ptid = threadIdx.x;                 // 0..255
     const int nunits = (nzp / 32) * 8;            // (32-depth group, 16-byte K chunk)
     const int N = d.N, msk = N - 1;
-    const float2* g32 = d.g32;
+    const float2* g32 = d.rowtab32;
+    const size_t nzs = size_t(d.nzs);
     long long it = 0;
     bool ok = true;
     // The row table of each stage (32 GramRow entries, 1 KB) arrives by a bulk copy issued
@@ -349,8 +350,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
               // entries past the segment's last row belong to the next segment: padding here
               const bool ok2 = uv && zz[h2] < nz && (cc[h2] * 4 + rr) < nvalid;
               swv[h2][rr] = ok2 ? e.sw : 0.f;
-              gpv[h2][rr] = ok2 ? __ldg(g32 + e.offp + zz[h2]) : make_float2(0.f, 0.f);
-              gqv[h2][rr] = ok2 ? __ldg(g32 + e.offq + zz[h2]) : make_float2(0.f, 0.f);
+              gpv[h2][rr] = ok2 ? __ldg(g32 + size_t(e.offp) * nzs + zz[h2]) : make_float2(0.f, 0.f);
+              gqv[h2][rr] = ok2 ? __ldg(g32 + size_t(e.offq) * nzs + zz[h2]) : make_float2(0.f, 0.f);
             }
           }
 #pragma unroll

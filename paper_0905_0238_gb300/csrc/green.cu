@@ -53,7 +53,7 @@ __global__ void green_layer_kernel(Dev d, int want_steps) {
   const int n = int(fn % d.nk), f = int(fn / d.nk);
   const FreqConst fc = d.fc[f];
   const double L = double(d.N) * d.dx;
-  const double k = 2.0 * M_PI * double(n) / L;
+  const double k = d.kval ? d.kval[n] : 2.0 * M_PI * double(n) / L;
   const double2 om = cmk(fc.om_re, fc.om_im);
   const double2 om2 = om * om;
   const double inv_c2 = 1.0 / (d.layer_vel[j] * d.layer_vel[j]);

@@ -14,14 +14,18 @@
 #include "edt_internal.h"
 #include "cplx.cuh"
 
+#include <algorithm>
+
 namespace edt {
 
 namespace {
 
 constexpr int RF_WARPS = 4, RF_ROWS_PER_WARP = 32;
 
-// Z4: float4 loads per lane per table row, i.e. nz <= 64 * Z4 (two depths per float4)
-template <int Z4>
+// Z4: float4 loads per lane per table row, i.e. nz <= 64 * Z4 (two depths per float4).
+// FA: window geometry, where row ri of the subproblem is row ri of the assembled kernel
+// table and the second factor is the table's row of ones (all weights 1).
+template <int Z4, bool FA>
 __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
   constexpr int ZL = 64 * Z4;
   __shared__ float xs[2][ZL];
@@ -50,12 +54,22 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
     long long ri[2] = {r0 + i, r0 + (two ? i + 1 : i)};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const uint32_t row = d.rows[ri[h]];
-      const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
-      const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
-      const float4* gp = reinterpret_cast<const float4*>(d.g32 + (size_t(f) * d.nk + np) * d.nzs);
-      const float4* gq = reinterpret_cast<const float4*>(d.g32 + (size_t(f) * d.nk + nq) * d.nzs);
-      wv[h] = (h == 1 && !two) ? 0.f : (row_w2(row) ? 2.f : 1.f);
+      size_t rp, rq;
+      float w1 = 1.f;
+      if (FA) {
+        rp = size_t(ri[h]);
+        rq = size_t(d.ones_row);
+      } else {
+        const uint32_t row = d.rows[ri[h]];
+        const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
+        const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
+        rp = size_t(f) * d.nk + np;
+        rq = size_t(f) * d.nk + nq;
+        w1 = row_w2(row) ? 2.f : 1.f;
+      }
+      const float4* gp = reinterpret_cast<const float4*>(d.rowtab32 + rp * d.nzs);
+      const float4* gq = reinterpret_cast<const float4*>(d.rowtab32 + rq * d.nzs);
+      wv[h] = (h == 1 && !two) ? 0.f : w1;
 #pragma unroll
       for (int t = 0; t < Z4; ++t) {
         const int z = 2 * lane + 64 * t;
@@ -119,10 +133,11 @@ cudaError_t launch_refine(const Dev& d, cudaStream_t s) {
   // element of an odd nz is zero and meets x = 0
   const long long rows_per_cta = RF_WARPS * RF_ROWS_PER_WARP;
   const int nz_even = d.nzs;
-  dim3 g(unsigned((d.nf * (long long)d.N + rows_per_cta - 1) / rows_per_cta), d.nsub);
-  if (nz_even <= 64) refine_kernel<1><<<g, RF_WARPS * 32, 0, s>>>(d);
-  else if (nz_even <= 128) refine_kernel<2><<<g, RF_WARPS * 32, 0, s>>>(d);
-  else refine_kernel<4><<<g, RF_WARPS * 32, 0, s>>>(d);
+  dim3 g(unsigned((std::max(d.rows_max_sub, 1LL) + rows_per_cta - 1) / rows_per_cta), d.nsub);
+  const bool fa = d.geom == EDT_GEOM_WINDOW;
+  if (nz_even <= 64) fa ? refine_kernel<1, true><<<g, RF_WARPS * 32, 0, s>>>(d) : refine_kernel<1, false><<<g, RF_WARPS * 32, 0, s>>>(d);
+  else if (nz_even <= 128) fa ? refine_kernel<2, true><<<g, RF_WARPS * 32, 0, s>>>(d) : refine_kernel<2, false><<<g, RF_WARPS * 32, 0, s>>>(d);
+  else fa ? refine_kernel<4, true><<<g, RF_WARPS * 32, 0, s>>>(d) : refine_kernel<4, false><<<g, RF_WARPS * 32, 0, s>>>(d);
   return cudaGetLastError();
 }
 

@@ -48,7 +48,8 @@ __global__ void rhs_kernel(Dev d, int f0, int f1) {
 }
 
 // Operand metadata of the tensor-core Gram: the FP32 table rows g(|k_p|), g(|k_q|) of each
-// row and sqrt of its weight (weight-2 rows enter the Gram scaled by sqrt 2).
+// row (table row indices) and sqrt of its weight (weight-2 rows enter the Gram scaled by
+// sqrt 2).
 __global__ void gent_static_kernel(Dev d) {
   const int m = blockIdx.y;
   const long long r0 = d.row_off[m], nr = d.row_off[m + 1] - r0;
@@ -59,8 +60,8 @@ __global__ void gent_static_kernel(Dev d) {
   const int f = row_f(row), p = row_p(row), q = (p - m) & (N - 1);
   const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
   GramRow g;
-  g.offp = unsigned((size_t(f) * d.nk + np) * d.nzs);
-  g.offq = unsigned((size_t(f) * d.nk + nq) * d.nzs);
+  g.offp = unsigned(size_t(f) * d.nk + np);
+  g.offq = unsigned(size_t(f) * d.nk + nq);
   g.sw = row_w2(row) ? 1.41421356237309515f : 1.0f;
   g.pad = 0.f;
   d.gent[r0 + i] = g;
@@ -69,8 +70,7 @@ __global__ void gent_static_kernel(Dev d) {
 }  // namespace
 
 cudaError_t launch_gent_static(const Dev& d, cudaStream_t s) {
-  // a subproblem has at most nf * N rows
-  dim3 g(unsigned((d.nf * (long long)d.N + 255) / 256), d.nsub);
+  dim3 g(unsigned((d.rows_max_sub + 255) / 256), d.nsub);
   gent_static_kernel<<<g, 256, 0, s>>>(d);
   return cudaGetLastError();
 }

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libedt.so")
 EDT_OK, EDT_EINVAL, EDT_ENOMEM_WS, EDT_ENOTPD = 0, -1, -2, -3
 EDT_ETIMEOUT, EDT_ENONFINITE, EDT_ECUDA, EDT_EUNSUPPORTED = -4, -5, -6, -7
 EDT_FP64, EDT_MIXED = 0, 1
+EDT_GEOM_LINE, EDT_GEOM_WINDOW = 0, 1
 EDT_C64, EDT_C128, EDT_F32, EDT_F64 = 0, 1, 2, 3
 
 
@@ -32,6 +33,7 @@ class edt_config(C.Structure):
         ("precision", C.c_int), ("passes", C.c_int), ("refine", C.c_int),
         ("alpha", C.c_double), ("cutoff", C.c_double), ("fold", C.c_int),
         ("chol_df", C.c_int), ("freq_chunk", C.c_int),
+        ("geometry", C.c_int), ("ny", C.c_int), ("dy", C.c_double), ("wx", C.c_int), ("wy", C.c_int),
     ]
 
 
@@ -207,14 +209,34 @@ class Config:
     fold: int = 1
     chol_df: int = 0
     freq_chunk: int = 0
+    geometry: int = EDT_GEOM_LINE
+    ny: int = 1
+    dy: float = 1.0
+    wx: int = 1
+    wy: int = 1
 
     @classmethod
     def from_workload(cls, wl, **kw):
         base = dict(nx=wl.nx, dx=wl.dx, nz=wl.nz, dz=wl.dz, z0=wl.z0, freq_hz=wl.freq_hz,
                     eps=wl.eps, layer_top=wl.layer_top, layer_vel=wl.layer_vel,
                     alpha=wl.alpha, cutoff=wl.cutoff)
+        if hasattr(wl, "wx"):          # finite-aperture workload
+            base.update(geometry=EDT_GEOM_WINDOW, ny=wl.ny, dy=wl.dy, wx=wl.wx, wy=wl.wy,
+                        precision=EDT_MIXED, fold=0)
         base.update(kw)
         return cls(**base)
+
+    @property
+    def window(self) -> bool:
+        return self.geometry == EDT_GEOM_WINDOW
+
+    def data_shape(self, nfreq):
+        if self.window:
+            return (nfreq, self.ny, self.nx, self.wy, self.wx)
+        return (nfreq, self.nx, self.nx)
+
+    def model_shape(self):
+        return (self.ny, self.nx, self.nz) if self.window else (self.nx, self.nz)
 
 
 class Solver:
@@ -234,13 +256,14 @@ class Solver:
             nlayer=len(self._top), layer_top_m=self._top.ctypes.data_as(dp),
             layer_vel_mps=self._vel.ctypes.data_as(dp), precision=cfg.precision,
             passes=cfg.passes, refine=cfg.refine, alpha=cfg.alpha, cutoff=cfg.cutoff,
-            fold=cfg.fold, chol_df=cfg.chol_df, freq_chunk=cfg.freq_chunk)
+            fold=cfg.fold, chol_df=cfg.chol_df, freq_chunk=cfg.freq_chunk,
+            geometry=cfg.geometry, ny=cfg.ny, dy=cfg.dy, wx=cfg.wx, wy=cfg.wy)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.ctx = None
         self.ctx, self.ws_bytes = edt_create(c)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
         edt_set_workspace(self.ctx, self.workspace.data_ptr(), self.ws_bytes)
-        self.nsub = cfg.nx // 2 + 1
+        self.nsub = int(edt_get_stats(self.ctx).n_sub)
 
     def __del__(self):
         if getattr(self, "ctx", None):
@@ -263,10 +286,10 @@ class Solver:
     def invert(self, D, out=None, out_dtype=None):
         torch = self._torch
         nf = len(self._freq)
-        if not (D.is_cuda and D.is_contiguous()) or tuple(D.shape) != (nf, self.cfg.nx, self.cfg.nx):
-            raise ValueError("D must be a contiguous CUDA tensor of shape (nfreq, nx, nx)")
+        if not (D.is_cuda and D.is_contiguous()) or tuple(D.shape) != self.cfg.data_shape(nf):
+            raise ValueError(f"D must be a contiguous CUDA tensor of shape {self.cfg.data_shape(nf)}")
         if out is None:
-            out = torch.empty((self.cfg.nx, self.cfg.nz), device=self.device,
+            out = torch.empty(self.cfg.model_shape(), device=self.device,
                               dtype=out_dtype or torch.float64)
         edt_invert(self.ctx, D.data_ptr(), self._cdtype(D), out.data_ptr(), self._rdtype(out),
                    self._stream())
