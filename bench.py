@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_3d"],
+                    help="batched_3d: the finite-aperture 3D workload (a separate line, not the "
+                         "headline)")
     return ap.parse_args()
 
 
@@ -81,12 +84,53 @@ def job_throughput(world: int, units_per_step: int, steps: int, ms_total: float)
 
 
 # ------------------------------------------------------------------ CPU oracle timing
+def cpu_child_window(spec):
+    """Oracle sample of the batched 3D workload: kernel rows of a few (frequency, pair)
+    combinations by the wavenumber-sum route and one damped QR solve, extrapolated to the
+    cost of one pair (all frequencies) per two subproblems."""
+    import numpy as np
+    import synth
+    from oracle import edt3d
+    wl = synth.preset3d("batched_3d")
+    reps = edt3d.pair_representatives(wl)
+    nf = len(wl.freq_hz)
+    m = reps[spec["pair"]]
+    t_rows = []
+    for f in spec["freqs"]:
+        a = time.perf_counter()
+        edt3d.window_dft(edt3d.kernel_offsets_spectral(wl, f, m), axes=(0, 1))
+        t_rows.append(time.perf_counter() - a)
+    rng = synth.rng_for(2, salt=77)
+    keep = edt3d.kept_mask(wl, m)
+    R = int(keep.sum())
+    A = rng.standard_normal((R, wl.nz)) + 1j * rng.standard_normal((R, wl.nz))
+    d = rng.standard_normal(R) + 1j * rng.standard_normal(R)
+    a = time.perf_counter()
+    Ahat = np.vstack([A.real, A.imag])
+    from oracle.edt2d import damped_lstsq
+    damped_lstsq(Ahat, np.stack([np.concatenate([d.real, d.imag])] * 2, axis=1),
+                 wl.alpha * float(np.sum(Ahat ** 2)))
+    t_qr = time.perf_counter() - a
+    t_pair = nf * statistics.mean(t_rows) + t_qr
+    rate = 2.0 / t_pair
+    out = dict(value=rate, unit="subproblems/s", cores=1, kind="oracle",
+               sample=(f"FP64 numpy oracle, 1 thread: kernel rows of pair {m} at frequency indices "
+                       f"{spec['freqs']} by the wavenumber sum (mean {statistics.mean(t_rows):.2f} s "
+                       f"per frequency, x {nf} frequencies) plus one damped QR of its {R} rows "
+                       f"({t_qr:.2f} s); one pair = two subproblems; the data transform is not "
+                       f"counted"))
+    print("CPUJSON " + json.dumps(out))
+
+
 def cpu_child(spec_path):
     """Runs in a subprocess with single-threaded BLAS: time the oracle on a sample."""
     import numpy as np
     import synth
     from oracle import edt2d
     spec = json.load(open(spec_path))
+    if spec.get("workload") == "batched_3d":
+        cpu_child_window(spec)
+        return
     wl = synth.preset(spec["workload"])
     rng = synth.rng_for(1, salt=77)
     D = synth.random_data(rng, (len(wl.freq_hz), wl.nx, wl.nx), np.complex64).astype(np.complex128)
@@ -116,8 +160,8 @@ def cpu_child(spec_path):
     print("CPUJSON " + json.dumps(out))
 
 
-def run_cpu_baseline(ms):
-    spec = dict(workload=WORKLOAD, ms=list(ms))
+def run_cpu_baseline(ms, spec=None):
+    spec = spec or dict(workload=WORKLOAD, ms=list(ms))
     with tempfile.NamedTemporaryFile("w", suffix=".json", delete=False) as f:
         json.dump(spec, f)
         path = f.name
@@ -217,6 +261,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched_3d":
+        main_window(args, world, rank, local)
         return
 
     import numpy as np
@@ -406,6 +453,133 @@ def main():
         gpu_launches=int(st.launches_per_invert) * args.steps,
         roofline=roof, stage_ms=stage_ms, accuracy=acc, variants=variants, clocks=clk,
         cpu_baseline=cpu)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_window(args, world, rank, local):
+    """The finite-aperture 3D workload: 128 x 128 midpoints (12.5 m), 16 x 16 half-offsets,
+    64 frequencies 4-50 Hz, 200 depths of 10 m, 20 random layers, alpha = 1e-2, seeded
+    complex64 random data of the workload's shape (any data define a valid least-squares
+    problem); 16 384 subproblems (midpoint wavenumbers) per inversion, 8 194 pair systems."""
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_0905_0238_gb300 import build as libbuild
+    libbuild.build()
+    from paper_0905_0238_gb300 import Config, Solver
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = synth.preset3d("batched_3d")
+    nf = len(wl.freq_hz)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.SEED_BASE + 2 + 1000 * line_salt(rank))
+    shape = (nf, wl.ny, wl.nx, wl.wy, wl.wx)
+    D = torch.complex(torch.randn(shape, device=dev, generator=gen),
+                      torch.randn(shape, device=dev, generator=gen)).contiguous()
+    s = Solver(Config.from_workload(wl, passes=args.passes, refine=args.refine,
+                                    chol_df=args.chol_df), device=dev)
+    Vout = torch.empty((wl.ny, wl.nx, wl.nz), device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        s.invert(D, out=Vout)
+    torch.cuda.synchronize()
+    st = s.stats()
+    if st.n_notpd or st.n_nonfinite:
+        raise RuntimeError(f"window path: {st.n_notpd} not PD, {st.n_nonfinite} non-finite")
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    s.set_profiling(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.invert(D, out=Vout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    stages, ncalls = s.read_profile()
+    s.set_profiling(False)
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world)
+    sub_per_step = wl.nx * wl.ny
+    value = job_throughput(world, sub_per_step, args.steps, ms_total)
+    # end to end through the host-buffer entry point
+    Dh = D.cpu().pin_memory()
+    Vh = torch.empty((wl.ny, wl.nx, wl.nz), dtype=torch.float32).pin_memory()
+    s.invert_host(Dh, Vh)
+    torch.cuda.synchronize()
+    barrier()
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(args.steps):
+        s.invert_host(Dh, Vh)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(h0.elapsed_time(h1), world)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    stage_ms = {k: v / max(ncalls, 1) for k, v in stages.items()}
+    nzp = (wl.nz + 31) // 32 * 32
+    ncols = (nzp + 16) + (nzp - 128 + 16 if nzp > 128 else 0)
+    issued = args.passes * 2.0 * (2 * st.gram_rows_padded) * 128 * ncols
+    gram_ms = stage_ms.get("gram", 0.0)
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = issued / (gram_ms / 1e3) / 1e12 if gram_ms > 0 else None
+    roof = dict(bound="tensor", kernel="gram_tc_kernel", achieved=achieved, peak=peak,
+                unit="TFLOP/s", frac=(achieved / peak) if achieved else None, traffic=None,
+                peak_source="MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                flops_per_launch=issued, gram_ms=gram_ms,
+                useful_flops_per_launch=2.0 * (2 * st.rows_solved) * wl.nz * (wl.nz + 2))
+    # kernel-row assembly: per frequency the window products U are written and read once
+    # and every kept row's nz values are written into the row table
+    W = wl.wx * wl.wy
+    k3_bytes = nf * 2 * W * wl.nz * wl.nx * wl.ny * 8 + st.rows_solved * wl.nz * 8
+    k3_ms = stage_ms.get("kernel_rows", 0.0)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = run_cpu_baseline(None, dict(workload="batched_3d", pair=4100, freqs=[10, 40]))
+        except Exception as ex:
+            cpu = dict(value=None, unit="subproblems/s", cores=0, kind="oracle", sample=str(ex)[:300])
+    line = dict(
+        metric="subproblems_per_sec", value=value, unit="subproblems/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=ms_total / args.steps,
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="bf16x3+f32acc+f64",
+        data="synthetic (seeded complex64 random data)",
+        config=dict(workload=("batched_3d: 128x128 midpoints dx=dy 12.5 m, 16x16 half-offsets "
+                              "(offsets every 25 m), 64 freqs 4-50 Hz, nz 200 dz 10 m, 20 layers"),
+                    l2="inputs larger than L2 (2.1 GB data per step)", passes=args.passes,
+                    refine=args.refine, alpha=wl.alpha, pairs=int(st.n_sub),
+                    rows_total=int(st.rows_total), parallelism=f"replicas x{world}"),
+        model_pts_per_sec=world * wl.nx * wl.ny * wl.nz * args.steps / (ms_total / 1e3),
+        e2e=dict(value=job_throughput(world, sub_per_step, args.steps, ms_e2e), unit="subproblems/s",
+                 h2d_bytes_per_step=int(Dh.numel() * Dh.element_size()),
+                 d2h_bytes_per_step=int(Vh.numel() * Vh.element_size())),
+        gpu_launches=int(st.launches_per_invert) * args.steps,
+        roofline=roof,
+        kernel_rows=dict(bound="hbm", ms=k3_ms, algorithmic_bytes=k3_bytes,
+                         achieved_gbs=k3_bytes / (k3_ms / 1e3) / 1e9 if k3_ms > 0 else None,
+                         peak_gbs=peaks.get("hbm_gbs")),
+        stage_ms=stage_ms, clocks=clk, cpu_baseline=cpu)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

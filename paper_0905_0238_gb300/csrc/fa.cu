@@ -12,7 +12,8 @@
 // window transform acts on U before one transform over y gives every k_m at once.
 // Stages per frequency: fa_gspace (spectrum from the table, inverse 2D FFT -> G), fa_u
 // (products and the window transform per y), fa_mrows (2D FFT of U_j per (j, z) plane,
-// then the kept rows of that plane are written into the row table A32[row][z]).
+// clusters of 4 consecutive depths, then the kept rows of (f, j) are written into the row
+// table A32[row][z] four depths at a time from the cluster's distributed shared memory).
 //
 // Data: the window transform of D[f][m][w] per midpoint (fa_dwin, written transposed as
 // Dw[f][j][m]), then per (f, j) plane the midpoint FFT and the split right-hand sides of
@@ -25,45 +26,51 @@
 #include "wfft.cuh"
 
 #include <algorithm>
+#include <cooperative_groups.h>
 
 namespace edt {
 
 namespace {
 
-constexpr int FA_THREADS = 512;   // plane kernels
+// threads of the plane kernels: a 2D plane fills shared memory (one CTA per SM), so it takes
+// the most warps a CTA can have; a line is one warp's FFT
+template <int PY> __host__ __device__ constexpr int plane_threads() { return PY > 0 ? 1024 : 128; }
 constexpr int FW_THREADS = 256;   // window-transform kernels
 
-__host__ __device__ constexpr int plane_ld(int nx) { return nx + 1; }   // odd row stride
+// Plane layout in shared memory: element (y, x) at y * ld + 2 (y/16) + x + 2 (x/16) with
+// ld = 1 mod 16, so that along a row and along a column element i sits at i + 2 (i/16)
+// modulo 16 complex slots (32 banks).  Every access pattern of the 16-thread line FFT below
+// (stride-16 loads, the paired reads of its second pass, the natural-order stores) then
+// sends the 16 lanes of each 8-byte phase to 16 distinct slot pairs: no bank conflicts.
+__host__ __device__ constexpr int plane_ld(int nx) { return (nx + 2 * (nx / 16) + 15) / 16 * 16 + 1; }
+__host__ __device__ constexpr int plane_words(int nx, int ny) {
+  return (ny - 1) * plane_ld(nx) + 2 * ((ny - 1) / 16) + (nx - 1) + 2 * ((nx - 1) / 16) + 1;
+}
+__device__ __forceinline__ int paddr(int y, int x, int ld) { return y * ld + 2 * (y >> 4) + x + 2 * (x >> 4); }
 
-// 2D transform of one plane s[ny][ld] in shared memory, nx = 32 PX, ny = 32 PY (PY = 0:
+// 2D transform of one plane in shared memory (layout above), nx = 32 PX, ny = 32 PY (PY = 0:
 // ny = 1).  Warps take rows, then columns, each line a register-resident warp FFT; the
 // twiddle table is that of length nx (ny == nx when PY > 0).
-template <int PX, int PY, int SG>
-__device__ void plane_fft2(float2* s, int ld, const float2* tw) {
-  constexpr int NX = 32 * PX, NY = PY > 0 ? 32 * PY : 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < NY; r += nw) {
-    float2 v[PX];
+// Load a contiguous [NY][NX] plane into the shared layout: every thread issues all of its loads
+// before its shared stores, so a CTA keeps the whole plane's reads in flight.
+template <int NX, int NY, int LD, int T>
+__device__ __forceinline__ void load_plane(float2* s, const float2* P) {
+  constexpr int TOT = NX * NY;
+  if (TOT % T == 0) {
+    constexpr int PER = TOT % T == 0 ? TOT / T : 1;
+    float2 r[PER];
 #pragma unroll
-    for (int a = 0; a < PX; ++a) v[a] = s[r * ld + 32 * a + lane];
-    warp_fft<PX>(v, tw, NX, SG, lane);
-    const int br = rbits(lane, 5) * PX;
+    for (int i = 0; i < PER; ++i) r[i] = P[threadIdx.x + i * T];
 #pragma unroll
-    for (int k = 0; k < PX; ++k) s[r * ld + k + br] = v[k];
-  }
-  __syncthreads();
-  if (PY > 0) {
-    constexpr int QY = PY > 0 ? PY : 1;
-    for (int c = warp; c < NX; c += nw) {
-      float2 v[QY];
-#pragma unroll
-      for (int a = 0; a < QY; ++a) v[a] = s[(32 * a + lane) * ld + c];
-      warp_fft<QY>(v, tw, NY, SG, lane);
-      const int br = rbits(lane, 5) * QY;
-#pragma unroll
-      for (int k = 0; k < QY; ++k) s[(k + br) * ld + c] = v[k];
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * T, y = e / NX, x = e - y * NX;
+      s[paddr(y, x, LD)] = r[i];
     }
-    __syncthreads();
+  } else {
+    for (int e = threadIdx.x; e < TOT; e += blockDim.x) {
+      const int y = e / NX, x = e - y * NX;
+      s[paddr(y, x, LD)] = P[e];
+    }
   }
 }
 
@@ -76,6 +83,27 @@ __device__ __forceinline__ float2 w16(int k) {
                            0.f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
   return make_float2(C[k & 15], -C[(k + 12) & 15]);        // e^{-2 pi i k/16} = (cos, -sin)
 }
+
+// In-register DFTs of R points with either sign (the 2D plane transforms)
+template <int R, int SG> struct Dft;
+template <int SG> struct Dft<2, SG> {
+  __device__ static __forceinline__ void run(float2 (&a)[2]) {
+    const float2 u = a[0], v = a[1];
+    a[0] = u + v; a[1] = u - v;
+  }
+};
+template <int SG> struct Dft<4, SG> {
+  __device__ static __forceinline__ void run(float2 (&a)[4]) {
+    const float2 b0 = a[0] + a[2], b1 = a[0] - a[2], b2 = a[1] + a[3], b3 = rot4<SG>(a[1] - a[3]);
+    a[0] = b0 + b2; a[2] = b0 - b2; a[1] = b1 + b3; a[3] = b1 - b3;
+  }
+};
+template <int SG> struct Dft<8, SG> {
+  __device__ static __forceinline__ void run(float2 (&a)[8]) { dft8<SG>(a); }
+};
+template <int SG> struct Dft<16, SG> {
+  __device__ static __forceinline__ void run(float2 (&a)[16]);
+};
 
 template <int W> __device__ __forceinline__ void reg_dft(float2 (&a)[W]);
 template <> __device__ __forceinline__ void reg_dft<1>(float2 (&)[1]) {}
@@ -102,6 +130,118 @@ template <> __device__ __forceinline__ void reg_dft<16>(float2 (&a)[16]) {
   }
 }
 
+template <int SG>
+__device__ __forceinline__ void Dft<16, SG>::run(float2 (&a)[16]) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { e[i] = a[2 * i]; o[i] = a[2 * i + 1]; }
+  dft8<SG>(e);
+  dft8<SG>(o);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float2 t = o[k] * tw_sg<SG>(w16(k));
+    a[k] = e[k] + t;
+    a[k + 8] = e[k] - t;
+  }
+}
+
+// N-point FFT (N = 16 R, R in {2, 4, 8}) of one line by a group of 16 threads, t = 0..15,
+// in place in shared memory (element i at s[addr(i)]).  With n = 16 a + t and
+// k = k1 + R k2: pass 1 takes the R-point DFT over a of x[16 a + t] and applies W_N^{t k1},
+// keeping the result in the slots 16 k1 + t; pass 2 takes the 16-point DFT over t for each
+// k1, split between the thread pair (2 k1, 2 k1 + 1) as the 8-point DFTs of the even and the
+// odd t (the odd half times W_16^k2), exchanged by one shuffle per value, and writes
+// X[k1 + R k2] in natural order.  tw: W_N^e (sign -1) for e < N.  A group is a half-warp.
+// src: where pass 1 reads the line (null: the shared slots themselves).
+template <int R, int SG, class Addr>
+__device__ __forceinline__ void group_fft(float2* s, const Addr& addr, int t, const float2* tw,
+                                          const float2* src = nullptr) {
+  const unsigned gm = 0xffffu << (threadIdx.x & 16);         // this half-warp
+  float2 v[R];
+  if (src) {
+#pragma unroll
+    for (int a = 0; a < R; ++a) v[a] = src[16 * a + t];
+  } else {
+#pragma unroll
+    for (int a = 0; a < R; ++a) v[a] = s[addr(16 * a + t)];
+  }
+  Dft<R, SG>::run(v);
+#pragma unroll
+  for (int k1 = 1; k1 < R; ++k1) v[k1] = v[k1] * tw_sg<SG>(tw[t * k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < R; ++k1) s[addr(16 * k1 + t)] = v[k1];
+  __syncwarp(gm);
+  const int k1 = t >> 1, h = t & 1;
+  const bool act = k1 < R;
+  float2 u[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) u[i] = act ? s[addr(16 * k1 + 2 * i + h)] : make_float2(0.f, 0.f);
+  dft8<SG>(u);
+  if (h) {
+#pragma unroll
+    for (int k2 = 1; k2 < 8; ++k2) u[k2] = u[k2] * tw_sg<SG>(w16(k2));
+  }
+  float2 p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    p[i].x = __shfl_xor_sync(gm, u[i].x, 1);
+    p[i].y = __shfl_xor_sync(gm, u[i].y, 1);
+  }
+  __syncwarp(gm);                                            // pass-2 reads before the writes
+  if (act) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float2 e = h ? p[i] : u[i], o = h ? u[i] : p[i];
+      s[addr(k1 + R * (i + 8 * h))] = h ? e - o : e + o;
+    }
+  }
+  __syncwarp(gm);
+}
+
+struct RowAddr {
+  int r, ld;
+  __device__ __forceinline__ int operator()(int i) const { return paddr(r, i, ld); }
+};
+struct ColAddr {
+  int c, ld;
+  __device__ __forceinline__ int operator()(int i) const { return paddr(i, c, ld); }
+};
+
+// gsrc: a row-major [NY][NX] plane in global memory that the row pass reads directly (its
+// loads then overlap other groups' arithmetic); null: the plane is already in s.
+template <int PX, int PY, int SG>
+__device__ void plane_fft2(float2* s, int ld, const float2* tw, const float2* tws,
+                           const float2* gsrc = nullptr) {
+  constexpr int NX = 32 * PX, NY = PY > 0 ? 32 * PY : 1;
+  if constexpr (PY > 0) {
+    // square plane: one group of 16 threads per line, rows then columns
+    constexpr int R = NX / 16;
+    const int t = threadIdx.x & 15, grp = threadIdx.x >> 4, ng = blockDim.x >> 4;
+    for (int r = grp; r < NY; r += ng)
+      group_fft<R, SG>(s, RowAddr{r, ld}, t, tws, gsrc ? gsrc + size_t(r) * NX : nullptr);
+    __syncthreads();
+    for (int c = grp; c < NX; c += ng) group_fft<R, SG>(s, ColAddr{c, ld}, t, tws);
+    __syncthreads();
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < NY; r += nw) {
+    float2 v[PX];
+#pragma unroll
+    for (int a = 0; a < PX; ++a) v[a] = s[paddr(r, 32 * a + lane, ld)];
+    warp_fft<PX>(v, tw, NX, SG, lane);
+    const int br = rbits(lane, 5) * PX;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) s[paddr(r, k + br, ld)] = v[k];
+  }
+  __syncthreads();
+}
+
+// W_N^e (sign -1) for e < N in shared memory, from the context's table of length N
+__device__ __forceinline__ void plane_twiddles(float2* tws, const float2* tw32, int N) {
+  for (int e = threadIdx.x; e < N; e += blockDim.x) tws[e] = tw_at(tw32, e, N);
+}
+
 // signed-index DFT over a window of W samples: out[j] = sum_w exp(-2 pi i j w/W) in[w] with
 // j, w in [-W/2, W/2): the plain DFT of (-1)^w in[w], times (-1)^j (-1)^(W/2) (W >= 2).
 __host__ __device__ constexpr bool alt_sign_end(int W) { return W >= 2 && ((W / 2) & 1); }
@@ -110,24 +250,26 @@ __device__ __forceinline__ float2 neg_if(float2 v, bool n) { return n ? make_flo
 // ---- kernel rows -----------------------------------------------------------------------
 // G(y, z) for one frequency: CTA per z.
 template <int PX, int PY>
-__global__ void __launch_bounds__(FA_THREADS) fa_gspace_kernel(Dev d, int f) {
+__global__ void __launch_bounds__(plane_threads<PY>()) fa_gspace_kernel(Dev d, int f) {
   constexpr int NX = 32 * PX, NY = PY > 0 ? 32 * PY : 1, LD = plane_ld(NX);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s = reinterpret_cast<float2*>(smem_raw);
   const int z = blockIdx.x, hx = NX / 2 + 1;
   const float2* g = d.g32 + size_t(f) * d.nk * d.nzs + z;
+  float2* tws = s + plane_words(NX, NY);
+  plane_twiddles(tws, d.tw32, NX);
   for (int e = threadIdx.x; e < NX * NY; e += blockDim.x) {
     const int ay = e / NX, ax = e - ay * NX;
     const int qy = min(ay, NY - ay), qx = min(ax, NX - ax);
-    s[ay * LD + ax] = g[size_t(qy * hx + qx) * d.nzs];
+    s[paddr(ay, ax, LD)] = g[size_t(qy * hx + qx) * d.nzs];
   }
   __syncthreads();
-  plane_fft2<PX, PY, +1>(s, LD, d.tw32);
+  plane_fft2<PX, PY, +1>(s, LD, d.tw32, tws);
   const float sc = float(1.0 / (double(NX) * NY * d.dx * d.dy));
   float2* G = d.Gs + size_t(z) * NX * NY;
   for (int e = threadIdx.x; e < NX * NY; e += blockDim.x) {
     const int y = e / NX, x = e - y * NX;
-    const float2 v = s[y * LD + x];
+    const float2 v = s[paddr(y, x, LD)];
     G[e] = make_float2(sc * v.x, sc * v.y);
   }
 }
@@ -152,13 +294,13 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d) {
   const float2* G = d.Gs + size_t(z) * d.nxy;
   for (int e = threadIdx.x; e < (WY + 1) * nx; e += blockDim.x) {
     const int t = e / nx, x = e - t * nx;
-    const int row = ((yy + t - WY / 2) % ny + ny) % ny;
+    const int row = (yy + t - WY / 2 + ny) & (ny - 1);      // ny is a power of two
     Grow[e] = G[size_t(row) * nx + x];
   }
   __syncthreads();
   for (int x0 = 0; x0 < nx; x0 += UPB) {
     {
-      const int ux = threadIdx.x / WY, iwy = threadIdx.x - ux * WY, x = x0 + ux;
+      const int iwy = threadIdx.x / UPB, ux = threadIdx.x - iwy * UPB, x = x0 + ux;   // lanes over x
       if (x < nx) {
         const int wyv = iwy - WY / 2;
         const float2* Gm = Grow + (WY / 2 - wyv) * nx;    // row yy - wy
@@ -167,7 +309,7 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d) {
 #pragma unroll
         for (int ix = 0; ix < WX; ++ix) {
           const int wxv = ix - WX / 2;
-          const float2 p = Gm[(x - wxv + nx) % nx] * Gp[(x + wxv + nx) % nx];
+          const float2 p = Gm[(x - wxv + nx) & (nx - 1)] * Gp[(x + wxv + nx) & (nx - 1)];
           a[ix] = neg_if(p, WX >= 2 && (ix & 1));
         }
         reg_dft<WX>(a);
@@ -194,26 +336,57 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d) {
   }
 }
 
-// M(k_m; f, j, z) for one (j, z) plane: 2D FFT of U_j, then the kept rows of (f, j).
+// M(k_m; f, j, z) for ZC consecutive depths of one j: a cluster of ZC CTAs, one (j, z) plane
+// each (2D FFT of U_j in shared memory); then every CTA takes a share of the kept rows of
+// (f, j) and reads the ZC depths of each from the cluster's planes (distributed shared
+// memory), so each row's depths z0..z0+ZC-1 are written as one 32-byte store.
+constexpr int ZC = 4;
+
 template <int PX, int PY>
-__global__ void __launch_bounds__(FA_THREADS) fa_mrows_kernel(Dev d, int f, float2 cf) {
+__global__ void __cluster_dims__(1, ZC, 1) __launch_bounds__(plane_threads<PY>())
+fa_mrows_kernel(Dev d, int f, float2 cf) {
+  namespace cg = cooperative_groups;
   constexpr int NX = 32 * PX, NY = PY > 0 ? 32 * PY : 1, LD = plane_ld(NX);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s = reinterpret_cast<float2*>(smem_raw);
-  const int j = blockIdx.x, z = blockIdx.y;
-  const float2* P = d.U + (size_t(j) * d.nz + z) * (NX * NY);
-  for (int e = threadIdx.x; e < NX * NY; e += blockDim.x) {
-    const int y = e / NX, x = e - y * NX;
-    s[y * LD + x] = P[e];
+  float2* tws = s + plane_words(NX, NY);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int j = blockIdx.x, z = blockIdx.y, rank = int(cluster.block_rank()), z0 = z - rank;
+  if (z < d.nz) {                        // every CTA reaches both cluster barriers below
+    const float2* P = d.U + (size_t(j) * d.nz + z) * (NX * NY);
+    plane_twiddles(tws, d.tw32, NX);
+    if (PY > 0) {
+      __syncthreads();
+      plane_fft2<PX, PY, +1>(s, LD, d.tw32, tws, P);
+    } else {
+      load_plane<NX, NY, LD, plane_threads<PY>()>(s, P);
+      __syncthreads();
+      plane_fft2<PX, PY, +1>(s, LD, d.tw32, tws);
+    }
   }
-  __syncthreads();
-  plane_fft2<PX, PY, +1>(s, LD, d.tw32);
+  cluster.sync();
+  const float2* ps[ZC];
+#pragma unroll
+  for (int k = 0; k < ZC; ++k) ps[k] = cluster.map_shared_rank(s, k);
   const int e0 = d.fj_off[f * d.W + j], e1 = d.fj_off[f * d.W + j + 1];
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+  const int n = e1 - e0, per = (n + ZC - 1) / ZC;
+  const int a0 = e0 + rank * per, a1 = min(e1, a0 + per);
+  for (int e = a0 + threadIdx.x; e < a1; e += blockDim.x) {
     const int2 ent = d.fj_ent[e];
-    const int y = ent.x / NX, x = ent.x - y * NX;
-    d.A32[size_t(ent.y) * d.nzs + z] = cf * s[y * LD + x];
+    const int y = ent.x / NX, x = ent.x - y * NX, off = paddr(y, x, LD);
+    float2 v[ZC];
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) v[k] = z0 + k < d.nz ? cf * ps[k][off] : make_float2(0.f, 0.f);
+    float2* dst = d.A32 + size_t(ent.y) * d.nzs + z0;
+    if (z0 + ZC <= d.nzs) {
+      reinterpret_cast<float4*>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+      reinterpret_cast<float4*>(dst)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    } else {
+#pragma unroll
+      for (int k = 0; k < ZC; ++k) if (z0 + k < d.nzs) dst[k] = v[k];
+    }
   }
+  cluster.sync();                        // peers may still read this CTA's plane
 }
 
 // ---- data ------------------------------------------------------------------------------
@@ -258,24 +431,28 @@ __global__ void __launch_bounds__(FW_THREADS) fa_dwin_kernel(Dev d, const TIN* D
 
 // Midpoint FFT of one (f, j) plane of Dw and the split right-hand sides of its kept rows.
 template <int PX, int PY>
-__global__ void __launch_bounds__(FA_THREADS) fa_drhs_kernel(Dev d) {
+__global__ void __launch_bounds__(plane_threads<PY>()) fa_drhs_kernel(Dev d) {
   constexpr int NX = 32 * PX, NY = PY > 0 ? 32 * PY : 1, LD = plane_ld(NX);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s = reinterpret_cast<float2*>(smem_raw);
   const int j = blockIdx.x, f = blockIdx.y;
+  float2* tws = s + plane_words(NX, NY);
   const float2* P = d.Dw + (size_t(f) * d.W + j) * (NX * NY);
-  for (int e = threadIdx.x; e < NX * NY; e += blockDim.x) {
-    const int y = e / NX, x = e - y * NX;
-    s[y * LD + x] = P[e];
+  plane_twiddles(tws, d.tw32, NX);
+  if (PY > 0) {
+    __syncthreads();
+    plane_fft2<PX, PY, -1>(s, LD, d.tw32, tws, P);
+  } else {
+    load_plane<NX, NY, LD, plane_threads<PY>()>(s, P);
+    __syncthreads();
+    plane_fft2<PX, PY, -1>(s, LD, d.tw32, tws);
   }
-  __syncthreads();
-  plane_fft2<PX, PY, -1>(s, LD, d.tw32);
   const int e0 = d.fj_off[f * d.W + j], e1 = d.fj_off[f * d.W + j + 1];
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int2 ent = d.fj_ent[e];
     const int y = ent.x / NX, x = ent.x - y * NX;
     const int ny2 = (NY - y) % NY, nx2 = (NX - x) % NX;
-    const float2 a = s[y * LD + x], b = s[ny2 * LD + nx2];
+    const float2 a = s[paddr(y, x, LD)], b = s[paddr(ny2, nx2, LD)];
     reinterpret_cast<float4*>(d.rhs)[ent.y] =
         make_float4(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.y - b.y), -0.5f * (a.x - b.x));
   }
@@ -326,12 +503,12 @@ template <int WX, int WY>
 size_t u_smem(int nx) { return (size_t(ExLayout<WX, WY>::SIZE) + size_t(WY + 1) * nx) * sizeof(float2); }
 
 template <int PX, int PY>
-size_t plane_smem() { return size_t(PY > 0 ? 32 * PY : 1) * plane_ld(32 * PX) * sizeof(float2); }
+size_t plane_smem() { return size_t(plane_words(32 * PX, PY > 0 ? 32 * PY : 1) + 32 * PX) * sizeof(float2); }
 
 template <int PX, int PY>
 cudaError_t rows_for(const Dev& d, int f, float2 cf, cudaStream_t s) {
   const size_t sm = plane_smem<PX, PY>();
-  fa_gspace_kernel<PX, PY><<<d.nz, FA_THREADS, sm, s>>>(d, f);
+  fa_gspace_kernel<PX, PY><<<d.nz, plane_threads<PY>(), sm, s>>>(d, f);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 gu(d.ny, d.nz);
@@ -343,7 +520,7 @@ cudaError_t rows_for(const Dev& d, int f, float2 cf, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  fa_mrows_kernel<PX, PY><<<dim3(d.W, d.nz), FA_THREADS, sm, s>>>(d, f, cf);
+  fa_mrows_kernel<PX, PY><<<dim3(d.W, (d.nz + ZC - 1) / ZC * ZC), plane_threads<PY>(), sm, s>>>(d, f, cf);
   return cudaGetLastError();
 }
 
@@ -404,7 +581,7 @@ cudaError_t launch_fa_data(const Dev& d, const void* D, int D_dtype, cudaStream_
   const int px = d.N / 32, py = d.ny == 1 ? 0 : d.ny / 32;
 #define FA_DR(PX, PY) \
   if (px == PX && py == PY) { \
-    fa_drhs_kernel<PX, PY><<<dim3(d.W, d.nf), FA_THREADS, plane_smem<PX, PY>(), s>>>(d); \
+    fa_drhs_kernel<PX, PY><<<dim3(d.W, d.nf), plane_threads<PY>(), plane_smem<PX, PY>(), s>>>(d); \
     return cudaGetLastError(); \
   }
   FA_SHAPES(FA_DR)
