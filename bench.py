@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default launch shapes instead of the autotuned ones")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_3d"],
                     help="batched_3d: the finite-aperture 3D workload (a separate line, not the "
                          "headline)")
@@ -303,6 +305,9 @@ def main():
                                         refine=args.refine, chol_df=args.chol_df), device=dev)
     Vout = torch.empty((wl.nx, wl.nz), device=dev, dtype=torch.float32)
     stream = torch.cuda.current_stream(dev)
+    tuning = None
+    if not args.no_autotune:
+        tuning = mixed.autotune(D, out=Vout, reps=3)     # launch shapes (same arithmetic)
     for _ in range(max(3, args.warmup)):
         mixed.invert(D, out=Vout)
     torch.cuda.synchronize()
@@ -445,7 +450,8 @@ def main():
         config=dict(workload=workload_summary(wl), l2="inputs larger than L2 (268 MB data per step)",
                     passes=args.passes, refine=args.refine, chol_df=args.chol_df, alpha=wl.alpha,
                     rows_total=int(st.rows_total), rows_solved=int(st.rows_solved),
-                    parallelism=f"replicas x{world} (independent lines)"),
+                    parallelism=f"replicas x{world} (independent lines)",
+                    launch_shapes=(tuning or mixed.tuning()), autotuned=tuning is not None),
         model_pts_per_sec=world * wl.nx * wl.nz * args.steps / (ms_total / 1e3),
         e2e=dict(value=e2e_value, unit="subproblems/s",
                  h2d_bytes_per_step=int(Dh.numel() * Dh.element_size()),
@@ -489,6 +495,9 @@ def main_window(args, world, rank, local):
                                     chol_df=args.chol_df), device=dev)
     Vout = torch.empty((wl.ny, wl.nx, wl.nz), device=dev, dtype=torch.float32)
     stream = torch.cuda.current_stream(dev)
+    tuning = None
+    if not args.no_autotune:
+        tuning = s.autotune(D, out=Vout, reps=1)
     for _ in range(max(3, args.warmup)):
         s.invert(D, out=Vout)
     torch.cuda.synchronize()
@@ -569,7 +578,8 @@ def main_window(args, world, rank, local):
                               "(offsets every 25 m), 64 freqs 4-50 Hz, nz 200 dz 10 m, 20 layers"),
                     l2="inputs larger than L2 (2.1 GB data per step)", passes=args.passes,
                     refine=args.refine, alpha=wl.alpha, pairs=int(st.n_sub),
-                    rows_total=int(st.rows_total), parallelism=f"replicas x{world}"),
+                    rows_total=int(st.rows_total), parallelism=f"replicas x{world}",
+                    launch_shapes=(tuning or s.tuning()), autotuned=tuning is not None),
         model_pts_per_sec=world * wl.nx * wl.ny * wl.nz * args.steps / (ms_total / 1e3),
         e2e=dict(value=job_throughput(world, sub_per_step, args.steps, ms_e2e), unit="subproblems/s",
                  h2d_bytes_per_step=int(Dh.numel() * Dh.element_size()),

@@ -155,6 +155,21 @@ typedef struct {
                                    spectrum buffer holds one chunk, about 32 MB)         */
 } edt_stats;
 
+/* Launch shapes the autotuner chooses among (candidates in brackets; all give the same
+ * results up to FP32 summation order). */
+typedef struct {
+  int band_budget_mb;           /* line geometry, mixed: bytes of band spectra per transform
+                                   chunk, in MB [16, 32, 48, 96]; default 48                */
+  int band_cols;                /* line geometry, mixed: band columns per column-FFT block
+                                   [4, 8, 16]; default 8                                    */
+  int refine_shape;             /* mixed: refinement CTA shape, 0 = 4 warps x 32 rows,
+                                   1 = 8 x 32, 2 = 4 x 64, 3 = 8 x 16; default 0           */
+  int window_ztile;             /* window geometry: depths per kernel-row cluster [2, 4, 8];
+                                   default 4                                                */
+  double invert_ms;             /* edt_invert time with these shapes when the autotuner
+                                   chose them (0 if never tuned)                           */
+} edt_tuning;
+
 /* Create a context for `cfg` and report the device workspace it needs.
  * Returns EDT_OK, EDT_EINVAL or EDT_EUNSUPPORTED.  *out is NULL on failure. */
 int edt_create(edt_ctx** out, const edt_config* cfg, size_t* workspace_bytes);
@@ -175,6 +190,17 @@ int edt_invert(edt_ctx* ctx, const void* D_dev, int D_dtype, void* V_dev, int V_
  * stream stay the same (a change re-captures).  Requires a non-default stream; calls on the
  * legacy default stream, and calls made while profiling is on, run uncaptured. */
 int edt_set_graph(edt_ctx* ctx, int on);
+
+/* Autotuner: for each tunable launch shape in turn, time `reps` (>= 1) edt_invert calls on
+ * the caller's data with every candidate (the others at their current best) and keep the
+ * fastest (coordinate descent, CUDA events on `stream`, minimum over the reps).  The tuned
+ * shapes stay with the context; V_dev receives the last inversion.  Synchronises `stream`.
+ * Must not run while the stream is being captured. */
+int edt_autotune(edt_ctx* ctx, const void* D_dev, int D_dtype, void* V_dev, int V_dtype,
+                 void* stream, int reps);
+/* The current launch shapes; setting them validates every field (EDT_EINVAL). */
+int edt_get_tuning(const edt_ctx* ctx, edt_tuning* out);
+int edt_set_tuning(edt_ctx* ctx, const edt_tuning* in);
 
 /* edt_invert from host buffers: copies D to the device, inverts, copies V back, all on
  * `stream` (asynchronous; the host buffers must stay valid until the stream syncs).

@@ -59,7 +59,7 @@ struct PolicyShuffle {
 };
 
 constexpr int BR_WARPS = 8;    // receiver lines per block in the row pass
-constexpr int BC_COLS = 8;     // band columns per block in the column pass
+// band columns per block in the column pass: 4, 8 or 16 (the autotuner's choice)
 
 template <class F>
 __device__ __forceinline__ void fill_twiddles(float2* tws, const float2* tw32) {
@@ -104,8 +104,9 @@ __host__ __device__ constexpr int cols_ld() {
   return ((F::N + F::N / 16 > F::SCRATCH ? F::N + F::N / 16 : F::SCRATCH) | 1);
 }
 
-template <class F>
-__global__ void __launch_bounds__(BC_COLS * 32, F::MINB_COLS) band_cols_kernel(Dev d, int blk0) {
+template <class F, int BC_COLS>
+__global__ void __launch_bounds__(BC_COLS * 32, (F::MINB_COLS * 8) / BC_COLS > 0 ? (F::MINB_COLS * 8) / BC_COLS : 1)
+band_cols_kernel(Dev d, int blk0) {
   constexpr int N = F::N, LD = cols_ld<F>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);            // [BC_COLS][LD]
@@ -187,8 +188,8 @@ __global__ void __launch_bounds__(256) band_rhs_kernel(Dev d, const long long* c
 }
 
 template <class F>
-size_t cols_smem() {
-  return (size_t(BC_COLS) * cols_ld<F>() + (F::SCRATCH > 0 ? Fft512::TWS : 0)) * sizeof(float2);
+size_t cols_smem(int bc) {
+  return (size_t(bc) * cols_ld<F>() + (F::SCRATCH > 0 ? Fft512::TWS : 0)) * sizeof(float2);
 }
 
 template <class F>
@@ -203,7 +204,11 @@ cudaError_t run_chunk(const Dev& d, const BandChunk& ch, const void* D, int D_dt
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ch.nbcol > 0) {
-    band_cols_kernel<F><<<unsigned(ch.nbcol), BC_COLS * 32, cols_smem<F>(), s>>>(d, ch.bcol0);
+    const unsigned nb2 = unsigned(ch.nbcol);
+    const size_t sm = cols_smem<F>(d.tune_bc);
+    if (d.tune_bc == 4) band_cols_kernel<F, 4><<<nb2, 4 * 32, sm, s>>>(d, ch.bcol0);
+    else if (d.tune_bc == 16) band_cols_kernel<F, 16><<<nb2, 16 * 32, sm, s>>>(d, ch.bcol0);
+    else band_cols_kernel<F, 8><<<nb2, 8 * 32, sm, s>>>(d, ch.bcol0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ch.nrow > 0) {
@@ -216,15 +221,19 @@ cudaError_t run_chunk(const Dev& d, const BandChunk& ch, const void* D, int D_dt
 
 template <class F>
 cudaError_t prepare_policy() {
-  return cudaFuncSetAttribute(band_cols_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(cols_smem<F>()));
+  cudaError_t e = cudaFuncSetAttribute(band_cols_kernel<F, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(cols_smem<F>(4)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(band_cols_kernel<F, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cols_smem<F>(8)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(band_cols_kernel<F, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cols_smem<F>(16)));
+  return e;
 }
 
 }  // namespace
 
 bool band_supported(int N) { return N >= 32 && N <= 1024; }
 
-int band_cols_per_block() { return BC_COLS; }
 
 cudaError_t launch_band_chunk(const Dev& d, const BandChunk& ch, const void* D, int D_dtype, cudaStream_t s) {
   switch (d.N) {

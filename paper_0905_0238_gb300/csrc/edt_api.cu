@@ -63,6 +63,10 @@ struct edt_ctx {
   std::vector<BandChunk> bchunks;
   size_t band_ymax = 0, band_xmax = 0;   // complex elements of the largest chunk's Y and Xc
   int band_maxplanes = 0;
+  // launch shapes (autotuned) and the workspace maxima over their candidates
+  int band_budget_mb = 48, tune_bc = 8, tune_rf = 0, tune_zc = 4;
+  size_t ws_band_elems = 0, ws_bcol = 0, ws_cpre = 0;
+  double tuned_ms = 0.0;
   std::vector<long long> counts_cut;
   std::vector<double2> tw64;
   std::vector<float2> tw32;
@@ -231,8 +235,8 @@ void plan_band(edt_ctx* c, double cmin) {
       b.lo = -N / 2 + 1; b.w = N;
     }
   }
-  const size_t budget = size_t(48) << 20;                  // bytes of Y + Xc per chunk
-  const int bc = band_cols_per_block();
+  const size_t budget = size_t(c->band_budget_mb) << 20;   // bytes of Y + Xc per chunk
+  const int bc = c->tune_bc;
   int f0 = 0;
   while (f0 < nf) {
     BandChunk ch{f0, f0, int(c->bcol.size()), 0, 0, int(c->bchunks.size())};
@@ -367,6 +371,17 @@ void plan(edt_ctx* c) {
     const size_t want = g.freq_chunk > 0 ? size_t(g.freq_chunk) : (size_t(256) << 20) / plane;
     c->fchunk = int(std::max<size_t>(1, std::min<size_t>(c->nf, want)));
   }
+  // the workspace holds the band buffers and tables of every autotuning candidate
+  for (int mb : {16, 32, 48, 96})
+    for (int bc : {4, 8, 16}) {
+      const int mb0 = c->band_budget_mb, bc0 = c->tune_bc;
+      c->band_budget_mb = mb; c->tune_bc = bc;
+      plan_band(c, cmin);
+      c->ws_band_elems = std::max(c->ws_band_elems, ((c->band_ymax * sizeof(float2) + 255) / 256 * 256) / sizeof(float2) + c->band_xmax);
+      c->ws_bcol = std::max(c->ws_bcol, c->bcol.size());
+      c->ws_cpre = std::max(c->ws_cpre, c->cpre.size());
+      c->band_budget_mb = mb0; c->tune_bc = bc0;
+    }
   plan_band(c, cmin);
   }
   c->rows_max_sub = 0;
@@ -451,8 +466,8 @@ void layout(edt_ctx* c) {
   take(c->r_roff, (ns + 1) * sizeof(long long));
   take(c->r_roffmf, ns * (nf + 1) * sizeof(long long));
   take(c->r_band, nf * sizeof(BandInfo));
-  take(c->r_bcol, std::max<size_t>(c->bcol.size(), 1) * sizeof(int2));
-  take(c->r_cpre, std::max<size_t>(c->cpre.size(), 1) * sizeof(long long));
+  take(c->r_bcol, std::max<size_t>(std::max(c->ws_bcol, c->bcol.size()), 1) * sizeof(int2));
+  take(c->r_cpre, std::max<size_t>(std::max(c->ws_cpre, c->cpre.size()), 1) * sizeof(long long));
   const size_t nxy = c->nxy, W = c->W, nzs = size_t((c->nz + 1) & ~1);
   take(c->r_kval, std::max<size_t>(c->kval.size(), 1) * sizeof(double));
   take(c->r_pairm, std::max<size_t>(c->pair_m.size(), 1) * sizeof(int));
@@ -478,7 +493,8 @@ void layout(edt_ctx* c) {
   // full planes of the forward model (and of the FP64 transform), or the band spectra of
   // one chunk (Y, then Xc at a 256-byte boundary); one call uses one of the two
   take(c->r_X, std::max(size_t(c->fchunk) * N * N * (mixed ? sizeof(float2) : sizeof(double2)),
-                        align_up(c->band_ymax * sizeof(float2), 256) + c->band_xmax * sizeof(float2)));
+                        std::max(align_up(c->band_ymax * sizeof(float2), 256) + c->band_xmax * sizeof(float2),
+                                 c->ws_band_elems * sizeof(float2))));
   take(c->r_Dst, (c->win ? nf * nxy * W : nf * N * N) * sizeof(double2));
   take(c->r_Vst, (c->win ? nxy : N) * nz * sizeof(double));
   // right-hand sides; the mixed path's tensor-core Gram bulk-copies whole stages of 32 rows,
@@ -520,6 +536,7 @@ void bind(edt_ctx* c) {
   d.row_off_mf = at<const long long*>(c, c->r_roffmf);
   d.fchunk = c->fchunk;
   d.rows_max_sub = c->rows_max_sub;
+  d.tune_bc = c->tune_bc; d.tune_rf = c->tune_rf; d.tune_zc = c->tune_zc;
   d.geom = c->win ? EDT_GEOM_WINDOW : EDT_GEOM_LINE;
   d.ny = c->ny; d.wx = c->wx; d.wy = c->wy; d.W = c->W; d.nxy = c->nxy; d.dy = c->cfg.dy;
   d.kval = c->win ? at<const double*>(c, c->r_kval) : nullptr;
@@ -742,6 +759,33 @@ static void drop_graph(edt_ctx* c) {
   c->gexec = nullptr;
 }
 
+// Make the context's launch shapes current: re-plan the band chunks (line geometry), rebind
+// and re-upload the band tables, forget a captured graph.
+static int apply_tuning(edt_ctx* c) {
+  drop_graph(c);
+  if (c->band_mode) {
+    const double cmin = *std::min_element(c->vel.begin(), c->vel.end());
+    plan_band(c, cmin);
+  }
+  if (!c->ws) return EDT_OK;
+  bind(c);
+  if (c->band_mode) {
+    EDT_TRYI(upload(c, c->r_band, c->band));
+    if (!c->bcol.empty()) EDT_TRYI(upload(c, c->r_bcol, c->bcol));
+    if (!c->cpre.empty()) EDT_TRYI(upload(c, c->r_cpre, c->cpre));
+  }
+  return EDT_OK;
+}
+
+static bool valid_tuning(const edt_tuning* t) {
+  const bool mb = t->band_budget_mb == 16 || t->band_budget_mb == 32 || t->band_budget_mb == 48 ||
+                  t->band_budget_mb == 96;
+  const bool bc = t->band_cols == 4 || t->band_cols == 8 || t->band_cols == 16;
+  const bool rf = t->refine_shape >= 0 && t->refine_shape <= 3;
+  const bool zc = t->window_ztile == 2 || t->window_ztile == 4 || t->window_ztile == 8;
+  return mb && bc && rf && zc;
+}
+
 int edt_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, void* stream) {
   if (!c || !D || !V) return EDT_EINVAL;
   if (!c->ws) return EDT_ENOMEM_WS;
@@ -772,6 +816,86 @@ int edt_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, voi
   }
   c->last_status = r;
   return r;
+}
+
+int edt_get_tuning(const edt_ctx* c, edt_tuning* o) {
+  if (!c || !o) return EDT_EINVAL;
+  o->band_budget_mb = c->band_budget_mb;
+  o->band_cols = c->tune_bc;
+  o->refine_shape = c->tune_rf;
+  o->window_ztile = c->tune_zc;
+  o->invert_ms = c->tuned_ms;
+  return EDT_OK;
+}
+
+int edt_set_tuning(edt_ctx* c, const edt_tuning* t) {
+  if (!c || !t || !valid_tuning(t)) return EDT_EINVAL;
+  c->band_budget_mb = t->band_budget_mb;
+  c->tune_bc = t->band_cols;
+  c->tune_rf = t->refine_shape;
+  c->tune_zc = t->window_ztile;
+  return apply_tuning(c);
+}
+
+int edt_autotune(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, void* stream, int reps) {
+  if (!c || !D || !V || reps < 1) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
+  if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool mixed = c->cfg.precision == EDT_MIXED;
+  cudaEvent_t e0, e1;
+  EDT_TRY(cudaEventCreate(&e0));
+  EDT_TRY(cudaEventCreate(&e1));
+  auto time_invert = [&](double* best) -> int {
+    *best = 1e300;
+    for (int r = 0; r < reps + 1; ++r) {             // the first call warms up
+      cudaEventRecord(e0, s);
+      const int rc = run_invert(c, D, D_dtype, V, V_dtype, s);
+      if (rc != EDT_OK) return rc;
+      cudaEventRecord(e1, s);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) return cuda_fail(e);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) *best = std::min(*best, double(ms));
+    }
+    return EDT_OK;
+  };
+  edt_tuning cur;
+  edt_get_tuning(c, &cur);
+  int rc = apply_tuning(c);
+  double best = 0.0;
+  if (rc == EDT_OK) rc = time_invert(&best);
+  // one coordinate at a time; candidates that do not apply to this geometry are skipped
+  struct Axis { int* field; std::vector<int> cand; bool on; };
+  std::vector<Axis> axes = {
+      {&cur.band_budget_mb, {16, 32, 48, 96}, c->band_mode},
+      {&cur.band_cols, {4, 8, 16}, c->band_mode},
+      {&cur.refine_shape, {0, 1, 2, 3}, mixed && c->cfg.refine > 0},
+      {&cur.window_ztile, {2, 4, 8}, c->win},
+  };
+  for (Axis& a : axes) {
+    if (rc != EDT_OK || !a.on) continue;
+    const int keep = *a.field;
+    int pick = keep;
+    for (int v : a.cand) {
+      if (v == keep) continue;
+      *a.field = v;
+      if ((rc = edt_set_tuning(c, &cur)) != EDT_OK) break;
+      double ms = 0.0;
+      if ((rc = time_invert(&ms)) != EDT_OK) break;
+      if (ms < best) { best = ms; pick = v; }
+    }
+    *a.field = pick;
+    if (rc == EDT_OK) rc = edt_set_tuning(c, &cur);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != EDT_OK) return rc;
+  c->tuned_ms = best;
+  c->last_stream = s;
+  return run_invert(c, D, D_dtype, V, V_dtype, s);
 }
 
 int edt_set_graph(edt_ctx* c, int on) {

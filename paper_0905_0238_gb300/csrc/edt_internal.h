@@ -81,6 +81,10 @@ struct Dev {
   long long rows_max_sub;       // most rows of any subproblem
   const long long* row_off_mf;  // [nsub][nf + 1]: first row of frequency f within subproblem m
   int fchunk;                   // frequency planes per chunk of the full-plane transform
+  // launch shapes picked by the autotuner (edt_autotune): band-column block width (4, 8,
+  // 16), refinement CTA shape (0: 4 warps x 32 rows, 1: 8 x 32, 2: 4 x 64, 3: 8 x 16),
+  // depths per kernel-row cluster of the window geometry (2, 4, 8)
+  int tune_bc, tune_rf, tune_zc;
   // band-limited transform (mixed path)
   const BandInfo* band;         // [nf]
   const int2* bcol;             // column-pass block table: (f, first band column)
@@ -144,7 +148,6 @@ cudaError_t launch_rhs(const Dev& d, int f0, int nfc, cudaStream_t s);
 cudaError_t launch_gent_static(const Dev& d, cudaStream_t s);
 // Band-limited transform and right-hand sides of one chunk (FP32, mixed path, 32 <= N <= 1024).
 bool band_supported(int N);
-int band_cols_per_block();
 cudaError_t launch_band_chunk(const Dev& d, const BandChunk& ch, const void* D, int D_dtype, cudaStream_t s);
 cudaError_t prepare_band(const Dev& d);
 

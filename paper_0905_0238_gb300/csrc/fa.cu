@@ -339,10 +339,9 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d) {
 // M(k_m; f, j, z) for ZC consecutive depths of one j: a cluster of ZC CTAs, one (j, z) plane
 // each (2D FFT of U_j in shared memory); then every CTA takes a share of the kept rows of
 // (f, j) and reads the ZC depths of each from the cluster's planes (distributed shared
-// memory), so each row's depths z0..z0+ZC-1 are written as one 32-byte store.
-constexpr int ZC = 4;
-
-template <int PX, int PY>
+// memory), so each row's depths z0..z0+ZC-1 are written together (8 ZC contiguous bytes).
+// ZC: depths per cluster, 2, 4 or 8 (the autotuner's choice).
+template <int PX, int PY, int ZC>
 __global__ void __cluster_dims__(1, ZC, 1) __launch_bounds__(plane_threads<PY>())
 fa_mrows_kernel(Dev d, int f, float2 cf) {
   namespace cg = cooperative_groups;
@@ -379,8 +378,9 @@ fa_mrows_kernel(Dev d, int f, float2 cf) {
     for (int k = 0; k < ZC; ++k) v[k] = z0 + k < d.nz ? cf * ps[k][off] : make_float2(0.f, 0.f);
     float2* dst = d.A32 + size_t(ent.y) * d.nzs + z0;
     if (z0 + ZC <= d.nzs) {
-      reinterpret_cast<float4*>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-      reinterpret_cast<float4*>(dst)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+#pragma unroll
+      for (int k = 0; k < ZC; k += 2)
+        reinterpret_cast<float4*>(dst)[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
     } else {
 #pragma unroll
       for (int k = 0; k < ZC; ++k) if (z0 + k < d.nzs) dst[k] = v[k];
@@ -520,7 +520,11 @@ cudaError_t rows_for(const Dev& d, int f, float2 cf, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  fa_mrows_kernel<PX, PY><<<dim3(d.W, (d.nz + ZC - 1) / ZC * ZC), plane_threads<PY>(), sm, s>>>(d, f, cf);
+  const int zc = d.tune_zc;
+  const dim3 gm(d.W, (d.nz + zc - 1) / zc * zc);
+  if (zc == 2) fa_mrows_kernel<PX, PY, 2><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
+  else if (zc == 8) fa_mrows_kernel<PX, PY, 8><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
+  else fa_mrows_kernel<PX, PY, 4><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
   return cudaGetLastError();
 }
 
@@ -543,7 +547,9 @@ cudaError_t prepare_plane() {
   const int sm = int(plane_smem<PX, PY>());
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(fa_gspace_kernel<PX, PY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(fa_drhs_kernel<PX, PY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 

@@ -20,12 +20,11 @@ namespace edt {
 
 namespace {
 
-constexpr int RF_WARPS = 4, RF_ROWS_PER_WARP = 32;
-
 // Z4: float4 loads per lane per table row, i.e. nz <= 64 * Z4 (two depths per float4).
 // FA: window geometry, where row ri of the subproblem is row ri of the assembled kernel
 // table and the second factor is the table's row of ones (all weights 1).
-template <int Z4, bool FA>
+// RF_WARPS warps per CTA, RF_ROWS_PER_WARP rows per warp: the CTA shape (autotuned).
+template <int Z4, bool FA, int RF_WARPS, int RF_ROWS_PER_WARP>
 __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
   constexpr int ZL = 64 * Z4;
   __shared__ float xs[2][ZL];
@@ -128,16 +127,26 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
 
 }  // namespace
 
+template <int W, int R>
+void refine_shape(const Dev& d, cudaStream_t s) {
+  const long long rows_per_cta = W * R;
+  dim3 g(unsigned((std::max(d.rows_max_sub, 1LL) + rows_per_cta - 1) / rows_per_cta), d.nsub);
+  const bool fa = d.geom == EDT_GEOM_WINDOW;
+  const int nz_even = d.nzs;
+  if (nz_even <= 64) fa ? refine_kernel<1, true, W, R><<<g, W * 32, 0, s>>>(d) : refine_kernel<1, false, W, R><<<g, W * 32, 0, s>>>(d);
+  else if (nz_even <= 128) fa ? refine_kernel<2, true, W, R><<<g, W * 32, 0, s>>>(d) : refine_kernel<2, false, W, R><<<g, W * 32, 0, s>>>(d);
+  else fa ? refine_kernel<4, true, W, R><<<g, W * 32, 0, s>>>(d) : refine_kernel<4, false, W, R><<<g, W * 32, 0, s>>>(d);
+}
+
 cudaError_t launch_refine(const Dev& d, cudaStream_t s) {
   // table rows have an even stride (nzs), so 16-byte loads are aligned; the padding
   // element of an odd nz is zero and meets x = 0
-  const long long rows_per_cta = RF_WARPS * RF_ROWS_PER_WARP;
-  const int nz_even = d.nzs;
-  dim3 g(unsigned((std::max(d.rows_max_sub, 1LL) + rows_per_cta - 1) / rows_per_cta), d.nsub);
-  const bool fa = d.geom == EDT_GEOM_WINDOW;
-  if (nz_even <= 64) fa ? refine_kernel<1, true><<<g, RF_WARPS * 32, 0, s>>>(d) : refine_kernel<1, false><<<g, RF_WARPS * 32, 0, s>>>(d);
-  else if (nz_even <= 128) fa ? refine_kernel<2, true><<<g, RF_WARPS * 32, 0, s>>>(d) : refine_kernel<2, false><<<g, RF_WARPS * 32, 0, s>>>(d);
-  else fa ? refine_kernel<4, true><<<g, RF_WARPS * 32, 0, s>>>(d) : refine_kernel<4, false><<<g, RF_WARPS * 32, 0, s>>>(d);
+  switch (d.tune_rf) {
+    case 1: refine_shape<8, 32>(d, s); break;
+    case 2: refine_shape<4, 64>(d, s); break;
+    case 3: refine_shape<8, 16>(d, s); break;
+    default: refine_shape<4, 32>(d, s); break;
+  }
   return cudaGetLastError();
 }
 

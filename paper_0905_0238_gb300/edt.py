@@ -47,6 +47,13 @@ class edt_stats(C.Structure):
     ]
 
 
+class edt_tuning(C.Structure):
+    _fields_ = [
+        ("band_budget_mb", C.c_int), ("band_cols", C.c_int), ("refine_shape", C.c_int),
+        ("window_ztile", C.c_int), ("invert_ms", C.c_double),
+    ]
+
+
 class EdtError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = _lib().edt_strerror(code).decode()
@@ -82,6 +89,9 @@ def _lib() -> C.CDLL:
         L.edt_get_stats.argtypes = [vp, C.POINTER(edt_stats)]
         L.edt_set_profiling.argtypes = [vp, i]
         L.edt_set_graph.argtypes = [vp, i]
+        L.edt_autotune.argtypes = [vp, vp, i, vp, i, vp, i]
+        L.edt_get_tuning.argtypes = [vp, C.POINTER(edt_tuning)]
+        L.edt_set_tuning.argtypes = [vp, C.POINTER(edt_tuning)]
         L.edt_read_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_char_p), i,
                                        C.POINTER(i)]
         L.edt_strerror.argtypes = [i]
@@ -92,7 +102,7 @@ def _lib() -> C.CDLL:
         for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
                      "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
-                     "edt_set_graph"):
+                     "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning"):
             getattr(L, name).restype = i
         _LIB = L
     return _LIB
@@ -165,6 +175,21 @@ def edt_get_stats(ctx) -> edt_stats:
     st = edt_stats()
     _check(_lib().edt_get_stats(ctx, C.byref(st)), "edt_get_stats")
     return st
+
+
+def edt_autotune(ctx, D_ptr: int, D_dtype: int, V_ptr: int, V_dtype: int, stream: int, reps: int = 2):
+    _check(_lib().edt_autotune(ctx, C.c_void_p(D_ptr), D_dtype, C.c_void_p(V_ptr), V_dtype,
+                               C.c_void_p(stream), reps), "edt_autotune")
+
+
+def edt_get_tuning(ctx) -> edt_tuning:
+    t = edt_tuning()
+    _check(_lib().edt_get_tuning(ctx, C.byref(t)), "edt_get_tuning")
+    return t
+
+
+def edt_set_tuning(ctx, t: edt_tuning):
+    _check(_lib().edt_set_tuning(ctx, C.byref(t)), "edt_set_tuning")
 
 
 def edt_set_graph(ctx, on: bool):
@@ -343,6 +368,25 @@ class Solver:
 
     def set_graph(self, on=True):
         edt_set_graph(self.ctx, on)
+
+    def autotune(self, D, out=None, reps=2):
+        """Pick the fastest launch shapes on data D (see edt_autotune); returns the tuning."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty(self.cfg.model_shape(), device=self.device, dtype=torch.float64)
+        edt_autotune(self.ctx, D.data_ptr(), self._cdtype(D), out.data_ptr(), self._rdtype(out),
+                     self._stream(), reps)
+        return self.tuning()
+
+    def tuning(self):
+        t = edt_get_tuning(self.ctx)
+        return {k: getattr(t, k) for k, _ in edt_tuning._fields_}
+
+    def set_tuning(self, **kw):
+        t = edt_get_tuning(self.ctx)
+        for k, v in kw.items():
+            setattr(t, k, v)
+        edt_set_tuning(self.ctx, t)
 
     def set_profiling(self, on=True):
         edt_set_profiling(self.ctx, on)

@@ -91,3 +91,37 @@ def test_host_row_plan_matches_oracle_cut(name):
         else:
             # reciprocal pairs merge: at least half the rows remain, at most all of them
             assert st.rows_total / 2 <= st.rows_solved < st.rows_total
+
+
+def test_tuning_is_validated_and_kept_without_gpu():
+    """Launch shapes: defaults, a valid change is kept, invalid values are rejected."""
+    import numpy as np
+    from paper_0905_0238_gb300 import edt
+    import synth
+    wl = synth.preset("production_2d")
+    dp = ctypes.POINTER(ctypes.c_double)
+    fr = np.ascontiguousarray(wl.freq_hz); tp = np.ascontiguousarray(wl.layer_top)
+    vl = np.ascontiguousarray(wl.layer_vel)
+    cfg = edt.edt_config(nx=wl.nx, dx=wl.dx, nz=wl.nz, dz=wl.dz, z0=wl.z0, nfreq=len(fr),
+                         freq_hz=fr.ctypes.data_as(dp), eps=wl.eps, nlayer=len(tp),
+                         layer_top_m=tp.ctypes.data_as(dp), layer_vel_mps=vl.ctypes.data_as(dp),
+                         precision=edt.EDT_MIXED, passes=3, refine=1, alpha=wl.alpha,
+                         cutoff=wl.cutoff, fold=1)
+    ctx, ws0 = edt.edt_create(cfg)
+    t = edt.edt_get_tuning(ctx)
+    assert (t.band_budget_mb, t.band_cols, t.refine_shape, t.window_ztile) == (48, 8, 0, 4)
+    st0 = edt.edt_get_stats(ctx)
+    t.band_budget_mb, t.band_cols, t.refine_shape = 16, 4, 2
+    edt.edt_set_tuning(ctx, t)
+    t2 = edt.edt_get_tuning(ctx)
+    assert (t2.band_budget_mb, t2.band_cols, t2.refine_shape) == (16, 4, 2)
+    st = edt.edt_get_stats(ctx)
+    assert st.workspace_bytes == st0.workspace_bytes       # sized for every candidate
+    assert st.freq_chunk <= st0.freq_chunk                 # smaller budget, smaller chunks
+    for field, bad in (("band_budget_mb", 20), ("band_cols", 6), ("refine_shape", 4), ("window_ztile", 3)):
+        tb = edt.edt_get_tuning(ctx)
+        setattr(tb, field, bad)
+        with pytest.raises(edt.EdtError) as ei:
+            edt.edt_set_tuning(ctx, tb)
+        assert ei.value.code == edt.EDT_EINVAL
+    edt.edt_destroy(ctx)
