@@ -57,6 +57,9 @@
  *   - The caller owns every input/output buffer and the device workspace; nothing is
  *     allocated on the device after edt_create (edt_invert is safe to capture in a graph
  *     once edt_set_workspace has run).  edt_create allocates host memory only.
+ *   - edt_invert forks one internal stream (created by edt_set_workspace) from `stream` for
+ *     the depth march, which overlaps the data transform, and joins it back before the
+ *     Gram; to the caller the call is ordered on `stream` as a whole.
  *   - Errors are negative return codes (below); no exception crosses the ABI.  A context
  *     must not be used by two threads at once.
  */
@@ -166,6 +169,9 @@ typedef struct {
                                    1 = 8 x 32, 2 = 4 x 64, 3 = 8 x 16; default 0           */
   int window_ztile;             /* window geometry: depths per kernel-row cluster [2, 4, 8];
                                    default 4                                                */
+  int overlap;                  /* 1: depth march (and window kernel rows) on the internal
+                                   stream, concurrent with the data transform; 0: in
+                                   sequence on the caller's stream [0, 1]; default 1        */
   double invert_ms;             /* edt_invert time with these shapes when the autotuner
                                    chose them (0 if never tuned)                           */
 } edt_tuning;
@@ -258,8 +264,9 @@ int edt_row_counts(const edt_ctx* ctx, long long* counts);
 int edt_get_stats(edt_ctx* ctx, edt_stats* out);
 
 /* Per-stage device timing.  With profiling on, every edt_invert (up to 256 calls between
- * reads) records CUDA events
- * around its stages; edt_read_profile synchronises and returns the summed milliseconds
+ * reads) records CUDA events at the beginning and end of each stage on the stream the stage
+ * runs on (the depth march overlaps the data transform, so the stage times may add up to
+ * more than the call); edt_read_profile synchronises and returns the summed milliseconds
  * per stage since the last reset (names[i] static strings), then resets.
  * Returns the number of stages written (<= max_stages), or a negative code. */
 int edt_set_profiling(edt_ctx* ctx, int on);

@@ -64,7 +64,7 @@ struct edt_ctx {
   size_t band_ymax = 0, band_xmax = 0;   // complex elements of the largest chunk's Y and Xc
   int band_maxplanes = 0;
   // launch shapes (autotuned) and the workspace maxima over their candidates
-  int band_budget_mb = 48, tune_bc = 8, tune_rf = 0, tune_zc = 4;
+  int band_budget_mb = 48, tune_bc = 8, tune_rf = 0, tune_zc = 4, tune_ov = 1;
   size_t ws_band_elems = 0, ws_bcol = 0, ws_cpre = 0;
   double tuned_ms = 0.0;
   std::vector<long long> counts_cut;
@@ -92,8 +92,12 @@ struct edt_ctx {
   cudaStream_t g_s = nullptr;
   // profiling
   bool prof = false;
-  static constexpr int NSTAGE = 10;       // marks; NSTAGE - 1 timed stages
-  std::vector<cudaEvent_t> ev;   // [calls][NSTAGE + 1]
+  static constexpr int NSTAGE = 9;        // timed stages
+  std::vector<cudaEvent_t> ev;   // [calls][NSTAGE][begin, end]
+  // auxiliary stream of edt_invert: the depth march (and the window geometry's kernel rows)
+  // runs there concurrently with the data transform on the caller's stream
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int prof_calls = 0;
   int prof_used[NSTAGE] = {};
 };
@@ -104,7 +108,7 @@ constexpr int kProfCalls = 256;   // calls whose stage events are kept between r
 
 const char* kStageNames[edt_ctx::NSTAGE] = {"green", "kernel_rows", "transform_rhs", "trace_reset",
                                             "gram", "gram_reduce", "cholesky", "refine",
-                                            "inverse", "unused"};
+                                            "inverse"};
 
 int validate(const edt_config* c) {
   if (!c) return EDT_EINVAL;
@@ -597,9 +601,10 @@ int upload(edt_ctx* c, const Region& r, const std::vector<T>& v) {
 #define EDT_TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return cuda_fail(_e); } while (0)
 #define EDT_TRYI(x) do { int _r = (x); if (_r != EDT_OK) return _r; } while (0)
 
-void prof_mark(edt_ctx* c, int stage, cudaStream_t s) {
+// begin (end = 0) or end (end = 1) of a stage, recorded on the stream the stage runs on
+void prof_ev(edt_ctx* c, int stage, int end, cudaStream_t s) {
   if (!c->prof || c->prof_calls >= kProfCalls) return;
-  cudaEventRecord(c->ev[size_t(c->prof_calls) * (edt_ctx::NSTAGE + 1) + stage], s);
+  cudaEventRecord(c->ev[(size_t(c->prof_calls) * edt_ctx::NSTAGE + stage) * 2 + end], s);
   c->prof_used[stage] = 1;
 }
 
@@ -639,26 +644,44 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
   c->last_stream = s;
-  prof_mark(c, 0, s);
-  EDT_TRY(launch_green(d, s, mixed ? GREEN_G32 : GREEN_G64));
-  prof_mark(c, 1, s);
-  EDT_TRYI(kernel_rows(c, s));
-  prof_mark(c, 2, s);
+  // fork: the depth march (FP64-bound) and, for the window geometry, the kernel rows it
+  // feeds run on the auxiliary stream while the data transform (FP32 and memory) runs on s
+  const bool ov = c->tune_ov != 0;
+  cudaStream_t sg = ov ? c->aux : s;
+  if (ov) {
+    EDT_TRY(cudaEventRecord(c->ev_fork, s));
+    EDT_TRY(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+  }
+  prof_ev(c, 0, 0, sg);
+  EDT_TRY(launch_green(d, sg, mixed ? GREEN_G32 : GREEN_G64));
+  prof_ev(c, 0, 1, sg);
+  prof_ev(c, 1, 0, sg);
+  EDT_TRYI(kernel_rows(c, sg));
+  prof_ev(c, 1, 1, sg);
+  if (ov) EDT_TRY(cudaEventRecord(c->ev_join, c->aux));
+  prof_ev(c, 2, 0, s);
   EDT_TRYI(transform_rhs(c, D, D_dtype, s));
-  prof_mark(c, 3, s);
+  prof_ev(c, 2, 1, s);
+  if (ov) EDT_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
+  prof_ev(c, 3, 0, s);
   if (mixed) EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
-  prof_mark(c, 4, s);
+  prof_ev(c, 3, 1, s);
+  prof_ev(c, 4, 0, s);
   if (mixed) {
     EDT_TRY(launch_gram_tc(d, s));
-    prof_mark(c, 5, s);
+    prof_ev(c, 4, 1, s);
+    prof_ev(c, 5, 0, s);
     EDT_TRY(launch_gram_reduce(d, s));
   } else {
     EDT_TRY(launch_gram_f64(d, s));
-    prof_mark(c, 5, s);
+    prof_ev(c, 4, 1, s);
+    prof_ev(c, 5, 0, s);
   }
-  prof_mark(c, 6, s);
+  prof_ev(c, 5, 1, s);
+  prof_ev(c, 6, 0, s);
   EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
-  prof_mark(c, 7, s);
+  prof_ev(c, 6, 1, s);
+  prof_ev(c, 7, 0, s);
   if (mixed) {
     for (int it = 0; it < c->cfg.refine; ++it) {
       EDT_TRY(cudaMemsetAsync(d.r, 0, sizeof(double) * d.nsub * d.nz * 2, s));
@@ -666,10 +689,11 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
       EDT_TRY(launch_refine_update(d, s));
     }
   }
-  prof_mark(c, 8, s);
+  prof_ev(c, 7, 1, s);
+  prof_ev(c, 8, 0, s);
   if (c->win) EDT_TRY(launch_fa_inverse(d, V, V_dtype, s));
   else EDT_TRY(launch_inverse(d, V, V_dtype, s));
-  prof_mark(c, 9, s);
+  prof_ev(c, 8, 1, s);
   if (c->prof && c->prof_calls < kProfCalls) c->prof_calls++;
   return EDT_OK;
 }
@@ -750,6 +774,11 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   if (c->cfg.precision == EDT_MIXED) EDT_TRY(prepare_gram_tc(c->dev));
   if (c->band_mode) EDT_TRY(prepare_band(c->dev));
   if (c->win) EDT_TRY(prepare_fa(c->dev));
+  if (!c->aux) {
+    EDT_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    EDT_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    EDT_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
   EDT_TRY(cudaDeviceSynchronize());
   return EDT_OK;
 }
@@ -783,7 +812,8 @@ static bool valid_tuning(const edt_tuning* t) {
   const bool bc = t->band_cols == 4 || t->band_cols == 8 || t->band_cols == 16;
   const bool rf = t->refine_shape >= 0 && t->refine_shape <= 3;
   const bool zc = t->window_ztile == 2 || t->window_ztile == 4 || t->window_ztile == 8;
-  return mb && bc && rf && zc;
+  const bool ov = t->overlap == 0 || t->overlap == 1;
+  return mb && bc && rf && zc && ov;
 }
 
 int edt_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, void* stream) {
@@ -824,6 +854,7 @@ int edt_get_tuning(const edt_ctx* c, edt_tuning* o) {
   o->band_cols = c->tune_bc;
   o->refine_shape = c->tune_rf;
   o->window_ztile = c->tune_zc;
+  o->overlap = c->tune_ov;
   o->invert_ms = c->tuned_ms;
   return EDT_OK;
 }
@@ -834,6 +865,7 @@ int edt_set_tuning(edt_ctx* c, const edt_tuning* t) {
   c->tune_bc = t->band_cols;
   c->tune_rf = t->refine_shape;
   c->tune_zc = t->window_ztile;
+  c->tune_ov = t->overlap;
   return apply_tuning(c);
 }
 
@@ -874,6 +906,7 @@ int edt_autotune(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, v
       {&cur.band_cols, {4, 8, 16}, c->band_mode},
       {&cur.refine_shape, {0, 1, 2, 3}, mixed && c->cfg.refine > 0},
       {&cur.window_ztile, {2, 4, 8}, c->win},
+      {&cur.overlap, {0, 1}, true},
   };
   for (Axis& a : axes) {
     if (rc != EDT_OK || !a.on) continue;
@@ -1033,7 +1066,7 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
 int edt_set_profiling(edt_ctx* c, int on) {
   if (!c) return EDT_EINVAL;
   if (on && c->ev.empty()) {
-    c->ev.resize(size_t(kProfCalls) * (edt_ctx::NSTAGE + 1));
+    c->ev.resize(size_t(kProfCalls) * edt_ctx::NSTAGE * 2);
     for (auto& e : c->ev) EDT_TRY(cudaEventCreate(&e));
   }
   c->prof = on != 0;
@@ -1044,16 +1077,17 @@ int edt_set_profiling(edt_ctx* c, int on) {
 
 int edt_read_profile(edt_ctx* c, double* ms, const char** names, int max_stages, int* n_calls) {
   if (!c || !ms) return EDT_EINVAL;
-  const int ns = std::min(max_stages, edt_ctx::NSTAGE - 1);
+  const int ns = std::min(max_stages, edt_ctx::NSTAGE);
   for (int i = 0; i < ns; ++i) { ms[i] = 0.0; if (names) names[i] = kStageNames[i]; }
   if (n_calls) *n_calls = c->prof_calls;
   if (c->prof_calls > 0) {
-    const int K = edt_ctx::NSTAGE + 1;
-    EDT_TRY(cudaEventSynchronize(c->ev[size_t(c->prof_calls - 1) * K + (edt_ctx::NSTAGE - 1)]));
+    const int K = edt_ctx::NSTAGE;
+    // the last stage of the last call ends after every other event of that call
+    EDT_TRY(cudaEventSynchronize(c->ev[(size_t(c->prof_calls - 1) * K + (K - 1)) * 2 + 1]));
     for (int call = 0; call < c->prof_calls; ++call)
       for (int i = 0; i < ns; ++i) {
         float t = 0.f;
-        EDT_TRY(cudaEventElapsedTime(&t, c->ev[size_t(call) * K + i], c->ev[size_t(call) * K + i + 1]));
+        EDT_TRY(cudaEventElapsedTime(&t, c->ev[(size_t(call) * K + i) * 2], c->ev[(size_t(call) * K + i) * 2 + 1]));
         ms[i] += t;
       }
   }
@@ -1081,6 +1115,9 @@ void edt_destroy(edt_ctx* c) {
   if (!c) return;
   drop_graph(c);
   for (auto& e : c->ev) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->aux) cudaStreamDestroy(c->aux);
   delete c;
 }
 

@@ -37,6 +37,12 @@ constexpr int C_KAP = 0, C_RHO = 1, C_AMP = 2, C_E = 3, C_EI = 4, C_EH = 5, C_IN
 // FP32 copies for the fast evaluation: kappa.x and kappa.y as (hi, lo) pairs, amp, rho
 constexpr int NCOEF32 = 8;
 
+// coefficient array layout [f][layer][slot][n]: consecutive wavenumbers are adjacent, so the
+// per-(f, n) threads of every kernel below read and write them coalesced
+__device__ __forceinline__ size_t cix(const Dev& d, int f, int n, int j, int k) {
+  return ((size_t(f) * d.nlayer + j) * NCOEF + k) * d.nk + n;
+}
+
 // 1 / b with one real division (|b| is O(1e-3 .. 1e3) for every use here)
 __device__ __forceinline__ double2 cinv(double2 b) {
   const double r = 1.0 / (b.x * b.x + b.y * b.y);
@@ -48,9 +54,9 @@ __global__ void green_layer_kernel(Dev d, int want_steps) {
   const int J = d.nlayer;
   const long long total = (long long)d.nf * d.nk * J;
   if (gid >= total) return;
-  const int j = int(gid % J);
-  const long long fn = gid / J;
-  const int n = int(fn % d.nk), f = int(fn / d.nk);
+  const int n = int(gid % d.nk);                   // wavenumber fastest: coalesced stores
+  const long long fj = gid / d.nk;
+  const int j = int(fj % J), f = int(fj / J);
   const FreqConst fc = d.fc[f];
   const double L = double(d.N) * d.dx;
   const double k = d.kval ? d.kval[n] : 2.0 * M_PI * double(n) / L;
@@ -58,18 +64,18 @@ __global__ void green_layer_kernel(Dev d, int want_steps) {
   const double2 om2 = om * om;
   const double inv_c2 = 1.0 / (d.layer_vel[j] * d.layer_vel[j]);
   const double2 kap = csqrt_upper(cmk(om2.x * inv_c2 - k * k, om2.y * inv_c2));
-  double2* c = d.coef + gid * NCOEF;
-  c[C_KAP] = kap;
+  double2* c = d.coef;
+  c[cix(d, f, n, j, C_KAP)] = kap;
   if (j < J - 1) {
     const double h = d.layer_top[j + 1] - d.layer_top[j];
-    c[C_EH] = cexp(cmk(-kap.y * h, kap.x * h));
+    c[cix(d, f, n, j, C_EH)] = cexp(cmk(-kap.y * h, kap.x * h));
   } else {
-    c[C_EH] = cmk(1.0, 0.0);
+    c[cix(d, f, n, j, C_EH)] = cmk(1.0, 0.0);
   }
   if (want_steps) {
     const double2 E = cexp(cmk(-kap.y * d.dz, kap.x * d.dz));
-    c[C_E] = E;
-    c[C_EI] = cdiv(cmk(1.0, 0.0), E);
+    c[cix(d, f, n, j, C_E)] = E;
+    c[cix(d, f, n, j, C_EI)] = cdiv(cmk(1.0, 0.0), E);
   }
 }
 
@@ -78,34 +84,34 @@ __global__ void green_recursion_kernel(Dev d) {
   const int f = blockIdx.y;
   if (n >= d.nk) return;
   const int J = d.nlayer;
-  double2* c = d.coef + (size_t(f) * d.nk + n) * size_t(J) * NCOEF;
+  double2* c = d.coef;
   const double2 one = cmk(1.0, 0.0);
   // upward recursion for the reflection coefficient of the stack below each interface
   double2 r_next = cmk(0.0, 0.0);
-  c[(J - 1) * NCOEF + C_RHO] = cmk(0.0, 0.0);
-  double2 kn = c[(J - 1) * NCOEF + C_KAP];
+  c[cix(d, f, n, J - 1, C_RHO)] = cmk(0.0, 0.0);
+  double2 kn = c[cix(d, f, n, J - 1, C_KAP)];
   for (int j = J - 2; j >= 0; --j) {
-    const double2 kj = c[j * NCOEF + C_KAP], eh = c[j * NCOEF + C_EH];
+    const double2 kj = c[cix(d, f, n, j, C_KAP)], eh = c[cix(d, f, n, j, C_EH)];
     const double2 inv1r = cinv(one + r_next);             // 1 / (1 + r_{j+1})
     const double2 y = kn * (one - r_next) * inv1r;
     const double2 rho = (kj - y) * cinv(kj + y);
-    c[j * NCOEF + C_RHO] = rho;
-    c[j * NCOEF + C_INV1R] = inv1r;
+    c[cix(d, f, n, j, C_RHO)] = rho;
+    c[cix(d, f, n, j, C_INV1R)] = inv1r;
     r_next = rho * (eh * eh);
     kn = kj;
   }
   // downward recursion for the downgoing amplitude; jump g'(0+) - g'(0-) = -1
-  const double2 k0 = c[C_KAP];
+  const double2 k0 = c[cix(d, f, n, 0, C_KAP)];
   double2 amp = cmk(0.0, 0.5) * cinv(k0);
   for (int j = 0; j < J - 1; ++j) {
-    c[j * NCOEF + C_AMP] = amp;
-    amp = amp * c[j * NCOEF + C_EH] * (one + c[j * NCOEF + C_RHO]) * c[j * NCOEF + C_INV1R];
+    c[cix(d, f, n, j, C_AMP)] = amp;
+    amp = amp * c[cix(d, f, n, j, C_EH)] * (one + c[cix(d, f, n, j, C_RHO)]) * c[cix(d, f, n, j, C_INV1R)];
   }
-  c[(J - 1) * NCOEF + C_AMP] = amp;
+  c[cix(d, f, n, J - 1, C_AMP)] = amp;
   if (d.coef32) {
     float* c32 = d.coef32 + (size_t(f) * d.nk + n) * size_t(J) * NCOEF32;
     for (int j = 0; j < J; ++j) {
-      const double2 kap = c[j * NCOEF + C_KAP], a = c[j * NCOEF + C_AMP], r = c[j * NCOEF + C_RHO];
+      const double2 kap = c[cix(d, f, n, j, C_KAP)], a = c[cix(d, f, n, j, C_AMP)], r = c[cix(d, f, n, j, C_RHO)];
       const float kxh = float(kap.x), kyh = float(kap.y);
       float* o = c32 + j * NCOEF32;
       o[0] = kxh; o[1] = float(kap.x - double(kxh));
@@ -127,7 +133,8 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval64_kernel(Dev d) {
   const int n = n0 + lane;
   const int J = d.nlayer;
   const bool valid = n < d.nk;
-  const double2* c = d.coef + (size_t(f) * d.nk + (valid ? n : 0)) * size_t(J) * NCOEF;
+  const double2* c = d.coef;
+  const int nn0 = valid ? n : 0;
   const double sq = sqrt(d.fc[f].s_abs);
   for (int zc = warp * EV_ZC; zc < d.nz; zc += EV_WARPS * EV_ZC) {
     int cur = -1;
@@ -137,11 +144,11 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval64_kernel(Dev d) {
       const int l = d.z_layer[z];
       if (l != cur) {             // anchor: direct evaluation at layer entry / chunk start
         cur = l;
-        const double2 kap = c[l * NCOEF + C_KAP];
-        rho = c[l * NCOEF + C_RHO];
-        amp = c[l * NCOEF + C_AMP];
-        E = c[l * NCOEF + C_E];
-        Ei = c[l * NCOEF + C_EI];
+        const double2 kap = c[cix(d, f, nn0, l, C_KAP)];
+        rho = c[cix(d, f, nn0, l, C_RHO)];
+        amp = c[cix(d, f, nn0, l, C_AMP)];
+        E = c[cix(d, f, nn0, l, C_E)];
+        Ei = c[cix(d, f, nn0, l, C_EI)];
         const double off = d.z_off[z];
         e1 = cexp(cmk(-kap.y * off, kap.x * off));
         if (l < J - 1) {

@@ -50,7 +50,7 @@ class edt_stats(C.Structure):
 class edt_tuning(C.Structure):
     _fields_ = [
         ("band_budget_mb", C.c_int), ("band_cols", C.c_int), ("refine_shape", C.c_int),
-        ("window_ztile", C.c_int), ("invert_ms", C.c_double),
+        ("window_ztile", C.c_int), ("overlap", C.c_int), ("invert_ms", C.c_double),
     ]
 
 

@@ -109,7 +109,7 @@ def test_tuning_is_validated_and_kept_without_gpu():
                          cutoff=wl.cutoff, fold=1)
     ctx, ws0 = edt.edt_create(cfg)
     t = edt.edt_get_tuning(ctx)
-    assert (t.band_budget_mb, t.band_cols, t.refine_shape, t.window_ztile) == (48, 8, 0, 4)
+    assert (t.band_budget_mb, t.band_cols, t.refine_shape, t.window_ztile, t.overlap) == (48, 8, 0, 4, 1)
     st0 = edt.edt_get_stats(ctx)
     t.band_budget_mb, t.band_cols, t.refine_shape = 16, 4, 2
     edt.edt_set_tuning(ctx, t)
@@ -118,7 +118,8 @@ def test_tuning_is_validated_and_kept_without_gpu():
     st = edt.edt_get_stats(ctx)
     assert st.workspace_bytes == st0.workspace_bytes       # sized for every candidate
     assert st.freq_chunk <= st0.freq_chunk                 # smaller budget, smaller chunks
-    for field, bad in (("band_budget_mb", 20), ("band_cols", 6), ("refine_shape", 4), ("window_ztile", 3)):
+    for field, bad in (("band_budget_mb", 20), ("band_cols", 6), ("refine_shape", 4), ("window_ztile", 3),
+                       ("overlap", 2)):
         tb = edt.edt_get_tuning(ctx)
         setattr(tb, field, bad)
         with pytest.raises(edt.EdtError) as ei:

@@ -26,9 +26,9 @@ def line_case():
     return wl, np.ascontiguousarray(D.astype(np.complex64)), V_or
 
 
-@pytest.mark.parametrize("shape", [dict(band_budget_mb=16, band_cols=4, refine_shape=1),
-                                   dict(band_budget_mb=32, band_cols=16, refine_shape=2),
-                                   dict(band_budget_mb=96, band_cols=8, refine_shape=3)])
+@pytest.mark.parametrize("shape", [dict(band_budget_mb=16, band_cols=4, refine_shape=1, overlap=0),
+                                   dict(band_budget_mb=32, band_cols=16, refine_shape=2, overlap=1),
+                                   dict(band_budget_mb=96, band_cols=8, refine_shape=3, overlap=0)])
 def test_line_launch_shapes_match_oracle(line_case, shape):
     from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED
     wl, D, V_or = line_case
