@@ -182,11 +182,20 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
     }
     __syncthreads();
     if (fail) break;
+    // the FP32 copy of the factor (refinement's correction solves) is written as each part
+    // of L is final; its upper triangle is never read
+    float* L32 = d.L32 ? d.L32 + size_t(m) * n * n : nullptr;
     for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
       int i = e / kb, j = e - i * kb;
-      if (j <= i) A[size_t(k0 + i) * n + k0 + j] = sD[i * LDP + j];
+      if (j <= i) {
+        A[size_t(k0 + i) * n + k0 + j] = sD[i * LDP + j];
+        if (L32) L32[size_t(k0 + i) * n + k0 + j] = float(sD[i * LDP + j]);
+      }
     }
-    for (int j = threadIdx.x; j < kb; j += blockDim.x) d.dinv[size_t(m) * n + k0 + j] = sInv[j];
+    for (int j = threadIdx.x; j < kb; j += blockDim.x) {
+      d.dinv[size_t(m) * n + k0 + j] = sInv[j];
+      if (L32) d.dinv32[size_t(m) * n + k0 + j] = float(sInv[j]);
+    }
     const int t0 = k0 + kb, t = n - t0;
     // panel: row i of the block column solves x L_kk^T = a
     for (int i = threadIdx.x; i < t; i += blockDim.x) {
@@ -206,6 +215,12 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
 #pragma unroll
       for (int j = 0; j < NB; ++j)
         if (j < kb) { Ai[j] = x[j]; sP[i * LDP + j] = x[j]; }
+      if (L32) {
+        float* Li = L32 + size_t(t0 + i) * n + k0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+          if (j < kb) Li[j] = float(x[j]);
+      }
     }
     __syncthreads();
     // trailing lower triangle: A[i][j] -= sum_l P[i][l] P[j][l], 4x4 tiles
@@ -300,6 +315,103 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
   if (threadIdx.x == 0) d.status[m] = bad ? EDT_ENONFINITE : EDT_OK;
 }
 
+// Solve L L^T y = sb in FP32 with the rounded factor (the refinement's correction: the
+// residual r - lam x carries the FP64 information, the correction only needs the factor to
+// a few digits; cond(G + lam I) * 2^-24 bounds its relative error).  Same blocking as the
+// FP64 solve.
+__device__ void chol_solve32_2rhs(const float* A, const float* dinv, int n, float* sb, float (*sL)[LDP]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nblk = (n + NB - 1) / NB;
+  for (int bk = 0; bk < nblk; ++bk) {
+    const int k0 = bk * NB, kb = min(NB, n - k0);
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int i = e / kb, j = e - i * kb;
+      sL[i][j] = j <= i ? A[size_t(k0 + i) * n + k0 + j] : 0.f;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float v0 = lane < kb ? sb[(k0 + lane) * 2] : 0.f, v1 = lane < kb ? sb[(k0 + lane) * 2 + 1] : 0.f;
+      for (int j = 0; j < kb; ++j) {
+        const float ij = dinv[k0 + j];
+        const float y0 = __shfl_sync(0xffffffffu, v0, j) * ij;
+        const float y1 = __shfl_sync(0xffffffffu, v1, j) * ij;
+        if (lane == j) { v0 = y0; v1 = y1; }
+        if (lane > j && lane < kb) { v0 = fmaf(-sL[lane][j], y0, v0); v1 = fmaf(-sL[lane][j], y1, v1); }
+      }
+      if (lane < kb) { sb[(k0 + lane) * 2] = v0; sb[(k0 + lane) * 2 + 1] = v1; }
+    }
+    __syncthreads();
+    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {
+      float s0 = sb[i * 2], s1 = sb[i * 2 + 1];
+      const float* Ai = A + size_t(i) * n + k0;
+      for (int l = 0; l < kb; ++l) {
+        const float a = Ai[l];
+        s0 = fmaf(-a, sb[(k0 + l) * 2], s0);
+        s1 = fmaf(-a, sb[(k0 + l) * 2 + 1], s1);
+      }
+      sb[i * 2] = s0; sb[i * 2 + 1] = s1;
+    }
+    __syncthreads();
+  }
+  for (int bk = nblk - 1; bk >= 0; --bk) {
+    const int k0 = bk * NB, kb = min(NB, n - k0);
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int i = e / kb, j = e - i * kb;
+      sL[i][j] = j <= i ? A[size_t(k0 + i) * n + k0 + j] : 0.f;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float v0 = lane < kb ? sb[(k0 + lane) * 2] : 0.f, v1 = lane < kb ? sb[(k0 + lane) * 2 + 1] : 0.f;
+      for (int j = kb - 1; j >= 0; --j) {
+        const float ij = dinv[k0 + j];
+        const float x0 = __shfl_sync(0xffffffffu, v0, j) * ij;
+        const float x1 = __shfl_sync(0xffffffffu, v1, j) * ij;
+        if (lane == j) { v0 = x0; v1 = x1; }
+        if (lane < j) { v0 = fmaf(-sL[j][lane], x0, v0); v1 = fmaf(-sL[j][lane], x1, v1); }
+      }
+      if (lane < kb) { sb[(k0 + lane) * 2] = v0; sb[(k0 + lane) * 2 + 1] = v1; }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k0; i += blockDim.x) {
+      float s0 = sb[i * 2], s1 = sb[i * 2 + 1];
+      for (int l = 0; l < kb; ++l) {
+        const float a = A[size_t(k0 + l) * n + i];
+        s0 = fmaf(-a, sb[(k0 + l) * 2], s0);
+        s1 = fmaf(-a, sb[(k0 + l) * 2 + 1], s1);
+      }
+      sb[i * 2] = s0; sb[i * 2 + 1] = s1;
+    }
+    __syncthreads();
+  }
+}
+
+// Refinement update with the FP32 factor: x += (LL^T)^-1 (r - lam x); r - lam x in FP64,
+// rounded to FP32 for the solve, the correction added to x in FP64.
+__global__ void __launch_bounds__(256) chol_refine32_kernel(Dev d) {
+  extern __shared__ __align__(16) float sb32[];
+  __shared__ float sL[NB][LDP];
+  const int m = blockIdx.x, n = d.nz;
+  double* xo = d.x + size_t(m) * n * 2;
+  if (d.row_off[m + 1] == d.row_off[m] || d.status[m] != EDT_OK) {
+    if (d.status[m] != EDT_OK)
+      for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    return;
+  }
+  const double lam = d.trace[m];
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
+    sb32[i] = float(d.r[size_t(m) * n * 2 + i] - lam * xo[i]);
+  __syncthreads();
+  chol_solve32_2rhs(d.L32 + size_t(m) * n * n, d.dinv32 + size_t(m) * n, n, sb32, sL);
+  bool bad = false;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+    const double v = xo[i] + double(sb32[i]);
+    xo[i] = v;
+    if (!isfinite(v)) bad = true;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0 && bad) d.status[m] = EDT_ENONFINITE;
+}
+
 // mode 0: x = (LL^T)^-1 b; mode 1 (refinement): x += (LL^T)^-1 (r - lam x).
 __global__ void __launch_bounds__(256) chol_solve_kernel(Dev d, int mode) {
   extern __shared__ __align__(16) double sb[];
@@ -362,7 +474,8 @@ cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
 }
 
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s) {
-  chol_solve_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 1);
+  if (d.L32) chol_refine32_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(float), s>>>(d);
+  else chol_solve_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 1);
   return cudaGetLastError();
 }
 

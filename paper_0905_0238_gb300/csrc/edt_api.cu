@@ -79,7 +79,7 @@ struct edt_ctx {
   void* ws = nullptr;
   Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
-      r_dinv, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
+      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
   Dev dev{};
   cudaStream_t last_stream = nullptr;
   int last_status = EDT_OK;
@@ -508,6 +508,8 @@ void layout(edt_ctx* c) {
   take(c->r_gpart, mixed ? size_t(c->nslot) * TC_M * tc_cols(c->nz) * sizeof(float) : 0);
   take(c->r_G, ns * nz * nz * sizeof(double));
   take(c->r_dinv, ns * nz * sizeof(double));
+  take(c->r_L32, mixed && c->cfg.refine > 0 ? ns * nz * nz * sizeof(float) : 0);
+  take(c->r_dinv32, mixed && c->cfg.refine > 0 ? ns * nz * sizeof(float) : 0);
   take(c->r_b, ns * nz * 2 * sizeof(double));
   take(c->r_tr, ns * sizeof(double));
   take(c->r_x, ns * nz * 2 * sizeof(double));
@@ -581,6 +583,8 @@ void bind(edt_ctx* c) {
   d.gpart = c->r_gpart.bytes ? at<float*>(c, c->r_gpart) : nullptr;
   d.G = at<double*>(c, c->r_G);
   d.dinv = at<double*>(c, c->r_dinv);
+  d.L32 = c->r_L32.bytes ? at<float*>(c, c->r_L32) : nullptr;
+  d.dinv32 = c->r_dinv32.bytes ? at<float*>(c, c->r_dinv32) : nullptr;
   d.b = at<double*>(c, c->r_b);
   d.trace = at<double*>(c, c->r_tr);
   d.x = at<double*>(c, c->r_x);

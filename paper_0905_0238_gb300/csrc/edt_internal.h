@@ -123,6 +123,9 @@ struct Dev {
   float* gpart;                 // tensor-core Gram partial tiles [nslot][TM_COLS * 128]
   double* G;                    // [nsub][nz][nz]  Gram, then its Cholesky factor
   double* dinv;                 // [nsub][nz]      1 / diagonal of the factor
+  float* L32;                   // [nsub][nz][nz]  FP32 copy of the factor (mixed path: the
+                                //                 refinement's correction solves)
+  float* dinv32;                // [nsub][nz]
   double* b;                    // [nsub][nz][2]
   double* trace;                // [nsub]
   double* x;                    // [nsub][nz][2]
