@@ -157,25 +157,29 @@ template <int R, int SG, class Addr>
 __device__ __forceinline__ void group_fft(float2* s, const Addr& addr, int t, const float2* tw,
                                           const float2* src = nullptr) {
   const unsigned gm = 0xffffu << (threadIdx.x & 16);         // this half-warp
+  // slot addresses are affine along each pass (the layout's skew steps at multiples of 16):
+  // pass 1 reads slots 16 a + t, pass 2 reads 16 k1 + 2 i + h
+  const int a1 = addr(t), s1 = addr(16) - addr(0), s2 = addr(2) - addr(0);
   float2 v[R];
   if (src) {
 #pragma unroll
     for (int a = 0; a < R; ++a) v[a] = src[16 * a + t];
   } else {
 #pragma unroll
-    for (int a = 0; a < R; ++a) v[a] = s[addr(16 * a + t)];
+    for (int a = 0; a < R; ++a) v[a] = s[a1 + a * s1];
   }
   Dft<R, SG>::run(v);
 #pragma unroll
   for (int k1 = 1; k1 < R; ++k1) v[k1] = v[k1] * tw_sg<SG>(tw[t * k1]);
 #pragma unroll
-  for (int k1 = 0; k1 < R; ++k1) s[addr(16 * k1 + t)] = v[k1];
+  for (int k1 = 0; k1 < R; ++k1) s[a1 + k1 * s1] = v[k1];
   __syncwarp(gm);
   const int k1 = t >> 1, h = t & 1;
   const bool act = k1 < R;
+  const int a2 = addr(16 * (act ? k1 : 0) + h);
   float2 u[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) u[i] = act ? s[addr(16 * k1 + 2 * i + h)] : make_float2(0.f, 0.f);
+  for (int i = 0; i < 8; ++i) u[i] = act ? s[a2 + i * s2] : make_float2(0.f, 0.f);
   dft8<SG>(u);
   if (h) {
 #pragma unroll
