@@ -478,7 +478,7 @@ void layout(edt_ctx* c) {
   take(c->r_fjoff, std::max<size_t>(c->fj_off.size(), 1) * sizeof(int));
   take(c->r_fjent, std::max<size_t>(c->fj_ent.size(), 1) * sizeof(int2));
   take(c->r_Gs, c->win ? nz * nxy * sizeof(float2) : 0);
-  take(c->r_U, c->win ? W * nz * nxy * sizeof(float2) : 0);
+  take(c->r_U, c->win ? W * nz * (size_t(c->ny / 2 + 1) * N) * sizeof(float2) : 0);
   take(c->r_Dw, c->win ? nf * W * nxy * sizeof(float2) : 0);
   take(c->r_A32, c->win ? (R + 1) * nzs * sizeof(float2) : 0);
   take(c->r_tw64, (N / 2) * sizeof(double2));

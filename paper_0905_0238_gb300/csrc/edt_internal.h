@@ -100,7 +100,8 @@ struct Dev {
   const int* fj_off;            // [nf * W + 1] entry ranges of the (f, j) lists
   const int2* fj_ent;           // (midpoint index, row) of every row, grouped by (f, j)
   float2* Gs;                   // [nz][ny][nx] G(y, z) of one frequency
-  float2* U;                    // [W][nz][ny][nx] window products of one frequency
+  float2* U;                    // [W][nz][ny/2 + 1][nx] window products of one frequency
+                                //   (centrosymmetric in y: rows 0..ny/2 stored)
   float2* Dw;                   // [nf][W][ny][nx] window-transformed data
   float2* A32;                  // [rows + 1][nzs] kernel rows, then a row of ones
   long long ones_row;           // index of the ones row in A32

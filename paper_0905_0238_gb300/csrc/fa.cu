@@ -153,17 +153,20 @@ __device__ __forceinline__ void Dft<16, SG>::run(float2 (&a)[16]) {
 // odd t (the odd half times W_16^k2), exchanged by one shuffle per value, and writes
 // X[k1 + R k2] in natural order.  tw: W_N^e (sign -1) for e < N.  A group is a half-warp.
 // src: where pass 1 reads the line (null: the shared slots themselves).
+// src: where pass 1 reads the line (null: the shared slots themselves); rev: read it
+// mirrored, element i at src[(-i) mod N].
 template <int R, int SG, class Addr>
 __device__ __forceinline__ void group_fft(float2* s, const Addr& addr, int t, const float2* tw,
-                                          const float2* src = nullptr) {
+                                          const float2* src = nullptr, bool rev = false) {
   const unsigned gm = 0xffffu << (threadIdx.x & 16);         // this half-warp
   // slot addresses are affine along each pass (the layout's skew steps at multiples of 16):
   // pass 1 reads slots 16 a + t, pass 2 reads 16 k1 + 2 i + h
   const int a1 = addr(t), s1 = addr(16) - addr(0), s2 = addr(2) - addr(0);
   float2 v[R];
   if (src) {
+    constexpr int N = 16 * R;
 #pragma unroll
-    for (int a = 0; a < R; ++a) v[a] = src[16 * a + t];
+    for (int a = 0; a < R; ++a) v[a] = src[rev ? ((N - 16 * a - t) & (N - 1)) : 16 * a + t];
   } else {
 #pragma unroll
     for (int a = 0; a < R; ++a) v[a] = s[a1 + a * s1];
@@ -211,18 +214,22 @@ struct ColAddr {
   __device__ __forceinline__ int operator()(int i) const { return paddr(i, c, ld); }
 };
 
-// gsrc: a row-major [NY][NX] plane in global memory that the row pass reads directly (its
-// loads then overlap other groups' arithmetic); null: the plane is already in s.
+// gsrc: a row-major plane in global memory that the row pass reads directly (its loads then
+// overlap other groups' arithmetic); null: the plane is already in s.  grows: rows stored in
+// gsrc; a centrosymmetric plane (P(-y) = P(y)) keeps rows 0..NY/2 only and row r > NY/2 is
+// row NY - r mirrored.
 template <int PX, int PY, int SG>
 __device__ void plane_fft2(float2* s, int ld, const float2* tw, const float2* tws,
-                           const float2* gsrc = nullptr) {
+                           const float2* gsrc = nullptr, int grows = 1 << 30) {
   constexpr int NX = 32 * PX, NY = PY > 0 ? 32 * PY : 1;
   if constexpr (PY > 0) {
     // square plane: one group of 16 threads per line, rows then columns
     constexpr int R = NX / 16;
     const int t = threadIdx.x & 15, grp = threadIdx.x >> 4, ng = blockDim.x >> 4;
-    for (int r = grp; r < NY; r += ng)
-      group_fft<R, SG>(s, RowAddr{r, ld}, t, tws, gsrc ? gsrc + size_t(r) * NX : nullptr);
+    for (int r = grp; r < NY; r += ng) {
+      const bool mir = r >= grows;
+      group_fft<R, SG>(s, RowAddr{r, ld}, t, tws, gsrc ? gsrc + size_t(mir ? NY - r : r) * NX : nullptr, mir);
+    }
     __syncthreads();
     for (int c = grp; c < NX; c += ng) group_fft<R, SG>(s, ColAddr{c, ld}, t, tws);
     __syncthreads();
@@ -287,6 +294,7 @@ template <int WX, int WY> struct ExLayout {
 };
 
 // U_j(y, z) for one frequency: CTA per (y row, z), window transform per y in registers.
+// G is even, so U_j(-y) = U_j(y): only the rows y_y = 0..ny/2 are formed and stored.
 template <int WX, int WY>
 __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d) {
   using L = ExLayout<WX, WY>;
@@ -333,7 +341,7 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d) {
 #pragma unroll
       for (int jy = 0; jy < WY; ++jy) {
         const float2 v = neg_if(b[jy], WY >= 2 && ((jy & 1) != alt_sign_end(WY)));
-        d.U[(size_t(jy * WX + jx) * d.nz + z) * d.nxy + size_t(yy) * nx + x] = v;
+        d.U[((size_t(jy * WX + jx) * d.nz + z) * (ny / 2 + 1) + yy) * nx + x] = v;
       }
     }
     __syncthreads();
@@ -356,11 +364,12 @@ fa_mrows_kernel(Dev d, int f, float2 cf) {
   cg::cluster_group cluster = cg::this_cluster();
   const int j = blockIdx.x, z = blockIdx.y, rank = int(cluster.block_rank()), z0 = z - rank;
   if (z < d.nz) {                        // every CTA reaches both cluster barriers below
-    const float2* P = d.U + (size_t(j) * d.nz + z) * (NX * NY);
+    constexpr int NYH = NY / 2 + 1;      // stored rows of the centrosymmetric plane
+    const float2* P = d.U + (size_t(j) * d.nz + z) * (NYH * NX);
     plane_twiddles(tws, d.tw32, NX);
     if (PY > 0) {
       __syncthreads();
-      plane_fft2<PX, PY, +1>(s, LD, d.tw32, tws, P);
+      plane_fft2<PX, PY, +1>(s, LD, d.tw32, tws, P, NYH);
     } else {
       load_plane<NX, NY, LD, plane_threads<PY>()>(s, P);
       __syncthreads();
@@ -515,7 +524,7 @@ cudaError_t rows_for(const Dev& d, int f, float2 cf, cudaStream_t s) {
   fa_gspace_kernel<PX, PY><<<d.nz, plane_threads<PY>(), sm, s>>>(d, f);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 gu(d.ny, d.nz);
+  dim3 gu(d.ny / 2 + 1, d.nz);
   switch (d.wx * 32 + d.wy) {
 #define FA_U(WX, WY) case WX * 32 + WY: fa_u_kernel<WX, WY><<<gu, FW_THREADS, u_smem<WX, WY>(d.N), s>>>(d); break;
     FA_U(1, 1) FA_U(2, 1) FA_U(4, 1) FA_U(8, 1) FA_U(16, 1)
