@@ -54,6 +54,7 @@ struct edt_ctx {
   std::vector<int> fj_off;             // [nf * W + 1]
   std::vector<int2> fj_ent;            // [rows] (midpoint index, row) grouped by (f, j)
   std::vector<double2> cf;             // [nf] omega~^2 dx dy dz
+  std::vector<int> jact, jmap, nact;   // active offset wavenumbers per frequency
   long long rows_max_sub = 0;
   // band-limited transform of the mixed path
   bool band_mode = false;
@@ -77,7 +78,7 @@ struct edt_ctx {
   // workspace
   size_t ws_bytes = 0;
   void* ws = nullptr;
-  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
+  Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_jact, r_jmap, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
       r_dinv, r_L32, r_dinv32, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
   Dev dev{};
@@ -205,6 +206,16 @@ void plan_window(edt_ctx* c, double cmin) {
     c->fj_ent.insert(c->fj_ent.end(), lists[i].begin(), lists[i].end());
   }
   c->fj_off[lists.size()] = int(c->fj_ent.size());
+  c->jact.assign(size_t(nf) * W, -1);
+  c->jmap.assign(size_t(nf) * W, -1);
+  c->nact.assign(nf, 0);
+  for (int f = 0; f < nf; ++f)
+    for (int j = 0; j < W; ++j)
+      if (!lists[size_t(f) * W + j].empty()) {
+        c->jmap[size_t(f) * W + j] = c->nact[f];
+        c->jact[size_t(f) * W + c->nact[f]] = j;
+        c->nact[f]++;
+      }
   c->cf.resize(nf);
   for (int f = 0; f < nf; ++f) {
     const double2 om = make_double2(c->fc[f].om_re, c->fc[f].om_im);
@@ -477,8 +488,11 @@ void layout(edt_ctx* c) {
   take(c->r_pairm, std::max<size_t>(c->pair_m.size(), 1) * sizeof(int));
   take(c->r_fjoff, std::max<size_t>(c->fj_off.size(), 1) * sizeof(int));
   take(c->r_fjent, std::max<size_t>(c->fj_ent.size(), 1) * sizeof(int2));
+  take(c->r_jact, std::max<size_t>(c->jact.size(), 1) * sizeof(int));
+  take(c->r_jmap, std::max<size_t>(c->jmap.size(), 1) * sizeof(int));
   take(c->r_Gs, c->win ? nz * nxy * sizeof(float2) : 0);
-  take(c->r_U, c->win ? W * nz * (size_t(c->ny / 2 + 1) * N) * sizeof(float2) : 0);
+  const size_t wact = c->nact.empty() ? 1 : size_t(std::max(1, *std::max_element(c->nact.begin(), c->nact.end())));
+  take(c->r_U, c->win ? wact * nz * (size_t(c->ny / 2 + 1) * N) * sizeof(float2) : 0);
   take(c->r_Dw, c->win ? nf * W * nxy * sizeof(float2) : 0);
   take(c->r_A32, c->win ? (R + 1) * nzs * sizeof(float2) : 0);
   take(c->r_tw64, (N / 2) * sizeof(double2));
@@ -549,6 +563,8 @@ void bind(edt_ctx* c) {
   d.pair_m = at<const int*>(c, c->r_pairm);
   d.fj_off = at<const int*>(c, c->r_fjoff);
   d.fj_ent = at<const int2*>(c, c->r_fjent);
+  d.jact = at<const int*>(c, c->r_jact);
+  d.jmap = at<const int*>(c, c->r_jmap);
   d.Gs = c->r_Gs.bytes ? at<float2*>(c, c->r_Gs) : nullptr;
   d.U = c->r_U.bytes ? at<float2*>(c, c->r_U) : nullptr;
   d.Dw = c->r_Dw.bytes ? at<float2*>(c, c->r_Dw) : nullptr;
@@ -640,7 +656,7 @@ int transform_rhs(edt_ctx* c, const void* D, int D_dtype, cudaStream_t s) {
 // Window geometry: the assembled kernel rows of every frequency into the row table.
 int kernel_rows(edt_ctx* c, cudaStream_t s) {
   if (!c->win) return EDT_OK;
-  for (int f = 0; f < c->nf; ++f) EDT_TRY(launch_fa_rows(c->dev, f, c->cf[f], s));
+  for (int f = 0; f < c->nf; ++f) EDT_TRY(launch_fa_rows(c->dev, f, c->nact[f], c->cf[f], s));
   return EDT_OK;
 }
 
@@ -752,6 +768,8 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRYI(upload(c, c->r_pairm, c->pair_m));
   EDT_TRYI(upload(c, c->r_fjoff, c->fj_off));
   EDT_TRYI(upload(c, c->r_fjent, c->fj_ent));
+  EDT_TRYI(upload(c, c->r_jact, c->jact));
+  EDT_TRYI(upload(c, c->r_jmap, c->jmap));
   EDT_TRYI(upload(c, c->r_tw64, c->tw64));
   EDT_TRYI(upload(c, c->r_tw32, c->tw32));
   EDT_TRYI(upload(c, c->r_segm, c->seg_m));
@@ -1045,9 +1063,11 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + tr_launches +
                            chol_launches(c->nz);
   if (c->win) {
-    // green (3), per frequency rows (3), data (2), Gram (2), Cholesky, refinement (2 per
-    // step), inverse (completion, FP64 row and column transforms, output: 3 or 4)
-    o->launches_per_invert = 3 + 3 * c->nf + 2 + 2 + chol_launches(c->nz) + 2 * c->cfg.refine +
+    // green (3), rows (3) per frequency that keeps any, data (2), Gram (2), Cholesky,
+    // refinement (2 per step), inverse (completion, FP64 row and column transforms, output: 3 or 4)
+    int fk = 0;
+    for (int n : c->nact) fk += n > 0;
+    o->launches_per_invert = 3 + 3 * fk + 2 + 2 + chol_launches(c->nz) + 2 * c->cfg.refine +
                              (c->ny > 1 ? 4 : 3);
   }
   o->freq_chunk = c->band_mode ? c->band_maxplanes : c->fchunk;

@@ -99,6 +99,9 @@ struct Dev {
   const int* pair_m;            // [nsub] midpoint index my * nx + mx of each pair's k_m
   const int* fj_off;            // [nf * W + 1] entry ranges of the (f, j) lists
   const int2* fj_ent;           // (midpoint index, row) of every row, grouped by (f, j)
+  const int* jact;              // [nf][W] active offset wavenumbers of each frequency (those
+                                //   with kept rows), compacted; then -1
+  const int* jmap;              // [nf][W] position of j among the active ones, or -1
   float2* Gs;                   // [nz][ny][nx] G(y, z) of one frequency
   float2* U;                    // [W][nz][ny/2 + 1][nx] window products of one frequency
                                 //   (centrosymmetric in y: rows 0..ny/2 stored)
@@ -158,7 +161,7 @@ cudaError_t prepare_band(const Dev& d);
 // Window geometry (csrc/fa.cu): kernel rows of frequency f into A32, data transform and
 // right-hand sides, the inverse transform to V[ny][nx][nz]; supported grids and windows.
 bool fa_supported(int nx, int ny, int wx, int wy);
-cudaError_t launch_fa_rows(const Dev& d, int f, double2 cf, cudaStream_t s);
+cudaError_t launch_fa_rows(const Dev& d, int f, int nact, double2 cf, cudaStream_t s);
 cudaError_t launch_fa_data(const Dev& d, const void* D, int D_dtype, cudaStream_t s);
 cudaError_t launch_fa_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s);
 cudaError_t launch_fa_setup(const Dev& d, long long nrows, cudaStream_t s);

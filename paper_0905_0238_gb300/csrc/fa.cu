@@ -294,10 +294,12 @@ template <int WX, int WY> struct ExLayout {
 };
 
 // U_j(y, z) for one frequency: CTA per (y row, z), window transform per y in registers.
-// G is even, so U_j(-y) = U_j(y): only the rows y_y = 0..ny/2 are formed and stored.
+// G is even, so U_j(-y) = U_j(y): only the rows y_y = 0..ny/2 are formed and stored, and only
+// for the offset wavenumbers j that have kept rows at this frequency (compacted).
 template <int WX, int WY>
-__global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d) {
+__global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d, int f) {
   using L = ExLayout<WX, WY>;
+  const int* jmap = d.jmap + size_t(f) * WX * WY;
   constexpr int UPB = L::UPB;                              // y points per pass
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* ex = reinterpret_cast<float2*>(smem_raw);       // exchange, L::SIZE
@@ -340,8 +342,10 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d) {
       reg_dft<WY>(b);
 #pragma unroll
       for (int jy = 0; jy < WY; ++jy) {
+        const int ja = jmap[jy * WX + jx];                  // only offset wavenumbers with rows
+        if (ja < 0) continue;
         const float2 v = neg_if(b[jy], WY >= 2 && ((jy & 1) != alt_sign_end(WY)));
-        d.U[((size_t(jy * WX + jx) * d.nz + z) * (ny / 2 + 1) + yy) * nx + x] = v;
+        d.U[((size_t(ja) * d.nz + z) * (ny / 2 + 1) + yy) * nx + x] = v;
       }
     }
     __syncthreads();
@@ -362,10 +366,12 @@ fa_mrows_kernel(Dev d, int f, float2 cf) {
   float2* s = reinterpret_cast<float2*>(smem_raw);
   float2* tws = s + plane_words(NX, NY);
   cg::cluster_group cluster = cg::this_cluster();
-  const int j = blockIdx.x, z = blockIdx.y, rank = int(cluster.block_rank()), z0 = z - rank;
+  // blockIdx.x: position among the frequency's active offset wavenumbers
+  const int ja = blockIdx.x, j = d.jact[size_t(f) * d.W + ja];
+  const int z = blockIdx.y, rank = int(cluster.block_rank()), z0 = z - rank;
   if (z < d.nz) {                        // every CTA reaches both cluster barriers below
     constexpr int NYH = NY / 2 + 1;      // stored rows of the centrosymmetric plane
-    const float2* P = d.U + (size_t(j) * d.nz + z) * (NYH * NX);
+    const float2* P = d.U + (size_t(ja) * d.nz + z) * (NYH * NX);
     plane_twiddles(tws, d.tw32, NX);
     if (PY > 0) {
       __syncthreads();
@@ -519,14 +525,15 @@ template <int PX, int PY>
 size_t plane_smem() { return size_t(plane_words(32 * PX, PY > 0 ? 32 * PY : 1) + 32 * PX) * sizeof(float2); }
 
 template <int PX, int PY>
-cudaError_t rows_for(const Dev& d, int f, float2 cf, cudaStream_t s) {
+cudaError_t rows_for(const Dev& d, int f, int nact, float2 cf, cudaStream_t s) {
+  if (nact == 0) return cudaSuccess;     // no kept row at this frequency
   const size_t sm = plane_smem<PX, PY>();
   fa_gspace_kernel<PX, PY><<<d.nz, plane_threads<PY>(), sm, s>>>(d, f);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 gu(d.ny / 2 + 1, d.nz);
   switch (d.wx * 32 + d.wy) {
-#define FA_U(WX, WY) case WX * 32 + WY: fa_u_kernel<WX, WY><<<gu, FW_THREADS, u_smem<WX, WY>(d.N), s>>>(d); break;
+#define FA_U(WX, WY) case WX * 32 + WY: fa_u_kernel<WX, WY><<<gu, FW_THREADS, u_smem<WX, WY>(d.N), s>>>(d, f); break;
     FA_U(1, 1) FA_U(2, 1) FA_U(4, 1) FA_U(8, 1) FA_U(16, 1)
     FA_U(2, 2) FA_U(4, 4) FA_U(8, 8) FA_U(16, 16) FA_U(4, 2) FA_U(8, 4) FA_U(16, 8)
 #undef FA_U
@@ -534,7 +541,7 @@ cudaError_t rows_for(const Dev& d, int f, float2 cf, cudaStream_t s) {
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int zc = d.tune_zc;
-  const dim3 gm(d.W, (d.nz + zc - 1) / zc * zc);
+  const dim3 gm(nact, (d.nz + zc - 1) / zc * zc);
   if (zc == 2) fa_mrows_kernel<PX, PY, 2><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
   else if (zc == 8) fa_mrows_kernel<PX, PY, 8><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
   else fa_mrows_kernel<PX, PY, 4><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
@@ -584,10 +591,10 @@ bool fa_supported(int nx, int ny, int wx, int wy) {
   return shape && win && wx <= nx && wy <= ny;
 }
 
-cudaError_t launch_fa_rows(const Dev& d, int f, double2 cf, cudaStream_t s) {
+cudaError_t launch_fa_rows(const Dev& d, int f, int nact, double2 cf, cudaStream_t s) {
   const float2 c = make_float2(float(cf.x), float(cf.y));
   const int px = d.N / 32, py = d.ny == 1 ? 0 : d.ny / 32;
-#define FA_R(PX, PY) if (px == PX && py == PY) return rows_for<PX, PY>(d, f, c, s);
+#define FA_R(PX, PY) if (px == PX && py == PY) return rows_for<PX, PY>(d, f, nact, c, s);
   FA_SHAPES(FA_R)
 #undef FA_R
   return cudaErrorInvalidValue;
