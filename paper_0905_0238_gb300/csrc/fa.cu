@@ -11,9 +11,10 @@
 // half-offset w into G(y - w) G(y + w) and the midpoint phase exp(-i k_m.w) cancels, so the
 // window transform acts on U before one transform over y gives every k_m at once.
 // Stages per frequency: fa_gspace (spectrum from the table, inverse 2D FFT -> G), fa_u
-// (products and the window transform per y), fa_mrows (2D FFT of U_j per (j, z) plane,
-// clusters of 4 consecutive depths, then the kept rows of (f, j) are written into the row
-// table A32[row][z] four depths at a time from the cluster's distributed shared memory).
+// (products and the window transform per y), fa_mrows (2D FFT of U_j per (j, z) plane, from
+// its rows 0..ny/2 since U_j is centrosymmetric; clusters of ZC consecutive depths, then the
+// kept rows of (f, j) are written into the row table A32[row][z] ZC depths at a time from the
+// cluster's distributed shared memory).
 //
 // Data: the window transform of D[f][m][w] per midpoint (fa_dwin, written transposed as
 // Dw[f][j][m]), then per (f, j) plane the midpoint FFT and the split right-hand sides of
@@ -35,6 +36,8 @@ namespace {
 // threads of the plane kernels: a 2D plane fills shared memory (one CTA per SM), so it takes
 // the most warps a CTA can have; a line is one warp's FFT
 template <int PY> __host__ __device__ constexpr int plane_threads() { return PY > 0 ? 1024 : 128; }
+// the kernel-row planes are half planes (below): two CTAs of 512 threads share an SM
+template <int PY> __host__ __device__ constexpr int mrows_threads() { return PY > 0 ? 512 : 128; }
 constexpr int FW_THREADS = 256;   // window-transform kernels
 
 // Plane layout in shared memory: element (y, x) at y * ld + 2 (y/16) + x + 2 (x/16) with
@@ -248,6 +251,105 @@ __device__ void plane_fft2(float2* s, int ld, const float2* tw, const float2* tw
   __syncthreads();
 }
 
+// 2D transform of a centrosymmetric N x N plane (P(-y) = P(y), so its transform X is
+// centrosymmetric too) from its rows 0..N/2, in a half plane of N/2 + 3 rows (layout above):
+//   row pass:    rows r = 0..N/2 transformed in place (read from gsrc, row-major N/2+1 rows);
+//                V(r, k) for k > N/2 equals V(N - r, N - k) of the rows not stored.
+//   column pass: columns c = 0..N/2 only (X(ky, kx) = X(-ky, -kx) gives the rest).  Element
+//                e of column c is V(e, c) for e < N/2, else V(N - e, N - c) (column c' =
+//                (N - c) mod N), read from the stored rows.  Its 128 slots ("homes") for the
+//                in-place transform: e < N/2 at (e, c); e >= N/2 at (e - N/2, c') for
+//                0 < c < N/2, and in the spare rows N/2 + 1 (c = 0) and N/2 + 2 (c = N/2).
+//                The lines of different columns touch disjoint slots (column c owns rows
+//                0..N/2 of columns c and c'), so the groups run without block barriers.
+// Result: X(ky, kx) at sym_addr(ky, kx).
+template <int N>
+__device__ __forceinline__ int sym_addr(int ky, int kx, int ld) {
+  constexpr int H = N / 2;
+  if (kx > H) { ky = (N - ky) & (N - 1); kx = N - kx; }
+  if (ky < H) return paddr(ky, kx, ld);
+  if (kx == 0) return paddr(H + 1, ky - H, ld);
+  if (kx == H) return paddr(H + 2, ky - H, ld);
+  return paddr(ky - H, N - kx, ld);
+}
+__host__ __device__ constexpr int sym_plane_words(int n) { return plane_words(n, n / 2 + 3); }
+
+// column c of the half plane, N = 16 R, by the 16 threads t of a half-warp (the line FFT of
+// group_fft with the home map above; every home address is affine along each access
+// sequence, so each is a per-thread base plus a constant step)
+template <int R, int SG>
+__device__ __forceinline__ void sym_col_fft(float2* s, int c, int ld, int t, const float2* tw) {
+  constexpr int N = 16 * R, H = N / 2, HR = R / 2;
+  const unsigned gm = 0xffffu << (threadIdx.x & 16);
+  const int cm = (N - c) & (N - 1);
+  const bool spec = c == 0 || c == H;
+  const int srow = c == 0 ? H + 1 : H + 2;
+  const int RS = 16 * ld + 2;                                 // 16 rows further
+  // pass 1: element 16 a + t; a < R/2 at row 16 a + t of c, else row N - 16 a - t of c'
+  const int lo = paddr(t, c, ld), hi = paddr(H - t, cm, ld);
+  float2 v[R];
+#pragma unroll
+  for (int a = 0; a < R; ++a) v[a] = s[a < HR ? lo + a * RS : hi - (a - HR) * RS];
+  __syncwarp(gm);                     // columns 0 and N/2 read slots that other lanes store to
+  Dft<R, SG>::run(v);
+#pragma unroll
+  for (int k1 = 1; k1 < R; ++k1) v[k1] = v[k1] * tw_sg<SG>(tw[t * k1]);
+  const int h1 = spec ? paddr(srow, t, ld) : paddr(t, cm, ld);   // home of element N/2 + t
+  const int hs = spec ? 18 : RS;                                    // 16 elements further
+#pragma unroll
+  for (int k1 = 0; k1 < R; ++k1) s[k1 < HR ? lo + k1 * RS : h1 + (k1 - HR) * hs] = v[k1];
+  __syncwarp(gm);
+  // pass 2: the pair (2 k1, 2 k1 + 1) reads elements 16 k1 + 2 i + h
+  const int k1 = t >> 1, h = t & 1;
+  const bool act = k1 < R;
+  const int kk = act ? k1 : 0;
+  int b2, s2 = 2 * ld;
+  if (kk < HR) b2 = paddr(16 * kk + h, c, ld);
+  else if (!spec) b2 = paddr(16 * (kk - HR) + h, cm, ld);
+  else { b2 = paddr(srow, 16 * (kk - HR) + h, ld); s2 = 2; }
+  float2 u[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) u[i] = act ? s[b2 + i * s2] : make_float2(0.f, 0.f);
+  dft8<SG>(u);
+  if (h) {
+#pragma unroll
+    for (int k2 = 1; k2 < 8; ++k2) u[k2] = u[k2] * tw_sg<SG>(w16(k2));
+  }
+  float2 p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    p[i].x = __shfl_xor_sync(gm, u[i].x, 1);
+    p[i].y = __shfl_xor_sync(gm, u[i].y, 1);
+  }
+  __syncwarp(gm);
+  // outputs X[k1 + R (i + 8 h)]: h = 0 at row k1 + R i of c; h = 1 at row k1 + R i of c'
+  // (column k1 + R i of the spare row for c = 0, N/2); the skew term 2 ((R i) >> 4) is the
+  // same in both forms because k1 < R
+  if (act) {
+    int b3, s3 = R * ld;
+    if (!h) b3 = paddr(k1, c, ld);
+    else if (!spec) b3 = paddr(k1, cm, ld);
+    else { b3 = paddr(srow, k1, ld); s3 = R; }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float2 e = h ? p[i] : u[i], o = h ? u[i] : p[i];
+      s[b3 + i * s3 + 2 * ((R * i) >> 4)] = h ? e - o : e + o;
+    }
+  }
+  __syncwarp(gm);
+}
+
+// the half-plane transform above; gsrc: rows 0..N/2 of the plane, row-major in global memory
+template <int PX, int SG>
+__device__ void sym_plane_fft2(float2* s, int ld, const float2* tws, const float2* gsrc) {
+  constexpr int N = 32 * PX, R = N / 16, H = N / 2;
+  const int t = threadIdx.x & 15, grp = threadIdx.x >> 4, ng = blockDim.x >> 4;
+  for (int r = grp; r <= H; r += ng) group_fft<R, SG>(s, RowAddr{r, ld}, t, tws, gsrc + size_t(r) * N);
+  __syncthreads();
+  for (int c = grp; c <= H; c += ng) sym_col_fft<R, SG>(s, c, ld, t, tws);
+  __syncthreads();
+}
+
 // W_N^e (sign -1) for e < N in shared memory, from the context's table of length N
 __device__ __forceinline__ void plane_twiddles(float2* tws, const float2* tw32, int N) {
   for (int e = threadIdx.x; e < N; e += blockDim.x) tws[e] = tw_at(tw32, e, N);
@@ -353,18 +455,19 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d, int f) {
 }
 
 // M(k_m; f, j, z) for ZC consecutive depths of one j: a cluster of ZC CTAs, one (j, z) plane
-// each (2D FFT of U_j in shared memory); then every CTA takes a share of the kept rows of
+// each (2D FFT of U_j in shared memory; a grid plane as the centrosymmetric half plane, two
+// CTAs per SM); then every CTA takes a share of the kept rows of
 // (f, j) and reads the ZC depths of each from the cluster's planes (distributed shared
 // memory), so each row's depths z0..z0+ZC-1 are written together (8 ZC contiguous bytes).
 // ZC: depths per cluster, 2, 4 or 8 (the autotuner's choice).
 template <int PX, int PY, int ZC>
-__global__ void __cluster_dims__(1, ZC, 1) __launch_bounds__(plane_threads<PY>())
+__global__ void __cluster_dims__(1, ZC, 1) __launch_bounds__(mrows_threads<PY>(), PY > 0 ? 2 : 1)
 fa_mrows_kernel(Dev d, int f, float2 cf) {
   namespace cg = cooperative_groups;
   constexpr int NX = 32 * PX, NY = PY > 0 ? 32 * PY : 1, LD = plane_ld(NX);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s = reinterpret_cast<float2*>(smem_raw);
-  float2* tws = s + plane_words(NX, NY);
+  float2* tws = s + (PY > 0 ? sym_plane_words(NX) : plane_words(NX, NY));
   cg::cluster_group cluster = cg::this_cluster();
   // blockIdx.x: position among the frequency's active offset wavenumbers
   const int ja = blockIdx.x, j = d.jact[size_t(f) * d.W + ja];
@@ -373,11 +476,12 @@ fa_mrows_kernel(Dev d, int f, float2 cf) {
     constexpr int NYH = NY / 2 + 1;      // stored rows of the centrosymmetric plane
     const float2* P = d.U + (size_t(ja) * d.nz + z) * (NYH * NX);
     plane_twiddles(tws, d.tw32, NX);
-    if (PY > 0) {
+    if constexpr (PY > 0) {
+      static_assert(PX == PY, "square planes");
       __syncthreads();
-      plane_fft2<PX, PY, +1>(s, LD, d.tw32, tws, P, NYH);
+      sym_plane_fft2<PX, +1>(s, LD, tws, P);
     } else {
-      load_plane<NX, NY, LD, plane_threads<PY>()>(s, P);
+      load_plane<NX, NY, LD, mrows_threads<PY>()>(s, P);
       __syncthreads();
       plane_fft2<PX, PY, +1>(s, LD, d.tw32, tws);
     }
@@ -391,7 +495,8 @@ fa_mrows_kernel(Dev d, int f, float2 cf) {
   const int a0 = e0 + rank * per, a1 = min(e1, a0 + per);
   for (int e = a0 + threadIdx.x; e < a1; e += blockDim.x) {
     const int2 ent = d.fj_ent[e];
-    const int y = ent.x / NX, x = ent.x - y * NX, off = paddr(y, x, LD);
+    const int y = ent.x / NX, x = ent.x - y * NX;
+    const int off = PY > 0 ? sym_addr<NX>(y, x, LD) : paddr(y, x, LD);
     float2 v[ZC];
 #pragma unroll
     for (int k = 0; k < ZC; ++k) v[k] = z0 + k < d.nz ? cf * ps[k][off] : make_float2(0.f, 0.f);
@@ -523,6 +628,10 @@ size_t u_smem(int nx) { return (size_t(ExLayout<WX, WY>::SIZE) + size_t(WY + 1) 
 
 template <int PX, int PY>
 size_t plane_smem() { return size_t(plane_words(32 * PX, PY > 0 ? 32 * PY : 1) + 32 * PX) * sizeof(float2); }
+template <int PX, int PY>
+size_t mrows_smem() {
+  return PY > 0 ? size_t(sym_plane_words(32 * PX) + 32 * PX) * sizeof(float2) : plane_smem<PX, PY>();
+}
 
 template <int PX, int PY>
 cudaError_t rows_for(const Dev& d, int f, int nact, float2 cf, cudaStream_t s) {
@@ -542,9 +651,10 @@ cudaError_t rows_for(const Dev& d, int f, int nact, float2 cf, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int zc = d.tune_zc;
   const dim3 gm(nact, (d.nz + zc - 1) / zc * zc);
-  if (zc == 2) fa_mrows_kernel<PX, PY, 2><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
-  else if (zc == 8) fa_mrows_kernel<PX, PY, 8><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
-  else fa_mrows_kernel<PX, PY, 4><<<gm, plane_threads<PY>(), sm, s>>>(d, f, cf);
+  const size_t smr = mrows_smem<PX, PY>();
+  if (zc == 2) fa_mrows_kernel<PX, PY, 2><<<gm, mrows_threads<PY>(), smr, s>>>(d, f, cf);
+  else if (zc == 8) fa_mrows_kernel<PX, PY, 8><<<gm, mrows_threads<PY>(), smr, s>>>(d, f, cf);
+  else fa_mrows_kernel<PX, PY, 4><<<gm, mrows_threads<PY>(), smr, s>>>(d, f, cf);
   return cudaGetLastError();
 }
 
@@ -567,9 +677,10 @@ cudaError_t prepare_plane() {
   const int sm = int(plane_smem<PX, PY>());
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(fa_gspace_kernel<PX, PY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+  const int smr = int(mrows_smem<PX, PY>());
+  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smr)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smr)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fa_mrows_kernel<PX, PY, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smr)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(fa_drhs_kernel<PX, PY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
