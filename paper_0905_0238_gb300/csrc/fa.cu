@@ -51,6 +51,7 @@ __host__ __device__ constexpr int plane_words(int nx, int ny) {
 }
 __device__ __forceinline__ int paddr(int y, int x, int ld) { return y * ld + 2 * (y >> 4) + x + 2 * (x >> 4); }
 
+
 // 2D transform of one plane in shared memory (layout above), nx = 32 PX, ny = 32 PY (PY = 0:
 // ny = 1).  Warps take rows, then columns, each line a register-resident warp FFT; the
 // twiddle table is that of length nx (ny == nx when PY > 0).
@@ -399,7 +400,7 @@ template <int WX, int WY> struct ExLayout {
 // G is even, so U_j(-y) = U_j(y): only the rows y_y = 0..ny/2 are formed and stored, and only
 // for the offset wavenumbers j that have kept rows at this frequency (compacted).
 template <int WX, int WY>
-__global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d, int f) {
+__global__ void __launch_bounds__(FW_THREADS, 4) fa_u_kernel(Dev d, int f) {
   using L = ExLayout<WX, WY>;
   const int* jmap = d.jmap + size_t(f) * WX * WY;
   constexpr int UPB = L::UPB;                              // y points per pass
@@ -413,6 +414,15 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d, int f) {
     const int row = (yy + t - WY / 2 + ny) & (ny - 1);      // ny is a power of two
     Grow[e] = G[size_t(row) * nx + x];
   }
+  // the second pass gives each thread the same x offset and KX values of jx in every pass
+  // (jx = jx2 + k WY); its stores go to the compacted planes of the active (jx, jy), or nowhere
+  constexpr int KX = UPB * WX / FW_THREADS;                // = WX / WY
+  static_assert(KX >= 1 && KX * FW_THREADS == UPB * WX, "whole passes");
+  const int jx2 = threadIdx.x / UPB, ux2 = threadIdx.x - jx2 * UPB;
+  const size_t pstride = size_t(d.nz) * (ny / 2 + 1) * nx;
+  float2* Urow = d.U + (size_t(z) * (ny / 2 + 1) + yy) * nx + ux2;
+  __shared__ int jat[WX * WY];
+  for (int e = threadIdx.x; e < WX * WY; e += blockDim.x) jat[e] = jmap[e];
   __syncthreads();
   for (int x0 = 0; x0 < nx; x0 += UPB) {
     {
@@ -435,19 +445,19 @@ __global__ void __launch_bounds__(FW_THREADS) fa_u_kernel(Dev d, int f) {
       }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < UPB * WX; t += blockDim.x) {
-      const int jx = t / UPB, ux = t - jx * UPB, x = x0 + ux;   // consecutive threads: consecutive x
-      if (x >= nx) continue;
-      float2 b[WY];
+    if (x0 + ux2 < nx) {                                   // consecutive threads: consecutive x
 #pragma unroll
-      for (int iwy = 0; iwy < WY; ++iwy) b[iwy] = neg_if(ex[L::at(jx, ux, iwy)], WY >= 2 && (iwy & 1));
-      reg_dft<WY>(b);
+      for (int k = 0; k < KX; ++k) {
+        float2 b[WY];
 #pragma unroll
-      for (int jy = 0; jy < WY; ++jy) {
-        const int ja = jmap[jy * WX + jx];                  // only offset wavenumbers with rows
-        if (ja < 0) continue;
-        const float2 v = neg_if(b[jy], WY >= 2 && ((jy & 1) != alt_sign_end(WY)));
-        d.U[((size_t(ja) * d.nz + z) * (ny / 2 + 1) + yy) * nx + x] = v;
+        for (int iwy = 0; iwy < WY; ++iwy)
+          b[iwy] = neg_if(ex[L::at(jx2 + k * WY, ux2, iwy)], WY >= 2 && (iwy & 1));
+        reg_dft<WY>(b);
+#pragma unroll
+        for (int jy = 0; jy < WY; ++jy) {
+          const int ja = jat[jy * WX + jx2 + k * WY];
+          if (ja >= 0) Urow[ja * pstride + x0] = neg_if(b[jy], WY >= 2 && ((jy & 1) != alt_sign_end(WY)));
+        }
       }
     }
     __syncthreads();
@@ -475,12 +485,13 @@ fa_mrows_kernel(Dev d, int f, float2 cf) {
   if (z < d.nz) {                        // every CTA reaches both cluster barriers below
     constexpr int NYH = NY / 2 + 1;      // stored rows of the centrosymmetric plane
     const float2* P = d.U + (size_t(ja) * d.nz + z) * (NYH * NX);
-    plane_twiddles(tws, d.tw32, NX);
     if constexpr (PY > 0) {
       static_assert(PX == PY, "square planes");
+      plane_twiddles(tws, d.tw32, NX);
       __syncthreads();
       sym_plane_fft2<PX, +1>(s, LD, tws, P);
     } else {
+      plane_twiddles(tws, d.tw32, NX);
       load_plane<NX, NY, LD, mrows_threads<PY>()>(s, P);
       __syncthreads();
       plane_fft2<PX, PY, +1>(s, LD, d.tw32, tws);
