@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default launch shapes instead of the autotuned ones")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_3d"],
-                    help="batched_3d: the finite-aperture 3D workload (a separate line, not the "
-                         "headline)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batched_3d", "differentiation_2d"],
+                    help="batched_3d: the finite-aperture 3D workload; differentiation_2d: misfit "
+                         "gradients on the production geometry (separate lines, not the headline)")
     return ap.parse_args()
 
 
@@ -124,6 +125,32 @@ def cpu_child_window(spec):
     print("CPUJSON " + json.dumps(out))
 
 
+def cpu_child_grad(spec):
+    """Oracle sample of the misfit gradients: J, dJ/dV and dJ/dc of one frequency of the
+    production geometry (the gradients are sums over frequencies), scaled to one full
+    evaluation (all frequencies)."""
+    import synth
+    from oracle import edt2d, grad2d
+    wl = synth.preset(WORKLOAD)
+    wl.cutoff = 0.0
+    nf = len(wl.freq_hz)
+    wl.freq_hz = wl.freq_hz[[spec["freq"]]]
+    rng = synth.rng_for(3, 11)
+    Vt = synth.perturbation_random_field(rng, wl.nx, wl.dx, wl.nz, wl.dz, wl.z0, wl.layer_top,
+                                         wl.layer_vel)
+    D = edt2d.forward(wl, Vt)
+    a = time.perf_counter()
+    grad2d.misfit(wl, 0.5 * Vt, D)
+    grad2d.grad_V(wl, 0.5 * Vt, D)
+    grad2d.grad_c(wl, 0.5 * Vt, D)
+    t = time.perf_counter() - a
+    out = dict(value=1.0 / (t * nf), unit="gradients/s", cores=1, kind="oracle",
+               sample=(f"FP64 numpy oracle, 1 thread: J, dJ/dV and dJ/dc (forward-mode depth march, "
+                       f"{len(wl.layer_vel)} layers) of frequency index {spec['freq']} "
+                       f"({t:.1f} s), x {nf} frequencies"))
+    print("CPUJSON " + json.dumps(out))
+
+
 def cpu_child(spec_path):
     """Runs in a subprocess with single-threaded BLAS: time the oracle on a sample."""
     import numpy as np
@@ -132,6 +159,9 @@ def cpu_child(spec_path):
     spec = json.load(open(spec_path))
     if spec.get("workload") == "batched_3d":
         cpu_child_window(spec)
+        return
+    if spec.get("workload") == "differentiation_2d":
+        cpu_child_grad(spec)
         return
     wl = synth.preset(spec["workload"])
     rng = synth.rng_for(1, salt=77)
@@ -266,6 +296,9 @@ def main():
         return
     if args.workload == "batched_3d":
         main_window(args, world, rank, local)
+        return
+    if args.workload == "differentiation_2d":
+        main_grad(args, world, rank, local)
         return
 
     import numpy as np
@@ -596,6 +629,123 @@ def main_window(args, world, rank, local):
                          achieved_gbs=k3_bytes / (k3_ms / 1e3) / 1e9 if k3_ms > 0 else None,
                          peak_gbs=peaks.get("hbm_gbs")),
         stage_ms=stage_ms, clocks=clk, cpu_baseline=cpu)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_grad(args, world, rank, local):
+    """Misfit gradients on the production geometry (FP32): 512 x 512, 128 frequencies 3-60 Hz,
+    256 depths of 8 m, 20 layers; data = Born data of a 3 % random field plus 20 dB noise,
+    model = half that field.  One step = one evaluation of J = ||F V - D||^2, dJ/dV (adjoint
+    Born) and dJ/dc for the 20 layer velocities (reverse-mode depth march)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_0905_0238_gb300 import build as libbuild
+    libbuild.build()
+    from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = synth.preset(WORKLOAD)
+    wl.cutoff = 0.0
+    rng = synth.rng_for(3, salt=line_salt(rank))
+    Vt = synth.perturbation_random_field(rng, wl.nx, wl.dx, wl.nz, wl.dz, wl.z0, wl.layer_top,
+                                         wl.layer_vel)
+    s = Solver(Config.from_workload(wl, precision=EDT_MIXED), device=dev)
+    D = s.forward(torch.from_numpy(Vt.astype(np.float32)).to(dev), out_dtype=torch.complex64)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.SEED_BASE + 3 + 1000 * rank)
+    p_sig = (D.abs() ** 2).mean(dim=(1, 2), keepdim=True)
+    sd = torch.sqrt(p_sig / 10 ** (wl.snr_db / 10) / 2)
+    D = (D + torch.complex(torch.randn(D.shape, device=dev, generator=gen),
+                           torch.randn(D.shape, device=dev, generator=gen)) * sd).contiguous()
+    V = torch.from_numpy((0.5 * Vt).astype(np.float32)).to(dev).contiguous()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        s.misfit_grad(V, D)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J, gV, gc = s.misfit_grad(V, D)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world)
+    value = job_throughput(world, 1, args.steps, ms_total)
+    # end to end: pinned host inputs in, J and both gradients back to pinned host memory
+    Dh = D.cpu().pin_memory()
+    Vh = V.cpu().pin_memory()
+    gVh = torch.empty_like(Vh).pin_memory()
+    gch = torch.empty((len(wl.layer_vel),), dtype=torch.float64).pin_memory()
+    Jh = torch.empty((), dtype=torch.float64).pin_memory()
+    Dd, Vd = torch.empty_like(D), torch.empty_like(V)
+    torch.cuda.synchronize()
+    barrier()
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(args.steps):
+        Dd.copy_(Dh, non_blocking=True)
+        Vd.copy_(Vh, non_blocking=True)
+        J, gV, gc = s.misfit_grad(Vd, Dd)
+        Jh.copy_(J, non_blocking=True)
+        gVh.copy_(gV, non_blocking=True)
+        gch.copy_(gc, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(h0.elapsed_time(h1), world)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    nf, N, nz = len(wl.freq_hz), wl.nx, wl.nz
+    # four contractions over (f, p, q, z): residual, adjoint Born, and the two legs of dJ/dg,
+    # each a complex product (6 flops) and a complex multiply-add (8 flops) per term
+    flops = 56.0 * nf * N * N * nz
+    peak = 152 * 128 * 2 * 2.07 / 1e3        # FP32 FMA lanes x 2 flops x 2.07 GHz -> TFLOP/s
+    achieved = flops / (ms_total / args.steps / 1e3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = run_cpu_baseline(None, dict(workload="differentiation_2d", freq=127))
+        except Exception as ex:
+            cpu = dict(value=None, unit="gradients/s", cores=0, kind="oracle", sample=str(ex)[:300])
+    line = dict(
+        metric="misfit_gradients_per_sec", value=value, unit="gradients/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=ms_total / args.steps,
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64acc",
+        data="synthetic (Born data of a seeded 3% random field + 20 dB noise; model = half the field)",
+        config=dict(workload=(f"differentiation_2d: {N}x{N} dx {wl.dx} m, {nf} freqs "
+                              f"{wl.freq_hz.min():g}-{wl.freq_hz.max():g} Hz, nz {nz} dz {wl.dz} m, "
+                              f"{len(wl.layer_vel)} layers; J, dJ/dV, dJ/dc per step"),
+                    l2="inputs larger than L2 (268 MB data)", parallelism=f"replicas x{world}"),
+        model_pts_per_sec=world * N * nz * args.steps / (ms_total / 1e3),
+        e2e=dict(value=job_throughput(world, 1, args.steps, ms_e2e), unit="gradients/s",
+                 h2d_bytes_per_step=int(D.numel() * D.element_size() + V.numel() * V.element_size()),
+                 d2h_bytes_per_step=int(gV.numel() * gV.element_size() + gc.numel() * 8 + 8)),
+        gpu_launches=None,
+        roofline=dict(bound="alu", kernel="grad_residual + grad_vhat + grad_gbar x2 (whole call)",
+                      achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                      traffic=None, peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                      flops_per_launch=flops),
+        J=float(J), clocks=clk, cpu_baseline=cpu)
+    line["gpu_launches"] = int(s.stats().launches_per_grad) * args.steps
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

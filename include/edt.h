@@ -156,6 +156,8 @@ typedef struct {
   int freq_chunk;               /* frequency planes the data transform and the
                                    right-hand-side gather process per chunk (the
                                    spectrum buffer holds one chunk, about 32 MB)         */
+  int launches_per_grad;        /* CUDA kernels one edt_misfit_grad launches (0 where it
+                                   is unsupported)                                       */
 } edt_stats;
 
 /* Launch shapes the autotuner chooses among (candidates in brackets; all give the same
@@ -219,6 +221,28 @@ int edt_invert_host(edt_ctx* ctx, const void* D_host, int D_dtype, void* V_host,
  * evaluated spectrally.  Precision follows cfg.precision (FP32 for EDT_MIXED). */
 int edt_forward(edt_ctx* ctx, const void* V_dev, int V_dtype, void* D_dev, int D_dtype,
                 void* stream);
+
+/* Misfit of a model against data and its gradients (line geometry, EDT_MIXED; FP32
+ * arithmetic with FP64 accumulation across frequencies):
+ *   J = || F(c0) V - D ||^2 = sum_f sum_is sum_ir |(F V - D)(f, is, ir)|^2,
+ * F the Born operator of edt_forward with every row (no evanescent cut), and
+ *   gV[x][z]  = dJ/dV(x, z)  (adjoint Born: 2 F^T (F V - D)),
+ *   gc[l]     = dJ/dc_l, the derivative with respect to the velocity of layer l of the
+ *               reference, through the depth march of g (reverse-mode differentiation of
+ *               the reflectivity recursion, recomputed, not stored).
+ * V_dev: [nx][nz] (EDT_F32 or EDT_F64), D_dev: [nfreq][nx][nx] (EDT_C64 or EDT_C128);
+ * outputs are device pointers: J_dev one double, gV_dev [nx][nz] of V_dtype, gc_dev
+ * double[nlayer].  Requires nx >= 64 and nlayer <= 64 (else EDT_EUNSUPPORTED).  The
+ * evaluation is in the (p, q) spectral domain, where the data transform is nx times a
+ * unitary map per axis, so J = (1/nx^2) sum |D2-domain residual|^2 exactly. */
+int edt_misfit_grad(edt_ctx* ctx, const void* V_dev, int V_dtype, const void* D_dev,
+                    int D_dtype, double* J_dev, void* gV_dev, double* gc_dev, void* stream);
+
+/* Replace the layer velocities of the reference (same layer tops); every later call uses
+ * them (the depth march runs in every call).  With cutoff > 0 the row plan depends on the
+ * slowest velocity, so that minimum must stay the same (else EDT_EINVAL: create a new
+ * context).  The host array is copied before the call returns. */
+int edt_set_reference(edt_ctx* ctx, const double* layer_vel_mps, void* stream);
 
 /* Reference Green's function table g(k_n, z_j; omega~_f), n = 0..nx/2, as complex128
  * [nfreq][nx/2+1][nz] (computed in FP64 by the depth march). */

@@ -80,7 +80,7 @@ struct edt_ctx {
   void* ws = nullptr;
   Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_jact, r_jmap, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
-      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_status, r_flags;
+      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_gscr, r_adj, r_gacc, r_status, r_flags;
   Dev dev{};
   cudaStream_t last_stream = nullptr;
   int last_status = EDT_OK;
@@ -530,6 +530,12 @@ void layout(edt_ctx* c) {
   take(c->r_r, ns * nz * 2 * sizeof(double));
   take(c->r_vhat, ns * nz * sizeof(double2));
   take(c->r_vfull, (c->win ? nxy : N) * nz * sizeof(double2));
+  // misfit gradients: line geometry, mixed path (their dJ/dg buffer aliases r_g64, which
+  // holds nf (N/2 + 1) nz complex doubles >= nf N nz complex floats)
+  const bool grad = !c->win && mixed && c->nlayer <= GRAD_MAX_LAYERS && N >= 64;
+  take(c->r_gscr, grad ? nf * size_t(c->nlayer) * 8 * nk * sizeof(double2) : 0);
+  take(c->r_adj, grad ? size_t(N) * nz * sizeof(double2) : 0);
+  take(c->r_gacc, grad ? size_t(1 + c->nlayer) * sizeof(double) : 0);
   take(c->r_status, ns * sizeof(int));
   take(c->r_flags, 8 * sizeof(unsigned));
   c->ws_bytes = align_up(off, 256);
@@ -607,6 +613,10 @@ void bind(edt_ctx* c) {
   d.r = at<double*>(c, c->r_r);
   d.vhat = at<double2*>(c, c->r_vhat);
   d.vfull = at<double2*>(c, c->r_vfull);
+  d.gscr = c->r_gscr.bytes ? at<double2*>(c, c->r_gscr) : nullptr;
+  d.adj = c->r_adj.bytes ? at<double2*>(c, c->r_adj) : nullptr;
+  d.gacc = c->r_gacc.bytes ? at<double*>(c, c->r_gacc) : nullptr;
+  d.gbar = c->r_gscr.bytes ? reinterpret_cast<float2*>(d.g64) : nullptr;
   d.status = at<int*>(c, c->r_status);
   d.flags = at<unsigned*>(c, c->r_flags);
 }
@@ -990,6 +1000,39 @@ int edt_forward(edt_ctx* c, const void* V, int V_dtype, void* D, int D_dtype, vo
   return EDT_OK;
 }
 
+int edt_misfit_grad(edt_ctx* c, const void* V, int V_dtype, const void* D, int D_dtype,
+                    double* J, void* gV, double* gc, void* stream) {
+  if (!c || !V || !D || !J || !gV || !gc) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
+  if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
+  if (!grad_supported(c->dev)) return EDT_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  EDT_TRY(launch_green(c->dev, s, GREEN_G32));
+  EDT_TRY(launch_misfit_grad(c->dev, V, V_dtype, D, D_dtype, J, gV, gc, s));
+  return EDT_OK;
+}
+
+int edt_set_reference(edt_ctx* c, const double* vel, void* stream) {
+  if (!c || !vel) return EDT_EINVAL;
+  for (int l = 0; l < c->nlayer; ++l)
+    if (!(vel[l] > 0.0) || !std::isfinite(vel[l])) return EDT_EINVAL;
+  if (c->cfg.cutoff > 0.0) {
+    // the row plan (the evanescent cut) was made for the slowest velocity
+    const double cmin_old = *std::min_element(c->vel.begin(), c->vel.end());
+    const double cmin_new = *std::min_element(vel, vel + c->nlayer);
+    if (cmin_new != cmin_old) return EDT_EINVAL;
+  }
+  std::copy(vel, vel + c->nlayer, c->vel.begin());
+  if (c->ws) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EDT_TRY(cudaMemcpyAsync(at<void*>(c, c->r_lvel), c->vel.data(), c->nlayer * sizeof(double),
+                            cudaMemcpyHostToDevice, s));
+  }
+  return EDT_OK;
+}
+
 int edt_green(edt_ctx* c, void* g_dev, void* stream) {
   if (!c || !g_dev) return EDT_EINVAL;
   if (!c->ws) return EDT_ENOMEM_WS;
@@ -1071,6 +1114,10 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
                              (c->ny > 1 ? 4 : 3);
   }
   o->freq_chunk = c->band_mode ? c->band_maxplanes : c->fchunk;
+  // misfit gradient: green (3), zero, lateral DFT, per chunk transform (2) and four
+  // contractions, reverse depth march, inverse lateral DFT, finalize
+  o->launches_per_grad = grad_supported(c->dev) && c->fchunk > 0
+                             ? 3 + 2 + 6 * ((c->nf + c->fchunk - 1) / c->fchunk) + 3 : 0;
   o->gram_rows_padded = 0;
   for (long long n : c->seg_nrow) o->gram_rows_padded += (n + TC_KC - 1) / TC_KC * TC_KC;
   if (c->ws) {

@@ -135,7 +135,12 @@ struct Dev {
   double* x;                    // [nsub][nz][2]
   double* r;                    // [nsub][nz][2]
   double2* vhat;                // [nsub][nz]
-  double2* vfull;               // [N][nz] scratch for the forward model
+  double2* vfull;               // [N][nz] scratch for the forward model (Vhat of V)
+  // misfit gradients (line geometry, mixed path)
+  double2* gscr;                // [nf][nlayer][8][nk] depth-march states and cotangents
+  double2* adj;                 // [N][nz] Ahat = F^H R2 summed over frequencies
+  double* gacc;                 // [1 + nlayer] sum |R2|^2, then dJ/dc_l
+  float2* gbar;                 // [nf][N][nz] dJ/dg per full lateral index (aliases g64)
   int* status;                  // [nsub]
   unsigned int* flags;          // [8] device-side error flags
 };
@@ -180,6 +185,18 @@ cudaError_t launch_refine_update(const Dev& d, cudaStream_t s);   // x += (LL^T)
 cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s);
 cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
                            cudaStream_t s);
+// vfull[m][z] = sum_x V[x][z] e^{-i k_m x} (FP64)
+cudaError_t launch_lateral_dft(const Dev& d, const void* V, int V_dtype, cudaStream_t s);
+// out[x][z] = scale Re sum_m in[m][z] e^{+i k_m x} over every m (FP64 transform)
+cudaError_t launch_lateral_idft_real(const Dev& d, const double2* in, double scale, void* out,
+                                     int out_dtype, cudaStream_t s);
+
+// Misfit J = ||F V - D||^2 and its gradients (csrc/grad.cu); layers the reverse-mode depth
+// march supports (its per-(f, k) scratch is sized by it).
+constexpr int GRAD_MAX_LAYERS = 64;
+bool grad_supported(const Dev& d);
+cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const void* D, int D_dtype,
+                               double* J, void* gV, double* gc, cudaStream_t s);
 
 // One-time kernel attribute setup (opt-in shared memory), done outside any stream capture.
 cudaError_t prepare_fft(const Dev& d);

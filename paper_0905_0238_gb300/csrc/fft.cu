@@ -382,6 +382,28 @@ __global__ void born_spectral_kernel(Dev d, cplx_t<T>* X, int f0) {
   X[size_t(blockIdx.z) * N * N + size_t(q0 + tq) * N + p0 + tp] = cmk(T(acc.x), T(acc.y));
 }
 
+// out[x][z] = scale Re sum_m in[m][z] e^{+i k_m x}: one block per z tile, every m given.
+__global__ void lateral_idft_kernel(Dev d, const double2* in, double scale, void* out, int out_dtype) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* s = reinterpret_cast<double2*>(smem_raw);
+  const int N = d.N, logn = ilog2(N), ld = padded_len(N) + 1;
+  const int z0 = blockIdx.x * INV_ZT;
+  const int nzt = min(INV_ZT, d.nz - z0);
+  for (int e = threadIdx.x; e < N * nzt; e += blockDim.x) {
+    const int m = e / nzt, t = e - m * nzt;
+    s[t * ld + pd(bitrev(m, logn))] = in[size_t(m) * d.nz + z0 + t];
+  }
+  __syncthreads();
+  block_fft<double, double2>(s, N, logn, nzt, ld, d.tw64, +1);
+  for (int e = threadIdx.x; e < N * nzt; e += blockDim.x) {
+    const int xi = e / nzt, t = e - xi * nzt;
+    const double v = s[t * ld + pd(xi)].x * scale;
+    const size_t o = size_t(xi) * d.nz + z0 + t;
+    if (out_dtype == EDT_F64) reinterpret_cast<double*>(out)[o] = v;
+    else reinterpret_cast<float*>(out)[o] = float(v);
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -425,6 +447,9 @@ cudaError_t prepare_fft(const Dev& d) {
   if ((e = cudaFuncSetAttribute(lateral_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(inv))) !=
       cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(lateral_idft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(inv))) !=
+      cudaSuccess)
+    return e;
   switch (N) {
     case 32: return wfft_cols_prepare<1>();
     case 64: return wfft_cols_prepare<2>();
@@ -439,6 +464,19 @@ cudaError_t prepare_fft(const Dev& d) {
 cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s) {
   size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);
   inverse_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lateral_dft(const Dev& d, const void* V, int V_dtype, cudaStream_t s) {
+  size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);
+  lateral_dft_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, V, V_dtype);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lateral_idft_real(const Dev& d, const double2* in, double scale, void* out,
+                                     int out_dtype, cudaStream_t s) {
+  size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);
+  lateral_idft_kernel<<<(d.nz + INV_ZT - 1) / INV_ZT, 256, smem, s>>>(d, in, scale, out, out_dtype);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,442 @@
+// Misfit gradients of the line geometry: J = ||F(c0) V - D||^2 of the Born operator (every
+// row; the modelling operator has no evanescent cut) and its gradients with respect to the
+// model V(x, z) and to the layer velocities c_l of the reference.
+//
+// Everything is evaluated in the (p, q) spectral domain.  The data transform D -> D2 is N
+// times a unitary map in each of its two lateral axes, so with c_J = 1/N^2
+//   J = c_J sum_f sum_{p,q} |R2_f(p, q)|^2,   R2 = s_f sum_j g_p g_q Vhat(p - q) - D2
+// (eqs. DMV and M read forward, g_n = g(k_n, z_j; omega~_f), Vhat(k_m, z_j) = sum_x V e^{-i k_m x}).
+// Differentiating:
+//   dJ/dV(x, z_j)  = 2 c_J Re sum_m Ahat(m, j) e^{+i k_m x},
+//                    Ahat(m, j) = sum_{f,p} conj(s_f g_p g_{p-m}) R2(p, p - m)      (adjoint Born)
+//   dJ/dg_f(n, j)  = 2 c_J s_f [S1(n, j) + S2(n, j)],
+//                    S1(n) = sum_q conj(R2(n, q)) g_q Vhat(n - q),
+//                    S2(n) = sum_p conj(R2(p, n)) g_p Vhat(p - n)
+//                          = sum_m conj(R2^T(n, n - m)) g_{n-m} conj(Vhat(m))  (V real),
+// folded onto the table index |n'| (g depends on k only through k^2), then
+//   dJ/dc_l = Re sum_{f,k,j} gbar_f(k, j) dg_f(k, j)/dc_l
+// by reverse-mode differentiation of the reflectivity recursion of the depth march (the
+// march is recomputed here, not stored by the forward pass).
+//
+// The FP32 table of the mixed path holds sqrt|s_f| g, so s_f g_p g_q = ph_f g32_p g32_q with
+// ph_f = s_f/|s_f|, and dJ/dg = sqrt|s_f| dJ/dg32 -> the factor 2 c_J ph_f sqrt|s_f| below.
+//
+// Kernels per chunk of frequency planes (X holds D2, then R2 in place):
+//   grad_residual  (p, q) tiles of 64 x 64, 4 x 4 per thread, depth in chunks of 16 in
+//                  shared memory: R2 and the partial sums of |R2|^2;
+//   grad_vhat      (m, j) outputs, 8 consecutive m per thread and one j per lane; the
+//                  thread walks p, so its 8 legs q = p - m slide by one per step and stay
+//                  in registers: Ahat accumulated across frequencies in FP64;
+//   grad_gbar<T>   (n, j) outputs, 8 consecutive n per thread walking m (legs q = n - m
+//                  slide the same way): S1 (T = 0) then S2 (T = 1) into the gbar buffer;
+// then once: grad_recursion (one thread per (f, k), FP64, the recursion forward and back),
+// the inverse lateral DFT of Ahat and a finalize kernel.
+#include "edt_internal.h"
+#include "cplx.cuh"
+
+#include <algorithm>
+
+namespace edt {
+
+namespace {
+
+__device__ __forceinline__ int tab_index(int n, int N) { return n <= (N >> 1) ? n : N - n; }
+
+// acc += a * b (complex)
+__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+
+__global__ void grad_zero_kernel(Dev d) {
+  const size_t n = size_t(d.N) * d.nz;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    d.adj[i] = make_double2(0.0, 0.0);
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i <= d.nlayer; i += blockDim.x) d.gacc[i] = 0.0;
+}
+
+// ---- residual R2 = ph_f sum_j g32_p g32_q Vhat(p - q) - D2, and sum |R2|^2 ------------------
+constexpr int RT = 64, RJC = 16, RTM = 2 * RT - 1;
+
+__global__ void __launch_bounds__(256) grad_residual_kernel(Dev d, int f0) {
+  __shared__ float2 gp[RJC][RT + 1], gq[RJC][RT + 1], vh[RJC][RTM + 2];
+  __shared__ double red[8];
+  const int N = d.N, fi = blockIdx.z, f = f0 + fi;
+  const int p0 = blockIdx.x * RT, q0 = blockIdx.y * RT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const float2* g = d.g32 + size_t(f) * d.nk * d.nzs;
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+  for (int j0 = 0; j0 < d.nz; j0 += RJC) {
+    for (int e = threadIdx.x; e < RT * RJC; e += blockDim.x) {
+      const int i = e / RJC, jj = e - i * RJC, j = j0 + jj;
+      const bool in = j < d.nz;
+      gp[jj][i] = in ? g[size_t(tab_index(p0 + i, N)) * d.nzs + j] : make_float2(0.f, 0.f);
+      gq[jj][i] = in ? g[size_t(tab_index(q0 + i, N)) * d.nzs + j] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < RTM * RJC; e += blockDim.x) {
+      const int i = e / RJC, jj = e - i * RJC, j = j0 + jj;
+      const int m = (p0 - q0 - (RT - 1) + i) & (N - 1);
+      const double2 v = j < d.nz ? d.vfull[size_t(m) * d.nz + j] : make_double2(0.0, 0.0);
+      vh[jj][i] = make_float2(float(v.x), float(v.y));
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int jj = 0; jj < RJC; ++jj) {
+      float2 ga[4], gb[4], v[7];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ga[a] = gp[jj][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) gb[b] = gq[jj][ty + 16 * b];
+      // p - q = tx - ty + 16 (a - b); slot p - q + RT - 1
+#pragma unroll
+      for (int t = 0; t < 7; ++t) v[t] = vh[jj][tx - ty + 16 * (t - 3) + RT - 1];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cmac(acc[a][b], ga[a] * gb[b], v[a - b + 3]);
+    }
+    __syncthreads();
+  }
+  const FreqConst fc = d.fc[f];
+  const float2 ph = make_float2(float(fc.rot_re), float(-fc.rot_im));     // s_f / |s_f|
+  float2* X = reinterpret_cast<float2*>(d.X) + size_t(fi) * N * N;
+  double jp = 0.0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const size_t o = size_t(q0 + ty + 16 * b) * N + p0 + tx + 16 * a;   // X[q][p] = D2(p, q)
+      const float2 r = ph * acc[a][b] - X[o];
+      X[o] = r;
+      jp += double(r.x) * r.x + double(r.y) * r.y;
+    }
+  const double t = block_sum(jp, red);
+  if (threadIdx.x == 0) atomicAdd(d.gacc, t);
+}
+
+// ---- Ahat(m, j) += conj(ph_f) sum_p conj(g32_p g32_{p-m}) R2(p, p - m) -----------------------
+constexpr int VM = 64, VPC = 16, VQR = VPC + VM - 1;
+
+__global__ void __launch_bounds__(256) grad_vhat_kernel(Dev d, int f0) {
+  __shared__ float2 gps[VPC][33], gqs[VQR][33], rs[VQR][VPC];
+  const int N = d.N, fi = blockIdx.z, f = f0 + fi;
+  const int m0 = blockIdx.x * VM, j0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = j0 + lane;
+  const float2* g = d.g32 + size_t(f) * d.nk * d.nzs;
+  const float2* X = reinterpret_cast<const float2*>(d.X) + size_t(fi) * N * N;
+  float2 acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int p0 = 0; p0 < N; p0 += VPC) {
+    // rows qi <-> q = p0 - m0 - (VM - 1) + qi (mod N)
+    for (int e = threadIdx.x; e < VQR * 32; e += blockDim.x) {
+      const int qi = e >> 5, jl = e & 31, jj = j0 + jl;
+      const int q = (p0 - m0 - (VM - 1) + qi) & (N - 1);
+      gqs[qi][jl] = jj < d.nz ? g[size_t(tab_index(q, N)) * d.nzs + jj] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < VPC * 32; e += blockDim.x) {
+      const int pl = e >> 5, jl = e & 31, jj = j0 + jl;
+      gps[pl][jl] = jj < d.nz ? g[size_t(tab_index(p0 + pl, N)) * d.nzs + jj] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < VQR * VPC; e += blockDim.x) {
+      const int qi = e / VPC, pl = e - qi * VPC;
+      const int q = (p0 - m0 - (VM - 1) + qi) & (N - 1);
+      rs[qi][pl] = X[size_t(q) * N + p0 + pl];
+    }
+    __syncthreads();
+    // thread's m_k = m0 + 8 w + k; at p = p0 + pl its leg q_k = p - m_k sits in row
+    // qi = pl - 8 w - k + VM - 1, one row further per step of p: a sliding window
+    float2 win[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) win[k] = gqs[VM - 1 - 8 * w - k][lane];
+#pragma unroll
+    for (int pl = 0; pl < VPC; ++pl) {
+      if (pl > 0) {
+#pragma unroll
+        for (int k = 7; k > 0; --k) win[k] = win[k - 1];
+        win[0] = gqs[pl + VM - 1 - 8 * w][lane];
+      }
+      const float2 gpv = gps[pl][lane];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cmac_conj(acc[k], gpv * win[k], rs[pl + VM - 1 - 8 * w - k][pl]);
+    }
+    __syncthreads();
+  }
+  if (j < d.nz) {
+    const FreqConst fc = d.fc[f];
+    const double2 cph = make_double2(fc.rot_re, fc.rot_im);               // conj(s_f)/|s_f|
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double2 v = cph * make_double2(double(acc[k].x), double(acc[k].y));
+      double* o = reinterpret_cast<double*>(d.adj + size_t(m0 + 8 * w + k) * d.nz + j);
+      atomicAdd(o, v.x);
+      atomicAdd(o + 1, v.y);
+    }
+  }
+}
+
+// ---- S(n, j) = sum_m conj(B(n, n - m)) g32_{n-m} W(m): B = R2, W = Vhat (T = 0) or
+//      B = R2^T, W = conj(Vhat) (T = 1); gbar_f(n, j) = 2 c_J ph_f sqrt|s_f| (S1 + S2) -------
+constexpr int GA = 64, GMC = 16, GQR = GA + GMC - 1;
+
+template <int T>
+__global__ void __launch_bounds__(256) grad_gbar_kernel(Dev d, int f0) {
+  __shared__ float2 gqs[GQR][33], ws[GMC][33];
+  __shared__ __align__(16) float2 bs[GMC][GA];
+  const int N = d.N, fi = blockIdx.z, f = f0 + fi;
+  const int a0 = blockIdx.x * GA, j0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = j0 + lane;
+  const float2* g = d.g32 + size_t(f) * d.nk * d.nzs;
+  const float2* X = reinterpret_cast<const float2*>(d.X) + size_t(fi) * N * N;
+  float2 acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int mc = 0; mc < N; mc += GMC) {
+    // rows qi <-> q = a0 - mc - (GMC - 1) + qi (mod N)
+    for (int e = threadIdx.x; e < GQR * 32; e += blockDim.x) {
+      const int qi = e >> 5, jl = e & 31, jj = j0 + jl;
+      const int q = (a0 - mc - (GMC - 1) + qi) & (N - 1);
+      gqs[qi][jl] = jj < d.nz ? g[size_t(tab_index(q, N)) * d.nzs + jj] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < GMC * 32; e += blockDim.x) {
+      const int mi = e >> 5, jl = e & 31, jj = j0 + jl;
+      double2 v = jj < d.nz ? d.vfull[size_t(mc + mi) * d.nz + jj] : make_double2(0.0, 0.0);
+      if (T) v.y = -v.y;
+      ws[mi][jl] = make_float2(float(v.x), float(v.y));
+    }
+    for (int e = threadIdx.x; e < GMC * GA; e += blockDim.x) {
+      const int mi = e / GA, al = e - mi * GA;
+      const int a = a0 + al, q = (a - mc - mi) & (N - 1);
+      // B(a, q): T = 0 -> R2(a, q) = X[q][a]; T = 1 -> R2(q, a) = X[a][q]
+      bs[mi][al] = T ? X[size_t(a) * N + q] : X[size_t(q) * N + a];
+    }
+    __syncthreads();
+    // thread's n_k = a0 + 8 w + k; at m = mc + mi its leg q_k = n_k - m sits in row
+    // qi = 8 w + k - mi + GMC - 1, one row lower per step of m
+    float2 win[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) win[k] = gqs[8 * w + k + GMC - 1][lane];
+#pragma unroll
+    for (int mi = 0; mi < GMC; ++mi) {
+      if (mi > 0) {
+#pragma unroll
+        for (int k = 7; k > 0; --k) win[k] = win[k - 1];
+        win[0] = gqs[8 * w - mi + GMC - 1][lane];
+      }
+      const float2 wv = ws[mi][lane];
+      const float4* b4 = reinterpret_cast<const float4*>(&bs[mi][8 * w]);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float4 bb = b4[h];
+        cmac_conj(acc[2 * h], make_float2(bb.x, bb.y), win[2 * h] * wv);
+        cmac_conj(acc[2 * h + 1], make_float2(bb.z, bb.w), win[2 * h + 1] * wv);
+      }
+    }
+    __syncthreads();
+  }
+  if (j < d.nz) {
+    const FreqConst fc = d.fc[f];
+    const double sc = 2.0 / (double(N) * N) * sqrt(fc.s_abs);
+    const float2 scale = make_float2(float(sc * fc.rot_re), float(-sc * fc.rot_im));
+    float2* G = d.gbar + size_t(f) * N * d.nz;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float2* o = G + size_t(a0 + 8 * w + k) * d.nz + j;
+      const float2 v = scale * acc[k];
+      if (T) *o = *o + v;
+      else *o = v;
+    }
+  }
+}
+
+// ---- dJ/dc_l: reverse-mode differentiation of the depth march ------------------------------
+// Per (f, k), FP64.  Forward (recomputed): kappa_l, rho_l, r_l, A_l as in the march
+// (upward: y = kappa_{l+1}(1 - r_{l+1})/(1 + r_{l+1}), rho_l = (kappa_l - y)/(kappa_l + y),
+// r_l = rho_l E_l, E_l = e^{2 i kappa_l h_l}; downward: A_0 = i/(2 kappa_0),
+// A_{l+1} = A_l F_l, F_l = e^{i kappa_l h_l}(1 + rho_l)/(1 + r_{l+1}); field
+// g(z) = A_l (P + rho_l Q), P = e^{i kappa_l d}, Q = e^{i kappa_l (2 h_l - d)}, d = z - t_l).
+// Every step is holomorphic in its inputs, so with dJ = Re(gbar dg) each input's cotangent
+// is the sum over its uses of (output cotangent) x (complex partial derivative).  Reverse
+// order: the field, the downward recursion (l descending), the upward one (l ascending),
+// finally d kappa_l/d c_l = -omega~^2/(c_l^3 kappa_l).
+constexpr int GS_KAP = 0, GS_RHO = 1, GS_R = 2, GS_A = 3, GS_BKAP = 4, GS_BRHO = 5, GS_BA = 6, GS_BR = 7;
+constexpr int GS_SLOTS = 8;
+
+__global__ void __launch_bounds__(128) grad_recursion_kernel(Dev d) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  const int J = d.nlayer, N = d.N;
+  const bool live = k < d.nk;
+  const int kk = live ? k : 0;
+  auto at = [&](int l, int slot) -> double2& {
+    return d.gscr[((size_t(f) * J + l) * GS_SLOTS + slot) * d.nk + kk];
+  };
+  const double2 one = cmk(1.0, 0.0), zero = cmk(0.0, 0.0), I = cmk(0.0, 1.0);
+  const FreqConst fc = d.fc[f];
+  const double2 om = cmk(fc.om_re, fc.om_im), om2 = om * om;
+  const double kx = 2.0 * M_PI * double(kk) / (double(N) * d.dx);
+  if (live) {
+    for (int l = 0; l < J; ++l) {
+      const double ic2 = 1.0 / (d.layer_vel[l] * d.layer_vel[l]);
+      at(l, GS_KAP) = csqrt_upper(cmk(om2.x * ic2 - kx * kx, om2.y * ic2));
+      at(l, GS_BKAP) = zero; at(l, GS_BRHO) = zero; at(l, GS_BA) = zero; at(l, GS_BR) = zero;
+    }
+    // upward recursion
+    at(J - 1, GS_R) = zero;
+    at(J - 1, GS_RHO) = zero;
+    for (int l = J - 2; l >= 0; --l) {
+      const double h = d.layer_top[l + 1] - d.layer_top[l];
+      const double2 kl = at(l, GS_KAP), kn = at(l + 1, GS_KAP), rn = at(l + 1, GS_R);
+      const double2 y = cdiv(kn * (one - rn), one + rn);
+      const double2 rho = cdiv(kl - y, kl + y);
+      const double2 E = cexp(cmk(-2.0 * kl.y * h, 2.0 * kl.x * h));
+      at(l, GS_RHO) = rho;
+      at(l, GS_R) = rho * E;
+    }
+    // downward recursion
+    double2 A = cdiv(cmk(0.0, 0.5), at(0, GS_KAP));
+    for (int l = 0; l < J; ++l) {
+      at(l, GS_A) = A;
+      if (l < J - 1) {
+        const double h = d.layer_top[l + 1] - d.layer_top[l];
+        const double2 kl = at(l, GS_KAP);
+        const double2 e1 = cexp(cmk(-kl.y * h, kl.x * h));
+        A = cdiv(A * e1 * (one + at(l, GS_RHO)), one + at(l + 1, GS_R));
+      }
+    }
+    // field: gbar on the table index |n'| = k (both n = k and n = N - k use this row)
+    const float2* G = d.gbar + size_t(f) * N * d.nz;
+    for (int j = 0; j < d.nz; ++j) {
+      float2 gb = G[size_t(kk) * d.nz + j];
+      if (kk > 0 && kk < N / 2) gb = gb + G[size_t(N - kk) * d.nz + j];
+      const double2 gbar = cmk(double(gb.x), double(gb.y));
+      const int l = d.z_layer[j];
+      const double dd = d.z_off[j];
+      const double2 kl = at(l, GS_KAP), Al = at(l, GS_A);
+      const double2 P = cexp(cmk(-kl.y * dd, kl.x * dd));
+      if (l < J - 1) {
+        const double h = d.layer_top[l + 1] - d.layer_top[l];
+        const double2 rho = at(l, GS_RHO);
+        const double2 Q = cexp(cmk(-kl.y * (2.0 * h - dd), kl.x * (2.0 * h - dd)));
+        at(l, GS_BA) = at(l, GS_BA) + gbar * (P + rho * Q);
+        at(l, GS_BRHO) = at(l, GS_BRHO) + gbar * Al * Q;
+        at(l, GS_BKAP) = at(l, GS_BKAP) + gbar * Al * I * (dd * P + (2.0 * h - dd) * (rho * Q));
+      } else {
+        at(l, GS_BA) = at(l, GS_BA) + gbar * P;
+        at(l, GS_BKAP) = at(l, GS_BKAP) + gbar * Al * I * (dd * P);
+      }
+    }
+    // downward recursion, reversed: A_{l+1} = A_l F_l
+    for (int l = J - 2; l >= 0; --l) {
+      const double h = d.layer_top[l + 1] - d.layer_top[l];
+      const double2 kl = at(l, GS_KAP), rho = at(l, GS_RHO), rn = at(l + 1, GS_R), Al = at(l, GS_A);
+      const double2 e1 = cexp(cmk(-kl.y * h, kl.x * h));
+      const double2 inv1r = cdiv(one, one + rn);
+      const double2 F = e1 * (one + rho) * inv1r;
+      const double2 bA1 = at(l + 1, GS_BA);
+      const double2 bF = bA1 * Al;
+      at(l, GS_BA) = at(l, GS_BA) + bA1 * F;
+      at(l, GS_BKAP) = at(l, GS_BKAP) + bF * F * cmk(0.0, h);
+      at(l, GS_BRHO) = at(l, GS_BRHO) + bF * e1 * inv1r;
+      at(l + 1, GS_BR) = at(l + 1, GS_BR) - bF * F * inv1r;
+    }
+    {
+      const double2 k0 = at(0, GS_KAP);
+      at(0, GS_BKAP) = at(0, GS_BKAP) + at(0, GS_BA) * cdiv(cmk(0.0, -0.5), k0 * k0);
+    }
+    // upward recursion, reversed (l ascending: r_l's cotangent is complete when l is reached)
+    for (int l = 0; l <= J - 2; ++l) {
+      const double h = d.layer_top[l + 1] - d.layer_top[l];
+      const double2 kl = at(l, GS_KAP), kn = at(l + 1, GS_KAP), rn = at(l + 1, GS_R), rho = at(l, GS_RHO);
+      const double2 E = cexp(cmk(-2.0 * kl.y * h, 2.0 * kl.x * h));
+      const double2 bR = at(l, GS_BR);
+      double2 bRho = at(l, GS_BRHO) + bR * E;
+      double2 bK = at(l, GS_BKAP) + bR * rho * E * cmk(0.0, 2.0 * h);
+      const double2 y = cdiv(kn * (one - rn), one + rn);
+      const double2 s = kl + y, s2 = s * s;
+      bK = bK + bRho * cdiv(2.0 * y, s2);
+      const double2 bY = bRho * cdiv(-2.0 * kl, s2);
+      at(l, GS_BKAP) = bK;
+      at(l + 1, GS_BKAP) = at(l + 1, GS_BKAP) + bY * cdiv(one - rn, one + rn);
+      const double2 opr = one + rn;
+      at(l + 1, GS_BR) = at(l + 1, GS_BR) + bY * kn * cdiv(cmk(-2.0, 0.0), opr * opr);
+    }
+  }
+  // dJ/dc_l = Re(kappabar_l dkappa_l/dc_l), summed over (f, k): warp sums, one atomic per warp
+  for (int l = 0; l < J; ++l) {
+    double v = 0.0;
+    if (live) {
+      const double c = d.layer_vel[l];
+      const double2 dk = cdiv(-1.0 / (c * c * c) * om2, at(l, GS_KAP));
+      v = (at(l, GS_BKAP) * dk).x;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(d.gacc + 1 + l, v);
+  }
+}
+
+__global__ void grad_finalize_kernel(Dev d, double* J, double* gc) {
+  const double cj = 1.0 / (double(d.N) * d.N);
+  if (threadIdx.x == 0) J[0] = cj * d.gacc[0];
+  for (int l = threadIdx.x; l < d.nlayer; l += blockDim.x) gc[l] = d.gacc[1 + l];
+}
+
+}  // namespace
+
+bool grad_supported(const Dev& d) {
+  return d.geom == EDT_GEOM_LINE && d.precision == EDT_MIXED && d.N >= 64 && d.nlayer <= GRAD_MAX_LAYERS &&
+         d.gscr != nullptr;
+}
+
+cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const void* D, int D_dtype,
+                               double* J, void* gV, double* gc, cudaStream_t s) {
+  cudaError_t e;
+  grad_zero_kernel<<<152, 256, 0, s>>>(d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_lateral_dft(d, V, V_dtype, s)) != cudaSuccess) return e;
+  const int N = d.N;
+  for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
+    const int nfc = std::min(d.fchunk, d.nf - f0);
+    if ((e = launch_transform<float>(d, D, D_dtype, f0, nfc, s)) != cudaSuccess) return e;
+    grad_residual_kernel<<<dim3(N / RT, N / RT, nfc), 256, 0, s>>>(d, f0);
+    const dim3 gj(N / VM, (d.nz + 31) / 32, nfc);
+    grad_vhat_kernel<<<gj, 256, 0, s>>>(d, f0);
+    grad_gbar_kernel<0><<<gj, 256, 0, s>>>(d, f0);
+    grad_gbar_kernel<1><<<gj, 256, 0, s>>>(d, f0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  grad_recursion_kernel<<<dim3((d.nk + 127) / 128, d.nf), 128, 0, s>>>(d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_lateral_idft_real(d, d.adj, 2.0 / (double(N) * N), gV, V_dtype, s)) != cudaSuccess) return e;
+  grad_finalize_kernel<<<1, 64, 0, s>>>(d, J, gc);
+  return cudaGetLastError();
+}
+
+}  // namespace edt

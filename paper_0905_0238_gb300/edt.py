@@ -44,6 +44,7 @@ class edt_stats(C.Structure):
         ("gram_flop", C.c_double), ("n_notpd", C.c_int), ("n_nonfinite", C.c_int),
         ("last_status", C.c_int), ("launches_per_invert", C.c_int),
         ("gram_rows_padded", C.c_longlong), ("freq_chunk", C.c_int),
+        ("launches_per_grad", C.c_int),
     ]
 
 
@@ -94,6 +95,8 @@ def _lib() -> C.CDLL:
         L.edt_set_tuning.argtypes = [vp, C.POINTER(edt_tuning)]
         L.edt_read_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_char_p), i,
                                        C.POINTER(i)]
+        L.edt_misfit_grad.argtypes = [vp, vp, i, vp, i, vp, vp, vp, vp]
+        L.edt_set_reference.argtypes = [vp, C.POINTER(d), vp]
         L.edt_strerror.argtypes = [i]
         L.edt_strerror.restype = C.c_char_p
         L.edt_last_cuda_error.restype = C.c_char_p
@@ -102,7 +105,8 @@ def _lib() -> C.CDLL:
         for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
                      "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
-                     "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning"):
+                     "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning",
+                     "edt_misfit_grad", "edt_set_reference"):
             getattr(L, name).restype = i
         _LIB = L
     return _LIB
@@ -207,6 +211,19 @@ def edt_read_profile(ctx, max_stages: int = 16):
     n = _check(_lib().edt_read_profile(ctx, ms, names, max_stages, C.byref(ncalls)),
                "edt_read_profile")
     return {names[i].decode(): ms[i] for i in range(n)}, ncalls.value
+
+
+def edt_misfit_grad(ctx, V_ptr: int, V_dtype: int, D_ptr: int, D_dtype: int, J_ptr: int,
+                    gV_ptr: int, gc_ptr: int, stream: int):
+    _check(_lib().edt_misfit_grad(ctx, C.c_void_p(V_ptr), V_dtype, C.c_void_p(D_ptr), D_dtype,
+                                  C.c_void_p(J_ptr), C.c_void_p(gV_ptr), C.c_void_p(gc_ptr),
+                                  C.c_void_p(stream)), "edt_misfit_grad")
+
+
+def edt_set_reference(ctx, vel: np.ndarray, stream: int):
+    v = np.ascontiguousarray(vel, dtype=np.float64)
+    _check(_lib().edt_set_reference(ctx, v.ctypes.data_as(C.POINTER(C.c_double)),
+                                    C.c_void_p(stream)), "edt_set_reference")
 
 
 def edt_destroy(ctx):
@@ -334,6 +351,28 @@ class Solver:
         edt_forward(self.ctx, V.data_ptr(), self._rdtype(V), D.data_ptr(), self._cdtype(D),
                     self._stream())
         return D
+
+    def misfit_grad(self, V, D):
+        """(J, dJ/dV, dJ/dc) of J = ||F V - D||^2 (see edt_misfit_grad): J a 0-d float64
+        device tensor, dJ/dV of V's shape and dtype, dJ/dc float64 [nlayer] on the device."""
+        torch = self._torch
+        nf = len(self._freq)
+        if not (D.is_cuda and D.is_contiguous()) or tuple(D.shape) != self.cfg.data_shape(nf):
+            raise ValueError(f"D must be a contiguous CUDA tensor of shape {self.cfg.data_shape(nf)}")
+        if not (V.is_cuda and V.is_contiguous()) or tuple(V.shape) != self.cfg.model_shape():
+            raise ValueError(f"V must be a contiguous CUDA tensor of shape {self.cfg.model_shape()}")
+        J = torch.empty((), device=self.device, dtype=torch.float64)
+        gV = torch.empty_like(V)
+        gc = torch.empty((len(self._top),), device=self.device, dtype=torch.float64)
+        edt_misfit_grad(self.ctx, V.data_ptr(), self._rdtype(V), D.data_ptr(), self._cdtype(D),
+                        J.data_ptr(), gV.data_ptr(), gc.data_ptr(), self._stream())
+        return J, gV, gc
+
+    def set_reference(self, layer_vel):
+        """Replace the layer velocities of the reference (same layer tops)."""
+        vel = np.ascontiguousarray(np.asarray(layer_vel, dtype=np.float64))
+        edt_set_reference(self.ctx, vel, self._stream())
+        self._vel = vel
 
     def green(self):
         torch = self._torch
