@@ -29,8 +29,10 @@
 //                  in registers: Ahat accumulated across frequencies in FP64;
 //   grad_gbar<T>   (n, j) outputs, 8 consecutive n per thread walking m (legs q = n - m
 //                  slide the same way): S1 (T = 0) then S2 (T = 1) into the gbar buffer;
-// then once: grad_recursion (one thread per (f, k), FP64, the recursion forward and back),
-// the inverse lateral DFT of Ahat and a finalize kernel.
+// then once, in FP64: grad_march (per (f, k): the recursion forward), grad_field (per
+// (f, k, layer): the field's depths of that layer, reversed), grad_reverse (per (f, k): the
+// two recursions reversed, then the per-layer sums); the inverse lateral DFT of Ahat and a
+// finalize kernel.
 #include "edt_internal.h"
 #include "cplx.cuh"
 
@@ -289,113 +291,168 @@ __global__ void __launch_bounds__(256) grad_gbar_kernel(Dev d, int f0) {
 constexpr int GS_KAP = 0, GS_RHO = 1, GS_R = 2, GS_A = 3, GS_BKAP = 4, GS_BRHO = 5, GS_BA = 6, GS_BR = 7;
 constexpr int GS_SLOTS = 8;
 
-__global__ void __launch_bounds__(128) grad_recursion_kernel(Dev d) {
+__device__ __forceinline__ double2& gs_at(const Dev& d, int f, int l, int slot, int k) {
+  return d.gscr[((size_t(f) * d.nlayer + l) * GS_SLOTS + slot) * d.nk + k];
+}
+
+// forward march per (f, k): kappa_l, rho_l, r_l, A_l; the cotangent slots cleared
+__global__ void __launch_bounds__(128) grad_march_kernel(Dev d) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
-  const int J = d.nlayer, N = d.N;
-  const bool live = k < d.nk;
-  const int kk = live ? k : 0;
-  auto at = [&](int l, int slot) -> double2& {
-    return d.gscr[((size_t(f) * J + l) * GS_SLOTS + slot) * d.nk + kk];
-  };
-  const double2 one = cmk(1.0, 0.0), zero = cmk(0.0, 0.0), I = cmk(0.0, 1.0);
+  if (k >= d.nk) return;
+  const int J = d.nlayer;
+  const double2 one = cmk(1.0, 0.0), zero = cmk(0.0, 0.0);
   const FreqConst fc = d.fc[f];
   const double2 om = cmk(fc.om_re, fc.om_im), om2 = om * om;
-  const double kx = 2.0 * M_PI * double(kk) / (double(N) * d.dx);
-  if (live) {
-    for (int l = 0; l < J; ++l) {
-      const double ic2 = 1.0 / (d.layer_vel[l] * d.layer_vel[l]);
-      at(l, GS_KAP) = csqrt_upper(cmk(om2.x * ic2 - kx * kx, om2.y * ic2));
-      at(l, GS_BKAP) = zero; at(l, GS_BRHO) = zero; at(l, GS_BA) = zero; at(l, GS_BR) = zero;
-    }
-    // upward recursion
-    at(J - 1, GS_R) = zero;
-    at(J - 1, GS_RHO) = zero;
-    for (int l = J - 2; l >= 0; --l) {
+  const double kx = 2.0 * M_PI * double(k) / (double(d.N) * d.dx);
+  for (int l = 0; l < J; ++l) {
+    const double ic2 = 1.0 / (d.layer_vel[l] * d.layer_vel[l]);
+    gs_at(d, f, l, GS_KAP, k) = csqrt_upper(cmk(om2.x * ic2 - kx * kx, om2.y * ic2));
+    gs_at(d, f, l, GS_BR, k) = zero;
+  }
+  // upward recursion
+  double2 rn = zero, kn = gs_at(d, f, J - 1, GS_KAP, k);
+  gs_at(d, f, J - 1, GS_R, k) = zero;
+  gs_at(d, f, J - 1, GS_RHO, k) = zero;
+  for (int l = J - 2; l >= 0; --l) {
+    const double h = d.layer_top[l + 1] - d.layer_top[l];
+    const double2 kl = gs_at(d, f, l, GS_KAP, k);
+    const double2 y = cdiv(kn * (one - rn), one + rn);
+    const double2 rho = cdiv(kl - y, kl + y);
+    const double2 E = cexp(cmk(-2.0 * kl.y * h, 2.0 * kl.x * h));
+    gs_at(d, f, l, GS_RHO, k) = rho;
+    rn = rho * E;
+    gs_at(d, f, l, GS_R, k) = rn;
+    kn = kl;
+  }
+  // downward recursion
+  double2 A = cdiv(cmk(0.0, 0.5), gs_at(d, f, 0, GS_KAP, k));
+  for (int l = 0; l < J; ++l) {
+    gs_at(d, f, l, GS_A, k) = A;
+    if (l < J - 1) {
       const double h = d.layer_top[l + 1] - d.layer_top[l];
-      const double2 kl = at(l, GS_KAP), kn = at(l + 1, GS_KAP), rn = at(l + 1, GS_R);
-      const double2 y = cdiv(kn * (one - rn), one + rn);
-      const double2 rho = cdiv(kl - y, kl + y);
-      const double2 E = cexp(cmk(-2.0 * kl.y * h, 2.0 * kl.x * h));
-      at(l, GS_RHO) = rho;
-      at(l, GS_R) = rho * E;
+      const double2 kl = gs_at(d, f, l, GS_KAP, k);
+      const double2 e1 = cexp(cmk(-kl.y * h, kl.x * h));
+      A = cdiv(A * e1 * (one + gs_at(d, f, l, GS_RHO, k)), one + gs_at(d, f, l + 1, GS_R, k));
     }
-    // downward recursion
-    double2 A = cdiv(cmk(0.0, 0.5), at(0, GS_KAP));
-    for (int l = 0; l < J; ++l) {
-      at(l, GS_A) = A;
-      if (l < J - 1) {
-        const double h = d.layer_top[l + 1] - d.layer_top[l];
-        const double2 kl = at(l, GS_KAP);
-        const double2 e1 = cexp(cmk(-kl.y * h, kl.x * h));
-        A = cdiv(A * e1 * (one + at(l, GS_RHO)), one + at(l + 1, GS_R));
-      }
+  }
+}
+
+// field, reversed, per (f, k, l): the depths z_j of layer l (a contiguous index range) give
+// A_l, rho_l, kappa_l their cotangents; gbar on the table index |n'| = k (rows n = k and
+// N - k).  Within the layer P and Q advance by e^{+-i kappa dz} from a direct start.
+__global__ void __launch_bounds__(128) grad_field_kernel(Dev d) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = d.nlayer;
+  if (gid >= (long long)d.nf * J * d.nk) return;
+  const int k = int(gid % d.nk);
+  const long long fl = gid / d.nk;
+  const int l = int(fl % J), f = int(fl / J);
+  // depth range of layer l: first j with z_layer[j] >= l and >= l + 1
+  auto lower = [&](int v) {
+    int lo = 0, hi = d.nz;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (d.z_layer[mid] < v) lo = mid + 1; else hi = mid;
     }
-    // field: gbar on the table index |n'| = k (both n = k and n = N - k use this row)
+    return lo;
+  };
+  const int j0 = lower(l), j1 = lower(l + 1);
+  double2 bA = cmk(0.0, 0.0), bRho = bA, bK = bA;
+  if (j0 < j1) {
+    const int N = d.N;
+    const double2 kl = gs_at(d, f, l, GS_KAP, k), Al = gs_at(d, f, l, GS_A, k);
+    const bool last = l == J - 1;
+    const double h = last ? 0.0 : d.layer_top[l + 1] - d.layer_top[l];
+    const double2 rho = last ? cmk(0.0, 0.0) : gs_at(d, f, l, GS_RHO, k);
+    const double dz = d.dz;
+    const double2 Ef = cexp(cmk(-kl.y * dz, kl.x * dz));          // e^{+i kappa dz}
+    const double2 Eb = cexp(cmk(kl.y * dz, -kl.x * dz));          // e^{-i kappa dz}
+    double dd = d.z_off[j0];
+    double2 P = cexp(cmk(-kl.y * dd, kl.x * dd));
+    double2 Q = last ? cmk(0.0, 0.0) : cexp(cmk(-kl.y * (2.0 * h - dd), kl.x * (2.0 * h - dd)));
     const float2* G = d.gbar + size_t(f) * N * d.nz;
-    for (int j = 0; j < d.nz; ++j) {
-      float2 gb = G[size_t(kk) * d.nz + j];
-      if (kk > 0 && kk < N / 2) gb = gb + G[size_t(N - kk) * d.nz + j];
+    const bool two = k > 0 && k < N / 2;
+    for (int j = j0; j < j1; ++j) {
+      dd = d.z_off[j];
+      float2 gb = G[size_t(k) * d.nz + j];
+      if (two) gb = gb + G[size_t(N - k) * d.nz + j];
       const double2 gbar = cmk(double(gb.x), double(gb.y));
-      const int l = d.z_layer[j];
-      const double dd = d.z_off[j];
-      const double2 kl = at(l, GS_KAP), Al = at(l, GS_A);
-      const double2 P = cexp(cmk(-kl.y * dd, kl.x * dd));
-      if (l < J - 1) {
-        const double h = d.layer_top[l + 1] - d.layer_top[l];
-        const double2 rho = at(l, GS_RHO);
-        const double2 Q = cexp(cmk(-kl.y * (2.0 * h - dd), kl.x * (2.0 * h - dd)));
-        at(l, GS_BA) = at(l, GS_BA) + gbar * (P + rho * Q);
-        at(l, GS_BRHO) = at(l, GS_BRHO) + gbar * Al * Q;
-        at(l, GS_BKAP) = at(l, GS_BKAP) + gbar * Al * I * (dd * P + (2.0 * h - dd) * (rho * Q));
+      const double2 gA = gbar * Al;
+      if (!last) {
+        bA = bA + gbar * (P + rho * Q);
+        bRho = bRho + gA * Q;
+        bK = bK + gA * cmk(0.0, 1.0) * (dd * P + (2.0 * h - dd) * (rho * Q));
+        Q = Q * Eb;
       } else {
-        at(l, GS_BA) = at(l, GS_BA) + gbar * P;
-        at(l, GS_BKAP) = at(l, GS_BKAP) + gbar * Al * I * (dd * P);
+        bA = bA + gbar * P;
+        bK = bK + gA * cmk(0.0, 1.0) * (dd * P);
       }
+      P = P * Ef;
     }
+  }
+  gs_at(d, f, l, GS_BA, k) = bA;
+  gs_at(d, f, l, GS_BRHO, k) = bRho;
+  gs_at(d, f, l, GS_BKAP, k) = bK;
+}
+
+// the two recursions reversed per (f, k), then dJ/dc_l = Re(kappabar_l dkappa_l/dc_l)
+// summed over (f, k): warp sums, one atomic per warp and layer
+__global__ void __launch_bounds__(128) grad_reverse_kernel(Dev d) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  const int J = d.nlayer;
+  const bool live = k < d.nk;
+  const int kk = live ? k : 0;
+  const double2 one = cmk(1.0, 0.0);
+  const FreqConst fc = d.fc[f];
+  const double2 om = cmk(fc.om_re, fc.om_im), om2 = om * om;
+  if (live) {
     // downward recursion, reversed: A_{l+1} = A_l F_l
+    double2 bA1 = gs_at(d, f, J - 1, GS_BA, kk);
     for (int l = J - 2; l >= 0; --l) {
       const double h = d.layer_top[l + 1] - d.layer_top[l];
-      const double2 kl = at(l, GS_KAP), rho = at(l, GS_RHO), rn = at(l + 1, GS_R), Al = at(l, GS_A);
+      const double2 kl = gs_at(d, f, l, GS_KAP, kk), rho = gs_at(d, f, l, GS_RHO, kk);
+      const double2 rn = gs_at(d, f, l + 1, GS_R, kk), Al = gs_at(d, f, l, GS_A, kk);
       const double2 e1 = cexp(cmk(-kl.y * h, kl.x * h));
       const double2 inv1r = cdiv(one, one + rn);
       const double2 F = e1 * (one + rho) * inv1r;
-      const double2 bA1 = at(l + 1, GS_BA);
       const double2 bF = bA1 * Al;
-      at(l, GS_BA) = at(l, GS_BA) + bA1 * F;
-      at(l, GS_BKAP) = at(l, GS_BKAP) + bF * F * cmk(0.0, h);
-      at(l, GS_BRHO) = at(l, GS_BRHO) + bF * e1 * inv1r;
-      at(l + 1, GS_BR) = at(l + 1, GS_BR) - bF * F * inv1r;
+      const double2 bA = gs_at(d, f, l, GS_BA, kk) + bA1 * F;
+      gs_at(d, f, l, GS_BKAP, kk) = gs_at(d, f, l, GS_BKAP, kk) + bF * F * cmk(0.0, h);
+      gs_at(d, f, l, GS_BRHO, kk) = gs_at(d, f, l, GS_BRHO, kk) + bF * e1 * inv1r;
+      gs_at(d, f, l + 1, GS_BR, kk) = gs_at(d, f, l + 1, GS_BR, kk) - bF * F * inv1r;
+      bA1 = bA;
     }
     {
-      const double2 k0 = at(0, GS_KAP);
-      at(0, GS_BKAP) = at(0, GS_BKAP) + at(0, GS_BA) * cdiv(cmk(0.0, -0.5), k0 * k0);
+      const double2 k0 = gs_at(d, f, 0, GS_KAP, kk);
+      gs_at(d, f, 0, GS_BKAP, kk) = gs_at(d, f, 0, GS_BKAP, kk) + bA1 * cdiv(cmk(0.0, -0.5), k0 * k0);
     }
     // upward recursion, reversed (l ascending: r_l's cotangent is complete when l is reached)
     for (int l = 0; l <= J - 2; ++l) {
       const double h = d.layer_top[l + 1] - d.layer_top[l];
-      const double2 kl = at(l, GS_KAP), kn = at(l + 1, GS_KAP), rn = at(l + 1, GS_R), rho = at(l, GS_RHO);
+      const double2 kl = gs_at(d, f, l, GS_KAP, kk), kn = gs_at(d, f, l + 1, GS_KAP, kk);
+      const double2 rn = gs_at(d, f, l + 1, GS_R, kk), rho = gs_at(d, f, l, GS_RHO, kk);
       const double2 E = cexp(cmk(-2.0 * kl.y * h, 2.0 * kl.x * h));
-      const double2 bR = at(l, GS_BR);
-      double2 bRho = at(l, GS_BRHO) + bR * E;
-      double2 bK = at(l, GS_BKAP) + bR * rho * E * cmk(0.0, 2.0 * h);
-      const double2 y = cdiv(kn * (one - rn), one + rn);
-      const double2 s = kl + y, s2 = s * s;
+      const double2 bR = gs_at(d, f, l, GS_BR, kk);
+      const double2 bRho = gs_at(d, f, l, GS_BRHO, kk) + bR * E;
+      double2 bK = gs_at(d, f, l, GS_BKAP, kk) + bR * rho * E * cmk(0.0, 2.0 * h);
+      const double2 opr = one + rn;
+      const double2 y = cdiv(kn * (one - rn), opr);
+      const double2 sm = kl + y, s2 = sm * sm;
       bK = bK + bRho * cdiv(2.0 * y, s2);
       const double2 bY = bRho * cdiv(-2.0 * kl, s2);
-      at(l, GS_BKAP) = bK;
-      at(l + 1, GS_BKAP) = at(l + 1, GS_BKAP) + bY * cdiv(one - rn, one + rn);
-      const double2 opr = one + rn;
-      at(l + 1, GS_BR) = at(l + 1, GS_BR) + bY * kn * cdiv(cmk(-2.0, 0.0), opr * opr);
+      gs_at(d, f, l, GS_BKAP, kk) = bK;
+      gs_at(d, f, l + 1, GS_BKAP, kk) = gs_at(d, f, l + 1, GS_BKAP, kk) + bY * cdiv(one - rn, opr);
+      gs_at(d, f, l + 1, GS_BR, kk) = gs_at(d, f, l + 1, GS_BR, kk) + bY * kn * cdiv(cmk(-2.0, 0.0), opr * opr);
     }
   }
-  // dJ/dc_l = Re(kappabar_l dkappa_l/dc_l), summed over (f, k): warp sums, one atomic per warp
   for (int l = 0; l < J; ++l) {
     double v = 0.0;
     if (live) {
       const double c = d.layer_vel[l];
-      const double2 dk = cdiv(-1.0 / (c * c * c) * om2, at(l, GS_KAP));
-      v = (at(l, GS_BKAP) * dk).x;
+      const double2 dk = cdiv(-1.0 / (c * c * c) * om2, gs_at(d, f, l, GS_KAP, kk));
+      v = (gs_at(d, f, l, GS_BKAP, kk) * dk).x;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(d.gacc + 1 + l, v);
@@ -432,7 +489,11 @@ cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const v
     grad_gbar_kernel<1><<<gj, 256, 0, s>>>(d, f0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  grad_recursion_kernel<<<dim3((d.nk + 127) / 128, d.nf), 128, 0, s>>>(d);
+  const dim3 gk((d.nk + 127) / 128, d.nf);
+  grad_march_kernel<<<gk, 128, 0, s>>>(d);
+  const long long nfl = (long long)d.nf * d.nlayer * d.nk;
+  grad_field_kernel<<<unsigned((nfl + 127) / 128), 128, 0, s>>>(d);
+  grad_reverse_kernel<<<gk, 128, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_lateral_idft_real(d, d.adj, 2.0 / (double(N) * N), gV, V_dtype, s)) != cudaSuccess) return e;
   grad_finalize_kernel<<<1, 64, 0, s>>>(d, J, gc);
