@@ -238,6 +238,21 @@ int edt_forward(edt_ctx* ctx, const void* V_dev, int V_dtype, void* D_dev, int D
 int edt_misfit_grad(edt_ctx* ctx, const void* V_dev, int V_dtype, const void* D_dev,
                     int D_dtype, double* J_dev, void* gV_dev, double* gc_dev, void* stream);
 
+/* Adjoint of the inversion (line geometry, EDT_MIXED).  edt_invert maps D linearly to V
+ * (the normal matrices and the damping depend on the reference only), V = S D; this call
+ * computes Dbar = S^T Vbar for the real inner products <V1, V2> = sum V1 V2 and
+ * <D1, D2> = Re sum conj(D1) D2 -- the gradient of any loss L(V) with respect to D, given
+ * Vbar = dL/dV.  It reuses the factors of the last successful edt_invert on this context
+ * (EDT_EINVAL if there is none, or if edt_gram, edt_set_workspace or edt_set_reference ran
+ * since): xbar from the lateral DFT of Vbar, bbar = (G + lam I)^-1 xbar with the same
+ * refinement steps as the forward solve (the transpose of the forward's own linear map),
+ * and for every kept row the split and the data transform reversed.  Vbar_dev: [nx][nz]
+ * (EDT_F32/EDT_F64); Dbar_dev: [nfreq][nx][nx] (EDT_C64/EDT_C128), fully written.  The
+ * solve's scratch (b, x, the residual and the right-hand sides) is overwritten; the
+ * factors and edt_get_vhat's result are not, so the call may be repeated for other Vbar. */
+int edt_invert_adjoint(edt_ctx* ctx, const void* Vbar_dev, int Vbar_dtype, void* Dbar_dev,
+                       int Dbar_dtype, void* stream);
+
 /* Replace the layer velocities of the reference (same layer tops); every later call uses
  * them (the depth march runs in every call).  With cutoff > 0 the row plan depends on the
  * slowest velocity, so that minimum must stay the same (else EDT_EINVAL: create a new

@@ -244,3 +244,49 @@ def adjoint(wl, D, g=None):
                                 axis=0)
     # adjoint of V -> sum_x V exp(-i k_m x), restricted to real V
     return np.real(np.fft.ifft(vh_adj, axis=0) * N)
+
+
+# ----------------------------------------------------------------------------- adjoint
+def invert_adjoint(wl, Vbar, g=None):
+    """Dbar = S^T Vbar for the linear map S: D -> V of :func:`invert` (the damped solves'
+    matrices depend on the reference only), for <V1, V2> = sum V1 V2 and
+    <D1, D2> = Re sum conj(D1) D2.  Every step of :func:`invert` reversed:
+
+    * V = Re (1/N) sum_m Vhat(m) e^{i k_m x} with Vhat(m) = x_+ + i x_- (m = 0..N/2) and its
+      conjugate at -m gives xbar(m) = (c_m/N) (Re, Im) sum_x Vbar e^{-i k_m x}, c_m = 1 at the
+      self-paired m and 2 otherwise;
+    * x = argmin ||Ahat x - dhat||^2 + lam ||x||^2 = (Ahat^T Ahat + lam I)^-1 Ahat^T dhat gives
+      dhat_bar = Ahat (Ahat^T Ahat + lam I)^-1 xbar;
+    * d_+ = (a + b)/2, d_- = (a - b)/(2i) with a = D2(p, q), b = D2(q, p) give
+      abar = dbar_+/2 + (i/2) dbar_-, bbar = dbar_+/2 - (i/2) dbar_-;
+    * D2 = T D with T/N unitary per axis gives Dbar = T^H D2bar = N^2 T^-1 D2bar.
+    """
+    N = wl.nx
+    nz = wl.nz
+    if g is None:
+        g = green_table(wl)
+    vb = np.fft.fft(np.asarray(Vbar, dtype=np.float64), axis=0)       # sum_x Vbar e^{-i k_m x}
+    D2bar = np.zeros((len(wl.freq_hz), N, N), dtype=np.complex128)
+    for m in range(N // 2 + 1):
+        rows = kept_rows(wl, m)
+        if len(rows) == 0:
+            continue
+        self_paired = (m == 0) or (2 * m == N)
+        c = (1.0 if self_paired else 2.0) / N
+        A = kernel_rows(wl, m, rows, g)
+        Ahat = np.vstack([A.real, A.imag])
+        lam = wl.alpha * np.sum(Ahat ** 2)
+        H = Ahat.T @ Ahat + lam * np.eye(nz)
+        cols = [c * vb[m].real] + ([] if self_paired else [c * vb[m].imag])
+        y = np.linalg.solve(H, np.stack(cols, axis=1))
+        db = Ahat @ y                                                 # (2R, ncol)
+        R = len(rows)
+        dp = db[:R, 0] + 1j * db[R:, 0]
+        dm = (db[:R, 1] + 1j * db[R:, 1]) if not self_paired else np.zeros(R, complex)
+        abar = 0.5 * dp + 0.5j * dm
+        bbar = 0.5 * dp - 0.5j * dm
+        f, p = rows[:, 0], rows[:, 1]
+        q = (p - m) % N
+        np.add.at(D2bar, (f, p, q), abar)
+        np.add.at(D2bar, (f, q, p), bbar)
+    return N ** 2 * inverse_data_transform(D2bar)

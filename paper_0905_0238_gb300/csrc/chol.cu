@@ -473,6 +473,11 @@ cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_chol_resolve(const Dev& d, cudaStream_t s) {
+  chol_solve_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s) {
   if (d.L32) chol_refine32_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(float), s>>>(d);
   else chol_solve_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 1);

@@ -58,6 +58,7 @@ struct edt_ctx {
   long long rows_max_sub = 0;
   // band-limited transform of the mixed path
   bool band_mode = false;
+  bool have_factor = false;            // the workspace holds the factors of the last edt_invert
   std::vector<BandInfo> band;
   std::vector<int2> bcol;
   std::vector<long long> cpre;
@@ -755,6 +756,7 @@ int edt_create(edt_ctx** out, const edt_config* cfg, size_t* workspace_bytes) {
 }
 
 int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
+  if (c) c->have_factor = false;
   if (!c || !ws) return EDT_EINVAL;
   if (bytes < c->ws_bytes) return EDT_ENOMEM_WS;
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return EDT_EINVAL;
@@ -877,7 +879,22 @@ int edt_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, voi
     r = run_invert(c, D, D_dtype, V, V_dtype, s);
   }
   c->last_status = r;
+  c->have_factor = r == EDT_OK;
   return r;
+}
+
+int edt_invert_adjoint(edt_ctx* c, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype, void* stream) {
+  if (!c || !Vbar || !Dbar) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (Dbar_dtype != EDT_C64 && Dbar_dtype != EDT_C128) return EDT_EINVAL;
+  if (Vbar_dtype != EDT_F32 && Vbar_dtype != EDT_F64) return EDT_EINVAL;
+  if (c->win || c->cfg.precision != EDT_MIXED) return EDT_EUNSUPPORTED;
+  if (!c->have_factor) return EDT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  EDT_TRY(launch_invert_adjoint(c->dev, Vbar, Vbar_dtype, Dbar, Dbar_dtype, c->cfg.refine, c->r_rhs.bytes, s));
+  c->have_factor = true;                  // the factors are untouched; b, x, r and rhs are not
+  return EDT_OK;
 }
 
 int edt_get_tuning(const edt_ctx* c, edt_tuning* o) {
@@ -1025,6 +1042,7 @@ int edt_set_reference(edt_ctx* c, const double* vel, void* stream) {
     if (cmin_new != cmin_old) return EDT_EINVAL;
   }
   std::copy(vel, vel + c->nlayer, c->vel.begin());
+  c->have_factor = false;                 // the factors belong to the old reference
   if (c->ws) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EDT_TRY(cudaMemcpyAsync(at<void*>(c, c->r_lvel), c->vel.data(), c->nlayer * sizeof(double),
@@ -1052,6 +1070,7 @@ int edt_get_vhat(edt_ctx* c, void* vhat_dev, void* stream) {
 }
 
 int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr, void* stream) {
+  if (c) c->have_factor = false;
   if (!c || !D || !G || !b || !tr) return EDT_EINVAL;
   if (!c->ws) return EDT_ENOMEM_WS;
   if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;

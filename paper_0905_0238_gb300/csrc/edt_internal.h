@@ -191,6 +191,16 @@ cudaError_t launch_lateral_dft(const Dev& d, const void* V, int V_dtype, cudaStr
 cudaError_t launch_lateral_idft_real(const Dev& d, const double2* in, double scale, void* out,
                                      int out_dtype, cudaStream_t s);
 
+// Adjoint of the data transform on the chunk's planes X (FP32) into D[f0 .. f0 + nfc).
+cudaError_t launch_transform_adjoint(const Dev& d, void* D, int D_dtype, int f0, int nfc, cudaStream_t s);
+// x = (LL^T)^-1 b with the factors of the last factorisation (no refactorisation).
+cudaError_t launch_chol_resolve(const Dev& d, cudaStream_t s);
+// Dbar = S^T Vbar for the linear map S: D -> V of the last edt_invert (mixed line path),
+// with `refine` refinement steps like the forward solve; rhs_bytes: size of d.rhs (zeroed
+// as scratch).
+cudaError_t launch_invert_adjoint(const Dev& d, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype,
+                                  int refine, size_t rhs_bytes, cudaStream_t s);
+
 // Misfit J = ||F V - D||^2 and its gradients (csrc/grad.cu); layers the reverse-mode depth
 // march supports (its per-(f, k) scratch is sized by it).
 constexpr int GRAD_MAX_LAYERS = 64;

@@ -495,6 +495,16 @@ cudaError_t forward_chunk(const Dev& d, void* D, int D_dtype, int f0, int nfc, c
   return rows_fft<T>(d, d.X, xdtype, Dc, D_dtype, (long long)nfc * d.N, +1, T(1) / T(d.N), s);
 }
 
+// Adjoint of the data transform on the chunk's planes X[fi][q][p] (FP32): the conjugate
+// transpose of pass 2 (sign -, unscaled) then of pass 1 (sign +, unscaled) into D[f0 + fi].
+cudaError_t launch_transform_adjoint(const Dev& d, void* D, int D_dtype, int f0, int nfc, cudaStream_t s) {
+  const size_t esz = D_dtype == EDT_C64 ? sizeof(float2) : sizeof(double2);
+  void* Dc = static_cast<char*>(D) + size_t(f0) * d.N * d.N * esz;
+  cudaError_t e = cols_fft<float>(d, reinterpret_cast<float2*>(d.X), nfc, -1, 1.f, s);
+  if (e != cudaSuccess) return e;
+  return rows_fft<float>(d, d.X, EDT_C64, Dc, D_dtype, (long long)nfc * d.N, +1, 1.f, s);
+}
+
 cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
                            cudaStream_t s) {
   size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);

@@ -465,7 +465,108 @@ __global__ void grad_finalize_kernel(Dev d, double* J, double* gc) {
   for (int l = threadIdx.x; l < d.nlayer; l += blockDim.x) gc[l] = d.gacc[1 + l];
 }
 
+// ---- adjoint of the inversion D -> V (linear in D: G and lam depend on the rows only) --------
+// V = (1/N) Re sum_m Vhat(m) e^{i k_m x} with Vhat(m) = x_+ + i x_- for m = 0..N/2 and the
+// conjugate for -m, so dV/dx_+(m) = (c_m/N) cos(k_m x), dV/dx_-(m) = -(c_m/N) sin(k_m x),
+// c_m = 1 at the self-paired m (x_- = 0 there) and 2 otherwise: xbar(m) = (c_m/N) DFT(Vbar)(m).
+// xbar goes where the forward solve reads b.
+__global__ void adj_xbar_kernel(Dev d) {
+  const int m = blockIdx.x, N = d.N;
+  const bool self = m == 0 || 2 * m == N;
+  const double c = (self ? 1.0 : 2.0) / double(N);
+  for (int z = threadIdx.x; z < d.nz; z += blockDim.x) {
+    const double2 v = d.vfull[size_t(m) * d.nz + z];
+    d.b[(size_t(m) * d.nz + z) * 2 + 0] = c * v.x;
+    d.b[(size_t(m) * d.nz + z) * 2 + 1] = self ? 0.0 : c * v.y;
+  }
+}
+
+// r += xbar: with zero right-hand sides the refinement kernel leaves r = -Ahat^T Ahat y, so
+// this makes r - lam y = xbar - (Ahat^T Ahat + lam I) y, the residual of the adjoint solve.
+__global__ void adj_addb_kernel(Dev d) {
+  const size_t n = size_t(d.nsub) * d.nz * 2;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    d.r[i] += d.b[i];
+}
+
+// Per kept row (f, p) of m at frequencies [f0, f1), with bbar = (G + lam I)^-1 xbar in d.x:
+// b_+- = sum_rows w Re(conj(row) rhs_+-) gives rhsbar = w sum_z row(z) bbar(z); then the
+// rotation rhs = rot d, the split d_+ = (a + c)/2, d_- = (a - c)/(2i) with a = D2(p, q),
+// c = D2(q, p) (folded rows: a and c the means with D2(-q, -p), D2(-p, -q)) are reversed and
+// scattered (atomically) into the chunk's planes X[fi][q][p] = D2bar(p, q).
+__global__ void __launch_bounds__(256) adj_rows_kernel(Dev d, int f0, int f1) {
+  const int m = blockIdx.y, N = d.N, msk = N - 1;
+  if (d.status[m] != EDT_OK) return;
+  const long long r0 = d.row_off_mf[size_t(m) * (d.nf + 1) + f0];
+  const long long r1 = d.row_off_mf[size_t(m) * (d.nf + 1) + f1];
+  const double* yb = d.x + size_t(m) * d.nz * 2;
+  float2* X = reinterpret_cast<float2*>(d.X);
+  for (long long ri = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; ri < r1;
+       ri += (long long)gridDim.x * blockDim.x) {
+    const uint32_t row = d.rows[ri];
+    const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
+    const float2* g1 = d.g32 + (size_t(f) * d.nk + tab_index(p, N)) * d.nzs;
+    const float2* g2 = d.g32 + (size_t(f) * d.nk + tab_index(q, N)) * d.nzs;
+    float2 sp = make_float2(0.f, 0.f), sm = sp;
+    for (int z = 0; z < d.nz; ++z) {
+      const float2 t = g1[z] * g2[z];
+      const float bp = float(yb[2 * z]), bm = float(yb[2 * z + 1]);
+      sp.x = fmaf(t.x, bp, sp.x); sp.y = fmaf(t.y, bp, sp.y);
+      sm.x = fmaf(t.x, bm, sm.x); sm.y = fmaf(t.y, bm, sm.y);
+    }
+    const bool w2 = row_w2(row);
+    const FreqConst fc = d.fc[f];
+    const float2 crot = make_float2(float(fc.rot_re), float(-fc.rot_im));   // conj(rot)
+    const float w = w2 ? 2.f : 1.f;
+    const float2 dp = crot * (w * sp), dm = crot * (w * sm);
+    // abar = dp/2 + (i/2) dm, cbar = dp/2 - (i/2) dm; folded rows split each in halves
+    const float h = w2 ? 0.25f : 0.5f;
+    const float2 abar = make_float2(h * (dp.x - dm.y), h * (dp.y + dm.x));
+    const float2 cbar = make_float2(h * (dp.x + dm.y), h * (dp.y - dm.x));
+    float2* P = X + size_t(f - f0) * N * N;
+    auto add = [&](int pp, int qq, float2 v) {             // D2bar(pp, qq) at X[qq][pp]
+      float* o = reinterpret_cast<float*>(P + size_t(qq & msk) * N + (pp & msk));
+      atomicAdd(o, v.x);
+      atomicAdd(o + 1, v.y);
+    };
+    add(p, q, abar);
+    add(q, p, cbar);
+    if (w2) {
+      add(-q, -p, abar);
+      add(-p, -q, cbar);
+    }
+  }
+}
+
 }  // namespace
+
+// The forward solve with k refinement steps is x = sum_{i<=k} (I - Ht^-1 H)^i Ht^-1 b (Ht the
+// factored matrix, H = Ahat^T Ahat + lam I from the rows), a symmetric map: its transpose is
+// the same iteration applied to xbar, run here with the forward's own kernels.
+cudaError_t launch_invert_adjoint(const Dev& d, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype,
+                                  int refine, size_t rhs_bytes, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = launch_lateral_dft(d, Vbar, Vbar_dtype, s)) != cudaSuccess) return e;
+  adj_xbar_kernel<<<d.nsub, 256, 0, s>>>(d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_chol_resolve(d, s)) != cudaSuccess) return e;
+  if (refine > 0 && (e = cudaMemsetAsync(d.rhs, 0, rhs_bytes, s)) != cudaSuccess) return e;
+  for (int it = 0; it < refine; ++it) {
+    if ((e = cudaMemsetAsync(d.r, 0, sizeof(double) * d.nsub * d.nz * 2, s)) != cudaSuccess) return e;
+    if ((e = launch_refine(d, s)) != cudaSuccess) return e;
+    adj_addb_kernel<<<152, 256, 0, s>>>(d);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_refine_update(d, s)) != cudaSuccess) return e;
+  }
+  for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
+    const int nfc = std::min(d.fchunk, d.nf - f0);
+    if ((e = cudaMemsetAsync(d.X, 0, size_t(nfc) * d.N * d.N * sizeof(float2), s)) != cudaSuccess) return e;
+    adj_rows_kernel<<<dim3(8, d.nsub), 256, 0, s>>>(d, f0, f0 + nfc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_transform_adjoint(d, Dbar, Dbar_dtype, f0, nfc, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 bool grad_supported(const Dev& d) {
   return d.geom == EDT_GEOM_LINE && d.precision == EDT_MIXED && d.N >= 64 && d.nlayer <= GRAD_MAX_LAYERS &&

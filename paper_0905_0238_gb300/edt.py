@@ -96,6 +96,7 @@ def _lib() -> C.CDLL:
         L.edt_read_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_char_p), i,
                                        C.POINTER(i)]
         L.edt_misfit_grad.argtypes = [vp, vp, i, vp, i, vp, vp, vp, vp]
+        L.edt_invert_adjoint.argtypes = [vp, vp, i, vp, i, vp]
         L.edt_set_reference.argtypes = [vp, C.POINTER(d), vp]
         L.edt_strerror.argtypes = [i]
         L.edt_strerror.restype = C.c_char_p
@@ -106,7 +107,7 @@ def _lib() -> C.CDLL:
                      "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
                      "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning",
-                     "edt_misfit_grad", "edt_set_reference"):
+                     "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint"):
             getattr(L, name).restype = i
         _LIB = L
     return _LIB
@@ -218,6 +219,12 @@ def edt_misfit_grad(ctx, V_ptr: int, V_dtype: int, D_ptr: int, D_dtype: int, J_p
     _check(_lib().edt_misfit_grad(ctx, C.c_void_p(V_ptr), V_dtype, C.c_void_p(D_ptr), D_dtype,
                                   C.c_void_p(J_ptr), C.c_void_p(gV_ptr), C.c_void_p(gc_ptr),
                                   C.c_void_p(stream)), "edt_misfit_grad")
+
+
+def edt_invert_adjoint(ctx, Vbar_ptr: int, Vbar_dtype: int, Dbar_ptr: int, Dbar_dtype: int,
+                       stream: int):
+    _check(_lib().edt_invert_adjoint(ctx, C.c_void_p(Vbar_ptr), Vbar_dtype, C.c_void_p(Dbar_ptr),
+                                     Dbar_dtype, C.c_void_p(stream)), "edt_invert_adjoint")
 
 
 def edt_set_reference(ctx, vel: np.ndarray, stream: int):
@@ -367,6 +374,19 @@ class Solver:
         edt_misfit_grad(self.ctx, V.data_ptr(), self._rdtype(V), D.data_ptr(), self._cdtype(D),
                         J.data_ptr(), gV.data_ptr(), gc.data_ptr(), self._stream())
         return J, gV, gc
+
+    def invert_adjoint(self, Vbar, out_dtype=None):
+        """Dbar = S^T Vbar for the linear map S: D -> V of the last invert (see
+        edt_invert_adjoint); Dbar has the data's shape."""
+        torch = self._torch
+        nf = len(self._freq)
+        if not (Vbar.is_cuda and Vbar.is_contiguous()) or tuple(Vbar.shape) != self.cfg.model_shape():
+            raise ValueError(f"Vbar must be a contiguous CUDA tensor of shape {self.cfg.model_shape()}")
+        Dbar = torch.empty(self.cfg.data_shape(nf), device=self.device,
+                           dtype=out_dtype or torch.complex128)
+        edt_invert_adjoint(self.ctx, Vbar.data_ptr(), self._rdtype(Vbar), Dbar.data_ptr(),
+                           self._cdtype(Dbar), self._stream())
+        return Dbar
 
     def set_reference(self, layer_vel):
         """Replace the layer velocities of the reference (same layer tops)."""

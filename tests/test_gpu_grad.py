@@ -148,3 +148,30 @@ def test_config1_geometry_single_frequency_matches_oracle(fi):
     assert abs(float(J.cpu()) - J_or) < 1e-5 * J_or
     assert rel_l2(gc.cpu().numpy(), gc_or) < 1e-5
     assert rel_l2(gV.cpu().numpy(), gV_or) < 1e-5
+
+
+@pytest.mark.parametrize("fold", [1, 0])
+def test_invert_adjoint_matches_oracle(fold):
+    """Dbar = S^T Vbar of the mixed inversion against the oracle's adjoint (FP64 solves with
+    the FP64 normal matrix): relative L2 within the mixed path's accuracy; and the
+    dot-product identity <S D, Vbar> = Re <D, S^T Vbar> of the GPU pair itself."""
+    from tests.gpu_helpers import small_workload
+    wl = small_workload(nx=64, nz=24, nf=6, alpha=1e-3, cutoff=1.0)
+    rng = np.random.default_rng(4)
+    Vbar = rng.standard_normal((wl.nx, wl.nz))
+    D = rng.standard_normal((6, wl.nx, wl.nx)) + 1j * rng.standard_normal((6, wl.nx, wl.nx))
+    want = edt2d.invert_adjoint(wl, Vbar)
+    s = solver(wl, fold=fold)
+    V = s.invert(dev(D))
+    Dbar = s.invert_adjoint(dev(Vbar))
+    got = Dbar.cpu().numpy()
+    assert rel_l2(got, want) < 1e-5, rel_l2(got, want)
+    lhs = float(torch.sum(V * dev(Vbar)).cpu())
+    rhs = float(np.real(np.vdot(D, got)))
+    assert abs(lhs - rhs) < 1e-4 * abs(lhs), (lhs, rhs)
+    # autograd: V = invert(D) and dL/dD for L = <V, Vbar>
+    from paper_0905_0238_gb300.autograd import invert
+    Dt = dev(D).requires_grad_(True)
+    Vt = invert(s, Dt)
+    torch.sum(Vt * dev(Vbar)).backward()
+    assert rel_l2(Dt.grad.cpu().numpy(), got) < 1e-6

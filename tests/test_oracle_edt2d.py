@@ -176,3 +176,41 @@ def test_pins_catch_planted_mistakes(monkeypatch):
         om = edt2d.complex_omega(wl.freq_hz, wl.eps)
         Db = born_space_domain(om[0], g[0], V, wl.dx, wl.dz)
         assert not np.allclose(D[0], Db, rtol=1e-6)
+
+
+@pytest.mark.parametrize("cutoff", [1.0, 0.0])
+def test_invert_adjoint_dot_product(cutoff):
+    """<S D, Vbar> = Re <D, S^T Vbar>: the inversion is linear in D, and the adjoint is the
+    transpose of that linear map (random D and Vbar)."""
+    import synth
+    tops, vel = synth.layers_gradient_staircase(1500.0, 2500.0, 60.0, 10.0, sub=2)
+    wl = synth.Workload("adj", nx=16, dx=10.0, freq_hz=synth.freqs_uniform(4, 10.0, 40.0),
+                        eps=0.15, nz=6, dz=10.0, z0=0.0, layer_top=tops, layer_vel=vel,
+                        alpha=1e-3, cutoff=cutoff)
+    rng = np.random.default_rng(9)
+    D = rng.standard_normal((4, 16, 16)) + 1j * rng.standard_normal((4, 16, 16))
+    Vbar = rng.standard_normal((16, 6))
+    V, _ = edt2d.invert(wl, D)
+    Dbar = edt2d.invert_adjoint(wl, Vbar)
+    lhs = float(np.sum(V * Vbar))
+    rhs = float(np.real(np.vdot(D, Dbar)))
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_invert_adjoint_pin_catches_a_row_mismatch(monkeypatch):
+    """A planted mistake -- the adjoint dropping the last kept row of every system, as a
+    cut evaluated differently from the forward's would -- breaks the dot-product identity."""
+    import synth
+    tops, vel = synth.layers_gradient_staircase(1500.0, 2500.0, 60.0, 10.0, sub=2)
+    wl = synth.Workload("adj", nx=16, dx=10.0, freq_hz=synth.freqs_uniform(4, 10.0, 40.0),
+                        eps=0.15, nz=6, dz=10.0, z0=0.0, layer_top=tops, layer_vel=vel,
+                        alpha=1e-3, cutoff=1.0)
+    rng = np.random.default_rng(9)
+    D = rng.standard_normal((4, 16, 16)) + 1j * rng.standard_normal((4, 16, 16))
+    Vbar = rng.standard_normal((16, 6))
+    V, _ = edt2d.invert(wl, D)
+    lhs = float(np.sum(V * Vbar))
+    orig = edt2d.kept_rows
+    monkeypatch.setattr(edt2d, "kept_rows", lambda w, m: orig(w, m)[:-1])
+    rhs = float(np.real(np.vdot(D, edt2d.invert_adjoint(wl, Vbar))))
+    assert abs(lhs - rhs) > 1e-6 * abs(lhs)
