@@ -710,6 +710,30 @@ def main_grad(args, world, rank, local):
     h1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(h0.elapsed_time(h1), world)
+    # adjoint of the production inversion (cut on, as edt_invert runs it): dL/dD for a
+    # loss of V, timed beside the inversion it differentiates
+    inv = Solver(Config.from_workload(synth.preset(WORKLOAD), precision=EDT_MIXED), device=dev)
+    Vout = torch.empty((wl.nx, wl.nz), device=dev, dtype=torch.float32)
+    Vbar = torch.randn((wl.nx, wl.nz), device=dev, generator=gen, dtype=torch.float32)
+    for _ in range(3):
+        inv.invert(D, out=Vout)
+        inv.invert_adjoint(Vbar, out_dtype=torch.complex64)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a2 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.steps):
+        inv.invert(D, out=Vout)
+    a1.record(stream)
+    for _ in range(args.steps):
+        Dbar = inv.invert_adjoint(Vbar, out_dtype=torch.complex64)
+    a2.record(stream)
+    torch.cuda.synchronize()
+    adj = dict(invert_ms=a0.elapsed_time(a1) / args.steps, invert_adjoint_ms=a1.elapsed_time(a2) / args.steps,
+               note="edt_invert_adjoint (dL/dD through the damped solve, one refinement step) after "
+                    "edt_invert on the production inversion (cut on); c64 Dbar")
+    del inv
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -744,7 +768,7 @@ def main_grad(args, world, rank, local):
                       achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                       traffic=None, peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
                       flops_per_launch=flops),
-        J=float(J), clocks=clk, cpu_baseline=cpu)
+        J=float(J), solve_adjoint=adj, clocks=clk, cpu_baseline=cpu)
     line["gpu_launches"] = int(s.stats().launches_per_grad) * args.steps
     print(json.dumps(line))
     if world > 1:
