@@ -212,9 +212,19 @@ int edt_set_tuning(edt_ctx* ctx, const edt_tuning* in);
 
 /* edt_invert from host buffers: copies D to the device, inverts, copies V back, all on
  * `stream` (asynchronous; the host buffers must stay valid until the stream syncs).
- * Uses the staging areas inside the workspace. */
+ * Uses the staging areas inside the workspace.  With the host pipeline on (below) the copy
+ * of D runs on an internal stream into one of two staging buffers, so consecutive calls
+ * overlap one call's input copy with the previous call's stages. */
 int edt_invert_host(edt_ctx* ctx, const void* D_host, int D_dtype, void* V_host,
                     int V_dtype, void* stream);
+
+/* on = 1: edt_invert_host copies D_host on the context's internal copy stream, waiting only
+ * for the call before last (which used the same staging buffer), not for earlier work on
+ * `stream`; the inversion then waits for the copy on `stream`, and V is copied back on
+ * `stream`.  D_host must therefore be complete when the call is made (written by the host,
+ * not by device work still pending on `stream`).  on = 0 (default): every step on
+ * `stream` in order. */
+int edt_set_host_pipeline(edt_ctx* ctx, int on);
 
 /* Born forward model V -> D in the same discrete model (eq. Born with omega~^2):
  * D(is, ir) = omega~^2 dx dz sum_x sum_j G(x_ir - x, z_j) V(x, z_j) G(x - x_is, z_j),

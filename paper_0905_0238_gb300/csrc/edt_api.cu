@@ -100,6 +100,13 @@ struct edt_ctx {
   // runs there concurrently with the data transform on the caller's stream
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // host-buffer calls: the input copy on its own stream into one of two staging buffers, so
+  // one call's copy overlaps the previous call's stages (edt_set_host_pipeline)
+  bool host_pipe = false;
+  int host_buf = 0;
+  size_t dst_half = 0;
+  cudaStream_t cpy = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   int prof_calls = 0;
   int prof_used[NSTAGE] = {};
 };
@@ -514,7 +521,8 @@ void layout(edt_ctx* c) {
   take(c->r_X, std::max(size_t(c->fchunk) * N * N * (mixed ? sizeof(float2) : sizeof(double2)),
                         std::max(align_up(c->band_ymax * sizeof(float2), 256) + c->band_xmax * sizeof(float2),
                                  c->ws_band_elems * sizeof(float2))));
-  take(c->r_Dst, (c->win ? nf * nxy * W : nf * N * N) * sizeof(double2));
+  c->dst_half = align_up((c->win ? nf * nxy * W : nf * N * N) * sizeof(double2), 256);
+  take(c->r_Dst, 2 * c->dst_half);                 // two staging buffers
   take(c->r_Vst, (c->win ? nxy : N) * nz * sizeof(double));
   // right-hand sides; the mixed path's tensor-core Gram bulk-copies whole stages of 32 rows,
   // so its array (like the row metadata) carries 32 rows of padding
@@ -812,6 +820,11 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
     EDT_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
     EDT_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     EDT_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    EDT_TRY(cudaStreamCreateWithFlags(&c->cpy, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      EDT_TRY(cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming));
+      EDT_TRY(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming));
+    }
   }
   EDT_TRY(cudaDeviceSynchronize());
   return EDT_OK;
@@ -997,10 +1010,34 @@ int edt_invert_host(edt_ctx* c, const void* D_host, int D_dtype, void* V_host, i
   const size_t dbytes = size_t(c->nf) * (c->win ? size_t(c->nxy) * c->W : size_t(c->N) * c->N) *
                         (D_dtype == EDT_C64 ? 8 : 16);
   const size_t vbytes = size_t(c->win ? c->nxy : c->N) * c->nz * (V_dtype == EDT_F32 ? 4 : 8);
-  EDT_TRY(cudaMemcpyAsync(c->dev.Dstage, D_host, dbytes, cudaMemcpyHostToDevice, s));
-  int r = run_invert(c, c->dev.Dstage, D_dtype, c->dev.Vstage, V_dtype, s);
+  c->last_stream = s;
+  int r;
+  if (!c->host_pipe) {
+    EDT_TRY(cudaMemcpyAsync(c->dev.Dstage, D_host, dbytes, cudaMemcpyHostToDevice, s));
+    r = run_invert(c, c->dev.Dstage, D_dtype, c->dev.Vstage, V_dtype, s);
+  } else {
+    // the copy waits only for the last call that read this staging buffer, not for earlier
+    // work on `stream`; the stages wait for the copy
+    const int b = c->host_buf;
+    c->host_buf ^= 1;
+    void* Dst = static_cast<char*>(c->dev.Dstage) + size_t(b) * c->dst_half;
+    EDT_TRY(cudaStreamWaitEvent(c->cpy, c->ev_free[b], 0));
+    EDT_TRY(cudaMemcpyAsync(Dst, D_host, dbytes, cudaMemcpyHostToDevice, c->cpy));
+    EDT_TRY(cudaEventRecord(c->ev_in[b], c->cpy));
+    EDT_TRY(cudaStreamWaitEvent(s, c->ev_in[b], 0));
+    r = run_invert(c, Dst, D_dtype, c->dev.Vstage, V_dtype, s);
+    if (r == EDT_OK) EDT_TRY(cudaEventRecord(c->ev_free[b], s));
+  }
+  c->last_status = r;
+  c->have_factor = r == EDT_OK;
   if (r != EDT_OK) return r;
   EDT_TRY(cudaMemcpyAsync(V_host, c->dev.Vstage, vbytes, cudaMemcpyDeviceToHost, s));
+  return EDT_OK;
+}
+
+int edt_set_host_pipeline(edt_ctx* c, int on) {
+  if (!c) return EDT_EINVAL;
+  c->host_pipe = on != 0;
   return EDT_OK;
 }
 
@@ -1205,6 +1242,11 @@ void edt_destroy(edt_ctx* c) {
   if (!c) return;
   drop_graph(c);
   for (auto& e : c->ev) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
+    if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
+  }
+  if (c->cpy) cudaStreamDestroy(c->cpy);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->aux) cudaStreamDestroy(c->aux);

@@ -97,6 +97,7 @@ def _lib() -> C.CDLL:
                                        C.POINTER(i)]
         L.edt_misfit_grad.argtypes = [vp, vp, i, vp, i, vp, vp, vp, vp]
         L.edt_invert_adjoint.argtypes = [vp, vp, i, vp, i, vp]
+        L.edt_set_host_pipeline.argtypes = [vp, i]
         L.edt_set_reference.argtypes = [vp, C.POINTER(d), vp]
         L.edt_strerror.argtypes = [i]
         L.edt_strerror.restype = C.c_char_p
@@ -107,7 +108,8 @@ def _lib() -> C.CDLL:
                      "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
                      "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning",
-                     "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint"):
+                     "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint",
+                     "edt_set_host_pipeline"):
             getattr(L, name).restype = i
         _LIB = L
     return _LIB
@@ -227,6 +229,10 @@ def edt_invert_adjoint(ctx, Vbar_ptr: int, Vbar_dtype: int, Dbar_ptr: int, Dbar_
                                      Dbar_dtype, C.c_void_p(stream)), "edt_invert_adjoint")
 
 
+def edt_set_host_pipeline(ctx, on: bool):
+    _check(_lib().edt_set_host_pipeline(ctx, int(bool(on))), "edt_set_host_pipeline")
+
+
 def edt_set_reference(ctx, vel: np.ndarray, stream: int):
     v = np.ascontiguousarray(vel, dtype=np.float64)
     _check(_lib().edt_set_reference(ctx, v.ctypes.data_as(C.POINTER(C.c_double)),
@@ -343,6 +349,10 @@ class Solver:
         edt_invert(self.ctx, D.data_ptr(), self._cdtype(D), out.data_ptr(), self._rdtype(out),
                    self._stream())
         return out
+
+    def set_host_pipeline(self, on=True):
+        """Overlap invert_host's input copy with the previous call (see edt_set_host_pipeline)."""
+        edt_set_host_pipeline(self.ctx, on)
 
     def invert_host(self, D_host, V_host):
         """Host-buffer entry point: copies in, inverts, copies out on the current stream."""
