@@ -778,7 +778,7 @@ def main_grad(args, world, rank, local):
                  h2d_bytes_per_step=int(D.numel() * D.element_size() + V.numel() * V.element_size()),
                  d2h_bytes_per_step=int(gV.numel() * gV.element_size() + gc.numel() * 8 + 8)),
         gpu_launches=None,
-        roofline=dict(bound="alu", kernel="grad_residual + grad_vhat + grad_gbar x2 (whole call)",
+        roofline=dict(bound="alu", kernel="grad_residual + grad_vhat + grad_gbar (whole call)",
                       achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                       traffic=None, peak_source="derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
                       flops_per_launch=flops),

@@ -1170,10 +1170,10 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
                              (c->ny > 1 ? 4 : 3);
   }
   o->freq_chunk = c->band_mode ? c->band_maxplanes : c->fchunk;
-  // misfit gradient: green (3), zero, lateral DFT, per chunk transform (2) and four
+  // misfit gradient: green (3), zero, lateral DFT, per chunk transform (2) and three
   // contractions, depth march forward / field / reversed (3), inverse lateral DFT, finalize
   o->launches_per_grad = grad_supported(c->dev) && c->fchunk > 0
-                             ? 3 + 2 + 6 * ((c->nf + c->fchunk - 1) / c->fchunk) + 5 : 0;
+                             ? 3 + 2 + 5 * ((c->nf + c->fchunk - 1) / c->fchunk) + 5 : 0;
   o->gram_rows_padded = 0;
   for (long long n : c->seg_nrow) o->gram_rows_padded += (n + TC_KC - 1) / TC_KC * TC_KC;
   if (c->ws) {

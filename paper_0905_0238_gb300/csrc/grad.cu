@@ -27,8 +27,9 @@
 //   grad_vhat      (m, j) outputs, 8 consecutive m per thread and one j per lane; the
 //                  thread walks p, so its 8 legs q = p - m slide by one per step and stay
 //                  in registers: Ahat accumulated across frequencies in FP64;
-//   grad_gbar<T>   (n, j) outputs, 8 consecutive n per thread walking m (legs q = n - m
-//                  slide the same way): S1 (T = 0) then S2 (T = 1) into the gbar buffer;
+//   grad_gbar      (n, j) outputs, 8 consecutive n per thread walking m (legs q = n - m
+//                  slide the same way): S1 and S2 together (the same legs and Vhat) into
+//                  the gbar buffer;
 // then once, in FP64: grad_march (per (f, k): the recursion forward), grad_field (per
 // (f, k, layer): the field's depths of that layer, reversed), grad_reverse (per (f, k): the
 // two recursions reversed, then the per-layer sums); the inverse lateral DFT of Ahat and a
@@ -81,7 +82,7 @@ __global__ void grad_zero_kernel(Dev d) {
 // ---- residual R2 = ph_f sum_j g32_p g32_q Vhat(p - q) - D2, and sum |R2|^2 ------------------
 constexpr int RT = 64, RJC = 16, RTM = 2 * RT - 1;
 
-__global__ void __launch_bounds__(256) grad_residual_kernel(Dev d, int f0) {
+__global__ void __launch_bounds__(256, 3) grad_residual_kernel(Dev d, int f0) {
   __shared__ float2 gp[RJC][RT + 1], gq[RJC][RT + 1], vh[RJC][RTM + 2];
   __shared__ double red[8];
   const int N = d.N, fi = blockIdx.z, f = f0 + fi;
@@ -203,14 +204,13 @@ __global__ void __launch_bounds__(256) grad_vhat_kernel(Dev d, int f0) {
   }
 }
 
-// ---- S(n, j) = sum_m conj(B(n, n - m)) g32_{n-m} W(m): B = R2, W = Vhat (T = 0) or
-//      B = R2^T, W = conj(Vhat) (T = 1); gbar_f(n, j) = 2 c_J ph_f sqrt|s_f| (S1 + S2) -------
+// ---- S1 + S2 at (n, j): sum_m [conj(R2(n, n - m)) Vhat(m) + conj(R2(n - m, n)) conj(Vhat(m))]
+//      g32_{n-m}; gbar_f(n, j) = 2 c_J ph_f sqrt|s_f| (S1 + S2) ----------------------------------
 constexpr int GA = 64, GMC = 16, GQR = GA + GMC - 1;
 
-template <int T>
 __global__ void __launch_bounds__(256) grad_gbar_kernel(Dev d, int f0) {
   __shared__ float2 gqs[GQR][33], ws[GMC][33];
-  __shared__ __align__(16) float2 bs[GMC][GA];
+  __shared__ __align__(16) float2 bs[2][GMC][GA];      // [0]: R2(n, q), [1]: R2(q, n)
   const int N = d.N, fi = blockIdx.z, f = f0 + fi;
   const int a0 = blockIdx.x * GA, j0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -229,15 +229,14 @@ __global__ void __launch_bounds__(256) grad_gbar_kernel(Dev d, int f0) {
     }
     for (int e = threadIdx.x; e < GMC * 32; e += blockDim.x) {
       const int mi = e >> 5, jl = e & 31, jj = j0 + jl;
-      double2 v = jj < d.nz ? d.vfull[size_t(mc + mi) * d.nz + jj] : make_double2(0.0, 0.0);
-      if (T) v.y = -v.y;
+      const double2 v = jj < d.nz ? d.vfull[size_t(mc + mi) * d.nz + jj] : make_double2(0.0, 0.0);
       ws[mi][jl] = make_float2(float(v.x), float(v.y));
     }
     for (int e = threadIdx.x; e < GMC * GA; e += blockDim.x) {
       const int mi = e / GA, al = e - mi * GA;
       const int a = a0 + al, q = (a - mc - mi) & (N - 1);
-      // B(a, q): T = 0 -> R2(a, q) = X[q][a]; T = 1 -> R2(q, a) = X[a][q]
-      bs[mi][al] = T ? X[size_t(a) * N + q] : X[size_t(q) * N + a];
+      bs[0][mi][al] = X[size_t(q) * N + a];           // R2(a, q) = X[q][a]
+      bs[1][mi][al] = X[size_t(a) * N + q];           // R2(q, a) = X[a][q]
     }
     __syncthreads();
     // thread's n_k = a0 + 8 w + k; at m = mc + mi its leg q_k = n_k - m sits in row
@@ -252,13 +251,16 @@ __global__ void __launch_bounds__(256) grad_gbar_kernel(Dev d, int f0) {
         for (int k = 7; k > 0; --k) win[k] = win[k - 1];
         win[0] = gqs[8 * w - mi + GMC - 1][lane];
       }
-      const float2 wv = ws[mi][lane];
-      const float4* b4 = reinterpret_cast<const float4*>(&bs[mi][8 * w]);
+      const float2 wv = ws[mi][lane], wc = make_float2(wv.x, -wv.y);
+      const float4* b0 = reinterpret_cast<const float4*>(&bs[0][mi][8 * w]);
+      const float4* b1 = reinterpret_cast<const float4*>(&bs[1][mi][8 * w]);
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        const float4 bb = b4[h];
-        cmac_conj(acc[2 * h], make_float2(bb.x, bb.y), win[2 * h] * wv);
-        cmac_conj(acc[2 * h + 1], make_float2(bb.z, bb.w), win[2 * h + 1] * wv);
+        const float4 x0 = b0[h], x1 = b1[h];
+        cmac_conj(acc[2 * h], make_float2(x0.x, x0.y), win[2 * h] * wv);
+        cmac_conj(acc[2 * h], make_float2(x1.x, x1.y), win[2 * h] * wc);
+        cmac_conj(acc[2 * h + 1], make_float2(x0.z, x0.w), win[2 * h + 1] * wv);
+        cmac_conj(acc[2 * h + 1], make_float2(x1.z, x1.w), win[2 * h + 1] * wc);
       }
     }
     __syncthreads();
@@ -269,12 +271,7 @@ __global__ void __launch_bounds__(256) grad_gbar_kernel(Dev d, int f0) {
     const float2 scale = make_float2(float(sc * fc.rot_re), float(-sc * fc.rot_im));
     float2* G = d.gbar + size_t(f) * N * d.nz;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      float2* o = G + size_t(a0 + 8 * w + k) * d.nz + j;
-      const float2 v = scale * acc[k];
-      if (T) *o = *o + v;
-      else *o = v;
-    }
+    for (int k = 0; k < 8; ++k) G[size_t(a0 + 8 * w + k) * d.nz + j] = scale * acc[k];
   }
 }
 
@@ -495,25 +492,35 @@ __global__ void adj_addb_kernel(Dev d) {
 // c = D2(q, p) (folded rows: a and c the means with D2(-q, -p), D2(-p, -q)) are reversed and
 // scattered (atomically) into the chunk's planes X[fi][q][p] = D2bar(p, q).
 __global__ void __launch_bounds__(256) adj_rows_kernel(Dev d, int f0, int f1) {
+  __shared__ float2 bb[512];                          // (bbar_+, bbar_-) per depth, nz <= 512
   const int m = blockIdx.y, N = d.N, msk = N - 1;
   if (d.status[m] != EDT_OK) return;
+  const double* yb = d.x + size_t(m) * d.nz * 2;
+  for (int z = threadIdx.x; z < d.nz; z += blockDim.x) bb[z] = make_float2(float(yb[2 * z]), float(yb[2 * z + 1]));
+  __syncthreads();
   const long long r0 = d.row_off_mf[size_t(m) * (d.nf + 1) + f0];
   const long long r1 = d.row_off_mf[size_t(m) * (d.nf + 1) + f1];
-  const double* yb = d.x + size_t(m) * d.nz * 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   float2* X = reinterpret_cast<float2*>(d.X);
-  for (long long ri = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; ri < r1;
-       ri += (long long)gridDim.x * blockDim.x) {
+  // one warp per row, lanes over depth
+  for (long long ri = r0 + (long long)blockIdx.x * nwarp + warp; ri < r1; ri += (long long)gridDim.x * nwarp) {
     const uint32_t row = d.rows[ri];
     const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
     const float2* g1 = d.g32 + (size_t(f) * d.nk + tab_index(p, N)) * d.nzs;
     const float2* g2 = d.g32 + (size_t(f) * d.nk + tab_index(q, N)) * d.nzs;
     float2 sp = make_float2(0.f, 0.f), sm = sp;
-    for (int z = 0; z < d.nz; ++z) {
-      const float2 t = g1[z] * g2[z];
-      const float bp = float(yb[2 * z]), bm = float(yb[2 * z + 1]);
-      sp.x = fmaf(t.x, bp, sp.x); sp.y = fmaf(t.y, bp, sp.y);
-      sm.x = fmaf(t.x, bm, sm.x); sm.y = fmaf(t.y, bm, sm.y);
+    for (int z = lane; z < d.nz; z += 32) {
+      const float2 t = g1[z] * g2[z], b2 = bb[z];
+      sp.x = fmaf(t.x, b2.x, sp.x); sp.y = fmaf(t.y, b2.x, sp.y);
+      sm.x = fmaf(t.x, b2.y, sm.x); sm.y = fmaf(t.y, b2.y, sm.y);
     }
+    for (int o = 16; o > 0; o >>= 1) {
+      sp.x += __shfl_xor_sync(0xffffffffu, sp.x, o);
+      sp.y += __shfl_xor_sync(0xffffffffu, sp.y, o);
+      sm.x += __shfl_xor_sync(0xffffffffu, sm.x, o);
+      sm.y += __shfl_xor_sync(0xffffffffu, sm.y, o);
+    }
+    if (lane != 0) continue;
     const bool w2 = row_w2(row);
     const FreqConst fc = d.fc[f];
     const float2 crot = make_float2(float(fc.rot_re), float(-fc.rot_im));   // conj(rot)
@@ -561,7 +568,7 @@ cudaError_t launch_invert_adjoint(const Dev& d, const void* Vbar, int Vbar_dtype
   for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
     const int nfc = std::min(d.fchunk, d.nf - f0);
     if ((e = cudaMemsetAsync(d.X, 0, size_t(nfc) * d.N * d.N * sizeof(float2), s)) != cudaSuccess) return e;
-    adj_rows_kernel<<<dim3(8, d.nsub), 256, 0, s>>>(d, f0, f0 + nfc);
+    adj_rows_kernel<<<dim3(32, d.nsub), 256, 0, s>>>(d, f0, f0 + nfc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_transform_adjoint(d, Dbar, Dbar_dtype, f0, nfc, s)) != cudaSuccess) return e;
   }
@@ -586,8 +593,7 @@ cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const v
     grad_residual_kernel<<<dim3(N / RT, N / RT, nfc), 256, 0, s>>>(d, f0);
     const dim3 gj(N / VM, (d.nz + 31) / 32, nfc);
     grad_vhat_kernel<<<gj, 256, 0, s>>>(d, f0);
-    grad_gbar_kernel<0><<<gj, 256, 0, s>>>(d, f0);
-    grad_gbar_kernel<1><<<gj, 256, 0, s>>>(d, f0);
+    grad_gbar_kernel<<<gj, 256, 0, s>>>(d, f0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const dim3 gk((d.nk + 127) / 128, d.nf);
