@@ -812,6 +812,7 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
     }
   }
   EDT_TRY(prepare_fft(c->dev));
+  EDT_TRY(prepare_grad(c->dev));
   EDT_TRY(prepare_chol(c->dev));
   if (c->cfg.precision == EDT_MIXED) EDT_TRY(prepare_gram_tc(c->dev));
   if (c->band_mode) EDT_TRY(prepare_band(c->dev));

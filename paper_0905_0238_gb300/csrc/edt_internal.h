@@ -212,6 +212,7 @@ cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const v
 cudaError_t prepare_fft(const Dev& d);
 cudaError_t prepare_chol(const Dev& d);
 cudaError_t prepare_gram_tc(const Dev& d);
+cudaError_t prepare_grad(const Dev& d);
 
 // Tensor-core Gram tiling (shared by host planning and the kernel).
 constexpr int TC_M = 128;              // MMA rows (depth unknowns per M tile)

@@ -45,6 +45,12 @@ namespace {
 
 __device__ __forceinline__ int tab_index(int n, int N) { return n <= (N >> 1) ? n : N - n; }
 
+// 1 / b with one real division (the depth march's denominators are O(1e-4 .. 1e1))
+__device__ __forceinline__ double2 crcp(double2 b) {
+  const double r = 1.0 / (b.x * b.x + b.y * b.y);
+  return cmk(b.x * r, -b.y * r);
+}
+
 // acc += a * b (complex)
 __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
@@ -143,10 +149,14 @@ __global__ void __launch_bounds__(256, 3) grad_residual_kernel(Dev d, int f0) {
 }
 
 // ---- Ahat(m, j) += conj(ph_f) sum_p conj(g32_p g32_{p-m}) R2(p, p - m) -----------------------
-constexpr int VM = 64, VPC = 16, VQR = VPC + VM - 1;
+constexpr int VM = 64, VPC = 32, VQR = VPC + VM - 1;
+constexpr size_t VHAT_SMEM = (size_t(VPC) * 33 + size_t(VQR) * 33 + size_t(VQR) * VPC) * sizeof(float2);
 
-__global__ void __launch_bounds__(256) grad_vhat_kernel(Dev d, int f0) {
-  __shared__ float2 gps[VPC][33], gqs[VQR][33], rs[VQR][VPC];
+__global__ void __launch_bounds__(256, 3) grad_vhat_kernel(Dev d, int f0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 (*gps)[33] = reinterpret_cast<float2 (*)[33]>(smem_raw);
+  float2 (*gqs)[33] = reinterpret_cast<float2 (*)[33]>(smem_raw + size_t(VPC) * 33 * sizeof(float2));
+  float2 (*rs)[VPC] = reinterpret_cast<float2 (*)[VPC]>(smem_raw + size_t(VPC + VQR) * 33 * sizeof(float2));
   const int N = d.N, fi = blockIdx.z, f = f0 + fi;
   const int m0 = blockIdx.x * VM, j0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -207,10 +217,14 @@ __global__ void __launch_bounds__(256) grad_vhat_kernel(Dev d, int f0) {
 // ---- S1 + S2 at (n, j): sum_m [conj(R2(n, n - m)) Vhat(m) + conj(R2(n - m, n)) conj(Vhat(m))]
 //      g32_{n-m}; gbar_f(n, j) = 2 c_J ph_f sqrt|s_f| (S1 + S2) ----------------------------------
 constexpr int GA = 64, GMC = 16, GQR = GA + GMC - 1;
+constexpr size_t GBAR_SMEM = (size_t(2) * GMC * GA + size_t(GQR) * 33 + size_t(GMC) * 33) * sizeof(float2);
 
-__global__ void __launch_bounds__(256) grad_gbar_kernel(Dev d, int f0) {
-  __shared__ float2 gqs[GQR][33], ws[GMC][33];
-  __shared__ __align__(16) float2 bs[2][GMC][GA];      // [0]: R2(n, q), [1]: R2(q, n)
+__global__ void __launch_bounds__(256, 3) grad_gbar_kernel(Dev d, int f0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // bs[2][GMC][GA] first (16-byte aligned rows for the float4 reads): [0] R2(n, q), [1] R2(q, n)
+  float2 (*bs)[GMC][GA] = reinterpret_cast<float2 (*)[GMC][GA]>(smem_raw);
+  float2 (*gqs)[33] = reinterpret_cast<float2 (*)[33]>(smem_raw + size_t(2) * GMC * GA * sizeof(float2));
+  float2 (*ws)[33] = reinterpret_cast<float2 (*)[33]>(smem_raw + (size_t(2) * GMC * GA + size_t(GQR) * 33) * sizeof(float2));
   const int N = d.N, fi = blockIdx.z, f = f0 + fi;
   const int a0 = blockIdx.x * GA, j0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -314,8 +328,8 @@ __global__ void __launch_bounds__(128) grad_march_kernel(Dev d) {
   for (int l = J - 2; l >= 0; --l) {
     const double h = d.layer_top[l + 1] - d.layer_top[l];
     const double2 kl = gs_at(d, f, l, GS_KAP, k);
-    const double2 y = cdiv(kn * (one - rn), one + rn);
-    const double2 rho = cdiv(kl - y, kl + y);
+    const double2 y = kn * (one - rn) * crcp(one + rn);
+    const double2 rho = (kl - y) * crcp(kl + y);
     const double2 E = cexp(cmk(-2.0 * kl.y * h, 2.0 * kl.x * h));
     gs_at(d, f, l, GS_RHO, k) = rho;
     rn = rho * E;
@@ -323,14 +337,14 @@ __global__ void __launch_bounds__(128) grad_march_kernel(Dev d) {
     kn = kl;
   }
   // downward recursion
-  double2 A = cdiv(cmk(0.0, 0.5), gs_at(d, f, 0, GS_KAP, k));
+  double2 A = cmk(0.0, 0.5) * crcp(gs_at(d, f, 0, GS_KAP, k));
   for (int l = 0; l < J; ++l) {
     gs_at(d, f, l, GS_A, k) = A;
     if (l < J - 1) {
       const double h = d.layer_top[l + 1] - d.layer_top[l];
       const double2 kl = gs_at(d, f, l, GS_KAP, k);
       const double2 e1 = cexp(cmk(-kl.y * h, kl.x * h));
-      A = cdiv(A * e1 * (one + gs_at(d, f, l, GS_RHO, k)), one + gs_at(d, f, l + 1, GS_R, k));
+      A = A * e1 * (one + gs_at(d, f, l, GS_RHO, k)) * crcp(one + gs_at(d, f, l + 1, GS_R, k));
     }
   }
 }
@@ -412,7 +426,7 @@ __global__ void __launch_bounds__(128) grad_reverse_kernel(Dev d) {
       const double2 kl = gs_at(d, f, l, GS_KAP, kk), rho = gs_at(d, f, l, GS_RHO, kk);
       const double2 rn = gs_at(d, f, l + 1, GS_R, kk), Al = gs_at(d, f, l, GS_A, kk);
       const double2 e1 = cexp(cmk(-kl.y * h, kl.x * h));
-      const double2 inv1r = cdiv(one, one + rn);
+      const double2 inv1r = crcp(one + rn);
       const double2 F = e1 * (one + rho) * inv1r;
       const double2 bF = bA1 * Al;
       const double2 bA = gs_at(d, f, l, GS_BA, kk) + bA1 * F;
@@ -423,7 +437,7 @@ __global__ void __launch_bounds__(128) grad_reverse_kernel(Dev d) {
     }
     {
       const double2 k0 = gs_at(d, f, 0, GS_KAP, kk);
-      gs_at(d, f, 0, GS_BKAP, kk) = gs_at(d, f, 0, GS_BKAP, kk) + bA1 * cdiv(cmk(0.0, -0.5), k0 * k0);
+      gs_at(d, f, 0, GS_BKAP, kk) = gs_at(d, f, 0, GS_BKAP, kk) + bA1 * cmk(0.0, -0.5) * crcp(k0 * k0);
     }
     // upward recursion, reversed (l ascending: r_l's cotangent is complete when l is reached)
     for (int l = 0; l <= J - 2; ++l) {
@@ -434,21 +448,21 @@ __global__ void __launch_bounds__(128) grad_reverse_kernel(Dev d) {
       const double2 bR = gs_at(d, f, l, GS_BR, kk);
       const double2 bRho = gs_at(d, f, l, GS_BRHO, kk) + bR * E;
       double2 bK = gs_at(d, f, l, GS_BKAP, kk) + bR * rho * E * cmk(0.0, 2.0 * h);
-      const double2 opr = one + rn;
-      const double2 y = cdiv(kn * (one - rn), opr);
-      const double2 sm = kl + y, s2 = sm * sm;
-      bK = bK + bRho * cdiv(2.0 * y, s2);
-      const double2 bY = bRho * cdiv(-2.0 * kl, s2);
+      const double2 iopr = crcp(one + rn);
+      const double2 y = kn * (one - rn) * iopr;
+      const double2 sm = kl + y, is2 = crcp(sm * sm);
+      bK = bK + bRho * (2.0 * y) * is2;
+      const double2 bY = bRho * (-2.0 * kl) * is2;
       gs_at(d, f, l, GS_BKAP, kk) = bK;
-      gs_at(d, f, l + 1, GS_BKAP, kk) = gs_at(d, f, l + 1, GS_BKAP, kk) + bY * cdiv(one - rn, opr);
-      gs_at(d, f, l + 1, GS_BR, kk) = gs_at(d, f, l + 1, GS_BR, kk) + bY * kn * cdiv(cmk(-2.0, 0.0), opr * opr);
+      gs_at(d, f, l + 1, GS_BKAP, kk) = gs_at(d, f, l + 1, GS_BKAP, kk) + bY * (one - rn) * iopr;
+      gs_at(d, f, l + 1, GS_BR, kk) = gs_at(d, f, l + 1, GS_BR, kk) + bY * kn * (-2.0 * (iopr * iopr));
     }
   }
   for (int l = 0; l < J; ++l) {
     double v = 0.0;
     if (live) {
       const double c = d.layer_vel[l];
-      const double2 dk = cdiv(-1.0 / (c * c * c) * om2, gs_at(d, f, l, GS_KAP, kk));
+      const double2 dk = (-1.0 / (c * c * c)) * om2 * crcp(gs_at(d, f, l, GS_KAP, kk));
       v = (gs_at(d, f, l, GS_BKAP, kk) * dk).x;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -575,6 +589,12 @@ cudaError_t launch_invert_adjoint(const Dev& d, const void* Vbar, int Vbar_dtype
   return cudaSuccess;
 }
 
+cudaError_t prepare_grad(const Dev&) {
+  cudaError_t e = cudaFuncSetAttribute(grad_vhat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(VHAT_SMEM));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(grad_gbar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(GBAR_SMEM));
+}
+
 bool grad_supported(const Dev& d) {
   return d.geom == EDT_GEOM_LINE && d.precision == EDT_MIXED && d.N >= 64 && d.nlayer <= GRAD_MAX_LAYERS &&
          d.gscr != nullptr;
@@ -592,8 +612,8 @@ cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const v
     if ((e = launch_transform<float>(d, D, D_dtype, f0, nfc, s)) != cudaSuccess) return e;
     grad_residual_kernel<<<dim3(N / RT, N / RT, nfc), 256, 0, s>>>(d, f0);
     const dim3 gj(N / VM, (d.nz + 31) / 32, nfc);
-    grad_vhat_kernel<<<gj, 256, 0, s>>>(d, f0);
-    grad_gbar_kernel<<<gj, 256, 0, s>>>(d, f0);
+    grad_vhat_kernel<<<gj, 256, VHAT_SMEM, s>>>(d, f0);
+    grad_gbar_kernel<<<gj, 256, GBAR_SMEM, s>>>(d, f0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const dim3 gk((d.nk + 127) / 128, d.nf);
