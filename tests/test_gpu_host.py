@@ -4,7 +4,7 @@ device-buffer inversion of the same data."""
 import numpy as np
 import pytest
 
-from tests.gpu_helpers import small_workload, dev
+from tests.gpu_helpers import small_workload, dev, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,4 +27,5 @@ def test_invert_host_matches_device_call(pipe):
             s.invert_host(D, V)
         torch.cuda.synchronize()
         for V, w in zip(Vh, want):
-            assert np.array_equal(V.numpy(), w)
+            # the refinement sums across blocks with FP64 atomics: equal up to that order
+            assert rel_l2(V.numpy(), w) < 1e-6
