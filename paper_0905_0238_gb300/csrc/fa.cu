@@ -424,11 +424,17 @@ __global__ void __launch_bounds__(FW_THREADS, 4) fa_u_kernel(Dev d, int f) {
   __shared__ int jat[WX * WY];
   for (int e = threadIdx.x; e < WX * WY; e += blockDim.x) jat[e] = jmap[e];
   __syncthreads();
+  // The products are centrosymmetric in w, P(w) = G(y - w) G(y + w) = P(-w), so the
+  // x-transform of window row +wy is that of row -wy at the reversed offset wavenumber,
+  // plus the one product the window does not hold (w_x = +WX/2 against -WX/2):
+  //   A_{+wy}(j) = A_{-wy}(-j) + (-1)^j [P(WX/2, -wy) - P(-WX/2, -wy)];
+  // the thread of row -wy (wy = 1 .. WY/2 - 1) writes both rows, row +wy's thread idles.
   for (int x0 = 0; x0 < nx; x0 += UPB) {
     {
       const int iwy = threadIdx.x / UPB, ux = threadIdx.x - iwy * UPB, x = x0 + ux;   // lanes over x
-      if (x < nx) {
-        const int wyv = iwy - WY / 2;
+      const int wyv = iwy - WY / 2;
+      const bool derived = WY >= 4 && wyv >= 1;
+      if (x < nx && !derived) {
         const float2* Gm = Grow + (WY / 2 - wyv) * nx;    // row yy - wy
         const float2* Gp = Grow + (WY / 2 + wyv) * nx;    // row yy + wy
         float2 a[WX];
@@ -438,10 +444,21 @@ __global__ void __launch_bounds__(FW_THREADS, 4) fa_u_kernel(Dev d, int f) {
           const float2 p = Gm[(x - wxv + nx) & (nx - 1)] * Gp[(x + wxv + nx) & (nx - 1)];
           a[ix] = neg_if(p, WX >= 2 && (ix & 1));
         }
+        const bool source = WY >= 4 && wyv < 0 && wyv > -WY / 2;
+        float2 cr = make_float2(0.f, 0.f);
+        if (source)                                       // a[0] = P(-WX/2, wy), unsigned
+          cr = Gm[(x - WX / 2 + nx) & (nx - 1)] * Gp[(x + WX / 2 + nx) & (nx - 1)] - a[0];
         reg_dft<WX>(a);
 #pragma unroll
-        for (int jx = 0; jx < WX; ++jx)
-          ex[L::at(jx, ux, iwy)] = neg_if(a[jx], WX >= 2 && ((jx & 1) != alt_sign_end(WX)));
+        for (int jx = 0; jx < WX; ++jx) a[jx] = neg_if(a[jx], WX >= 2 && ((jx & 1) != alt_sign_end(WX)));
+#pragma unroll
+        for (int jx = 0; jx < WX; ++jx) ex[L::at(jx, ux, iwy)] = a[jx];
+        if (source) {
+          const int iwd = WY / 2 - wyv;                   // row +wy
+#pragma unroll
+          for (int jx = 0; jx < WX; ++jx)
+            ex[L::at(jx, ux, iwd)] = a[(WX - jx) & (WX - 1)] + neg_if(cr, ((jx + WX / 2) & 1) != 0);
+        }
       }
     }
     __syncthreads();
