@@ -22,7 +22,7 @@
 // ph_f = s_f/|s_f|, and dJ/dg = sqrt|s_f| dJ/dg32 -> the factor 2 c_J ph_f sqrt|s_f| below.
 //
 // Kernels per chunk of frequency planes (X holds D2, then R2 in place):
-//   grad_residual  (p, q) tiles of 64 x 64, 4 x 4 per thread, depth in chunks of 16 in
+//   grad_residual  (p, q) tiles of 64 x 64, 4 x 4 per thread, depth in chunks of 32 in
 //                  shared memory: R2 and the partial sums of |R2|^2;
 //   grad_vhat      (m, j) outputs, 8 consecutive m per thread and one j per lane; the
 //                  thread walks p, so its 8 legs q = p - m slide by one per step and stay
@@ -86,10 +86,14 @@ __global__ void grad_zero_kernel(Dev d) {
 }
 
 // ---- residual R2 = ph_f sum_j g32_p g32_q Vhat(p - q) - D2, and sum |R2|^2 ------------------
-constexpr int RT = 64, RJC = 16, RTM = 2 * RT - 1;
+constexpr int RT = 64, RJC = 32, RTM = 2 * RT - 1;
+constexpr size_t RES_SMEM = (size_t(2) * RJC * (RT + 1) + size_t(RJC) * (RTM + 2)) * sizeof(float2);
 
 __global__ void __launch_bounds__(256, 3) grad_residual_kernel(Dev d, int f0) {
-  __shared__ float2 gp[RJC][RT + 1], gq[RJC][RT + 1], vh[RJC][RTM + 2];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 (*gp)[RT + 1] = reinterpret_cast<float2 (*)[RT + 1]>(smem_raw);
+  float2 (*gq)[RT + 1] = reinterpret_cast<float2 (*)[RT + 1]>(smem_raw + size_t(RJC) * (RT + 1) * sizeof(float2));
+  float2 (*vh)[RTM + 2] = reinterpret_cast<float2 (*)[RTM + 2]>(smem_raw + size_t(2) * RJC * (RT + 1) * sizeof(float2));
   __shared__ double red[8];
   const int N = d.N, fi = blockIdx.z, f = f0 + fi;
   const int p0 = blockIdx.x * RT, q0 = blockIdx.y * RT;
@@ -149,14 +153,19 @@ __global__ void __launch_bounds__(256, 3) grad_residual_kernel(Dev d, int f0) {
 }
 
 // ---- Ahat(m, j) += conj(ph_f) sum_p conj(g32_p g32_{p-m}) R2(p, p - m) -----------------------
-constexpr int VM = 64, VPC = 32, VQR = VPC + VM - 1;
-constexpr size_t VHAT_SMEM = (size_t(VPC) * 33 + size_t(VQR) * 33 + size_t(VQR) * VPC) * sizeof(float2);
+constexpr int VM = 64, VPC = 32, VQR = VPC + VM - 1, VLT = VQR + 2;   // VLT odd
+constexpr size_t VHAT_SMEM = (size_t(VPC) * 33 + size_t(VQR) * 33 + size_t(VPC) * VLT + 1) * sizeof(float2);
+static_assert(VLT % 2 == 1, "odd row length: each step's 8 residuals start 16-byte aligned");
 
 __global__ void __launch_bounds__(256, 3) grad_vhat_kernel(Dev d, int f0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 (*gps)[33] = reinterpret_cast<float2 (*)[33]>(smem_raw);
   float2 (*gqs)[33] = reinterpret_cast<float2 (*)[33]>(smem_raw + size_t(VPC) * 33 * sizeof(float2));
-  float2 (*rs)[VPC] = reinterpret_cast<float2 (*)[VPC]>(smem_raw + size_t(VPC + VQR) * 33 * sizeof(float2));
+  // residual tile transposed, rsT[pl * VLT + qi] = R2(p0 + pl, q(qi)): at step pl a thread's 8
+  // legs are the run qi = pl - 8w + 56 .. pl - 8w + 63, whose start pl (VLT + 1) - 8w + 56 is
+  // even, so the run is read with four 16-byte broadcast loads
+  constexpr size_t RS_OFF = (size_t(VPC + VQR) * 33 + 1) & ~size_t(1);   // even: 16-byte aligned
+  float2* rsT = reinterpret_cast<float2*>(smem_raw + RS_OFF * sizeof(float2));
   const int N = d.N, fi = blockIdx.z, f = f0 + fi;
   const int m0 = blockIdx.x * VM, j0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(256, 3) grad_vhat_kernel(Dev d, int f0) {
     for (int e = threadIdx.x; e < VQR * VPC; e += blockDim.x) {
       const int qi = e / VPC, pl = e - qi * VPC;
       const int q = (p0 - m0 - (VM - 1) + qi) & (N - 1);
-      rs[qi][pl] = X[size_t(q) * N + p0 + pl];
+      rsT[pl * VLT + qi] = X[size_t(q) * N + p0 + pl];
     }
     __syncthreads();
     // thread's m_k = m0 + 8 w + k; at p = p0 + pl its leg q_k = p - m_k sits in row
@@ -196,8 +205,13 @@ __global__ void __launch_bounds__(256, 3) grad_vhat_kernel(Dev d, int f0) {
         win[0] = gqs[pl + VM - 1 - 8 * w][lane];
       }
       const float2 gpv = gps[pl][lane];
+      const float4* r4 = reinterpret_cast<const float4*>(rsT + pl * VLT + pl + VM - 8 - 8 * w);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) cmac_conj(acc[k], gpv * win[k], rs[pl + VM - 1 - 8 * w - k][pl]);
+      for (int h = 0; h < 4; ++h) {                      // legs k = 7 - 2h (.xy) and 6 - 2h (.zw)
+        const float4 rr = r4[h];
+        cmac_conj(acc[7 - 2 * h], gpv * win[7 - 2 * h], make_float2(rr.x, rr.y));
+        cmac_conj(acc[6 - 2 * h], gpv * win[6 - 2 * h], make_float2(rr.z, rr.w));
+      }
     }
     __syncthreads();
   }
@@ -590,7 +604,9 @@ cudaError_t launch_invert_adjoint(const Dev& d, const void* Vbar, int Vbar_dtype
 }
 
 cudaError_t prepare_grad(const Dev&) {
-  cudaError_t e = cudaFuncSetAttribute(grad_vhat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(VHAT_SMEM));
+  cudaError_t e = cudaFuncSetAttribute(grad_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RES_SMEM));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(grad_vhat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(VHAT_SMEM));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(grad_gbar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(GBAR_SMEM));
 }
@@ -610,7 +626,7 @@ cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const v
   for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
     const int nfc = std::min(d.fchunk, d.nf - f0);
     if ((e = launch_transform<float>(d, D, D_dtype, f0, nfc, s)) != cudaSuccess) return e;
-    grad_residual_kernel<<<dim3(N / RT, N / RT, nfc), 256, 0, s>>>(d, f0);
+    grad_residual_kernel<<<dim3(N / RT, N / RT, nfc), 256, RES_SMEM, s>>>(d, f0);
     const dim3 gj(N / VM, (d.nz + 31) / 32, nfc);
     grad_vhat_kernel<<<gj, 256, VHAT_SMEM, s>>>(d, f0);
     grad_gbar_kernel<<<gj, 256, GBAR_SMEM, s>>>(d, f0);
