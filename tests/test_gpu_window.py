@@ -92,3 +92,28 @@ def test_batched_grid_sampled_pairs():
         m = reps[idx]
         want = edt3d.solve_pair(wl, d, edt3d.kernel_rows_for(wl, m), m)
         assert rel_l2(vh[idx], want) < 1e-5, (m, rel_l2(vh[idx], want))
+
+
+@pytest.mark.parametrize("nx,ny,wx,wy,nf,nz", [
+    (64, 64, 8, 4, 3, 12),      # rectangular window: derived rows with WY < WX, two jx per thread
+    (32, 32, 4, 2, 4, 10),      # WY = 2: no derived rows
+    (64, 64, 16, 8, 2, 9),      # 16 x 8 window, odd depth count
+    (128, 1, 8, 1, 4, 16),      # lines of 128 and 512 points
+    (512, 1, 4, 1, 3, 12),
+])
+def test_window_shapes_match_oracle(nx, ny, wx, wy, nf, nz):
+    """More grid and window shapes at alpha = 1e-3.  (At alpha = 1e-4 the 64 x 64 grid with the
+    8 x 4 window, half the offsets of the square window, reaches 1.6e-5: the FP32 kernel rows'
+    rounding amplified by the weaker damping, the same with or without the mirrored-row
+    shortcut of the window products.)"""
+    wl = workload(nx, ny, wx, wy, nf=nf, nz=nz, alpha=1e-3)
+    D = born_data(wl, salt=11)
+    V_or, vh_or = edt3d.invert(wl, D)
+    s = solver(wl)
+    V = s.invert(dev(D.astype(np.complex64)), out_dtype=torch.float32).cpu().numpy()
+    st = s.stats()
+    assert st.n_notpd == 0 and st.n_nonfinite == 0
+    reps = edt3d.pair_representatives(wl)
+    want = np.stack([vh_or[m[1], m[0]] for m in reps])
+    assert rel_l2(s.vhat().cpu().numpy(), want) < 1e-5
+    assert rel_l2(V, V_or) < 1e-5
