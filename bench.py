@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default launch shapes instead of the autotuned ones")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batched_3d", "differentiation_2d"],
+                    choices=[WORKLOAD, "batched_3d", "differentiation_2d", "streaming"],
                     help="batched_3d: the finite-aperture 3D workload; differentiation_2d: misfit "
-                         "gradients on the production geometry (separate lines, not the headline)")
+                         "gradients on the production geometry; streaming: 4096 independent 1D "
+                         "subproblems in Poisson bursts (separate lines, not the headline)")
     return ap.parse_args()
 
 
@@ -151,6 +152,22 @@ def cpu_child_grad(spec):
     print("CPUJSON " + json.dumps(out))
 
 
+def cpu_child_stream(spec):
+    """Oracle sample of the streaming workload: QR solves of every 512th request of the stream."""
+    from synth import stream
+    from oracle import stream1d
+    subs = stream.stream_requests(spec["n"], salt=0)
+    idx = list(range(0, spec["n"], spec["every"]))
+    a = time.perf_counter()
+    for i in idx:
+        stream1d.solve(subs[i])
+    t = time.perf_counter() - a
+    out = dict(value=len(idx) / t, unit="subproblems/s", cores=1, kind="oracle",
+               sample=(f"FP64 numpy oracle, 1 thread: Green's rows and Householder QR of requests "
+                       f"{idx} of the {spec['n']}-request stream ({t:.1f} s)"))
+    print("CPUJSON " + json.dumps(out))
+
+
 def cpu_child(spec_path):
     """Runs in a subprocess with single-threaded BLAS: time the oracle on a sample."""
     import numpy as np
@@ -162,6 +179,9 @@ def cpu_child(spec_path):
         return
     if spec.get("workload") == "differentiation_2d":
         cpu_child_grad(spec)
+        return
+    if spec.get("workload") == "streaming":
+        cpu_child_stream(spec)
         return
     wl = synth.preset(spec["workload"])
     rng = synth.rng_for(1, salt=77)
@@ -296,6 +316,9 @@ def main():
         return
     if args.workload == "batched_3d":
         main_window(args, world, rank, local)
+        return
+    if args.workload == "streaming":
+        main_stream(args, world, rank, local)
         return
     if args.workload == "differentiation_2d":
         main_grad(args, world, rank, local)
@@ -784,6 +807,166 @@ def main_grad(args, world, rank, local):
                       flops_per_launch=flops),
         J=float(J), solve_adjoint=adj, clocks=clk, cpu_baseline=cpu)
     line["gpu_launches"] = int(s.stats().launches_per_grad) * args.steps
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_stream(args, world, rank, local):
+    """Streaming batched solves: 4096 independent 1D subproblems (depth counts uniform 64-512,
+    rows uniform 128-4096, random layered references of 5-30 layers, complex64 data) arriving
+    in Poisson bursts of 32-512.  One step = the whole stream.
+
+    value: subproblems / device time in which the batches' launches ran (the union of their
+    intervals: consecutive batches overlap on the two arenas' streams; inputs resident, the
+    host-device copies outside those intervals); e2e: the same stream submitted through
+    edt_stream_submit from host arrays burst after burst with no pause, host wall time from the
+    first submit to the last result; latency: the bursts submitted at Poisson arrival times at
+    70 % of the saturated burst rate, completion (CUDA event) minus scheduled arrival."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from synth import stream as ss
+    from paper_0905_0238_gb300 import build as libbuild
+    libbuild.build()
+    from paper_0905_0238_gb300 import Stream
+    from paper_0905_0238_gb300.edt import edt_stream_request_bytes
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n_total = 4096
+    subs = ss.stream_requests(n_total, salt=rank)
+    sizes, _ = ss.burst_schedule(n_total, rate_hz=1.0, salt=rank)
+    cuts = np.concatenate([[0], np.cumsum(sizes)])
+    bursts = [subs[cuts[i]:cuts[i + 1]] for i in range(len(sizes))]
+    rb = np.array([edt_stream_request_bytes(x) for x in subs], dtype=np.int64)
+    burst_bytes = max(int(rb[cuts[i]:cuts[i + 1]].sum()) for i in range(len(sizes)))
+    s = Stream(max_batch=512, workspace_bytes=2 * (burst_bytes + (64 << 20)), device=dev)
+
+    def run_all():
+        t0 = time.perf_counter()
+        tickets = [s.submit(bb) for bb in bursts]
+        out = [s.wait(t) for t in tickets]
+        return time.perf_counter() - t0, out
+
+    for _ in range(max(3, args.warmup)):
+        run_all()
+    st0 = s.stats()
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    s.epoch()
+    wall = []
+    for _ in range(args.steps):
+        t, out = run_all()
+        wall.append(t)
+    barrier()
+    clk = clocks.stop()
+    st1 = s.stats()
+    # device time: union of the intervals in which some batch's launches ran (the two arenas'
+    # streams overlap consecutive batches); host-device copies outside those intervals
+    dev_ms = max_over_ranks(st1["busy_ms"], world)
+    sum_ms = st1["compute_ms"] - st0["compute_ms"]
+    value = world * n_total * args.steps / (dev_ms / 1e3)
+    wall_s = max_over_ranks(sum(wall), world)
+    e2e = world * n_total * args.steps / wall_s
+    bad = sum(int(np.count_nonzero(o[1])) for o in out)
+    # per-launch split of one pass (CUDA events between the launches)
+    s.set_profiling(True)
+    run_all()
+    prof, nb = s.read_profile()
+    s.set_profiling(False)
+    # open-loop latency at 70 % of the saturated burst rate
+    rate = 0.7 * len(bursts) / (sum(wall) / len(wall))
+    _, arrive = ss.burst_schedule(n_total, rate_hz=rate, salt=rank)
+    s.epoch()
+    t_epoch = time.perf_counter()
+    tickets = []
+    for bb, ta in zip(bursts, arrive):
+        now = time.perf_counter() - t_epoch
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append(s.submit(bb))
+    lat = []
+    for t, ta, bb in zip(tickets, arrive, bursts):
+        _, _, done_ms = s.wait(t)
+        lat += [done_ms - 1e3 * ta] * len(bb)
+    lat = np.array(lat)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    # algorithmic work of one pass
+    nz = np.array([x.nz for x in subs], dtype=np.float64)
+    nr = np.array([x.nrow for x in subs], dtype=np.float64)
+    chol_flops = float(np.sum(nz ** 3 / 3 + 4 * nz ** 2))
+    gram_flops = float(np.sum(2 * (2 * nr) * nz * (nz + 2)))
+    chol_ms = prof.get("chol", 0.0)
+    gram_ms = prof.get("st_gram", 0.0)
+    kern = max(prof, key=prof.get) if prof else None
+    fp64_peak = 1.25        # TFLOP/s: GB300 FP64 (nominal; the FMA probe measured 1.19)
+    roof = dict(bound="alu", kernel="chol (FP64 Cholesky + solves, all requests of a pass)",
+                achieved=chol_flops / (chol_ms / 1e3) / 1e12 if chol_ms else None, peak=fp64_peak,
+                unit="TFLOP/s", traffic=None,
+                peak_source="nominal GB300 FP64 rate (1.25 TFLOP/s); MEASURED_PEAKS has no FP64 entry",
+                flops_per_pass=chol_flops)
+    roof["frac"] = roof["achieved"] / fp64_peak if roof["achieved"] else None
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    bf16 = peaks.get("bf16_tflops_sustained") or 1686.2
+    gram_issued = 0.0
+    for x in subs:
+        nzt = -(-x.nz // 128)
+        kst = -(-x.nrow // 32)
+        for ti in range(nzt):
+            for tj in range(ti, nzt):
+                ncol = 144 if tj == nzt - 1 else 128
+                gram_issued += 3 * 2 * 128 * ncol * 64 * kst
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = run_cpu_baseline(None, dict(workload="streaming", n=n_total, every=512))
+        except Exception as ex:
+            cpu = dict(value=None, unit="subproblems/s", cores=0, kind="oracle", sample=str(ex)[:300])
+    h2d = st1["bytes_in"] - st0["bytes_in"]
+    d2h = st1["bytes_out"] - st0["bytes_out"]
+    line = dict(
+        metric="subproblems_per_sec", value=value, unit="subproblems/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=dev_ms / args.steps,
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="bf16x3+f32+f64",
+        data="synthetic (seeded requests: layered references, band rows, complex Gaussian data)",
+        config=dict(workload=(f"streaming: {n_total} 1D subproblems, nz U(64,512), rows U(128,4096), "
+                              f"5-30 layers, {len(bursts)} Poisson bursts of 32-512; one step = the "
+                              f"whole stream"),
+                    l2="inputs larger than L2 (each burst's row tables, several GB)",
+                    parallelism=f"replicas x{world}", batches_per_pass=nb,
+                    launch_ms_summed_over_batches=sum_ms / args.steps,
+                    workspace_gb=round(2 * (burst_bytes + (64 << 20)) / 1e9, 2)),
+        e2e=dict(value=e2e, unit="subproblems/s", h2d_bytes_per_step=int(h2d // args.steps),
+                 d2h_bytes_per_step=int(d2h // args.steps),
+                 note="saturated: bursts submitted back to back from host arrays, host wall time"),
+        latency_ms=dict(p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)),
+                        max=float(lat.max()), offered_bursts_per_s=rate,
+                        note="open loop, Poisson burst arrivals at 70 % of the saturated burst rate; "
+                             "completion (CUDA event after the result copy) minus arrival"),
+        kernels_ms_per_pass={k: v for k, v in prof.items()},
+        gram=dict(issued_tflop_per_pass=gram_issued / 1e12, useful_tflop_per_pass=gram_flops / 1e12,
+                  achieved_tflops=gram_issued / (gram_ms / 1e3) / 1e12 if gram_ms else None,
+                  peak_tflops=bf16, frac=(gram_issued / (gram_ms / 1e3) / 1e12 / bf16) if gram_ms else None),
+        dominant_kernel=kern, nonzero_status=bad,
+        gpu_launches=int(st1["launches_per_batch"]) * int((st1["batches"] - st0["batches"])),
+        roofline=roof, clocks=clk, cpu_baseline=cpu)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

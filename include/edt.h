@@ -322,6 +322,115 @@ int edt_set_profiling(edt_ctx* ctx, int on);
 int edt_read_profile(edt_ctx* ctx, double* ms, const char** names, int max_stages,
                      int* n_calls);
 
+/* ---------------------------------------------------------------- streaming 1D solves
+ * A stream of independent 1D depth subproblems.  Each request is the split system of one
+ * midpoint wavenumber (eqs. DMV, M and Split of Section "Two dimensions") standing on its own,
+ * with its own layered reference, depth grid, frequencies and rows.  Request r solves, for
+ * real x_+ and x_- (nz unknowns each),
+ *     min ||Ahat x_+- - dhat_+-||^2 + lam ||x_+-||^2,     lam = alpha trace(Ahat^T Ahat),
+ * Ahat = [Re a; Im a], dhat_+- = [Re d_+-; Im d_+-], a_i(z_j) = s_f g(kval[p], z_j) g(kval[q], z_j)
+ * for row i = (f, p, q), s_f = omega~_f^2 dz / dx, omega~_f = 2 pi freq_hz[f] + i eps,
+ * z_j = z0 + (j + 1/2) dz, g the Green's function of the layered reference (the depth march of
+ * edt_green); the result is Vhat(z_j) = x_+(z_j) + i x_-(z_j).  Arithmetic follows EDT_MIXED:
+ * FP32 Green's table (FP64 vertical wavenumbers), split BF16 tensor-core Gram with FP32
+ * accumulation, FP64 Cholesky, one refinement step (FP32 residual accumulated in FP64, FP32
+ * correction solve).
+ *
+ * Requests are admitted by device memory: the caller's workspace is split into two arenas, a
+ * submitted list is cut in order into batches whose summed edt_stream_request_bytes fit one
+ * arena (and at most max_batch requests), and each batch runs as one set of eight launches
+ * over all its requests.  The two arenas have a CUDA stream each, so one batch's launches
+ * overlap the next batch's copies and launches while the host packs the batch after into
+ * pinned staging.  All state stays on the device until the results of a batch are copied
+ * back. */
+typedef struct {
+  int nz;                       /* unknowns (depths), 1..512                                */
+  double dz, z0;                /* depth step > 0 (m) and offset: z_j = z0 + (j + 1/2) dz     */
+  double eps;                   /* omega~ = omega + i eps (1/s), >= 0                        */
+  double alpha;                 /* damping factor, >= 0                                      */
+  double dx;                    /* lateral spacing (m) in s_f, > 0                           */
+  int nlayer;                   /* 1..64 layers; top of layer 0 at 0, tops increasing;       */
+  const double* layer_top_m;    /*   the last layer is a half-space                          */
+  const double* layer_vel_mps;  /*   velocities > 0                                          */
+  int nfreq;                    /* >= 1 */
+  const double* freq_hz;        /* [nfreq], > 0                                              */
+  int nk;                       /* >= 1 */
+  const double* kval;           /* [nk] lateral wavenumbers |k| (rad/m), >= 0                */
+  int nrow;                     /* >= 0 rows                                                 */
+  const int* rows;              /* [nrow][3] (f, p, q): f < nfreq, p, q < nk                 */
+  const float* data;            /* [nrow][4] complex64 pairs: d_+ (re, im), d_- (re, im)     */
+} edt_sub1d;
+
+typedef struct edt_stream edt_stream;   /* opaque; owned by the library */
+
+typedef struct {
+  long long requests;           /* requests solved since creation                            */
+  long long batches;            /* batches launched                                          */
+  double compute_ms;            /* summed device time of the batches' launches (CUDA events,
+                                   host-device copies excluded)                             */
+  double busy_ms;               /* since the last edt_stream_epoch: union over the delivered
+                                   batches of the intervals in which their launches ran
+                                   (overlapping batches counted once)                       */
+  long long bytes_in, bytes_out;/* host-to-device and device-to-host bytes copied            */
+  int launches_per_batch;       /* CUDA kernels one batch launches                           */
+  size_t arena_bytes;           /* device bytes of one arena (half the workspace)            */
+  int max_batch;
+} edt_stream_stats;
+
+/* Device bytes a request occupies in an arena (>= 0), or EDT_EINVAL for an invalid one. */
+long long edt_stream_request_bytes(const edt_sub1d* sub);
+
+/* Admission plan (host only): requests 0..n-1, of request_bytes[i] device bytes, are cut in
+ * order into batches of at most max_batch requests whose summed bytes plus the fixed per-batch
+ * overhead fit arena_bytes; batch_of[i] receives the batch index of request i.  Returns the
+ * number of batches, EDT_ENOMEM_WS if a request alone does not fit, or EDT_EINVAL. */
+int edt_stream_plan(int n, const long long* request_bytes, long long arena_bytes, int max_batch,
+                    int* batch_of);
+
+/* Create a stream solver on the current device.  max_batch: 1..4096 requests per batch.
+ * stream: NULL, or a CUDA stream (cudaStream_t) whose work submitted before each
+ * edt_stream_submit the batches of that call wait for (they run on the solver's own two
+ * streams).  *workspace_min receives the smallest workspace that admits the largest possible
+ * request (nz = 512, nrow = 4096) in each arena. */
+int edt_stream_create(edt_stream** out, int max_batch, void* stream, size_t* workspace_min);
+
+/* Hand the solver its device workspace (caller-owned, >= 256-byte aligned, kept until
+ * edt_stream_destroy).  Waits for any batch in flight.  EDT_ENOMEM_WS if too small. */
+int edt_stream_set_workspace(edt_stream* s, void* ws_dev, size_t bytes);
+
+/* Submit n requests.  Their host arrays may be freed when the call returns (they are packed
+ * into pinned staging).  Results arrive in vhat_host (complex128 interleaved, the requests'
+ * nz values one after another, sum of nz entries) and status_host (EDT_OK, EDT_ENOTPD,
+ * EDT_ENONFINITE or EDT_ETIMEOUT per request); both must stay valid until edt_stream_wait on
+ * *ticket returns.  A request larger than an arena fails the call with EDT_ENOMEM_WS before
+ * anything is launched.  Returns EDT_OK, EDT_EINVAL, EDT_ENOMEM_WS or EDT_ECUDA. */
+int edt_stream_submit(edt_stream* s, int n, const edt_sub1d* subs, double* vhat_host,
+                      int* status_host, long long* ticket);
+
+/* Block until every batch of the ticket is done and its results are in the caller's arrays.
+ * done_ms (may be NULL) receives the completion time of its last batch in milliseconds after
+ * the last edt_stream_epoch (CUDA events; -1 if no epoch was set). */
+int edt_stream_wait(edt_stream* s, long long ticket, double* done_ms);
+
+/* Non-blocking: *done = 1 if every batch of the ticket has completed on the device. */
+int edt_stream_query(edt_stream* s, long long ticket, int* done);
+
+/* Synchronise the stream and record the time origin of edt_stream_wait's done_ms. */
+int edt_stream_epoch(edt_stream* s);
+
+int edt_stream_get_stats(const edt_stream* s, edt_stream_stats* out);
+
+/* Per-launch device timing: with profiling on, CUDA events are recorded between the eight
+ * launches of every batch; edt_stream_read_profile delivers the batches in flight, returns the
+ * summed milliseconds per launch (names[i] static strings) since the last read, the number of
+ * batches they cover in *n_batches, and resets.  Returns the number of entries written. */
+int edt_stream_set_profiling(edt_stream* s, int on);
+int edt_stream_read_profile(edt_stream* s, double* ms, const char** names, int max_kernels,
+                            long long* n_batches);
+
+/* Wait for the batches in flight and release the solver (not the caller's workspace). */
+void edt_stream_destroy(edt_stream* s);
+
 /* Message for a status code; message of the last CUDA error seen by the library. */
 const char* edt_strerror(int code);
 const char* edt_last_cuda_error(void);

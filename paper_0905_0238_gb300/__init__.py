@@ -5,4 +5,4 @@ Python side: :mod:`paper_0905_0238_gb300.edt` (ctypes binding and a workspace-ow
 ``Solver``) and :mod:`paper_0905_0238_gb300.build` (in-tree nvcc build of ``libedt.so``).
 """
 from .edt import *  # noqa: F401,F403
-from .edt import Config, Solver, EdtError  # noqa: F401
+from .edt import Config, Solver, EdtError, Stream  # noqa: F401

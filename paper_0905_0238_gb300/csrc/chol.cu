@@ -119,21 +119,25 @@ __device__ void chol_solve_2rhs(const double* A, const double* dinv, int n, doub
 // pair, products by the exact fma error transformation plus the two cross terms, sums by
 // TwoSum -- about 48-bit accurate, then subtracted from the FP64 matrix.  Diagonal blocks,
 // panels, pivots, storage and the solves stay FP64.
-template <bool DF>
+// VAR = true: every subproblem m has its own size sub_n[m], its matrices at element offset
+// sub_goff[m] of G (and L32) and its vectors at sub_voff[m] (streaming batches).
+template <bool DF, bool VAR>
 __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
   extern __shared__ __align__(16) double sm[];
-  const int n = d.nz;
+  const int m = VAR && d.sub_order ? d.sub_order[blockIdx.x] : blockIdx.x;
+  const int n = VAR ? d.sub_n[m] : d.nz;
+  const size_t go = VAR ? size_t(d.sub_goff[m]) : size_t(m) * n * n;
+  const size_t vo = VAR ? size_t(d.sub_voff[m]) : size_t(m) * n;
   double* sP = sm;                          // [n][LDP] panel
   double* sD = sP + size_t(n) * LDP;        // [NB][LDP] diagonal block
   double* sb = sD + NB * LDP;               // [n][2] right-hand sides
   double* red = sb + 2 * n;                 // [33] reduction scratch
   __shared__ int fail;
   __shared__ double sInv[NB];
-  const int m = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* A = d.G + size_t(m) * n * n;
+  double* A = d.G + go;
   const long long nr = d.row_off[m + 1] - d.row_off[m];
-  double* xo = d.x + size_t(m) * n * 2;
+  double* xo = d.x + vo * 2;
   if (threadIdx.x == 0) fail = 0;
   if (nr == 0) {
     for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
@@ -151,8 +155,8 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
   const double lam = d.alpha * tr;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     A[size_t(i) * n + i] += lam;
-    sb[2 * i + 0] = d.b[(size_t(m) * n + i) * 2 + 0];
-    sb[2 * i + 1] = d.b[(size_t(m) * n + i) * 2 + 1];
+    sb[2 * i + 0] = d.b[(vo + i) * 2 + 0];
+    sb[2 * i + 1] = d.b[(vo + i) * 2 + 1];
   }
   if (threadIdx.x == 0) d.trace[m] = lam;     // from here on the slot holds lam
   __syncthreads();
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
     if (fail) break;
     // the FP32 copy of the factor (refinement's correction solves) is written as each part
     // of L is final; its upper triangle is never read
-    float* L32 = d.L32 ? d.L32 + size_t(m) * n * n : nullptr;
+    float* L32 = d.L32 ? d.L32 + go : nullptr;
     for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
       int i = e / kb, j = e - i * kb;
       if (j <= i) {
@@ -193,8 +197,8 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
       }
     }
     for (int j = threadIdx.x; j < kb; j += blockDim.x) {
-      d.dinv[size_t(m) * n + k0 + j] = sInv[j];
-      if (L32) d.dinv32[size_t(m) * n + k0 + j] = float(sInv[j]);
+      d.dinv[vo + k0 + j] = sInv[j];
+      if (L32) d.dinv32[vo + k0 + j] = float(sInv[j]);
     }
     const int t0 = k0 + kb, t = n - t0;
     // panel: row i of the block column solves x L_kk^T = a
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
     if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
     return;
   }
-  chol_solve_2rhs(A, d.dinv + size_t(m) * n, n, sb, reinterpret_cast<double (*)[LDP]>(sD));
+  chol_solve_2rhs(A, d.dinv + vo, n, sb, reinterpret_cast<double (*)[LDP]>(sD));
   bool bad = false;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
     xo[i] = sb[i];
@@ -387,11 +391,15 @@ __device__ void chol_solve32_2rhs(const float* A, const float* dinv, int n, floa
 
 // Refinement update with the FP32 factor: x += (LL^T)^-1 (r - lam x); r - lam x in FP64,
 // rounded to FP32 for the solve, the correction added to x in FP64.
+template <bool VAR>
 __global__ void __launch_bounds__(256) chol_refine32_kernel(Dev d) {
   extern __shared__ __align__(16) float sb32[];
   __shared__ float sL[NB][LDP];
-  const int m = blockIdx.x, n = d.nz;
-  double* xo = d.x + size_t(m) * n * 2;
+  const int m = blockIdx.x;
+  const int n = VAR ? d.sub_n[m] : d.nz;
+  const size_t go = VAR ? size_t(d.sub_goff[m]) : size_t(m) * n * n;
+  const size_t vo = VAR ? size_t(d.sub_voff[m]) : size_t(m) * n;
+  double* xo = d.x + vo * 2;
   if (d.row_off[m + 1] == d.row_off[m] || d.status[m] != EDT_OK) {
     if (d.status[m] != EDT_OK)
       for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
@@ -399,9 +407,9 @@ __global__ void __launch_bounds__(256) chol_refine32_kernel(Dev d) {
   }
   const double lam = d.trace[m];
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
-    sb32[i] = float(d.r[size_t(m) * n * 2 + i] - lam * xo[i]);
+    sb32[i] = float(d.r[vo * 2 + i] - lam * xo[i]);
   __syncthreads();
-  chol_solve32_2rhs(d.L32 + size_t(m) * n * n, d.dinv32 + size_t(m) * n, n, sb32, sL);
+  chol_solve32_2rhs(d.L32 + go, d.dinv32 + vo, n, sb32, sL);
   bool bad = false;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
     const double v = xo[i] + double(sb32[i]);
@@ -460,16 +468,17 @@ int chol_launches(int nz) { return 1; }
 static size_t chol_smem(int nz) { return (size_t(nz) * LDP + NB * LDP + 2 * nz + 40) * sizeof(double); }
 
 cudaError_t prepare_chol(const Dev& d) {
-  cudaError_t e = cudaFuncSetAttribute(chol_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(chol_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(chol_smem(d.nz)));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(chol_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(chol_smem(d.nz)));
+  return cudaFuncSetAttribute(chol_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(chol_smem(d.nz)));
 }
 
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
   size_t smem = chol_smem(d.nz);
-  if (d.chol_df) chol_kernel<true><<<d.nsub, 256, smem, s>>>(d, trace_mode);
-  else chol_kernel<false><<<d.nsub, 256, smem, s>>>(d, trace_mode);
+  if (d.chol_df) chol_kernel<true, false><<<d.nsub, 256, smem, s>>>(d, trace_mode);
+  else chol_kernel<false, false><<<d.nsub, 256, smem, s>>>(d, trace_mode);
   return cudaGetLastError();
 }
 
@@ -479,8 +488,25 @@ cudaError_t launch_chol_resolve(const Dev& d, cudaStream_t s) {
 }
 
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s) {
-  if (d.L32) chol_refine32_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(float), s>>>(d);
+  if (d.L32) chol_refine32_kernel<false><<<d.nsub, 256, size_t(2 * d.nz) * sizeof(float), s>>>(d);
   else chol_solve_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 1);
+  return cudaGetLastError();
+}
+
+// Streaming batches: subproblem m has size sub_n[m] <= nmax; lam = trace[m] (trace_mode 1
+// with alpha = 1: the caller accumulates alpha * trace).
+cudaError_t prepare_chol_var(int nmax) {
+  return cudaFuncSetAttribute(chol_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(chol_smem(nmax)));
+}
+
+cudaError_t launch_chol_var(const Dev& d, int nmax, cudaStream_t s) {
+  chol_kernel<false, true><<<d.nsub, 256, chol_smem(nmax), s>>>(d, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_update_var(const Dev& d, int nmax, cudaStream_t s) {
+  chol_refine32_kernel<true><<<d.nsub, 256, size_t(2 * nmax) * sizeof(float), s>>>(d);
   return cudaGetLastError();
 }
 

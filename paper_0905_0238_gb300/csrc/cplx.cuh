@@ -62,4 +62,24 @@ __host__ __device__ __forceinline__ double2 csqrt_upper(double2 w) {
   return z;
 }
 
+// e^{i kappa x} for kappa = (kx, ky) and x >= 0 given as FP32 (hi, lo) pairs, ~1e-7
+// relative: the phase kx x is formed as an unevaluated sum p + q (exact product of the high
+// parts by fma, plus the cross terms), reduced modulo 2 pi with a three-constant Cody-Waite
+// split (2 pi = C1 + C2 + C3, C1 = 6.28125 so that k C1 is exact for |k| < 2^16), and
+// evaluated with FP32 sincos; the decay e^{-ky x} uses the FP32 product.
+__device__ __forceinline__ float2 expi_ff(float kxh, float kxl, float kyh, float xh, float xl) {
+  const float C1 = 6.28125f, C2 = 0.0019353071693331003f, C3 = 1.0253131677018246e-11f;
+  const float p = kxh * xh;
+  const float q = fmaf(kxh, xh, -p) + fmaf(kxh, xl, kxl * xh);
+  const float k = rintf(p * 0.15915493667125702f);
+  float r = fmaf(-k, C1, p);
+  r = fmaf(-k, C2, r);
+  r = fmaf(-k, C3, r);
+  r += q;
+  float sn, cs;
+  sincosf(r, &sn, &cs);
+  const float mag = expf(-kyh * (xh + xl));
+  return make_float2(mag * cs, mag * sn);
+}
+
 }  // namespace edt

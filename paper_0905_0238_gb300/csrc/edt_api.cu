@@ -28,6 +28,8 @@ struct Region { size_t off = 0, bytes = 0; };
 
 }  // namespace
 
+int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
 }  // namespace edt
 
 using namespace edt;

@@ -143,7 +143,15 @@ struct Dev {
   float2* gbar;                 // [nf][N][nz] dJ/dg per full lateral index (aliases g64)
   int* status;                  // [nsub]
   unsigned int* flags;          // [8] device-side error flags
+  // streaming batches (per-subproblem sizes; null for a context's own subproblems)
+  const int* sub_n;             // [nsub] unknowns of subproblem m
+  const long long* sub_goff;    // [nsub] element offset of its matrix in G and L32
+  const long long* sub_voff;    // [nsub] element offset of its vectors (dinv; b, x, r x 2)
+  const int* sub_order;         // [nsub] launch order of the factorisations (largest first), or null
 };
+
+// Record a CUDA error for edt_last_cuda_error; returns EDT_ECUDA.
+int record_cuda_error(cudaError_t e);
 
 // ---- launchers (each returns cudaGetLastError()) ---------------------------------------
 constexpr int GREEN_G64 = 1, GREEN_G32 = 2;   // tables launch_green writes
@@ -207,6 +215,11 @@ constexpr int GRAD_MAX_LAYERS = 64;
 bool grad_supported(const Dev& d);
 cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const void* D, int D_dtype,
                                double* J, void* gV, double* gc, cudaStream_t s);
+
+// Streaming batches: Cholesky and refinement update with per-subproblem sizes (<= nmax).
+cudaError_t prepare_chol_var(int nmax);
+cudaError_t launch_chol_var(const Dev& d, int nmax, cudaStream_t s);
+cudaError_t launch_refine_update_var(const Dev& d, int nmax, cudaStream_t s);
 
 // One-time kernel attribute setup (opt-in shared memory), done outside any stream capture.
 cudaError_t prepare_fft(const Dev& d);

@@ -181,26 +181,6 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval64_kernel(Dev d) {
   }
 }
 
-// e^{i kappa x} for kappa = (kx, ky) and x >= 0 given as FP32 (hi, lo) pairs, ~1e-7
-// relative: the phase kx x is formed as an unevaluated sum p + q (exact product of the high
-// parts by fma, plus the cross terms), reduced modulo 2 pi with a three-constant Cody-Waite
-// split (2 pi = C1 + C2 + C3, C1 = 6.28125 so that k C1 is exact for |k| < 2^16), and
-// evaluated with FP32 sincos; the decay e^{-ky x} uses the FP32 product.
-__device__ __forceinline__ float2 expi_ff(float kxh, float kxl, float kyh, float xh, float xl) {
-  const float C1 = 6.28125f, C2 = 0.0019353071693331003f, C3 = 1.0253131677018246e-11f;
-  const float p = kxh * xh;
-  const float q = fmaf(kxh, xh, -p) + fmaf(kxh, xl, kxl * xh);
-  const float k = rintf(p * 0.15915493667125702f);
-  float r = fmaf(-k, C1, p);
-  r = fmaf(-k, C2, r);
-  r = fmaf(-k, C3, r);
-  r += q;
-  float sn, cs;
-  sincosf(r, &sn, &cs);
-  const float mag = expf(-kyh * (xh + xl));
-  return make_float2(mag * cs, mag * sn);
-}
-
 __global__ void green_eval32_kernel(Dev d) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)d.nf * d.nk * d.nz;

@@ -55,6 +55,27 @@ class edt_tuning(C.Structure):
     ]
 
 
+class edt_sub1d(C.Structure):
+    _fields_ = [
+        ("nz", C.c_int), ("dz", C.c_double), ("z0", C.c_double),
+        ("eps", C.c_double), ("alpha", C.c_double), ("dx", C.c_double),
+        ("nlayer", C.c_int), ("layer_top_m", C.POINTER(C.c_double)),
+        ("layer_vel_mps", C.POINTER(C.c_double)),
+        ("nfreq", C.c_int), ("freq_hz", C.POINTER(C.c_double)),
+        ("nk", C.c_int), ("kval", C.POINTER(C.c_double)),
+        ("nrow", C.c_int), ("rows", C.POINTER(C.c_int)), ("data", C.POINTER(C.c_float)),
+    ]
+
+
+class edt_stream_stats(C.Structure):
+    _fields_ = [
+        ("requests", C.c_longlong), ("batches", C.c_longlong), ("compute_ms", C.c_double),
+        ("busy_ms", C.c_double),
+        ("bytes_in", C.c_longlong), ("bytes_out", C.c_longlong),
+        ("launches_per_batch", C.c_int), ("arena_bytes", C.c_size_t), ("max_batch", C.c_int),
+    ]
+
+
 class EdtError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = _lib().edt_strerror(code).decode()
@@ -110,6 +131,25 @@ def _lib() -> C.CDLL:
                      "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning",
                      "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint",
                      "edt_set_host_pipeline"):
+            getattr(L, name).restype = i
+        ll = C.c_longlong
+        L.edt_stream_request_bytes.argtypes = [C.POINTER(edt_sub1d)]
+        L.edt_stream_request_bytes.restype = ll
+        L.edt_stream_plan.argtypes = [i, C.POINTER(ll), ll, i, C.POINTER(i)]
+        L.edt_stream_create.argtypes = [C.POINTER(vp), i, vp, C.POINTER(sz)]
+        L.edt_stream_set_workspace.argtypes = [vp, vp, sz]
+        L.edt_stream_submit.argtypes = [vp, i, C.POINTER(edt_sub1d), vp, vp, C.POINTER(ll)]
+        L.edt_stream_wait.argtypes = [vp, ll, C.POINTER(d)]
+        L.edt_stream_query.argtypes = [vp, ll, C.POINTER(i)]
+        L.edt_stream_epoch.argtypes = [vp]
+        L.edt_stream_get_stats.argtypes = [vp, C.POINTER(edt_stream_stats)]
+        L.edt_stream_set_profiling.argtypes = [vp, i]
+        L.edt_stream_read_profile.argtypes = [vp, C.POINTER(d), C.POINTER(C.c_char_p), i, C.POINTER(ll)]
+        L.edt_stream_destroy.argtypes = [vp]
+        L.edt_stream_destroy.restype = None
+        for name in ("edt_stream_plan", "edt_stream_create", "edt_stream_set_workspace",
+                     "edt_stream_submit", "edt_stream_wait", "edt_stream_query", "edt_stream_epoch",
+                     "edt_stream_get_stats", "edt_stream_set_profiling", "edt_stream_read_profile"):
             getattr(L, name).restype = i
         _LIB = L
     return _LIB
@@ -462,3 +502,164 @@ class Solver:
 
     def read_profile(self):
         return edt_read_profile(self.ctx)
+
+
+# ---- streaming 1D subproblems (edt_stream_*) ---------------------------------------------
+def _sub1d_array(subs):
+    """ctypes array of edt_sub1d for objects with the fields of synth.stream.Sub1D, plus the
+    numpy arrays it points into (kept alive by the caller until the submit returns)."""
+    arr = (edt_sub1d * max(len(subs), 1))()
+    keep = []
+    dp, ip, fp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_float)
+    for i, s in enumerate(subs):
+        tops = np.ascontiguousarray(s.layer_top, dtype=np.float64)
+        vel = np.ascontiguousarray(s.layer_vel, dtype=np.float64)
+        fr = np.ascontiguousarray(s.freq_hz, dtype=np.float64)
+        kv = np.ascontiguousarray(s.kval, dtype=np.float64)
+        rows = np.ascontiguousarray(s.rows, dtype=np.int32).reshape(-1, 3)
+        data = np.ascontiguousarray(s.data, dtype=np.complex64).reshape(-1, 2).view(np.float32)
+        keep += [tops, vel, fr, kv, rows, data]
+        e = arr[i]
+        e.nz, e.dz, e.z0 = int(s.nz), float(s.dz), float(s.z0)
+        e.eps, e.alpha, e.dx = float(s.eps), float(s.alpha), float(s.dx)
+        e.nlayer = len(tops)
+        e.layer_top_m, e.layer_vel_mps = tops.ctypes.data_as(dp), vel.ctypes.data_as(dp)
+        e.nfreq, e.freq_hz = len(fr), fr.ctypes.data_as(dp)
+        e.nk, e.kval = len(kv), kv.ctypes.data_as(dp)
+        e.nrow, e.rows, e.data = rows.shape[0], rows.ctypes.data_as(ip), data.ctypes.data_as(fp)
+    return arr, keep
+
+
+def edt_stream_request_bytes(sub) -> int:
+    arr, keep = _sub1d_array([sub])
+    return _check(_lib().edt_stream_request_bytes(arr), "edt_stream_request_bytes")
+
+
+def edt_stream_plan(request_bytes, arena_bytes: int, max_batch: int):
+    """(number of batches, batch index of every request) of the admission plan."""
+    rb = np.ascontiguousarray(request_bytes, dtype=np.int64)
+    out = np.zeros(len(rb), dtype=np.int32)
+    nb = _check(_lib().edt_stream_plan(len(rb), rb.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                       int(arena_bytes), int(max_batch),
+                                       out.ctypes.data_as(C.POINTER(C.c_int))), "edt_stream_plan")
+    return nb, out
+
+
+def edt_stream_create(max_batch: int, stream: int = 0):
+    ctx, ws = C.c_void_p(), C.c_size_t()
+    _check(_lib().edt_stream_create(C.byref(ctx), int(max_batch), C.c_void_p(stream), C.byref(ws)),
+           "edt_stream_create")
+    return ctx, ws.value
+
+
+def edt_stream_set_workspace(ctx, ptr: int, nbytes: int):
+    _check(_lib().edt_stream_set_workspace(ctx, C.c_void_p(ptr), nbytes), "edt_stream_set_workspace")
+
+
+def edt_stream_submit(ctx, subs, vhat: np.ndarray, status: np.ndarray) -> int:
+    arr, keep = _sub1d_array(subs)
+    t = C.c_longlong()
+    _check(_lib().edt_stream_submit(ctx, len(subs), arr, vhat.ctypes.data, status.ctypes.data, C.byref(t)),
+           "edt_stream_submit")
+    return t.value
+
+
+def edt_stream_wait(ctx, ticket: int) -> float:
+    ms = C.c_double()
+    _check(_lib().edt_stream_wait(ctx, int(ticket), C.byref(ms)), "edt_stream_wait")
+    return ms.value
+
+
+def edt_stream_query(ctx, ticket: int) -> bool:
+    done = C.c_int()
+    _check(_lib().edt_stream_query(ctx, int(ticket), C.byref(done)), "edt_stream_query")
+    return bool(done.value)
+
+
+def edt_stream_epoch(ctx):
+    _check(_lib().edt_stream_epoch(ctx), "edt_stream_epoch")
+
+
+def edt_stream_get_stats(ctx) -> edt_stream_stats:
+    st = edt_stream_stats()
+    _check(_lib().edt_stream_get_stats(ctx, C.byref(st)), "edt_stream_get_stats")
+    return st
+
+
+def edt_stream_set_profiling(ctx, on: bool):
+    _check(_lib().edt_stream_set_profiling(ctx, int(bool(on))), "edt_stream_set_profiling")
+
+
+def edt_stream_read_profile(ctx, max_kernels: int = 8):
+    """({kernel name: summed ms}, batches covered) since the last read."""
+    ms = (C.c_double * max_kernels)()
+    names = (C.c_char_p * max_kernels)()
+    nb = C.c_longlong()
+    n = _check(_lib().edt_stream_read_profile(ctx, ms, names, max_kernels, C.byref(nb)),
+               "edt_stream_read_profile")
+    return {names[i].decode(): ms[i] for i in range(n)}, nb.value
+
+
+class Stream:
+    """A streaming solver of independent 1D subproblems with a torch-owned device workspace.
+
+    ``submit(subs)`` admits the requests (objects with the fields of ``synth.stream.Sub1D``)
+    and returns a ticket; ``wait(ticket)`` returns the list of Vhat arrays (complex128, one per
+    request), their status codes and the completion time in ms after the last ``epoch()``.
+    """
+
+    def __init__(self, max_batch: int = 512, workspace_bytes: Optional[int] = None, device=None):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.ctx, self.ws_min = edt_stream_create(max_batch, 0)
+        nbytes = max(int(self.ws_min), int(workspace_bytes or 0))
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        edt_stream_set_workspace(self.ctx, self.workspace.data_ptr(), nbytes)
+        self._pending = {}
+
+    def submit(self, subs) -> int:
+        nz = [int(s.nz) for s in subs]
+        vhat = np.empty(sum(nz), dtype=np.complex128)
+        status = np.empty(len(subs), dtype=np.int32)
+        t = edt_stream_submit(self.ctx, subs, vhat, status)
+        self._pending[t] = (nz, vhat, status)
+        return t
+
+    def wait(self, ticket: int):
+        ms = edt_stream_wait(self.ctx, ticket)
+        nz, vhat, status = self._pending.pop(ticket)
+        cuts = np.cumsum([0] + nz)
+        return [vhat[cuts[i]:cuts[i + 1]] for i in range(len(nz))], status, ms
+
+    def query(self, ticket: int) -> bool:
+        return edt_stream_query(self.ctx, ticket)
+
+    def solve(self, subs):
+        """Submit and wait: (list of Vhat, status)."""
+        v, st, _ = self.wait(self.submit(subs))
+        return v, st
+
+    def epoch(self):
+        edt_stream_epoch(self.ctx)
+
+    def set_profiling(self, on=True):
+        edt_stream_set_profiling(self.ctx, on)
+
+    def read_profile(self):
+        return edt_stream_read_profile(self.ctx)
+
+    def stats(self):
+        st = edt_stream_get_stats(self.ctx)
+        return {k: getattr(st, k) for k, _ in edt_stream_stats._fields_}
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            _lib().edt_stream_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
