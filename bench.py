@@ -965,7 +965,7 @@ def main_stream(args, world, rank, local):
                   achieved_tflops=gram_issued / (gram_ms / 1e3) / 1e12 if gram_ms else None,
                   peak_tflops=bf16, frac=(gram_issued / (gram_ms / 1e3) / 1e12 / bf16) if gram_ms else None),
         dominant_kernel=kern, nonzero_status=bad,
-        gpu_launches=int(st1["launches_per_batch"]) * int((st1["batches"] - st0["batches"])),
+        gpu_launches=int(st1["launches"] - st0["launches"]),
         roofline=roof, clocks=clk, cpu_baseline=cpu)
     print(json.dumps(line))
     if world > 1:

@@ -338,8 +338,9 @@ int edt_read_profile(edt_ctx* ctx, double* ms, const char** names, int max_stage
  *
  * Requests are admitted by device memory: the caller's workspace is split into two arenas, a
  * submitted list is cut in order into batches whose summed edt_stream_request_bytes fit one
- * arena (and at most max_batch requests), and each batch runs as one set of eight launches
- * over all its requests.  The two arenas have a CUDA stream each, so one batch's launches
+ * arena (and at most max_batch requests), and each batch runs as eight stages whose launches
+ * cover all its requests (the FP64 Cholesky as a panel and a tile-update launch per 32-column
+ * step, so that a large factorisation spreads over many SMs).  The two arenas have a CUDA stream each, so one batch's launches
  * overlap the next batch's copies and launches while the host packs the batch after into
  * pinned staging.  All state stays on the device until the results of a batch are copied
  * back. */
@@ -372,7 +373,9 @@ typedef struct {
                                    batches of the intervals in which their launches ran
                                    (overlapping batches counted once)                       */
   long long bytes_in, bytes_out;/* host-to-device and device-to-host bytes copied            */
-  int launches_per_batch;       /* CUDA kernels one batch launches                           */
+  long long launches;           /* CUDA kernels launched (all batches)                       */
+  int launches_per_batch;       /* most kernels one batch launched: 7 + 2 per 32-column step of
+                                   its blocked Cholesky, at most 39                          */
   size_t arena_bytes;           /* device bytes of one arena (half the workspace)            */
   int max_batch;
 } edt_stream_stats;
@@ -420,8 +423,8 @@ int edt_stream_epoch(edt_stream* s);
 
 int edt_stream_get_stats(const edt_stream* s, edt_stream_stats* out);
 
-/* Per-launch device timing: with profiling on, CUDA events are recorded between the eight
- * launches of every batch; edt_stream_read_profile delivers the batches in flight, returns the
+/* Per-stage device timing: with profiling on, batches run one at a time (no overlap between
+ * the two arenas' streams) and CUDA events are recorded between the eight stages of every batch; edt_stream_read_profile delivers the batches in flight, returns the
  * summed milliseconds per launch (names[i] static strings) since the last read, the number of
  * batches they cover in *n_batches, and resets.  Returns the number of entries written. */
 int edt_stream_set_profiling(edt_stream* s, int on);

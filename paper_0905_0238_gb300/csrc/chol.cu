@@ -421,11 +421,15 @@ __global__ void __launch_bounds__(256) chol_refine32_kernel(Dev d) {
 }
 
 // mode 0: x = (LL^T)^-1 b; mode 1 (refinement): x += (LL^T)^-1 (r - lam x).
+template <bool VAR>
 __global__ void __launch_bounds__(256) chol_solve_kernel(Dev d, int mode) {
   extern __shared__ __align__(16) double sb[];
   __shared__ double sL[NB][LDP];
-  const int m = blockIdx.x, n = d.nz;
-  double* xo = d.x + size_t(m) * n * 2;
+  const int m = blockIdx.x;
+  const int n = VAR ? d.sub_n[m] : d.nz;
+  const size_t go = VAR ? size_t(d.sub_goff[m]) : size_t(m) * n * n;
+  const size_t vo = VAR ? size_t(d.sub_voff[m]) : size_t(m) * n;
+  double* xo = d.x + vo * 2;
   const bool has_rows = d.row_off[m + 1] > d.row_off[m];
   if (!has_rows || d.status[m] != EDT_OK) {
     if (mode == 0 || d.status[m] != EDT_OK)
@@ -434,9 +438,9 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(Dev d, int mode) {
   }
   const double lam = d.trace[m];
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
-    sb[i] = mode == 0 ? d.b[size_t(m) * n * 2 + i] : d.r[size_t(m) * n * 2 + i] - lam * xo[i];
+    sb[i] = mode == 0 ? d.b[vo * 2 + i] : d.r[vo * 2 + i] - lam * xo[i];
   __syncthreads();
-  chol_solve_2rhs(d.G + size_t(m) * n * n, d.dinv + size_t(m) * n, n, sb, sL);
+  chol_solve_2rhs(d.G + go, d.dinv + vo, n, sb, sL);
   bool bad = false;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
     const double v = mode == 0 ? sb[i] : xo[i] + sb[i];
@@ -445,6 +449,169 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(Dev d, int mode) {
   }
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0 && bad) d.status[m] = EDT_ENONFINITE;
+}
+
+// ------------------------------------------------------------------ blocked Cholesky, several
+// launches per factorisation: step k (columns k0 = 32 k .. k0 + 31) is one panel launch (one CTA
+// per active subproblem: diagonal block by one warp, panel rows by row-per-thread triangular
+// solves) and one update launch over 64 x 64 tiles of every active subproblem's trailing lower
+// triangle, so a large factorisation spreads over many SMs instead of running on one.
+constexpr int UT = 64;
+
+template <bool VAR>
+__device__ __forceinline__ void sub_geom(const Dev& d, int m, int& n, size_t& go, size_t& vo) {
+  n = VAR ? d.sub_n[m] : d.nz;
+  go = VAR ? size_t(d.sub_goff[m]) : size_t(m) * n * n;
+  vo = VAR ? size_t(d.sub_voff[m]) : size_t(m) * n;
+}
+
+// trace_mode 0: trace from the diagonal of G; 1: lam = alpha * trace[m] (the producer's trace).
+template <bool VAR>
+__global__ void __launch_bounds__(256) cb_panel_kernel(Dev d, int k0, const int* act, int trace_mode) {
+  __shared__ double sD[NB * LDP];
+  __shared__ double sInv[NB];
+  __shared__ double red[40];
+  __shared__ int fail;
+  const int m = act[blockIdx.x];
+  int n;
+  size_t go, vo;
+  sub_geom<VAR>(d, m, n, go, vo);
+  if (d.status[m] != EDT_OK) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* A = d.G + go;
+  if (threadIdx.x == 0) fail = 0;
+  if (k0 == 0) {
+    double tr;
+    if (trace_mode == 0) {
+      double t = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) t += A[size_t(i) * n + i];
+      tr = block_sum(t, red);
+    } else {
+      tr = d.trace[m];
+    }
+    const double lam = d.alpha * tr;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) A[size_t(i) * n + i] += lam;
+    __syncthreads();
+    if (threadIdx.x == 0) d.trace[m] = lam;
+  }
+  const int kb = min(NB, n - k0);
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e - i * kb;
+    if (j <= i) sD[i * LDP + j] = A[size_t(k0 + i) * n + k0 + j];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = 0; j < kb; ++j) {
+      const double djj = sD[j * LDP + j];
+      if (!(djj > 0.0) || !isfinite(djj)) { if (lane == 0) fail = 1; break; }
+      const double inv = rsqrt(djj);
+      __syncwarp();
+      if (lane == j) { sD[j * LDP + j] = djj * inv; sInv[j] = inv; }
+      if (lane > j && lane < kb) sD[lane * LDP + j] *= inv;
+      __syncwarp();
+      if (lane > j && lane < kb) {
+        const double lij = sD[lane * LDP + j];
+        for (int l = j + 1; l <= lane; ++l) sD[lane * LDP + l] -= lij * sD[l * LDP + j];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (fail) {
+    if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
+    return;
+  }
+  float* L32 = d.L32 ? d.L32 + go : nullptr;
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e - i * kb;
+    if (j <= i) {
+      A[size_t(k0 + i) * n + k0 + j] = sD[i * LDP + j];
+      if (L32) L32[size_t(k0 + i) * n + k0 + j] = float(sD[i * LDP + j]);
+    }
+  }
+  for (int j = threadIdx.x; j < kb; j += blockDim.x) {
+    d.dinv[vo + k0 + j] = sInv[j];
+    if (L32) d.dinv32[vo + k0 + j] = float(sInv[j]);
+  }
+  const int t0 = k0 + kb;
+  for (int i = t0 + threadIdx.x; i < n; i += blockDim.x) {
+    double x[NB];
+    double* Ai = A + size_t(i) * n + k0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) x[j] = j < kb ? Ai[j] : 0.0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j < kb) {
+        double sacc = x[j];
+#pragma unroll
+        for (int l = 0; l < j; ++l) sacc -= x[l] * sD[j * LDP + l];
+        x[j] = sacc * sInv[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      if (j < kb) Ai[j] = x[j];
+    if (L32) {
+      float* Li = L32 + size_t(i) * n + k0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        if (j < kb) Li[j] = float(x[j]);
+    }
+  }
+}
+
+// One 64 x 64 tile (bi, bj <= bi) of the trailing lower triangle: C -= P_bi P_bj^T; thread
+// (ti, tj) owns rows ti + 16 u and columns tj + 16 v (conflict-free shared-memory reads).
+template <bool VAR>
+__global__ void __launch_bounds__(256) cb_update_kernel(Dev d, int k0, const int* act,
+                                                        const long long* tpre, int nact) {
+  __shared__ double Pi[UT * LDP], Pj[UT * LDP];
+  int lo = 0, hi = nact - 1;
+  const long long t = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tpre[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const int m = act[lo];
+  int n;
+  size_t go, vo;
+  sub_geom<VAR>(d, m, n, go, vo);
+  if (d.status[m] != EDT_OK) return;
+  const int kb = min(NB, n - k0), t0 = k0 + kb;
+  const int e = int(t - tpre[lo]);
+  int bi = int((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+  while (bi * (bi + 1) / 2 > e) --bi;
+  while ((bi + 1) * (bi + 2) / 2 <= e) ++bi;
+  const int bj = e - bi * (bi + 1) / 2;
+  const int r0 = t0 + bi * UT, c0 = t0 + bj * UT;
+  double* A = d.G + go;
+  for (int q = threadIdx.x; q < UT * kb; q += blockDim.x) {
+    const int i = q / kb, l = q - i * kb;
+    Pi[i * LDP + l] = r0 + i < n ? A[size_t(r0 + i) * n + k0 + l] : 0.0;
+    Pj[i * LDP + l] = c0 + i < n ? A[size_t(c0 + i) * n + k0 + l] : 0.0;
+  }
+  __syncthreads();
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  double acc[4][4] = {};
+  for (int l = 0; l < kb; ++l) {
+    double pi[4], pj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pi[u] = Pi[(ti + 16 * u) * LDP + l];
+      pj[u] = Pj[(tj + 16 * u) * LDP + l];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fma(pi[u], pj[v], acc[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int row = r0 + ti + 16 * u, col = c0 + tj + 16 * v;
+      if (row < n && col <= row) A[size_t(row) * n + col] -= acc[u][v];
+    }
 }
 
 __global__ void trace_diag_kernel(Dev d) {
@@ -483,13 +650,13 @@ cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
 }
 
 cudaError_t launch_chol_resolve(const Dev& d, cudaStream_t s) {
-  chol_solve_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 0);
+  chol_solve_kernel<false><<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s) {
   if (d.L32) chol_refine32_kernel<false><<<d.nsub, 256, size_t(2 * d.nz) * sizeof(float), s>>>(d);
-  else chol_solve_kernel<<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 1);
+  else chol_solve_kernel<false><<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 1);
   return cudaGetLastError();
 }
 
@@ -500,9 +667,41 @@ cudaError_t prepare_chol_var(int nmax) {
                               int(chol_smem(nmax)));
 }
 
+int chol_block_cols() { return NB; }
+
 cudaError_t launch_chol_var(const Dev& d, int nmax, cudaStream_t s) {
   chol_kernel<false, true><<<d.nsub, 256, chol_smem(nmax), s>>>(d, 1);
   return cudaGetLastError();
+}
+
+// Blocked form: nstep panel + update launches, then the solves.  act + k * nsub lists the
+// subproblems active at step k (n > 32 k, rows > 0), nact[k] of them; tpre + k * (nsub + 1) the
+// prefix sums of their trailing tile counts (tpre[k][nact[k]] tiles in the update launch).
+template <bool VAR>
+static cudaError_t blocked(const Dev& d, int nmax, int nstep, const int* act, const int* nact,
+                           const long long* tpre, const long long* ntile, int trace_mode, cudaStream_t s) {
+  for (int k = 0; k < nstep; ++k) {
+    if (nact[k] == 0) continue;
+    cb_panel_kernel<VAR><<<nact[k], 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub, trace_mode);
+    if (ntile[k] > 0)
+      cb_update_kernel<VAR><<<unsigned(ntile[k]), 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub,
+                                                               tpre + size_t(k) * (d.nsub + 1), nact[k]);
+  }
+  chol_solve_kernel<VAR><<<d.nsub, 256, size_t(2 * nmax) * sizeof(double), s>>>(d, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_blocked(const Dev& d, bool var, int nmax, int nstep, const int* act_dev,
+                                const int* nact_host, const long long* tpre_dev,
+                                const long long* ntile_host, int trace_mode, cudaStream_t s) {
+  return var ? blocked<true>(d, nmax, nstep, act_dev, nact_host, tpre_dev, ntile_host, trace_mode, s)
+             : blocked<false>(d, nmax, nstep, act_dev, nact_host, tpre_dev, ntile_host, trace_mode, s);
+}
+
+int chol_blocked_tiles(int n, int k0) {
+  const int t0 = k0 + (n - k0 < NB ? n - k0 : NB);
+  const int T = (n - t0 + UT - 1) / UT;
+  return T > 0 ? T * (T + 1) / 2 : 0;
 }
 
 cudaError_t launch_refine_update_var(const Dev& d, int nmax, cudaStream_t s) {

@@ -220,6 +220,14 @@ cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const v
 cudaError_t prepare_chol_var(int nmax);
 cudaError_t launch_chol_var(const Dev& d, int nmax, cudaStream_t s);
 cudaError_t launch_refine_update_var(const Dev& d, int nmax, cudaStream_t s);
+// Blocked Cholesky over several launches (panel + tile update per 32-column step, then the
+// solves); see chol.cu for the step lists.  chol_blocked_tiles: update tiles of step k0 of an
+// n-unknown subproblem; chol_block_cols: the panel width.
+cudaError_t launch_chol_blocked(const Dev& d, bool var, int nmax, int nstep, const int* act_dev,
+                                const int* nact_host, const long long* tpre_dev,
+                                const long long* ntile_host, int trace_mode, cudaStream_t s);
+int chol_blocked_tiles(int n, int k0);
+int chol_block_cols();
 
 // One-time kernel attribute setup (opt-in shared memory), done outside any stream capture.
 cudaError_t prepare_fft(const Dev& d);

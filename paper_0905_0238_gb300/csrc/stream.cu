@@ -4,7 +4,7 @@
 //     min ||Ahat x_+- - dhat_+-||^2 + lam ||x_+-||^2,   lam = alpha trace(Ahat^T Ahat),
 // Ahat = [Re a; Im a], a_i(z_j) = s_f g(k_p, z_j) g(k_q, z_j) for row i = (f, p, q).
 //
-// A batch of requests runs as eight launches, every one covering all requests of the batch:
+// A batch of requests runs as eight stages, every launch covering all requests of the batch:
 //   st_prep   per depth: layer index and the depth below its top as FP32 (hi, lo) pairs;
 //   st_coef   per (request, f, k): vertical wavenumbers in FP64 (complex square root), the
 //             reflectivity recursion of the depth march (upward for the reflection coefficients,
@@ -18,7 +18,9 @@
 //   st_gram   persistent tcgen05 kernel over (request, 128-depth tile pair) items: bulk copies
 //             stage the hi/lo tiles, three BF16 MMAs per K step accumulate in tensor memory,
 //             the epilogue writes the FP64 lower triangle of G and b_+- = Ahat^T dhat_+-;
-//   chol      FP64 Cholesky of G + lam I and the two solves (per-request size);
+//   chol      FP64 Cholesky of G + lam I in 32-column steps (a panel launch and a 64 x 64 tile
+//             update launch per step over every active request, so one large factorisation
+//             spreads over many SMs), then the two solves (per-request size);
 //   st_refine matrix-free residual Ahat^T (dhat - Ahat x), FP32 products, FP64 accumulation;
 //   update    x += (LL^T)^-1 (r - lam x) with the FP32 copy of the factor.
 // Every wait of the tensor-core kernel is bounded; on expiry it raises a device flag.
@@ -527,7 +529,8 @@ cudaError_t launch_stream_batch(const StBatch& b, int nmax, cudaStream_t s, cuda
   d.b = b.b; d.x = b.x; d.r = b.r; d.trace = b.trace; d.status = b.status;
   d.row_off = b.row_off;
   d.sub_n = b.sub_n; d.sub_goff = b.sub_goff; d.sub_voff = b.sub_voff; d.sub_order = b.sub_order;
-  cudaError_t e = launch_chol_var(d, nmax, s);
+  cudaError_t e = launch_chol_blocked(d, true, nmax, b.cb_nstep, b.cb_act, b.cb_nact_host, b.cb_tpre,
+                                      b.cb_ntile_host, 1, s);
   if (e != cudaSuccess) return e;
   mark(6);
   if (b.tot_rc > 0) st_refine_kernel<<<unsigned(b.tot_rc), 256, 0, s>>>(b);

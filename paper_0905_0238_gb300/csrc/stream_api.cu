@@ -18,7 +18,6 @@ int st_cuda_fail(cudaError_t e) { return record_cuda_error(e); }
 
 constexpr size_t AL = 256;                       // array alignment inside an arena
 constexpr size_t TILE_AL = 1024;                 // per-request tile alignment (bulk copies)
-constexpr int ST_LAUNCHES = 8;
 constexpr size_t FIXED_BYTES = 64 * 1024;        // per-batch tables and alignment slack
 
 size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -54,6 +53,7 @@ size_t bytes_of(const ReqShape& r) {
   b += size_t(r.nz) * r.nz * (sizeof(double) + sizeof(float));      // G, L32
   b += size_t(r.nz) * (sizeof(double) + sizeof(float) + 6 * sizeof(double));   // dinv(32), b, x, r
   b += sizeof(double) + sizeof(int);                                 // trace, status
+  b += size_t(ST_MAX_NZ / 32) * (sizeof(int) + sizeof(long long));   // blocked-Cholesky step lists
   return al(b, 64);
 }
 
@@ -259,6 +259,12 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   const size_t o_goff = take(sizeof(long long) * n);
   const size_t o_voff = take(sizeof(long long) * n);
   const size_t o_order = take(sizeof(int) * n);
+  int nmax = 1;
+  for (int i = 0; i < n; ++i) nmax = std::max(nmax, sh[i].nz);
+  const int nb_cols = chol_block_cols();
+  const int nstep = (nmax + nb_cols - 1) / nb_cols;
+  const size_t o_cbact = take(sizeof(int) * size_t(nstep) * n);
+  const size_t o_cbpre = take(sizeof(long long) * size_t(nstep) * (n + 1));
   const size_t o_items = take(sizeof(StItem) * std::max<size_t>(all.size(), 1));
   const size_t o_cta = take(sizeof(int) * (ncta + 1));
   const size_t o_dbl = take(sizeof(double) * n_dbl);
@@ -353,6 +359,25 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   }
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order, order + n, [&](int a, int b) { return sh[a].nz > sh[b].nz; });
+  // blocked Cholesky step lists: requests with rows and more than 32 k unknowns, largest first
+  int* cbact = reinterpret_cast<int*>(P + o_cbact);
+  long long* cbpre = reinterpret_cast<long long*>(P + o_cbpre);
+  std::vector<int> cb_nact(nstep, 0);
+  std::vector<long long> cb_ntile(nstep, 0);
+  for (int k = 0; k < nstep; ++k) {
+    int na = 0;
+    long long* tp = cbpre + size_t(k) * (n + 1);
+    tp[0] = 0;
+    for (int ii = 0; ii < n; ++ii) {
+      const int i = order[ii];
+      if (sh[i].nrow == 0 || sh[i].nz <= k * nb_cols) continue;
+      cbact[size_t(k) * n + na] = i;
+      tp[na + 1] = tp[na] + chol_blocked_tiles(sh[i].nz, k * nb_cols);
+      ++na;
+    }
+    cb_nact[k] = na;
+    cb_ntile[k] = tp[na];
+  }
   StItem* items = reinterpret_cast<StItem*>(P + o_items);
   int* cta0 = reinterpret_cast<int*>(P + o_cta);
   int ni = 0;
@@ -397,11 +422,18 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   b.sub_order = reinterpret_cast<int*>(A + o_order);
   b.flags = reinterpret_cast<unsigned int*>(A + o_flags);
   b.tot_z = pre_z[n]; b.tot_fk = pre_fk[n]; b.tot_fkz = pre_fkz[n]; b.tot_tw = pre_tw[n]; b.tot_rc = pre_rc[n];
-  int nmax = 1;
-  for (int i = 0; i < n; ++i) nmax = std::max(nmax, sh[i].nz);
+  b.cb_nstep = nstep;
+  b.cb_act = reinterpret_cast<const int*>(A + o_cbact);
+  b.cb_tpre = reinterpret_cast<const long long*>(A + o_cbpre);
+  b.cb_nact_host = cb_nact.data();
+  b.cb_ntile_host = cb_ntile.data();
+  int nlaunch = 1 + (b.tot_fk > 0) + (b.tot_fkz > 0) + (b.tot_tw > 0) + (ncta > 0) + 1 + (b.tot_rc > 0) + 1;
+  for (int k = 0; k < nstep; ++k) nlaunch += (cb_nact[k] > 0) + (cb_ntile[k] > 0);
 
   cudaError_t ce = cudaSuccess;
-  if (s->user) {
+  if (s->profiling && s->slot[k ^ 1].batch >= 0)       // profiled batches run one at a time
+    ce = cudaStreamWaitEvent(sl.st, s->slot[k ^ 1].done, 0);
+  if (ce == cudaSuccess && s->user) {
     ce = cudaEventRecord(s->ev_user, s->user);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(sl.st, s->ev_user, 0);
   }
@@ -423,6 +455,8 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   sl.batch = id;
   s->stats.requests += n;
   s->stats.batches += 1;
+  s->stats.launches += nlaunch;
+  s->stats.launches_per_batch = std::max(s->stats.launches_per_batch, nlaunch);
   s->stats.bytes_in += (long long)in_bytes;
   s->stats.bytes_out += (long long)out_bytes;
   *batch_id = id;
@@ -467,7 +501,6 @@ int edt_stream_create(edt_stream** out, int max_batch, void* stream, size_t* wor
     edt_stream_destroy(s);
     return st_cuda_fail(e);
   }
-  s->stats.launches_per_batch = ST_LAUNCHES;
   s->stats.max_batch = max_batch;
   if (workspace_min) *workspace_min = min_workspace();
   *out = s;

@@ -75,6 +75,13 @@ struct StBatch {
   unsigned int* flags;           // [1] tensor-core wait expired
   // launch extents (host side)
   long long tot_z, tot_fk, tot_fkz, tot_tw, tot_rc;
+  // blocked Cholesky: per 32-column step k the active requests (device, [nstep][nreq]), their
+  // prefix sums of update tiles (device, [nstep][nreq + 1]); counts on the host
+  int cb_nstep;
+  const int* cb_act;
+  const long long* cb_tpre;
+  const int* cb_nact_host;
+  const long long* cb_ntile_host;
 };
 
 constexpr int ST_NKERNEL = 8;

@@ -71,7 +71,7 @@ class edt_stream_stats(C.Structure):
     _fields_ = [
         ("requests", C.c_longlong), ("batches", C.c_longlong), ("compute_ms", C.c_double),
         ("busy_ms", C.c_double),
-        ("bytes_in", C.c_longlong), ("bytes_out", C.c_longlong),
+        ("bytes_in", C.c_longlong), ("bytes_out", C.c_longlong), ("launches", C.c_longlong),
         ("launches_per_batch", C.c_int), ("arena_bytes", C.c_size_t), ("max_batch", C.c_int),
     ]
 
