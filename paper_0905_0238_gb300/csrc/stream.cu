@@ -9,7 +9,7 @@
 //   st_coef   per (request, f, k): vertical wavenumbers in FP64 (complex square root), the
 //             reflectivity recursion of the depth march (upward for the reflection coefficients,
 //             downward for the amplitudes) in FP32 with double-float phases;
-//   st_eval   per (request, f, k, z): the FP32 table sqrt|s_f| g(k, z);
+//   st_eval   per (request, 8 (f, k) rows) x depth: the FP32 table sqrt|s_f| g(k, z);
 //   st_tiles  per (request, 32 complex rows, 32 depths): the kernel rows |s_f| g_p g_q, split
 //             into BF16 hi and lo and stored K-major in the 128-byte-swizzled layout the tensor
 //             cores read (the unit phase of s_f moves onto the data, which leaves the
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(128) st_coef_kernel(StBatch b) {
     // Im >= 0, then one Newton step kappa + (w - kappa^2) / (2 kappa): the square of the FP32
     // kappa is exact in FP64, so the residual is exact to FP64 rounding and the (hi, lo) pair
     // carries kappa to ~1e-14 relative with four FP64 products instead of a complex FP64 root
-    const double ic2 = 1.0 / (vel[j] * vel[j]);
+    const double ic2 = vel[J + j];                     // 1 / c_j^2, formed on the host
     const double wr2 = om2r * ic2 - kv2, wi2 = om2i * ic2;
     const float2 k32 = csqrt_upper32(make_float2(float(wr2), float(wi2)));
     const double rr = wr2 - (double(k32.x) * k32.x - double(k32.y) * k32.y);
@@ -165,25 +165,37 @@ __global__ void __launch_bounds__(128) st_coef_kernel(StBatch b) {
   }
 }
 
-// g32 = sqrt|s_f| A_l [exp(i kappa_l off) + rho_l exp(i kappa_l (2 h_l - off))]
-__global__ void st_eval_kernel(StBatch b) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= b.pre_fkz[b.nreq]) return;
-  const int q = find_req(b.pre_fkz, b.nreq, i);
+// g32 = sqrt|s_f| A_l [exp(i kappa_l off) + rho_l exp(i kappa_l (2 h_l - off))]: one CTA per
+// (request, 8 consecutive (f, k) rows), threads over depth (the depth's layer and offsets are
+// read once, the request found once per CTA)
+constexpr int EV_ROWS = 8;
+
+__global__ void __launch_bounds__(256) st_eval_kernel(StBatch b) {
+  const int q = find_req(b.pre_eb, b.nreq, blockIdx.x);
   const StSub S = b.sub[q];
-  const int e = int(i - b.pre_fkz[q]);        // < nf nk nz of one request (< 2^31)
-  const int z = e % S.nz;
-  const int fk = e / S.nz;
-  const int l = b.zl[S.o_v + z];
-  const float4 zo = b.zt[S.o_v + z];
-  const float4* c4 = reinterpret_cast<const float4*>(b.coef + S.o_coef + (size_t(fk) * S.nl + l) * 8);
-  const float4 k4 = c4[0], ar = c4[1];
-  float2 ex = expi_ff(k4.x, k4.y, k4.z, zo.x, zo.y);
-  if (l + 1 < S.nl) ex = ex + make_float2(ar.z, ar.w) * expi_ff(k4.x, k4.y, k4.z, zo.z, zo.w);
-  const float wr = 6.283185307179586f * float(b.dbl[S.o_freq + fk / S.nk]);
-  const float sq = sqrtf((wr * wr + S.eps2) * S.dzdx);   // sqrt|s_f|
-  const float2 g = make_float2(ar.x, ar.y) * ex;
-  b.g32[S.o_g + size_t(fk) * S.nzs + z] = make_float2(sq * g.x, sq * g.y);
+  const int fk0 = int(blockIdx.x - b.pre_eb[q]) * EV_ROWS;
+  const int nfk = S.nf * S.nk;
+  __shared__ float sq_row[EV_ROWS];                         // sqrt|s_f| of each row's frequency
+  if (threadIdx.x < EV_ROWS && fk0 + int(threadIdx.x) < nfk) {
+    const float wr = 6.283185307179586f * float(b.dbl[S.o_freq + (fk0 + threadIdx.x) / S.nk]);
+    sq_row[threadIdx.x] = sqrtf((wr * wr + S.eps2) * S.dzdx);
+  }
+  __syncthreads();
+  for (int z = threadIdx.x; z < S.nz; z += blockDim.x) {
+    const int l = b.zl[S.o_v + z];
+    const float4 zo = b.zt[S.o_v + z];
+    const bool two = l + 1 < S.nl;
+    for (int r = 0; r < EV_ROWS && fk0 + r < nfk; ++r) {
+      const int fk = fk0 + r;
+      const float4* c4 = reinterpret_cast<const float4*>(b.coef + S.o_coef + (size_t(fk) * S.nl + l) * 8);
+      const float4 k4 = c4[0], ar = c4[1];
+      float2 ex = expi_ff(k4.x, k4.y, k4.z, zo.x, zo.y);
+      if (two) ex = ex + make_float2(ar.z, ar.w) * expi_ff(k4.x, k4.y, k4.z, zo.z, zo.w);
+      const float sq = sq_row[r];
+      const float2 g = make_float2(ar.x, ar.y) * ex;
+      b.g32[S.o_g + size_t(fk) * S.nzs + z] = make_float2(sq * g.x, sq * g.y);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------- operand tiles
@@ -515,7 +527,7 @@ cudaError_t launch_stream_batch(const StBatch& b, int nmax, cudaStream_t s, cuda
   mark(1);
   if (b.tot_fk > 0) st_coef_kernel<<<blocks_for(b.tot_fk, 128), 128, 0, s>>>(b);
   mark(2);
-  if (b.tot_fkz > 0) st_eval_kernel<<<blocks_for(b.tot_fkz, 256), 256, 0, s>>>(b);
+  if (b.tot_eb > 0) st_eval_kernel<<<unsigned(b.tot_eb), 256, 0, s>>>(b);
   mark(3);
   if (b.tot_tw > 0) st_tiles_kernel<<<blocks_for(b.tot_tw * 32, 256), 256, 0, s>>>(b);
   mark(4);

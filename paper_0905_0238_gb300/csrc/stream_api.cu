@@ -44,7 +44,7 @@ size_t bytes_of(const ReqShape& r) {
   size_t b = 0;
   b += sizeof(StSub) + 7 * sizeof(long long) + sizeof(int) + 2 * sizeof(long long);
   b += size_t(r.nzt) * (r.nzt + 1) / 2 * sizeof(StItem);
-  b += sizeof(double) * size_t(2 * r.nl + r.nf + r.nk);
+  b += sizeof(double) * size_t(3 * r.nl + r.nf + r.nk);
   b += size_t(r.nrow) * (sizeof(int4) + 2 * sizeof(float4));        // rows, data, rotated data
   b += size_t(r.nz) * (sizeof(float4) + sizeof(int));               // depth tables
   b += size_t(r.fk) * r.nl * 8 * sizeof(float);                     // recursion coefficients
@@ -245,7 +245,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   long long n_dbl = 0, n_rows = 0, n_z = 0, n_coef = 0, n_g = 0, n_G = 0;
   size_t n_tile = 0;
   for (int i = 0; i < n; ++i) {
-    n_dbl += 2 * sh[i].nl + sh[i].nf + sh[i].nk;
+    n_dbl += 3 * sh[i].nl + sh[i].nf + sh[i].nk;
     n_rows += sh[i].nrow;
     n_z += sh[i].nz;
     n_coef += sh[i].fk * sh[i].nl * 8;
@@ -301,7 +301,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   char* P = static_cast<char*>(sl.pin_in);
   StSub* sub = reinterpret_cast<StSub*>(P + o_sub);
   long long* pre = reinterpret_cast<long long*>(P + o_pre);
-  long long *pre_z = pre, *pre_fk = pre + (n + 1), *pre_fkz = pre + 2 * (n + 1), *pre_tw = pre + 3 * (n + 1),
+  long long *pre_z = pre, *pre_fk = pre + (n + 1), *pre_eb = pre + 2 * (n + 1), *pre_tw = pre + 3 * (n + 1),
             *pre_rc = pre + 4 * (n + 1), *row_off = pre + 5 * (n + 1);
   int* subn = reinterpret_cast<int*>(P + o_subn);
   long long* goff = reinterpret_cast<long long*>(P + o_goff);
@@ -312,7 +312,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   float* data = reinterpret_cast<float*>(P + o_data);
   long long c_dbl = 0, c_rows = 0, c_z = 0, c_coef = 0, c_g = 0, c_G = 0;
   size_t c_tile = 0;
-  pre_z[0] = pre_fk[0] = pre_fkz[0] = pre_tw[0] = pre_rc[0] = row_off[0] = 0;
+  pre_z[0] = pre_fk[0] = pre_eb[0] = pre_tw[0] = pre_rc[0] = row_off[0] = 0;
   for (int i = 0; i < n; ++i) {
     const edt_sub1d& q = subs[i0 + i];
     const ReqShape& r = sh[i];
@@ -324,7 +324,8 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
     S.o_lay = c_dbl;
     std::memcpy(dbl + c_dbl, q.layer_top_m, sizeof(double) * r.nl);
     std::memcpy(dbl + c_dbl + r.nl, q.layer_vel_mps, sizeof(double) * r.nl);
-    c_dbl += 2 * r.nl;
+    for (int j = 0; j < r.nl; ++j) dbl[c_dbl + 2 * r.nl + j] = 1.0 / (q.layer_vel_mps[j] * q.layer_vel_mps[j]);
+    c_dbl += 3 * r.nl;
     S.o_freq = c_dbl;
     std::memcpy(dbl + c_dbl, q.freq_hz, sizeof(double) * r.nf);
     c_dbl += r.nf;
@@ -352,7 +353,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
     subn[i] = r.nz; goff[i] = S.o_G; voff[i] = S.o_v;
     pre_z[i + 1] = pre_z[i] + r.nz;
     pre_fk[i + 1] = pre_fk[i] + r.fk;
-    pre_fkz[i + 1] = pre_fkz[i] + r.fk * r.nz;
+    pre_eb[i + 1] = pre_eb[i] + (r.fk + 7) / 8;
     pre_tw[i + 1] = pre_tw[i] + (long long)r.kst * (4 * r.nzt + 1);
     pre_rc[i + 1] = pre_rc[i] + (r.nrow + ST_REFINE_ROWS - 1) / ST_REFINE_ROWS;
     row_off[i + 1] = row_off[i] + r.nrow;
@@ -393,7 +394,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   b.nreq = n; b.ncta = ncta;
   b.sub = reinterpret_cast<const StSub*>(A + o_sub);
   const long long* dpre = reinterpret_cast<const long long*>(A + o_pre);
-  b.pre_z = dpre; b.pre_fk = dpre + (n + 1); b.pre_fkz = dpre + 2 * (n + 1); b.pre_tw = dpre + 3 * (n + 1);
+  b.pre_z = dpre; b.pre_fk = dpre + (n + 1); b.pre_eb = dpre + 2 * (n + 1); b.pre_tw = dpre + 3 * (n + 1);
   b.pre_rc = dpre + 4 * (n + 1);
   b.row_off = const_cast<long long*>(dpre + 5 * (n + 1));
   b.items = reinterpret_cast<const StItem*>(A + o_items);
@@ -421,13 +422,13 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   b.sub_voff = reinterpret_cast<long long*>(A + o_voff);
   b.sub_order = reinterpret_cast<int*>(A + o_order);
   b.flags = reinterpret_cast<unsigned int*>(A + o_flags);
-  b.tot_z = pre_z[n]; b.tot_fk = pre_fk[n]; b.tot_fkz = pre_fkz[n]; b.tot_tw = pre_tw[n]; b.tot_rc = pre_rc[n];
+  b.tot_z = pre_z[n]; b.tot_fk = pre_fk[n]; b.tot_eb = pre_eb[n]; b.tot_tw = pre_tw[n]; b.tot_rc = pre_rc[n];
   b.cb_nstep = nstep;
   b.cb_act = reinterpret_cast<const int*>(A + o_cbact);
   b.cb_tpre = reinterpret_cast<const long long*>(A + o_cbpre);
   b.cb_nact_host = cb_nact.data();
   b.cb_ntile_host = cb_ntile.data();
-  int nlaunch = 1 + (b.tot_fk > 0) + (b.tot_fkz > 0) + (b.tot_tw > 0) + (ncta > 0) + 1 + (b.tot_rc > 0) + 1;
+  int nlaunch = 1 + (b.tot_fk > 0) + (b.tot_eb > 0) + (b.tot_tw > 0) + (ncta > 0) + 1 + (b.tot_rc > 0) + 1;
   for (int k = 0; k < nstep; ++k) nlaunch += (cb_nact[k] > 0) + (cb_ntile[k] > 0);
 
   cudaError_t ce = cudaSuccess;

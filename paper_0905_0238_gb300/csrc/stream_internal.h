@@ -24,7 +24,7 @@ struct StSub {
   int kst;                // K stages of 32 complex rows
   double dz, z0, eps, dx, alpha;
   float eps2, dzdx;       // eps^2 and dz / dx as FP32
-  long long o_lay;        // dbl: layer tops [nl], then velocities [nl]
+  long long o_lay;        // dbl: layer tops [nl], velocities [nl], 1 / velocity^2 [nl]
   long long o_freq;       // dbl: frequencies [nf] (Hz)
   long long o_kval;       // dbl: wavenumbers [nk] (rad/m)
   long long o_row;        // rows / data [nrow]
@@ -44,7 +44,7 @@ struct StBatch {
   const StSub* sub;              // [nreq]
   const long long* pre_z;        // [nreq + 1] prefix sums of nz
   const long long* pre_fk;       //            of nf * nk
-  const long long* pre_fkz;      //            of nf * nk * nz
+  const long long* pre_eb;       //            of ceil(nf * nk / 8)  (table-evaluation CTAs)
   const long long* pre_tw;       //            of kst * (4 nzt + 1)  (tile-writer warps)
   const long long* pre_rc;       //            of ceil(nrow / 256)   (refinement CTAs)
   const StItem* items;           // Gram items grouped by CTA
@@ -74,7 +74,7 @@ struct StBatch {
   int* sub_order;                // [nreq] requests by decreasing nz (Cholesky launch order)
   unsigned int* flags;           // [1] tensor-core wait expired
   // launch extents (host side)
-  long long tot_z, tot_fk, tot_fkz, tot_tw, tot_rc;
+  long long tot_z, tot_fk, tot_eb, tot_tw, tot_rc;
   // blocked Cholesky: per 32-column step k the active requests (device, [nstep][nreq]), their
   // prefix sums of update tiles (device, [nstep][nreq + 1]); counts on the host
   int cb_nstep;
