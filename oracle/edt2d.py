@@ -146,8 +146,53 @@ def damped_lstsq(Ahat, dhat, lam):
     return solve_triangular(R, Q.T @ rhs, lower=False)
 
 
-def solve_wavenumber(wl, D2, m, g=None, return_system=False):
-    """Vhat(k_m, z) for one midpoint wavenumber index 0 <= m <= N/2 (eqs. DMV, M, Split)."""
+def kz_basis(nz):
+    """Orthonormal real basis of depth vectors in order of vertical wavenumber index l:
+    the constant, (cos, sin)(2 pi l j / nz) for l = 1 .. ceil(nz/2) - 1, and (-1)^j for even nz.
+    Returns (P [nz][nz], l of every column); k_z = 2 pi l / (nz dz)."""
+    j = np.arange(nz)
+    cols, ls = [np.ones(nz) / np.sqrt(nz)], [0]
+    for l in range(1, (nz + 1) // 2):
+        cols.append(np.sqrt(2.0 / nz) * np.cos(2 * np.pi * l * j / nz))
+        ls.append(l)
+        cols.append(np.sqrt(2.0 / nz) * np.sin(2 * np.pi * l * j / nz))
+        ls.append(l)
+    if nz % 2 == 0:
+        cols.append(np.where(j % 2 == 0, 1.0, -1.0) / np.sqrt(nz))
+        ls.append(nz // 2)
+    return np.stack(cols, axis=1), np.array(ls)
+
+
+def kz_disk_keep(wl, m, factor):
+    """Columns of :func:`kz_basis` inside the disk |(k_m, k_z)| <= factor omega_max / c0 of
+    Section "Numerical Examples" (c0 = the slowest reference velocity, omega_max = 2 pi f_max)."""
+    K = factor * 2 * np.pi * float(np.max(wl.freq_hz)) / float(np.min(wl.layer_vel))
+    km = abs(lateral_wavenumbers(wl.nx, wl.dx)[m])
+    _, ls = kz_basis(wl.nz)
+    kz = 2 * np.pi * ls / (wl.nz * wl.dz)
+    return km ** 2 + kz ** 2 <= K ** 2
+
+
+def tsvd_lstsq(A, d, tol):
+    """Truncated-SVD solution of A x = d (Section "Numerical Examples"): x = V S~^-1 U^T d with
+    1/s_j kept for s_j >= sigma; sigma = tol if tol > 0, else |tol| times the largest s_j."""
+    U, sv, Vt = np.linalg.svd(A, full_matrices=False)
+    if sv.size == 0:
+        return np.zeros((A.shape[1], d.shape[1]))
+    sigma = tol if tol > 0 else abs(tol) * sv[0]
+    inv = np.where(sv >= sigma, 1.0 / np.where(sv > 0, sv, 1.0), 0.0)
+    return Vt.T @ (inv[:, None] * (U.T @ d))
+
+
+def solve_wavenumber(wl, D2, m, g=None, return_system=False, solver="damped", tsvd_tol=-1e-3,
+                     kz_disk=0.0):
+    """Vhat(k_m, z) for one midpoint wavenumber index 0 <= m <= N/2 (eqs. DMV, M, Split).
+
+    ``solver``: "damped" (zeroth-order Tikhonov, lam = alpha ||Ahat||_F^2) or "tsvd" (the
+    paper's truncated SVD with tolerance ``tsvd_tol``, see :func:`tsvd_lstsq`).  ``kz_disk`` > 0
+    restricts the unknowns to the vertical wavenumbers inside the disk of
+    :func:`kz_disk_keep` (x = P c over the kept columns P of :func:`kz_basis`; the damping
+    keeps lam of the unrestricted system)."""
     N = wl.nx
     if not 0 <= m <= N // 2:
         raise ValueError("m must lie in [0, N/2]")
@@ -165,7 +210,18 @@ def solve_wavenumber(wl, D2, m, g=None, return_system=False):
         cols.append(np.concatenate([dm.real, dm.imag]))
     dhat = np.stack(cols, axis=1)
     lam = wl.alpha * np.sum(Ahat ** 2)
-    x = damped_lstsq(Ahat, dhat, lam)
+    if kz_disk > 0:
+        P = kz_basis(nz)[0][:, kz_disk_keep(wl, m, kz_disk)]
+    else:
+        P = np.eye(nz)
+    if P.shape[1] == 0:
+        x = np.zeros((nz, dhat.shape[1]))
+    elif solver == "tsvd":
+        x = P @ tsvd_lstsq(Ahat @ P, dhat, tsvd_tol)
+    elif solver == "damped":
+        x = P @ damped_lstsq(Ahat @ P, dhat, lam)
+    else:
+        raise ValueError("solver must be 'damped' or 'tsvd'")
     vhat = x[:, 0] + (1j * x[:, 1] if not self_paired else 0.0)
     if return_system:
         return vhat, dict(Ahat=Ahat, dhat=dhat, lam=lam, x=x, rows=rows)
@@ -181,18 +237,19 @@ def hermitian_complete(vhat_half, N):
     return out
 
 
-def invert(wl, D, ms=None):
+def invert(wl, D, ms=None, **solve_kw):
     """The whole inversion: data D[f][is][ir] -> (V[x][z] real, Vhat[m][z] for 0 <= m <= N/2).
 
     With ``ms`` given, only those wavenumbers are solved (the others stay zero) and V is
-    not meaningful; used to time or check a subset.
+    not meaningful; used to time or check a subset.  ``solve_kw`` selects the solver variant
+    of :func:`solve_wavenumber` (truncated SVD, vertical-wavenumber disk).
     """
     N = wl.nx
     D2 = data_transform(D)
     g = green_table(wl)
     vh = np.zeros((N // 2 + 1, wl.nz), dtype=np.complex128)
     for m in (range(N // 2 + 1) if ms is None else ms):
-        vh[m] = solve_wavenumber(wl, D2, m, g)
+        vh[m] = solve_wavenumber(wl, D2, m, g, **solve_kw)
     V = inverse_lateral_dft(hermitian_complete(vh, N))
     return V.real, vh
 
