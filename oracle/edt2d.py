@@ -180,7 +180,7 @@ def tsvd_lstsq(A, d, tol):
     if sv.size == 0:
         return np.zeros((A.shape[1], d.shape[1]))
     sigma = tol if tol > 0 else abs(tol) * sv[0]
-    inv = np.where(sv >= sigma, 1.0 / np.where(sv > 0, sv, 1.0), 0.0)
+    inv = np.where((sv >= sigma) & (sv > 0), 1.0 / np.where(sv > 0, sv, 1.0), 0.0)
     return Vt.T @ (inv[:, None] * (U.T @ d))
 
 

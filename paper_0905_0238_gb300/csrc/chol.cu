@@ -39,43 +39,6 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
-// Cholesky of the kb x kb diagonal block in sD (lower, leading dimension LDP) by one warp, in
-// place, with 1 / L_jj in sInv: lane i holds row i in registers and each column's pivot and
-// entries travel by shuffles, so the updates of a row within a column are independent FMAs
-// (the same operations in the same order as the column-by-column update in shared memory).
-// rsqrt pivots: multiplications replace divisions.  A non-positive or non-finite pivot sets *fail.
-__device__ __forceinline__ void factor_block_warp(double* sD, double* sInv, int kb, int lane, int* fail) {
-  double r[NB];
-#pragma unroll
-  for (int l = 0; l < NB; ++l) r[l] = (lane < kb && l <= lane) ? sD[lane * LDP + l] : 0.0;
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    if (j < kb && ok) {
-      const double djj = __shfl_sync(0xffffffffu, r[j], j);
-      if (!(djj > 0.0) || !isfinite(djj)) {
-        ok = false;
-      } else {
-        const double inv = rsqrt(djj);
-        if (lane == j) r[j] = djj * inv;
-        else if (lane > j) r[j] *= inv;
-        if (lane == 0) sInv[j] = inv;
-#pragma unroll
-        for (int l = j + 1; l < NB; ++l) {
-          const double llj = __shfl_sync(0xffffffffu, r[j], l);
-          if (lane >= l) r[l] -= r[j] * llj;
-        }
-      }
-    }
-  }
-  if (!ok && lane == 0) *fail = 1;
-  if (lane < kb) {
-#pragma unroll
-    for (int l = 0; l < NB; ++l)
-      if (l <= lane) sD[lane * LDP + l] = r[l];
-  }
-}
-
 // Solve L L^T x = sb in place (two right-hand sides, sb[i][0..1]); L lower in A (ld n).
 __device__ void chol_solve_2rhs(const double* A, const double* dinv, int n, double* sb,
                                 double (*sL)[LDP]) {
@@ -102,14 +65,14 @@ __device__ void chol_solve_2rhs(const double* A, const double* dinv, int n, doub
     }
     __syncthreads();
     for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {   // b_i -= L[i][blk] . y
+      double s0 = sb[i * 2], s1 = sb[i * 2 + 1];
       const double* Ai = A + size_t(i) * n + k0;
-      double p0[2] = {sb[i * 2], 0.0}, p1[2] = {sb[i * 2 + 1], 0.0};   // two chains per side
       for (int l = 0; l < kb; ++l) {
         const double a = Ai[l];
-        p0[l & 1] -= a * sb[(k0 + l) * 2];
-        p1[l & 1] -= a * sb[(k0 + l) * 2 + 1];
+        s0 -= a * sb[(k0 + l) * 2];
+        s1 -= a * sb[(k0 + l) * 2 + 1];
       }
-      sb[i * 2] = p0[0] + p0[1]; sb[i * 2 + 1] = p1[0] + p1[1];
+      sb[i * 2] = s0; sb[i * 2 + 1] = s1;
     }
     __syncthreads();
   }
@@ -134,13 +97,13 @@ __device__ void chol_solve_2rhs(const double* A, const double* dinv, int n, doub
     }
     __syncthreads();
     for (int i = threadIdx.x; i < k0; i += blockDim.x) {   // y_i -= sum_l L[k0+l][i] x_l
-      double p0[2] = {sb[i * 2], 0.0}, p1[2] = {sb[i * 2 + 1], 0.0};
+      double s0 = sb[i * 2], s1 = sb[i * 2 + 1];
       for (int l = 0; l < kb; ++l) {
         const double a = A[size_t(k0 + l) * n + i];
-        p0[l & 1] -= a * sb[(k0 + l) * 2];
-        p1[l & 1] -= a * sb[(k0 + l) * 2 + 1];
+        s0 -= a * sb[(k0 + l) * 2];
+        s1 -= a * sb[(k0 + l) * 2 + 1];
       }
-      sb[i * 2] = p0[0] + p0[1]; sb[i * 2 + 1] = p1[0] + p1[1];
+      sb[i * 2] = s0; sb[i * 2 + 1] = s1;
     }
     __syncthreads();
   }
@@ -201,7 +164,22 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
       if (j <= i) sD[i * LDP + j] = A[size_t(k0 + i) * n + k0 + j];
     }
     __syncthreads();
-    if (warp == 0) factor_block_warp(sD, sInv, kb, lane, &fail);
+    if (warp == 0) {
+      for (int j = 0; j < kb; ++j) {
+        const double djj = sD[j * LDP + j];
+        if (!(djj > 0.0) || !isfinite(djj)) { if (lane == 0) fail = 1; break; }
+        const double inv = rsqrt(djj);          // 1 / L_jj; multiplications replace divisions
+        __syncwarp();
+        if (lane == j) { sD[j * LDP + j] = djj * inv; sInv[j] = inv; }
+        if (lane > j && lane < kb) sD[lane * LDP + j] *= inv;
+        __syncwarp();
+        if (lane > j && lane < kb) {
+          const double lij = sD[lane * LDP + j];
+          for (int l = j + 1; l <= lane; ++l) sD[lane * LDP + l] -= lij * sD[l * LDP + j];
+        }
+        __syncwarp();
+      }
+    }
     __syncthreads();
     if (fail) break;
     // the FP32 copy of the factor (refinement's correction solves) is written as each part
@@ -228,11 +206,10 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
         if (j < kb) {
-          // four independent partial sums: the FP64 latency chain is j / 4 long, not j
-          double p[4] = {x[j], 0.0, 0.0, 0.0};
+          double s = x[j];
 #pragma unroll
-          for (int l = 0; l < j; ++l) p[l & 3] -= x[l] * sD[j * LDP + l];
-          x[j] = ((p[0] + p[1]) + (p[2] + p[3])) * sInv[j];
+          for (int l = 0; l < j; ++l) s -= x[l] * sD[j * LDP + l];
+          x[j] = s * sInv[j];
         }
       }
 #pragma unroll
@@ -519,7 +496,22 @@ __global__ void __launch_bounds__(256) cb_panel_kernel(Dev d, int k0, const int*
     if (j <= i) sD[i * LDP + j] = A[size_t(k0 + i) * n + k0 + j];
   }
   __syncthreads();
-  if (warp == 0) factor_block_warp(sD, sInv, kb, lane, &fail);
+  if (warp == 0) {
+    for (int j = 0; j < kb; ++j) {
+      const double djj = sD[j * LDP + j];
+      if (!(djj > 0.0) || !isfinite(djj)) { if (lane == 0) fail = 1; break; }
+      const double inv = rsqrt(djj);
+      __syncwarp();
+      if (lane == j) { sD[j * LDP + j] = djj * inv; sInv[j] = inv; }
+      if (lane > j && lane < kb) sD[lane * LDP + j] *= inv;
+      __syncwarp();
+      if (lane > j && lane < kb) {
+        const double lij = sD[lane * LDP + j];
+        for (int l = j + 1; l <= lane; ++l) sD[lane * LDP + l] -= lij * sD[l * LDP + j];
+      }
+      __syncwarp();
+    }
+  }
   __syncthreads();
   if (fail) {
     if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
@@ -546,10 +538,10 @@ __global__ void __launch_bounds__(256) cb_panel_kernel(Dev d, int k0, const int*
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       if (j < kb) {
-        double p[4] = {x[j], 0.0, 0.0, 0.0};         // four independent partial sums
+        double sacc = x[j];
 #pragma unroll
-        for (int l = 0; l < j; ++l) p[l & 3] -= x[l] * sD[j * LDP + l];
-        x[j] = ((p[0] + p[1]) + (p[2] + p[3])) * sInv[j];
+        for (int l = 0; l < j; ++l) sacc -= x[l] * sD[j * LDP + l];
+        x[j] = sacc * sInv[j];
       }
     }
 #pragma unroll
