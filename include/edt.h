@@ -134,7 +134,22 @@ typedef struct {
   int wx, wy;                   /* window geometry: half-offsets per axis (powers of
                                    two, 1..16; wx <= nx, wy <= ny); the half-offset
                                    spacing equals the midpoint spacing                  */
+  /* Solver variants of Section "Numerical Examples" (line geometry, EDT_FP64 only; else
+   * EDT_EUNSUPPORTED):                                                                  */
+  int solver;                   /* EDT_SOLVE_DAMPED (0, default) or EDT_SOLVE_TSVD (1):
+                                   x = V S~^-1 U^T dhat, 1/s_j kept for s_j >= sigma, from
+                                   the eigenpairs of the FP64 normal matrix; nz <= 96    */
+  double tsvd_tol;              /* sigma: > 0 absolute, < 0 relative (|tol| * s_max),
+                                   0: every positive singular value                      */
+  double kz_disk;               /* > 0: restrict the unknowns of k_m to the vertical
+                                   wavenumbers k_z = 2 pi l / (nz dz) (orthonormal real
+                                   depth basis: constant, cos/sin of 2 pi l j / nz, and
+                                   (-1)^j) with k_m^2 + k_z^2 <= (kz_disk omega_max /
+                                   c_min)^2, c_min the slowest layer; 0: off             */
 } edt_config;
+
+#define EDT_SOLVE_DAMPED 0
+#define EDT_SOLVE_TSVD   1
 
 /* Host-side statistics of a context; the device-side fields are refreshed by
  * edt_get_stats, which synchronises the context's last stream. */

@@ -76,6 +76,11 @@ struct edt_ctx {
   std::vector<float2> tw32;
   // tensor-core Gram schedule
   std::vector<int> seg_m, cta_seg0, m_slot0;
+  // solver variants: kept vertical-wavenumber columns per subproblem and the depth basis
+  bool variant = false;
+  std::vector<int> kz_p;
+  std::vector<long long> kz_goff, kz_voff;
+  std::vector<double> kz_P;
   std::vector<long long> seg_row0, seg_nrow;
   int ncta_gram = 0, nslot = 0;
   // workspace
@@ -83,7 +88,8 @@ struct edt_ctx {
   void* ws = nullptr;
   Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_jact, r_jmap, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
-      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_gscr, r_adj, r_gacc, r_status, r_flags;
+      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_gscr, r_adj, r_gacc, r_status, r_flags,
+      r_kzP, r_kzp, r_kzgoff, r_kzvoff, r_kzG, r_kzT, r_kzb, r_kzx;
   Dev dev{};
   cudaStream_t last_stream = nullptr;
   int last_status = EDT_OK;
@@ -149,6 +155,12 @@ int validate(const edt_config* c) {
   if (c->chol_df != 0 && c->chol_df != 1) return EDT_EINVAL;
   if (c->freq_chunk < 0) return EDT_EINVAL;
   if (c->geometry != EDT_GEOM_LINE && c->geometry != EDT_GEOM_WINDOW) return EDT_EINVAL;
+  if (c->solver != EDT_SOLVE_DAMPED && c->solver != EDT_SOLVE_TSVD) return EDT_EINVAL;
+  if (!std::isfinite(c->tsvd_tol) || !(c->kz_disk >= 0) || !std::isfinite(c->kz_disk)) return EDT_EINVAL;
+  if (c->solver == EDT_SOLVE_TSVD || c->kz_disk > 0) {
+    if (c->precision != EDT_FP64 || c->geometry != EDT_GEOM_LINE) return EDT_EUNSUPPORTED;
+    if (c->solver == EDT_SOLVE_TSVD && c->nz > TSVD_MAX_NZ) return EDT_EUNSUPPORTED;
+  }
   if (c->geometry == EDT_GEOM_WINDOW) {
     if (c->ny < 1 || c->wx < 1 || c->wy < 1 || !(c->dy > 0)) return EDT_EINVAL;
     if (c->precision != EDT_MIXED) return EDT_EUNSUPPORTED;
@@ -291,6 +303,51 @@ void plan_band(edt_ctx* c, double cmin) {
     c->band_maxplanes = std::max(c->band_maxplanes, ch.f1 - ch.f0);
     c->bchunks.push_back(ch);
     f0 = ch.f1;
+  }
+}
+
+// Solver variants: the depth basis (columns in order of |k_z|: constant, then cos and sin of
+// 2 pi l j / nz for l = 1, 2, ..., then (-1)^j for even nz, each normalised) and, for the disk
+// |(k_m, k_z)| <= kz_disk omega_max / c_min, the number of leading columns kept per k_m.
+void plan_variant(edt_ctx* c) {
+  const edt_config& g = c->cfg;
+  c->variant = g.solver == EDT_SOLVE_TSVD || g.kz_disk > 0;
+  c->kz_p.clear(); c->kz_goff.clear(); c->kz_voff.clear(); c->kz_P.clear();
+  if (!(g.kz_disk > 0)) return;
+  const int nz = c->nz;
+  std::vector<int> lcol(nz);
+  c->kz_P.assign(size_t(nz) * nz, 0.0);
+  int col = 0;
+  for (int l = 0; l <= nz / 2; ++l) {
+    const bool pair = l > 0 && 2 * l < nz;
+    for (int part = 0; part < (pair ? 2 : 1); ++part) {
+      for (int j = 0; j < nz; ++j) {
+        double v;
+        if (l == 0) v = 1.0 / std::sqrt(double(nz));
+        else if (!pair) v = (j % 2 == 0 ? 1.0 : -1.0) / std::sqrt(double(nz));
+        else v = std::sqrt(2.0 / nz) * (part == 0 ? std::cos(2.0 * M_PI * l * j / nz) : std::sin(2.0 * M_PI * l * j / nz));
+        c->kz_P[size_t(j) * nz + col] = v;
+      }
+      lcol[col++] = l;
+    }
+  }
+  double fmax = 0.0, cmin = 1e300;
+  for (double f : c->freq) fmax = std::max(fmax, f);
+  for (double v : c->vel) cmin = std::min(cmin, v);
+  const double K = g.kz_disk * 2.0 * M_PI * fmax / cmin;
+  c->kz_p.resize(c->nsub);
+  c->kz_goff.resize(c->nsub);
+  c->kz_voff.resize(c->nsub);
+  for (int m = 0; m < c->nsub; ++m) {
+    const double km = 2.0 * M_PI * m / (c->N * g.dx);
+    int p = 0;
+    for (int k = 0; k < nz; ++k) {
+      const double kz = 2.0 * M_PI * lcol[k] / (nz * g.dz);
+      if (km * km + kz * kz <= K * K) p = k + 1; else break;
+    }
+    c->kz_p[m] = p;
+    c->kz_goff[m] = (long long)m * nz * nz;
+    c->kz_voff[m] = (long long)m * nz;
   }
 }
 
@@ -470,6 +527,7 @@ void plan(edt_ctx* c) {
     c->cta_seg0.insert(c->cta_seg0.end(), cta_slots.begin(), cta_slots.end());
     c->nslot = int(segs.size());
   }
+  plan_variant(c);
 }
 
 void layout(edt_ctx* c) {
@@ -549,6 +607,15 @@ void layout(edt_ctx* c) {
   take(c->r_gacc, grad ? size_t(1 + c->nlayer) * sizeof(double) : 0);
   take(c->r_status, ns * sizeof(int));
   take(c->r_flags, 8 * sizeof(unsigned));
+  const bool disk = !c->kz_p.empty();
+  take(c->r_kzP, disk ? size_t(nz) * nz * sizeof(double) : 0);
+  take(c->r_kzp, disk ? ns * sizeof(int) : 0);
+  take(c->r_kzgoff, disk ? ns * sizeof(long long) : 0);
+  take(c->r_kzvoff, disk ? ns * sizeof(long long) : 0);
+  take(c->r_kzG, disk ? ns * nz * nz * sizeof(double) : 0);
+  take(c->r_kzT, disk ? ns * nz * nz * sizeof(double) : 0);
+  take(c->r_kzb, disk ? ns * nz * 2 * sizeof(double) : 0);
+  take(c->r_kzx, disk ? ns * nz * 2 * sizeof(double) : 0);
   c->ws_bytes = align_up(off, 256);
 }
 
@@ -630,6 +697,17 @@ void bind(edt_ctx* c) {
   d.gbar = c->r_gscr.bytes ? reinterpret_cast<float2*>(d.g64) : nullptr;
   d.status = at<int*>(c, c->r_status);
   d.flags = at<unsigned*>(c, c->r_flags);
+  d.solver = c->cfg.solver;
+  d.tsvd_tol = c->cfg.tsvd_tol;
+  const bool disk = c->r_kzP.bytes > 0;
+  d.kz_P = disk ? at<const double*>(c, c->r_kzP) : nullptr;
+  d.kz_p = disk ? at<const int*>(c, c->r_kzp) : nullptr;
+  d.kz_goff = disk ? at<const long long*>(c, c->r_kzgoff) : nullptr;
+  d.kz_voff = disk ? at<const long long*>(c, c->r_kzvoff) : nullptr;
+  d.kz_G = disk ? at<double*>(c, c->r_kzG) : nullptr;
+  d.kz_T = disk ? at<double*>(c, c->r_kzT) : nullptr;
+  d.kz_b = disk ? at<double*>(c, c->r_kzb) : nullptr;
+  d.kz_x = disk ? at<double*>(c, c->r_kzx) : nullptr;
 }
 
 template <typename T>
@@ -720,7 +798,8 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   }
   prof_ev(c, 5, 1, s);
   prof_ev(c, 6, 0, s);
-  EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
+  if (c->variant) EDT_TRY(launch_solve_variant(d, s));
+  else EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
   prof_ev(c, 6, 1, s);
   prof_ev(c, 7, 0, s);
   if (mixed) {
@@ -813,6 +892,14 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
       EDT_TRY(launch_gent_static(c->dev, nullptr));
     }
   }
+  if (!c->kz_P.empty()) {
+    EDT_TRYI(upload(c, c->r_kzP, c->kz_P));
+    EDT_TRYI(upload(c, c->r_kzp, c->kz_p));
+    EDT_TRYI(upload(c, c->r_kzgoff, c->kz_goff));
+    EDT_TRYI(upload(c, c->r_kzvoff, c->kz_voff));
+    EDT_TRY(prepare_chol_var(c->nz));
+  }
+  if (c->variant) EDT_TRY(prepare_variants(c->nz));
   EDT_TRY(prepare_fft(c->dev));
   EDT_TRY(prepare_grad(c->dev));
   EDT_TRY(prepare_chol(c->dev));
@@ -1164,6 +1251,9 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   }
   o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + tr_launches +
                            chol_launches(c->nz);
+  // solver variants replace the Cholesky launch: trace, two projections, the solve (Cholesky
+  // or Jacobi), the back-projection with the disk; the Jacobi kernel alone without it
+  if (c->variant) o->launches_per_invert += (c->kz_p.empty() ? 1 : 5) - chol_launches(c->nz);
   if (c->win) {
     // green (3), rows (3) per frequency that keeps any, data (2), Gram (2), Cholesky,
     // refinement (2 per step), inverse (completion, FP64 row and column transforms, output: 3 or 4)

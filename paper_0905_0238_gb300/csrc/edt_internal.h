@@ -148,6 +148,17 @@ struct Dev {
   const long long* sub_goff;    // [nsub] element offset of its matrix in G and L32
   const long long* sub_voff;    // [nsub] element offset of its vectors (dinv; b, x, r x 2)
   const int* sub_order;         // [nsub] launch order of the factorisations (largest first), or null
+  // solver variants (FP64 line path): vertical-wavenumber basis and restricted systems
+  int solver;                   // EDT_SOLVE_DAMPED or EDT_SOLVE_TSVD
+  double tsvd_tol;
+  const double* kz_P;           // [nz][nz] orthonormal real depth basis, columns by |k_z|
+  const int* kz_p;              // [nsub] kept columns p(m) (null: no disk)
+  const long long* kz_goff;     // [nsub] m * nz * nz
+  const long long* kz_voff;     // [nsub] m * nz
+  double* kz_G;                 // [nsub][p][p] restricted normal matrices (stride nz * nz)
+  double* kz_T;                 // [nsub][nz][p] scratch G P_p
+  double* kz_b;                 // [nsub][nz][2] restricted right-hand sides
+  double* kz_x;                 // [nsub][nz][2] restricted solutions
 };
 
 // Record a CUDA error for edt_last_cuda_error; returns EDT_ECUDA.
@@ -228,6 +239,13 @@ cudaError_t launch_chol_blocked(const Dev& d, bool var, int nmax, int nstep, con
                                 const long long* ntile_host, int trace_mode, cudaStream_t s);
 int chol_blocked_tiles(int n, int k0);
 int chol_block_cols();
+
+// Solver variants (csrc/variants.cu): the truncated SVD (nz <= TSVD_MAX_NZ) and the
+// vertical-wavenumber disk, in place of the Cholesky stage of the FP64 line path.
+constexpr int TSVD_MAX_NZ = 96;
+size_t tsvd_smem_bytes(int p);
+cudaError_t prepare_variants(int nz);
+cudaError_t launch_solve_variant(const Dev& d, cudaStream_t s);
 
 // One-time kernel attribute setup (opt-in shared memory), done outside any stream capture.
 cudaError_t prepare_fft(const Dev& d);

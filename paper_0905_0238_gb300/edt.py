@@ -20,6 +20,7 @@ EDT_OK, EDT_EINVAL, EDT_ENOMEM_WS, EDT_ENOTPD = 0, -1, -2, -3
 EDT_ETIMEOUT, EDT_ENONFINITE, EDT_ECUDA, EDT_EUNSUPPORTED = -4, -5, -6, -7
 EDT_FP64, EDT_MIXED = 0, 1
 EDT_GEOM_LINE, EDT_GEOM_WINDOW = 0, 1
+EDT_SOLVE_DAMPED, EDT_SOLVE_TSVD = 0, 1
 EDT_C64, EDT_C128, EDT_F32, EDT_F64 = 0, 1, 2, 3
 
 
@@ -34,6 +35,7 @@ class edt_config(C.Structure):
         ("alpha", C.c_double), ("cutoff", C.c_double), ("fold", C.c_int),
         ("chol_df", C.c_int), ("freq_chunk", C.c_int),
         ("geometry", C.c_int), ("ny", C.c_int), ("dy", C.c_double), ("wx", C.c_int), ("wy", C.c_int),
+        ("solver", C.c_int), ("tsvd_tol", C.c_double), ("kz_disk", C.c_double),
     ]
 
 
@@ -309,6 +311,9 @@ class Config:
     dy: float = 1.0
     wx: int = 1
     wy: int = 1
+    solver: int = 0            # EDT_SOLVE_DAMPED or EDT_SOLVE_TSVD (FP64 line path)
+    tsvd_tol: float = 0.0      # truncated SVD: > 0 absolute sigma, < 0 relative to s_max
+    kz_disk: float = 0.0       # > 0: |(k_m, k_z)| <= kz_disk omega_max / c_min
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -352,7 +357,8 @@ class Solver:
             layer_vel_mps=self._vel.ctypes.data_as(dp), precision=cfg.precision,
             passes=cfg.passes, refine=cfg.refine, alpha=cfg.alpha, cutoff=cfg.cutoff,
             fold=cfg.fold, chol_df=cfg.chol_df, freq_chunk=cfg.freq_chunk,
-            geometry=cfg.geometry, ny=cfg.ny, dy=cfg.dy, wx=cfg.wx, wy=cfg.wy)
+            geometry=cfg.geometry, ny=cfg.ny, dy=cfg.dy, wx=cfg.wx, wy=cfg.wy,
+            solver=cfg.solver, tsvd_tol=cfg.tsvd_tol, kz_disk=cfg.kz_disk)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.ctx = None
         self.ctx, self.ws_bytes = edt_create(c)

@@ -126,3 +126,34 @@ def test_tuning_is_validated_and_kept_without_gpu():
             edt.edt_set_tuning(ctx, tb)
         assert ei.value.code == edt.EDT_EINVAL
     edt.edt_destroy(ctx)
+
+
+def test_solver_variant_validation_without_gpu():
+    """Truncated SVD and the vertical-wavenumber disk: FP64 line path only, TSVD up to 96
+    depths; invalid values are rejected before any device work."""
+    import numpy as np
+    from paper_0905_0238_gb300 import edt
+    freq = np.array([5.0, 10.0]); top = np.array([0.0, 100.0]); vel = np.array([1500.0, 2000.0])
+    dp = ctypes.POINTER(ctypes.c_double)
+
+    def code(**kw):
+        base = dict(nx=32, dx=10.0, nz=16, dz=10.0, z0=0.0, nfreq=2, freq_hz=freq.ctypes.data_as(dp),
+                    eps=0.15, nlayer=2, layer_top_m=top.ctypes.data_as(dp),
+                    layer_vel_mps=vel.ctypes.data_as(dp), precision=edt.EDT_FP64, passes=1,
+                    refine=1, alpha=1e-3, cutoff=1.0, fold=1)
+        base.update(kw)
+        ctx, ws = ctypes.c_void_p(), ctypes.c_size_t()
+        rc = edt._lib().edt_create(ctypes.byref(ctx), ctypes.byref(edt.edt_config(**base)), ctypes.byref(ws))
+        if ctx.value:
+            edt._lib().edt_destroy(ctx)
+        return rc, ws.value
+
+    assert code(solver=1, tsvd_tol=-1e-3)[0] == edt.EDT_OK
+    assert code(solver=1, nz=97)[0] == edt.EDT_EUNSUPPORTED
+    assert code(solver=1, precision=edt.EDT_MIXED, passes=3)[0] == edt.EDT_EUNSUPPORTED
+    assert code(kz_disk=2.2, precision=edt.EDT_MIXED, passes=3)[0] == edt.EDT_EUNSUPPORTED
+    assert code(kz_disk=-1.0)[0] == edt.EDT_EINVAL
+    assert code(solver=2)[0] == edt.EDT_EINVAL
+    rc0, ws0 = code()
+    rc1, ws1 = code(kz_disk=2.2)
+    assert rc0 == rc1 == edt.EDT_OK and ws1 > ws0
