@@ -321,6 +321,10 @@ int edt_green_noalloc(int nx, double dx, int nz, double dz, double z0, int nfreq
                       const double* freq_hz, double eps, int nlayer, const double* layer_top_m,
                       const double* layer_vel_mps, void* g_dev, void* stream);
 
+/* Vertical-wavenumber disk (kz_disk > 0): p[m] = the depth-basis columns kept for midpoint index
+ * m = 0..nx/2 (host only).  Returns nx/2 + 1, or EDT_EINVAL without the disk. */
+int edt_kz_disk_columns(const edt_ctx* ctx, int* p);
+
 /* Per-subproblem complex row counts after the cut (before folding): counts[nx/2+1]. */
 int edt_row_counts(const edt_ctx* ctx, long long* counts);
 

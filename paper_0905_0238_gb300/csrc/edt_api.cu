@@ -1228,6 +1228,12 @@ int edt_row_counts(const edt_ctx* c, long long* counts) {
   return EDT_OK;
 }
 
+int edt_kz_disk_columns(const edt_ctx* c, int* p) {
+  if (!c || !p || c->kz_p.empty()) return EDT_EINVAL;
+  for (int m = 0; m < c->nsub; ++m) p[m] = c->kz_p[m];
+  return c->nsub;
+}
+
 int edt_get_stats(edt_ctx* c, edt_stats* o) {
   if (!c || !o) return EDT_EINVAL;
   std::memset(o, 0, sizeof(*o));

@@ -135,6 +135,8 @@ def _lib() -> C.CDLL:
                      "edt_set_host_pipeline"):
             getattr(L, name).restype = i
         ll = C.c_longlong
+        L.edt_kz_disk_columns.argtypes = [vp, C.POINTER(i)]
+        L.edt_kz_disk_columns.restype = i
         L.edt_stream_request_bytes.argtypes = [C.POINTER(edt_sub1d)]
         L.edt_stream_request_bytes.restype = ll
         L.edt_stream_plan.argtypes = [i, C.POINTER(ll), ll, i, C.POINTER(i)]
@@ -218,6 +220,12 @@ def edt_row_counts(ctx, nsub: int) -> np.ndarray:
     out = (C.c_longlong * nsub)()
     _check(_lib().edt_row_counts(ctx, out), "edt_row_counts")
     return np.array(out[:], dtype=np.int64)
+
+
+def edt_kz_disk_columns(ctx, nsub: int) -> np.ndarray:
+    out = np.zeros(nsub, dtype=np.int32)
+    _check(_lib().edt_kz_disk_columns(ctx, out.ctypes.data_as(C.POINTER(C.c_int))), "edt_kz_disk_columns")
+    return out
 
 
 def edt_get_stats(ctx) -> edt_stats:

@@ -157,3 +157,31 @@ def test_solver_variant_validation_without_gpu():
     rc0, ws0 = code()
     rc1, ws1 = code(kz_disk=2.2)
     assert rc0 == rc1 == edt.EDT_OK and ws1 > ws0
+
+
+def test_disk_plan_matches_the_oracle_without_gpu():
+    """The host plan of the vertical-wavenumber disk keeps, for every midpoint index, the same
+    number of depth-basis columns as the oracle's disk (same basis order, same inequality)."""
+    import numpy as np
+    import synth
+    from oracle import edt2d
+    from paper_0905_0238_gb300 import edt
+    dp = ctypes.POINTER(ctypes.c_double)
+    for wl, factor in ((synth.preset("paper_2d"), 1.2), (synth.preset("small_2d"), 0.7)):
+        fr = np.ascontiguousarray(wl.freq_hz, dtype=np.float64)
+        top = np.ascontiguousarray(wl.layer_top, dtype=np.float64)
+        vel = np.ascontiguousarray(wl.layer_vel, dtype=np.float64)
+        cfg = edt.edt_config(nx=wl.nx, dx=wl.dx, nz=wl.nz, dz=wl.dz, z0=wl.z0, nfreq=len(fr),
+                             freq_hz=fr.ctypes.data_as(dp), eps=wl.eps, nlayer=len(top),
+                             layer_top_m=top.ctypes.data_as(dp), layer_vel_mps=vel.ctypes.data_as(dp),
+                             precision=edt.EDT_FP64, passes=1, refine=0, alpha=wl.alpha,
+                             cutoff=wl.cutoff, fold=1, kz_disk=factor)
+        ctx, ws = ctypes.c_void_p(), ctypes.c_size_t()
+        assert edt._lib().edt_create(ctypes.byref(ctx), ctypes.byref(cfg), ctypes.byref(ws)) == edt.EDT_OK
+        try:
+            got = edt.edt_kz_disk_columns(ctx, wl.nx // 2 + 1)
+        finally:
+            edt._lib().edt_destroy(ctx)
+        want = [int(edt2d.kz_disk_keep(wl, m, factor).sum()) for m in range(wl.nx // 2 + 1)]
+        assert list(got) == want
+        assert min(want) < wl.nz          # the disk removes columns on these shapes
