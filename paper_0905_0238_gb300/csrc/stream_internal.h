@@ -85,11 +85,11 @@ struct StBatch {
 };
 
 constexpr int ST_NKERNEL = 8;
-extern const char* const kStreamKernels[ST_NKERNEL];   // names of the eight launches
+extern const char* const kStreamKernels[ST_NKERNEL];   // names of the eight stages
 
 int st_gram_smem_bytes();
 cudaError_t prepare_stream();
-// The eight launches of one batch on stream s (nmax: largest nz of the batch); with ev
+// The eight stages of one batch on stream s (nmax: largest nz of the batch); with ev
 // non-null, ev[0..8] are recorded before the first, between consecutive and after the last.
 cudaError_t launch_stream_batch(const StBatch& b, int nmax, cudaStream_t s, cudaEvent_t* ev);
 
