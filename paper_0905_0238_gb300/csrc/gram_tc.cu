@@ -167,7 +167,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     // ------------------------------------------------------------ producers + epilogue
     const int ptid = threadIdx.x;                 // 0..255
     const int nunits = (nzp / 32) * 8;            // (32-depth group, 16-byte K chunk)
-    const int N = d.N, msk = N - 1;
     const float2* g32 = d.rowtab32;
     const size_t nzs = size_t(d.nzs);
     long long it = 0;
