@@ -74,3 +74,21 @@ def test_admission_plan_edge_cases():
     with pytest.raises(edt.EdtError) as e:
         edt.edt_stream_plan([10], 1 << 30, 0)
     assert e.value.code == edt.EDT_EINVAL
+
+
+def test_request_marshalling_round_trips():
+    """The ctypes view of a request carries every field and array of the Python request."""
+    import ctypes
+    subs = stream.stream_requests(3, salt=23)
+    arr, keep = edt._sub1d_array(subs)
+    for s, e in zip(subs, arr):
+        assert (e.nz, e.nlayer, e.nfreq, e.nk, e.nrow) == (s.nz, len(s.layer_top), len(s.freq_hz), len(s.kval), s.nrow)
+        assert (e.dz, e.z0, e.eps, e.alpha, e.dx) == (s.dz, s.z0, s.eps, s.alpha, s.dx)
+        np.testing.assert_array_equal(np.ctypeslib.as_array(e.layer_top_m, (e.nlayer,)), s.layer_top)
+        np.testing.assert_array_equal(np.ctypeslib.as_array(e.layer_vel_mps, (e.nlayer,)), s.layer_vel)
+        np.testing.assert_array_equal(np.ctypeslib.as_array(e.freq_hz, (e.nfreq,)), s.freq_hz)
+        np.testing.assert_array_equal(np.ctypeslib.as_array(e.kval, (e.nk,)), s.kval)
+        np.testing.assert_array_equal(np.ctypeslib.as_array(e.rows, (e.nrow, 3)), s.rows)
+        d = np.ctypeslib.as_array(e.data, (e.nrow, 4))
+        np.testing.assert_array_equal(d[:, 0] + 1j * d[:, 1], s.data[:, 0])
+        np.testing.assert_array_equal(d[:, 2] + 1j * d[:, 3], s.data[:, 1])
