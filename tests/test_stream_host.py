@@ -78,7 +78,6 @@ def test_admission_plan_edge_cases():
 
 def test_request_marshalling_round_trips():
     """The ctypes view of a request carries every field and array of the Python request."""
-    import ctypes
     subs = stream.stream_requests(3, salt=23)
     arr, keep = edt._sub1d_array(subs)
     for s, e in zip(subs, arr):
