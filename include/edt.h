@@ -311,12 +311,16 @@ int edt_gram(edt_ctx* ctx, const void* D_dev, int D_dtype, void* G_dev, void* b_
  * keeps until the process exits.  Frequencies are processed in chunks that fit it.
  * Limits: nx a power of two >= 2; one frequency's coefficients, (nx/2+1) * nlayer * 112
  * bytes, must fit in the 8 MiB (else EDT_EUNSUPPORTED).  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  Every call reuses the same array, so calls
- * whose work overlaps on the GPU (other streams, other host threads) race on it; each
- * call fully writes the scratch it reads, so nothing carries over between calls.
- * Host arrays may be freed when the call returns; the computation is asynchronous on
- * `stream`.  Returns EDT_OK, EDT_EINVAL, EDT_EUNSUPPORTED or EDT_ECUDA. */
+ * up the array's device address (cudaGetSymbolAddress) with that device current and keeps
+ * it for the life of the process: the call is not valid on a device after a
+ * cudaDeviceReset of it.  The call copies its host arrays through pageable memory, so it
+ * must never run while `stream` is being captured into a CUDA graph (nor, on the legacy
+ * stream, while any thread captures in global mode): it checks and returns EDT_EINVAL
+ * then.  Every call reuses the same array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it; each call fully writes the scratch it reads,
+ * so nothing carries over between calls.  Host arrays may be freed when the call returns;
+ * the computation is asynchronous on `stream`.  Returns EDT_OK, EDT_EINVAL,
+ * EDT_EUNSUPPORTED or EDT_ECUDA. */
 int edt_green_noalloc(int nx, double dx, int nz, double dz, double z0, int nfreq,
                       const double* freq_hz, double eps, int nlayer, const double* layer_top_m,
                       const double* layer_vel_mps, void* g_dev, void* stream);

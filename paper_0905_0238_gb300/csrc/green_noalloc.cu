@@ -33,7 +33,8 @@ std::mutex g_addr_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device (host code only knows a
-// host-side stand-in for the symbol).  Looked up once per device.
+// host-side stand-in for the symbol).  Looked up once per device and kept for the life of
+// the process, so it does not survive a cudaDeviceReset of that device.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -90,11 +91,23 @@ extern "C" int edt_green_noalloc(int nx, double dx, int nz, double dz, double z0
     --chunk;
   const size_t o_coef = up256(o_fc + sizeof(FreqConst) * chunk);
 
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The call stages host arrays that die when it returns (pageable copies), so it must
+  // never be recorded into a graph: refuse it while its stream (or, for the legacy
+  // stream, any global-mode capture) is capturing.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+  if (ce == cudaErrorStreamCaptureImplicit) {
+    (void)cudaGetLastError();
+    return EDT_EINVAL;
+  }
+  if (ce != cudaSuccess) return record_cuda_error(ce);
+  if (cs != cudaStreamCaptureStatusNone) return EDT_EINVAL;
+
   void* base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return EDT_ECUDA;
   char* sb = static_cast<char*>(base);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   std::vector<int> zl(nz);
   std::vector<double> zo(nz);

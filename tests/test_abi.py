@@ -185,3 +185,21 @@ def test_disk_plan_matches_the_oracle_without_gpu():
         want = [int(edt2d.kz_disk_keep(wl, m, factor).sum()) for m in range(wl.nx // 2 + 1)]
         assert list(got) == want
         assert min(want) < wl.nz          # the disk removes columns on these shapes
+
+
+def test_green_noalloc_rejects_oversized_coefficients_without_gpu():
+    """One frequency's recursion coefficients ((nx/2+1) * nlayer * 112 bytes) must fit the
+    allocation-free call's 8 MiB scratch: nx = 2048 with 74 layers needs 8.5 MB and is refused
+    on the host, before any device call (nothing is launched)."""
+    import numpy as np
+    from paper_0905_0238_gb300 import edt
+    tops = np.arange(74) * 20.0
+    vel = np.linspace(1500.0, 3600.0, 74)
+    assert 1025 * 74 * 112 > (8 << 20)
+    with pytest.raises(edt.EdtError) as ei:
+        edt.edt_green_noalloc(2048, 12.5, 16, 50.0, 0.0, np.array([10.0]), 0.15, tops, vel,
+                              0x1000, 0)
+    assert ei.value.code == edt.EDT_EUNSUPPORTED
+    with pytest.raises(edt.EdtError) as ei:
+        edt.edt_green_noalloc(48, 12.5, 16, 50.0, 0.0, np.array([10.0]), 0.15, tops, vel, 0x1000, 0)
+    assert ei.value.code == edt.EDT_EINVAL
