@@ -85,8 +85,10 @@ extern "C" {
 
 /* ---- enumerations ---------------------------------------------------------------- */
 #define EDT_FP64   0   /* every stage in IEEE double                                          */
-#define EDT_MIXED  1   /* FP32 transforms, BF16 tensor-core Gram with FP32 accumulation,
-                          FP64 Cholesky and FP64-accumulated iterative refinement          */
+#define EDT_MIXED  1   /* FP32 transforms, tensor-core Gram from 16-bit hi/lo operand pairs
+                          (FP16 with power-of-two scales on the line geometry, BF16 on the
+                          window geometry) with FP32 accumulation, FP64 Cholesky and
+                          iterative refinement with an FP64-summed residual               */
 
 #define EDT_GEOM_LINE    0   /* 2D line, every source/receiver pair recorded (default)  */
 #define EDT_GEOM_WINDOW  1   /* finite half-offset window on an nx x ny midpoint grid   */
@@ -114,7 +116,7 @@ typedef struct {
   const double* layer_vel_mps;  /* [nlayer], > 0; the last layer is a half-space         */
   int precision;                /* EDT_FP64 or EDT_MIXED                                 */
   int passes;                   /* mixed: 1 = BF16 Gram, 3 = split BF16x3 Gram           */
-  int refine;                   /* mixed: refinement steps (0..4, default 1)             */
+  int refine;                   /* mixed: refinement steps (0..8, default 1)             */
   double alpha;                 /* damping: lam = alpha * trace(Gram) (>= 0)             */
   double cutoff;                /* evanescent cut factor; <= 0 keeps every row           */
   int fold;                     /* 1: merge the identical reciprocal rows (p,q),(-q,-p)
@@ -146,6 +148,19 @@ typedef struct {
                                    depth basis: constant, cos/sin of 2 pi l j / nz, and
                                    (-1)^j) with k_m^2 + k_z^2 <= (kz_disk omega_max /
                                    c_min)^2, c_min the slowest layer; 0: off             */
+  int gram_seg_rows;            /* mixed path: most complex rows one FP32 tensor-memory
+                                   accumulation of the Gram covers before it is flushed
+                                   to a partial tile that is summed in FP64 (rounded up
+                                   to a multiple of 32; shorter runs lose less to FP32
+                                   accumulation); 0 = automatic                          */
+  int resid;                    /* mixed: arithmetic of the refinement residual
+                                   r = Ahat^T (dhat - Ahat x): 1 = FP32 rows and products,
+                                   FP64 sums across warps and blocks; 2 = FP64-accurate:
+                                   rows from a double-float table (FP32 hi + lo of the
+                                   FP64 depth march), the accumulation Ahat^T u by exact
+                                   products and compensated sums (line geometry only);
+                                   0 = automatic: 2 on the line geometry when
+                                   alpha < 1e-3, else 1                                 */
 } edt_config;
 
 #define EDT_SOLVE_DAMPED 0

@@ -30,6 +30,18 @@ struct Region { size_t off = 0, bytes = 0; };
 
 int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
 
+// Most complex rows one FP32 tensor-memory accumulation of the Gram covers (a segment);
+// longer runs are split into several segments, each flushed to its own partial tile.
+// Damping below which the automatic residual mode switches to double-float: with FP32
+// products the residual's rounding reaches x amplified by up to 1 / lam, which at alpha
+// ~1e-5 approaches the 1e-5 parity bar.
+constexpr double kResidDfAlpha = 1e-3;
+
+static long long gram_seg_cap(const edt_config& g) {
+  if (g.gram_seg_rows > 0) return (long long)(g.gram_seg_rows + TC_KC - 1) / TC_KC * TC_KC;
+  return 1LL << 40;
+}
+
 }  // namespace edt
 
 using namespace edt;
@@ -61,6 +73,7 @@ struct edt_ctx {
   // band-limited transform of the mixed path
   bool band_mode = false;
   bool have_factor = false;            // the workspace holds the factors of the last edt_invert
+  bool resid_df = false;               // double-float refinement residual (line geometry, mixed)
   std::vector<BandInfo> band;
   std::vector<int2> bcol;
   std::vector<long long> cpre;
@@ -87,7 +100,7 @@ struct edt_ctx {
   size_t ws_bytes = 0;
   void* ws = nullptr;
   Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_jact, r_jmap, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
-      r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
+      r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_g32lo, r_rowmax, r_gscale, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
       r_dinv, r_L32, r_dinv32, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_gscr, r_adj, r_gacc, r_status, r_flags,
       r_kzP, r_kzp, r_kzgoff, r_kzvoff, r_kzG, r_kzT, r_kzb, r_kzx;
   Dev dev{};
@@ -123,7 +136,7 @@ namespace {
 
 constexpr int kProfCalls = 256;   // calls whose stage events are kept between reads
 
-const char* kStageNames[edt_ctx::NSTAGE] = {"green", "kernel_rows", "transform_rhs", "trace_reset",
+const char* kStageNames[edt_ctx::NSTAGE] = {"green", "kernel_rows", "transform_rhs", "gram_prep",
                                             "gram", "gram_reduce", "cholesky", "refine",
                                             "inverse"};
 
@@ -144,7 +157,7 @@ int validate(const edt_config* c) {
   if (c->precision != EDT_FP64 && c->precision != EDT_MIXED) return EDT_EINVAL;
   if (c->precision == EDT_MIXED) {
     if (c->passes != 1 && c->passes != 3) return EDT_EINVAL;
-    if (c->refine < 0 || c->refine > 4) return EDT_EINVAL;
+    if (c->refine < 0 || c->refine > 8) return EDT_EINVAL;
     if (c->nz > 256) return EDT_EUNSUPPORTED;
     // the tensor-core producer addresses the FP32 table with 32-bit element offsets
     if (double(c->nfreq) * (c->nx / 2 + 1) * c->nz >= 4294967295.0) return EDT_EUNSUPPORTED;
@@ -153,7 +166,9 @@ int validate(const edt_config* c) {
   if (!std::isfinite(c->cutoff)) return EDT_EINVAL;
   if (c->fold != 0 && c->fold != 1) return EDT_EINVAL;
   if (c->chol_df != 0 && c->chol_df != 1) return EDT_EINVAL;
-  if (c->freq_chunk < 0) return EDT_EINVAL;
+  if (c->freq_chunk < 0 || c->gram_seg_rows < 0) return EDT_EINVAL;
+  if (c->resid < 0 || c->resid > 2) return EDT_EINVAL;
+  if (c->resid == 2 && (c->geometry == EDT_GEOM_WINDOW || c->precision != EDT_MIXED)) return EDT_EUNSUPPORTED;
   if (c->geometry != EDT_GEOM_LINE && c->geometry != EDT_GEOM_WINDOW) return EDT_EINVAL;
   if (c->solver != EDT_SOLVE_DAMPED && c->solver != EDT_SOLVE_TSVD) return EDT_EINVAL;
   if (!std::isfinite(c->tsvd_tol) || !(c->kz_disk >= 0) || !std::isfinite(c->kz_disk)) return EDT_EINVAL;
@@ -491,12 +506,13 @@ void plan(edt_ctx* c) {
     std::vector<std::vector<int>> cta_segs(ncta);
     struct Seg { int m, cta; long long r0, n; };
     std::vector<Seg> segs;
+    const long long cap = gram_seg_cap(g);
     for (int k = 0; k < ncta; ++k) {
       long long a = total * k / ncta, b = total * (k + 1) / ncta;
       long long r = a;
       while (r < b) {
         int m = int(std::upper_bound(c->row_off.begin(), c->row_off.end(), r) - c->row_off.begin()) - 1;
-        long long e = std::min(b, c->row_off[m + 1]);
+        long long e = std::min(std::min(b, c->row_off[m + 1]), r + cap);
         segs.push_back({m, k, r, e - r});
         r = e;
       }
@@ -576,6 +592,9 @@ void layout(edt_ctx* c) {
   take(c->r_coef32, mixed ? nf * nk * c->nlayer * 8 * sizeof(float) : 0);
   take(c->r_g64, nf * nk * nz * sizeof(double2));
   take(c->r_g32, mixed ? nf * nk * size_t((c->nz + 1) & ~1) * sizeof(float2) : 0);
+  take(c->r_g32lo, c->resid_df ? nf * nk * size_t((c->nz + 1) & ~1) * sizeof(float2) : 0);
+  take(c->r_rowmax, mixed && !c->win ? nf * nk * sizeof(float) : 0);
+  take(c->r_gscale, mixed && !c->win ? std::max<size_t>(c->nslot, 1) * sizeof(int2) : 0);
   // full planes of the forward model (and of the FP64 transform), or the band spectra of
   // one chunk (Y, then Xc at a 256-byte boundary); one call uses one of the two
   take(c->r_X, std::max(size_t(c->fchunk) * N * N * (mixed ? sizeof(float2) : sizeof(double2)),
@@ -674,6 +693,11 @@ void bind(edt_ctx* c) {
   d.fc32_sqrt_s = at<const float*>(c, c->r_fc32);
   d.g64 = at<double2*>(c, c->r_g64);
   d.g32 = c->r_g32.bytes ? at<float2*>(c, c->r_g32) : nullptr;
+  d.g32lo = c->r_g32lo.bytes ? at<float2*>(c, c->r_g32lo) : nullptr;
+  d.rowmax = c->r_rowmax.bytes ? at<float*>(c, c->r_rowmax) : nullptr;
+  d.gscale = c->r_gscale.bytes ? at<int2*>(c, c->r_gscale) : nullptr;
+  d.f16 = d.gscale != nullptr;
+  d.resid_df = c->resid_df ? 1 : 0;
   d.rowtab32 = c->win ? d.A32 : d.g32;
   d.X = at<void*>(c, c->r_X);
   d.Dstage = at<void*>(c, c->r_Dst);
@@ -727,6 +751,15 @@ void prof_ev(edt_ctx* c, int stage, int end, cudaStream_t s) {
   c->prof_used[stage] = 1;
 }
 
+// Tables the depth march writes for an inversion: FP64 (FP64 path); the FP32 table by the
+// fast FP32 evaluation (mixed path with the FP32 residual, ~1e-7 relative); the FP32 table
+// rounded from the FP64 evaluation with its remainder, the double-float pair the FP64-accurate
+// residual reads (mixed line path, resid 2).
+int green_tables(const edt_ctx* c) {
+  if (c->cfg.precision != EDT_MIXED) return GREEN_G64;
+  return c->resid_df ? GREEN_G32DF : GREEN_G32;
+}
+
 // Data transform and right-hand-side gather, chunk by chunk of frequency planes.
 int transform_rhs(edt_ctx* c, const void* D, int D_dtype, cudaStream_t s) {
   const Dev& d = c->dev;
@@ -772,7 +805,7 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
     EDT_TRY(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
   }
   prof_ev(c, 0, 0, sg);
-  EDT_TRY(launch_green(d, sg, mixed ? GREEN_G32 : GREEN_G64));
+  EDT_TRY(launch_green(d, sg, green_tables(c)));
   prof_ev(c, 0, 1, sg);
   prof_ev(c, 1, 0, sg);
   EDT_TRYI(kernel_rows(c, sg));
@@ -783,7 +816,10 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_ev(c, 2, 1, s);
   if (ov) EDT_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   prof_ev(c, 3, 0, s);
-  if (mixed) EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
+  if (mixed) {
+    EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
+    EDT_TRY(launch_gram_scale(d, s));
+  }
   prof_ev(c, 3, 1, s);
   prof_ev(c, 4, 0, s);
   if (mixed) {
@@ -837,6 +873,11 @@ int edt_create(edt_ctx** out, const edt_config* cfg, size_t* workspace_bytes) {
   c->cfg.layer_top_m = c->tops.data();
   c->cfg.layer_vel_mps = c->vel.data();
   if (c->cfg.precision == EDT_FP64) { c->cfg.passes = 0; c->cfg.refine = 0; }
+  // refinement residual: double-float on the line geometry when asked, or automatically
+  // when the damping is weak enough for FP32 rounding in the residual to show
+  c->win = c->cfg.geometry == EDT_GEOM_WINDOW;
+  c->resid_df = c->cfg.precision == EDT_MIXED && !c->win && c->cfg.refine > 0 &&
+                (c->cfg.resid == 2 || (c->cfg.resid == 0 && c->cfg.alpha < kResidDfAlpha));
   plan(c);
   layout(c);
   if (workspace_bytes) *workspace_bytes = c->ws_bytes;
@@ -882,6 +923,7 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRY(cudaMemset(at<void*>(c, c->r_flags), 0, c->r_flags.bytes));
   EDT_TRY(cudaMemset(at<void*>(c, c->r_x), 0, c->r_x.bytes));
   if (c->r_g32.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_g32), 0, c->r_g32.bytes));
+  if (c->r_g32lo.bytes) EDT_TRY(cudaMemset(at<void*>(c, c->r_g32lo), 0, c->r_g32lo.bytes));
   if (c->r_gent.bytes) {
     EDT_TRY(cudaMemset(at<void*>(c, c->r_gent), 0, c->r_gent.bytes));
     EDT_TRY(cudaMemset(at<void*>(c, c->r_rhs), 0, c->r_rhs.bytes));
@@ -1205,11 +1247,12 @@ int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr,
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
   c->last_stream = s;
-  EDT_TRY(launch_green(d, s, mixed ? GREEN_G32 : GREEN_G64));
+  EDT_TRY(launch_green(d, s, green_tables(c)));
   EDT_TRYI(kernel_rows(c, s));
   EDT_TRYI(transform_rhs(c, D, D_dtype, s));
   if (mixed) {
     EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
+    EDT_TRY(launch_gram_scale(d, s));
     EDT_TRY(launch_gram_tc(d, s));
     EDT_TRY(launch_gram_reduce(d, s));
   } else {
@@ -1256,7 +1299,7 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
     for (const BandChunk& ch : c->bchunks) tr_launches += 1 + (ch.nbcol > 0) + (ch.nrow > 0);
   }
   o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + tr_launches +
-                           chol_launches(c->nz);
+                           chol_launches(c->nz) + gram_scale_launches(c->dev);
   // solver variants replace the Cholesky launch: trace, two projections, the solve (Cholesky
   // or Jacobi), the back-projection with the disk; the Jacobi kernel alone without it
   if (c->variant) o->launches_per_invert += (c->kz_p.empty() ? 1 : 5) - chol_launches(c->nz);

@@ -119,6 +119,16 @@ struct Dev {
   float* coef32;                // [nf][nk][nlayer][8] FP32 copies for the fast evaluation
   double2* g64;                 // [nf][nk][nz]
   float2* g32;                  // [nf][nk][nzs] sqrt|s_f| g, mixed path (padding zero)
+  float2* g32lo;                // [nf][nk][nzs] its FP32 remainder: g32 + g32lo carries the
+                                //   FP64 table to ~1e-14 (line geometry, mixed path)
+  float* rowmax;                // [nf * nk] max over depth of |g32| per table row
+  int2* gscale;                 // [nseg] tensor-core Gram: exponents k of the power-of-two
+                                //   scales 2^k of each segment's kernel rows and data rows
+                                //   (FP16 operands)
+  int f16;                      // tensor-core Gram operands: 1 = FP16 with per-segment
+                                //   scales (line geometry), 0 = BF16 (window geometry)
+  int resid_df;                 // refinement residual: 1 = double-float accumulation from
+                                //   the double-float table, 0 = FP32 products
   void* X;                      // [fchunk][N][N] complex, path precision (one chunk of planes)
   void* Dstage;                 // host-call staging of D (complex128-sized)
   void* Vstage;                 // host-call staging of V (double-sized)
@@ -165,8 +175,9 @@ struct Dev {
 int record_cuda_error(cudaError_t e);
 
 // ---- launchers (each returns cudaGetLastError()) ---------------------------------------
-constexpr int GREEN_G64 = 1, GREEN_G32 = 2;   // tables launch_green writes
-// GREEN_G32 alone: the fast FP32 evaluation for the mixed path (no FP64 table)
+constexpr int GREEN_G64 = 1, GREEN_G32 = 2, GREEN_G32DF = 4;   // tables launch_green writes
+// GREEN_G32 alone: the fast FP32 evaluation for the mixed path (no FP64 table);
+// GREEN_G32DF: the FP64 evaluation written as the double-float pair g32 + g32lo (no g64)
 cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables);
 
 // Data transform of frequency planes [f0, f0 + nfc) into X, then the split right-hand
@@ -195,6 +206,8 @@ cudaError_t fft2_f64(const Dev& d, double2* X, int planes, int ny, int sign, dou
 
 cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace
+int gram_scale_launches(const Dev& d);                          // FP16 operand scales: 0 or 2 kernels
+cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s);    // per-segment FP16 operand scales
 cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s);   // partials -> G, b (FP64)
 cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s);   // trace[m] = sum_z G[m][z][z]
 int chol_launches(int nz);                                      // kernels of launch_chol_solve

@@ -13,9 +13,17 @@
 //     in TMEM and written out as an FP32 partial tile, summed per subproblem afterwards;
 //   * warps 0-15 are producers: for 32 complex rows per pipeline stage they rebuild the
 //     kernel rows a(z) = |s_f| g(k_p, z) g(k_q, z) from the L2-resident FP32 table of
-//     sqrt|s_f| g, scale weight-2 rows by sqrt 2, split into BF16 hi (and lo), and store
-//     them K-major with the 128-byte swizzle; (Re a, Im a) of one complex row are two
+//     sqrt|s_f| g, scale weight-2 rows by sqrt 2, split into hi (and lo) 16-bit halves, and
+//     store them K-major with the 128-byte swizzle; (Re a, Im a) of one complex row are two
 //     adjacent K elements.  The data rows d_+, d_- occupy two extra operand rows;
+//   * operand type: FP16 (line geometry) or BF16 (window geometry).  FP16's 11-bit
+//     significand makes the hi + lo pair a 22-bit row (BF16: 16 bits), at the same MMA rate,
+//     but its range is narrow, so each segment's kernel rows and data rows are multiplied
+//     by powers of two (chosen by gram_scale_kernel from per-row maxima of the table) that
+//     put the segment's largest value just under 2^14; the reduction divides them out
+//     exactly.  The Gram's representation error sets the contraction rate of the iterative
+//     refinement (it is amplified by 1 / lam in the null space of Ahat), so the FP16 pair
+//     lets one refinement step reach 1e-5 at damping two orders of magnitude weaker;
 //   * warp 16 issues tcgen05.mma (M = 128, K = 16) from one thread: both operands are
 //     views of the same stage tile (A = depth rows of one 128-row half, B = all depth rows
 //     plus the data rows), so one generated tile feeds the whole upper block row;
@@ -26,6 +34,7 @@
 #include "edt_internal.h"
 #include "cplx.cuh"
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include "tc_ptx.cuh"
 
 namespace edt {
@@ -52,7 +61,46 @@ constexpr int TAB_BYTES = TC_KC * int(sizeof(GramRow) + sizeof(float4));
 using namespace tcx;
 
 
-template <int PASSES>
+// Exponent k of the scale 2^k for a positive bound v in [2^(e-1), 2^e): k = 14 - e puts the
+// scaled bound in [2^13, 2^14); clamped so that 2^k stays a normal float.
+__device__ __forceinline__ int pow2_exp(float v) {
+  if (!(v > 0.f) || !isfinite(v)) return 0;
+  int e;
+  frexpf(v, &e);
+  return max(-120, min(120, 14 - e));
+}
+
+// 2^k as a double, exactly (|k| <= 1000)
+__device__ __forceinline__ double pow2d(int k) {
+  return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
+// (lo_k, hi_k) as two 16-bit values in one word, .x at the lower address (smaller K)
+template <bool F16>
+__device__ __forceinline__ uint32_t pack16(float lo_k, float hi_k) {
+  if (F16) {
+    __half2 v = __floats2half2_rn(lo_k, hi_k);
+    return *reinterpret_cast<uint32_t*>(&v);
+  }
+  return pack_bf16(lo_k, hi_k);
+}
+template <bool F16>
+__device__ __forceinline__ float2 unpack16(uint32_t w) {
+  if (F16) return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+}
+// hi and lo words of four complex values (eight K elements)
+template <bool F16>
+__device__ __forceinline__ void split16(const float2 (&v)[4], uint4& h, uint4& l) {
+  h.x = pack16<F16>(v[0].x, v[0].y); h.y = pack16<F16>(v[1].x, v[1].y);
+  h.z = pack16<F16>(v[2].x, v[2].y); h.w = pack16<F16>(v[3].x, v[3].y);
+  const float2 h0 = unpack16<F16>(h.x), h1 = unpack16<F16>(h.y);
+  const float2 h2 = unpack16<F16>(h.z), h3 = unpack16<F16>(h.w);
+  l.x = pack16<F16>(v[0].x - h0.x, v[0].y - h0.y); l.y = pack16<F16>(v[1].x - h1.x, v[1].y - h1.y);
+  l.z = pack16<F16>(v[2].x - h2.x, v[2].y - h2.y); l.w = pack16<F16>(v[3].x - h3.x, v[3].y - h3.y);
+}
+
+template <int PASSES, bool F16>
 __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
   constexpr int STAGES = PASSES == 1 ? 4 : 3;
   constexpr int NCOMP = PASSES == 1 ? 1 : 2;
@@ -137,7 +185,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
           for (int kk = 0; kk < 4; ++kk) {
             for (int i = 0; i < ni; ++i) {
               const uint32_t ao = uint32_t(ia[i]) * ROWB + kk * 32, bo = uint32_t(ib[i]) * ROWB + kk * 32;
-              const uint32_t idesc = idesc_bf16(TC_M, in_[i]);
+              const uint32_t idesc = F16 ? idesc_f16(TC_M, in_[i]) : idesc_bf16(TC_M, in_[i]);
               const uint32_t dt = tmem + uint32_t(ic[i]);
               const uint32_t acc0 = (st > 0 || kk > 0) ? 1u : 0u;
               mma_bf16(dt, sw128_desc(hi + ao), sw128_desc(hi + bo), idesc, acc0);
@@ -198,10 +246,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     float tr_hi = 0.f, tr_lo = 0.f;      // Kahan-compensated FP32 trace of the segment
     for (int si = s0; si < s1 && ok; ++si) {
       const int slot = slots[si];
-      const int m = d.seg_m[slot];
       const long long nrow = d.seg_nrow[slot];
       const long long nst = (nrow + TC_KC - 1) / TC_KC;
-      (void)m;
+      // power-of-two scales of this segment's kernel rows and data rows (FP16 operands)
+      const int2 se = F16 ? d.gscale[slot] : make_int2(0, 0);
+      const float2 sc = make_float2(ldexpf(1.f, se.x), ldexpf(1.f, se.y));
       tr_hi = 0.f; tr_lo = 0.f;
       for (long long st = 0; st < nst; ++st, ++it) {
         const int s = int(it % STAGES);
@@ -235,7 +284,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
               const GramRow e = rt[cc[h2] * 4 + rr];
               // entries past the segment's last row belong to the next segment: padding here
               const bool ok2 = uv && zz[h2] < nz && (cc[h2] * 4 + rr) < nvalid;
-              swv[h2][rr] = ok2 ? e.sw : 0.f;
+              swv[h2][rr] = ok2 ? e.sw * sc.x : 0.f;
               gpv[h2][rr] = ok2 ? __ldg(g32 + size_t(e.offp) * nzs + zz[h2]) : make_float2(0.f, 0.f);
               gqv[h2][rr] = ok2 ? __ldg(g32 + size_t(e.offq) * nzs + zz[h2]) : make_float2(0.f, 0.f);
             }
@@ -250,19 +299,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
               a[rr] = make_float2(swv[h2][rr] * v.x, swv[h2][rr] * v.y);
               trs = fmaf(a[rr].x, a[rr].x, fmaf(a[rr].y, a[rr].y, trs));
             }
-            uint4 h;
-            h.x = pack_bf16(a[0].x, a[0].y); h.y = pack_bf16(a[1].x, a[1].y);
-            h.z = pack_bf16(a[2].x, a[2].y); h.w = pack_bf16(a[3].x, a[3].y);
             const uint32_t off = sw_off(zz[h2], cc[h2]);
-            *reinterpret_cast<uint4*>(hi + off) = h;
             if (PASSES == 3) {
-              uint4 l;
-              const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
-              float2 h0 = __bfloat1622float2(hb[0]), h1 = __bfloat1622float2(hb[1]);
-              float2 hh2 = __bfloat1622float2(hb[2]), h3 = __bfloat1622float2(hb[3]);
-              l.x = pack_bf16(a[0].x - h0.x, a[0].y - h0.y); l.y = pack_bf16(a[1].x - h1.x, a[1].y - h1.y);
-              l.z = pack_bf16(a[2].x - hh2.x, a[2].y - hh2.y); l.w = pack_bf16(a[3].x - h3.x, a[3].y - h3.y);
+              uint4 h, l;
+              split16<F16>(a, h, l);
+              *reinterpret_cast<uint4*>(hi + off) = h;
               *reinterpret_cast<uint4*>(lo + off) = l;
+            } else {
+              uint4 h;
+              h.x = pack16<F16>(a[0].x, a[0].y); h.y = pack16<F16>(a[1].x, a[1].y);
+              h.z = pack16<F16>(a[2].x, a[2].y); h.w = pack16<F16>(a[3].x, a[3].y);
+              *reinterpret_cast<uint4*>(hi + off) = h;
             }
           }
         }
@@ -273,23 +320,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr) {
             const float4 dd = rdat[c * 4 + rr];
-            const float sw = rt[c * 4 + rr].sw;
+            const float sw = rt[c * 4 + rr].sw * sc.y;
             v[rr] = which ? make_float2(sw * dd.z, sw * dd.w) : make_float2(sw * dd.x, sw * dd.y);
             if (c * 4 + rr >= nvalid) v[rr] = make_float2(0.f, 0.f);
           }
-          uint4 h;
-          h.x = pack_bf16(v[0].x, v[0].y); h.y = pack_bf16(v[1].x, v[1].y);
-          h.z = pack_bf16(v[2].x, v[2].y); h.w = pack_bf16(v[3].x, v[3].y);
           const uint32_t off = sw_off(nzp + which, c);
-          *reinterpret_cast<uint4*>(hi + off) = h;
           if (PASSES == 3) {
-            uint4 l;
-            const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&h);
-            float2 h0 = __bfloat1622float2(hb[0]), h1 = __bfloat1622float2(hb[1]);
-            float2 h2 = __bfloat1622float2(hb[2]), h3 = __bfloat1622float2(hb[3]);
-            l.x = pack_bf16(v[0].x - h0.x, v[0].y - h0.y); l.y = pack_bf16(v[1].x - h1.x, v[1].y - h1.y);
-            l.z = pack_bf16(v[2].x - h2.x, v[2].y - h2.y); l.w = pack_bf16(v[3].x - h3.x, v[3].y - h3.y);
+            uint4 h, l;
+            split16<F16>(v, h, l);
+            *reinterpret_cast<uint4*>(hi + off) = h;
             *reinterpret_cast<uint4*>(lo + off) = l;
+          } else {
+            uint4 h;
+            h.x = pack16<F16>(v[0].x, v[0].y); h.y = pack16<F16>(v[1].x, v[1].y);
+            h.z = pack16<F16>(v[2].x, v[2].y); h.w = pack16<F16>(v[3].x, v[3].y);
+            *reinterpret_cast<uint4*>(hi + off) = h;
           }
         }
         {   // Kahan: tr_hi + tr_lo carries the segment's trace without FP64 arithmetic
@@ -316,8 +361,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
       }
       tc_fence_before();
       mbar_arrive(acc_empty);
-      // trace(G) of this segment, summed over the warp in FP64
-      double tr = double(tr_hi) - double(tr_lo);
+      // trace(G) of this segment, summed over the warp in FP64 (the kernel-row scale
+      // divided out exactly: it is a power of two)
+      double tr = (double(tr_hi) - double(tr_lo)) * pow2d(-2 * se.x);
       for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
       if (lane == 0) atomicAdd(&d.trace[d.seg_m[slot]], tr);
     }
@@ -328,6 +374,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
   if (warp == PRODUCER_WARPS) {
     tc_fence_after();
     tmem_dealloc(tmem, alloc_cols);
+  }
+}
+
+// Largest modulus over depth of every row of the FP32 table (one warp per row).
+__global__ void table_rowmax_kernel(Dev d, long long nrows) {
+  const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  const float2* t = d.rowtab32 + size_t(r) * d.nzs;
+  float mx = 0.f;
+  for (int z = lane; z < d.nz; z += 32) {
+    const float2 v = t[z];
+    mx = fmaxf(mx, sqrtf(v.x * v.x + v.y * v.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) d.rowmax[r] = mx;
+}
+
+// Per segment: bounds of its kernel rows (sqrt(w) |g_p| |g_q| over depth, from the row
+// maxima) and of its data rows, turned into power-of-two scales for the FP16 operands.
+__global__ void gram_scale_kernel(Dev d) {
+  __shared__ float red[2][32];
+  const int slot = blockIdx.x;
+  const long long r0 = d.seg_row0[slot], n = d.seg_nrow[slot];
+  const float4* rhs = reinterpret_cast<const float4*>(d.rhs);
+  float ma = 0.f, md = 0.f;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const GramRow e = d.gent[r0 + i];
+    ma = fmaxf(ma, e.sw * d.rowmax[e.offp] * d.rowmax[e.offq]);
+    const float4 v = rhs[r0 + i];
+    md = fmaxf(md, e.sw * fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[0][warp] = ma; red[1][warp] = md; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) { ma = fmaxf(ma, red[0][w]); md = fmaxf(md, red[1][w]); }
+    d.gscale[slot] = make_int2(pow2_exp(ma), pow2_exp(md));
   }
 }
 
@@ -347,7 +435,10 @@ __global__ void gram_reduce_kernel(Dev d) {
     if (a < TC_M) { lanei = a; col = b; }
     else { lanei = a - TC_M; col = c1 + (b - TC_M); }
     double s = 0.0;
-    for (int sl = sl0; sl < sl1; ++sl) s += double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
+    for (int sl = sl0; sl < sl1; ++sl) {
+      const double v = double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
+      s += d.gscale ? v * pow2d(-2 * d.gscale[sl].x) : v;
+    }
     d.G[size_t(m) * nG + e] = s;
   } else if (e < nG + 2 * nz) {
     const int zi = int((e - nG) >> 1), k = int((e - nG) & 1);
@@ -355,7 +446,10 @@ __global__ void gram_reduce_kernel(Dev d) {
     if (zi < TC_M) { lanei = zi; col = nzp + k; }
     else { lanei = zi - TC_M; col = c1 + (nzp - TC_M) + k; }
     double s = 0.0;
-    for (int sl = sl0; sl < sl1; ++sl) s += double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
+    for (int sl = sl0; sl < sl1; ++sl) {
+      const double v = double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
+      s += d.gscale ? v * pow2d(-d.gscale[sl].x - d.gscale[sl].y) : v;
+    }
     d.b[(size_t(m) * nz + zi) * 2 + k] = s;
   }
 }
@@ -372,17 +466,35 @@ int tc_smem_bytes(int nz, int passes) {
 
 cudaError_t prepare_gram_tc(const Dev& d) {
   const int smem = tc_smem_bytes(d.nz, d.passes);
-  return d.passes == 3
-             ? cudaFuncSetAttribute(gram_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-             : cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (d.f16)
+    return d.passes == 3 ? cudaFuncSetAttribute(gram_tc_kernel<3, true>, attr, smem)
+                         : cudaFuncSetAttribute(gram_tc_kernel<1, true>, attr, smem);
+  return d.passes == 3 ? cudaFuncSetAttribute(gram_tc_kernel<3, false>, attr, smem)
+                       : cudaFuncSetAttribute(gram_tc_kernel<1, false>, attr, smem);
+}
+
+int gram_scale_launches(const Dev& d) { return d.f16 && d.ncta_gram > 0 ? 2 : 0; }
+
+cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s) {
+  if (!d.f16 || d.ncta_gram <= 0) return cudaSuccess;
+  const long long nrows = (long long)d.nf * d.nk;
+  table_rowmax_kernel<<<unsigned((nrows + 7) / 8), 256, 0, s>>>(d, nrows);
+  gram_scale_kernel<<<d.nseg, 256, 0, s>>>(d);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s) {
   const int smem = tc_smem_bytes(d.nz, d.passes);
   cudaError_t e;
   if (d.ncta_gram > 0) {
-    if (d.passes == 3) gram_tc_kernel<3><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
-    else gram_tc_kernel<1><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
+    if (d.f16) {
+      if (d.passes == 3) gram_tc_kernel<3, true><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
+      else gram_tc_kernel<1, true><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
+    } else {
+      if (d.passes == 3) gram_tc_kernel<3, false><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
+      else gram_tc_kernel<1, false><<<d.ncta_gram, NTHREADS, smem, s>>>(d);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -16,9 +16,11 @@
 // Kernels: green_layer (one thread per (f, n, layer): vertical wavenumber and the layer's
 // phase factors, the FP64 transcendentals, fully parallel), green_recursion (one thread
 // per (f, n): the two recursions, FP64), then one of two evaluations:
-//   green_eval64  (FP64 table): a CTA per (f, block of 32 n); each warp marches a chunk of
-//                 depths by the recurrence and stages its tile in shared memory so the
-//                 table rows are written coalesced;
+//   green_eval64  (FP64 table, and/or the FP32 table sqrt|s_f| g rounded from it, with the
+//                 rounding remainder as a second FP32 table for a double-float pair):
+//                 a CTA per (f, block of 32 n); each warp marches a chunk of depths by the
+//                 recurrence and stages its tile in shared memory so the table rows are
+//                 written coalesced;
 //   green_eval32  (FP32 table sqrt|s_f| g for the mixed path): one thread per (f, n, z);
 //                 each exponential's phase and decay are formed and range-reduced in FP64
 //                 (Cody-Waite for the phase, integer/fraction split for the decay) and
@@ -172,9 +174,15 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval64_kernel(Dev d) {
       const int z = zc + zi;
       if (nn < d.nk && z < d.nz) {
         const double2 v = tile[warp][nl][zi];
-        const size_t o = (size_t(f) * d.nk + nn) * d.nz + z;
-        d.g64[o] = v;
-        if (d.g32) d.g32[(size_t(f) * d.nk + nn) * d.nzs + z] = make_float2(float(sq * v.x), float(sq * v.y));
+        if (d.g64) d.g64[(size_t(f) * d.nk + nn) * d.nz + z] = v;
+        if (d.g32) {
+          // sqrt|s_f| g rounded to FP32, and (double-float table) the FP32 rounding of the rest
+          const double sx = sq * v.x, sy = sq * v.y;
+          const float hx = float(sx), hy = float(sy);
+          const size_t o32 = (size_t(f) * d.nk + nn) * d.nzs + z;
+          d.g32[o32] = make_float2(hx, hy);
+          if (d.g32lo) d.g32lo[o32] = make_float2(float(sx - double(hx)), float(sy - double(hy)));
+        }
       }
     }
     __syncwarp();
@@ -216,7 +224,9 @@ cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables) {
     green_eval32_kernel<<<unsigned((ne + 255) / 256), 256, 0, s>>>(d);
   } else {
     Dev e = d;
-    if (!(tables & GREEN_G32)) e.g32 = nullptr;
+    if (!(tables & (GREEN_G32 | GREEN_G32DF))) e.g32 = nullptr;
+    if (!(tables & GREEN_G32DF)) e.g32lo = nullptr;
+    if (!(tables & GREEN_G64)) e.g64 = nullptr;
     dim3 g2((d.nk + 31) / 32, d.nf);
     green_eval64_kernel<<<g2, EV_WARPS * 32, 0, s>>>(e);
   }

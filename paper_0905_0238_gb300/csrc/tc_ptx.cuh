@@ -1,5 +1,5 @@
 // Inline-PTX wrappers for the tcgen05 kernels (sm_103a): mbarriers, one-dimensional bulk
-// copies, tensor-memory allocation and loads, BF16 MMA with FP32 accumulation, and the
+// copies, tensor-memory allocation and loads, BF16/FP16 MMA with FP32 accumulation, and the
 // shared-memory layout of a K-major operand with the 128-byte swizzle.
 #pragma once
 #include <cuda_runtime.h>
@@ -114,6 +114,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
 __host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// Instruction descriptor: FP16 x FP16 -> FP32 (operand formats 0), both K-major, M x N.
+__host__ __device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {

@@ -36,6 +36,7 @@ class edt_config(C.Structure):
         ("chol_df", C.c_int), ("freq_chunk", C.c_int),
         ("geometry", C.c_int), ("ny", C.c_int), ("dy", C.c_double), ("wx", C.c_int), ("wy", C.c_int),
         ("solver", C.c_int), ("tsvd_tol", C.c_double), ("kz_disk", C.c_double),
+        ("gram_seg_rows", C.c_int), ("resid", C.c_int),
     ]
 
 
@@ -322,6 +323,8 @@ class Config:
     solver: int = 0            # EDT_SOLVE_DAMPED or EDT_SOLVE_TSVD (FP64 line path)
     tsvd_tol: float = 0.0      # truncated SVD: > 0 absolute sigma, < 0 relative to s_max
     kz_disk: float = 0.0       # > 0: |(k_m, k_z)| <= kz_disk omega_max / c_min
+    gram_seg_rows: int = 0     # mixed: rows per FP32 Gram accumulation (0 = automatic)
+    resid: int = 0             # mixed: refinement residual, 1 FP32, 2 double-float, 0 automatic
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -366,7 +369,8 @@ class Solver:
             passes=cfg.passes, refine=cfg.refine, alpha=cfg.alpha, cutoff=cfg.cutoff,
             fold=cfg.fold, chol_df=cfg.chol_df, freq_chunk=cfg.freq_chunk,
             geometry=cfg.geometry, ny=cfg.ny, dy=cfg.dy, wx=cfg.wx, wy=cfg.wy,
-            solver=cfg.solver, tsvd_tol=cfg.tsvd_tol, kz_disk=cfg.kz_disk)
+            solver=cfg.solver, tsvd_tol=cfg.tsvd_tol, kz_disk=cfg.kz_disk,
+            gram_seg_rows=cfg.gram_seg_rows, resid=cfg.resid)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.ctx = None
         self.ctx, self.ws_bytes = edt_create(c)

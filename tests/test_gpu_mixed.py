@@ -3,10 +3,11 @@
 The tensor-core normal matrices are compared with Ahat^T Ahat formed in FP64 from the
 oracle's own kernel rows (a matmul in the test; the oracle itself never forms a Gram);
 the end-to-end inversion with the oracle's QR solution.  Tolerances: Gram relative
-Frobenius 5e-3 with BF16 operands, 2e-5 with the split BF16x3 operands; trace(G) 5e-7
-(the FP32 table sqrt|s_f| g is accurate to ~2e-7 relative: FP64-reduced arguments, FP32
+Frobenius 5e-3 with one 16-bit operand pass, 2e-5 with the split hi/lo operands; trace(G)
+5e-7 (the FP32 table sqrt|s_f| g is accurate to ~2e-7 relative: FP64-reduced arguments, FP32
 sincos/exp2, so each |a|^2 carries up to ~5e-7);
-V and Vhat 1e-5 relative L2 after one refinement step.
+V and Vhat 1e-5 relative L2 after one refinement step, and at weak damping (alpha down to
+1e-6, the FP64-accurate residual, one to three steps) on noisy data.
 """
 import numpy as np
 import pytest
@@ -127,3 +128,66 @@ def test_double_float_cholesky_option(nx, nz, nf):
     Vdf = s.invert(dev(D)).cpu().numpy()
     assert rel_l2(Vdf, V64) < 1e-9
     assert rel_l2(Vdf, V_or) < 1e-5
+
+
+def _noisy_case(case, alpha):
+    import synth as _s
+    if case == "prod_layers":
+        wp = _s.preset("production_2d")
+        return small_workload(nx=64, nz=128, nf=8, alpha=alpha, dz=8.0, layers=(wp.layer_top, wp.layer_vel))
+    nx, nz, nf = {"grad40": (32, 40, 6), "grad130": (64, 130, 4), "grad256": (32, 256, 3)}[case]
+    return small_workload(nx=nx, nz=nz, nf=nf, alpha=alpha, dz=8.0)
+
+
+@pytest.mark.parametrize("alpha,refine", [(1e-4, 1), (1e-5, 1), (1e-6, 3)])
+@pytest.mark.parametrize("case", ["grad40", "grad130", "grad256", "prod_layers"])
+def test_invert_mixed_weak_damping(case, alpha, refine):
+    """Weak damping on 20 dB data: the split FP16 Gram sets the refinement's contraction and
+    the FP64-accurate residual (chosen automatically below alpha = 1e-3) its limit; one step
+    reaches 1e-5 down to alpha = 1e-5, three steps at 1e-6."""
+    wl = _noisy_case(case, alpha)
+    D = born_data(wl, salt=2)
+    V_or, vh_or = edt2d.invert(wl, D.astype(np.complex128))
+    s = solver(wl, passes=3, refine=refine)
+    V = s.invert(dev(D)).cpu().numpy()
+    st = s.stats()
+    assert st.n_notpd == 0 and st.n_nonfinite == 0
+    assert rel_l2(s.vhat().cpu().numpy(), vh_or) < 1e-5
+    assert rel_l2(V, V_or) < 1e-5, rel_l2(V, V_or)
+
+
+def test_fp64_accurate_residual_lowers_the_weak_damping_floor():
+    """At alpha = 1e-6 with three steps, the FP32 residual (FP32 table and products) stalls
+    above the double-float residual's error."""
+    from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED
+    wl = _noisy_case("grad40", 1e-6)
+    D = born_data(wl, salt=2)
+    V_or, _ = edt2d.invert(wl, D.astype(np.complex128))
+    err = {}
+    for resid in (1, 2):
+        cfg = Config.from_workload(wl, precision=EDT_MIXED, passes=3, refine=3, resid=resid)
+        err[resid] = rel_l2(Solver(cfg).invert(dev(D)).cpu().numpy(), V_or)
+    assert err[2] < 1e-5 and err[2] < err[1] / 2, err
+
+
+def test_shorter_gram_segments_reduce_the_accumulation_error():
+    """Long FP32 tensor-memory accumulations lose low bits systematically (the diagonal is
+    biased low); flushing every 32 rows to an FP64-summed partial tile shrinks the Gram's
+    error against A^T A (256-point line, 128 frequencies: ~2.6 k rows per CTA segment)."""
+    from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED
+    wp = synth.preset("production_2d")
+    wl = small_workload(nx=256, nz=64, nf=128, fmin=3.0, fmax=60.0, dx=12.5, dz=8.0, alpha=1e-2,
+                        layers=(wp.layer_top, wp.layer_vel))
+    D = synth.random_data(synth.rng_for(3, salt=77), (len(wl.freq_hz), wl.nx, wl.nx), np.complex64)
+    D2 = edt2d.data_transform(D.astype(np.complex128))
+    g = edt2d.green_table(wl)
+    refs = {}
+    for m in (0, 20, 120):
+        _, sysd = edt2d.solve_wavenumber(wl, D2, m, g=g, return_system=True)
+        refs[m] = sysd["Ahat"].T @ sysd["Ahat"]
+    err = {}
+    for cap in (0, 32):
+        s = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=3, gram_seg_rows=cap))
+        G = s.gram(dev(D))[0].cpu().numpy()
+        err[cap] = max(rel_l2(G[m], refs[m]) for m in refs)
+    assert err[32] < err[0] / 3 and err[32] < 5e-6, err

@@ -94,6 +94,7 @@ def test_batched_grid_sampled_pairs():
         assert rel_l2(vh[idx], want) < 1e-5, (m, rel_l2(vh[idx], want))
 
 
+@pytest.mark.parametrize("alpha,refine", [(1e-3, 1), (1e-4, 2)])
 @pytest.mark.parametrize("nx,ny,wx,wy,nf,nz", [
     (64, 64, 8, 4, 3, 12),      # rectangular window: derived rows with WY < WX, two jx per thread
     (32, 32, 4, 2, 4, 10),      # WY = 2: no derived rows
@@ -101,15 +102,14 @@ def test_batched_grid_sampled_pairs():
     (128, 1, 8, 1, 4, 16),      # lines of 128 and 512 points
     (512, 1, 4, 1, 3, 12),
 ])
-def test_window_shapes_match_oracle(nx, ny, wx, wy, nf, nz):
-    """More grid and window shapes at alpha = 1e-3.  (At alpha = 1e-4 the 64 x 64 grid with the
-    8 x 4 window, half the offsets of the square window, reaches 1.6e-5: the FP32 kernel rows'
-    rounding amplified by the weaker damping, the same with or without the mirrored-row
-    shortcut of the window products.)"""
-    wl = workload(nx, ny, wx, wy, nf=nf, nz=nz, alpha=1e-3)
+def test_window_shapes_match_oracle(nx, ny, wx, wy, nf, nz, alpha, refine):
+    """More grid and window shapes at alpha = 1e-3 (one refinement step) and 1e-4 (two: the
+    window Gram's BF16 hi/lo rows make one step contract by only ~0.2 at that damping; the
+    64 x 64 grid with the 8 x 4 window is at 6e-6 after one step, 1.3e-6 after two)."""
+    wl = workload(nx, ny, wx, wy, nf=nf, nz=nz, alpha=alpha)
     D = born_data(wl, salt=11)
     V_or, vh_or = edt3d.invert(wl, D)
-    s = solver(wl)
+    s = solver(wl, refine=refine)
     V = s.invert(dev(D.astype(np.complex64)), out_dtype=torch.float32).cpu().numpy()
     st = s.stats()
     assert st.n_notpd == 0 and st.n_nonfinite == 0
