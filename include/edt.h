@@ -188,6 +188,9 @@ typedef struct {
                                    spectrum buffer holds one chunk, about 32 MB)         */
   int launches_per_grad;        /* CUDA kernels one edt_misfit_grad launches (0 where it
                                    is unsupported)                                       */
+  int gram_timeouts;            /* 1 if a bounded wait of the tensor-core Gram expired in
+                                   the last edt_invert / edt_gram (its result is then
+                                   invalid and last_status is EDT_ETIMEOUT), else 0      */
 } edt_stats;
 
 /* Launch shapes the autotuner chooses among (candidates in brackets; all give the same
@@ -261,6 +264,19 @@ int edt_set_host_pipeline(edt_ctx* ctx, int on);
  * evaluated spectrally.  Precision follows cfg.precision (FP32 for EDT_MIXED). */
 int edt_forward(edt_ctx* ctx, const void* V_dev, int V_dtype, void* D_dev, int D_dtype,
                 void* stream);
+
+/* Adjoint Born operator (Section "Two dimensions", eq. Born and its decoupled form eq. DMV):
+ * V = F^T D, the adjoint of edt_forward's map V -> D for the inner products
+ * <D1, D2> = Re sum conj(D1) D2 and <V1, V2> = sum V1 V2, i.e. with D2 = T(D) / nx^2 (T the
+ * data transform of the header, whose adjoint inverse is T / nx^2),
+ *   Vbar_hat(k_m, z_j) = sum_f sum_p conj(s_f g(k_p, z_j) g(k_{p-m}, z_j)) D2_f(p, p - m),
+ *   V(x_i, z_j) = Re sum_m Vbar_hat(k_m, z_j) exp(+i k_m x_i),   s_f = omega~_f^2 dz / dx.
+ * D_dev: complex [nfreq][nx][nx] (EDT_C64 or EDT_C128), caller-owned; V_dev: real [nx][nz]
+ * (EDT_F32 or EDT_F64), overwritten.  EDT_FP64: FP64 transform and contraction; EDT_MIXED:
+ * FP32 transform and table, FP32 products with FP64 sums across frequencies (needs nx >= 64
+ * and at most 64 layers, as edt_misfit_grad).  Line geometry only (else EDT_EUNSUPPORTED).
+ * Asynchronous on `stream`; uses the workspace (not the factors of the last edt_invert). */
+int edt_adjoint(edt_ctx* ctx, const void* D_dev, int D_dtype, void* V_dev, int V_dtype, void* stream);
 
 /* Misfit of a model against data and its gradients (line geometry, EDT_MIXED; FP32
  * arithmetic with FP64 accumulation across frequencies):
@@ -347,8 +363,22 @@ int edt_kz_disk_columns(const edt_ctx* ctx, int* p);
 /* Per-subproblem complex row counts after the cut (before folding): counts[nx/2+1]. */
 int edt_row_counts(const edt_ctx* ctx, long long* counts);
 
-/* Fill *out; synchronises the stream of the last device call on this context. */
+/* Fill *out; synchronises the stream of the last device call on this context.  A device
+ * wait that expired in the last edt_invert (every wait of the tensor-core Gram is bounded,
+ * about 2 s) shows here as gram_timeouts = 1 and last_status = EDT_ETIMEOUT: edt_invert
+ * itself returns before the device work ends, so this is where the failure surfaces. */
 int edt_get_stats(edt_ctx* ctx, edt_stats* out);
+
+/* Test hook for the failure path of the bounded device waits (failure detection exercised
+ * without a GPU fault; not for production use).  wait_cycles > 0 replaces the
+ * ~2 s budget of every bounded wait of the tensor-core Gram by that many SM clock cycles;
+ * stall = 1 (requires wait_cycles > 0) makes the Gram's MMA issuer wait on an mbarrier that
+ * nothing completes, so the wait runs out, the kernel raises its flag, releases the
+ * producers through its abort flag, drains its MMAs and copies, frees its tensor memory
+ * and returns; edt_get_stats then reports EDT_ETIMEOUT.  stall = 0, wait_cycles = 0 restore
+ * normal operation; the context stays usable throughout.  Host-only; returns EDT_OK or
+ * EDT_EINVAL. */
+int edt_set_wait_test(edt_ctx* ctx, long long wait_cycles, int stall);
 
 /* Per-stage device timing.  With profiling on, every edt_invert (up to 256 calls between
  * reads) records CUDA events at the beginning and end of each stage on the stream the stage
@@ -466,6 +496,10 @@ int edt_stream_get_stats(const edt_stream* s, edt_stream_stats* out);
  * summed milliseconds per launch (names[i] static strings) since the last read, the number of
  * batches they cover in *n_batches, and resets.  Returns the number of entries written. */
 int edt_stream_set_profiling(edt_stream* s, int on);
+/* Test hook for the streaming Gram's bounded waits, as edt_set_wait_test: batches submitted
+ * while stall = 1 take the timeout path and report EDT_ETIMEOUT for each of their requests;
+ * later batches (stall = 0) run normally. */
+int edt_stream_set_wait_test(edt_stream* s, long long wait_cycles, int stall);
 int edt_stream_read_profile(edt_stream* s, double* ms, const char** names, int max_kernels,
                             long long* n_batches);
 

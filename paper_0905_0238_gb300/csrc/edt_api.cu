@@ -796,6 +796,8 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
   c->last_stream = s;
+  // the Gram's wait-expired flag describes this call only
+  if (mixed) EDT_TRY(cudaMemsetAsync(d.flags, 0, sizeof(unsigned), s));
   // fork: the depth march (FP64-bound) and, for the window geometry, the kernel rows it
   // feeds run on the auxiliary stream while the data transform (FP32 and memory) runs on s
   const bool ov = c->tune_ov != 0;
@@ -1186,6 +1188,20 @@ int edt_forward(edt_ctx* c, const void* V, int V_dtype, void* D, int D_dtype, vo
   return EDT_OK;
 }
 
+int edt_adjoint(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, void* stream) {
+  if (!c || !D || !V) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
+  if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
+  if (c->win) return EDT_EUNSUPPORTED;
+  if (c->cfg.precision == EDT_MIXED && !grad_supported(c->dev)) return EDT_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  EDT_TRY(launch_green(c->dev, s, c->cfg.precision == EDT_MIXED ? GREEN_G32 : GREEN_G64));
+  EDT_TRY(launch_adjoint(c->dev, D, D_dtype, V, V_dtype, s));
+  return EDT_OK;
+}
+
 int edt_misfit_grad(edt_ctx* c, const void* V, int V_dtype, const void* D, int D_dtype,
                     double* J, void* gV, double* gc, void* stream) {
   if (!c || !V || !D || !J || !gV || !gc) return EDT_EINVAL;
@@ -1328,7 +1344,19 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
       if (v == EDT_ENOTPD) o->n_notpd++;
       if (v == EDT_ENONFINITE) o->n_nonfinite++;
     }
+    unsigned fl = 0;
+    e = cudaMemcpy(&fl, c->dev.flags, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    o->gram_timeouts = fl ? 1 : 0;
+    if (fl) o->last_status = EDT_ETIMEOUT;
   }
+  return EDT_OK;
+}
+
+int edt_set_wait_test(edt_ctx* c, long long wait_cycles, int stall) {
+  if (!c || wait_cycles < 0 || (stall != 0 && stall != 1) || (stall && wait_cycles == 0)) return EDT_EINVAL;
+  c->dev.wait_cycles = wait_cycles;
+  c->dev.wait_stall = stall;
   return EDT_OK;
 }
 

@@ -152,7 +152,10 @@ struct Dev {
   double* gacc;                 // [1 + nlayer] sum |R2|^2, then dJ/dc_l
   float2* gbar;                 // [nf][N][nz] dJ/dg per full lateral index (aliases g64)
   int* status;                  // [nsub]
-  unsigned int* flags;          // [8] device-side error flags
+  unsigned int* flags;          // [8] device-side error flags; [0]: a tensor-core Gram wait expired
+  long long wait_cycles;        // budget of the tensor-core Gram's bounded waits (0: about 2 s)
+  int wait_stall;               // wait test: the Gram's MMA issuer waits on a barrier that
+                                //   nothing completes, so the kernel takes its timeout path
   // streaming batches (per-subproblem sizes; null for a context's own subproblems)
   const int* sub_n;             // [nsub] unknowns of subproblem m
   const long long* sub_goff;    // [nsub] element offset of its matrix in G and L32
@@ -239,6 +242,11 @@ constexpr int GRAD_MAX_LAYERS = 64;
 bool grad_supported(const Dev& d);
 cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const void* D, int D_dtype,
                                double* J, void* gV, double* gc, cudaStream_t s);
+// V = F^T D, the adjoint Born operator (line geometry; the mixed path needs grad_supported).
+cudaError_t launch_adjoint(const Dev& d, const void* D, int D_dtype, void* V, int V_dtype, cudaStream_t s);
+// FP64 data transform of frequency planes [f0, f0 + nfc) and their adjoint-Born contraction,
+// accumulated into vfull.
+cudaError_t launch_adjoint64_chunk(const Dev& d, const void* D, int D_dtype, int f0, int nfc, cudaStream_t s);
 
 // Streaming batches: Cholesky and refinement update with per-subproblem sizes (<= nmax).
 cudaError_t prepare_chol_var(int nmax);

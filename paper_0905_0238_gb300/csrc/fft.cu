@@ -505,6 +505,45 @@ cudaError_t launch_transform_adjoint(const Dev& d, void* D, int D_dtype, int f0,
   return rows_fft<float>(d, d.X, EDT_C64, Dc, D_dtype, (long long)nfc * d.N, +1, 1.f, s);
 }
 
+// Adjoint of the spectral Born model on one chunk of FP64 planes X[fi][q][p] = D2(p, q):
+// vfull[m][z] += sum_f sum_p conj(s_f g(k_p, z) g(k_{p-m}, z)) D2(p, p - m), one thread per
+// (m, z) (a warp over 32 consecutive depths of one m: table reads coalesced, the D2 value
+// broadcast).
+__global__ void __launch_bounds__(256) born_adjoint64_kernel(Dev d, int f0, int nfc) {
+  const int N = d.N, msk = N - 1;
+  const int z = blockIdx.y * 32 + (threadIdx.x & 31);
+  const int m = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (z >= d.nz || m >= N) return;
+  const double2* X = reinterpret_cast<const double2*>(d.X);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int fi = 0; fi < nfc; ++fi) {
+    const int f = f0 + fi;
+    const FreqConst fc = d.fc[f];
+    const double2 om = make_double2(fc.om_re, fc.om_im);
+    const double2 sf = (d.dz / d.dx) * (om * om);
+    const double2* g = d.g64 + size_t(f) * d.nk * d.nz;
+    const double2* Xf = X + size_t(fi) * N * N;
+    double2 sum = make_double2(0.0, 0.0);
+    for (int p = 0; p < N; ++p) {
+      const int q = (p - m) & msk;
+      const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
+      const double2 a = g[size_t(np) * d.nz + z] * g[size_t(nq) * d.nz + z];
+      const double2 x = Xf[size_t(q) * N + p];
+      sum = sum + make_double2(a.x * x.x + a.y * x.y, a.x * x.y - a.y * x.x);   // conj(a) x
+    }
+    acc = acc + make_double2(sf.x * sum.x + sf.y * sum.y, sf.x * sum.y - sf.y * sum.x);   // conj(s_f) sum
+  }
+  double2* out = d.vfull + size_t(m) * d.nz + z;
+  *out = *out + acc;
+}
+
+cudaError_t launch_adjoint64_chunk(const Dev& d, const void* D, int D_dtype, int f0, int nfc, cudaStream_t s) {
+  cudaError_t e = launch_transform<double>(d, D, D_dtype, f0, nfc, s);
+  if (e != cudaSuccess) return e;
+  born_adjoint64_kernel<<<dim3((d.N + 7) / 8, (d.nz + 31) / 32), 256, 0, s>>>(d, f0, nfc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,
                            cudaStream_t s) {
   size_t smem = size_t(INV_ZT) * (padded_len(d.N) + 1) * sizeof(double2);

@@ -616,6 +616,35 @@ bool grad_supported(const Dev& d) {
          d.gscr != nullptr;
 }
 
+// Adjoint Born operator of the line geometry, V = F^T D for <D1, D2> = Re sum conj(D1) D2 and
+// <V1, V2> = sum V1 V2: the adjoint of the inverse data transform is T / N^2 (T the data
+// transform, N times a unitary map per axis), then Vbar_hat(m, z) = sum_f sum_p
+// conj(s_f g(k_p, z) g(k_{p-m}, z)) D2(p, p - m) and V(x, z) = Re sum_m Vbar_hat(m, z) e^{+i k_m x}.
+// Mixed path: FP32 transform and the misfit gradient's adjoint-Born contraction (FP64 sums
+// across frequencies); FP64 path: FP64 transform and a direct FP64 contraction.
+cudaError_t launch_adjoint(const Dev& d, const void* D, int D_dtype, void* V, int V_dtype, cudaStream_t s) {
+  cudaError_t e;
+  const int N = d.N;
+  const double scale = 1.0 / (double(N) * N);
+  if (d.precision == EDT_FP64) {
+    if ((e = cudaMemsetAsync(d.vfull, 0, sizeof(double2) * size_t(N) * d.nz, s)) != cudaSuccess) return e;
+    for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
+      const int nfc = std::min(d.fchunk, d.nf - f0);
+      if ((e = launch_adjoint64_chunk(d, D, D_dtype, f0, nfc, s)) != cudaSuccess) return e;
+    }
+    return launch_lateral_idft_real(d, d.vfull, scale, V, V_dtype, s);
+  }
+  grad_zero_kernel<<<152, 256, 0, s>>>(d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
+    const int nfc = std::min(d.fchunk, d.nf - f0);
+    if ((e = launch_transform<float>(d, D, D_dtype, f0, nfc, s)) != cudaSuccess) return e;
+    grad_vhat_kernel<<<dim3(N / VM, (d.nz + 31) / 32, nfc), 256, VHAT_SMEM, s>>>(d, f0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return launch_lateral_idft_real(d, d.adj, scale, V, V_dtype, s);
+}
+
 cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const void* D, int D_dtype,
                                double* J, void* gV, double* gc, cudaStream_t s) {
   cudaError_t e;

@@ -119,12 +119,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
   uint64_t* acc_empty = acc_full + 1;      // epilogue -> MMA
   uint64_t* drain = acc_empty + 1;         // final commit: every issued MMA has completed
   uint64_t* tbar = drain + 1;              // [2] row-table bulk copies
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tbar + 2);
+  uint64_t* never = tbar + 2;              // never completed: the wait-test stall
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cta = blockIdx.x;
   const int s0 = d.cta_seg0[cta], s1 = d.cta_seg0[cta + 1];
+  const long long budget = d.wait_cycles > 0 ? d.wait_cycles : WAIT_CYCLES;
   const int* slots = d.cta_seg0 + d.ncta_gram + 1;
 
   // zero every operand stage once: padding rows stay zero for the whole kernel
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     mbar_init(drain, 1);
     mbar_init(&tbar[0], 1);
     mbar_init(&tbar[1], 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -164,19 +167,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     }
     const uint32_t ops_s = smem_u32(ops);
     long long it = 0;
-    bool ok = true;
+    // wait test: a barrier nothing completes, so this wait runs out and the kernel takes its
+    // timeout path (flag raised, producers released through the abort flag, TMEM freed)
+    bool ok = !(d.wait_stall && !mbar_wait(never, 0u, abort_flag, budget));
     for (int si = s0; si < s1 && ok; ++si) {
       const int slot = slots[si];
       const long long nrow = d.seg_nrow[slot];
       const long long nst = (nrow + TC_KC - 1) / TC_KC;
       const int k = si - s0;
       if (k > 0) {
-        if (!mbar_wait(acc_empty, unsigned((k - 1) & 1), abort_flag)) { ok = false; break; }
+        if (!mbar_wait(acc_empty, unsigned((k - 1) & 1), abort_flag, budget)) { ok = false; break; }
         tc_fence_after();
       }
       for (long long st = 0; st < nst; ++st, ++it) {
         const int s = int(it % STAGES);
-        if (!mbar_wait(&full[s], unsigned((it / STAGES) & 1), abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&full[s], unsigned((it / STAGES) & 1), abort_flag, budget)) { ok = false; break; }
         tc_fence_after();
         if (lane == 0) {
           const uint32_t hi = ops_s + uint32_t(s) * NCOMP * stage_bytes;
@@ -206,9 +211,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     // drain: wait (bounded, independent of the abort flag) until every issued MMA is done
     if (lane == 0) {
       mma_commit(drain);
-      const long long t0 = clock64();
-      while (!mbar_try_wait(drain, 0u) && clock64() - t0 < WAIT_CYCLES) {
-      }
+      mbar_drain(drain, 0u);
     }
     __syncwarp();
   } else {
@@ -223,6 +226,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
     // one stage ahead into a double buffer, so it is off the producers' critical path.
     int nsi = s0;                        // (segment, stage) of the next table copy to issue
     long long nst_next = 0;
+    long long tb_issued = 0, tb_done = 0;   // table copies issued (thread 0) and waited for
     auto issue_table = [&](long long it_next) {
       while (nsi < s1) {
         const int sl = slots[nsi];
@@ -236,6 +240,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
           bulk_g2s(tb + TC_KC * sizeof(GramRow), reinterpret_cast<const float4*>(d.rhs) + r,
                    TC_KC * sizeof(float4), &tbar[b]);
           ++nst_next;
+          ++tb_issued;
           return;
         }
         ++nsi;
@@ -255,9 +260,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
       for (long long st = 0; st < nst; ++st, ++it) {
         const int s = int(it % STAGES);
         if (it >= STAGES) {
-          if (!mbar_wait(&empty[s], unsigned(((it / STAGES) - 1) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&empty[s], unsigned(((it / STAGES) - 1) & 1), abort_flag, budget)) { ok = false; break; }
         }
-        if (!mbar_wait(&tbar[it & 1], unsigned((it >> 1) & 1), abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&tbar[it & 1], unsigned((it >> 1) & 1), abort_flag, budget)) { ok = false; break; }
+        tb_done = it + 1;
         const GramRow* rt = reinterpret_cast<const GramRow*>(rowtab + (it & 1) * TAB_BYTES);
         const float4* rdat = reinterpret_cast<const float4*>(rt + TC_KC);
         const int nvalid = int(min((long long)TC_KC, nrow - st * TC_KC));   // rows past it: padding
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
       }
       if (!ok) break;
       // epilogue: accumulator -> FP32 partial tile [col][128 lanes]
-      if (!mbar_wait(acc_full, unsigned((si - s0) & 1), abort_flag)) { ok = false; break; }
+      if (!mbar_wait(acc_full, unsigned((si - s0) & 1), abort_flag, budget)) { ok = false; break; }
       tc_fence_after();
       float* out = d.gpart + size_t(slot) * size_t(ncols) * TC_M;
       const int quarter = warp & 3, group = warp >> 2;   // TMEM lanes 32*quarter..+31
@@ -367,6 +373,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
       for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
       if (lane == 0) atomicAdd(&d.trace[d.seg_m[slot]], tr);
     }
+    // a table copy still in flight after an early exit must land before the CTA leaves
+    if (ptid == 0)
+      for (long long k = tb_done; k < tb_issued; ++k) mbar_drain(&tbar[k & 1], unsigned((k >> 1) & 1));
   }
 
   __syncthreads();
@@ -461,7 +470,7 @@ int tc_cols(int nz) { return cols_of(nzp_of(nz)); }
 int tc_smem_bytes(int nz, int passes) {
   const int zr = zrows_of(nzp_of(nz));
   const int stages = stages_of(passes), ncomp = passes == 1 ? 1 : 2;
-  return 1024 + stages * ncomp * zr * ROWB + 2 * TAB_BYTES + (2 * stages + 5) * 8 + 16;
+  return 1024 + stages * ncomp * zr * ROWB + 2 * TAB_BYTES + (2 * stages + 6) * 8 + 16;
 }
 
 cudaError_t prepare_gram_tc(const Dev& d) {

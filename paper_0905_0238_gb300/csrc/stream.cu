@@ -309,16 +309,19 @@ __global__ void __launch_bounds__(GS_THREADS, 1) st_gram_kernel(StBatch b) {
   uint64_t* acc_full = bars + 2 * GS_STAGES;   // accumulator complete
   uint64_t* acc_empty = acc_full + 1;          // epilogue done reading it
   uint64_t* drain = acc_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* never = drain + 1;                 // never completed: the wait-test stall
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k0 = b.cta_item0[blockIdx.x], k1 = b.cta_item0[blockIdx.x + 1];
+  const long long budget = b.wait_cycles > 0 ? b.wait_cycles : WAIT_CYCLES;
   if (threadIdx.x == 0) {
     for (int s = 0; s < GS_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 128);
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -341,7 +344,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1) st_gram_kernel(StBatch b) {
         const uint32_t bytes = 2 * nb + (diag ? 0u : 2u * GS_A);
         for (int s = 0; s < S.kst; ++s, ++it) {
           const int st = int(it % GS_STAGES);
-          if (it >= GS_STAGES && !mbar_wait(&empty[st], unsigned(((it / GS_STAGES) - 1) & 1), abort_flag)) {
+          if (it >= GS_STAGES &&
+              !mbar_wait(&empty[st], unsigned(((it / GS_STAGES) - 1) & 1), abort_flag, budget)) {
             ok = false;
             break;
           }
@@ -357,25 +361,30 @@ __global__ void __launch_bounds__(GS_THREADS, 1) st_gram_kernel(StBatch b) {
           }
         }
       }
+      // copies of the last GS_STAGES stages may still be in flight after an early exit:
+      // each must land before the CTA leaves
+      for (long long j = it > GS_STAGES ? it - GS_STAGES : 0; j < it; ++j)
+        mbar_drain(&full[j % GS_STAGES], unsigned((j / GS_STAGES) & 1));
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t ops_s = smem_u32(ops);
       long long it = 0;
-      bool ok = true;
+      // wait test: a barrier nothing completes, so the kernel takes its timeout path
+      bool ok = !(b.wait_stall && !mbar_wait(never, 0u, abort_flag, budget));
       for (int k = k0; k < k1 && ok; ++k) {
         const StItem itm = b.items[k];
         const StSub S = b.sub[itm.req];
         const bool last = itm.tj == S.nzt - 1, diag = itm.ti == itm.tj;
         const uint32_t idesc = idesc_bf16(ST_TILE, last ? ST_TILE + ST_DROWS : ST_TILE);
         if (k > k0) {
-          if (!mbar_wait(acc_empty, unsigned((k - k0 - 1) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(acc_empty, unsigned((k - k0 - 1) & 1), abort_flag, budget)) { ok = false; break; }
           tc_fence_after();
         }
         for (int s = 0; s < S.kst; ++s, ++it) {
           const int st = int(it % GS_STAGES);
-          if (!mbar_wait(&full[st], unsigned((it / GS_STAGES) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&full[st], unsigned((it / GS_STAGES) & 1), abort_flag, budget)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sb = ops_s + uint32_t(st) * GS_STAGE;
           const uint32_t bh = sb + 2 * GS_A, bl = bh + GS_B;
@@ -394,16 +403,14 @@ __global__ void __launch_bounds__(GS_THREADS, 1) st_gram_kernel(StBatch b) {
       }
       // drain: every issued MMA has completed before tensor memory is released
       mma_commit(drain);
-      const long long t0 = clock64();
-      while (!mbar_try_wait(drain, 0u) && clock64() - t0 < WAIT_CYCLES) {
-      }
+      mbar_drain(drain, 0u);
     }
     __syncwarp();
   } else {
     // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 = rows of the 128-row tile
     const int qd = warp & 3;
     for (int k = k0; k < k1; ++k) {
-      if (!mbar_wait(acc_full, unsigned((k - k0) & 1), abort_flag)) break;
+      if (!mbar_wait(acc_full, unsigned((k - k0) & 1), abort_flag, budget)) break;
       tc_fence_after();
       const StItem itm = b.items[k];
       const StSub S = b.sub[itm.req];

@@ -134,6 +134,8 @@ struct edt_stream {
     long long batch = -1;            // batch occupying the slot (results not yet delivered)
   } slot[2];
   bool profiling = false;
+  long long wait_cycles = 0;         // wait test (edt_stream_set_wait_test)
+  int wait_stall = 0;
   std::vector<std::pair<double, double>> busy;   // [t0, t1] of delivered batches after the epoch
   double kernel_ms[ST_NKERNEL] = {};
   long long profiled_batches = 0;
@@ -422,6 +424,8 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   b.sub_voff = reinterpret_cast<long long*>(A + o_voff);
   b.sub_order = reinterpret_cast<int*>(A + o_order);
   b.flags = reinterpret_cast<unsigned int*>(A + o_flags);
+  b.wait_cycles = s->wait_cycles;
+  b.wait_stall = s->wait_stall;
   b.tot_z = pre_z[n]; b.tot_fk = pre_fk[n]; b.tot_eb = pre_eb[n]; b.tot_tw = pre_tw[n]; b.tot_rc = pre_rc[n];
   b.cb_nstep = nstep;
   b.cb_act = reinterpret_cast<const int*>(A + o_cbact);
@@ -627,6 +631,13 @@ int edt_stream_get_stats(const edt_stream* s, edt_stream_stats* out) {
 int edt_stream_set_profiling(edt_stream* s, int on) {
   if (!s) return EDT_EINVAL;
   s->profiling = on != 0;
+  return EDT_OK;
+}
+
+int edt_stream_set_wait_test(edt_stream* s, long long wait_cycles, int stall) {
+  if (!s || wait_cycles < 0 || (stall != 0 && stall != 1) || (stall && wait_cycles == 0)) return EDT_EINVAL;
+  s->wait_cycles = wait_cycles;
+  s->wait_stall = stall;
   return EDT_OK;
 }
 

@@ -73,6 +73,8 @@ struct StBatch {
   long long* sub_voff;           // [nreq]
   int* sub_order;                // [nreq] requests by decreasing nz (Cholesky launch order)
   unsigned int* flags;           // [1] tensor-core wait expired
+  long long wait_cycles;         // budget of the Gram's bounded waits (0: about 2 s)
+  int wait_stall;                // wait test: the Gram issuer waits on a barrier nothing completes
   // launch extents (host side)
   long long tot_z, tot_fk, tot_eb, tot_tw, tot_rc;
   // blocked Cholesky: per 32-column step k the active requests (device, [nstep][nreq]), their

@@ -32,15 +32,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: returns false (and raises the abort flag) if the phase never completes.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
+// Bounded wait: returns false (and raises the abort flag) if the phase does not complete
+// within `budget` clock cycles, or as soon as another thread has raised the flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag,
+                                          long long budget = WAIT_CYCLES) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) { *abort_flag = 1; return false; }
+    if (clock64() - t0 > budget) { *abort_flag = 1; return false; }
   }
+}
+// Bounded wait that ignores the abort flag (draining copies or MMAs already in flight).
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, unsigned parity, long long budget = WAIT_CYCLES) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > budget) return false;
+  return true;
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

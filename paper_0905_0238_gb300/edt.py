@@ -47,7 +47,7 @@ class edt_stats(C.Structure):
         ("gram_flop", C.c_double), ("n_notpd", C.c_int), ("n_nonfinite", C.c_int),
         ("last_status", C.c_int), ("launches_per_invert", C.c_int),
         ("gram_rows_padded", C.c_longlong), ("freq_chunk", C.c_int),
-        ("launches_per_grad", C.c_int),
+        ("launches_per_grad", C.c_int), ("gram_timeouts", C.c_int),
     ]
 
 
@@ -104,6 +104,7 @@ def _lib() -> C.CDLL:
         L.edt_invert.argtypes = [vp, vp, i, vp, i, vp]
         L.edt_invert_host.argtypes = [vp, vp, i, vp, i, vp]
         L.edt_forward.argtypes = [vp, vp, i, vp, i, vp]
+        L.edt_adjoint.argtypes = [vp, vp, i, vp, i, vp]
         L.edt_green.argtypes = [vp, vp, vp]
         L.edt_get_vhat.argtypes = [vp, vp, vp]
         L.edt_row_counts.argtypes = [vp, C.POINTER(C.c_longlong)]
@@ -122,6 +123,7 @@ def _lib() -> C.CDLL:
         L.edt_misfit_grad.argtypes = [vp, vp, i, vp, i, vp, vp, vp, vp]
         L.edt_invert_adjoint.argtypes = [vp, vp, i, vp, i, vp]
         L.edt_set_host_pipeline.argtypes = [vp, i]
+        L.edt_set_wait_test.argtypes = [vp, C.c_longlong, i]
         L.edt_set_reference.argtypes = [vp, C.POINTER(d), vp]
         L.edt_strerror.argtypes = [i]
         L.edt_strerror.restype = C.c_char_p
@@ -129,11 +131,11 @@ def _lib() -> C.CDLL:
         L.edt_destroy.argtypes = [vp]
         L.edt_destroy.restype = None
         for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
-                     "edt_forward", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
+                     "edt_forward", "edt_adjoint", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
                      "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning",
                      "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint",
-                     "edt_set_host_pipeline"):
+                     "edt_set_host_pipeline", "edt_set_wait_test"):
             getattr(L, name).restype = i
         ll = C.c_longlong
         L.edt_kz_disk_columns.argtypes = [vp, C.POINTER(i)]
@@ -149,12 +151,14 @@ def _lib() -> C.CDLL:
         L.edt_stream_epoch.argtypes = [vp]
         L.edt_stream_get_stats.argtypes = [vp, C.POINTER(edt_stream_stats)]
         L.edt_stream_set_profiling.argtypes = [vp, i]
+        L.edt_stream_set_wait_test.argtypes = [vp, C.c_longlong, i]
         L.edt_stream_read_profile.argtypes = [vp, C.POINTER(d), C.POINTER(C.c_char_p), i, C.POINTER(ll)]
         L.edt_stream_destroy.argtypes = [vp]
         L.edt_stream_destroy.restype = None
         for name in ("edt_stream_plan", "edt_stream_create", "edt_stream_set_workspace",
                      "edt_stream_submit", "edt_stream_wait", "edt_stream_query", "edt_stream_epoch",
-                     "edt_stream_get_stats", "edt_stream_set_profiling", "edt_stream_read_profile"):
+                     "edt_stream_get_stats", "edt_stream_set_profiling", "edt_stream_read_profile",
+                     "edt_stream_set_wait_test"):
             getattr(L, name).restype = i
         _LIB = L
     return _LIB
@@ -190,6 +194,11 @@ def edt_invert_host(ctx, D_ptr: int, D_dtype: int, V_ptr: int, V_dtype: int, str
 def edt_forward(ctx, V_ptr: int, V_dtype: int, D_ptr: int, D_dtype: int, stream: int):
     _check(_lib().edt_forward(ctx, C.c_void_p(V_ptr), V_dtype, C.c_void_p(D_ptr), D_dtype,
                               C.c_void_p(stream)), "edt_forward")
+
+
+def edt_adjoint(ctx, D_ptr: int, D_dtype: int, V_ptr: int, V_dtype: int, stream: int):
+    _check(_lib().edt_adjoint(ctx, C.c_void_p(D_ptr), D_dtype, C.c_void_p(V_ptr), V_dtype,
+                              C.c_void_p(stream)), "edt_adjoint")
 
 
 def edt_green(ctx, g_ptr: int, stream: int):
@@ -288,6 +297,10 @@ def edt_set_reference(ctx, vel: np.ndarray, stream: int):
     v = np.ascontiguousarray(vel, dtype=np.float64)
     _check(_lib().edt_set_reference(ctx, v.ctypes.data_as(C.POINTER(C.c_double)),
                                     C.c_void_p(stream)), "edt_set_reference")
+
+
+def edt_set_wait_test(ctx, wait_cycles: int, stall: bool):
+    _check(_lib().edt_set_wait_test(ctx, int(wait_cycles), int(bool(stall))), "edt_set_wait_test")
 
 
 def edt_destroy(ctx):
@@ -427,6 +440,16 @@ class Solver:
                     self._stream())
         return D
 
+    def adjoint(self, D, out_dtype=None):
+        """V = F^T D, the adjoint Born operator (see edt_adjoint)."""
+        torch = self._torch
+        nf = len(self._freq)
+        if not (D.is_cuda and D.is_contiguous()) or tuple(D.shape) != self.cfg.data_shape(nf):
+            raise ValueError(f"D must be a contiguous CUDA tensor of shape {self.cfg.data_shape(nf)}")
+        V = torch.empty(self.cfg.model_shape(), device=self.device, dtype=out_dtype or torch.float64)
+        edt_adjoint(self.ctx, D.data_ptr(), self._cdtype(D), V.data_ptr(), self._rdtype(V), self._stream())
+        return V
+
     def misfit_grad(self, V, D):
         """(J, dJ/dV, dJ/dc) of J = ||F V - D||^2 (see edt_misfit_grad): J a 0-d float64
         device tensor, dJ/dV of V's shape and dtype, dJ/dc float64 [nlayer] on the device."""
@@ -518,6 +541,10 @@ class Solver:
     def set_profiling(self, on=True):
         edt_set_profiling(self.ctx, on)
 
+    def set_wait_test(self, wait_cycles=0, stall=False):
+        """Test hook: short bounded-wait budget and a Gram stall (see edt_set_wait_test)."""
+        edt_set_wait_test(self.ctx, wait_cycles, stall)
+
     def read_profile(self):
         return edt_read_profile(self.ctx)
 
@@ -608,6 +635,11 @@ def edt_stream_set_profiling(ctx, on: bool):
     _check(_lib().edt_stream_set_profiling(ctx, int(bool(on))), "edt_stream_set_profiling")
 
 
+def edt_stream_set_wait_test(ctx, wait_cycles: int, stall: bool):
+    _check(_lib().edt_stream_set_wait_test(ctx, int(wait_cycles), int(bool(stall))),
+           "edt_stream_set_wait_test")
+
+
 def edt_stream_read_profile(ctx, max_kernels: int = 8):
     """({kernel name: summed ms}, batches covered) since the last read."""
     ms = (C.c_double * max_kernels)()
@@ -663,6 +695,10 @@ class Stream:
 
     def set_profiling(self, on=True):
         edt_stream_set_profiling(self.ctx, on)
+
+    def set_wait_test(self, wait_cycles=0, stall=False):
+        """Test hook: short bounded-wait budget and a Gram stall (see edt_stream_set_wait_test)."""
+        edt_stream_set_wait_test(self.ctx, wait_cycles, stall)
 
     def read_profile(self):
         return edt_stream_read_profile(self.ctx)

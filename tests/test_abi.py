@@ -203,3 +203,26 @@ def test_green_noalloc_rejects_oversized_coefficients_without_gpu():
     with pytest.raises(edt.EdtError) as ei:
         edt.edt_green_noalloc(48, 12.5, 16, 50.0, 0.0, np.array([10.0]), 0.15, tops, vel, 0x1000, 0)
     assert ei.value.code == edt.EDT_EINVAL
+
+
+def test_wait_test_hook_validates_on_the_host():
+    """edt_set_wait_test is host-only: a stall needs a positive budget; negative budgets and
+    other stall values are refused."""
+    import numpy as np
+    from paper_0905_0238_gb300 import edt
+    freq = np.array([5.0, 10.0]); top = np.array([0.0, 100.0]); vel = np.array([1500.0, 2000.0])
+    dp = ctypes.POINTER(ctypes.c_double)
+    cfg = edt.edt_config(nx=32, dx=10.0, nz=16, dz=10.0, z0=0.0, nfreq=2, freq_hz=freq.ctypes.data_as(dp),
+                         eps=0.15, nlayer=2, layer_top_m=top.ctypes.data_as(dp),
+                         layer_vel_mps=vel.ctypes.data_as(dp), precision=edt.EDT_MIXED, passes=3,
+                         refine=1, alpha=1e-2, cutoff=1.0, fold=1)
+    ctx, _ = edt.edt_create(cfg)
+    try:
+        edt.edt_set_wait_test(ctx, 1000, True)
+        edt.edt_set_wait_test(ctx, 0, False)
+        for cyc, stall in ((0, True), (-1, False)):
+            with pytest.raises(edt.EdtError) as ei:
+                edt.edt_set_wait_test(ctx, cyc, stall)
+            assert ei.value.code == edt.EDT_EINVAL
+    finally:
+        edt.edt_destroy(ctx)
