@@ -122,9 +122,12 @@ typedef struct {
   int fold;                     /* 1: merge the identical reciprocal rows (p,q),(-q,-p)
                                    into one row of weight 2 (same normal equations);
                                    0: keep every row as the paper writes them           */
-  int chol_df;                  /* mixed path only: 1 = Cholesky trailing updates in
-                                   double-float (FP32 hi/lo pairs, ~48-bit) on the FP32
-                                   pipes, 0 = native FP64 everywhere (default)          */
+  int chol_df;                  /* mixed path only: the damped Cholesky factorisation and
+                                   solves in double-float (FP32 hi/lo pairs, ~48-bit,
+                                   error-free products and sums) on the FP32 pipes with
+                                   FP64 pivots (1, and 0 = automatic, the default), or
+                                   native FP64 throughout (2); the FP64 path always
+                                   factors in native FP64                               */
   int freq_chunk;               /* frequency planes per chunk of the data transform and
                                    the forward model (the spectrum buffer holds one
                                    chunk); 0 = automatic: as many planes as fit in
@@ -318,6 +321,13 @@ int edt_set_reference(edt_ctx* ctx, const double* layer_vel_mps, void* stream);
 /* Reference Green's function table g(k_n, z_j; omega~_f), n = 0..nx/2, as complex128
  * [nfreq][nx/2+1][nz] (computed in FP64 by the depth march). */
 int edt_green(edt_ctx* ctx, void* g_dev, void* stream);
+
+/* Copy the Cholesky factors of the last edt_invert on this context, G + lam I = L L^T per
+ * subproblem, as double [n_sub][nz][nz] into caller device memory: the lower triangle and
+ * the diagonal hold L (row-major), the strict upper triangle is unspecified.  EDT_EINVAL if
+ * no factorisation is held (no edt_invert since the workspace, reference or a stage call
+ * changed it, or a solver variant without a Cholesky ran). */
+int edt_get_factor(edt_ctx* ctx, void* L_dev, void* stream);
 
 /* Copy Vhat(k_m, z_j) of the last edt_invert on this context, m = 0..nx/2, as
  * complex128 [nx/2+1][nz], into caller device memory. */

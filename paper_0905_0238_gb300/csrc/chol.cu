@@ -634,18 +634,17 @@ cudaError_t prepare_chol(const Dev& d) {
   cudaError_t e = cudaFuncSetAttribute(chol_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(chol_smem(d.nz)));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(chol_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(chol_smem(d.nz)));
+  return prepare_chol_dfloat(d);
 }
 
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
-  size_t smem = chol_smem(d.nz);
-  if (d.chol_df) chol_kernel<true, false><<<d.nsub, 256, smem, s>>>(d, trace_mode);
-  else chol_kernel<false, false><<<d.nsub, 256, smem, s>>>(d, trace_mode);
+  if (d.chol_df) return launch_chol_dfloat(d, trace_mode, s);
+  chol_kernel<false, false><<<d.nsub, 256, chol_smem(d.nz), s>>>(d, trace_mode);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chol_resolve(const Dev& d, cudaStream_t s) {
+  if (d.chol_df) return launch_chol_dfloat_resolve(d, s);
   chol_solve_kernel<false><<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 0);
   return cudaGetLastError();
 }

@@ -1,0 +1,479 @@
+// Damped normal-equation solves (G + lam I) x_+- = b_+-, lam = alpha * trace(G), with the
+// factorisation carried in double-float arithmetic on the FP32 pipes.
+//
+// GB300 runs FP64 at 1/59 of the FP32 rate, so an FP64 Cholesky of 257 systems of 256
+// unknowns is bound by the FP64 pipe.  Here every value of the working matrix is held as an
+// unevaluated sum h + l of two floats (about 48 significant bits), in place of the FP64
+// matrix (the same 8 bytes per element), and the n^3/3 multiply-adds run on the FP32 pipes
+// with error-free transformations: each product a_h b_h is split exactly by fma (Dekker's
+// TwoProduct with a hardware fma), each addition's rounding error is captured by Knuth's
+// TwoSum, and the low parts collect the errors and the cross terms; the pivots' reciprocal
+// square roots take an FP32 estimate and one Newton step in double-float.  No FP64 arithmetic
+// remains in the factorisation.
+//
+// Blocked right-looking form over all subproblems at once, so that every step fills the GPU
+// (one CTA per subproblem would leave the serial parts of each factorisation on its SM's
+// critical path and 257 systems unevenly spread over 152 SMs):
+//   * the Gram reduction has written the lower triangle of G + lam I in double-float;
+//   * per 32-column step: cdf_diag factors and inverts the step's 32 x 32 diagonal block of
+//     every subproblem (1024 threads, one element each); cdf_panel multiplies the panel rows
+//     by the inverse (x = a L_kk^-T, independent outputs); cdf_update subtracts P P^T from the
+//     trailing lower triangle in 64 x 64 tiles of every subproblem (the panel staged
+//     transposed in shared memory, each thread a 4 x 4 interleaved register tile);
+//   * cdf_final: forward and backward substitution for both right-hand sides in
+//     double-float, each diagonal block by its inverse; the factor stays in double-float (the re-solve of the inversion adjoint
+//     and the factor export read the pairs), its high parts are written as the FP32 copy for
+//     the refinement's correction solves.
+// A non-positive or non-finite pivot marks the subproblem EDT_ENOTPD and zeroes its solution.
+#include "edt_internal.h"
+
+namespace edt {
+
+namespace {
+
+constexpr int FB = 32, FLD = FB + 1, FTHREADS = 256;
+constexpr int UT = 64, ULD = UT + 1;   // update tile and its padded shared row
+
+// ---- double-float arithmetic (float2: .x high part, .y low part) ----------------------------
+// The _rn intrinsics keep the compiler from contracting the error-free steps into fma.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 df_norm(float2 a) { return fast_two_sum(a.x, a.y); }
+__device__ __forceinline__ float2 df_of(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - double(h)));
+}
+__device__ __forceinline__ double df_val(float2 a) { return double(a.x) + double(a.y); }
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
+  return fast_two_sum(p, e);
+}
+// accumulator s (high sum, low sum; not normalised) += a * b
+__device__ __forceinline__ void df_acc(float2& s, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
+  const float2 t = two_sum(s.x, p);
+  s.x = t.x;
+  s.y = __fadd_rn(s.y, __fadd_rn(t.y, e));
+}
+__device__ __forceinline__ float2 shfl_df(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Solve L L^T y = sb for two right-hand sides (sb[i][0..1], double-float).  L is lower, double-
+// float in A (ld n); each 32 x 32 diagonal block also holds its inverse X = L_kk^-1 in its strict
+// upper triangle (X_il at (l, i)) with the diagonal 1 / L_ii in sInv, so every block solve is a
+// parallel matrix-vector product (warp k: right-hand side k, lane: row) instead of a sequential
+// chain, and the off-diagonal blocks are applied by thread-per-row (forward) or coalesced
+// column (backward) sweeps.  sX: [FB][FLD] shared scratch.
+__device__ void solve_df_2rhs(const float2* A, const float2* sInv, int n, float2* sb, float2* sX) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nblk = (n + FB - 1) / FB;
+  auto load_x = [&](int k0, int kb) {          // sX[i * FLD + l] = X_il (lower, with the diagonal)
+    constexpr int Q = FB * FB / FTHREADS;
+    float2 v[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int e = threadIdx.x + FTHREADS * q, i = e / FB, l = e - i * FB;
+      v[q] = make_float2(0.f, 0.f);
+      if (i < kb && l < kb) {
+        if (l < i) v[q] = A[size_t(k0 + l) * n + k0 + i];
+        else if (l == i) v[q] = sInv[k0 + i];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int e = threadIdx.x + FTHREADS * q, i = e / FB, l = e - i * FB;
+      sX[i * FLD + l] = v[q];
+    }
+  };
+  for (int bk = 0; bk < nblk; ++bk) {                       // forward: L y = b
+    const int k0 = bk * FB, kb = min(FB, n - k0);
+    load_x(k0, kb);
+    __syncthreads();
+    float2 y = make_float2(0.f, 0.f);
+    if (warp < 2 && lane < kb) {                            // y_blk = X b_blk
+      for (int l = 0; l <= lane; ++l) df_acc(y, sX[lane * FLD + l], sb[(k0 + l) * 2 + warp]);
+    }
+    __syncthreads();
+    if (warp < 2 && lane < kb) sb[(k0 + lane) * 2 + warp] = df_norm(y);
+    __syncthreads();
+    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {   // b_i -= L[i][blk] . y
+      float2 s0 = sb[i * 2], s1 = sb[i * 2 + 1];
+      const float2* Ai = A + size_t(i) * n + k0;
+      float2 av[FB];                                                  // loads in flight together
+#pragma unroll
+      for (int l = 0; l < FB; ++l) av[l] = l < kb ? Ai[l] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int l = 0; l < FB; ++l) {
+        if (l < kb) {
+          const float2 a = df_neg(av[l]);
+          df_acc(s0, a, sb[(k0 + l) * 2]);
+          df_acc(s1, a, sb[(k0 + l) * 2 + 1]);
+        }
+      }
+      sb[i * 2] = df_norm(s0); sb[i * 2 + 1] = df_norm(s1);
+    }
+    __syncthreads();
+  }
+  for (int bk = nblk - 1; bk >= 0; --bk) {                  // backward: L^T x = y
+    const int k0 = bk * FB, kb = min(FB, n - k0);
+    load_x(k0, kb);
+    __syncthreads();
+    float2 x = make_float2(0.f, 0.f);
+    if (warp < 2 && lane < kb) {                            // x_blk = X^T y_blk
+      for (int i = lane; i < kb; ++i) df_acc(x, sX[i * FLD + lane], sb[(k0 + i) * 2 + warp]);
+    }
+    __syncthreads();
+    if (warp < 2 && lane < kb) sb[(k0 + lane) * 2 + warp] = df_norm(x);
+    __syncthreads();
+    for (int i = threadIdx.x; i < k0; i += blockDim.x) {    // y_i -= sum_l L[k0+l][i] x_l
+      float2 s0 = sb[i * 2], s1 = sb[i * 2 + 1];
+      float2 av[FB];
+#pragma unroll
+      for (int l = 0; l < FB; ++l) av[l] = l < kb ? A[size_t(k0 + l) * n + i] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int l = 0; l < FB; ++l) {
+        if (l < kb) {
+          const float2 a = df_neg(av[l]);
+          df_acc(s0, a, sb[(k0 + l) * 2]);
+          df_acc(s1, a, sb[(k0 + l) * 2 + 1]);
+        }
+      }
+      sb[i * 2] = df_norm(s0); sb[i * 2 + 1] = df_norm(s1);
+    }
+    __syncthreads();
+  }
+}
+
+// 1 / sqrt(a) for a double-float a > 0: the FP32 estimate y0 and one Newton step carried in
+// double-float, y = y0 + y0 (1 - a y0^2) / 2 (the step doubles the ~23 correct bits).
+__device__ __forceinline__ float2 df_rsqrt(float2 a) {
+  const float y0 = rsqrtf(a.x);
+  const float2 y2 = df_mul(make_float2(y0, 0.f), make_float2(y0, 0.f));
+  const float2 r = df_add(make_float2(1.f, 0.f), df_neg(df_mul(a, y2)));   // 1 - a y0^2, small
+  return fast_two_sum(y0, 0.5f * y0 * r.x);
+}
+
+__device__ __forceinline__ bool has_rows(const Dev& d, int m) { return d.row_off[m + 1] > d.row_off[m]; }
+
+// Diagonal block of step k0 of every subproblem, factored and inverted in double-float by 1024
+// threads, thread (i, l) holding element (i, l): per column j the pivot's 1 / sqrt, the column
+// scale and the rank-1 update of the trailing block each take one step between barriers (the
+// column of L double-buffered in shared memory so that one step's readers and the next step's
+// writers never meet); then X = L_kk^-1 by the same right-looking sweep over the identity.
+// Writes L_kk (lower triangle), X (strict upper triangle, X_il at (l, i)) and the reciprocal
+// pivots (FP64) to dinv.  At k0 = 0 the status is set and the trace slot takes lam from here on.
+__global__ void __launch_bounds__(1024) cdf_diag_kernel(Dev d, int k0) {
+  __shared__ float2 sCol[2][FB], sInv[FB], sXr[2][FB];
+  __shared__ float2 sLf[FB * FLD];
+  __shared__ int fail;
+  const int m = blockIdx.x, n = d.nz;
+  if (!has_rows(d, m) || (k0 > 0 && d.status[m] != EDT_OK)) return;
+  const int kb = min(FB, n - k0);
+  const int i = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const bool in = i < kb && l <= i;
+  float2* A = reinterpret_cast<float2*>(d.G + size_t(m) * n * n);
+  float2 a = in ? A[size_t(k0 + i) * n + k0 + l] : make_float2(0.f, 0.f);
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    float2* col = sCol[j & 1];
+    if (i == j && l == j) {
+      const float2 djj = df_norm(a);
+      if (!(djj.x > 0.f) || !isfinite(djj.x)) {
+        fail = 1;
+      } else {
+        const float2 inv = df_rsqrt(djj);
+        a = df_mul(djj, inv);
+        sInv[j] = inv;
+        col[j] = a;
+      }
+    }
+    __syncthreads();
+    if (fail) break;                                  // the same value in every thread
+    if (l == j && i > j && i < kb) { a = df_mul(df_norm(a), sInv[j]); col[i] = a; }
+    __syncthreads();
+    if (l > j && i >= l && i < kb) df_acc(a, df_neg(col[i]), col[l]);
+  }
+  if (fail) {
+    if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
+    return;
+  }
+  a = df_norm(a);
+  if (in) { A[size_t(k0 + i) * n + k0 + l] = a; sLf[i * FLD + l] = a; }
+  if (threadIdx.x < kb) d.dinv[size_t(m) * n + k0 + threadIdx.x] = df_val(sInv[threadIdx.x]);
+  __syncthreads();
+  // X = L^-1: right-looking forward substitution on the identity, row k final at step k
+  float2 x = make_float2(i == l ? 1.f : 0.f, 0.f);
+  for (int k = 0; k < kb; ++k) {
+    float2* xr = sXr[k & 1];
+    if (i == k) {
+      if (l <= k) x = df_mul(df_norm(x), sInv[k]);
+      xr[l] = l <= k ? x : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (i > k && i < kb && l <= k) df_acc(x, df_neg(sLf[i * FLD + k]), xr[l]);
+  }
+  if (i < kb && l < i) A[size_t(k0 + l) * n + k0 + i] = df_norm(x);
+  if (threadIdx.x == 0) {
+    if (k0 == 0) { d.trace[m] = d.alpha * d.trace[m]; d.status[m] = EDT_OK; }
+  }
+}
+
+// Panel rows r0 .. r0 + 31 of subproblem blockIdx.y: x = a L_kk^-T = a X^T, x_j = sum_{l <= j}
+// a_l X_jl, all outputs independent.  Warp h of four computes the outputs j = h (mod 4) of all
+// 32 rows (lane = row): the rows sit transposed in shared memory (conflict-free), X is read by
+// broadcast.
+__global__ void __launch_bounds__(128) cdf_panel_kernel(Dev d, int k0) {
+  __shared__ float2 sA[FB * FLD], sX[FB * FLD];
+  const int m = blockIdx.y, n = d.nz;
+  if (!has_rows(d, m) || d.status[m] != EDT_OK) return;
+  const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+  float2* A = reinterpret_cast<float2*>(d.G + size_t(m) * n * n);
+  const int r0 = k0 + FB + blockIdx.x * 32, nr = min(32, n - r0);
+  {
+    constexpr int Q = FB / 4;
+    float2 av[Q], xv[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int r = h + 4 * q;                      // a warp: one row's 32 columns (coalesced)
+      av[q] = r < nr ? A[size_t(r0 + r) * n + k0 + lane] : make_float2(0.f, 0.f);
+      // X_{r, lane} from the upper triangle (at (lane, r)); the diagonal from dinv
+      xv[q] = lane < r ? A[size_t(k0 + lane) * n + k0 + r]
+                       : (lane == r ? df_of(d.dinv[size_t(m) * n + k0 + r]) : make_float2(0.f, 0.f));
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int r = h + 4 * q;
+      sA[lane * FLD + r] = av[q];
+      sX[r * FLD + lane] = xv[q];
+    }
+  }
+  __syncthreads();
+  float2 out[FB / 4];
+#pragma unroll
+  for (int q = 0; q < FB / 4; ++q) {
+    const int j = h + 4 * q;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int l = 0; l <= j; ++l) df_acc(acc, sA[l * FLD + lane], sX[j * FLD + l]);
+    out[q] = df_norm(acc);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < FB / 4; ++q) sA[(h + 4 * q) * FLD + lane] = out[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < FB / 4; ++q) {
+    const int r = h + 4 * q;
+    if (r < nr) A[size_t(r0 + r) * n + k0 + lane] = sA[lane * FLD + r];
+  }
+}
+
+// Trailing update of step k0: tile (I, J), I >= J, of 64 x 64 elements of the lower triangle
+// of rows / columns t0 = k0 + 32 .. n - 1 of subproblem blockIdx.y loses P_I P_J^T, P the
+// step's panel.  Thread (ty, tx) owns rows ty + 16 u and columns tx + 16 v (u, v < 4):
+// interleaved, so the shared panel reads are conflict-free and the global rows coalesced.
+__global__ void __launch_bounds__(256) cdf_update_kernel(Dev d, int k0) {
+  __shared__ float2 sI[FB * ULD], sJ[FB * ULD];   // transposed panel rows: [l][i]
+  const int m = blockIdx.y, n = d.nz;
+  if (!has_rows(d, m) || d.status[m] != EDT_OK) return;
+  const int t0 = k0 + FB;
+  const int pt = blockIdx.x;
+  int I = int((sqrtf(8.0f * pt + 1.0f) - 1.0f) * 0.5f);
+  while (I * (I + 1) / 2 > pt) --I;
+  while ((I + 1) * (I + 2) / 2 <= pt) ++I;
+  const int J = pt - I * (I + 1) / 2;
+  const int r0 = t0 + UT * I, c0 = t0 + UT * J;
+  float2* A = reinterpret_cast<float2*>(d.G + size_t(m) * n * n);
+  {
+    constexpr int NL = UT * FB / 256;              // 8 elements of each panel per thread
+    float2 vi[NL], vj[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + 256 * q, i = e / FB, l = e - i * FB;   // a warp: one row's 32 columns
+      vi[q] = r0 + i < n ? A[size_t(r0 + i) * n + k0 + l] : make_float2(0.f, 0.f);
+      vj[q] = c0 + i < n ? A[size_t(c0 + i) * n + k0 + l] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + 256 * q, i = e / FB, l = e - i * FB;
+      sI[l * ULD + i] = vi[q];
+      sJ[l * ULD + i] = vj[q];
+    }
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool diag = I == J;
+  float2 acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
+  for (int l = 0; l < FB; ++l) {
+    float2 pi[4], pj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { pi[u] = sI[l * ULD + ty + 16 * u]; pj[u] = sJ[l * ULD + tx + 16 * u]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r0 + ty + 16 * u < n)                                 // rows past n: nothing to update
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (!(diag && u < v)) df_acc(acc[u][v], pi[u], pj[v]);   // above the diagonal: unused
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = r0 + ty + 16 * u, j = c0 + tx + 16 * v;
+      if (i < n && j <= i && !(diag && u < v)) {
+        float2* a = A + size_t(i) * n + j;
+        *a = df_add(*a, df_neg(df_norm(acc[u][v])));
+      }
+    }
+}
+
+// Both substitutions and the solution; the factor stays in double-float (its readers take
+// the pairs), its high parts are the FP32 copy for the refinement's correction solves.
+__global__ void __launch_bounds__(FTHREADS) cdf_final_kernel(Dev d) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int m = blockIdx.x, n = d.nz;
+  const size_t go = size_t(m) * n * n, vo = size_t(m) * n;
+  float2* sb = reinterpret_cast<float2*>(smraw);            // [n][2]
+  float2* sInv = sb + 2 * n;                                // [n]
+  float2* sL = sInv + n;                                    // [FB][FLD]
+  double* xo = d.x + vo * 2;
+  if (!has_rows(d, m)) {
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    if (threadIdx.x == 0) { d.status[m] = EDT_OK; d.trace[m] = 0.0; }
+    return;
+  }
+  if (d.status[m] != EDT_OK) {
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    return;
+  }
+  const float2* A = reinterpret_cast<const float2*>(d.G + go);
+  float* L32 = d.L32 ? d.L32 + go : nullptr;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) sb[i] = df_of(d.b[vo * 2 + i]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double inv = d.dinv[vo + i];
+    sInv[i] = df_of(inv);
+    if (L32) d.dinv32[vo + i] = float(inv);
+  }
+  __syncthreads();
+  solve_df_2rhs(A, sInv, n, sb, sL);
+  bool bad = false;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+    const double v = df_val(sb[i]);
+    xo[i] = v;
+    if (!isfinite(v)) bad = true;
+  }
+  bad = __syncthreads_or(bad);
+  if (L32) {
+    // batches of eight loads before their stores (L32 and A may alias for the compiler)
+    const size_t tot = size_t(n) * n;
+    for (size_t e0 = threadIdx.x; e0 < tot; e0 += 8 * size_t(blockDim.x)) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const size_t e = e0 + size_t(q) * blockDim.x;
+        v[q] = e < tot ? A[e].x : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const size_t e = e0 + size_t(q) * blockDim.x;
+        if (e < tot) {
+          const int i = int(e / n), j = int(e - size_t(i) * n);
+          if (j <= i) L32[e] = v[q];
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && bad) d.status[m] = EDT_ENONFINITE;
+}
+
+// x = (L L^T)^-1 b with the double-float factor of the last factorisation (no refactorisation):
+// the inversion adjoint's re-solve.
+__global__ void __launch_bounds__(FTHREADS) cdf_resolve_kernel(Dev d) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int m = blockIdx.x, n = d.nz;
+  const size_t vo = size_t(m) * n;
+  float2* sb = reinterpret_cast<float2*>(smraw);
+  float2* sInv = sb + 2 * n;
+  float2* sL = sInv + n;
+  double* xo = d.x + vo * 2;
+  if (!has_rows(d, m) || d.status[m] != EDT_OK) {
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    return;
+  }
+  const float2* A = reinterpret_cast<const float2*>(d.G + size_t(m) * n * n);
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) sb[i] = df_of(d.b[vo * 2 + i]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sInv[i] = df_of(d.dinv[vo + i]);
+  __syncthreads();
+  solve_df_2rhs(A, sInv, n, sb, sL);
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = df_val(sb[i]);
+}
+
+// The double-float factor as FP64 [nsub][n][n] (lower triangle) into out.
+__global__ void cdf_export_kernel(Dev d, double* out) {
+  const size_t total = size_t(d.nsub) * d.nz * d.nz;
+  const float2* A = reinterpret_cast<const float2*>(d.G);
+  for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += size_t(gridDim.x) * blockDim.x) {
+    const size_t r = e % (size_t(d.nz) * d.nz);
+    const int i = int(r / d.nz), j = int(r - size_t(i) * d.nz);
+    out[e] = j <= i ? df_val(A[e]) : 0.0;
+  }
+}
+
+size_t cdf_final_smem(int n) { return size_t(3 * n + FB * FLD) * sizeof(float2); }
+
+}  // namespace
+
+int chol_dfloat_launches(int n) { return 1 + (n + FB - 1) / FB + 2 * ((n > FB) ? (n - 1) / FB : 0); }
+
+cudaError_t prepare_chol_dfloat(const Dev& d) {
+  cudaError_t e = cudaFuncSetAttribute(cdf_final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(cdf_final_smem(d.nz)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cdf_resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(cdf_final_smem(d.nz)));
+}
+
+cudaError_t launch_chol_dfloat_resolve(const Dev& d, cudaStream_t s) {
+  cdf_resolve_kernel<<<d.nsub, FTHREADS, cdf_final_smem(d.nz), s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_dfloat_export(const Dev& d, double* out, cudaStream_t s) {
+  cdf_export_kernel<<<4 * 152, 256, 0, s>>>(d, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s) {
+  (void)trace_mode;                       // the Gram reduction has added lam = alpha * trace
+  const int n = d.nz;
+  for (int k0 = 0; k0 < n; k0 += FB) {
+    cdf_diag_kernel<<<d.nsub, 1024, 0, s>>>(d, k0);
+    if (k0 + FB >= n) break;
+    const int t = n - k0 - FB, nt = (t + UT - 1) / UT;
+    cdf_panel_kernel<<<dim3((t + 31) / 32, d.nsub), 128, 0, s>>>(d, k0);
+    cdf_update_kernel<<<dim3(nt * (nt + 1) / 2, d.nsub), 256, 0, s>>>(d, k0);
+  }
+  cdf_final_kernel<<<d.nsub, FTHREADS, cdf_final_smem(n), s>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace edt

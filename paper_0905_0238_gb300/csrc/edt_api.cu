@@ -165,7 +165,7 @@ int validate(const edt_config* c) {
   if (!(c->alpha >= 0) || !std::isfinite(c->alpha)) return EDT_EINVAL;
   if (!std::isfinite(c->cutoff)) return EDT_EINVAL;
   if (c->fold != 0 && c->fold != 1) return EDT_EINVAL;
-  if (c->chol_df != 0 && c->chol_df != 1) return EDT_EINVAL;
+  if (c->chol_df < 0 || c->chol_df > 2) return EDT_EINVAL;
   if (c->freq_chunk < 0 || c->gram_seg_rows < 0) return EDT_EINVAL;
   if (c->resid < 0 || c->resid > 2) return EDT_EINVAL;
   if (c->resid == 2 && (c->geometry == EDT_GEOM_WINDOW || c->precision != EDT_MIXED)) return EDT_EUNSUPPORTED;
@@ -647,7 +647,8 @@ void bind(edt_ctx* c) {
   d.N = c->N; d.nk = c->nk; d.nz = c->nz; d.nf = c->nf; d.nsub = c->nsub; d.nlayer = c->nlayer;
   d.nzs = (c->nz + 1) & ~1;
   d.precision = c->cfg.precision; d.passes = c->cfg.passes; d.fold = c->cfg.fold;
-  d.chol_df = c->cfg.precision == EDT_MIXED ? c->cfg.chol_df : 0;
+  // the mixed path factors in double-float unless native FP64 is asked for (chol_df = 2)
+  d.chol_df = c->cfg.precision == EDT_MIXED && c->cfg.chol_df != 2 ? 1 : 0;
   d.alpha = c->cfg.alpha; d.dx = c->cfg.dx; d.dz = c->cfg.dz;
   d.fc = at<const FreqConst*>(c, c->r_fc);
   d.layer_top = at<const double*>(c, c->r_ltop);
@@ -828,7 +829,7 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
     EDT_TRY(launch_gram_tc(d, s));
     prof_ev(c, 4, 1, s);
     prof_ev(c, 5, 0, s);
-    EDT_TRY(launch_gram_reduce(d, s));
+    EDT_TRY(launch_gram_reduce(d, s, d.chol_df && !c->variant));
   } else {
     EDT_TRY(launch_gram_f64(d, s));
     prof_ev(c, 4, 1, s);
@@ -1246,6 +1247,16 @@ int edt_green(edt_ctx* c, void* g_dev, void* stream) {
   return EDT_OK;
 }
 
+int edt_get_factor(edt_ctx* c, void* L_dev, void* stream) {
+  if (!c || !L_dev) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (!c->have_factor || c->variant) return EDT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c->dev.chol_df) EDT_TRY(launch_chol_dfloat_export(c->dev, static_cast<double*>(L_dev), s));
+  else EDT_TRY(cudaMemcpyAsync(L_dev, c->dev.G, c->r_G.bytes, cudaMemcpyDeviceToDevice, s));
+  return EDT_OK;
+}
+
 int edt_get_vhat(edt_ctx* c, void* vhat_dev, void* stream) {
   if (!c || !vhat_dev) return EDT_EINVAL;
   if (!c->ws) return EDT_ENOMEM_WS;
@@ -1314,8 +1325,9 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
     tr_launches = 0;
     for (const BandChunk& ch : c->bchunks) tr_launches += 1 + (ch.nbcol > 0) + (ch.nrow > 0);
   }
+  const int chol_n = c->dev.chol_df ? chol_dfloat_launches(c->nz) : chol_launches(c->nz);
   o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + tr_launches +
-                           chol_launches(c->nz) + gram_scale_launches(c->dev);
+                           chol_n + gram_scale_launches(c->dev);
   // solver variants replace the Cholesky launch: trace, two projections, the solve (Cholesky
   // or Jacobi), the back-projection with the disk; the Jacobi kernel alone without it
   if (c->variant) o->launches_per_invert += (c->kz_p.empty() ? 1 : 5) - chol_launches(c->nz);
@@ -1324,7 +1336,7 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
     // refinement (2 per step), inverse (completion, FP64 row and column transforms, output: 3 or 4)
     int fk = 0;
     for (int n : c->nact) fk += n > 0;
-    o->launches_per_invert = 3 + 3 * fk + 2 + 2 + chol_launches(c->nz) + 2 * c->cfg.refine +
+    o->launches_per_invert = 3 + 3 * fk + 2 + 2 + chol_n + 2 * c->cfg.refine +
                              (c->ny > 1 ? 4 : 3);
   }
   o->freq_chunk = c->band_mode ? c->band_maxplanes : c->fchunk;

@@ -211,10 +211,17 @@ cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace
 int gram_scale_launches(const Dev& d);                          // FP16 operand scales: 0 or 2 kernels
 cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s);    // per-segment FP16 operand scales
-cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s);   // partials -> G, b (FP64)
+// partials -> G, b (FP64); df_out: the lower triangle of G + lam I as double-float pairs
+cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s, int df_out = 0);
 cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s);   // trace[m] = sum_z G[m][z][z]
 int chol_launches(int nz);                                      // kernels of launch_chol_solve
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s);
+// The double-float factorisation and solve (csrc/chol_df.cu), used when d.chol_df is set.
+cudaError_t prepare_chol_dfloat(const Dev& d);
+int chol_dfloat_launches(int nz);
+cudaError_t launch_chol_dfloat_resolve(const Dev& d, cudaStream_t s);           // x = (LL^T)^-1 b
+cudaError_t launch_chol_dfloat_export(const Dev& d, double* out, cudaStream_t s); // factor as FP64
+cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s);
 cudaError_t launch_refine(const Dev& d, cudaStream_t s);          // r += Ahat^T (dhat - Ahat x)
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s);   // x += (LL^T)^-1 (r - lam x)
 cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s);

@@ -428,8 +428,10 @@ __global__ void gram_scale_kernel(Dev d) {
   }
 }
 
-// Sum the partial tiles of each subproblem into the FP64 Gram (both triangles) and b.
-__global__ void gram_reduce_kernel(Dev d) {
+// Sum the partial tiles of each subproblem into the FP64 Gram (both triangles) and b.  With
+// df_out (the double-float factorisation follows) the lower triangle of G + lam I is written
+// instead, lam = alpha * trace, each value as a double-float pair (float2) in the same 8 bytes.
+__global__ void gram_reduce_kernel(Dev d, int df_out) {
   const int m = blockIdx.y;
   const int nz = d.nz, nzp = nzp_of(nz), ncols = cols_of(nzp);
   const int c1 = nzp + 16;
@@ -438,17 +440,40 @@ __global__ void gram_reduce_kernel(Dev d) {
   const long long nG = (long long)nz * nz;
   if (e < nG) {
     const int zi = int(e / nz), zj = int(e - (long long)zi * nz);
+    if (df_out && zj > zi) return;
     int a = zi, b = zj;
     if (a >= TC_M && b < TC_M) { a = zj; b = zi; }     // lower-left block from its transpose
     int lanei, col;
     if (a < TC_M) { lanei = a; col = b; }
     else { lanei = a - TC_M; col = c1 + (b - TC_M); }
-    double s = 0.0;
-    for (int sl = sl0; sl < sl1; ++sl) {
-      const double v = double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
-      s += d.gscale ? v * pow2d(-2 * d.gscale[sl].x) : v;
+    if (df_out) {
+      // the partial tiles (FP32, exact power-of-two scales) summed as a double-float pair by
+      // TwoSum on the FP32 pipes, then lam added on the diagonal
+      float sh = 0.f, sl_ = 0.f;
+      for (int sl = sl0; sl < sl1; ++sl) {
+        float v = d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei];
+        if (d.gscale) v = ldexpf(v, -2 * d.gscale[sl].x);
+        const float t = __fadd_rn(sh, v), bb = __fsub_rn(t, sh);
+        sl_ = __fadd_rn(sl_, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(v, bb)));
+        sh = t;
+      }
+      if (zi == zj) {
+        const double lam = d.alpha * d.trace[m];
+        const float lh = __double2float_rn(lam), ll = __double2float_rn(lam - double(lh));
+        const float t = __fadd_rn(sh, lh), bb = __fsub_rn(t, sh);
+        sl_ = __fadd_rn(sl_, __fadd_rn(__fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(lh, bb)), ll));
+        sh = t;
+      }
+      const float hs = __fadd_rn(sh, sl_);
+      reinterpret_cast<float2*>(d.G + size_t(m) * nG)[e] = make_float2(hs, __fsub_rn(sl_, __fsub_rn(hs, sh)));
+    } else {
+      double s = 0.0;
+      for (int sl = sl0; sl < sl1; ++sl) {
+        const double v = double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
+        s += d.gscale ? v * pow2d(-2 * d.gscale[sl].x) : v;
+      }
+      d.G[size_t(m) * nG + e] = s;
     }
-    d.G[size_t(m) * nG + e] = s;
   } else if (e < nG + 2 * nz) {
     const int zi = int((e - nG) >> 1), k = int((e - nG) & 1);
     int lanei, col;
@@ -509,10 +534,10 @@ cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s) {
   return cudaSuccess;
 }
 
-cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s) {
+cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s, int df_out) {
   const long long n = (long long)d.nz * d.nz + 2 * d.nz;
   dim3 g(unsigned((n + 255) / 256), d.nsub);
-  gram_reduce_kernel<<<g, 256, 0, s>>>(d);
+  gram_reduce_kernel<<<g, 256, 0, s>>>(d, df_out);
   return cudaGetLastError();
 }
 

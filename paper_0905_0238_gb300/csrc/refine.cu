@@ -135,9 +135,11 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
 //     (exact product errors of the hi parts, the TwoSum error of their sum, and the
 //     hi x lo cross terms);
 //   * the prediction and u = w (d - a_h . x) stay FP32;
-//   * every product a_h u is split exactly into p + e (fma), the p are summed per lane with
-//     Kahan compensation, the e and a_l u go to a low-order FP32 sum; the lane sums are
-//     combined in FP64 across warps and blocks.
+//   * every product a_h u is split exactly into p + e (fma), the p are summed per lane by
+//     TwoSum (Knuth's error-free addition: each addition's rounding error is captured
+//     exactly, the cascaded summation of Ogita, Rump and Oishi), the rounding errors, the e
+//     and the a_l u go to a low-order FP32 sum; the lane sums are combined in FP64 across
+//     warps and blocks.
 // The error-free steps use the _rn intrinsics so that no multiply-add is contracted.
 
 // exact product of two hi parts split as (rounded product, its error)
@@ -161,21 +163,22 @@ __device__ __forceinline__ void cmul_df(float2 ph, float2 pl, float2 qh, float2 
   al = make_float2(((e1 - e2) + er) + cr, ((e3 + e4) + ei) + ci);
 }
 
-// Kahan step: s + c carries the running sum (c the negated lost part)
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = __fsub_rn(x, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
+// TwoSum step: s + (the returned rounding error) = s_old + x exactly
+__device__ __forceinline__ float two_sum_acc(float& s, float x) {
+  const float t = __fadd_rn(s, x);
+  const float b = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, b)), __fsub_rn(x, b));
   s = t;
+  return e;
 }
 
-// acc[h] += Re(conj(a) u) with a = ah + al, u exact FP32
-__device__ __forceinline__ void acc_df(float& s, float& c, float& lo, float2 ah, float2 al, float2 u) {
+// (s, lo) += Re(conj(a) u) with a = ah + al, u exact FP32
+__device__ __forceinline__ void acc_df(float& s, float& lo, float2 ah, float2 al, float2 u) {
   const float p1 = __fmul_rn(ah.x, u.x), p2 = __fmul_rn(ah.y, u.y);
   const float e = two_prod_err(ah.x, u.x, p1) + two_prod_err(ah.y, u.y, p2);
-  kahan_add(s, c, p1);
-  kahan_add(s, c, p2);
-  lo += fmaf(al.x, u.x, fmaf(al.y, u.y, e));
+  const float r1 = two_sum_acc(s, p1);
+  const float r2 = two_sum_acc(s, p2);
+  lo += fmaf(al.x, u.x, fmaf(al.y, u.y, (e + r1) + r2));
 }
 
 template <int Z4, int RF_WARPS, int RF_ROWS_PER_WARP>
@@ -194,14 +197,14 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_df_kernel(Dev d) {
     xs[1][i] = i < nz ? float(d.x[(size_t(m) * nz + i) * 2 + 1]) : 0.f;
   }
   __syncthreads();
-  // [load t][depth 0/1 of the float4][rhs]: Kahan sum, its compensation, low-order sum
-  float as[Z4][2][2], ac[Z4][2][2], al_[Z4][2][2];
+  // [load t][depth 0/1 of the float4][rhs]: high-order sum, low-order sum
+  float as[Z4][2][2], al_[Z4][2][2];
 #pragma unroll
   for (int t = 0; t < Z4; ++t)
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int k = 0; k < 2; ++k) as[t][j][k] = ac[t][j][k] = al_[t][j][k] = 0.f;
+      for (int k = 0; k < 2; ++k) as[t][j][k] = al_[t][j][k] = 0.f;
   const float2* rhs = reinterpret_cast<const float2*>(d.rhs);
   const long long wb = c0 + warp * RF_ROWS_PER_WARP;
   const long long we = min(nr, wb + RF_ROWS_PER_WARP);
@@ -250,8 +253,8 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_df_kernel(Dev d) {
     for (int t = 0; t < Z4; ++t)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        acc_df(as[t][j][0], ac[t][j][0], al_[t][j][0], ah[t][j], al[t][j], up);
-        acc_df(as[t][j][1], ac[t][j][1], al_[t][j][1], ah[t][j], al[t][j], um);
+        acc_df(as[t][j][0], al_[t][j][0], ah[t][j], al[t][j], up);
+        acc_df(as[t][j][1], al_[t][j][1], ah[t][j], al[t][j], um);
       }
   }
 #pragma unroll
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_df_kernel(Dev d) {
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int k = 0; k < 2; ++k)
-        red[warp][k][z + j] = (double(as[t][j][k]) - double(ac[t][j][k])) + double(al_[t][j][k]);
+        red[warp][k][z + j] = double(as[t][j][k]) + double(al_[t][j][k]);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 2 * nz; i += blockDim.x) {

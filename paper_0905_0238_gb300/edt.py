@@ -107,6 +107,7 @@ def _lib() -> C.CDLL:
         L.edt_adjoint.argtypes = [vp, vp, i, vp, i, vp]
         L.edt_green.argtypes = [vp, vp, vp]
         L.edt_get_vhat.argtypes = [vp, vp, vp]
+        L.edt_get_factor.argtypes = [vp, vp, vp]
         L.edt_row_counts.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.edt_gram.argtypes = [vp, vp, i, vp, vp, vp, vp]
         d = C.c_double
@@ -131,7 +132,7 @@ def _lib() -> C.CDLL:
         L.edt_destroy.argtypes = [vp]
         L.edt_destroy.restype = None
         for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
-                     "edt_forward", "edt_adjoint", "edt_green", "edt_get_vhat", "edt_row_counts", "edt_gram",
+                     "edt_forward", "edt_adjoint", "edt_green", "edt_get_vhat", "edt_get_factor", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
                      "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning",
                      "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint",
@@ -203,6 +204,10 @@ def edt_adjoint(ctx, D_ptr: int, D_dtype: int, V_ptr: int, V_dtype: int, stream:
 
 def edt_green(ctx, g_ptr: int, stream: int):
     _check(_lib().edt_green(ctx, C.c_void_p(g_ptr), C.c_void_p(stream)), "edt_green")
+
+
+def edt_get_factor(ctx, ptr: int, stream: int):
+    _check(_lib().edt_get_factor(ctx, C.c_void_p(ptr), C.c_void_p(stream)), "edt_get_factor")
 
 
 def edt_get_vhat(ctx, ptr: int, stream: int):
@@ -492,6 +497,14 @@ class Solver:
                         dtype=torch.complex128)
         edt_green(self.ctx, g.data_ptr(), self._stream())
         return g
+
+    def factor(self):
+        """Cholesky factors of the last invert, [nsub][nz][nz] float64, L in the lower triangle
+        (the strict upper triangle is unspecified; see edt_get_factor)."""
+        torch = self._torch
+        L = torch.empty((self.nsub, self.cfg.nz, self.cfg.nz), device=self.device, dtype=torch.float64)
+        edt_get_factor(self.ctx, L.data_ptr(), self._stream())
+        return L
 
     def vhat(self):
         torch = self._torch

@@ -115,19 +115,40 @@ def test_graph_replay_matches_direct_calls():
         s.set_graph(False)
 
 
-@pytest.mark.parametrize("nx,nz,nf", [(32, 40, 6), (64, 130, 4), (32, 256, 3)])
-def test_double_float_cholesky_option(nx, nz, nf):
-    """Trailing updates in double-float give the native-FP64 result to ~1e-9 and stay
-    within the 1e-5 target against the oracle."""
+@pytest.mark.parametrize("nx,nz,nf,alpha", [(32, 40, 6, 1e-2), (64, 130, 4, 1e-2), (32, 256, 3, 1e-2),
+                                             (32, 256, 3, 1e-5), (64, 33, 5, 1e-4)])
+def test_double_float_cholesky_matches_native_fp64(nx, nz, nf, alpha):
+    """The double-float factorisation (the mixed path's default: FP32 pairs with error-free
+    products and sums, FP64 pivots) gives the native-FP64 factor of the same normal matrix
+    to 1e-13 relative per subproblem at alpha = 1e-2, and the same refined solution.  At
+    weaker damping both factors' sensitivity grows with kappa = cond(G + lam I) (the FP64
+    factor itself carries ~kappa 2^-53), so there the bound is max(1e-13, 8 kappa 2^-48): the
+    double-float unit roundoff scaled by the conditioning, with a small constant for the
+    rounding accumulated over the n operations of each entry; kappa is estimated from the
+    pivots, (max L_ii / min L_ii)^2."""
     from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED
-    wl = small_workload(nx=nx, nz=nz, nf=nf, alpha=1e-2, dz=8.0)
+    wl = small_workload(nx=nx, nz=nz, nf=nf, alpha=alpha, dz=8.0)
     D = born_data(wl, salt=7)
     V_or, _ = edt2d.invert(wl, D.astype(np.complex128))
-    V64 = solver(wl).invert(dev(D)).cpu().numpy()
-    s = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=3, refine=1, chol_df=1))
-    Vdf = s.invert(dev(D)).cpu().numpy()
-    assert rel_l2(Vdf, V64) < 1e-9
-    assert rel_l2(Vdf, V_or) < 1e-5
+    out = {}
+    for mode in (1, 2):
+        s = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=3, refine=1, chol_df=mode))
+        V = s.invert(dev(D)).cpu().numpy()
+        assert s.stats().n_notpd == 0
+        out[mode] = (V, np.tril(s.factor().cpu().numpy()))
+    (Vdf, Ldf), (V64, L64) = out[1], out[2]
+    for m in range(Ldf.shape[0]):
+        if np.any(L64[m]):
+            dg = np.abs(np.diag(L64[m]))
+            kappa = (dg.max() / dg.min()) ** 2
+            tol = 1e-13 if alpha >= 1e-2 else max(1e-13, 8 * kappa * 2.0 ** -48)
+            assert rel_l2(Ldf[m], L64[m]) < tol, (m, rel_l2(Ldf[m], L64[m]), kappa)
+    # after one refinement step the solution still depends, at first order, on the FP32 copy
+    # of the factor used by the correction solve, whose last bits differ between the two
+    # factorisations; at weak damping the conditioning amplifies that (both stay ~1e-6 from
+    # the oracle)
+    assert rel_l2(Vdf, V64) < (1e-10 if alpha >= 1e-2 else 1e-7)
+    assert rel_l2(Vdf, V_or) < 1e-5 and rel_l2(V64, V_or) < 1e-5
 
 
 def _noisy_case(case, alpha):
