@@ -637,8 +637,8 @@ cudaError_t prepare_chol(const Dev& d) {
   return prepare_chol_dfloat(d);
 }
 
-cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s) {
-  if (d.chol_df) return launch_chol_dfloat(d, trace_mode, s);
+cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s, const CholLookahead* la) {
+  if (d.chol_df) return launch_chol_dfloat(d, trace_mode, s, la);
   chol_kernel<false, false><<<d.nsub, 256, chol_smem(d.nz), s>>>(d, trace_mode);
   return cudaGetLastError();
 }

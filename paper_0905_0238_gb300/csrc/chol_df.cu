@@ -20,6 +20,9 @@
 //     by the inverse (x = a L_kk^-T, independent outputs); cdf_update subtracts P P^T from the
 //     trailing lower triangle in 64 x 64 tiles of every subproblem (the panel staged
 //     transposed in shared memory, each thread a 4 x 4 interleaved register tile);
+//   * look-ahead: the update of the tile column holding the next diagonal block and panel runs
+//     first, and the rest of the update runs on a second stream while the next diagonal block
+//     and panel proceed (the latency-bound small launches overlap the throughput-bound tiles);
 //   * cdf_final: forward and backward substitution for both right-hand sides in
 //     double-float, each diagonal block by its inverse; the factor stays in double-float (the re-solve of the inversion adjoint
 //     and the factor export read the pairs), its high parts are written as the FP32 copy for
@@ -287,16 +290,24 @@ __global__ void __launch_bounds__(128) cdf_panel_kernel(Dev d, int k0) {
 // of rows / columns t0 = k0 + 32 .. n - 1 of subproblem blockIdx.y loses P_I P_J^T, P the
 // step's panel.  Thread (ty, tx) owns rows ty + 16 u and columns tx + 16 v (u, v < 4):
 // interleaved, so the shared panel reads are conflict-free and the global rows coalesced.
-__global__ void __launch_bounds__(256) cdf_update_kernel(Dev d, int k0) {
+// part 0: every tile; 1: the first tile column J = 0 (it holds the next step's diagonal block
+// and panel); 2: the tiles J >= 1.
+__global__ void __launch_bounds__(256) cdf_update_kernel(Dev d, int k0, int part) {
   __shared__ float2 sI[FB * ULD], sJ[FB * ULD];   // transposed panel rows: [l][i]
   const int m = blockIdx.y, n = d.nz;
   if (!has_rows(d, m) || d.status[m] != EDT_OK) return;
   const int t0 = k0 + FB;
   const int pt = blockIdx.x;
-  int I = int((sqrtf(8.0f * pt + 1.0f) - 1.0f) * 0.5f);
-  while (I * (I + 1) / 2 > pt) --I;
-  while ((I + 1) * (I + 2) / 2 <= pt) ++I;
-  const int J = pt - I * (I + 1) / 2;
+  int I, J;
+  if (part == 1) {
+    I = pt; J = 0;
+  } else {
+    I = int((sqrtf(8.0f * pt + 1.0f) - 1.0f) * 0.5f);
+    while (I * (I + 1) / 2 > pt) --I;
+    while ((I + 1) * (I + 2) / 2 <= pt) ++I;
+    J = pt - I * (I + 1) / 2;
+    if (part == 2) { ++I; ++J; }
+  }
   const int r0 = t0 + UT * I, c0 = t0 + UT * J;
   float2* A = reinterpret_cast<float2*>(d.G + size_t(m) * n * n);
   {
@@ -442,7 +453,16 @@ size_t cdf_final_smem(int n) { return size_t(3 * n + FB * FLD) * sizeof(float2);
 
 }  // namespace
 
-int chol_dfloat_launches(int n) { return 1 + (n + FB - 1) / FB + 2 * ((n > FB) ? (n - 1) / FB : 0); }
+int chol_dfloat_launches(int n) {
+  int k = 1;                                        // the final solve
+  for (int k0 = 0; k0 < n; k0 += FB) {
+    ++k;                                            // diagonal block
+    if (k0 + FB >= n) break;
+    const int nt = (n - k0 - FB + UT - 1) / UT;
+    k += 1 + (nt < 2 ? 1 : 2);                      // panel, update (one or two parts)
+  }
+  return k;
+}
 
 cudaError_t prepare_chol_dfloat(const Dev& d) {
   cudaError_t e = cudaFuncSetAttribute(cdf_final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -462,16 +482,37 @@ cudaError_t launch_chol_dfloat_export(const Dev& d, double* out, cudaStream_t s)
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s) {
+cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s, const CholLookahead* la) {
   (void)trace_mode;                       // the Gram reduction has added lam = alpha * trace
   const int n = d.nz;
-  for (int k0 = 0; k0 < n; k0 += FB) {
+  const int nsteps = (n + FB - 1) / FB;
+  const bool ahead = la && la->side && la->nev >= 2 * nsteps + 1;
+  cudaError_t e;
+  // Look-ahead on two streams: step k's update of the tile column J = 0 runs on s, followed by
+  // the next diagonal block and panel (which read only that column); the update of the tiles
+  // J >= 1 runs on the side stream meanwhile.  Step k + 1's updates wait for it.
+  cudaEvent_t prev_rest = nullptr;
+  for (int step = 0, k0 = 0; k0 < n; ++step, k0 += FB) {
     cdf_diag_kernel<<<d.nsub, 1024, 0, s>>>(d, k0);
     if (k0 + FB >= n) break;
     const int t = n - k0 - FB, nt = (t + UT - 1) / UT;
     cdf_panel_kernel<<<dim3((t + 31) / 32, d.nsub), 128, 0, s>>>(d, k0);
-    cdf_update_kernel<<<dim3(nt * (nt + 1) / 2, d.nsub), 256, 0, s>>>(d, k0);
+    if (!ahead || nt < 2) {
+      if (prev_rest && (e = cudaStreamWaitEvent(s, prev_rest, 0)) != cudaSuccess) return e;
+      prev_rest = nullptr;
+      cdf_update_kernel<<<dim3(nt * (nt + 1) / 2, d.nsub), 256, 0, s>>>(d, k0, 0);
+      continue;
+    }
+    cudaEvent_t ev_panel = la->ev[2 * step], ev_rest = la->ev[2 * step + 1];
+    if ((e = cudaEventRecord(ev_panel, s)) != cudaSuccess) return e;
+    if (prev_rest && (e = cudaStreamWaitEvent(s, prev_rest, 0)) != cudaSuccess) return e;
+    cdf_update_kernel<<<dim3(nt, d.nsub), 256, 0, s>>>(d, k0, 1);
+    if ((e = cudaStreamWaitEvent(la->side, ev_panel, 0)) != cudaSuccess) return e;
+    cdf_update_kernel<<<dim3(nt * (nt - 1) / 2, d.nsub), 256, 0, la->side>>>(d, k0, 2);
+    if ((e = cudaEventRecord(ev_rest, la->side)) != cudaSuccess) return e;
+    prev_rest = ev_rest;
   }
+  if (prev_rest && (e = cudaStreamWaitEvent(s, prev_rest, 0)) != cudaSuccess) return e;
   cdf_final_kernel<<<d.nsub, FTHREADS, cdf_final_smem(n), s>>>(d);
   return cudaGetLastError();
 }

@@ -121,6 +121,7 @@ struct edt_ctx {
   // runs there concurrently with the data transform on the caller's stream
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<cudaEvent_t> ev_la;      // look-ahead of the double-float Cholesky (on aux)
   // host-buffer calls: the input copy on its own stream into one of two staging buffers, so
   // one call's copy overlaps the previous call's stages (edt_set_host_pipeline)
   bool host_pipe = false;
@@ -838,7 +839,10 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_ev(c, 5, 1, s);
   prof_ev(c, 6, 0, s);
   if (c->variant) EDT_TRY(launch_solve_variant(d, s));
-  else EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s));
+  else {
+    const CholLookahead la{c->aux, c->ev_la.data(), int(c->ev_la.size())};
+    EDT_TRY(launch_chol_solve(d, mixed ? 1 : 0, s, &la));
+  }
   prof_ev(c, 6, 1, s);
   prof_ev(c, 7, 0, s);
   if (mixed) {
@@ -960,6 +964,8 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
       EDT_TRY(cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming));
       EDT_TRY(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming));
     }
+    c->ev_la.assign(2 * ((c->nz + 31) / 32) + 1, nullptr);
+    for (auto& e : c->ev_la) EDT_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   EDT_TRY(cudaDeviceSynchronize());
   return EDT_OK;
@@ -1431,6 +1437,7 @@ void edt_destroy(edt_ctx* c) {
   if (c->cpy) cudaStreamDestroy(c->cpy);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (auto e : c->ev_la) if (e) cudaEventDestroy(e);
   if (c->aux) cudaStreamDestroy(c->aux);
   delete c;
 }

@@ -215,13 +215,21 @@ cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s);    // per-segment F
 cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s, int df_out = 0);
 cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s);   // trace[m] = sum_z G[m][z][z]
 int chol_launches(int nz);                                      // kernels of launch_chol_solve
-cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s);
+// The double-float factorisation (csrc/chol_df.cu) runs its updates with a one-step look-ahead
+// on two streams when given a side stream and 2 * ceil(nz / 32) + 1 events (joined back into s
+// before it returns).
+struct CholLookahead {
+  cudaStream_t side;
+  const cudaEvent_t* ev;
+  int nev;
+};
+cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s, const CholLookahead* la = nullptr);
 // The double-float factorisation and solve (csrc/chol_df.cu), used when d.chol_df is set.
 cudaError_t prepare_chol_dfloat(const Dev& d);
 int chol_dfloat_launches(int nz);
 cudaError_t launch_chol_dfloat_resolve(const Dev& d, cudaStream_t s);           // x = (LL^T)^-1 b
 cudaError_t launch_chol_dfloat_export(const Dev& d, double* out, cudaStream_t s); // factor as FP64
-cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s);
+cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s, const CholLookahead* la = nullptr);
 cudaError_t launch_refine(const Dev& d, cudaStream_t s);          // r += Ahat^T (dhat - Ahat x)
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s);   // x += (LL^T)^-1 (r - lam x)
 cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s);
