@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default launch shapes instead of the autotuned ones")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batched_3d", "differentiation_2d", "streaming", "paper_2d_tsvd"],
+                    choices=[WORKLOAD, "batched_3d", "differentiation_2d", "streaming", "paper_2d_tsvd",
+                             "fma_peak"],
                     help="batched_3d: the finite-aperture 3D workload; differentiation_2d: misfit "
                          "gradients on the production geometry; streaming: 4096 independent 1D "
                          "subproblems in Poisson bursts (separate lines, not the headline)")
@@ -361,6 +362,9 @@ def main():
     if args.workload == "differentiation_2d":
         main_grad(args, world, rank, local)
         return
+    if args.workload == "fma_peak":
+        main_fma_peak(args, world, rank, local)
+        return
 
     import numpy as np
     import torch
@@ -555,6 +559,8 @@ def main():
                 useful_tflops=useful_tf, useful_frac=(useful_tf / peak) if useful_tf else None,
                 gram_ms=gram_ms)
     stage_ms = {k: v / max(ncalls, 1) for k, v in stages.items()}
+    chol_roof = cholesky_roofline(wl.nz, wl.nx // 2 + 1, stage_ms.get("cholesky", 0.0),  # split systems
+                                  chol_fp64=args.chol_df == 2)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -581,8 +587,8 @@ def main():
                  serial_value=job_throughput(world, sub_per_step, args.steps, ms_e2e_serial),
                  serial_ms_per_step=ms_e2e_serial / args.steps),
         gpu_launches=int(st.launches_per_invert) * args.steps,
-        roofline=roof, stage_ms=stage_ms, accuracy=acc, variants=variants, clocks=clk,
-        cpu_baseline=cpu)
+        roofline=roof, cholesky_roofline=chol_roof, stage_ms=stage_ms, accuracy=acc,
+        variants=variants, clocks=clk, cpu_baseline=cpu)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -1124,6 +1130,44 @@ def main_paper(args, world, rank, local):
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def cholesky_roofline(nz, nsub, chol_ms, chol_fp64=False):
+    """Roofline of the damped Cholesky stage.  Algorithmic work per split system: nz^3/3 flops
+    for the factorisation and 4 nz^2 for the two right-hand sides' substitutions.  The default
+    factorisation runs in double-float on the FP32 pipes, so its FP64-equivalent rate is set
+    beside the device's measured FP64 multiply-add rate (what a native FP64 factorisation is
+    bounded by) and its measured FP32 rate (the pipe it actually uses)."""
+    from paper_0905_0238_gb300 import edt as _edt
+    fp64, fp32 = _edt.edt_measure_fma_rates()
+    flops = nsub * (nz ** 3 / 3.0 + 4.0 * nz ** 2)
+    ach = flops / (chol_ms * 1e-3) / 1e12 if chol_ms > 0 else None
+    return dict(bound="fp64 pipe" if chol_fp64 else "fp32 pipe (double-float arithmetic)",
+                kernel="chol_kernel" if chol_fp64 else "cdf_* (diag, panel, update, final)",
+                achieved=ach, unit="TFLOP/s (FP64-equivalent)", peak=fp64,
+                peak_source="edt_measure_fma_rates: FP64 multiply-add rate measured in this run",
+                frac=(ach / fp64) if (ach and fp64) else None,
+                fp32_peak=fp32, flops_per_call=flops, cholesky_ms=chol_ms)
+
+
+def main_fma_peak(args, world, rank, local):
+    """The device's FP64 and FP32 multiply-add rates (the denominators of the FP64 and
+    double-float rooflines), measured by the library's probe."""
+    import torch
+    from paper_0905_0238_gb300 import build as libbuild
+    libbuild.build()
+    from paper_0905_0238_gb300 import edt as _edt
+    torch.cuda.set_device(local)
+    rates = [_edt.edt_measure_fma_rates() for _ in range(max(1, args.steps))]
+    fp64 = max(r[0] for r in rates)
+    fp32 = max(r[1] for r in rates)
+    if rank == 0:
+        print(json.dumps(dict(metric="fma_tflops", value=fp64, unit="TFLOP/s (FP64 multiply-add)",
+                              n_gpus=1, steps=len(rates), warmup=0, higher_is_better=True,
+                              dtype="f64", data="synthetic",
+                              config=dict(workload="fma_peak: 8 independent multiply-add chains per "
+                                                   "thread, 8 CTAs of 256 threads per SM"),
+                              fp32_tflops=fp32, fp64_to_fp32=fp64 / fp32 if fp32 else None)))
 
 
 def _kernel_source_hash(name):

@@ -370,6 +370,13 @@ int edt_green_noalloc(int nx, double dx, int nz, double dz, double z0, int nfreq
  * m = 0..nx/2 (host only).  Returns nx/2 + 1, or EDT_EINVAL without the disk. */
 int edt_kz_disk_columns(const edt_ctx* ctx, int* p);
 
+/* Measured FP64 and FP32 fused multiply-add rates of the current device, in TFLOP/s (2 flops
+ * per multiply-add; the best of three timed launches of independent multiply-add chains over
+ * every SM).  A utility for stating rooflines (the library's double-float kernels trade FP64
+ * work for FP32 work); no counterpart in the paper.  Synchronous; allocates and frees a small
+ * device buffer, so not for use during stream capture.  Returns EDT_OK or EDT_ECUDA. */
+int edt_measure_fma_rates(double* fp64_tflops, double* fp32_tflops);
+
 /* Per-subproblem complex row counts after the cut (before folding): counts[nx/2+1]. */
 int edt_row_counts(const edt_ctx* ctx, long long* counts);
 

@@ -139,6 +139,8 @@ def _lib() -> C.CDLL:
                      "edt_set_host_pipeline", "edt_set_wait_test"):
             getattr(L, name).restype = i
         ll = C.c_longlong
+        L.edt_measure_fma_rates.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.edt_measure_fma_rates.restype = i
         L.edt_kz_disk_columns.argtypes = [vp, C.POINTER(i)]
         L.edt_kz_disk_columns.restype = i
         L.edt_stream_request_bytes.argtypes = [C.POINTER(edt_sub1d)]
@@ -229,6 +231,13 @@ def edt_green_noalloc(nx, dx, nz, dz, z0, freq_hz, eps, layer_top, layer_vel, g_
     _check(_lib().edt_green_noalloc(nx, dx, nz, dz, z0, len(fr), fr.ctypes.data_as(dp), eps,
                                     len(tp), tp.ctypes.data_as(dp), vl.ctypes.data_as(dp),
                                     C.c_void_p(g_ptr), C.c_void_p(stream)), "edt_green_noalloc")
+
+
+def edt_measure_fma_rates():
+    """(FP64, FP32) multiply-add rates of the current device in TFLOP/s."""
+    f64, f32 = C.c_double(), C.c_double()
+    _check(_lib().edt_measure_fma_rates(C.byref(f64), C.byref(f32)), "edt_measure_fma_rates")
+    return f64.value, f32.value
 
 
 def edt_row_counts(ctx, nsub: int) -> np.ndarray:
