@@ -164,6 +164,11 @@ typedef struct {
                                    products and compensated sums (line geometry only);
                                    0 = automatic: 2 on the line geometry when
                                    alpha < 1e-3, else 1                                 */
+  int sub_begin, sub_end;       /* line geometry: plan and solve only the subproblems
+                                   m in [sub_begin, sub_end) (0 <= sub_begin <= sub_end
+                                   <= nx/2 + 1); the others get no rows and Vhat = 0.
+                                   0, 0 = every subproblem.  The partitioned solve gives
+                                   each rank such a range (see edt_import_rhs).         */
 } edt_config;
 
 #define EDT_SOLVE_DAMPED 0
@@ -321,6 +326,51 @@ int edt_set_reference(edt_ctx* ctx, const double* layer_vel_mps, void* stream);
 /* Reference Green's function table g(k_n, z_j; omega~_f), n = 0..nx/2, as complex128
  * [nfreq][nx/2+1][nz] (computed in FP64 by the depth march). */
 int edt_green(edt_ctx* ctx, void* g_dev, void* stream);
+
+/* ---- partitioned solve (the subproblems are independent: Section "Two dimensions", the
+ * decoupling of eqs. DMV and M; Discussion) -----------------------------------------------
+ * A job sharded over ranks runs: on each rank, a context for its frequencies (a contiguous
+ * range of the job's frequency list, cfg.freq_hz restricted to it) produces the split
+ * right-hand sides of every subproblem (edt_export_rhs); the rows of each subproblem go to the
+ * rank owning it (an all-to-all; row blocks are contiguous per destination because the rows
+ * are ordered by subproblem, then frequency); each rank's context restricted to its
+ * subproblems (sub_begin, sub_end; all frequencies) places the received blocks
+ * (edt_import_rhs, one call per source) and solves (edt_solve_imported); the Vhat of all ranks
+ * are summed (disjoint supports) and edt_inverse_vhat returns V.  The result equals
+ * edt_invert's up to the summation order of the tensor-core Gram (FP64 path: bitwise the
+ * same arithmetic). */
+
+/* Offsets of each subproblem's solved rows (after the reciprocal folding) in the context's row
+ * order: off[nx/2 + 2].  Host only.  Returns nx/2 + 2 or EDT_EINVAL. */
+int edt_row_offsets(const edt_ctx* ctx, long long* off);
+
+/* Data transform and split right-hand sides of D (this context's frequencies, on the device)
+ * copied out to rhs_dev: off[nx/2 + 1] rows (edt_row_offsets) in the context's order
+ * (subproblem, then frequency, then receiver index), two complex values (d_+, d_-) each,
+ * rotated by the unit phase conj(s_f)/|s_f| (the kernel rows carry |s_f|): complex64 on the
+ * mixed path, complex128 on the FP64 path.  rhs_dev is the caller's.  Line geometry.
+ * Asynchronous on `stream`.  Returns EDT_OK, EDT_EINVAL (null pointer, bad dtype),
+ * EDT_ENOMEM_WS (no workspace), EDT_EUNSUPPORTED (window geometry, solver variants). */
+int edt_export_rhs(edt_ctx* ctx, const void* D_dev, int D_dtype, void* rhs_dev, void* stream);
+
+/* Place the rows of frequencies [f_begin, f_end) of every subproblem of this context into the
+ * workspace: block_dev holds nrows rows, ordered by subproblem, then frequency, as exported by
+ * a context holding exactly those frequencies (same grid, layers and cut; its rows of the
+ * subproblems outside this context's range are left out).  nrows must equal this context's row
+ * count at those frequencies, else EDT_EINVAL (block_dev may be null when it is 0).  Every
+ * frequency must be imported before edt_solve_imported.  Asynchronous on `stream`. */
+int edt_import_rhs(edt_ctx* ctx, const void* block_dev, long long nrows, int f_begin, int f_end,
+                   void* stream);
+
+/* The stages of edt_invert after the data transform (depth march, Gram, Cholesky, refinement)
+ * on the imported right-hand sides; writes Vhat(k_m, z_j) = x_+ + i x_- as complex128
+ * [nx/2 + 1][nz] (zero outside the context's subproblem range and for failed subproblems).
+ * Asynchronous on `stream`; edt_get_stats reports as after edt_invert. */
+int edt_solve_imported(edt_ctx* ctx, void* vhat_dev, void* stream);
+
+/* V from Vhat (complex128 [nx/2 + 1][nz]): the completion Vhat(-k_m) = conj Vhat(k_m)
+ * (eq. VSym) and the inverse lateral DFT, as edt_invert's last stage.  Line geometry. */
+int edt_inverse_vhat(edt_ctx* ctx, const void* vhat_dev, void* V_dev, int V_dtype, void* stream);
 
 /* Copy the Cholesky factors of the last edt_invert on this context, G + lam I = L L^T per
  * subproblem, as double [n_sub][nz][nz] into caller device memory: the lower triangle and

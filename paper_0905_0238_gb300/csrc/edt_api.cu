@@ -169,6 +169,9 @@ int validate(const edt_config* c) {
   if (c->chol_df < 0 || c->chol_df > 2) return EDT_EINVAL;
   if (c->freq_chunk < 0 || c->gram_seg_rows < 0) return EDT_EINVAL;
   if (c->resid < 0 || c->resid > 2) return EDT_EINVAL;
+  if (c->sub_begin < 0 || c->sub_end < 0 || c->sub_begin > c->sub_end) return EDT_EINVAL;
+  if (c->sub_end > c->nx / 2 + 1) return EDT_EINVAL;
+  if (c->sub_end > c->sub_begin && c->geometry == EDT_GEOM_WINDOW) return EDT_EUNSUPPORTED;
   if (c->resid == 2 && (c->geometry == EDT_GEOM_WINDOW || c->precision != EDT_MIXED)) return EDT_EUNSUPPORTED;
   if (c->geometry != EDT_GEOM_LINE && c->geometry != EDT_GEOM_WINDOW) return EDT_EINVAL;
   if (c->solver != EDT_SOLVE_DAMPED && c->solver != EDT_SOLVE_TSVD) return EDT_EINVAL;
@@ -431,10 +434,14 @@ void plan(edt_ctx* c) {
   c->row_off_mf.assign(size_t(c->nsub) * (c->nf + 1), 0);
   c->counts_cut.assign(c->nsub, 0);
   auto sidx = [N](int n) { return n <= N / 2 ? n : n - N; };
+  const bool ranged = g.sub_end > g.sub_begin;
   for (int m = 0; m < c->nsub; ++m) {
     c->row_off[m] = (long long)c->rows.size();
+    // a context restricted to subproblems [sub_begin, sub_end) plans no rows for the others
+    const bool inrange = !ranged || (m >= g.sub_begin && m < g.sub_end);
     for (int f = 0; f < c->nf; ++f) {
       c->row_off_mf[size_t(m) * (c->nf + 1) + f] = (long long)c->rows.size();
+      if (!inrange) continue;
       const double lim = c->fc[f].lim;
       // order p = 0, N/2, 1, N-1, 2, N-2, ...: rows p and -p read the same table row g(|p|),
       // so placed side by side the second read is served from L1
@@ -794,7 +801,10 @@ int kernel_rows(edt_ctx* c, cudaStream_t s) {
   return EDT_OK;
 }
 
-int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cudaStream_t s) {
+// One inversion on s.  do_transform = false: the right-hand sides were imported into the
+// workspace (edt_import_rhs); do_inverse = false: the solutions stay in the workspace.
+int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cudaStream_t s,
+               bool do_transform = true, bool do_inverse = true) {
   const Dev& d = c->dev;
   const bool mixed = c->cfg.precision == EDT_MIXED;
   c->last_stream = s;
@@ -816,7 +826,7 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_ev(c, 1, 1, sg);
   if (ov) EDT_TRY(cudaEventRecord(c->ev_join, c->aux));
   prof_ev(c, 2, 0, s);
-  EDT_TRYI(transform_rhs(c, D, D_dtype, s));
+  if (do_transform) EDT_TRYI(transform_rhs(c, D, D_dtype, s));
   prof_ev(c, 2, 1, s);
   if (ov) EDT_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   prof_ev(c, 3, 0, s);
@@ -854,8 +864,12 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   }
   prof_ev(c, 7, 1, s);
   prof_ev(c, 8, 0, s);
-  if (c->win) EDT_TRY(launch_fa_inverse(d, V, V_dtype, s));
-  else EDT_TRY(launch_inverse(d, V, V_dtype, s));
+  if (!do_inverse) {
+  } else if (c->win) {
+    EDT_TRY(launch_fa_inverse(d, V, V_dtype, s));
+  } else {
+    EDT_TRY(launch_inverse(d, V, V_dtype, s));
+  }
   prof_ev(c, 8, 1, s);
   if (c->prof && c->prof_calls < kProfCalls) c->prof_calls++;
   return EDT_OK;
@@ -1250,6 +1264,88 @@ int edt_green(edt_ctx* c, void* g_dev, void* stream) {
   c->last_stream = s;
   EDT_TRY(launch_green(c->dev, s, GREEN_G64));
   EDT_TRY(cudaMemcpyAsync(g_dev, c->dev.g64, c->r_g64.bytes, cudaMemcpyDeviceToDevice, s));
+  return EDT_OK;
+}
+
+int edt_row_offsets(const edt_ctx* c, long long* off) {
+  if (!c || !off) return EDT_EINVAL;
+  std::copy(c->row_off.begin(), c->row_off.end(), off);
+  return c->nsub + 1;
+}
+
+static size_t rhs_row_bytes(const edt_ctx* c) {
+  return 2 * (c->cfg.precision == EDT_MIXED ? sizeof(float2) : sizeof(double2));
+}
+
+int edt_export_rhs(edt_ctx* c, const void* D, int D_dtype, void* rhs_out, void* stream) {
+  if (!c || !D || !rhs_out) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (D_dtype != EDT_C64 && D_dtype != EDT_C128) return EDT_EINVAL;
+  if (c->win || c->variant) return EDT_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  c->have_factor = false;
+  EDT_TRYI(transform_rhs(c, D, D_dtype, s));
+  const size_t bytes = size_t(c->row_off[c->nsub]) * rhs_row_bytes(c);
+  if (bytes) EDT_TRY(cudaMemcpyAsync(rhs_out, c->dev.rhs, bytes, cudaMemcpyDeviceToDevice, s));
+  return EDT_OK;
+}
+
+int edt_import_rhs(edt_ctx* c, const void* block, long long nrows, int f_begin, int f_end,
+                   void* stream) {
+  if (!c || nrows < 0) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (f_begin < 0 || f_end < f_begin || f_end > c->nf) return EDT_EINVAL;
+  if (c->win || c->variant) return EDT_EUNSUPPORTED;
+  // the block must hold exactly this context's rows of those frequencies
+  long long want = 0;
+  for (int m = 0; m < c->nsub; ++m)
+    want += c->row_off_mf[size_t(m) * (c->nf + 1) + f_end] - c->row_off_mf[size_t(m) * (c->nf + 1) + f_begin];
+  if (nrows != want || (want > 0 && !block)) return EDT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  c->have_factor = false;
+  const size_t rb = rhs_row_bytes(c);
+  const char* src = static_cast<const char*>(block);
+  char* dst = static_cast<char*>(c->dev.rhs);
+  long long so = 0;
+  for (int m = 0; m < c->nsub; ++m) {
+    const long long a = c->row_off_mf[size_t(m) * (c->nf + 1) + f_begin];
+    const long long b = c->row_off_mf[size_t(m) * (c->nf + 1) + f_end];
+    if (b > a)
+      EDT_TRY(cudaMemcpyAsync(dst + size_t(a) * rb, src + size_t(so) * rb, size_t(b - a) * rb,
+                              cudaMemcpyDeviceToDevice, s));
+    so += b - a;
+  }
+  return EDT_OK;
+}
+
+int edt_solve_imported(edt_ctx* c, void* vhat_dev, void* stream) {
+  if (!c || !vhat_dev) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (c->win || c->variant) return EDT_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int r = run_invert(c, nullptr, EDT_C64, nullptr, EDT_F64, s, false, false);
+  c->last_status = r;
+  if (r != EDT_OK) return r;
+  c->have_factor = true;
+  // the solutions x[m][z][0..1] are Vhat(k_m, z) = x_+ + i x_- in complex128 layout (x_- = 0 at
+  // the self-paired m; zero for failed subproblems and those outside the context's range)
+  EDT_TRY(cudaMemcpyAsync(vhat_dev, c->dev.x, c->r_x.bytes, cudaMemcpyDeviceToDevice, s));
+  return EDT_OK;
+}
+
+int edt_inverse_vhat(edt_ctx* c, const void* vhat_dev, void* V_dev, int V_dtype, void* stream) {
+  if (!c || !vhat_dev || !V_dev) return EDT_EINVAL;
+  if (!c->ws) return EDT_ENOMEM_WS;
+  if (V_dtype != EDT_F32 && V_dtype != EDT_F64) return EDT_EINVAL;
+  if (c->win) return EDT_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  c->have_factor = false;
+  EDT_TRY(cudaMemcpyAsync(c->dev.x, vhat_dev, c->r_x.bytes, cudaMemcpyDeviceToDevice, s));
+  EDT_TRY(cudaMemsetAsync(c->dev.status, 0, sizeof(int) * c->nsub, s));
+  EDT_TRY(launch_inverse(c->dev, V_dev, V_dtype, s));
   return EDT_OK;
 }
 

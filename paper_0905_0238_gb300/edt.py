@@ -36,7 +36,7 @@ class edt_config(C.Structure):
         ("chol_df", C.c_int), ("freq_chunk", C.c_int),
         ("geometry", C.c_int), ("ny", C.c_int), ("dy", C.c_double), ("wx", C.c_int), ("wy", C.c_int),
         ("solver", C.c_int), ("tsvd_tol", C.c_double), ("kz_disk", C.c_double),
-        ("gram_seg_rows", C.c_int), ("resid", C.c_int),
+        ("gram_seg_rows", C.c_int), ("resid", C.c_int), ("sub_begin", C.c_int), ("sub_end", C.c_int),
     ]
 
 
@@ -108,6 +108,12 @@ def _lib() -> C.CDLL:
         L.edt_green.argtypes = [vp, vp, vp]
         L.edt_get_vhat.argtypes = [vp, vp, vp]
         L.edt_get_factor.argtypes = [vp, vp, vp]
+        L.edt_row_offsets.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.edt_row_offsets.restype = i
+        L.edt_export_rhs.argtypes = [vp, vp, i, vp, vp]
+        L.edt_import_rhs.argtypes = [vp, vp, C.c_longlong, i, i, vp]
+        L.edt_solve_imported.argtypes = [vp, vp, vp]
+        L.edt_inverse_vhat.argtypes = [vp, vp, vp, i, vp]
         L.edt_row_counts.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.edt_gram.argtypes = [vp, vp, i, vp, vp, vp, vp]
         d = C.c_double
@@ -132,7 +138,8 @@ def _lib() -> C.CDLL:
         L.edt_destroy.argtypes = [vp]
         L.edt_destroy.restype = None
         for name in ("edt_create", "edt_set_workspace", "edt_invert", "edt_invert_host",
-                     "edt_forward", "edt_adjoint", "edt_green", "edt_get_vhat", "edt_get_factor", "edt_row_counts", "edt_gram",
+                     "edt_forward", "edt_adjoint", "edt_green", "edt_get_vhat", "edt_get_factor", "edt_export_rhs",
+                     "edt_import_rhs", "edt_solve_imported", "edt_inverse_vhat", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
                      "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning",
                      "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint",
@@ -206,6 +213,31 @@ def edt_adjoint(ctx, D_ptr: int, D_dtype: int, V_ptr: int, V_dtype: int, stream:
 
 def edt_green(ctx, g_ptr: int, stream: int):
     _check(_lib().edt_green(ctx, C.c_void_p(g_ptr), C.c_void_p(stream)), "edt_green")
+
+
+def edt_row_offsets(ctx, nsub: int) -> np.ndarray:
+    out = (C.c_longlong * (nsub + 1))()
+    _check(_lib().edt_row_offsets(ctx, out), "edt_row_offsets")
+    return np.array(out[:], dtype=np.int64)
+
+
+def edt_export_rhs(ctx, D_ptr: int, D_dtype: int, rhs_ptr: int, stream: int):
+    _check(_lib().edt_export_rhs(ctx, C.c_void_p(D_ptr), D_dtype, C.c_void_p(rhs_ptr), C.c_void_p(stream)),
+           "edt_export_rhs")
+
+
+def edt_import_rhs(ctx, block_ptr: int, nrows: int, f_begin: int, f_end: int, stream: int):
+    _check(_lib().edt_import_rhs(ctx, C.c_void_p(block_ptr), nrows, f_begin, f_end, C.c_void_p(stream)),
+           "edt_import_rhs")
+
+
+def edt_solve_imported(ctx, vhat_ptr: int, stream: int):
+    _check(_lib().edt_solve_imported(ctx, C.c_void_p(vhat_ptr), C.c_void_p(stream)), "edt_solve_imported")
+
+
+def edt_inverse_vhat(ctx, vhat_ptr: int, V_ptr: int, V_dtype: int, stream: int):
+    _check(_lib().edt_inverse_vhat(ctx, C.c_void_p(vhat_ptr), C.c_void_p(V_ptr), V_dtype, C.c_void_p(stream)),
+           "edt_inverse_vhat")
 
 
 def edt_get_factor(ctx, ptr: int, stream: int):
@@ -352,6 +384,8 @@ class Config:
     kz_disk: float = 0.0       # > 0: |(k_m, k_z)| <= kz_disk omega_max / c_min
     gram_seg_rows: int = 0     # mixed: rows per FP32 Gram accumulation (0 = automatic)
     resid: int = 0             # mixed: refinement residual, 1 FP32, 2 double-float, 0 automatic
+    sub_begin: int = 0         # line geometry: solve only subproblems [sub_begin, sub_end)
+    sub_end: int = 0           #   (0, 0: all)
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -363,6 +397,26 @@ class Config:
                         precision=EDT_MIXED, fold=0)
         base.update(kw)
         return cls(**base)
+
+    def c_config(self):
+        """(edt_config, arrays): the C configuration and the FP64 arrays it points into, which
+        the caller keeps alive for as long as the context is being created."""
+        arrays = tuple(np.ascontiguousarray(a, dtype=np.float64)
+                       for a in (self.freq_hz, self.layer_top, self.layer_vel))
+        freq, top, vel = arrays
+        dp = C.POINTER(C.c_double)
+        c = edt_config(
+            nx=self.nx, dx=self.dx, nz=self.nz, dz=self.dz, z0=self.z0,
+            nfreq=len(freq), freq_hz=freq.ctypes.data_as(dp), eps=self.eps,
+            nlayer=len(top), layer_top_m=top.ctypes.data_as(dp),
+            layer_vel_mps=vel.ctypes.data_as(dp), precision=self.precision,
+            passes=self.passes, refine=self.refine, alpha=self.alpha, cutoff=self.cutoff,
+            fold=self.fold, chol_df=self.chol_df, freq_chunk=self.freq_chunk,
+            geometry=self.geometry, ny=self.ny, dy=self.dy, wx=self.wx, wy=self.wy,
+            solver=self.solver, tsvd_tol=self.tsvd_tol, kz_disk=self.kz_disk,
+            gram_seg_rows=self.gram_seg_rows, resid=self.resid, sub_begin=self.sub_begin,
+            sub_end=self.sub_end)
+        return c, arrays
 
     @property
     def window(self) -> bool:
@@ -384,20 +438,7 @@ class Solver:
         import torch
         self._torch = torch
         self.cfg = cfg
-        self._freq = np.ascontiguousarray(cfg.freq_hz, dtype=np.float64)
-        self._top = np.ascontiguousarray(cfg.layer_top, dtype=np.float64)
-        self._vel = np.ascontiguousarray(cfg.layer_vel, dtype=np.float64)
-        dp = C.POINTER(C.c_double)
-        c = edt_config(
-            nx=cfg.nx, dx=cfg.dx, nz=cfg.nz, dz=cfg.dz, z0=cfg.z0,
-            nfreq=len(self._freq), freq_hz=self._freq.ctypes.data_as(dp), eps=cfg.eps,
-            nlayer=len(self._top), layer_top_m=self._top.ctypes.data_as(dp),
-            layer_vel_mps=self._vel.ctypes.data_as(dp), precision=cfg.precision,
-            passes=cfg.passes, refine=cfg.refine, alpha=cfg.alpha, cutoff=cfg.cutoff,
-            fold=cfg.fold, chol_df=cfg.chol_df, freq_chunk=cfg.freq_chunk,
-            geometry=cfg.geometry, ny=cfg.ny, dy=cfg.dy, wx=cfg.wx, wy=cfg.wy,
-            solver=cfg.solver, tsvd_tol=cfg.tsvd_tol, kz_disk=cfg.kz_disk,
-            gram_seg_rows=cfg.gram_seg_rows, resid=cfg.resid)
+        c, (self._freq, self._top, self._vel) = cfg.c_config()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.ctx = None
         self.ctx, self.ws_bytes = edt_create(c)

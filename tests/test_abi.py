@@ -226,3 +226,51 @@ def test_wait_test_hook_validates_on_the_host():
             assert ei.value.code == edt.EDT_EINVAL
     finally:
         edt.edt_destroy(ctx)
+
+
+def test_ranged_and_sharded_row_plans_without_gpu():
+    """A context over a subproblem range plans the full plan's rows inside it and none outside;
+    contexts over contiguous frequency shards plan, per subproblem, row counts that add up to
+    the full plan's (the oracle's cut restricted to each shard); the import refuses a block
+    whose row count differs from the context's before touching any device memory."""
+    import numpy as np
+    import synth
+    from oracle import edt2d
+    from paper_0905_0238_gb300 import edt, Config
+    from paper_0905_0238_gb300.partition import GpuBackend, plan_partition
+    wl = synth.preset("small_2d")
+    nsub = wl.nx // 2 + 1
+    full = GpuBackend(Config.from_workload(wl, precision=edt.EDT_FP64, fold=0)).sub_rows()
+    assert [int(x) for x in full] == [len(edt2d.kept_rows(wl, m)) for m in range(nsub)]
+    for prec in (edt.EDT_FP64, edt.EDT_MIXED):
+        base = Config.from_workload(wl, precision=prec)
+        rows = GpuBackend(base).sub_rows()
+        fb, mb = plan_partition(rows, len(wl.freq_hz), 3)
+        for r in range(3):
+            c, _arrays = Config.from_workload(wl, precision=prec, sub_begin=mb[r],
+                                              sub_end=mb[r + 1]).c_config()
+            ctx, _ = edt.edt_create(c)
+            try:
+                got = np.diff(edt.edt_row_offsets(ctx, nsub))
+                with pytest.raises(edt.EdtError) as ei:       # no workspace: refused first
+                    edt.edt_import_rhs(ctx, 0, 0, 0, 1, 0)
+                assert ei.value.code == edt.EDT_ENOMEM_WS
+            finally:
+                edt.edt_destroy(ctx)
+            want = np.where((np.arange(nsub) >= mb[r]) & (np.arange(nsub) < mb[r + 1]), rows, 0)
+            assert np.array_equal(got, want)
+        shard_sum = np.zeros(nsub, dtype=np.int64)
+        for r in range(3):
+            c, _arrays = Config.from_workload(
+                wl, precision=prec, freq_hz=list(wl.freq_hz)[fb[r]:fb[r + 1]]).c_config()
+            ctx, _ = edt.edt_create(c)
+            try:
+                shard_sum += np.diff(edt.edt_row_offsets(ctx, nsub))
+            finally:
+                edt.edt_destroy(ctx)
+        assert np.array_equal(shard_sum, rows)
+    for b, e in ((3, 2), (0, nsub + 1), (-1, 2)):
+        c, _arrays = Config.from_workload(wl, sub_begin=b, sub_end=e).c_config()
+        with pytest.raises(edt.EdtError) as ei:
+            edt.edt_create(c)
+        assert ei.value.code == edt.EDT_EINVAL
