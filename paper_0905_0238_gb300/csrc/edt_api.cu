@@ -101,7 +101,7 @@ struct edt_ctx {
   void* ws = nullptr;
   Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_jact, r_jmap, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_g32lo, r_rowmax, r_gscale, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
-      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_x, r_r, r_vhat, r_vfull, r_gscr, r_adj, r_gacc, r_status, r_flags,
+      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_tpart, r_x, r_r, r_rpart, r_vhat, r_vfull, r_gscr, r_adj, r_gacc, r_status, r_flags,
       r_kzP, r_kzp, r_kzgoff, r_kzvoff, r_kzG, r_kzT, r_kzb, r_kzx;
   Dev dev{};
   cudaStream_t last_stream = nullptr;
@@ -622,8 +622,11 @@ void layout(edt_ctx* c) {
   take(c->r_dinv32, mixed && c->cfg.refine > 0 ? ns * nz * sizeof(float) : 0);
   take(c->r_b, ns * nz * 2 * sizeof(double));
   take(c->r_tr, ns * sizeof(double));
+  take(c->r_tpart, mixed ? std::max<size_t>(c->nslot, 1) * gram_trace_parts() * sizeof(double) : 0);
   take(c->r_x, ns * nz * 2 * sizeof(double));
   take(c->r_r, ns * nz * 2 * sizeof(double));
+  take(c->r_rpart, mixed && c->cfg.refine > 0
+                       ? ns * size_t(refine_stride(c->rows_max_sub)) * nz * 2 * sizeof(double) : 0);
   take(c->r_vhat, ns * nz * sizeof(double2));
   take(c->r_vfull, (c->win ? nxy : N) * nz * sizeof(double2));
   // misfit gradients: line geometry, mixed path (their dJ/dg buffer aliases r_g64, which
@@ -720,8 +723,11 @@ void bind(edt_ctx* c) {
   d.dinv32 = c->r_dinv32.bytes ? at<float*>(c, c->r_dinv32) : nullptr;
   d.b = at<double*>(c, c->r_b);
   d.trace = at<double*>(c, c->r_tr);
+  d.tpart = c->r_tpart.bytes ? at<double*>(c, c->r_tpart) : nullptr;
   d.x = at<double*>(c, c->r_x);
   d.r = at<double*>(c, c->r_r);
+  d.rpart = c->r_rpart.bytes ? at<double*>(c, c->r_rpart) : nullptr;
+  d.rf_stride = refine_stride(c->rows_max_sub);
   d.vhat = at<double2*>(c, c->r_vhat);
   d.vfull = at<double2*>(c, c->r_vfull);
   d.gscr = c->r_gscr.bytes ? at<double2*>(c, c->r_gscr) : nullptr;
@@ -830,10 +836,7 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_ev(c, 2, 1, s);
   if (ov) EDT_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   prof_ev(c, 3, 0, s);
-  if (mixed) {
-    EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
-    EDT_TRY(launch_gram_scale(d, s));
-  }
+  if (mixed) EDT_TRY(launch_gram_scale(d, s));
   prof_ev(c, 3, 1, s);
   prof_ev(c, 4, 0, s);
   if (mixed) {
@@ -857,7 +860,6 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_ev(c, 7, 0, s);
   if (mixed) {
     for (int it = 0; it < c->cfg.refine; ++it) {
-      EDT_TRY(cudaMemsetAsync(d.r, 0, sizeof(double) * d.nsub * d.nz * 2, s));
       EDT_TRY(launch_refine(d, s));
       EDT_TRY(launch_refine_update(d, s));
     }
@@ -1380,7 +1382,6 @@ int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr,
   EDT_TRYI(kernel_rows(c, s));
   EDT_TRYI(transform_rhs(c, D, D_dtype, s));
   if (mixed) {
-    EDT_TRY(cudaMemsetAsync(d.trace, 0, sizeof(double) * d.nsub, s));
     EDT_TRY(launch_gram_scale(d, s));
     EDT_TRY(launch_gram_tc(d, s));
     EDT_TRY(launch_gram_reduce(d, s));
@@ -1421,24 +1422,24 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   o->last_status = c->last_status;
   // kernels launched by one edt_invert: green (3), per frequency chunk transform (2) and
   // right-hand sides (1), Gram (FP64: 1; mixed: tensor-core + reduce 2), batched Cholesky,
-  // per refinement step (2), inverse (1)
+  // per refinement step (3: partial residuals, their ordered sum, the update), inverse (1)
   int tr_launches = c->fchunk > 0 ? 3 * ((c->nf + c->fchunk - 1) / c->fchunk) : 0;
   if (c->band_mode) {
     tr_launches = 0;
     for (const BandChunk& ch : c->bchunks) tr_launches += 1 + (ch.nbcol > 0) + (ch.nrow > 0);
   }
   const int chol_n = c->dev.chol_df ? chol_dfloat_launches(c->nz) : chol_launches(c->nz);
-  o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 2 * c->cfg.refine : 5) + tr_launches +
+  o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 3 * c->cfg.refine : 5) + tr_launches +
                            chol_n + gram_scale_launches(c->dev);
   // solver variants replace the Cholesky launch: trace, two projections, the solve (Cholesky
   // or Jacobi), the back-projection with the disk; the Jacobi kernel alone without it
   if (c->variant) o->launches_per_invert += (c->kz_p.empty() ? 1 : 5) - chol_launches(c->nz);
   if (c->win) {
     // green (3), rows (3) per frequency that keeps any, data (2), Gram (2), Cholesky,
-    // refinement (2 per step), inverse (completion, FP64 row and column transforms, output: 3 or 4)
+    // refinement (3 per step), inverse (completion, FP64 row and column transforms, output: 3 or 4)
     int fk = 0;
     for (int n : c->nact) fk += n > 0;
-    o->launches_per_invert = 3 + 3 * fk + 2 + 2 + chol_n + 2 * c->cfg.refine +
+    o->launches_per_invert = 3 + 3 * fk + 2 + 2 + chol_n + 3 * c->cfg.refine +
                              (c->ny > 1 ? 4 : 3);
   }
   o->freq_chunk = c->band_mode ? c->band_maxplanes : c->fchunk;

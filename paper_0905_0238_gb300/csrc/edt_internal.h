@@ -142,8 +142,12 @@ struct Dev {
   float* dinv32;                // [nsub][nz]
   double* b;                    // [nsub][nz][2]
   double* trace;                // [nsub]
+  double* tpart;                // [nslot][gram_trace_parts()] tensor-core Gram: trace of each
+                                //   segment per producer warp, summed in order by the reduction
   double* x;                    // [nsub][nz][2]
   double* r;                    // [nsub][nz][2]
+  double* rpart;                // [nsub][rf_stride][nz][2] refinement: each CTA's partial
+  int rf_stride;                //   residual, summed in CTA order into r (deterministic)
   double2* vhat;                // [nsub][nz]
   double2* vfull;               // [N][nz] scratch for the forward model (Vhat of V)
   // misfit gradients (line geometry, mixed path)
@@ -210,6 +214,7 @@ cudaError_t fft2_f64(const Dev& d, double2* X, int planes, int ny, int sign, dou
 cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace
 int gram_scale_launches(const Dev& d);                          // FP16 operand scales: 0 or 2 kernels
+int gram_trace_parts();                                         // trace partials per Gram segment
 cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s);    // per-segment FP16 operand scales
 // partials -> G, b (FP64); df_out: the lower triangle of G + lam I as double-float pairs
 cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s, int df_out = 0);
@@ -230,7 +235,9 @@ int chol_dfloat_launches(int nz);
 cudaError_t launch_chol_dfloat_resolve(const Dev& d, cudaStream_t s);           // x = (LL^T)^-1 b
 cudaError_t launch_chol_dfloat_export(const Dev& d, double* out, cudaStream_t s); // factor as FP64
 cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s, const CholLookahead* la = nullptr);
-cudaError_t launch_refine(const Dev& d, cudaStream_t s);          // r += Ahat^T (dhat - Ahat x)
+// r = Ahat^T (dhat - Ahat x): per-CTA partials, then their sum in CTA order (2 launches)
+cudaError_t launch_refine(const Dev& d, cudaStream_t s);
+int refine_stride(long long rows_max_sub);                      // refinement CTAs per subproblem, at most
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s);   // x += (LL^T)^-1 (r - lam x)
 cudaError_t launch_inverse(const Dev& d, void* V, int V_dtype, cudaStream_t s);
 cudaError_t launch_forward(const Dev& d, const void* V, int V_dtype, void* D, int D_dtype,

@@ -587,7 +587,6 @@ cudaError_t launch_invert_adjoint(const Dev& d, const void* Vbar, int Vbar_dtype
   if ((e = launch_chol_resolve(d, s)) != cudaSuccess) return e;
   if (refine > 0 && (e = cudaMemsetAsync(d.rhs, 0, rhs_bytes, s)) != cudaSuccess) return e;
   for (int it = 0; it < refine; ++it) {
-    if ((e = cudaMemsetAsync(d.r, 0, sizeof(double) * d.nsub * d.nz * 2, s)) != cudaSuccess) return e;
     if ((e = launch_refine(d, s)) != cudaSuccess) return e;
     adj_addb_kernel<<<152, 256, 0, s>>>(d);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -367,11 +367,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
       }
       tc_fence_before();
       mbar_arrive(acc_empty);
-      // trace(G) of this segment, summed over the warp in FP64 (the kernel-row scale
-      // divided out exactly: it is a power of two)
+      // trace(G) of this warp's rows of the segment, summed over the warp in FP64 (the
+      // kernel-row scale divided out exactly: it is a power of two); the reduction adds the
+      // partials of all warps and segments of a subproblem in a fixed order
       double tr = (double(tr_hi) - double(tr_lo)) * pow2d(-2 * se.x);
       for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-      if (lane == 0) atomicAdd(&d.trace[d.seg_m[slot]], tr);
+      if (lane == 0) d.tpart[size_t(slot) * PRODUCER_WARPS + warp] = tr;
     }
     // a table copy still in flight after an early exit must land before the CTA leaves
     if (ptid == 0)
@@ -431,6 +432,13 @@ __global__ void gram_scale_kernel(Dev d) {
 // Sum the partial tiles of each subproblem into the FP64 Gram (both triangles) and b.  With
 // df_out (the double-float factorisation follows) the lower triangle of G + lam I is written
 // instead, lam = alpha * trace, each value as a double-float pair (float2) in the same 8 bytes.
+// trace(G) of subproblem m: the per-warp partials of its segments, in slot and warp order
+__device__ __forceinline__ double trace_of(const Dev& d, int sl0, int sl1) {
+  double t = 0.0;
+  for (int i = sl0 * PRODUCER_WARPS; i < sl1 * PRODUCER_WARPS; ++i) t += d.tpart[i];
+  return t;
+}
+
 __global__ void gram_reduce_kernel(Dev d, int df_out) {
   const int m = blockIdx.y;
   const int nz = d.nz, nzp = nzp_of(nz), ncols = cols_of(nzp);
@@ -438,6 +446,7 @@ __global__ void gram_reduce_kernel(Dev d, int df_out) {
   const int sl0 = d.m_slot0[m], sl1 = d.m_slot0[m + 1];
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nG = (long long)nz * nz;
+  if (e == 0) d.trace[m] = trace_of(d, sl0, sl1);
   if (e < nG) {
     const int zi = int(e / nz), zj = int(e - (long long)zi * nz);
     if (df_out && zj > zi) return;
@@ -458,7 +467,7 @@ __global__ void gram_reduce_kernel(Dev d, int df_out) {
         sh = t;
       }
       if (zi == zj) {
-        const double lam = d.alpha * d.trace[m];
+        const double lam = d.alpha * trace_of(d, sl0, sl1);
         const float lh = __double2float_rn(lam), ll = __double2float_rn(lam - double(lh));
         const float t = __fadd_rn(sh, lh), bb = __fsub_rn(t, sh);
         sl_ = __fadd_rn(sl_, __fadd_rn(__fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(lh, bb)), ll));
@@ -491,6 +500,8 @@ __global__ void gram_reduce_kernel(Dev d, int df_out) {
 }  // namespace
 
 int tc_cols(int nz) { return cols_of(nzp_of(nz)); }
+
+int gram_trace_parts() { return PRODUCER_WARPS; }
 
 int tc_smem_bytes(int nz, int passes) {
   const int zr = zrows_of(nzp_of(nz));

@@ -4,7 +4,9 @@
 // a(z) = |s_f| g(k_p, z) g(k_q, z) is rebuilt from the FP32 table sqrt|s_f| g (rounded from
 // the FP64 depth march), the row's prediction sum_z a(z) x(z) and residual u = d~ - a.x are
 // formed in FP32, and w Re(conj(a(z)) u) is accumulated per lane in FP32 over the warp's 32
-// rows (partial sums of <= 32 terms), then summed across warps and blocks in FP64.  Table
+// rows (partial sums of <= 32 terms), then summed across warps in FP64; each CTA stores its
+// partial and refine_sum adds the partials of a subproblem in CTA order, so repeated calls
+// give the same bits.  Table
 // rows are read with 16-byte loads (two depths per load) when nz is even, two rows at a time
 // per warp so that both rows' loads are in flight together.  Each warp walks its rows two at a time so that the table loads of
 // both rows are in flight together; rows p and -p sit side by side in the row order and
@@ -116,12 +118,13 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
     red[warp][0][z + 1] = acc[t][1][0]; red[warp][1][z + 1] = acc[t][1][1];
   }
   __syncthreads();
+  double* part = d.rpart + (size_t(m) * d.rf_stride + blockIdx.x) * nz * 2;
   for (int i = threadIdx.x; i < 2 * nz; i += blockDim.x) {
     const int z = i >> 1, k = i & 1;
     double sacc = 0.0;
 #pragma unroll
     for (int w = 0; w < RF_WARPS; ++w) sacc += red[w][k][z];
-    atomicAdd(&d.r[(size_t(m) * nz + z) * 2 + k], sacc);
+    part[i] = sacc;
   }
 }
 
@@ -267,16 +270,47 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_df_kernel(Dev d) {
         red[warp][k][z + j] = double(as[t][j][k]) + double(al_[t][j][k]);
   }
   __syncthreads();
+  double* part = d.rpart + (size_t(m) * d.rf_stride + blockIdx.x) * nz * 2;
   for (int i = threadIdx.x; i < 2 * nz; i += blockDim.x) {
     const int z = i >> 1, k = i & 1;
     double sacc = 0.0;
 #pragma unroll
     for (int w = 0; w < RF_WARPS; ++w) sacc += red[w][k][z];
-    atomicAdd(&d.r[(size_t(m) * nz + z) * 2 + k], sacc);
+    part[i] = sacc;
+  }
+}
+
+// r(m) = the partials of subproblem m's CTAs in CTA order (zero for a failed subproblem,
+// whose CTAs stored nothing)
+__global__ void __launch_bounds__(256) refine_sum_kernel(Dev d, int rpc) {
+  const int m = blockIdx.x, nz = d.nz;
+  const long long nr = d.row_off[m + 1] - d.row_off[m];
+  const int ncta = d.status[m] == EDT_OK ? int((nr + rpc - 1) / rpc) : 0;
+  const double* part = d.rpart + size_t(m) * d.rf_stride * nz * 2;
+  for (int i = threadIdx.x; i < 2 * nz; i += blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < ncta; ++c) t += part[size_t(c) * nz * 2 + i];
+    d.r[size_t(m) * nz * 2 + i] = t;
+  }
+}
+
+// rows per refinement CTA of the autotuned shape tune_rf (warps x rows per warp)
+int refine_rows_per_cta(int tune_rf) {
+  switch (tune_rf) {
+    case 1: return 8 * 32;
+    case 2: return 4 * 64;
+    case 3: return 8 * 16;
+    default: return 4 * 32;
   }
 }
 
 }  // namespace
+
+int refine_stride(long long rows_max_sub) {
+  int least = refine_rows_per_cta(0);
+  for (int t = 1; t <= 3; ++t) least = std::min(least, refine_rows_per_cta(t));
+  return int((std::max(rows_max_sub, 1LL) + least - 1) / least);
+}
 
 template <int W, int R>
 void refine_df_shape(const Dev& d, cudaStream_t s) {
@@ -308,14 +342,15 @@ cudaError_t launch_refine(const Dev& d, cudaStream_t s) {
       case 3: refine_df_shape<8, 16>(d, s); break;
       default: refine_df_shape<4, 32>(d, s); break;
     }
-    return cudaGetLastError();
+  } else {
+    switch (d.tune_rf) {
+      case 1: refine_shape<8, 32>(d, s); break;
+      case 2: refine_shape<4, 64>(d, s); break;
+      case 3: refine_shape<8, 16>(d, s); break;
+      default: refine_shape<4, 32>(d, s); break;
+    }
   }
-  switch (d.tune_rf) {
-    case 1: refine_shape<8, 32>(d, s); break;
-    case 2: refine_shape<4, 64>(d, s); break;
-    case 3: refine_shape<8, 16>(d, s); break;
-    default: refine_shape<4, 32>(d, s); break;
-  }
+  refine_sum_kernel<<<d.nsub, 256, 0, s>>>(d, refine_rows_per_cta(d.tune_rf));
   return cudaGetLastError();
 }
 

@@ -96,12 +96,7 @@ __global__ void st_prep_kernel(StBatch b) {
   split_ff(two, t.z, t.w);
   b.zt[S.o_v + z] = t;
   b.zl[S.o_v + z] = l;
-  b.r[(S.o_v + z) * 2 + 0] = 0.0;
-  b.r[(S.o_v + z) * 2 + 1] = 0.0;
-  if (z == 0) {
-    b.trace[q] = 0.0;
-    b.status[q] = EDT_OK;
-  }
+  if (z == 0) b.status[q] = EDT_OK;
 }
 
 // ------------------------------------------------------------------------- depth march
@@ -245,8 +240,9 @@ __global__ void __launch_bounds__(256) st_tiles_kernel(StBatch b) {
       *reinterpret_cast<uint4*>(b.tiles + tile_off(S, s, 1, z, c)) = l;
     }
     for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-    if (lane == 0 && tr != 0.f) atomicAdd(&b.trace[q], S.alpha * double(tr));
+    if (lane == 0) b.twtr[w] = S.alpha * double(tr);
   } else {
+    if (lane == 0) b.twtr[w] = 0.0;
     const int drow0 = S.nzt * ST_TILE;
     if (lane < 8) {
       // chunk c = lane: complex rows 4c .. 4c + 3 of the stage, data d' = conj(u_f) d (u_f the
@@ -444,9 +440,21 @@ __global__ void __launch_bounds__(GS_THREADS, 1) st_gram_kernel(StBatch b) {
   }
 }
 
+// alpha trace(Ahat^T Ahat) of each request: the parts of its tile-writer warps in a fixed order
+// (lane l takes parts l, l + 32, ...; then a butterfly over the lanes), one warp per request.
+__global__ void __launch_bounds__(256) st_trace_kernel(StBatch b) {
+  const int q = int(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (q >= b.nreq) return;
+  double t = 0.0;
+  for (long long w = b.pre_tw[q] + lane; w < b.pre_tw[q + 1]; w += 32) t += b.twtr[w];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) b.trace[q] = t;
+}
+
 // ------------------------------------------------------------------------- refinement residual
-// r += Ahat^T (dhat - Ahat x) over 256 rows per CTA (one warp per 32 rows, lanes over depth);
-// FP32 products, warp partials summed in FP64 and added to r with FP64 atomics.
+// Ahat^T (dhat - Ahat x) over 256 rows per CTA (one warp per 32 rows, lanes over depth); FP32
+// products, warp partials summed in FP64 into the CTA's partial; st_rsum adds a request's
+// partials in CTA order.
 __global__ void __launch_bounds__(256) st_refine_kernel(StBatch b) {
   constexpr int NZL = ST_MAX_NZ / 32;
   __shared__ float xs[2][ST_MAX_NZ];
@@ -501,12 +509,28 @@ __global__ void __launch_bounds__(256) st_refine_kernel(StBatch b) {
     if (z < S.nz) { red[warp][0][z] = acc0[i]; red[warp][1][z] = acc1[i]; }
   }
   __syncthreads();
+  double* part = b.rcp + 2 * (b.pre_rz[q] + (long long)chunk * S.nz);
   for (int e = threadIdx.x; e < 2 * S.nz; e += blockDim.x) {
     const int side = e / S.nz, z = e - side * S.nz;
     double t = 0.0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += double(red[w][side][z]);
-    atomicAdd(&b.r[(S.o_v + z) * 2 + side], t);
+    part[e] = t;
+  }
+}
+
+// r of request blockIdx.x: its refinement CTAs' partials in CTA order (zero after a failure,
+// when they stored nothing)
+__global__ void __launch_bounds__(256) st_rsum_kernel(StBatch b) {
+  const int q = blockIdx.x;
+  const StSub S = b.sub[q];
+  const int ncta = b.status[q] == EDT_OK ? int(b.pre_rc[q + 1] - b.pre_rc[q]) : 0;
+  const double* part = b.rcp + 2 * b.pre_rz[q];
+  for (int e = threadIdx.x; e < 2 * S.nz; e += blockDim.x) {
+    const int side = e / S.nz, z = e - side * S.nz;
+    double t = 0.0;
+    for (int c = 0; c < ncta; ++c) t += part[size_t(c) * 2 * S.nz + e];
+    b.r[(S.o_v + z) * 2 + side] = t;
   }
 }
 
@@ -536,7 +560,10 @@ cudaError_t launch_stream_batch(const StBatch& b, int nmax, cudaStream_t s, cuda
   mark(2);
   if (b.tot_eb > 0) st_eval_kernel<<<unsigned(b.tot_eb), 256, 0, s>>>(b);
   mark(3);
-  if (b.tot_tw > 0) st_tiles_kernel<<<blocks_for(b.tot_tw * 32, 256), 256, 0, s>>>(b);
+  if (b.tot_tw > 0) {
+    st_tiles_kernel<<<blocks_for(b.tot_tw * 32, 256), 256, 0, s>>>(b);
+    st_trace_kernel<<<blocks_for((long long)b.nreq * 32, 256), 256, 0, s>>>(b);
+  }
   mark(4);
   if (b.ncta > 0) st_gram_kernel<<<b.ncta, GS_THREADS, st_gram_smem_bytes(), s>>>(b);
   mark(5);
@@ -552,7 +579,10 @@ cudaError_t launch_stream_batch(const StBatch& b, int nmax, cudaStream_t s, cuda
                                       b.cb_ntile_host, 1, s);
   if (e != cudaSuccess) return e;
   mark(6);
-  if (b.tot_rc > 0) st_refine_kernel<<<unsigned(b.tot_rc), 256, 0, s>>>(b);
+  if (b.tot_rc > 0) {
+    st_refine_kernel<<<unsigned(b.tot_rc), 256, 0, s>>>(b);
+    st_rsum_kernel<<<unsigned(b.nreq), 256, 0, s>>>(b);
+  }
   mark(7);
   e = launch_refine_update_var(d, nmax, s);
   mark(8);

@@ -42,7 +42,7 @@ ReqShape shape_of(const edt_sub1d& s) {
 // Device bytes of one request inside a batch (every per-request slice, plus its alignment).
 size_t bytes_of(const ReqShape& r) {
   size_t b = 0;
-  b += sizeof(StSub) + 7 * sizeof(long long) + sizeof(int) + 2 * sizeof(long long);
+  b += sizeof(StSub) + 8 * sizeof(long long) + sizeof(int) + 2 * sizeof(long long);
   b += size_t(r.nzt) * (r.nzt + 1) / 2 * sizeof(StItem);
   b += sizeof(double) * size_t(3 * r.nl + r.nf + r.nk);
   b += size_t(r.nrow) * (sizeof(int4) + 2 * sizeof(float4));        // rows, data, rotated data
@@ -53,6 +53,8 @@ size_t bytes_of(const ReqShape& r) {
   b += size_t(r.nz) * r.nz * (sizeof(double) + sizeof(float));      // G, L32
   b += size_t(r.nz) * (sizeof(double) + sizeof(float) + 6 * sizeof(double));   // dinv(32), b, x, r
   b += sizeof(double) + sizeof(int);                                 // trace, status
+  b += size_t(r.kst) * (4 * r.nzt + 1) * sizeof(double);            // trace parts
+  b += size_t((r.nrow + ST_REFINE_ROWS - 1) / ST_REFINE_ROWS) * r.nz * 2 * sizeof(double);  // residual partials
   b += size_t(ST_MAX_NZ / 32) * (sizeof(int) + sizeof(long long));   // blocked-Cholesky step lists
   return al(b, 64);
 }
@@ -244,7 +246,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   // ---- arena layout: inputs (one host-to-device copy), device scratch, outputs (one copy back)
   size_t off = 0;
   auto take = [&](size_t bytes, size_t a = AL) { off = al(off, a); size_t o = off; off += bytes; return o; };
-  long long n_dbl = 0, n_rows = 0, n_z = 0, n_coef = 0, n_g = 0, n_G = 0;
+  long long n_dbl = 0, n_rows = 0, n_z = 0, n_coef = 0, n_g = 0, n_G = 0, n_tw = 0, n_rz = 0;
   size_t n_tile = 0;
   for (int i = 0; i < n; ++i) {
     n_dbl += 3 * sh[i].nl + sh[i].nf + sh[i].nk;
@@ -254,9 +256,11 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
     n_g = (n_g + 31) / 32 * 32 + sh[i].fk * sh[i].nzs;
     n_tile = al(n_tile, TILE_AL) + sh[i].tile_bytes;
     n_G += (long long)sh[i].nz * sh[i].nz;
+    n_tw += (long long)sh[i].kst * (4 * sh[i].nzt + 1);
+    n_rz += (long long)((sh[i].nrow + ST_REFINE_ROWS - 1) / ST_REFINE_ROWS) * sh[i].nz;
   }
   const size_t o_sub = take(sizeof(StSub) * n);
-  const size_t o_pre = take(sizeof(long long) * 6 * size_t(n + 1));
+  const size_t o_pre = take(sizeof(long long) * 7 * size_t(n + 1));
   const size_t o_subn = take(sizeof(int) * n);
   const size_t o_goff = take(sizeof(long long) * n);
   const size_t o_voff = take(sizeof(long long) * n);
@@ -286,6 +290,8 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   const size_t o_b = take(sizeof(double) * 2 * n_z);
   const size_t o_r = take(sizeof(double) * 2 * n_z);
   const size_t o_trace = take(sizeof(double) * n);
+  const size_t o_twtr = take(sizeof(double) * std::max<long long>(n_tw, 1));
+  const size_t o_rcp = take(sizeof(double) * 2 * std::max<long long>(n_rz, 1));
   const size_t x_bytes = sizeof(double) * 2 * size_t(n_z);
   const size_t o_x = take(x_bytes);                          // output section: x, status, flags
   const size_t o_status = o_x + x_bytes;
@@ -304,7 +310,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   StSub* sub = reinterpret_cast<StSub*>(P + o_sub);
   long long* pre = reinterpret_cast<long long*>(P + o_pre);
   long long *pre_z = pre, *pre_fk = pre + (n + 1), *pre_eb = pre + 2 * (n + 1), *pre_tw = pre + 3 * (n + 1),
-            *pre_rc = pre + 4 * (n + 1), *row_off = pre + 5 * (n + 1);
+            *pre_rc = pre + 4 * (n + 1), *row_off = pre + 5 * (n + 1), *pre_rz = pre + 6 * (n + 1);
   int* subn = reinterpret_cast<int*>(P + o_subn);
   long long* goff = reinterpret_cast<long long*>(P + o_goff);
   long long* voff = reinterpret_cast<long long*>(P + o_voff);
@@ -314,7 +320,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   float* data = reinterpret_cast<float*>(P + o_data);
   long long c_dbl = 0, c_rows = 0, c_z = 0, c_coef = 0, c_g = 0, c_G = 0;
   size_t c_tile = 0;
-  pre_z[0] = pre_fk[0] = pre_eb[0] = pre_tw[0] = pre_rc[0] = row_off[0] = 0;
+  pre_z[0] = pre_fk[0] = pre_eb[0] = pre_tw[0] = pre_rc[0] = row_off[0] = pre_rz[0] = 0;
   for (int i = 0; i < n; ++i) {
     const edt_sub1d& q = subs[i0 + i];
     const ReqShape& r = sh[i];
@@ -358,6 +364,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
     pre_eb[i + 1] = pre_eb[i] + (r.fk + 7) / 8;
     pre_tw[i + 1] = pre_tw[i] + (long long)r.kst * (4 * r.nzt + 1);
     pre_rc[i + 1] = pre_rc[i] + (r.nrow + ST_REFINE_ROWS - 1) / ST_REFINE_ROWS;
+    pre_rz[i + 1] = pre_rz[i] + (long long)((r.nrow + ST_REFINE_ROWS - 1) / ST_REFINE_ROWS) * r.nz;
     row_off[i + 1] = row_off[i] + r.nrow;
   }
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -398,6 +405,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   const long long* dpre = reinterpret_cast<const long long*>(A + o_pre);
   b.pre_z = dpre; b.pre_fk = dpre + (n + 1); b.pre_eb = dpre + 2 * (n + 1); b.pre_tw = dpre + 3 * (n + 1);
   b.pre_rc = dpre + 4 * (n + 1);
+  b.pre_rz = dpre + 6 * (n + 1);
   b.row_off = const_cast<long long*>(dpre + 5 * (n + 1));
   b.items = reinterpret_cast<const StItem*>(A + o_items);
   b.cta_item0 = reinterpret_cast<const int*>(A + o_cta);
@@ -418,6 +426,8 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   b.x = reinterpret_cast<double*>(A + o_x);
   b.r = reinterpret_cast<double*>(A + o_r);
   b.trace = reinterpret_cast<double*>(A + o_trace);
+  b.twtr = reinterpret_cast<double*>(A + o_twtr);
+  b.rcp = reinterpret_cast<double*>(A + o_rcp);
   b.status = reinterpret_cast<int*>(A + o_status);
   b.sub_n = reinterpret_cast<int*>(A + o_subn);
   b.sub_goff = reinterpret_cast<long long*>(A + o_goff);
@@ -432,7 +442,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   b.cb_tpre = reinterpret_cast<const long long*>(A + o_cbpre);
   b.cb_nact_host = cb_nact.data();
   b.cb_ntile_host = cb_ntile.data();
-  int nlaunch = 1 + (b.tot_fk > 0) + (b.tot_eb > 0) + (b.tot_tw > 0) + (ncta > 0) + 1 + (b.tot_rc > 0) + 1;
+  int nlaunch = 1 + (b.tot_fk > 0) + (b.tot_eb > 0) + 2 * (b.tot_tw > 0) + (ncta > 0) + 1 + 2 * (b.tot_rc > 0) + 1;
   for (int k = 0; k < nstep; ++k) nlaunch += (cb_nact[k] > 0) + (cb_ntile[k] > 0);
 
   cudaError_t ce = cudaSuccess;

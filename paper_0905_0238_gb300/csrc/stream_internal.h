@@ -47,6 +47,7 @@ struct StBatch {
   const long long* pre_eb;       //            of ceil(nf * nk / 8)  (table-evaluation CTAs)
   const long long* pre_tw;       //            of kst * (4 nzt + 1)  (tile-writer warps)
   const long long* pre_rc;       //            of ceil(nrow / 256)   (refinement CTAs)
+  const long long* pre_rz;       //            of ceil(nrow / 256) * nz (refinement partials / 2)
   const StItem* items;           // Gram items grouped by CTA
   const int* cta_item0;          // [ncta + 1]
   const double* dbl;             // layer tables, frequencies, wavenumbers
@@ -66,6 +67,8 @@ struct StBatch {
   double* x;
   double* r;
   double* trace;                 // alpha trace(Ahat^T Ahat), then lam
+  double* twtr;                  // [tot_tw] alpha * trace part of each tile-writer warp
+  double* rcp;                   // [pre_rz[nreq]][2] each refinement CTA's partial residual
   int* status;
   long long* row_off;            // [nreq + 1] prefix sums of nrow
   int* sub_n;                    // [nreq]

@@ -27,5 +27,5 @@ def test_invert_host_matches_device_call(pipe):
             s.invert_host(D, V)
         torch.cuda.synchronize()
         for V, w in zip(Vh, want):
-            # the refinement sums across blocks with FP64 atomics: equal up to that order
-            assert rel_l2(V.numpy(), w) < 1e-6
+            # every cross-block sum runs in a fixed order: the same bits as the direct call
+            assert np.array_equal(V.numpy(), w)

@@ -110,8 +110,8 @@ def test_graph_replay_matches_direct_calls():
             out.fill_(float("nan"))
             s.invert(Dd, out=out)
             st.synchronize()
-            # FP64 atomics in the trace and residual sums make the last bits order-dependent
-            assert rel_l2(out.cpu().numpy(), ref) < 1e-10
+            # every cross-block sum runs in a fixed order: the same bits as the direct call
+            assert np.array_equal(out.cpu().numpy(), ref)
         s.set_graph(False)
 
 
