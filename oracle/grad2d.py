@@ -152,6 +152,71 @@ def grad_c(wl, V, D):
     return out
 
 
+def invert_tangent(wl, D, l):
+    """(V, dV/dc_l): the damped inversion of :func:`oracle.edt2d.invert` and its derivative with
+    respect to the velocity of layer l, by forward-mode differentiation of every step in order.
+
+    The data D do not depend on the reference; the kernel rows do (eq. M, through g), and so
+    do the normal matrix and the damping lam = alpha ||Ahat||_F^2.  The set of kept rows is
+    held fixed (the evanescent cut is a threshold on the slowest velocity; a derivative sees
+    no change of it).  Per midpoint index m, with x the damped least-squares solution of
+    Ahat x = dhat:
+        (Ahat^T Ahat + lam I) x = Ahat^T dhat,
+    differentiated:
+        (Ahat^T Ahat + lam I) dx = dAhat^T (dhat - Ahat x) - Ahat^T dAhat x - dlam x,
+        dlam = 2 alpha <Ahat, dAhat>_F,
+    with dAhat the real and imaginary parts of dA = s_f (dg_p g_q + g_p dg_q).  The system
+    for dx is solved with the R factor of the same augmented QR the solution uses
+    (R^T R = Ahat^T Ahat + lam I).  Then dV follows from dVhat by the same linear map as V
+    from Vhat (eq. VSym and the inverse lateral DFT)."""
+    from scipy.linalg import solve_triangular
+    from .edt2d import (data_transform, kept_rows, split_rhs, hermitian_complete,
+                        inverse_lateral_dft)
+    N = wl.nx
+    D2 = data_transform(D)
+    g, dg = green_table_tangent(wl, l)
+    s = born_scale(wl)
+    vh = np.zeros((N // 2 + 1, wl.nz), dtype=np.complex128)
+    dvh = np.zeros_like(vh)
+    for m in range(N // 2 + 1):
+        rows = kept_rows(wl, m)
+        if len(rows) == 0:
+            continue
+        f, p = rows[:, 0], rows[:, 1]
+        q = (p - m) % N
+        A = s[f, None] * g[f, p, :] * g[f, q, :]
+        dA = s[f, None] * (dg[f, p, :] * g[f, q, :] + g[f, p, :] * dg[f, q, :])
+        Ahat = np.vstack([A.real, A.imag])
+        dAhat = np.vstack([dA.real, dA.imag])
+        dp, dm = split_rhs(D2, m, rows)
+        self_paired = (m == 0) or (2 * m == N)
+        cols = [np.concatenate([dp.real, dp.imag])]
+        if not self_paired:
+            cols.append(np.concatenate([dm.real, dm.imag]))
+        dhat = np.stack(cols, axis=1)
+        lam = wl.alpha * np.sum(Ahat ** 2)
+        dlam = 2.0 * wl.alpha * np.sum(Ahat * dAhat)
+        nz = wl.nz
+        aug = np.vstack([Ahat, np.sqrt(lam) * np.eye(nz)])
+        Q, R = np.linalg.qr(aug, mode="reduced")
+        x = solve_triangular(R, Q.T @ np.vstack([dhat, np.zeros((nz, dhat.shape[1]))]), lower=False)
+        rhs = dAhat.T @ (dhat - Ahat @ x) - Ahat.T @ (dAhat @ x) - dlam * x
+        dx = solve_triangular(R, solve_triangular(R, rhs, trans="T", lower=False), lower=False)
+        vh[m] = x[:, 0] + (1j * x[:, 1] if not self_paired else 0.0)
+        dvh[m] = dx[:, 0] + (1j * dx[:, 1] if not self_paired else 0.0)
+    V = inverse_lateral_dft(hermitian_complete(vh, N)).real
+    dV = inverse_lateral_dft(hermitian_complete(dvh, N)).real
+    return V, dV
+
+
+def invert_grad_c(wl, D, Vbar):
+    """dL/dc_l = <Vbar, dV/dc_l> for every layer l (L any loss of the inverted model V with
+    dL/dV = Vbar), from :func:`invert_tangent`."""
+    Vbar = np.asarray(Vbar, dtype=np.float64)
+    return np.array([float(np.sum(Vbar * invert_tangent(wl, D, l)[1]))
+                     for l in range(len(wl.layer_vel))])
+
+
 def with_velocities(wl, vel):
     """A copy of the workload with the layer velocities replaced."""
     import copy

@@ -132,3 +132,77 @@ def test_planted_mistakes_fail_the_difference_pin(monkeypatch):
 
     monkeypatch.setattr(grad2d, "green_layered_tangent", inside_only)
     assert abs(grad2d.grad_c(wl, V, D)[l] - want) > 1e-2 * abs(want)
+
+
+# ---- the inversion's derivative with respect to the reference (dV/dc_l through the damped solve)
+def _inv_case(alpha, cutoff, nx=8, nz=5, nf=3, salt=4):
+    wl = tiny(nlayer=4, nx=nx, nz=nz, nf=nf)
+    wl.alpha = alpha
+    wl.cutoff = cutoff
+    rng = np.random.default_rng(salt)
+    V = synth.perturbation_blobs(rng, wl.nx, wl.dx, wl.nz, wl.dz, wl.z0, wl.layer_top,
+                                 wl.layer_vel, nblob=2, sigma=15.0)
+    from oracle import edt2d
+    D = edt2d.forward(wl, V)
+    D = D + 0.1 * np.sqrt(np.mean(np.abs(D) ** 2)) * synth.random_data(rng, D.shape)
+    return wl, D
+
+
+@pytest.mark.parametrize("l,alpha", [(0, 1e-1), (1, 1e-3), (3, 1e-2), (2, 1e-5)])
+def test_invert_tangent_matches_differences(l, alpha):
+    """dV/dc_l against central differences of the oracle's own inversion (no cut, so the row
+    set cannot change with the velocities), at strong and weak damping."""
+    from oracle import edt2d
+    wl, D = _inv_case(alpha, 0.0)
+    V, dV = grad2d.invert_tangent(wl, D, l)
+    assert rel(V, edt2d.invert(wl, D)[0]) < 1e-13
+
+    def V_of(c):
+        v = wl.layer_vel.copy()
+        v[l] = c
+        return edt2d.invert(grad2d.with_velocities(wl, v), D)[0]
+
+    want = central(V_of, wl.layer_vel[l], 1e-3 * wl.layer_vel[l])
+    assert rel(dV, want) < 1e-6
+
+
+@pytest.mark.parametrize("l", [1, 3])
+def test_invert_grad_c_with_the_cut_matches_differences(l):
+    """With the evanescent cut, layers other than the slowest leave the row set unchanged:
+    dL/dc_l = <Vbar, dV/dc_l> against central differences of L(c) = <Vbar, V(c)>."""
+    from oracle import edt2d
+    wl, D = _inv_case(1e-2, 1.0, nx=16, nz=6, nf=4, salt=5)
+    assert l != int(np.argmin(wl.layer_vel))
+    Vbar = np.random.default_rng(6).standard_normal((wl.nx, wl.nz))
+    gc = grad2d.invert_grad_c(wl, D, Vbar)
+
+    def L_of(c):
+        v = wl.layer_vel.copy()
+        v[l] = c
+        return float(np.sum(Vbar * edt2d.invert(grad2d.with_velocities(wl, v), D)[0]))
+
+    want = central(L_of, wl.layer_vel[l], 1e-3 * wl.layer_vel[l])
+    assert abs(gc[l] - want) < 1e-6 * abs(want)
+
+
+def test_invert_tangent_planted_mistake_fails_the_difference_pin(monkeypatch):
+    """A derivative of the table with the wrong sign (a plausible slip in the chain rule) is
+    caught by the difference pin at the damping where the lam term matters most."""
+    from oracle import edt2d
+    wl, D = _inv_case(1e-1, 0.0)
+    l = 1
+
+    def V_of(c):
+        v = wl.layer_vel.copy()
+        v[l] = c
+        return edt2d.invert(grad2d.with_velocities(wl, v), D)[0]
+
+    want = central(V_of, wl.layer_vel[l], 1e-3 * wl.layer_vel[l])
+    orig = grad2d.green_table_tangent
+
+    def half(w, ll):
+        g, dg = orig(w, ll)
+        return g, 0.5 * dg
+
+    monkeypatch.setattr(grad2d, "green_table_tangent", half)
+    assert rel(grad2d.invert_tangent(wl, D, l)[1], want) > 1e-2
