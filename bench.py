@@ -812,10 +812,13 @@ def main_grad(args, world, rank, local):
     for _ in range(3):
         inv.invert(D, out=Vout)
         inv.invert_adjoint(Vbar, out_dtype=torch.complex64)
+        inv.invert_vjp(Vbar, want_D=False)
     torch.cuda.synchronize()
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
     a2 = torch.cuda.Event(enable_timing=True)
+    a3 = torch.cuda.Event(enable_timing=True)
+    a4 = torch.cuda.Event(enable_timing=True)
     a0.record(stream)
     for _ in range(args.steps):
         inv.invert(D, out=Vout)
@@ -823,10 +826,20 @@ def main_grad(args, world, rank, local):
     for _ in range(args.steps):
         Dbar = inv.invert_adjoint(Vbar, out_dtype=torch.complex64)
     a2.record(stream)
+    for _ in range(args.steps):
+        _, gc_solve = inv.invert_vjp(Vbar, want_D=False)
+    a3.record(stream)
+    for _ in range(args.steps):
+        Dbar, gc_solve = inv.invert_vjp(Vbar, out_dtype=torch.complex64)
+    a4.record(stream)
     torch.cuda.synchronize()
     adj = dict(invert_ms=a0.elapsed_time(a1) / args.steps, invert_adjoint_ms=a1.elapsed_time(a2) / args.steps,
-               note="edt_invert_adjoint (dL/dD through the damped solve, one refinement step) after "
-                    "edt_invert on the production inversion (cut on); c64 Dbar")
+               invert_grad_c_ms=a2.elapsed_time(a3) / args.steps,
+               invert_vjp_both_ms=a3.elapsed_time(a4) / args.steps,
+               note="after edt_invert on the production inversion (cut on, one refinement step): "
+                    "edt_invert_adjoint (dL/dD through the damped solve, c64 Dbar); edt_invert_vjp "
+                    "with dL/dc only (rows, normal-matrix and damping derivatives, reverse depth "
+                    "march) and with both outputs")
     del inv
     if rank != 0:
         if world > 1:

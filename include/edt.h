@@ -312,10 +312,29 @@ int edt_misfit_grad(edt_ctx* ctx, const void* V_dev, int V_dtype, const void* D_
  * refinement steps as the forward solve (the transpose of the forward's own linear map),
  * and for every kept row the split and the data transform reversed.  Vbar_dev: [nx][nz]
  * (EDT_F32/EDT_F64); Dbar_dev: [nfreq][nx][nx] (EDT_C64/EDT_C128), fully written.  The
- * solve's scratch (b, x, the residual and the right-hand sides) is overwritten; the
- * factors and edt_get_vhat's result are not, so the call may be repeated for other Vbar. */
+ * solve's scratch (b, x, the residual) is overwritten; the factors, the right-hand sides and
+ * edt_get_vhat's result are not, so the call may be repeated for other Vbar. */
 int edt_invert_adjoint(edt_ctx* ctx, const void* Vbar_dev, int Vbar_dtype, void* Dbar_dev,
                        int Dbar_dtype, void* stream);
+
+/* The inversion's vector-Jacobian products with respect to the data and to the reference
+ * (line geometry, EDT_MIXED), for Vbar = dL/dV after a successful edt_invert (same
+ * preconditions as edt_invert_adjoint):
+ *   Dbar_dev (may be null): as edt_invert_adjoint;
+ *   gc_dev   (may be null): double[nlayer], gc[l] = dL/dc_l through the damped solve.  Per
+ *     midpoint index m the solution of (Ahat^T Ahat + lam I) x = Ahat^T dhat, lam = alpha
+ *     tr(Ahat^T Ahat), depends on the layer velocities through the kernel rows (eq. M, the
+ *     depth march of g) and through lam; with mu = (Ahat^T Ahat + lam I)^-1 xbar,
+ *       dL/dc_l = sum_m [ mu^T dAhat^T (dhat - Ahat x) - mu^T Ahat^T dAhat x - dlam mu^T x ],
+ *     dlam = 2 alpha <Ahat, dAhat>, the rows' derivatives taken by reverse-mode
+ *     differentiation of the depth march (as edt_misfit_grad).  The set of kept rows is held
+ *     fixed (the evanescent cut does not move with the velocities).  Needs nx >= 64,
+ *     nlayer <= 64 and nz <= 512 (else EDT_EUNSUPPORTED).
+ * At least one output must be given (else EDT_EINVAL).  The factors, the tables and the
+ * right-hand sides of the forward call are kept, so the call may be repeated for other Vbar;
+ * edt_get_vhat still returns the forward's Vhat.  Asynchronous on `stream`. */
+int edt_invert_vjp(edt_ctx* ctx, const void* Vbar_dev, int Vbar_dtype, void* Dbar_dev, int Dbar_dtype,
+                   double* gc_dev, void* stream);
 
 /* Replace the layer velocities of the reference (same layer tops); every later call uses
  * them (the depth march runs in every call).  With cutoff > 0 the row plan depends on the

@@ -5,9 +5,10 @@ backward gives dJ/dV through the adjoint Born operator and dJ/d(layer velocities
 the reverse-mode depth march, both computed by the library's CUDA kernels in one call
 (``edt_misfit_grad``).
 
-``invert(solver, D)`` returns the inverted model V whose backward gives dL/dD through the
-adjoint of the damped solve (``edt_invert_adjoint``, which reuses the factors of the forward
-call; run the backward before the solver inverts with another reference).
+``invert(solver, D, layer_vel=None)`` returns the inverted model V whose backward gives dL/dD
+through the adjoint of the damped solve and, when the layer velocities are given, dL/dc
+through the solve's dependence on the reference (``edt_invert_vjp``, which reuses the factors
+of the forward call; run the backward before the solver inverts again).
 """
 from __future__ import annotations
 
@@ -38,20 +39,32 @@ def born_misfit(solver, V, layer_vel, D):
 
 
 class Invert(torch.autograd.Function):
-    """V = S D, the damped inversion of a line-geometry ``Solver`` (EDT_MIXED)."""
+    """V = S(c) D, the damped inversion of a line-geometry ``Solver`` (EDT_MIXED): linear in D,
+    and a function of the layer velocities c through the kernel rows and the damping."""
 
     @staticmethod
-    def forward(ctx, D, solver, out_dtype):
+    def forward(ctx, D, layer_vel, solver, out_dtype):
+        if layer_vel is not None:
+            solver.set_reference(layer_vel.detach().cpu().numpy())
         ctx.solver = solver
         ctx.d_dtype = D.dtype
+        ctx.vel_meta = None if layer_vel is None else (layer_vel.device, layer_vel.dtype)
         return solver.invert(D.detach().contiguous(), out_dtype=out_dtype)
 
     @staticmethod
     def backward(ctx, Vbar):
-        Dbar = ctx.solver.invert_adjoint(Vbar.contiguous(), out_dtype=ctx.d_dtype)
-        return Dbar, None, None
+        want_D = ctx.needs_input_grad[0]
+        want_c = ctx.vel_meta is not None and ctx.needs_input_grad[1]
+        if not (want_D or want_c):
+            return None, None, None, None
+        Dbar, gc = ctx.solver.invert_vjp(Vbar.contiguous(), want_D=want_D, want_c=want_c,
+                                         out_dtype=ctx.d_dtype)
+        if gc is not None:
+            gc = gc.to(*ctx.vel_meta)
+        return Dbar, gc, None, None
 
 
-def invert(solver, D, out_dtype=None):
-    """V = S D, differentiable in D (the inversion is linear in the data)."""
-    return Invert.apply(D, solver, out_dtype or torch.float64)
+def invert(solver, D, layer_vel=None, out_dtype=None):
+    """V = S(c) D, differentiable in D and, given as a tensor, in the layer velocities c (the
+    solver's reference is set to them)."""
+    return Invert.apply(D, layer_vel, solver, out_dtype or torch.float64)

@@ -96,12 +96,15 @@ struct edt_ctx {
   std::vector<double> kz_P;
   std::vector<long long> seg_row0, seg_nrow;
   int ncta_gram = 0, nslot = 0;
+  // reference gradient through the solve: the rows reading each table row (f, |n|)
+  std::vector<int2> tref;
+  std::vector<long long> tref_off;
   // workspace
   size_t ws_bytes = 0;
   void* ws = nullptr;
   Region r_fc, r_ltop, r_lvel, r_zl, r_zo, r_rows, r_roff, r_roffmf, r_band, r_bcol, r_cpre, r_kval, r_pairm, r_fjoff, r_fjent, r_jact, r_jmap, r_Gs, r_U, r_Dw, r_A32, r_tw64, r_tw32, r_segm, r_segr0,
       r_segn, r_ctas, r_mslot, r_zo32, r_fc32, r_coef, r_coef32, r_g64, r_g32, r_g32lo, r_rowmax, r_gscale, r_X, r_Dst, r_Vst, r_rhs, r_gent, r_gpart, r_G,
-      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_tpart, r_x, r_r, r_rpart, r_vhat, r_vfull, r_gscr, r_adj, r_gacc, r_status, r_flags,
+      r_dinv, r_L32, r_dinv32, r_b, r_tr, r_tpart, r_x, r_r, r_rpart, r_rowc, r_xmu, r_gam, r_tref, r_treoff, r_vhat, r_vfull, r_gscr, r_adj, r_gacc, r_gcpart, r_status, r_flags,
       r_kzP, r_kzp, r_kzgoff, r_kzvoff, r_kzG, r_kzT, r_kzb, r_kzx;
   Dev dev{};
   cudaStream_t last_stream = nullptr;
@@ -370,6 +373,13 @@ void plan_variant(edt_ctx* c) {
   }
 }
 
+// the reference gradient through the solve: line geometry, mixed path, the depth march's
+// reverse-mode limits (misfit gradient) and at most 512 depths (the row products' vectors)
+bool ref_grad_planned(const edt_ctx* c) {
+  return c->cfg.precision == EDT_MIXED && !c->win && c->nlayer <= GRAD_MAX_LAYERS && c->N >= 64 &&
+         c->nz <= 512;
+}
+
 void plan(edt_ctx* c) {
   const edt_config& g = c->cfg;
   c->N = g.nx; c->nk = g.nx / 2 + 1; c->nz = g.nz; c->nf = g.nfreq; c->nsub = g.nx / 2 + 1;
@@ -491,6 +501,32 @@ void plan(edt_ctx* c) {
   }
   c->rows_max_sub = 0;
   for (int m = 0; m < c->nsub; ++m) c->rows_max_sub = std::max(c->rows_max_sub, c->row_off[m + 1] - c->row_off[m]);
+  // reference gradient through the solve (line geometry, mixed path): group the rows by the
+  // table rows (f, |p|) and (f, |q|) they read, each group in row order
+  c->tref.clear();
+  c->tref_off.clear();
+  if (ref_grad_planned(c)) {
+    const size_t nte = size_t(c->nf) * c->nk;
+    auto tab = [N](int n) { return n <= N / 2 ? n : N - n; };
+    std::vector<long long> cnt(nte + 1, 0);
+    for (int m = 0; m < c->nsub; ++m)
+      for (long long r = c->row_off[m]; r < c->row_off[m + 1]; ++r) {
+        const uint32_t row = c->rows[r];
+        const int f = row_f(row), p = row_p(row), q = (p - m + N) % N;
+        cnt[size_t(f) * c->nk + tab(p) + 1]++;
+        cnt[size_t(f) * c->nk + tab(q) + 1]++;
+      }
+    for (size_t i = 0; i < nte; ++i) cnt[i + 1] += cnt[i];
+    c->tref_off = cnt;
+    c->tref.resize(size_t(cnt[nte]));
+    for (int m = 0; m < c->nsub; ++m)
+      for (long long r = c->row_off[m]; r < c->row_off[m + 1]; ++r) {
+        const uint32_t row = c->rows[r];
+        const int f = row_f(row), p = row_p(row), q = (p - m + N) % N;
+        c->tref[size_t(cnt[size_t(f) * c->nk + tab(p)]++)] = make_int2(int(r), m << 1);
+        c->tref[size_t(cnt[size_t(f) * c->nk + tab(q)]++)] = make_int2(int(r), (m << 1) | 1);
+      }
+  }
   // twiddles e^{-2 pi i k / N}
   c->tw64.resize(N / 2);
   c->tw32.resize(N / 2);
@@ -635,6 +671,13 @@ void layout(edt_ctx* c) {
   take(c->r_gscr, grad ? nf * size_t(c->nlayer) * 8 * nk * sizeof(double2) : 0);
   take(c->r_adj, grad ? size_t(N) * nz * sizeof(double2) : 0);
   take(c->r_gacc, grad ? size_t(1 + c->nlayer) * sizeof(double) : 0);
+  take(c->r_gcpart, grad ? size_t(nf) * ((nk + 127) / 128) * 4 * c->nlayer * sizeof(double) : 0);
+  const bool rg = ref_grad_planned(c);
+  take(c->r_rowc, rg ? std::max<size_t>(R, 1) * 2 * sizeof(float4) : 0);
+  take(c->r_xmu, rg ? ns * nz * sizeof(float4) : 0);
+  take(c->r_gam, rg ? ns * sizeof(double) : 0);
+  take(c->r_tref, rg ? std::max<size_t>(c->tref.size(), 1) * sizeof(int2) : 0);
+  take(c->r_treoff, rg ? c->tref_off.size() * sizeof(long long) : 0);
   take(c->r_status, ns * sizeof(int));
   take(c->r_flags, 8 * sizeof(unsigned));
   const bool disk = !c->kz_p.empty();
@@ -733,7 +776,14 @@ void bind(edt_ctx* c) {
   d.gscr = c->r_gscr.bytes ? at<double2*>(c, c->r_gscr) : nullptr;
   d.adj = c->r_adj.bytes ? at<double2*>(c, c->r_adj) : nullptr;
   d.gacc = c->r_gacc.bytes ? at<double*>(c, c->r_gacc) : nullptr;
+  d.gcpart = c->r_gcpart.bytes ? at<double*>(c, c->r_gcpart) : nullptr;
   d.gbar = c->r_gscr.bytes ? reinterpret_cast<float2*>(d.g64) : nullptr;
+  d.rowc = c->r_rowc.bytes ? at<float4*>(c, c->r_rowc) : nullptr;
+  d.xmu = c->r_xmu.bytes ? at<float4*>(c, c->r_xmu) : nullptr;
+  d.gam = c->r_gam.bytes ? at<double*>(c, c->r_gam) : nullptr;
+  d.tref = c->r_tref.bytes ? at<const int2*>(c, c->r_tref) : nullptr;
+  d.tref_off = c->r_treoff.bytes ? at<const long long*>(c, c->r_treoff) : nullptr;
+  d.refine_nodata = 0;
   d.status = at<int*>(c, c->r_status);
   d.flags = at<unsigned*>(c, c->r_flags);
   d.solver = c->cfg.solver;
@@ -924,6 +974,8 @@ int edt_set_workspace(edt_ctx* c, void* ws, size_t bytes) {
   EDT_TRYI(upload(c, c->r_zo32, c->z_off32));
   EDT_TRYI(upload(c, c->r_fc32, c->fc32));
   EDT_TRYI(upload(c, c->r_rows, c->rows));
+  if (!c->tref.empty()) EDT_TRYI(upload(c, c->r_tref, c->tref));
+  if (!c->tref_off.empty()) EDT_TRYI(upload(c, c->r_treoff, c->tref_off));
   EDT_TRYI(upload(c, c->r_roff, c->row_off));
   EDT_TRYI(upload(c, c->r_roffmf, c->row_off_mf));
   EDT_TRYI(upload(c, c->r_band, c->band));
@@ -1053,18 +1105,25 @@ int edt_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, voi
   return r;
 }
 
-int edt_invert_adjoint(edt_ctx* c, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype, void* stream) {
-  if (!c || !Vbar || !Dbar) return EDT_EINVAL;
+int edt_invert_vjp(edt_ctx* c, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype, double* gc,
+                   void* stream) {
+  if (!c || !Vbar || (!Dbar && !gc)) return EDT_EINVAL;
   if (!c->ws) return EDT_ENOMEM_WS;
-  if (Dbar_dtype != EDT_C64 && Dbar_dtype != EDT_C128) return EDT_EINVAL;
+  if (Dbar && Dbar_dtype != EDT_C64 && Dbar_dtype != EDT_C128) return EDT_EINVAL;
   if (Vbar_dtype != EDT_F32 && Vbar_dtype != EDT_F64) return EDT_EINVAL;
   if (c->win || c->cfg.precision != EDT_MIXED) return EDT_EUNSUPPORTED;
+  if (gc && (!grad_supported(c->dev) || !c->dev.tref)) return EDT_EUNSUPPORTED;
   if (!c->have_factor) return EDT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c->last_stream = s;
-  EDT_TRY(launch_invert_adjoint(c->dev, Vbar, Vbar_dtype, Dbar, Dbar_dtype, c->cfg.refine, c->r_rhs.bytes, s));
-  c->have_factor = true;                  // the factors are untouched; b, x, r and rhs are not
+  EDT_TRY(launch_invert_vjp(c->dev, Vbar, Vbar_dtype, Dbar, Dbar_dtype, gc, c->cfg.refine, s));
+  c->have_factor = true;                  // the factors, tables and right-hand sides are untouched
   return EDT_OK;
+}
+
+int edt_invert_adjoint(edt_ctx* c, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype, void* stream) {
+  if (!Dbar) return EDT_EINVAL;
+  return edt_invert_vjp(c, Vbar, Vbar_dtype, Dbar, Dbar_dtype, nullptr, stream);
 }
 
 int edt_get_tuning(const edt_ctx* c, edt_tuning* o) {

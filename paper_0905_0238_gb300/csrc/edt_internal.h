@@ -153,8 +153,16 @@ struct Dev {
   // misfit gradients (line geometry, mixed path)
   double2* gscr;                // [nf][nlayer][8][nk] depth-march states and cotangents
   double2* adj;                 // [N][nz] Ahat = F^H R2 summed over frequencies
-  double* gacc;                 // [1 + nlayer] sum |R2|^2, then dJ/dc_l
+  double* gacc;                 // [1 + nlayer] sum |R2|^2
+  double* gcpart;               // [warps of the reverse march][nlayer] partial dJ/dc_l
   float2* gbar;                 // [nf][N][nz] dJ/dg per full lateral index (aliases g64)
+  // dL/dc through the damped solve (line geometry, mixed path)
+  float4* rowc;                 // [rows_solved][2] per row (u_+, u_-) = d - A x, (v_+, v_-) = -A mu
+  float4* xmu;                  // [nsub][nz] (x_+, x_-, mu_+, mu_-) in FP32
+  double* gam;                  // [nsub] -2 alpha sum_k mu_k . x_k
+  const int2* tref;             // [2 rows_solved] (row, m << 1 | side), grouped by table row
+  const long long* tref_off;    // [nf * nk + 1] the groups' offsets
+  int refine_nodata;            // refinement residual without the data term (adjoint solves)
   int* status;                  // [nsub]
   unsigned int* flags;          // [8] device-side error flags; [0]: a tensor-core Gram wait expired
   long long wait_cycles;        // budget of the tensor-core Gram's bounded waits (0: about 2 s)
@@ -252,11 +260,13 @@ cudaError_t launch_lateral_idft_real(const Dev& d, const double2* in, double sca
 cudaError_t launch_transform_adjoint(const Dev& d, void* D, int D_dtype, int f0, int nfc, cudaStream_t s);
 // x = (LL^T)^-1 b with the factors of the last factorisation (no refactorisation).
 cudaError_t launch_chol_resolve(const Dev& d, cudaStream_t s);
-// Dbar = S^T Vbar for the linear map S: D -> V of the last edt_invert (mixed line path),
-// with `refine` refinement steps like the forward solve; rhs_bytes: size of d.rhs (zeroed
-// as scratch).
-cudaError_t launch_invert_adjoint(const Dev& d, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype,
-                                  int refine, size_t rhs_bytes, cudaStream_t s);
+// The vector-Jacobian products of the last edt_invert (mixed line path) for Vbar = dL/dV:
+// Dbar = S^T Vbar (S: D -> V, linear) when Dbar is set, and gc[l] = dL/dc_l through the damped
+// solve (the kernel rows and lam depend on the reference) when gc is set (needs
+// grad_supported and the row groups).  mu = (G + lam I)^-1 xbar with `refine` refinement
+// steps like the forward solve.
+cudaError_t launch_invert_vjp(const Dev& d, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype,
+                              double* gc, int refine, cudaStream_t s);
 
 // Misfit J = ||F V - D||^2 and its gradients (csrc/grad.cu); layers the reverse-mode depth
 // march supports (its per-(f, k) scratch is sized by it).

@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(128) grad_march_kernel(Dev d) {
 // field, reversed, per (f, k, l): the depths z_j of layer l (a contiguous index range) give
 // A_l, rho_l, kappa_l their cotangents; gbar on the table index |n'| = k (rows n = k and
 // N - k).  Within the layer P and Q advance by e^{+-i kappa dz} from a direct start.
-__global__ void __launch_bounds__(128) grad_field_kernel(Dev d) {
+// gb64: the cotangent already on the table index in FP64 ([nf][nk][nz]), else d.gbar.
+__global__ void __launch_bounds__(128) grad_field_kernel(Dev d, const double2* gb64) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int J = d.nlayer;
   if (gid >= (long long)d.nf * J * d.nk) return;
@@ -400,9 +401,14 @@ __global__ void __launch_bounds__(128) grad_field_kernel(Dev d) {
     const bool two = k > 0 && k < N / 2;
     for (int j = j0; j < j1; ++j) {
       dd = d.z_off[j];
-      float2 gb = G[size_t(k) * d.nz + j];
-      if (two) gb = gb + G[size_t(N - k) * d.nz + j];
-      const double2 gbar = cmk(double(gb.x), double(gb.y));
+      double2 gbar;
+      if (gb64) {
+        gbar = gb64[(size_t(f) * d.nk + k) * d.nz + j];
+      } else {
+        float2 gb = G[size_t(k) * d.nz + j];
+        if (two) gb = gb + G[size_t(N - k) * d.nz + j];
+        gbar = cmk(double(gb.x), double(gb.y));
+      }
       const double2 gA = gbar * Al;
       if (!last) {
         bA = bA + gbar * (P + rho * Q);
@@ -422,7 +428,8 @@ __global__ void __launch_bounds__(128) grad_field_kernel(Dev d) {
 }
 
 // the two recursions reversed per (f, k), then dJ/dc_l = Re(kappabar_l dkappa_l/dc_l)
-// summed over (f, k): warp sums, one atomic per warp and layer
+// summed over (f, k): warp sums, one partial per warp and layer (added in warp order by the
+// finalize kernel, so the result does not depend on the order the warps ran in)
 __global__ void __launch_bounds__(128) grad_reverse_kernel(Dev d) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
@@ -480,14 +487,20 @@ __global__ void __launch_bounds__(128) grad_reverse_kernel(Dev d) {
       v = (gs_at(d, f, l, GS_BKAP, kk) * dk).x;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(d.gacc + 1 + l, v);
+    const size_t wid = (size_t(blockIdx.y) * gridDim.x + blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if ((threadIdx.x & 31) == 0) d.gcpart[wid * J + l] = v;
   }
 }
 
-__global__ void grad_finalize_kernel(Dev d, double* J, double* gc) {
+// nw: the reverse kernel's warps (their partials are added in warp order)
+__global__ void grad_finalize_kernel(Dev d, double* J, double* gc, int nw) {
   const double cj = 1.0 / (double(d.N) * d.N);
-  if (threadIdx.x == 0) J[0] = cj * d.gacc[0];
-  for (int l = threadIdx.x; l < d.nlayer; l += blockDim.x) gc[l] = d.gacc[1 + l];
+  if (threadIdx.x == 0 && J) J[0] = cj * d.gacc[0];
+  for (int l = threadIdx.x; l < d.nlayer; l += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += d.gcpart[size_t(w) * d.nlayer + l];
+    gc[l] = t;
+  }
 }
 
 // ---- adjoint of the inversion D -> V (linear in D: G and lam depend on the rows only) --------
@@ -573,31 +586,210 @@ __global__ void __launch_bounds__(256) adj_rows_kernel(Dev d, int f0, int f1) {
   }
 }
 
+// ---- dL/dc_l through the damped solve ----------------------------------------------------
+// Per subproblem m, x solves (Ahat^T Ahat + lam I) x = Ahat^T dhat with lam = alpha tr(Ahat^T
+// Ahat) (the Gram's trace, the sum of w |A|^2 over the rows); the kernel rows A = g32_p g32_q
+// (g32 = sqrt|s_f| g; the data carry the unit phase of s_f) depend on the reference.  With
+// mu = (Ahat^T Ahat + lam I)^-1 xbar, differentiating the normal equations gives the
+// cotangent of a complex row (dL = Re sum_z conj(Abar) dA)
+//   Abar = w [ sum_k (u_k mu_k + v_k x_k) + gamma A ],
+//   u_k = d_k - A . x_k,  v_k = -A . mu_k,  gamma = -2 alpha sum_k mu_k . x_k,
+// (k over the two right-hand sides +-; w = 2 for a folded row).  With dA = sqrt|s_f| (g32_q dg_p
+// + g32_p dg_q) the table's cotangent in the convention dL = Re sum gbar dg is
+//   gbar(f, |p|) += sqrt|s_f| g32_q conj(Abar),   gbar(f, |q|) += sqrt|s_f| g32_p conj(Abar),
+// gathered per table row over the rows that read it (row groups built with the plan, in row
+// order: no atomics), FP32 products, FP64 sums; then the depth march is reversed as for the
+// misfit gradient.
+constexpr int IG_WARPS = 8, IG_RPW = 16;             // 128 rows per CTA of the row products
+
+// Per row the products with the depth vectors of its subproblem: mode 0 (before the adjoint
+// solve) u_k = d_k - A . x_k with x the forward solution (Vhat), mode 1 v_k = -A . mu_k with mu
+// in x; the first CTA of each subproblem also stores the FP32 vectors and, in mode 1, gamma.
+__global__ void __launch_bounds__(IG_WARPS * 32) ig_rowdot_kernel(Dev d, int mode) {
+  __shared__ float vs[2][512];
+  __shared__ double red[IG_WARPS];
+  const int m = blockIdx.y, nz = d.nz, N = d.N, msk = N - 1;
+  const bool ok = d.status[m] == EDT_OK;
+  const long long r0 = d.row_off[m], nr = d.row_off[m + 1] - r0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double bsum = 0.0;
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+    float a = 0.f, b = 0.f;
+    if (ok) {
+      if (mode) {
+        const double mp = d.x[(size_t(m) * nz + z) * 2], mm = d.x[(size_t(m) * nz + z) * 2 + 1];
+        const double2 xv = d.vhat[size_t(m) * nz + z];
+        bsum += mp * xv.x + mm * xv.y;
+        a = float(mp); b = float(mm);
+      } else {
+        const double2 xv = d.vhat[size_t(m) * nz + z];
+        a = float(xv.x); b = float(xv.y);
+      }
+    }
+    vs[0][z] = a; vs[1][z] = b;
+    if (blockIdx.x == 0) {
+      float4* o = d.xmu + size_t(m) * nz + z;
+      if (mode) { o->z = a; o->w = b; } else { o->x = a; o->y = b; }
+    }
+  }
+  if (mode && blockIdx.x == 0) {
+    for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+    if (lane == 0) red[warp] = bsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < IG_WARPS; ++w) t += red[w];
+      d.gam[m] = ok ? -2.0 * d.alpha * t : 0.0;
+    }
+  }
+  __syncthreads();
+  const long long wb = (long long)blockIdx.x * IG_WARPS * IG_RPW + warp * IG_RPW;
+  const long long we = min(nr, wb + IG_RPW);
+  const float2* rhs = reinterpret_cast<const float2*>(d.rhs);
+  for (long long i = wb; i < we; ++i) {
+    const long long ri = r0 + i;
+    const uint32_t row = d.rows[ri];
+    const int f = row_f(row), p = row_p(row), q = (p - m) & msk;
+    const float2* gp = d.g32 + (size_t(f) * d.nk + tab_index(p, N)) * d.nzs;
+    const float2* gq = d.g32 + (size_t(f) * d.nk + tab_index(q, N)) * d.nzs;
+    float2 sp = make_float2(0.f, 0.f), sm = sp;
+    for (int z = lane; z < nz; z += 32) {
+      const float2 t = gp[z] * gq[z];
+      const float a = vs[0][z], b = vs[1][z];
+      sp.x = fmaf(t.x, a, sp.x); sp.y = fmaf(t.y, a, sp.y);
+      sm.x = fmaf(t.x, b, sm.x); sm.y = fmaf(t.y, b, sm.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sp.x += __shfl_xor_sync(0xffffffffu, sp.x, o); sp.y += __shfl_xor_sync(0xffffffffu, sp.y, o);
+      sm.x += __shfl_xor_sync(0xffffffffu, sm.x, o); sm.y += __shfl_xor_sync(0xffffffffu, sm.y, o);
+    }
+    if (lane == 0) {
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ok) {
+        if (mode) {
+          o = make_float4(-sp.x, -sp.y, -sm.x, -sm.y);
+        } else {
+          const float2 dp = rhs[2 * ri], dm = rhs[2 * ri + 1];
+          o = make_float4(dp.x - sp.x, dp.y - sp.y, dm.x - sm.x, dm.y - sm.y);
+        }
+      }
+      d.rowc[2 * ri + mode] = o;
+    }
+  }
+}
+
+// One warp per table row (f, n), n = 0 .. N/2, lanes over depth (NZL per lane): gbar of that
+// row from every row that reads it, in row order; 32 rows summed in FP32, then into FP64.
+template <int NZL>
+__global__ void __launch_bounds__(256) ig_gather_kernel(Dev d) {
+  const long long te = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (te >= (long long)d.nf * d.nk) return;
+  const int lane = threadIdx.x & 31, nz = d.nz, N = d.N, msk = N - 1;
+  const int f = int(te / d.nk);
+  const float2* gs = d.g32 + size_t(te) * d.nzs;
+  float2 self[NZL], part[NZL];
+  double2 acc[NZL];
+#pragma unroll
+  for (int t = 0; t < NZL; ++t) {
+    const int z = lane + 32 * t;
+    self[t] = z < nz ? gs[z] : make_float2(0.f, 0.f);
+    part[t] = make_float2(0.f, 0.f);
+    acc[t] = make_double2(0.0, 0.0);
+  }
+  const long long b0 = d.tref_off[te], b1 = d.tref_off[te + 1];
+  for (long long i = b0; i < b1; ++i) {
+    const int2 rf = d.tref[i];
+    const int m = rf.y >> 1, side = rf.y & 1;
+    const uint32_t row = d.rows[rf.x];
+    const int p = row_p(row), q = (p - m) & msk;
+    const float2* go = d.g32 + (size_t(f) * d.nk + tab_index(side ? p : q, N)) * d.nzs;
+    const float4 u = d.rowc[2 * size_t(rf.x)], v = d.rowc[2 * size_t(rf.x) + 1];
+    const float w = row_w2(row) ? 2.f : 1.f, gam = float(d.gam[m]);
+    const float4* xm = d.xmu + size_t(m) * nz;
+#pragma unroll
+    for (int t = 0; t < NZL; ++t) {
+      const int z = lane + 32 * t;
+      if (z < nz) {
+        const float2 g2 = go[z];
+        const float4 xv = xm[z];                       // (x_+, x_-, mu_+, mu_-)
+        const float2 A = self[t] * g2;
+        float2 ab;
+        ab.x = fmaf(u.x, xv.z, fmaf(u.z, xv.w, fmaf(v.x, xv.x, fmaf(v.z, xv.y, gam * A.x))));
+        ab.y = fmaf(u.y, xv.z, fmaf(u.w, xv.w, fmaf(v.y, xv.x, fmaf(v.w, xv.y, gam * A.y))));
+        ab.x *= w; ab.y *= w;
+        part[t].x = fmaf(g2.x, ab.x, fmaf(g2.y, ab.y, part[t].x));      // g2 conj(ab)
+        part[t].y = fmaf(g2.y, ab.x, fmaf(-g2.x, ab.y, part[t].y));
+      }
+    }
+    if (((i - b0) & 31) == 31) {
+#pragma unroll
+      for (int t = 0; t < NZL; ++t) {
+        acc[t].x += double(part[t].x); acc[t].y += double(part[t].y);
+        part[t] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  const double sq = sqrt(d.fc[f].s_abs);
+  double2* out = d.g64 + size_t(te) * nz;
+#pragma unroll
+  for (int t = 0; t < NZL; ++t) {
+    const int z = lane + 32 * t;
+    if (z < nz) out[z] = make_double2(sq * (acc[t].x + double(part[t].x)), sq * (acc[t].y + double(part[t].y)));
+  }
+}
+
 }  // namespace
 
 // The forward solve with k refinement steps is x = sum_{i<=k} (I - Ht^-1 H)^i Ht^-1 b (Ht the
 // factored matrix, H = Ahat^T Ahat + lam I from the rows), a symmetric map: its transpose is
 // the same iteration applied to xbar, run here with the forward's own kernels.
-cudaError_t launch_invert_adjoint(const Dev& d, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype,
-                                  int refine, size_t rhs_bytes, cudaStream_t s) {
+cudaError_t launch_invert_vjp(const Dev& d0, const void* Vbar, int Vbar_dtype, void* Dbar, int Dbar_dtype,
+                              double* gc, int refine, cudaStream_t s) {
   cudaError_t e;
+  // the adjoint solve's refinement residual is xbar - (Ahat^T Ahat + lam I) y: the rows'
+  // data term is left out (the right-hand sides stay for later calls)
+  Dev d = d0;
+  d.refine_nodata = 1;
+  const dim3 rg(unsigned((std::max(d.rows_max_sub, 1LL) + IG_WARPS * IG_RPW - 1) / (IG_WARPS * IG_RPW)), d.nsub);
+  if (gc) {
+    ig_rowdot_kernel<<<rg, IG_WARPS * 32, 0, s>>>(d, 0);          // u = d - A x
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if ((e = launch_lateral_dft(d, Vbar, Vbar_dtype, s)) != cudaSuccess) return e;
   adj_xbar_kernel<<<d.nsub, 256, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_chol_resolve(d, s)) != cudaSuccess) return e;
-  if (refine > 0 && (e = cudaMemsetAsync(d.rhs, 0, rhs_bytes, s)) != cudaSuccess) return e;
   for (int it = 0; it < refine; ++it) {
     if ((e = launch_refine(d, s)) != cudaSuccess) return e;
     adj_addb_kernel<<<152, 256, 0, s>>>(d);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_refine_update(d, s)) != cudaSuccess) return e;
   }
-  for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
-    const int nfc = std::min(d.fchunk, d.nf - f0);
-    if ((e = cudaMemsetAsync(d.X, 0, size_t(nfc) * d.N * d.N * sizeof(float2), s)) != cudaSuccess) return e;
-    adj_rows_kernel<<<dim3(32, d.nsub), 256, 0, s>>>(d, f0, f0 + nfc);
+  if (Dbar) {
+    for (int f0 = 0; f0 < d.nf; f0 += d.fchunk) {
+      const int nfc = std::min(d.fchunk, d.nf - f0);
+      if ((e = cudaMemsetAsync(d.X, 0, size_t(nfc) * d.N * d.N * sizeof(float2), s)) != cudaSuccess) return e;
+      adj_rows_kernel<<<dim3(32, d.nsub), 256, 0, s>>>(d, f0, f0 + nfc);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launch_transform_adjoint(d, Dbar, Dbar_dtype, f0, nfc, s)) != cudaSuccess) return e;
+    }
+  }
+  if (gc) {
+    ig_rowdot_kernel<<<rg, IG_WARPS * 32, 0, s>>>(d, 1);          // v = -A mu, gamma
+    const unsigned gg = unsigned(((long long)d.nf * d.nk + 7) / 8);
+    if (d.nz <= 64) ig_gather_kernel<2><<<gg, 256, 0, s>>>(d);
+    else if (d.nz <= 128) ig_gather_kernel<4><<<gg, 256, 0, s>>>(d);
+    else if (d.nz <= 256) ig_gather_kernel<8><<<gg, 256, 0, s>>>(d);
+    else ig_gather_kernel<16><<<gg, 256, 0, s>>>(d);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_transform_adjoint(d, Dbar, Dbar_dtype, f0, nfc, s)) != cudaSuccess) return e;
+    grad_zero_kernel<<<152, 256, 0, s>>>(d);
+    const dim3 gk((d.nk + 127) / 128, d.nf);
+    grad_march_kernel<<<gk, 128, 0, s>>>(d);
+    const long long nfl = (long long)d.nf * d.nlayer * d.nk;
+    grad_field_kernel<<<unsigned((nfl + 127) / 128), 128, 0, s>>>(d, d.g64);
+    grad_reverse_kernel<<<gk, 128, 0, s>>>(d);
+    grad_finalize_kernel<<<1, 64, 0, s>>>(d, nullptr, gc, int(gk.x * gk.y * 4));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -663,11 +855,11 @@ cudaError_t launch_misfit_grad(const Dev& d, const void* V, int V_dtype, const v
   const dim3 gk((d.nk + 127) / 128, d.nf);
   grad_march_kernel<<<gk, 128, 0, s>>>(d);
   const long long nfl = (long long)d.nf * d.nlayer * d.nk;
-  grad_field_kernel<<<unsigned((nfl + 127) / 128), 128, 0, s>>>(d);
+  grad_field_kernel<<<unsigned((nfl + 127) / 128), 128, 0, s>>>(d, nullptr);
   grad_reverse_kernel<<<gk, 128, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_lateral_idft_real(d, d.adj, 2.0 / (double(N) * N), gV, V_dtype, s)) != cudaSuccess) return e;
-  grad_finalize_kernel<<<1, 64, 0, s>>>(d, J, gc);
+  grad_finalize_kernel<<<1, 64, 0, s>>>(d, J, gc, int(gk.x * gk.y * 4));
   return cudaGetLastError();
 }
 

@@ -99,7 +99,9 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
         tm.x += __shfl_xor_sync(0xffffffffu, tm.x, o); tm.y += __shfl_xor_sync(0xffffffffu, tm.y, o);
       }
       const float w = wv[h];
-      const float2 dp = rhs[2 * ri[h]], dm = rhs[2 * ri[h] + 1];
+      const float2 zero2 = make_float2(0.f, 0.f);
+      const float2 dp = d.refine_nodata ? zero2 : rhs[2 * ri[h]];
+      const float2 dm = d.refine_nodata ? zero2 : rhs[2 * ri[h] + 1];
       const float2 up = make_float2(w * (dp.x - tp.x), w * (dp.y - tp.y));
       const float2 um = make_float2(w * (dm.x - tm.x), w * (dm.y - tm.y));
 #pragma unroll
@@ -249,7 +251,9 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_df_kernel(Dev d) {
       tp.x += __shfl_xor_sync(0xffffffffu, tp.x, o); tp.y += __shfl_xor_sync(0xffffffffu, tp.y, o);
       tm.x += __shfl_xor_sync(0xffffffffu, tm.x, o); tm.y += __shfl_xor_sync(0xffffffffu, tm.y, o);
     }
-    const float2 dp = rhs[2 * ri], dm = rhs[2 * ri + 1];
+    const float2 zero2 = make_float2(0.f, 0.f);
+    const float2 dp = d.refine_nodata ? zero2 : rhs[2 * ri];
+    const float2 dm = d.refine_nodata ? zero2 : rhs[2 * ri + 1];
     const float2 up = make_float2(w * (dp.x - tp.x), w * (dp.y - tp.y));
     const float2 um = make_float2(w * (dm.x - tm.x), w * (dm.y - tm.y));
 #pragma unroll

@@ -129,6 +129,7 @@ def _lib() -> C.CDLL:
                                        C.POINTER(i)]
         L.edt_misfit_grad.argtypes = [vp, vp, i, vp, i, vp, vp, vp, vp]
         L.edt_invert_adjoint.argtypes = [vp, vp, i, vp, i, vp]
+        L.edt_invert_vjp.argtypes = [vp, vp, i, vp, i, vp, vp]
         L.edt_set_host_pipeline.argtypes = [vp, i]
         L.edt_set_wait_test.argtypes = [vp, C.c_longlong, i]
         L.edt_set_reference.argtypes = [vp, C.POINTER(d), vp]
@@ -142,7 +143,7 @@ def _lib() -> C.CDLL:
                      "edt_import_rhs", "edt_solve_imported", "edt_inverse_vhat", "edt_row_counts", "edt_gram",
                      "edt_get_stats", "edt_set_profiling", "edt_read_profile", "edt_green_noalloc",
                      "edt_set_graph", "edt_autotune", "edt_get_tuning", "edt_set_tuning",
-                     "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint",
+                     "edt_misfit_grad", "edt_set_reference", "edt_invert_adjoint", "edt_invert_vjp",
                      "edt_set_host_pipeline", "edt_set_wait_test"):
             getattr(L, name).restype = i
         ll = C.c_longlong
@@ -327,6 +328,12 @@ def edt_misfit_grad(ctx, V_ptr: int, V_dtype: int, D_ptr: int, D_dtype: int, J_p
     _check(_lib().edt_misfit_grad(ctx, C.c_void_p(V_ptr), V_dtype, C.c_void_p(D_ptr), D_dtype,
                                   C.c_void_p(J_ptr), C.c_void_p(gV_ptr), C.c_void_p(gc_ptr),
                                   C.c_void_p(stream)), "edt_misfit_grad")
+
+
+def edt_invert_vjp(ctx, Vbar_ptr: int, Vbar_dtype: int, Dbar_ptr: int, Dbar_dtype: int, gc_ptr: int,
+                   stream: int):
+    _check(_lib().edt_invert_vjp(ctx, C.c_void_p(Vbar_ptr), Vbar_dtype, C.c_void_p(Dbar_ptr), Dbar_dtype,
+                                 C.c_void_p(gc_ptr), C.c_void_p(stream)), "edt_invert_vjp")
 
 
 def edt_invert_adjoint(ctx, Vbar_ptr: int, Vbar_dtype: int, Dbar_ptr: int, Dbar_dtype: int,
@@ -533,6 +540,22 @@ class Solver:
         edt_invert_adjoint(self.ctx, Vbar.data_ptr(), self._rdtype(Vbar), Dbar.data_ptr(),
                            self._cdtype(Dbar), self._stream())
         return Dbar
+
+    def invert_vjp(self, Vbar, want_D=True, want_c=True, out_dtype=None):
+        """(Dbar, gc) for Vbar = dL/dV after the last invert (see edt_invert_vjp): Dbar = dL/dD
+        with the data's shape, gc[l] = dL/dc_l through the damped solve; either may be None
+        when not wanted."""
+        torch = self._torch
+        nf = len(self._freq)
+        if not (Vbar.is_cuda and Vbar.is_contiguous()) or tuple(Vbar.shape) != self.cfg.model_shape():
+            raise ValueError(f"Vbar must be a contiguous CUDA tensor of shape {self.cfg.model_shape()}")
+        Dbar = torch.empty(self.cfg.data_shape(nf), device=self.device,
+                           dtype=out_dtype or torch.complex128) if want_D else None
+        gc = torch.empty((len(self._top),), device=self.device, dtype=torch.float64) if want_c else None
+        edt_invert_vjp(self.ctx, Vbar.data_ptr(), self._rdtype(Vbar), Dbar.data_ptr() if want_D else 0,
+                       self._cdtype(Dbar) if want_D else EDT_C64, gc.data_ptr() if want_c else 0,
+                       self._stream())
+        return Dbar, gc
 
     def set_reference(self, layer_vel):
         """Replace the layer velocities of the reference (same layer tops)."""

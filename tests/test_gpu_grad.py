@@ -175,3 +175,65 @@ def test_invert_adjoint_matches_oracle(fold):
     Vt = invert(s, Dt)
     torch.sum(Vt * dev(Vbar)).backward()
     assert rel_l2(Dt.grad.cpu().numpy(), got) < 1e-6
+
+
+def _inv_problem(wl, salt):
+    rng = synth.rng_for(7, salt)
+    V = synth.perturbation_blobs(rng, wl.nx, wl.dx, wl.nz, wl.dz, wl.z0, wl.layer_top,
+                                 wl.layer_vel, nblob=3, sigma=30.0, amp=0.05)
+    D = edt2d.forward(wl, V)
+    D = D + synth.noise_snr(synth.rng_for(7, salt + 50), D, 20.0)
+    Vbar = rng.standard_normal((wl.nx, wl.nz))
+    return D, Vbar
+
+
+@pytest.mark.parametrize("fold,alpha", [(1, 1e-2), (0, 1e-3), (1, 1e-4)])
+def test_invert_grad_c_matches_oracle(fold, alpha):
+    """dL/dc_l through the damped solve for L = <V, Vbar>: the GPU's reverse mode (row
+    cotangents gathered per table row, the depth march reversed) against the oracle's forward
+    mode (the derivative of the normal equations, lam included, one layer at a time); a second
+    call gives the same bits (the forward's data and factors are kept)."""
+    from tests.gpu_helpers import small_workload
+    wl = small_workload(nx=64, nz=24, nf=6, alpha=alpha, cutoff=1.0)
+    D, Vbar = _inv_problem(wl, 20 + fold)
+    gc_or = grad2d.invert_grad_c(wl, D, Vbar)
+    s = solver(wl, fold=fold, refine=2 if alpha < 1e-3 else 1)
+    s.invert(dev(D))
+    Dbar, gc = s.invert_vjp(dev(Vbar))
+    g = gc.cpu().numpy()
+    assert rel_l2(g, gc_or) < 1e-5, rel_l2(g, gc_or)
+    Dbar2, gc2 = s.invert_vjp(dev(Vbar))
+    assert np.array_equal(gc2.cpu().numpy(), g)
+    # Dbar alone, as edt_invert_adjoint gives it
+    assert rel_l2(Dbar.cpu().numpy(), s.invert_adjoint(dev(Vbar)).cpu().numpy()) < 1e-6
+
+
+def test_invert_autograd_returns_the_layer_gradient():
+    from tests.gpu_helpers import small_workload
+    from paper_0905_0238_gb300.autograd import invert
+    wl = small_workload(nx=64, nz=24, nf=6, alpha=1e-2, cutoff=1.0)
+    D, Vbar = _inv_problem(wl, 31)
+    s = solver(wl)
+    Dt = dev(D).requires_grad_(True)
+    vel = torch.tensor(wl.layer_vel, dtype=torch.float64, requires_grad=True)
+    V = invert(s, Dt, layer_vel=vel)
+    torch.sum(V * dev(Vbar)).backward()
+    gc_or = grad2d.invert_grad_c(wl, D, Vbar)
+    assert vel.grad is not None and vel.grad.shape == (len(wl.layer_vel),)
+    assert rel_l2(vel.grad.numpy(), gc_or) < 1e-5
+    assert rel_l2(Dt.grad.cpu().numpy(), edt2d.invert_adjoint(wl, Vbar)) < 1e-5
+
+
+def test_invert_grad_c_production_geometry_single_frequency():
+    """One frequency of the 512 x 512, 256-depth, 20-layer line with the evanescent cut: dL/dc
+    of three layers against the oracle (one frequency keeps the oracle's solves to seconds)."""
+    wl = synth.preset("production_2d")
+    wl.freq_hz = wl.freq_hz[[60]]
+    D, Vbar = _inv_problem(wl, 40)
+    s = solver(wl)
+    s.invert(dev(D))
+    _, gc = s.invert_vjp(dev(Vbar), want_D=False)
+    g = gc.cpu().numpy()
+    layers = [0, 7, 19]
+    want = np.array([float(np.sum(Vbar * grad2d.invert_tangent(wl, D, l)[1])) for l in layers])
+    assert rel_l2(g[layers], want) < 1e-5, (g[layers], want)
