@@ -23,13 +23,16 @@ __host__ __device__ inline int row_w2(uint32_t r) { return int((r >> 15) & 1u); 
 
 // Per-row operand metadata of the tensor-core Gram (fixed by the row plan, written once per
 // workspace): the two rows p, q of the FP32 row table whose elementwise product is the
-// kernel row (row r of the table starts at element r * nzs), and sqrt(weight).  The data
+// kernel row (row r of the table starts at element r * nzs), as byte offsets and as row
+// indices, and sqrt(weight).  The data
 // of a row, (d_+, d_-) as a float4 in the right-hand-side array, are scaled by sw on use.
 // Line geometry: the table is sqrt|s_f| g and the rows are g(|k_p|), g(|k_q|); window
 // geometry: the table holds the assembled kernel rows and q is a row of ones.
 struct GramRow {
-  unsigned offp, offq;
-  float sw, pad;
+  unsigned long long bp, bq;     // byte offsets of the two table rows (row * nzs * 8)
+  float sw;                      // sqrt(weight)
+  unsigned rp, rq;               // the two rows' indices
+  float pad;
 };
 
 // Wavenumber band of one frequency kept by the evanescent cut: signed indices

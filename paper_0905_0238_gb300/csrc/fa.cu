@@ -642,8 +642,10 @@ __global__ void fa_setup_kernel(Dev d, long long nrows) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nrows) {
     GramRow g;
-    g.offp = unsigned(t);
-    g.offq = unsigned(d.ones_row);
+    g.rp = unsigned(t);
+    g.rq = unsigned(d.ones_row);
+    g.bp = (unsigned long long)t * d.nzs * sizeof(float2);
+    g.bq = (unsigned long long)d.ones_row * d.nzs * sizeof(float2);
     g.sw = 1.f;
     g.pad = 0.f;
     d.gent[t] = g;

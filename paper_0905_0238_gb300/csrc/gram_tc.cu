@@ -13,7 +13,9 @@
 //     in TMEM and written out as an FP32 partial tile, summed per subproblem afterwards;
 //   * warps 0-15 are producers: for 32 complex rows per pipeline stage they rebuild the
 //     kernel rows a(z) = |s_f| g(k_p, z) g(k_q, z) from the L2-resident FP32 table of
-//     sqrt|s_f| g, scale weight-2 rows by sqrt 2, split into hi (and lo) 16-bit halves, and
+//     sqrt|s_f| g (unpredicated loads at byte offsets kept in the row table; padding rows
+//     and depths take weight 0), scale weight-2 rows by sqrt 2, split into hi (and lo)
+//     16-bit halves, and
 //     store them K-major with the 128-byte swizzle; (Re a, Im a) of one complex row are two
 //     adjacent K elements.  The data rows d_+, d_- occupy two extra operand rows;
 //   * operand type: FP16 (line geometry) or BF16 (window geometry).  FP16's 11-bit
@@ -157,14 +159,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
 
   if (warp == PRODUCER_WARPS) {
     // ------------------------------------------------------------ MMA issuer
-    // instruction list: (A first row, B first row, N, TMEM column)
-    int ia[3], ib[3], in_[3], ic[3], ni = 0;
-    {
-      int n0 = nzp + 16;
-      ia[ni] = 0; ib[ni] = 0; in_[ni] = n0 > 256 ? 256 : n0; ic[ni] = 0; ++ni;
-      if (n0 > 256) { ia[ni] = 0; ib[ni] = 256; in_[ni] = n0 - 256; ic[ni] = 256; ++ni; }
-      if (nzp > TC_M) { ia[ni] = TC_M; ib[ni] = TC_M; in_[ni] = nzp - TC_M + 16; ic[ni] = n0; ++ni; }
-    }
     const uint32_t ops_s = smem_u32(ops);
     long long it = 0;
     // wait test: a barrier nothing completes, so this wait runs out and the kernel takes its
@@ -186,12 +180,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
         if (lane == 0) {
           const uint32_t hi = ops_s + uint32_t(s) * NCOMP * stage_bytes;
           const uint32_t lo = hi + stage_bytes;
+          const int n0 = nzp + 16;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            for (int i = 0; i < ni; ++i) {
-              const uint32_t ao = uint32_t(ia[i]) * ROWB + kk * 32, bo = uint32_t(ib[i]) * ROWB + kk * 32;
-              const uint32_t idesc = F16 ? idesc_f16(TC_M, in_[i]) : idesc_bf16(TC_M, in_[i]);
-              const uint32_t dt = tmem + uint32_t(ic[i]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              int ar, br, n, col;
+              if (i == 0) { ar = 0; br = 0; n = n0 > 256 ? 256 : n0; col = 0; }
+              else if (i == 1) { if (n0 <= 256) continue; ar = 0; br = 256; n = n0 - 256; col = 256; }
+              else { if (nzp <= TC_M) continue; ar = TC_M; br = TC_M; n = nzp - TC_M + 16; col = n0; }
+              const uint32_t ao = uint32_t(ar) * ROWB + kk * 32, bo = uint32_t(br) * ROWB + kk * 32;
+              const uint32_t idesc = F16 ? idesc_f16(TC_M, n) : idesc_bf16(TC_M, n);
+              const uint32_t dt = tmem + uint32_t(col);
               const uint32_t acc0 = (st > 0 || kk > 0) ? 1u : 0u;
               mma_bf16(dt, sw128_desc(hi + ao), sw128_desc(hi + bo), idesc, acc0);
               if (PASSES == 3) {
@@ -268,7 +268,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
         const float4* rdat = reinterpret_cast<const float4*>(rt + TC_KC);
         const int nvalid = int(min((long long)TC_KC, nrow - st * TC_KC));   // rows past it: padding
         asm volatile("bar.sync 1, %0;" ::"n"(PRODUCER_WARPS * 32) : "memory");
-        asm volatile("bar.sync 1, %0;" ::"n"(PRODUCER_WARPS * 32) : "memory");
         if (ptid == 0) issue_table(it + 1);
         unsigned char* hi = ops + size_t(s) * NCOMP * stage_bytes;
         unsigned char* lo = hi + stage_bytes;
@@ -279,20 +278,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(Dev d) {
           float2 gpv[2][4], gqv[2][4];
           float swv[2][4];
           int zz[2], cc[2];
+          const char* gz[2];
 #pragma unroll
           for (int h2 = 0; h2 < 2; ++h2) {
             const int u = u0 + h2 * PRODUCER_WARPS;
             const bool uv = u < nunits;
             zz[h2] = uv ? (u >> 3) * 32 + lane : nzp;     // nzp: marks an absent unit
             cc[h2] = u & 7;
+            // this lane's depth in every table row (a padding depth reads depth 0, weight 0)
+            gz[h2] = reinterpret_cast<const char*>(g32 + (uv && zz[h2] < nz ? zz[h2] : 0));
 #pragma unroll
             for (int rr = 0; rr < 4; ++rr) {
               const GramRow e = rt[cc[h2] * 4 + rr];
               // entries past the segment's last row belong to the next segment: padding here
               const bool ok2 = uv && zz[h2] < nz && (cc[h2] * 4 + rr) < nvalid;
               swv[h2][rr] = ok2 ? e.sw * sc.x : 0.f;
-              gpv[h2][rr] = ok2 ? __ldg(g32 + size_t(e.offp) * nzs + zz[h2]) : make_float2(0.f, 0.f);
-              gqv[h2][rr] = ok2 ? __ldg(g32 + size_t(e.offq) * nzs + zz[h2]) : make_float2(0.f, 0.f);
+              gpv[h2][rr] = __ldg(reinterpret_cast<const float2*>(gz[h2] + e.bp));
+              gqv[h2][rr] = __ldg(reinterpret_cast<const float2*>(gz[h2] + e.bq));
             }
           }
 #pragma unroll
@@ -412,7 +414,7 @@ __global__ void gram_scale_kernel(Dev d) {
   float ma = 0.f, md = 0.f;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
     const GramRow e = d.gent[r0 + i];
-    ma = fmaxf(ma, e.sw * d.rowmax[e.offp] * d.rowmax[e.offq]);
+    ma = fmaxf(ma, e.sw * d.rowmax[e.rp] * d.rowmax[e.rq]);
     const float4 v = rhs[r0 + i];
     md = fmaxf(md, e.sw * fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
   }

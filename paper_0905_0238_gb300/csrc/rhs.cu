@@ -60,8 +60,10 @@ __global__ void gent_static_kernel(Dev d) {
   const int f = row_f(row), p = row_p(row), q = (p - m) & (N - 1);
   const int np = p <= N / 2 ? p : N - p, nq = q <= N / 2 ? q : N - q;
   GramRow g;
-  g.offp = unsigned(size_t(f) * d.nk + np);
-  g.offq = unsigned(size_t(f) * d.nk + nq);
+  g.rp = unsigned(size_t(f) * d.nk + np);
+  g.rq = unsigned(size_t(f) * d.nk + nq);
+  g.bp = (unsigned long long)g.rp * d.nzs * sizeof(float2);
+  g.bq = (unsigned long long)g.rq * d.nzs * sizeof(float2);
   g.sw = row_w2(row) ? 1.41421356237309515f : 1.0f;
   g.pad = 0.f;
   d.gent[r0 + i] = g;
