@@ -445,6 +445,9 @@ void plan(edt_ctx* c) {
   c->counts_cut.assign(c->nsub, 0);
   auto sidx = [N](int n) { return n <= N / 2 ? n : n - N; };
   const bool ranged = g.sub_end > g.sub_begin;
+  std::vector<uint32_t> kept;
+  std::vector<int> idx_of(size_t(N), -1);
+  std::vector<char> done;
   for (int m = 0; m < c->nsub; ++m) {
     c->row_off[m] = (long long)c->rows.size();
     // a context restricted to subproblems [sub_begin, sub_end) plans no rows for the others
@@ -453,8 +456,8 @@ void plan(edt_ctx* c) {
       c->row_off_mf[size_t(m) * (c->nf + 1) + f] = (long long)c->rows.size();
       if (!inrange) continue;
       const double lim = c->fc[f].lim;
-      // order p = 0, N/2, 1, N-1, 2, N-2, ...: rows p and -p read the same table row g(|p|),
-      // so placed side by side the second read is served from L1
+      // kept rows of (m, f), first in the order p = 0, N/2, 1, N-1, 2, N-2, ...
+      kept.clear();
       for (int pi = 0; pi < N; ++pi) {
         int p;
         if (pi == 0) p = 0;
@@ -469,11 +472,33 @@ void plan(edt_ctx* c) {
         c->counts_cut[m] += 1;
         if (g.fold) {
           const int pp = (N - q) % N;          // first index of the reciprocal partner (-q, -p)
-          if (pp == p) c->rows.push_back(row_pack(f, p, 0));
-          else if (p < pp) c->rows.push_back(row_pack(f, p, 1));
+          if (pp == p) kept.push_back(row_pack(f, p, 0));
+          else if (p < pp) kept.push_back(row_pack(f, p, 1));
         } else {
-          c->rows.push_back(row_pack(f, p, 0));
+          kept.push_back(row_pack(f, p, 0));
         }
+      }
+      // then in chains p, p - m, p - 2m, ...: row (p, q = p - m) and the next row (q, q - m)
+      // read the same table row g(|q|), so side by side the second read is served from L1.
+      // A chain starts at a row whose p + m is not kept (every row is in exactly one chain;
+      // rows left on a cycle are walked from the first of them).
+      if (m == 0 || kept.size() < 2) {
+        c->rows.insert(c->rows.end(), kept.begin(), kept.end());
+      } else {
+        for (size_t i = 0; i < kept.size(); ++i) idx_of[row_p(kept[i])] = int(i);
+        done.assign(kept.size(), 0);
+        auto walk = [&](size_t i0) {
+          for (int j = int(i0); j >= 0 && !done[size_t(j)];
+               j = idx_of[(row_p(kept[size_t(j)]) - m + N) % N]) {
+            done[size_t(j)] = 1;
+            c->rows.push_back(kept[size_t(j)]);
+          }
+        };
+        for (size_t i = 0; i < kept.size(); ++i)
+          if (idx_of[(row_p(kept[i]) + m) % N] < 0) walk(i);
+        for (size_t i = 0; i < kept.size(); ++i)
+          if (!done[i]) walk(i);
+        for (uint32_t r : kept) idx_of[row_p(r)] = -1;
       }
     }
   }
