@@ -263,6 +263,44 @@ def run_cpu_baseline(ms, spec=None):
     raise RuntimeError("cpu baseline failed:\n" + r.stdout[-2000:] + r.stderr[-2000:])
 
 
+def run_cpu_baseline_all_cores(max_cores=16):
+    """The oracle on every host core at once: one single-threaded child per core, each with its
+    own data transform, Green's table and one QR solve of a different midpoint index, started
+    together; the job's rate is the sum of the children's rates (each measured while all
+    children compete for the memory system)."""
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        ncores = os.cpu_count() or 1
+    ncores = max(1, min(int(max_cores), ncores))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs, paths = [], []
+    t0 = time.perf_counter()
+    for c in range(ncores):
+        spec = dict(workload=WORKLOAD, ms=[(1 + 17 * c) % 257])
+        with tempfile.NamedTemporaryFile("w", suffix=".json", delete=False) as f:
+            json.dump(spec, f)
+            paths.append(f.name)
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-child", paths[-1]],
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                                      env=env, cwd=ROOT))
+    rates = []
+    for pr in procs:
+        out, err = pr.communicate()
+        for line in out.splitlines():
+            if line.startswith("CPUJSON "):
+                rates.append(json.loads(line[8:])["value"])
+    wall = time.perf_counter() - t0
+    for pth in paths:
+        os.unlink(pth)
+    if len(rates) != ncores:
+        raise RuntimeError(f"{ncores - len(rates)} of {ncores} oracle children failed")
+    return dict(value=sum(rates), unit="subproblems/s", cores=ncores, kind="oracle",
+                sample=(f"{ncores} single-threaded FP64 numpy oracle processes at once (wall {wall:.1f} s), "
+                        f"each: the full data transform and Green's table amortised over the 257 split "
+                        f"systems plus one QR solve of its own midpoint index; the sum of their rates"))
+
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
     def __init__(self, gpu_index):
@@ -569,6 +607,11 @@ def main():
             cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
         except Exception as ex:  # the GPU number stands; report why the baseline is missing
             cpu = dict(value=None, unit="subproblems/s", cores=0, kind="oracle", sample=str(ex)[:300])
+        try:
+            cpu["all_cores"] = run_cpu_baseline_all_cores()
+        except Exception as ex:
+            cpu["all_cores"] = dict(value=None, unit="subproblems/s", cores=0, kind="oracle",
+                                    sample=str(ex)[:300])
 
     line = dict(
         metric="subproblems_per_sec", value=value, unit="subproblems/s", n_gpus=world,
