@@ -48,6 +48,9 @@ def parse():
                          "2 native FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--freq-stride", type=int, default=1,
+                    help="profiling aid: keep every k-th frequency of the 2D line (a smaller case of "
+                         "the same kernels for profiler captures; not a bench line)")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default launch shapes instead of the autotuned ones")
@@ -422,6 +425,8 @@ def main():
             dist.barrier()
 
     wl = synth.preset(WORKLOAD)
+    if args.freq_stride > 1:
+        wl.freq_hz = wl.freq_hz[::args.freq_stride]
     rng = synth.rng_for(1, salt=line_salt(rank))     # each rank: its own survey line
     V = synth.perturbation_random_field(rng, wl.nx, wl.dx, wl.nz, wl.dz, wl.z0,
                                         wl.layer_top, wl.layer_vel, corr=40.0, rms=0.03)
@@ -617,7 +622,7 @@ def main():
         metric="subproblems_per_sec", value=value, unit="subproblems/s", n_gpus=world,
         steps=args.steps, warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="f16x3+f32acc+f64", data="synthetic",
-        config=dict(workload=workload_summary(wl), l2="inputs larger than L2 (268 MB data per step)",
+        config=dict(workload=workload_summary(wl), l2=f"inputs larger than L2 ({D.numel() * D.element_size() / 1e6:.0f} MB data per step)",
                     passes=args.passes, refine=args.refine, chol_df=args.chol_df, alpha=wl.alpha,
                     rows_total=int(st.rows_total), rows_solved=int(st.rows_solved),
                     parallelism=f"replicas x{world} (independent lines)",
