@@ -217,7 +217,11 @@ __global__ void __launch_bounds__(1024) cdf_diag_kernel(Dev d, int k0) {
     return;
   }
   a = df_norm(a);
-  if (in) { A[size_t(k0 + i) * n + k0 + l] = a; sLf[i * FLD + l] = a; }
+  if (in) {
+    A[size_t(k0 + i) * n + k0 + l] = a;
+    sLf[i * FLD + l] = a;
+    if (d.L32) d.L32[size_t(m) * n * n + size_t(k0 + i) * n + k0 + l] = a.x;   // FP32 copy
+  }
   if (threadIdx.x < kb) d.dinv[size_t(m) * n + k0 + threadIdx.x] = df_val(sInv[threadIdx.x]);
   __syncthreads();
   // X = L^-1: right-looking forward substitution on the identity, row k final at step k
@@ -282,7 +286,11 @@ __global__ void __launch_bounds__(128) cdf_panel_kernel(Dev d, int k0) {
 #pragma unroll
   for (int q = 0; q < FB / 4; ++q) {
     const int r = h + 4 * q;
-    if (r < nr) A[size_t(r0 + r) * n + k0 + lane] = sA[lane * FLD + r];
+    if (r < nr) {
+      const float2 v = sA[lane * FLD + r];
+      A[size_t(r0 + r) * n + k0 + lane] = v;
+      if (d.L32) d.L32[size_t(m) * n * n + size_t(r0 + r) * n + k0 + lane] = v.x;   // FP32 copy
+    }
   }
 }
 
@@ -358,7 +366,8 @@ __global__ void __launch_bounds__(256) cdf_update_kernel(Dev d, int k0, int part
 }
 
 // Both substitutions and the solution; the factor stays in double-float (its readers take
-// the pairs), its high parts are the FP32 copy for the refinement's correction solves.
+// the pairs).  Its high parts, the FP32 copy for the refinement's correction solves, were
+// written by the diagonal-block and panel kernels as each element became final.
 __global__ void __launch_bounds__(FTHREADS) cdf_final_kernel(Dev d) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int m = blockIdx.x, n = d.nz;
@@ -393,26 +402,6 @@ __global__ void __launch_bounds__(FTHREADS) cdf_final_kernel(Dev d) {
     if (!isfinite(v)) bad = true;
   }
   bad = __syncthreads_or(bad);
-  if (L32) {
-    // batches of eight loads before their stores (L32 and A may alias for the compiler)
-    const size_t tot = size_t(n) * n;
-    for (size_t e0 = threadIdx.x; e0 < tot; e0 += 8 * size_t(blockDim.x)) {
-      float v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const size_t e = e0 + size_t(q) * blockDim.x;
-        v[q] = e < tot ? A[e].x : 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const size_t e = e0 + size_t(q) * blockDim.x;
-        if (e < tot) {
-          const int i = int(e / n), j = int(e - size_t(i) * n);
-          if (j <= i) L32[e] = v[q];
-        }
-      }
-    }
-  }
   if (threadIdx.x == 0 && bad) d.status[m] = EDT_ENONFINITE;
 }
 
