@@ -16,6 +16,7 @@
 // refinement kernel, gives one step of iterative refinement on the normal equations.
 #include "edt_internal.h"
 #include "cplx.cuh"
+#include "dfloat.cuh"
 
 namespace edt {
 
@@ -385,6 +386,85 @@ __device__ void chol_solve32_2rhs(const float* A, const float* dinv, int n, floa
   }
 }
 
+// Solve L L^T y = sb in double-float for two right-hand sides (sb[i][0..1]).  L is lower,
+// double-float in A (ld n), each 32 x 32 diagonal block holding its inverse X = L_kk^-1 in its
+// strict upper triangle (X_il at (l, i), written by the blocked panel step) with the diagonal
+// 1 / L_ii in dinv: every block solve is a parallel matrix-vector product (warp k: right-hand side k,
+// lane: row), the off-diagonal blocks are applied by thread-per-row (forward) or coalesced
+// column (backward) sweeps.  sX: [NB][LDP] shared scratch.
+__device__ void chol_solve_df_2rhs(const float2* A, const double* dinv, int n, float2* sb, float2* sX) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nblk = (n + NB - 1) / NB;
+  auto load_x = [&](int k0, int kb) {          // sX[i * LDP + l] = X_il (lower, with the diagonal)
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      const int i = e / NB, l = e - i * NB;
+      float2 v = make_float2(0.f, 0.f);
+      if (i < kb && l < kb) {
+        if (l < i) v = A[size_t(k0 + l) * n + k0 + i];
+        else if (l == i) v = df_of(dinv[k0 + i]);
+      }
+      sX[i * LDP + l] = v;
+    }
+  };
+  for (int bk = 0; bk < nblk; ++bk) {                       // forward: L y = b
+    const int k0 = bk * NB, kb = min(NB, n - k0);
+    load_x(k0, kb);
+    __syncthreads();
+    float2 y = make_float2(0.f, 0.f);
+    if (warp < 2 && lane < kb) {                            // y_blk = X b_blk
+      for (int l = 0; l <= lane; ++l) df_acc(y, sX[lane * LDP + l], sb[(k0 + l) * 2 + warp]);
+    }
+    __syncthreads();
+    if (warp < 2 && lane < kb) sb[(k0 + lane) * 2 + warp] = df_norm(y);
+    __syncthreads();
+    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {   // b_i -= L[i][blk] . y
+      float2 s0 = sb[i * 2], s1 = sb[i * 2 + 1];
+      const float2* Ai = A + size_t(i) * n + k0;
+      float2 av[NB];                                                  // loads in flight together
+#pragma unroll
+      for (int l = 0; l < NB; ++l) av[l] = l < kb ? Ai[l] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int l = 0; l < NB; ++l) {
+        if (l < kb) {
+          const float2 a = df_neg(av[l]);
+          df_acc(s0, a, sb[(k0 + l) * 2]);
+          df_acc(s1, a, sb[(k0 + l) * 2 + 1]);
+        }
+      }
+      sb[i * 2] = df_norm(s0); sb[i * 2 + 1] = df_norm(s1);
+    }
+    __syncthreads();
+  }
+  for (int bk = nblk - 1; bk >= 0; --bk) {                  // backward: L^T x = y
+    const int k0 = bk * NB, kb = min(NB, n - k0);
+    load_x(k0, kb);
+    __syncthreads();
+    float2 x = make_float2(0.f, 0.f);
+    if (warp < 2 && lane < kb) {                            // x_blk = X^T y_blk
+      for (int i = lane; i < kb; ++i) df_acc(x, sX[i * LDP + lane], sb[(k0 + i) * 2 + warp]);
+    }
+    __syncthreads();
+    if (warp < 2 && lane < kb) sb[(k0 + lane) * 2 + warp] = df_norm(x);
+    __syncthreads();
+    for (int i = threadIdx.x; i < k0; i += blockDim.x) {    // y_i -= sum_l L[k0+l][i] x_l
+      float2 s0 = sb[i * 2], s1 = sb[i * 2 + 1];
+      float2 av[NB];
+#pragma unroll
+      for (int l = 0; l < NB; ++l) av[l] = l < kb ? A[size_t(k0 + l) * n + i] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int l = 0; l < NB; ++l) {
+        if (l < kb) {
+          const float2 a = df_neg(av[l]);
+          df_acc(s0, a, sb[(k0 + l) * 2]);
+          df_acc(s1, a, sb[(k0 + l) * 2 + 1]);
+        }
+      }
+      sb[i * 2] = df_norm(s0); sb[i * 2 + 1] = df_norm(s1);
+    }
+    __syncthreads();
+  }
+}
+
 // Refinement update with the FP32 factor: x += (LL^T)^-1 (r - lam x); r - lam x in FP64,
 // rounded to FP32 for the solve, the correction added to x in FP64.
 template <bool VAR>
@@ -449,9 +529,14 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(Dev d, int mode) {
 
 // ------------------------------------------------------------------ blocked Cholesky, several
 // launches per factorisation: step k (columns k0 = 32 k .. k0 + 31) is one panel launch (one CTA
-// per active subproblem: diagonal block by one warp, panel rows by row-per-thread triangular
-// solves) and one update launch over 64 x 64 tiles of every active subproblem's trailing lower
-// triangle, so a large factorisation spreads over many SMs instead of running on one.
+// per active subproblem: the diagonal block factored and inverted, the panel rows multiplied by
+// the inverse) and one update launch over 64 x 64 tiles of every active subproblem's trailing
+// lower triangle, so a large factorisation spreads over many SMs instead of running on one.
+// The matrix is held in double-float (float2 (hi, lo) per entry, in the 8 bytes an FP64 entry
+// would take) and every step computes in double-float on the FP32 pipes: about 48 significant
+// bits against FP64's 53, at a small fraction of the cost on a part whose FP64 rate is 1/64 of
+// its FP32 rate.  The conversions FP64 <-> double-float run on the FP64 unit too, so the matrix
+// is converted once, by its producer, not on every access.
 constexpr int UT = 64;
 
 template <bool VAR>
@@ -461,11 +546,17 @@ __device__ __forceinline__ void sub_geom(const Dev& d, int m, int& n, size_t& go
   vo = VAR ? size_t(d.sub_voff[m]) : size_t(m) * n;
 }
 
-// trace_mode 0: trace from the diagonal of G; 1: lam = alpha * trace[m] (the producer's trace).
+// Panel step: the diagonal block is factored and inverted by all 256 threads (thread
+// (warp, lane) holds elements (warp + 8 q, lane), q < 4; per column one pivot step, one scale
+// step and one rank-1 update step between barriers, the column double-buffered in shared
+// memory), then every panel row is multiplied by X^T, X = L_kk^-1: x_j = sum_{l <= j} a_l X_jl,
+// outputs independent, one row per thread.  X is also written to the strict upper triangle of
+// the diagonal block (X_il at (l, i)) for the solves.  trace_mode 0: trace from the diagonal of
+// G; 1: lam = alpha * trace[m] (the producer's trace).
 template <bool VAR>
-__global__ void __launch_bounds__(256) cb_panel_kernel(Dev d, int k0, const int* act, int trace_mode) {
-  __shared__ double sD[NB * LDP];
-  __shared__ double sInv[NB];
+__global__ void __launch_bounds__(256) cb_panel_df_kernel(Dev d, int k0, const int* act, int trace_mode) {
+  __shared__ float2 sL[NB * LDP];                 // L_kk, then X = L_kk^-1 (both lower, [i][l])
+  __shared__ float2 sCol[2][NB], sInv[NB], sXr[2][NB];
   __shared__ double red[40];
   __shared__ int fail;
   const int m = act[blockIdx.x];
@@ -474,94 +565,144 @@ __global__ void __launch_bounds__(256) cb_panel_kernel(Dev d, int k0, const int*
   sub_geom<VAR>(d, m, n, go, vo);
   if (d.status[m] != EDT_OK) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* A = d.G + go;
+  float2* A = reinterpret_cast<float2*>(d.G) + go;
   if (threadIdx.x == 0) fail = 0;
   if (k0 == 0) {
     double tr;
     if (trace_mode == 0) {
       double t = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) t += A[size_t(i) * n + i];
+      for (int i = threadIdx.x; i < n; i += blockDim.x) t += df_val(A[size_t(i) * n + i]);
       tr = block_sum(t, red);
     } else {
       tr = d.trace[m];
     }
     const double lam = d.alpha * tr;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) A[size_t(i) * n + i] += lam;
+    const float2 lamf = df_of(lam);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) A[size_t(i) * n + i] = df_add(A[size_t(i) * n + i], lamf);
     __syncthreads();
     if (threadIdx.x == 0) d.trace[m] = lam;
   }
   const int kb = min(NB, n - k0);
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    const int i = e / kb, j = e - i * kb;
-    if (j <= i) sD[i * LDP + j] = A[size_t(k0 + i) * n + k0 + j];
+  float2 a[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = warp + 8 * q;
+    a[q] = i < kb && lane <= i ? A[size_t(k0 + i) * n + k0 + lane] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  if (warp == 0) {
-    for (int j = 0; j < kb; ++j) {
-      const double djj = sD[j * LDP + j];
-      if (!(djj > 0.0) || !isfinite(djj)) { if (lane == 0) fail = 1; break; }
-      const double inv = rsqrt(djj);
-      __syncwarp();
-      if (lane == j) { sD[j * LDP + j] = djj * inv; sInv[j] = inv; }
-      if (lane > j && lane < kb) sD[lane * LDP + j] *= inv;
-      __syncwarp();
-      if (lane > j && lane < kb) {
-        const double lij = sD[lane * LDP + j];
-        for (int l = j + 1; l <= lane; ++l) sD[lane * LDP + l] -= lij * sD[l * LDP + j];
+  for (int j = 0; j < kb; ++j) {
+    float2* col = sCol[j & 1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (warp + 8 * q == j && lane == j) {
+        const float2 djj = df_norm(a[q]);
+        if (!(djj.x > 0.f) || !isfinite(djj.x)) {
+          fail = 1;
+        } else {
+          const float2 inv = df_rsqrt(djj);
+          a[q] = df_mul(djj, inv);
+          sInv[j] = inv;
+          col[j] = a[q];
+        }
       }
-      __syncwarp();
+    }
+    __syncthreads();
+    if (fail) break;                                 // the same value in every thread
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = warp + 8 * q;
+      if (lane == j && i > j && i < kb) { a[q] = df_mul(df_norm(a[q]), sInv[j]); col[i] = a[q]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = warp + 8 * q;
+      if (lane > j && i >= lane && i < kb) df_acc(a[q], df_neg(col[i]), col[lane]);
     }
   }
-  __syncthreads();
   if (fail) {
     if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
     return;
   }
   float* L32 = d.L32 ? d.L32 + go : nullptr;
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    const int i = e / kb, j = e - i * kb;
-    if (j <= i) {
-      A[size_t(k0 + i) * n + k0 + j] = sD[i * LDP + j];
-      if (L32) L32[size_t(k0 + i) * n + k0 + j] = float(sD[i * LDP + j]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = warp + 8 * q;
+    if (i < kb && lane <= i) {
+      a[q] = df_norm(a[q]);
+      sL[i * LDP + lane] = a[q];
+      A[size_t(k0 + i) * n + k0 + lane] = a[q];
+      if (L32) L32[size_t(k0 + i) * n + k0 + lane] = a[q].x;
     }
   }
-  for (int j = threadIdx.x; j < kb; j += blockDim.x) {
-    d.dinv[vo + k0 + j] = sInv[j];
-    if (L32) d.dinv32[vo + k0 + j] = float(sInv[j]);
+  if (threadIdx.x < kb) {
+    d.dinv[vo + k0 + threadIdx.x] = df_val(sInv[threadIdx.x]);
+    if (L32) d.dinv32[vo + k0 + threadIdx.x] = sInv[threadIdx.x].x;
   }
-  const int t0 = k0 + kb;
-  for (int i = t0 + threadIdx.x; i < n; i += blockDim.x) {
-    double x[NB];
-    double* Ai = A + size_t(i) * n + k0;
+  __syncthreads();
+  // X = L_kk^-1: right-looking forward substitution on the identity, row k final at step k
+  float2 x[4];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) x[j] = j < kb ? Ai[j] : 0.0;
+  for (int q = 0; q < 4; ++q) x[q] = make_float2(warp + 8 * q == lane ? 1.f : 0.f, 0.f);
+  for (int k = 0; k < kb; ++k) {
+    float2* xr = sXr[k & 1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (warp + 8 * q == k) {
+        if (lane <= k) x[q] = df_mul(df_norm(x[q]), sInv[k]);
+        xr[lane] = lane <= k ? x[q] : make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = warp + 8 * q;
+      if (i > k && i < kb && lane <= k) df_acc(x[q], df_neg(sL[i * LDP + k]), xr[lane]);
+    }
+  }
+  __syncthreads();                                   // every read of L_kk done
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = warp + 8 * q;
+    const float2 v = i < kb && lane <= i ? df_norm(x[q]) : make_float2(0.f, 0.f);
+    sL[i * LDP + lane] = v;                           // X_{i, lane}; zero outside the block
+    if (i < kb && lane < i) A[size_t(k0 + lane) * n + k0 + i] = v;
+  }
+  __syncthreads();
+  for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {
+    float2* Ai = A + size_t(i) * n + k0;
+    float2 acc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int l = 0; l < NB; ++l) {
+      if (l < kb) {
+        const float2 al = Ai[l];
+#pragma unroll
+        for (int j = l; j < NB; ++j) df_acc(acc[j], al, sL[j * LDP + l]);
+      }
+    }
+    float* Li = L32 ? L32 + size_t(i) * n + k0 : nullptr;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       if (j < kb) {
-        double sacc = x[j];
-#pragma unroll
-        for (int l = 0; l < j; ++l) sacc -= x[l] * sD[j * LDP + l];
-        x[j] = sacc * sInv[j];
+        const float2 v = df_norm(acc[j]);
+        Ai[j] = v;
+        if (Li) Li[j] = v.x;
       }
-    }
-#pragma unroll
-    for (int j = 0; j < NB; ++j)
-      if (j < kb) Ai[j] = x[j];
-    if (L32) {
-      float* Li = L32 + size_t(i) * n + k0;
-#pragma unroll
-      for (int j = 0; j < NB; ++j)
-        if (j < kb) Li[j] = float(x[j]);
     }
   }
 }
 
-// One 64 x 64 tile (bi, bj <= bi) of the trailing lower triangle: C -= P_bi P_bj^T; thread
-// (ti, tj) owns rows ti + 16 u and columns tj + 16 v (conflict-free shared-memory reads).
+// One 64 x 64 tile (bi, bj <= bi) of the trailing lower triangle: C -= P_bi P_bj^T, the
+// 32-term dot products accumulated in double-float.  Thread (ty, tx) owns rows ty + 16 u and
+// columns tx + 16 v (u, v < 4): interleaved, so the shared panel reads are conflict-free and
+// the global rows coalesced.
+constexpr int ULD = UT + 1;
 template <bool VAR>
-__global__ void __launch_bounds__(256) cb_update_kernel(Dev d, int k0, const int* act,
-                                                        const long long* tpre, int nact) {
-  __shared__ double Pi[UT * LDP], Pj[UT * LDP];
+__global__ void __launch_bounds__(256) cb_update_df_kernel(Dev d, int k0, const int* act,
+                                                           const long long* tpre, int nact) {
+  __shared__ float2 sI[NB * ULD], sJ[NB * ULD];   // transposed panel rows: [l][i]
   int lo = 0, hi = nact - 1;
   const long long t = blockIdx.x;
   while (lo < hi) {
@@ -580,34 +721,80 @@ __global__ void __launch_bounds__(256) cb_update_kernel(Dev d, int k0, const int
   while ((bi + 1) * (bi + 2) / 2 <= e) ++bi;
   const int bj = e - bi * (bi + 1) / 2;
   const int r0 = t0 + bi * UT, c0 = t0 + bj * UT;
-  double* A = d.G + go;
-  for (int q = threadIdx.x; q < UT * kb; q += blockDim.x) {
-    const int i = q / kb, l = q - i * kb;
-    Pi[i * LDP + l] = r0 + i < n ? A[size_t(r0 + i) * n + k0 + l] : 0.0;
-    Pj[i * LDP + l] = c0 + i < n ? A[size_t(c0 + i) * n + k0 + l] : 0.0;
-  }
-  __syncthreads();
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
-  double acc[4][4] = {};
-  for (int l = 0; l < kb; ++l) {
-    double pi[4], pj[4];
+  float2* A = reinterpret_cast<float2*>(d.G) + go;
+  {
+    constexpr int NL = UT * NB / 256;               // 8 elements of each panel per thread
+    float2 vi[NL], vj[NL];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      pi[u] = Pi[(ti + 16 * u) * LDP + l];
-      pj[u] = Pj[(tj + 16 * u) * LDP + l];
+    for (int q = 0; q < NL; ++q) {
+      const int x = threadIdx.x + 256 * q, i = x / NB, l = x - i * NB;   // a warp: one row's 32 columns
+      vi[q] = r0 + i < n && l < kb ? A[size_t(r0 + i) * n + k0 + l] : make_float2(0.f, 0.f);
+      vj[q] = c0 + i < n && l < kb ? A[size_t(c0 + i) * n + k0 + l] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int q = 0; q < NL; ++q) {
+      const int x = threadIdx.x + 256 * q, i = x / NB, l = x - i * NB;
+      sI[l * ULD + i] = vi[q];
+      sJ[l * ULD + i] = vj[q];
+    }
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool diag = bi == bj;
+  float2 acc[4][4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = fma(pi[u], pj[v], acc[u][v]);
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
+  for (int l = 0; l < kb; ++l) {
+    float2 pi[4], pj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { pi[u] = sI[l * ULD + ty + 16 * u]; pj[u] = sJ[l * ULD + tx + 16 * u]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r0 + ty + 16 * u < n)                                 // rows past n: nothing to update
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (!(diag && u < v)) df_acc(acc[u][v], pi[u], pj[v]);   // above the diagonal: unused
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const int row = r0 + ti + 16 * u, col = c0 + tj + 16 * v;
-      if (row < n && col <= row) A[size_t(row) * n + col] -= acc[u][v];
+      const int row = r0 + ty + 16 * u, col = c0 + tx + 16 * v;
+      if (row < n && col <= row && !(diag && u < v)) {
+        float2* c = A + size_t(row) * n + col;
+        *c = df_add(*c, df_neg(df_norm(acc[u][v])));
+      }
     }
+}
+
+// x = (LL^T)^-1 b in double-float after the blocked factorisation (the inverse diagonal
+// blocks in the upper triangles); b and x FP64.
+template <bool VAR>
+__global__ void __launch_bounds__(256) chol_solve_df_kernel(Dev d) {
+  extern __shared__ __align__(16) float2 sbd[];
+  __shared__ float2 sX[NB * LDP];
+  const int m = blockIdx.x;
+  int n;
+  size_t go, vo;
+  sub_geom<VAR>(d, m, n, go, vo);
+  double* xo = d.x + vo * 2;
+  if (d.row_off[m + 1] == d.row_off[m] || d.status[m] != EDT_OK) {
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    return;
+  }
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) sbd[i] = df_of(d.b[vo * 2 + i]);
+  __syncthreads();
+  chol_solve_df_2rhs(reinterpret_cast<const float2*>(d.G) + go, d.dinv + vo, n, sbd, sX);
+  bool bad = false;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+    const double v = df_val(sbd[i]);
+    xo[i] = v;
+    if (!isfinite(v)) bad = true;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0 && bad) d.status[m] = EDT_ENONFINITE;
 }
 
 __global__ void trace_diag_kernel(Dev d) {
@@ -669,7 +856,8 @@ cudaError_t launch_chol_var(const Dev& d, int nmax, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Blocked form: nstep panel + update launches, then the solves.  act + k * nsub lists the
+// Blocked form: nstep panel + update launches, then the solves; d.G holds double-float entries
+// (a float2 in each 8-byte slot) and the solution is FP64.  act + k * nsub lists the
 // subproblems active at step k (n > 32 k, rows > 0), nact[k] of them; tpre + k * (nsub + 1) the
 // prefix sums of their trailing tile counts (tpre[k][nact[k]] tiles in the update launch).
 template <bool VAR>
@@ -677,12 +865,12 @@ static cudaError_t blocked(const Dev& d, int nmax, int nstep, const int* act, co
                            const long long* tpre, const long long* ntile, int trace_mode, cudaStream_t s) {
   for (int k = 0; k < nstep; ++k) {
     if (nact[k] == 0) continue;
-    cb_panel_kernel<VAR><<<nact[k], 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub, trace_mode);
+    cb_panel_df_kernel<VAR><<<nact[k], 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub, trace_mode);
     if (ntile[k] > 0)
-      cb_update_kernel<VAR><<<unsigned(ntile[k]), 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub,
-                                                               tpre + size_t(k) * (d.nsub + 1), nact[k]);
+      cb_update_df_kernel<VAR><<<unsigned(ntile[k]), 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub,
+                                                                  tpre + size_t(k) * (d.nsub + 1), nact[k]);
   }
-  chol_solve_kernel<VAR><<<d.nsub, 256, size_t(2 * nmax) * sizeof(double), s>>>(d, 0);
+  chol_solve_df_kernel<VAR><<<d.nsub, 256, size_t(2 * nmax) * sizeof(float2), s>>>(d);
   return cudaGetLastError();
 }
 

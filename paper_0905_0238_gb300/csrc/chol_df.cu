@@ -29,6 +29,7 @@
 //     the refinement's correction solves.
 // A non-positive or non-finite pivot marks the subproblem EDT_ENOTPD and zeroes its solution.
 #include "edt_internal.h"
+#include "dfloat.cuh"
 
 namespace edt {
 
@@ -36,45 +37,6 @@ namespace {
 
 constexpr int FB = 32, FLD = FB + 1, FTHREADS = 256;
 constexpr int UT = 64, ULD = UT + 1;   // update tile and its padded shared row
-
-// ---- double-float arithmetic (float2: .x high part, .y low part) ----------------------------
-// The _rn intrinsics keep the compiler from contracting the error-free steps into fma.
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
-}
-__device__ __forceinline__ float2 fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
-  const float s = __fadd_rn(a, b);
-  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-__device__ __forceinline__ float2 df_norm(float2 a) { return fast_two_sum(a.x, a.y); }
-__device__ __forceinline__ float2 df_of(double x) {
-  const float h = __double2float_rn(x);
-  return make_float2(h, __double2float_rn(x - double(h)));
-}
-__device__ __forceinline__ double df_val(float2 a) { return double(a.x) + double(a.y); }
-__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-  const float2 s = two_sum(a.x, b.x);
-  return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
-}
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  const float e = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
-  return fast_two_sum(p, e);
-}
-// accumulator s (high sum, low sum; not normalised) += a * b
-__device__ __forceinline__ void df_acc(float2& s, float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  const float e = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
-  const float2 t = two_sum(s.x, p);
-  s.x = t.x;
-  s.y = __fadd_rn(s.y, __fadd_rn(t.y, e));
-}
-__device__ __forceinline__ float2 shfl_df(float2 v, int src) {
-  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
 
 // Solve L L^T y = sb for two right-hand sides (sb[i][0..1], double-float).  L is lower, double-
 // float in A (ld n); each 32 x 32 diagonal block also holds its inverse X = L_kk^-1 in its strict
@@ -160,15 +122,6 @@ __device__ void solve_df_2rhs(const float2* A, const float2* sInv, int n, float2
     }
     __syncthreads();
   }
-}
-
-// 1 / sqrt(a) for a double-float a > 0: the FP32 estimate y0 and one Newton step carried in
-// double-float, y = y0 + y0 (1 - a y0^2) / 2 (the step doubles the ~23 correct bits).
-__device__ __forceinline__ float2 df_rsqrt(float2 a) {
-  const float y0 = rsqrtf(a.x);
-  const float2 y2 = df_mul(make_float2(y0, 0.f), make_float2(y0, 0.f));
-  const float2 r = df_add(make_float2(1.f, 0.f), df_neg(df_mul(a, y2)));   // 1 - a y0^2, small
-  return fast_two_sum(y0, 0.5f * y0 * r.x);
 }
 
 __device__ __forceinline__ bool has_rows(const Dev& d, int m) { return d.row_off[m + 1] > d.row_off[m]; }

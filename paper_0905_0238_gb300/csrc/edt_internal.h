@@ -288,7 +288,8 @@ cudaError_t prepare_chol_var(int nmax);
 cudaError_t launch_chol_var(const Dev& d, int nmax, cudaStream_t s);
 cudaError_t launch_refine_update_var(const Dev& d, int nmax, cudaStream_t s);
 // Blocked Cholesky over several launches (panel + tile update per 32-column step, then the
-// solves); see chol.cu for the step lists.  chol_blocked_tiles: update tiles of step k0 of an
+// solves), in double-float: d.G holds a float2 (hi, lo) pair in each 8-byte slot; see chol.cu
+// for the step lists.  chol_blocked_tiles: update tiles of step k0 of an
 // n-unknown subproblem; chol_block_cols: the panel width.
 cudaError_t launch_chol_blocked(const Dev& d, bool var, int nmax, int nstep, const int* act_dev,
                                 const int* nact_host, const long long* tpre_dev,

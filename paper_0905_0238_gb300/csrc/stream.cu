@@ -17,10 +17,11 @@
 //             alpha trace(Ahat^T Ahat) accumulated from the unrounded FP32 rows;
 //   st_gram   persistent tcgen05 kernel over (request, 128-depth tile pair) items: bulk copies
 //             stage the hi/lo tiles, three BF16 MMAs per K step accumulate in tensor memory,
-//             the epilogue writes the FP64 lower triangle of G and b_+- = Ahat^T dhat_+-;
-//   chol      FP64 Cholesky of G + lam I in 32-column steps (a panel launch and a 64 x 64 tile
-//             update launch per step over every active request, so one large factorisation
-//             spreads over many SMs), then the two solves (per-request size);
+//             the epilogue writes the lower triangle of G (the FP32 accumulators as double-
+//             float pairs (v, 0)) and b_+- = Ahat^T dhat_+- (FP64);
+//   chol      double-float Cholesky of G + lam I in 32-column steps (a panel launch and a
+//             64 x 64 tile update launch per step over every active request, so one large
+//             factorisation spreads over many SMs), then the two solves (per-request size);
 //   st_refine matrix-free residual Ahat^T (dhat - Ahat x), FP32 products, FP64 accumulation;
 //   update    x += (LL^T)^-1 (r - lam x) with the FP32 copy of the factor.
 // Every wait of the tensor-core kernel is bounded; on expiry it raises a device flag.
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1) st_gram_kernel(StBatch b) {
       const bool last = itm.tj == S.nzt - 1;
       const int ncol = last ? ST_TILE + ST_DROWS : ST_TILE;
       const int a = itm.ti * ST_TILE + qd * 32 + lane;
-      double* G = b.G + S.o_G;
+      float2* G = reinterpret_cast<float2*>(b.G) + S.o_G;
       for (int c0 = 0; c0 < ncol; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + (uint32_t(qd * 32) << 16) + uint32_t(c0), v);
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1) st_gram_kernel(StBatch b) {
           const int col = c0 + c;
           if (col < ST_TILE) {
             const int bc = itm.tj * ST_TILE + col;
-            if (a < S.nz && bc < S.nz) G[size_t(bc) * S.nz + a] = double(v[c]);   // lower triangle
+            if (a < S.nz && bc < S.nz) G[size_t(bc) * S.nz + a] = make_float2(v[c], 0.f);   // lower triangle
           } else if (col < ST_TILE + 2 && a < S.nz) {
             b.b[(S.o_v + a) * 2 + (col - ST_TILE)] = double(v[c]);
           }

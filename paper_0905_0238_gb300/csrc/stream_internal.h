@@ -32,7 +32,7 @@ struct StSub {
   long long o_coef;       // coef: [nf][nk][nl][8]
   long long o_g;          // g32: [nf][nk][nzs]
   long long o_tile;       // tiles (bytes): [kst][hi, lo][nzt * 128 + 16][128]
-  long long o_G;          // G (double), L32 (float): [nz][nz]
+  long long o_G;          // G (double-float pairs), L32 (float): [nz][nz]
 };
 
 // Tensor-core Gram work item: request, depth tile of the rows (ti) and of the columns (tj >= ti).
@@ -59,7 +59,7 @@ struct StBatch {
   float* coef;
   float2* g32;
   unsigned char* tiles;
-  double* G;
+  double* G;                     // [sum nz^2] double-float pairs (float2 per 8-byte slot)
   float* L32;
   double* dinv;
   float* dinv32;
