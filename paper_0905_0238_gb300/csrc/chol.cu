@@ -546,42 +546,24 @@ __device__ __forceinline__ void sub_geom(const Dev& d, int m, int& n, size_t& go
   vo = VAR ? size_t(d.sub_voff[m]) : size_t(m) * n;
 }
 
-// Panel step: the diagonal block is factored and inverted by all 256 threads (thread
-// (warp, lane) holds elements (warp + 8 q, lane), q < 4; per column one pivot step, one scale
-// step and one rank-1 update step between barriers, the column double-buffered in shared
-// memory), then every panel row is multiplied by X^T, X = L_kk^-1: x_j = sum_{l <= j} a_l X_jl,
-// outputs independent, one row per thread.  X is also written to the strict upper triangle of
-// the diagonal block (X_il at (l, i)) for the solves.  trace_mode 0: trace from the diagonal of
-// G; 1: lam = alpha * trace[m] (the producer's trace).
-template <bool VAR>
-__global__ void __launch_bounds__(256) cb_panel_df_kernel(Dev d, int k0, const int* act, int trace_mode) {
-  __shared__ float2 sL[NB * LDP];                 // L_kk, then X = L_kk^-1 (both lower, [i][l])
-  __shared__ float2 sCol[2][NB], sInv[NB], sXr[2][NB];
-  __shared__ double red[40];
-  __shared__ int fail;
-  const int m = act[blockIdx.x];
-  int n;
-  size_t go, vo;
-  sub_geom<VAR>(d, m, n, go, vo);
-  if (d.status[m] != EDT_OK) return;
+// Shared scratch of the diagonal-block factorisation.
+struct DiagScratch {
+  float2 L[NB * LDP];                             // L_kk (lower, [i][l])
+  float2 col[2][NB], inv[NB], xr[2][NB];
+  int fail;
+};
+
+// Diagonal block of step k0 of one subproblem (kb = min(32, n - k0) columns), factored and
+// inverted in double-float by the 256 threads of the calling CTA: thread (warp, lane) holds
+// elements (warp + 8 q, lane), q < 4; per column one pivot step, one scale step and one rank-1
+// update step between barriers (the column double-buffered in shared memory); then X = L_kk^-1
+// by the same right-looking sweep over the identity.  Writes L_kk (lower triangle) and its FP32
+// copy, X to the strict upper triangle (X_il at (l, i)), and the reciprocal pivots (FP64 and
+// FP32).  A non-positive or non-finite pivot sets EDT_ENOTPD.  Every thread of the CTA calls
+// it; A's block must be final and visible to the CTA.
+__device__ void cb_diag_block(float2* A, float* L32, double* dinv, float* dinv32, int* status, int n,
+                              int k0, DiagScratch& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float2* A = reinterpret_cast<float2*>(d.G) + go;
-  if (threadIdx.x == 0) fail = 0;
-  if (k0 == 0) {
-    double tr;
-    if (trace_mode == 0) {
-      double t = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) t += df_val(A[size_t(i) * n + i]);
-      tr = block_sum(t, red);
-    } else {
-      tr = d.trace[m];
-    }
-    const double lam = d.alpha * tr;
-    const float2 lamf = df_of(lam);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) A[size_t(i) * n + i] = df_add(A[size_t(i) * n + i], lamf);
-    __syncthreads();
-    if (threadIdx.x == 0) d.trace[m] = lam;
-  }
   const int kb = min(NB, n - k0);
   float2 a[4];
 #pragma unroll
@@ -589,29 +571,30 @@ __global__ void __launch_bounds__(256) cb_panel_df_kernel(Dev d, int k0, const i
     const int i = warp + 8 * q;
     a[q] = i < kb && lane <= i ? A[size_t(k0 + i) * n + k0 + lane] : make_float2(0.f, 0.f);
   }
+  if (threadIdx.x == 0) sh.fail = 0;
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    float2* col = sCol[j & 1];
+    float2* col = sh.col[j & 1];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (warp + 8 * q == j && lane == j) {
         const float2 djj = df_norm(a[q]);
         if (!(djj.x > 0.f) || !isfinite(djj.x)) {
-          fail = 1;
+          sh.fail = 1;
         } else {
           const float2 inv = df_rsqrt(djj);
           a[q] = df_mul(djj, inv);
-          sInv[j] = inv;
+          sh.inv[j] = inv;
           col[j] = a[q];
         }
       }
     }
     __syncthreads();
-    if (fail) break;                                 // the same value in every thread
+    if (sh.fail) break;                              // the same value in every thread
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = warp + 8 * q;
-      if (lane == j && i > j && i < kb) { a[q] = df_mul(df_norm(a[q]), sInv[j]); col[i] = a[q]; }
+      if (lane == j && i > j && i < kb) { a[q] = df_mul(df_norm(a[q]), sh.inv[j]); col[i] = a[q]; }
     }
     __syncthreads();
 #pragma unroll
@@ -620,24 +603,23 @@ __global__ void __launch_bounds__(256) cb_panel_df_kernel(Dev d, int k0, const i
       if (lane > j && i >= lane && i < kb) df_acc(a[q], df_neg(col[i]), col[lane]);
     }
   }
-  if (fail) {
-    if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
+  if (sh.fail) {
+    if (threadIdx.x == 0) *status = EDT_ENOTPD;
     return;
   }
-  float* L32 = d.L32 ? d.L32 + go : nullptr;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int i = warp + 8 * q;
     if (i < kb && lane <= i) {
       a[q] = df_norm(a[q]);
-      sL[i * LDP + lane] = a[q];
+      sh.L[i * LDP + lane] = a[q];
       A[size_t(k0 + i) * n + k0 + lane] = a[q];
       if (L32) L32[size_t(k0 + i) * n + k0 + lane] = a[q].x;
     }
   }
   if (threadIdx.x < kb) {
-    d.dinv[vo + k0 + threadIdx.x] = df_val(sInv[threadIdx.x]);
-    if (L32) d.dinv32[vo + k0 + threadIdx.x] = sInv[threadIdx.x].x;
+    dinv[k0 + threadIdx.x] = df_val(sh.inv[threadIdx.x]);
+    if (L32) dinv32[k0 + threadIdx.x] = sh.inv[threadIdx.x].x;
   }
   __syncthreads();
   // X = L_kk^-1: right-looking forward substitution on the identity, row k final at step k
@@ -645,11 +627,11 @@ __global__ void __launch_bounds__(256) cb_panel_df_kernel(Dev d, int k0, const i
 #pragma unroll
   for (int q = 0; q < 4; ++q) x[q] = make_float2(warp + 8 * q == lane ? 1.f : 0.f, 0.f);
   for (int k = 0; k < kb; ++k) {
-    float2* xr = sXr[k & 1];
+    float2* xr = sh.xr[k & 1];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (warp + 8 * q == k) {
-        if (lane <= k) x[q] = df_mul(df_norm(x[q]), sInv[k]);
+        if (lane <= k) x[q] = df_mul(df_norm(x[q]), sh.inv[k]);
         xr[lane] = lane <= k ? x[q] : make_float2(0.f, 0.f);
       }
     }
@@ -657,39 +639,100 @@ __global__ void __launch_bounds__(256) cb_panel_df_kernel(Dev d, int k0, const i
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = warp + 8 * q;
-      if (i > k && i < kb && lane <= k) df_acc(x[q], df_neg(sL[i * LDP + k]), xr[lane]);
+      if (i > k && i < kb && lane <= k) df_acc(x[q], df_neg(sh.L[i * LDP + k]), xr[lane]);
     }
   }
-  __syncthreads();                                   // every read of L_kk done
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int i = warp + 8 * q;
-    const float2 v = i < kb && lane <= i ? df_norm(x[q]) : make_float2(0.f, 0.f);
-    sL[i * LDP + lane] = v;                           // X_{i, lane}; zero outside the block
-    if (i < kb && lane < i) A[size_t(k0 + lane) * n + k0 + i] = v;
+    if (i < kb && lane < i) A[size_t(k0 + lane) * n + k0 + i] = df_norm(x[q]);
+  }
+}
+
+// Step 0 of every active subproblem: lam = alpha * trace added to the diagonal, then the first
+// diagonal block (later diagonal blocks are factored by the previous step's update launch).
+// trace_mode 0: trace from the diagonal of G; 1: from trace[m] (the producer's trace).
+template <bool VAR>
+__global__ void __launch_bounds__(256) cb_diag0_kernel(Dev d, const int* act, int trace_mode) {
+  __shared__ DiagScratch sh;
+  __shared__ double red[40];
+  const int m = act[blockIdx.x];
+  int n;
+  size_t go, vo;
+  sub_geom<VAR>(d, m, n, go, vo);
+  if (d.status[m] != EDT_OK) return;
+  float2* A = reinterpret_cast<float2*>(d.G) + go;
+  double tr;
+  if (trace_mode == 0) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += df_val(A[size_t(i) * n + i]);
+    tr = block_sum(t, red);
+  } else {
+    tr = d.trace[m];
+  }
+  const double lam = d.alpha * tr;
+  const float2 lamf = df_of(lam);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) A[size_t(i) * n + i] = df_add(A[size_t(i) * n + i], lamf);
+  __syncthreads();
+  if (threadIdx.x == 0) d.trace[m] = lam;
+  cb_diag_block(A, d.L32 ? d.L32 + go : nullptr, d.dinv + vo, d.dinv32 + vo, d.status + m, n, 0, sh);
+}
+
+// Panel rows of step k0: one CTA per 32-row chunk of an active subproblem's rows below the
+// diagonal block (cpre: prefix sums of the chunk counts over the active list).  x = a X^T,
+// x_j = sum_{l <= j} a_l X_jl, all outputs independent: the chunk sits transposed in shared
+// memory (rows read and written coalesced), warp h computes the outputs j = h + 8 q of the 32
+// rows (lane = row), X is read by broadcast.
+template <bool VAR>
+__global__ void __launch_bounds__(256) cb_prow_kernel(Dev d, int k0, const int* act, const long long* cpre,
+                                                      int nact) {
+  __shared__ float2 sA[NB * LDP], sX[NB * LDP];   // sA: [l][row]; sX: [j][l]
+  int lo = 0, hi = nact - 1;
+  const long long t = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cpre[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const int m = act[lo];
+  int n;
+  size_t go, vo;
+  sub_geom<VAR>(d, m, n, go, vo);
+  if (d.status[m] != EDT_OK) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kb = min(NB, n - k0);
+  const int r0 = k0 + kb + NB * int(t - cpre[lo]), nr = min(NB, n - r0);
+  const float2* Ac = reinterpret_cast<const float2*>(d.G) + go;
+  float2* A = reinterpret_cast<float2*>(d.G) + go;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = warp + 8 * q;                    // a warp: one row's 32 columns (coalesced)
+    sA[lane * LDP + r] = r < nr && lane < kb ? Ac[size_t(r0 + r) * n + k0 + lane] : make_float2(0.f, 0.f);
+    // X_{r, lane}: below the diagonal from the upper triangle (at (lane, r)), the diagonal
+    // from dinv
+    sX[r * LDP + lane] = r < kb && lane < r ? Ac[size_t(k0 + lane) * n + k0 + r]
+                         : (r < kb && lane == r ? df_of(d.dinv[vo + k0 + r]) : make_float2(0.f, 0.f));
   }
   __syncthreads();
-  for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {
-    float2* Ai = A + size_t(i) * n + k0;
-    float2 acc[NB];
+  float2 out[4];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) acc[j] = make_float2(0.f, 0.f);
+  for (int q = 0; q < 4; ++q) {
+    const int j = warp + 8 * q;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int l = 0; l <= j; ++l) df_acc(acc, sA[l * LDP + lane], sX[j * LDP + l]);
+    out[q] = df_norm(acc);
+  }
+  __syncthreads();
 #pragma unroll
-    for (int l = 0; l < NB; ++l) {
-      if (l < kb) {
-        const float2 al = Ai[l];
+  for (int q = 0; q < 4; ++q) sA[(warp + 8 * q) * LDP + lane] = out[q];
+  __syncthreads();
+  float* L32 = d.L32 ? d.L32 + go : nullptr;
 #pragma unroll
-        for (int j = l; j < NB; ++j) df_acc(acc[j], al, sL[j * LDP + l]);
-      }
-    }
-    float* Li = L32 ? L32 + size_t(i) * n + k0 : nullptr;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      if (j < kb) {
-        const float2 v = df_norm(acc[j]);
-        Ai[j] = v;
-        if (Li) Li[j] = v.x;
-      }
+  for (int q = 0; q < 4; ++q) {
+    const int r = warp + 8 * q;
+    if (r < nr && lane < kb) {
+      const float2 v = sA[lane * LDP + r];
+      A[size_t(r0 + r) * n + k0 + lane] = v;
+      if (L32) L32[size_t(r0 + r) * n + k0 + lane] = v.x;
     }
   }
 }
@@ -697,12 +740,19 @@ __global__ void __launch_bounds__(256) cb_panel_df_kernel(Dev d, int k0, const i
 // One 64 x 64 tile (bi, bj <= bi) of the trailing lower triangle: C -= P_bi P_bj^T, the
 // 32-term dot products accumulated in double-float.  Thread (ty, tx) owns rows ty + 16 u and
 // columns tx + 16 v (u, v < 4): interleaved, so the shared panel reads are conflict-free and
-// the global rows coalesced.
+// the global rows coalesced.  The CTA of tile (0, 0), whose rows and columns hold the next
+// step's diagonal block, factors that block after its own update (no other tile writes it).
 constexpr int ULD = UT + 1;
+union UpdateSmem {
+  struct { float2 I[NB * ULD], J[NB * ULD]; } p;  // transposed panel rows: [l][i]
+  DiagScratch dg;
+};
 template <bool VAR>
 __global__ void __launch_bounds__(256) cb_update_df_kernel(Dev d, int k0, const int* act,
                                                            const long long* tpre, int nact) {
-  __shared__ float2 sI[NB * ULD], sJ[NB * ULD];   // transposed panel rows: [l][i]
+  __shared__ UpdateSmem sm;
+  float2* sI = sm.p.I;
+  float2* sJ = sm.p.J;
   int lo = 0, hi = nact - 1;
   const long long t = blockIdx.x;
   while (lo < hi) {
@@ -767,6 +817,10 @@ __global__ void __launch_bounds__(256) cb_update_df_kernel(Dev d, int k0, const 
         *c = df_add(*c, df_neg(df_norm(acc[u][v])));
       }
     }
+  if (bi == 0) {                                   // the same in every thread of the CTA
+    __syncthreads();                               // the tile's writes visible, panels released
+    cb_diag_block(A, d.L32 ? d.L32 + go : nullptr, d.dinv + vo, d.dinv32 + vo, d.status + m, n, t0, sm.dg);
+  }
 }
 
 // x = (LL^T)^-1 b in double-float after the blocked factorisation (the inverse diagonal
@@ -856,16 +910,22 @@ cudaError_t launch_chol_var(const Dev& d, int nmax, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Blocked form: nstep panel + update launches, then the solves; d.G holds double-float entries
-// (a float2 in each 8-byte slot) and the solution is FP64.  act + k * nsub lists the
+// Blocked form: a step-0 diagonal launch, then per step a panel-row launch and an update
+// launch (which also factors the next diagonal blocks), then the solves; d.G holds double-float
+// entries (a float2 in each 8-byte slot) and the solution is FP64.  act + k * nsub lists the
 // subproblems active at step k (n > 32 k, rows > 0), nact[k] of them; tpre + k * (nsub + 1) the
-// prefix sums of their trailing tile counts (tpre[k][nact[k]] tiles in the update launch).
+// prefix sums of their trailing tile counts (ntile[k] tiles in the update launch), cpre the
+// same for their 32-row panel chunks (nchunk[k] in the panel-row launch).
 template <bool VAR>
 static cudaError_t blocked(const Dev& d, int nmax, int nstep, const int* act, const int* nact,
-                           const long long* tpre, const long long* ntile, int trace_mode, cudaStream_t s) {
+                           const long long* tpre, const long long* ntile, const long long* cpre,
+                           const long long* nchunk, int trace_mode, cudaStream_t s) {
+  if (nstep > 0 && nact[0] > 0) cb_diag0_kernel<VAR><<<nact[0], 256, 0, s>>>(d, act, trace_mode);
   for (int k = 0; k < nstep; ++k) {
     if (nact[k] == 0) continue;
-    cb_panel_df_kernel<VAR><<<nact[k], 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub, trace_mode);
+    if (nchunk[k] > 0)
+      cb_prow_kernel<VAR><<<unsigned(nchunk[k]), 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub,
+                                                              cpre + size_t(k) * (d.nsub + 1), nact[k]);
     if (ntile[k] > 0)
       cb_update_df_kernel<VAR><<<unsigned(ntile[k]), 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub,
                                                                   tpre + size_t(k) * (d.nsub + 1), nact[k]);
@@ -876,15 +936,23 @@ static cudaError_t blocked(const Dev& d, int nmax, int nstep, const int* act, co
 
 cudaError_t launch_chol_blocked(const Dev& d, bool var, int nmax, int nstep, const int* act_dev,
                                 const int* nact_host, const long long* tpre_dev,
-                                const long long* ntile_host, int trace_mode, cudaStream_t s) {
-  return var ? blocked<true>(d, nmax, nstep, act_dev, nact_host, tpre_dev, ntile_host, trace_mode, s)
-             : blocked<false>(d, nmax, nstep, act_dev, nact_host, tpre_dev, ntile_host, trace_mode, s);
+                                const long long* ntile_host, const long long* cpre_dev,
+                                const long long* nchunk_host, int trace_mode, cudaStream_t s) {
+  return var ? blocked<true>(d, nmax, nstep, act_dev, nact_host, tpre_dev, ntile_host, cpre_dev, nchunk_host,
+                             trace_mode, s)
+             : blocked<false>(d, nmax, nstep, act_dev, nact_host, tpre_dev, ntile_host, cpre_dev, nchunk_host,
+                              trace_mode, s);
 }
 
 int chol_blocked_tiles(int n, int k0) {
   const int t0 = k0 + (n - k0 < NB ? n - k0 : NB);
   const int T = (n - t0 + UT - 1) / UT;
   return T > 0 ? T * (T + 1) / 2 : 0;
+}
+
+int chol_blocked_chunks(int n, int k0) {
+  const int t0 = k0 + (n - k0 < NB ? n - k0 : NB);
+  return n > t0 ? (n - t0 + NB - 1) / NB : 0;
 }
 
 cudaError_t launch_refine_update_var(const Dev& d, int nmax, cudaStream_t s) {

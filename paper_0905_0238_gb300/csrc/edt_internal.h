@@ -293,8 +293,10 @@ cudaError_t launch_refine_update_var(const Dev& d, int nmax, cudaStream_t s);
 // n-unknown subproblem; chol_block_cols: the panel width.
 cudaError_t launch_chol_blocked(const Dev& d, bool var, int nmax, int nstep, const int* act_dev,
                                 const int* nact_host, const long long* tpre_dev,
-                                const long long* ntile_host, int trace_mode, cudaStream_t s);
+                                const long long* ntile_host, const long long* cpre_dev,
+                                const long long* nchunk_host, int trace_mode, cudaStream_t s);
 int chol_blocked_tiles(int n, int k0);
+int chol_blocked_chunks(int n, int k0);   // 32-row panel chunks below the diagonal block
 int chol_block_cols();
 
 // Solver variants (csrc/variants.cu): the truncated SVD (nz <= TSVD_MAX_NZ) and the

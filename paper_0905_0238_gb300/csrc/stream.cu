@@ -577,7 +577,7 @@ cudaError_t launch_stream_batch(const StBatch& b, int nmax, cudaStream_t s, cuda
   d.row_off = b.row_off;
   d.sub_n = b.sub_n; d.sub_goff = b.sub_goff; d.sub_voff = b.sub_voff; d.sub_order = b.sub_order;
   cudaError_t e = launch_chol_blocked(d, true, nmax, b.cb_nstep, b.cb_act, b.cb_nact_host, b.cb_tpre,
-                                      b.cb_ntile_host, 1, s);
+                                      b.cb_ntile_host, b.cb_cpre, b.cb_nchunk_host, 1, s);
   if (e != cudaSuccess) return e;
   mark(6);
   if (b.tot_rc > 0) {

@@ -55,7 +55,7 @@ size_t bytes_of(const ReqShape& r) {
   b += sizeof(double) + sizeof(int);                                 // trace, status
   b += size_t(r.kst) * (4 * r.nzt + 1) * sizeof(double);            // trace parts
   b += size_t((r.nrow + ST_REFINE_ROWS - 1) / ST_REFINE_ROWS) * r.nz * 2 * sizeof(double);  // residual partials
-  b += size_t(ST_MAX_NZ / 32) * (sizeof(int) + sizeof(long long));   // blocked-Cholesky step lists
+  b += size_t(ST_MAX_NZ / 32) * (sizeof(int) + 2 * sizeof(long long));   // blocked-Cholesky step lists
   return al(b, 64);
 }
 
@@ -271,6 +271,7 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   const int nstep = (nmax + nb_cols - 1) / nb_cols;
   const size_t o_cbact = take(sizeof(int) * size_t(nstep) * n);
   const size_t o_cbpre = take(sizeof(long long) * size_t(nstep) * (n + 1));
+  const size_t o_cbcpre = take(sizeof(long long) * size_t(nstep) * (n + 1));
   const size_t o_items = take(sizeof(StItem) * std::max<size_t>(all.size(), 1));
   const size_t o_cta = take(sizeof(int) * (ncta + 1));
   const size_t o_dbl = take(sizeof(double) * n_dbl);
@@ -372,21 +373,26 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   // blocked Cholesky step lists: requests with rows and more than 32 k unknowns, largest first
   int* cbact = reinterpret_cast<int*>(P + o_cbact);
   long long* cbpre = reinterpret_cast<long long*>(P + o_cbpre);
+  long long* cbcpre = reinterpret_cast<long long*>(P + o_cbcpre);
   std::vector<int> cb_nact(nstep, 0);
-  std::vector<long long> cb_ntile(nstep, 0);
+  std::vector<long long> cb_ntile(nstep, 0), cb_nchunk(nstep, 0);
   for (int k = 0; k < nstep; ++k) {
     int na = 0;
     long long* tp = cbpre + size_t(k) * (n + 1);
+    long long* cp = cbcpre + size_t(k) * (n + 1);
     tp[0] = 0;
+    cp[0] = 0;
     for (int ii = 0; ii < n; ++ii) {
       const int i = order[ii];
       if (sh[i].nrow == 0 || sh[i].nz <= k * nb_cols) continue;
       cbact[size_t(k) * n + na] = i;
       tp[na + 1] = tp[na] + chol_blocked_tiles(sh[i].nz, k * nb_cols);
+      cp[na + 1] = cp[na] + chol_blocked_chunks(sh[i].nz, k * nb_cols);
       ++na;
     }
     cb_nact[k] = na;
     cb_ntile[k] = tp[na];
+    cb_nchunk[k] = cp[na];
   }
   StItem* items = reinterpret_cast<StItem*>(P + o_items);
   int* cta0 = reinterpret_cast<int*>(P + o_cta);
@@ -440,10 +446,14 @@ int run_batch(edt_stream* s, const edt_sub1d* subs, int i0, int i1, double* vhat
   b.cb_nstep = nstep;
   b.cb_act = reinterpret_cast<const int*>(A + o_cbact);
   b.cb_tpre = reinterpret_cast<const long long*>(A + o_cbpre);
+  b.cb_cpre = reinterpret_cast<const long long*>(A + o_cbcpre);
   b.cb_nact_host = cb_nact.data();
   b.cb_ntile_host = cb_ntile.data();
+  b.cb_nchunk_host = cb_nchunk.data();
   int nlaunch = 1 + (b.tot_fk > 0) + (b.tot_eb > 0) + 2 * (b.tot_tw > 0) + (ncta > 0) + 1 + 2 * (b.tot_rc > 0) + 1;
-  for (int k = 0; k < nstep; ++k) nlaunch += (cb_nact[k] > 0) + (cb_ntile[k] > 0);
+  nlaunch += nstep > 0 && cb_nact[0] > 0;
+  for (int k = 0; k < nstep; ++k)
+    if (cb_nact[k] > 0) nlaunch += (cb_nchunk[k] > 0) + (cb_ntile[k] > 0);
 
   cudaError_t ce = cudaSuccess;
   if (s->profiling && s->slot[k ^ 1].batch >= 0)       // profiled batches run one at a time

@@ -87,6 +87,8 @@ struct StBatch {
   const long long* cb_tpre;
   const int* cb_nact_host;
   const long long* cb_ntile_host;
+  const long long* cb_cpre;      // [nstep][nreq + 1] prefix sums of the active requests' panel chunks
+  const long long* cb_nchunk_host;
 };
 
 constexpr int ST_NKERNEL = 8;
