@@ -753,11 +753,29 @@ __global__ void __launch_bounds__(256) cb_update_df_kernel(Dev d, int k0, const 
   __shared__ UpdateSmem sm;
   float2* sI = sm.p.I;
   float2* sJ = sm.p.J;
-  int lo = 0, hi = nact - 1;
+  // CTAs 0 .. nt0 - 1 take the tiles (0, 0) of the nt0 subproblems that have tiles (the active
+  // list is ordered by size, so those come first), so that the diagonal-block factorisations
+  // they carry start with the launch; the other tiles follow, subproblem by subproblem.
+  int lo = 0, hi = nact;
+  while (lo < hi) {                                // nt0: the first subproblem without tiles
+    const int mid = (lo + hi) >> 1;
+    if (tpre[mid + 1] > tpre[mid]) lo = mid + 1; else hi = mid;
+  }
+  const int nt0 = lo;
   const long long t = blockIdx.x;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tpre[mid] <= t) lo = mid; else hi = mid - 1;
+  int e;
+  if (t < nt0) {
+    lo = int(t);
+    e = 0;
+  } else {
+    const long long u = t - nt0;                   // among the tiles after each first one
+    lo = 0;
+    hi = nt0 - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tpre[mid] - mid <= u) lo = mid; else hi = mid - 1;
+    }
+    e = int(u - (tpre[lo] - lo)) + 1;
   }
   const int m = act[lo];
   int n;
@@ -765,7 +783,6 @@ __global__ void __launch_bounds__(256) cb_update_df_kernel(Dev d, int k0, const 
   sub_geom<VAR>(d, m, n, go, vo);
   if (d.status[m] != EDT_OK) return;
   const int kb = min(NB, n - k0), t0 = k0 + kb;
-  const int e = int(t - tpre[lo]);
   int bi = int((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
   while (bi * (bi + 1) / 2 > e) --bi;
   while ((bi + 1) * (bi + 2) / 2 <= e) ++bi;
