@@ -17,6 +17,7 @@
 #include "edt_internal.h"
 #include "cplx.cuh"
 #include "dfloat.cuh"
+#include "blksolve.cuh"
 
 namespace edt {
 
@@ -386,85 +387,6 @@ __device__ void chol_solve32_2rhs(const float* A, const float* dinv, int n, floa
   }
 }
 
-// Solve L L^T y = sb in double-float for two right-hand sides (sb[i][0..1]).  L is lower,
-// double-float in A (ld n), each 32 x 32 diagonal block holding its inverse X = L_kk^-1 in its
-// strict upper triangle (X_il at (l, i), written by the blocked panel step) with the diagonal
-// 1 / L_ii in dinv: every block solve is a parallel matrix-vector product (warp k: right-hand side k,
-// lane: row), the off-diagonal blocks are applied by thread-per-row (forward) or coalesced
-// column (backward) sweeps.  sX: [NB][LDP] shared scratch.
-__device__ void chol_solve_df_2rhs(const float2* A, const double* dinv, int n, float2* sb, float2* sX) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nblk = (n + NB - 1) / NB;
-  auto load_x = [&](int k0, int kb) {          // sX[i * LDP + l] = X_il (lower, with the diagonal)
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      const int i = e / NB, l = e - i * NB;
-      float2 v = make_float2(0.f, 0.f);
-      if (i < kb && l < kb) {
-        if (l < i) v = A[size_t(k0 + l) * n + k0 + i];
-        else if (l == i) v = df_of(dinv[k0 + i]);
-      }
-      sX[i * LDP + l] = v;
-    }
-  };
-  for (int bk = 0; bk < nblk; ++bk) {                       // forward: L y = b
-    const int k0 = bk * NB, kb = min(NB, n - k0);
-    load_x(k0, kb);
-    __syncthreads();
-    float2 y = make_float2(0.f, 0.f);
-    if (warp < 2 && lane < kb) {                            // y_blk = X b_blk
-      for (int l = 0; l <= lane; ++l) df_acc(y, sX[lane * LDP + l], sb[(k0 + l) * 2 + warp]);
-    }
-    __syncthreads();
-    if (warp < 2 && lane < kb) sb[(k0 + lane) * 2 + warp] = df_norm(y);
-    __syncthreads();
-    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {   // b_i -= L[i][blk] . y
-      float2 s0 = sb[i * 2], s1 = sb[i * 2 + 1];
-      const float2* Ai = A + size_t(i) * n + k0;
-      float2 av[NB];                                                  // loads in flight together
-#pragma unroll
-      for (int l = 0; l < NB; ++l) av[l] = l < kb ? Ai[l] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int l = 0; l < NB; ++l) {
-        if (l < kb) {
-          const float2 a = df_neg(av[l]);
-          df_acc(s0, a, sb[(k0 + l) * 2]);
-          df_acc(s1, a, sb[(k0 + l) * 2 + 1]);
-        }
-      }
-      sb[i * 2] = df_norm(s0); sb[i * 2 + 1] = df_norm(s1);
-    }
-    __syncthreads();
-  }
-  for (int bk = nblk - 1; bk >= 0; --bk) {                  // backward: L^T x = y
-    const int k0 = bk * NB, kb = min(NB, n - k0);
-    load_x(k0, kb);
-    __syncthreads();
-    float2 x = make_float2(0.f, 0.f);
-    if (warp < 2 && lane < kb) {                            // x_blk = X^T y_blk
-      for (int i = lane; i < kb; ++i) df_acc(x, sX[i * LDP + lane], sb[(k0 + i) * 2 + warp]);
-    }
-    __syncthreads();
-    if (warp < 2 && lane < kb) sb[(k0 + lane) * 2 + warp] = df_norm(x);
-    __syncthreads();
-    for (int i = threadIdx.x; i < k0; i += blockDim.x) {    // y_i -= sum_l L[k0+l][i] x_l
-      float2 s0 = sb[i * 2], s1 = sb[i * 2 + 1];
-      float2 av[NB];
-#pragma unroll
-      for (int l = 0; l < NB; ++l) av[l] = l < kb ? A[size_t(k0 + l) * n + i] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int l = 0; l < NB; ++l) {
-        if (l < kb) {
-          const float2 a = df_neg(av[l]);
-          df_acc(s0, a, sb[(k0 + l) * 2]);
-          df_acc(s1, a, sb[(k0 + l) * 2 + 1]);
-        }
-      }
-      sb[i * 2] = df_norm(s0); sb[i * 2 + 1] = df_norm(s1);
-    }
-    __syncthreads();
-  }
-}
-
 // Refinement update with the FP32 factor: x += (LL^T)^-1 (r - lam x); r - lam x in FP64,
 // rounded to FP32 for the solve, the correction added to x in FP64.
 template <bool VAR>
@@ -489,6 +411,37 @@ __global__ void __launch_bounds__(256) chol_refine32_kernel(Dev d) {
   bool bad = false;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
     const double v = xo[i] + double(sb32[i]);
+    xo[i] = v;
+    if (!isfinite(v)) bad = true;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0 && bad) d.status[m] = EDT_ENONFINITE;
+}
+
+// The same refinement update after a double-float factorisation, whose FP32 copy also holds
+// each diagonal block's inverse in the block's strict upper triangle: coalesced block
+// substitutions (see blk_solve_2rhs).
+template <bool VAR>
+__global__ void __launch_bounds__(256) chol_refine32x_kernel(Dev d) {
+  extern __shared__ __align__(16) float sbx[];    // [2 n] right-hand sides, scratch
+  const int m = blockIdx.x;
+  const int n = VAR ? d.sub_n[m] : d.nz;
+  const size_t go = VAR ? size_t(d.sub_goff[m]) : size_t(m) * n * n;
+  const size_t vo = VAR ? size_t(d.sub_voff[m]) : size_t(m) * n;
+  double* xo = d.x + vo * 2;
+  if (d.row_off[m + 1] == d.row_off[m] || d.status[m] != EDT_OK) {
+    if (d.status[m] != EDT_OK)
+      for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
+    return;
+  }
+  const double lam = d.trace[m];
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
+    sbx[i] = float(d.r[vo * 2 + i] - lam * xo[i]);
+  __syncthreads();
+  blk_solve_2rhs<F32Arith, 256>(d.L32 + go, d.dinv32 + vo, n, sbx, sbx + 2 * n);
+  bool bad = false;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+    const double v = xo[i] + double(sbx[i]);
     xo[i] = v;
     if (!isfinite(v)) bad = true;
   }
@@ -645,7 +598,11 @@ __device__ void cb_diag_block(float2* A, float* L32, double* dinv, float* dinv32
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int i = warp + 8 * q;
-    if (i < kb && lane < i) A[size_t(k0 + lane) * n + k0 + i] = df_norm(x[q]);
+    if (i < kb && lane < i) {
+      const float2 v = df_norm(x[q]);
+      A[size_t(k0 + lane) * n + k0 + i] = v;
+      if (L32) L32[size_t(k0 + lane) * n + k0 + i] = v.x;   // X in the FP32 copy too
+    }
   }
 }
 
@@ -841,11 +798,10 @@ __global__ void __launch_bounds__(256) cb_update_df_kernel(Dev d, int k0, const 
 }
 
 // x = (LL^T)^-1 b in double-float after the blocked factorisation (the inverse diagonal
-// blocks in the upper triangles); b and x FP64.
+// blocks in the upper triangles; see blk_solve_2rhs); b and x FP64.
 template <bool VAR>
 __global__ void __launch_bounds__(256) chol_solve_df_kernel(Dev d) {
-  extern __shared__ __align__(16) float2 sbd[];
-  __shared__ float2 sX[NB * LDP];
+  extern __shared__ __align__(16) float2 sbd[];   // [2 n] right-hand sides, [n] 1 / L_ii, scratch
   const int m = blockIdx.x;
   int n;
   size_t go, vo;
@@ -855,9 +811,11 @@ __global__ void __launch_bounds__(256) chol_solve_df_kernel(Dev d) {
     for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
     return;
   }
+  float2* sInv = sbd + 2 * n;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) sbd[i] = df_of(d.b[vo * 2 + i]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sInv[i] = df_of(d.dinv[vo + i]);
   __syncthreads();
-  chol_solve_df_2rhs(reinterpret_cast<const float2*>(d.G) + go, d.dinv + vo, n, sbd, sX);
+  blk_solve_2rhs<DfArith, 256>(reinterpret_cast<const float2*>(d.G) + go, sInv, n, sbd, sInv + n);
   bool bad = false;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
     const double v = df_val(sbd[i]);
@@ -908,7 +866,10 @@ cudaError_t launch_chol_resolve(const Dev& d, cudaStream_t s) {
 }
 
 cudaError_t launch_refine_update(const Dev& d, cudaStream_t s) {
-  if (d.L32) chol_refine32_kernel<false><<<d.nsub, 256, size_t(2 * d.nz) * sizeof(float), s>>>(d);
+  if (d.L32 && d.chol_df)
+    chol_refine32x_kernel<false><<<d.nsub, 256, size_t(2 * d.nz + blk_solve_scratch<F32Arith, 256>()) * sizeof(float),
+                                   s>>>(d);
+  else if (d.L32) chol_refine32_kernel<false><<<d.nsub, 256, size_t(2 * d.nz) * sizeof(float), s>>>(d);
   else chol_solve_kernel<false><<<d.nsub, 256, size_t(2 * d.nz) * sizeof(double), s>>>(d, 1);
   return cudaGetLastError();
 }
@@ -947,7 +908,8 @@ static cudaError_t blocked(const Dev& d, int nmax, int nstep, const int* act, co
       cb_update_df_kernel<VAR><<<unsigned(ntile[k]), 256, 0, s>>>(d, k * NB, act + size_t(k) * d.nsub,
                                                                   tpre + size_t(k) * (d.nsub + 1), nact[k]);
   }
-  chol_solve_df_kernel<VAR><<<d.nsub, 256, size_t(2 * nmax) * sizeof(float2), s>>>(d);
+  chol_solve_df_kernel<VAR><<<d.nsub, 256, size_t(3 * nmax + blk_solve_scratch<DfArith, 256>()) * sizeof(float2),
+                              s>>>(d);
   return cudaGetLastError();
 }
 
@@ -973,7 +935,8 @@ int chol_blocked_chunks(int n, int k0) {
 }
 
 cudaError_t launch_refine_update_var(const Dev& d, int nmax, cudaStream_t s) {
-  chol_refine32_kernel<true><<<d.nsub, 256, size_t(2 * nmax) * sizeof(float), s>>>(d);
+  chol_refine32x_kernel<true><<<d.nsub, 256, size_t(2 * nmax + blk_solve_scratch<F32Arith, 256>()) * sizeof(float),
+                                s>>>(d);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@
 // A non-positive or non-finite pivot marks the subproblem EDT_ENOTPD and zeroes its solution.
 #include "edt_internal.h"
 #include "dfloat.cuh"
+#include "blksolve.cuh"
 
 namespace edt {
 
@@ -37,92 +38,6 @@ namespace {
 
 constexpr int FB = 32, FLD = FB + 1, FTHREADS = 256;
 constexpr int UT = 64, ULD = UT + 1;   // update tile and its padded shared row
-
-// Solve L L^T y = sb for two right-hand sides (sb[i][0..1], double-float).  L is lower, double-
-// float in A (ld n); each 32 x 32 diagonal block also holds its inverse X = L_kk^-1 in its strict
-// upper triangle (X_il at (l, i)) with the diagonal 1 / L_ii in sInv, so every block solve is a
-// parallel matrix-vector product (warp k: right-hand side k, lane: row) instead of a sequential
-// chain, and the off-diagonal blocks are applied by thread-per-row (forward) or coalesced
-// column (backward) sweeps.  sX: [FB][FLD] shared scratch.
-__device__ void solve_df_2rhs(const float2* A, const float2* sInv, int n, float2* sb, float2* sX) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nblk = (n + FB - 1) / FB;
-  auto load_x = [&](int k0, int kb) {          // sX[i * FLD + l] = X_il (lower, with the diagonal)
-    constexpr int Q = FB * FB / FTHREADS;
-    float2 v[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int e = threadIdx.x + FTHREADS * q, i = e / FB, l = e - i * FB;
-      v[q] = make_float2(0.f, 0.f);
-      if (i < kb && l < kb) {
-        if (l < i) v[q] = A[size_t(k0 + l) * n + k0 + i];
-        else if (l == i) v[q] = sInv[k0 + i];
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int e = threadIdx.x + FTHREADS * q, i = e / FB, l = e - i * FB;
-      sX[i * FLD + l] = v[q];
-    }
-  };
-  for (int bk = 0; bk < nblk; ++bk) {                       // forward: L y = b
-    const int k0 = bk * FB, kb = min(FB, n - k0);
-    load_x(k0, kb);
-    __syncthreads();
-    float2 y = make_float2(0.f, 0.f);
-    if (warp < 2 && lane < kb) {                            // y_blk = X b_blk
-      for (int l = 0; l <= lane; ++l) df_acc(y, sX[lane * FLD + l], sb[(k0 + l) * 2 + warp]);
-    }
-    __syncthreads();
-    if (warp < 2 && lane < kb) sb[(k0 + lane) * 2 + warp] = df_norm(y);
-    __syncthreads();
-    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {   // b_i -= L[i][blk] . y
-      float2 s0 = sb[i * 2], s1 = sb[i * 2 + 1];
-      const float2* Ai = A + size_t(i) * n + k0;
-      float2 av[FB];                                                  // loads in flight together
-#pragma unroll
-      for (int l = 0; l < FB; ++l) av[l] = l < kb ? Ai[l] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int l = 0; l < FB; ++l) {
-        if (l < kb) {
-          const float2 a = df_neg(av[l]);
-          df_acc(s0, a, sb[(k0 + l) * 2]);
-          df_acc(s1, a, sb[(k0 + l) * 2 + 1]);
-        }
-      }
-      sb[i * 2] = df_norm(s0); sb[i * 2 + 1] = df_norm(s1);
-    }
-    __syncthreads();
-  }
-  for (int bk = nblk - 1; bk >= 0; --bk) {                  // backward: L^T x = y
-    const int k0 = bk * FB, kb = min(FB, n - k0);
-    load_x(k0, kb);
-    __syncthreads();
-    float2 x = make_float2(0.f, 0.f);
-    if (warp < 2 && lane < kb) {                            // x_blk = X^T y_blk
-      for (int i = lane; i < kb; ++i) df_acc(x, sX[i * FLD + lane], sb[(k0 + i) * 2 + warp]);
-    }
-    __syncthreads();
-    if (warp < 2 && lane < kb) sb[(k0 + lane) * 2 + warp] = df_norm(x);
-    __syncthreads();
-    for (int i = threadIdx.x; i < k0; i += blockDim.x) {    // y_i -= sum_l L[k0+l][i] x_l
-      float2 s0 = sb[i * 2], s1 = sb[i * 2 + 1];
-      float2 av[FB];
-#pragma unroll
-      for (int l = 0; l < FB; ++l) av[l] = l < kb ? A[size_t(k0 + l) * n + i] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int l = 0; l < FB; ++l) {
-        if (l < kb) {
-          const float2 a = df_neg(av[l]);
-          df_acc(s0, a, sb[(k0 + l) * 2]);
-          df_acc(s1, a, sb[(k0 + l) * 2 + 1]);
-        }
-      }
-      sb[i * 2] = df_norm(s0); sb[i * 2 + 1] = df_norm(s1);
-    }
-    __syncthreads();
-  }
-}
 
 __device__ __forceinline__ bool has_rows(const Dev& d, int m) { return d.row_off[m + 1] > d.row_off[m]; }
 
@@ -188,7 +103,11 @@ __global__ void __launch_bounds__(1024) cdf_diag_kernel(Dev d, int k0) {
     __syncthreads();
     if (i > k && i < kb && l <= k) df_acc(x, df_neg(sLf[i * FLD + k]), xr[l]);
   }
-  if (i < kb && l < i) A[size_t(k0 + l) * n + k0 + i] = df_norm(x);
+  if (i < kb && l < i) {
+    const float2 v = df_norm(x);
+    A[size_t(k0 + l) * n + k0 + i] = v;
+    if (d.L32) d.L32[size_t(m) * n * n + size_t(k0 + l) * n + k0 + i] = v.x;   // X in the FP32 copy too
+  }
   if (threadIdx.x == 0) {
     if (k0 == 0) { d.trace[m] = d.alpha * d.trace[m]; d.status[m] = EDT_OK; }
   }
@@ -327,7 +246,7 @@ __global__ void __launch_bounds__(FTHREADS) cdf_final_kernel(Dev d) {
   const size_t go = size_t(m) * n * n, vo = size_t(m) * n;
   float2* sb = reinterpret_cast<float2*>(smraw);            // [n][2]
   float2* sInv = sb + 2 * n;                                // [n]
-  float2* sL = sInv + n;                                    // [FB][FLD]
+  float2* sL = sInv + n;                                    // solve scratch
   double* xo = d.x + vo * 2;
   if (!has_rows(d, m)) {
     for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = 0.0;
@@ -347,7 +266,7 @@ __global__ void __launch_bounds__(FTHREADS) cdf_final_kernel(Dev d) {
     if (L32) d.dinv32[vo + i] = float(inv);
   }
   __syncthreads();
-  solve_df_2rhs(A, sInv, n, sb, sL);
+  blk_solve_2rhs<DfArith, FTHREADS>(A, sInv, n, sb, sL);
   bool bad = false;
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
     const double v = df_val(sb[i]);
@@ -376,7 +295,7 @@ __global__ void __launch_bounds__(FTHREADS) cdf_resolve_kernel(Dev d) {
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) sb[i] = df_of(d.b[vo * 2 + i]);
   for (int i = threadIdx.x; i < n; i += blockDim.x) sInv[i] = df_of(d.dinv[vo + i]);
   __syncthreads();
-  solve_df_2rhs(A, sInv, n, sb, sL);
+  blk_solve_2rhs<DfArith, FTHREADS>(A, sInv, n, sb, sL);
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) xo[i] = df_val(sb[i]);
 }
 
@@ -391,7 +310,7 @@ __global__ void cdf_export_kernel(Dev d, double* out) {
   }
 }
 
-size_t cdf_final_smem(int n) { return size_t(3 * n + FB * FLD) * sizeof(float2); }
+size_t cdf_final_smem(int n) { return size_t(3 * n + blk_solve_scratch<DfArith, FTHREADS>()) * sizeof(float2); }
 
 }  // namespace
 
