@@ -242,7 +242,8 @@ int edt_set_graph(edt_ctx* ctx, int on);
 
 /* Autotuner: for each tunable launch shape in turn, time `reps` (>= 1) edt_invert calls on
  * the caller's data with every candidate (the others at their current best) and keep the
- * fastest (coordinate descent, CUDA events on `stream`, minimum over the reps).  The tuned
+ * fastest (coordinate descent, CUDA events on `stream`; one warm-up call, then the reps back
+ * to back, their mean time per call).  The tuned
  * shapes stay with the context; V_dev receives the last inversion.  Synchronises `stream`.
  * Must not run while the stream is being captured. */
 int edt_autotune(edt_ctx* ctx, const void* D_dev, int D_dtype, void* V_dev, int V_dtype,

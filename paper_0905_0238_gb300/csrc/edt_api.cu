@@ -1182,19 +1182,21 @@ int edt_autotune(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, v
   cudaEvent_t e0, e1;
   EDT_TRY(cudaEventCreate(&e0));
   EDT_TRY(cudaEventCreate(&e1));
-  auto time_invert = [&](double* best) -> int {
-    *best = 1e300;
-    for (int r = 0; r < reps + 1; ++r) {             // the first call warms up
-      cudaEventRecord(e0, s);
-      const int rc = run_invert(c, D, D_dtype, V, V_dtype, s);
-      if (rc != EDT_OK) return rc;
-      cudaEventRecord(e1, s);
-      cudaError_t e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) return cuda_fail(e);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (r > 0) *best = std::min(*best, double(ms));
-    }
+  // steady-state time of one inversion: a warm-up call, then reps calls back to back between
+  // two events (what a caller inverting line after line sees; isolated calls each start on an
+  // idle device and rank some launch shapes differently)
+  auto time_invert = [&](double* per_call) -> int {
+    int rc = run_invert(c, D, D_dtype, V, V_dtype, s);
+    if (rc != EDT_OK) return rc;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r)
+      if ((rc = run_invert(c, D, D_dtype, V, V_dtype, s)) != EDT_OK) return rc;
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *per_call = double(ms) / reps;
     return EDT_OK;
   };
   edt_tuning cur;
