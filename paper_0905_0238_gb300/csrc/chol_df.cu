@@ -171,13 +171,32 @@ __global__ void __launch_bounds__(128) cdf_panel_kernel(Dev d, int k0) {
 // step's panel.  Thread (ty, tx) owns rows ty + 16 u and columns tx + 16 v (u, v < 4):
 // interleaved, so the shared panel reads are conflict-free and the global rows coalesced.
 // part 0: every tile; 1: the first tile column J = 0 (it holds the next step's diagonal block
-// and panel); 2: the tiles J >= 1.
+// and panel); 2: the tiles J >= 1.  Parts 0 and 1 also factor the next step's diagonal block:
+// the CTA of tile (0, 0), which holds that block and is its only writer, does so after its own
+// update, and those CTAs come first in the launch (1D grid: CTA t < nsub takes tile 0 of
+// subproblem t, the others follow) so that the factorisations overlap the remaining tiles.
+union UpdateSmem {
+  struct { float2 I[FB * ULD], J[FB * ULD]; } p;  // transposed panel rows: [l][i]
+  DfDiagScratch dg;
+};
 __global__ void __launch_bounds__(256) cdf_update_kernel(Dev d, int k0, int part) {
-  __shared__ float2 sI[FB * ULD], sJ[FB * ULD];   // transposed panel rows: [l][i]
-  const int m = blockIdx.y, n = d.nz;
+  __shared__ UpdateSmem sm;
+  float2* sI = sm.p.I;
+  float2* sJ = sm.p.J;
+  const int n = d.nz;
+  int m, pt;
+  if (part == 2) {
+    m = blockIdx.y;
+    pt = blockIdx.x;
+  } else if (int(blockIdx.x) < d.nsub) {
+    m = blockIdx.x;
+    pt = 0;
+  } else {
+    m = (blockIdx.x - d.nsub) % d.nsub;
+    pt = 1 + (blockIdx.x - d.nsub) / d.nsub;
+  }
   if (!has_rows(d, m) || d.status[m] != EDT_OK) return;
   const int t0 = k0 + FB;
-  const int pt = blockIdx.x;
   int I, J;
   if (part == 1) {
     I = pt; J = 0;
@@ -235,6 +254,11 @@ __global__ void __launch_bounds__(256) cdf_update_kernel(Dev d, int k0, int part
         *a = df_add(*a, df_neg(df_norm(acc[u][v])));
       }
     }
+  if (part != 2 && pt == 0) {                      // the same in every thread of the CTA
+    __syncthreads();                               // the tile's writes visible, panels released
+    df_diag_block(A, d.L32 ? d.L32 + size_t(m) * n * n : nullptr, d.dinv + size_t(m) * n,
+                  d.dinv32 ? d.dinv32 + size_t(m) * n : nullptr, d.status + m, n, t0, sm.dg);
+  }
 }
 
 // Both substitutions and the solution; the factor stays in double-float (its readers take
@@ -353,21 +377,22 @@ cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s, con
   // the next diagonal block and panel (which read only that column); the update of the tiles
   // J >= 1 runs on the side stream meanwhile.  Step k + 1's updates wait for it.
   cudaEvent_t prev_rest = nullptr;
-  for (int step = 0, k0 = 0; k0 < n; ++step, k0 += FB) {
-    cdf_diag_kernel<<<d.nsub, 1024, 0, s>>>(d, k0);
-    if (k0 + FB >= n) break;
+  // The diagonal block of step 0 has a launch of its own; every later one is factored by the
+  // previous step's update (parts 0 and 1) as soon as its tile is final.
+  cdf_diag_kernel<<<d.nsub, 1024, 0, s>>>(d, 0);
+  for (int step = 0, k0 = 0; k0 + FB < n; ++step, k0 += FB) {
     const int t = n - k0 - FB, nt = (t + UT - 1) / UT;
     cdf_panel_kernel<<<dim3((t + 31) / 32, d.nsub), 128, 0, s>>>(d, k0);
     if (!ahead || nt < 2) {
       if (prev_rest && (e = cudaStreamWaitEvent(s, prev_rest, 0)) != cudaSuccess) return e;
       prev_rest = nullptr;
-      cdf_update_kernel<<<dim3(nt * (nt + 1) / 2, d.nsub), 256, 0, s>>>(d, k0, 0);
+      cdf_update_kernel<<<unsigned(nt * (nt + 1) / 2 * d.nsub), 256, 0, s>>>(d, k0, 0);
       continue;
     }
     cudaEvent_t ev_panel = la->ev[2 * step], ev_rest = la->ev[2 * step + 1];
     if ((e = cudaEventRecord(ev_panel, s)) != cudaSuccess) return e;
     if (prev_rest && (e = cudaStreamWaitEvent(s, prev_rest, 0)) != cudaSuccess) return e;
-    cdf_update_kernel<<<dim3(nt, d.nsub), 256, 0, s>>>(d, k0, 1);
+    cdf_update_kernel<<<unsigned(nt * d.nsub), 256, 0, s>>>(d, k0, 1);
     if ((e = cudaStreamWaitEvent(la->side, ev_panel, 0)) != cudaSuccess) return e;
     cdf_update_kernel<<<dim3(nt * (nt - 1) / 2, d.nsub), 256, 0, la->side>>>(d, k0, 2);
     if ((e = cudaEventRecord(ev_rest, la->side)) != cudaSuccess) return e;
