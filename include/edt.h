@@ -87,8 +87,10 @@ extern "C" {
 #define EDT_FP64   0   /* every stage in IEEE double                                          */
 #define EDT_MIXED  1   /* FP32 transforms, tensor-core Gram from 16-bit hi/lo operand pairs
                           (FP16 with power-of-two scales on the line geometry, BF16 on the
-                          window geometry) with FP32 accumulation, FP64 Cholesky and
-                          iterative refinement with an FP64-summed residual               */
+                          window geometry) with FP32 accumulation, a Cholesky of FP64-class
+                          accuracy (double-float on the FP32 pipes by default, native FP64
+                          with chol_df = 2) and iterative refinement with an FP64-summed
+                          residual                                                         */
 
 #define EDT_GEOM_LINE    0   /* 2D line, every source/receiver pair recorded (default)  */
 #define EDT_GEOM_WINDOW  1   /* finite half-offset window on an nx x ny midpoint grid   */
@@ -488,13 +490,13 @@ int edt_read_profile(edt_ctx* ctx, double* ms, const char** names, int max_stage
  * z_j = z0 + (j + 1/2) dz, g the Green's function of the layered reference (the depth march of
  * edt_green); the result is Vhat(z_j) = x_+(z_j) + i x_-(z_j).  Arithmetic follows EDT_MIXED:
  * FP32 Green's table (FP64 vertical wavenumbers), split BF16 tensor-core Gram with FP32
- * accumulation, FP64 Cholesky, one refinement step (FP32 residual accumulated in FP64, FP32
- * correction solve).
+ * accumulation, double-float Cholesky (FP64-class, on the FP32 pipes), one refinement step
+ * (FP32 residual accumulated in FP64, FP32 correction solve).
  *
  * Requests are admitted by device memory: the caller's workspace is split into two arenas, a
  * submitted list is cut in order into batches whose summed edt_stream_request_bytes fit one
  * arena (and at most max_batch requests), and each batch runs as eight stages whose launches
- * cover all its requests (the FP64 Cholesky as a panel and a tile-update launch per 32-column
+ * cover all its requests (the Cholesky as a panel-row and a tile-update launch per 32-column
  * step, so that a large factorisation spreads over many SMs).  The two arenas have a CUDA stream each, so one batch's launches
  * overlap the next batch's copies and launches while the host packs the batch after into
  * pinned staging.  All state stays on the device until the results of a batch are copied

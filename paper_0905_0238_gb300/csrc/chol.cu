@@ -1,19 +1,25 @@
-// Damped normal-equation solves, FP64: (G + lam I) x_+- = b_+-, lam = alpha * trace(G).
+// Damped normal-equation solves (G + lam I) x_+- = b_+-, lam = alpha * trace(G): the native
+// FP64 factorisation, the per-request blocked factorisation of the streaming batches, and the
+// refinement's FP32 correction solves.
 //
 // Zeroth-order Tikhonov damping is the regularisation the paper's Discussion proposes in
-// place of its truncated SVD.  One block per midpoint wavenumber m (two resident per SM,
-// so one problem's serial panel steps overlap another's trailing update on the FP64
-// pipe): blocked right-looking Cholesky with 32-column panels, in place on the
-// L2-resident matrix -- the diagonal block factored by one warp in shared memory, the
-// panel by row-per-thread triangular solves, the trailing lower triangle by 4x4 FP64
-// register tiles.  Then forward and backward substitution for the two right-hand sides
-// with each 32x32 diagonal block staged in shared memory and solved by one warp with
-// shuffles, and the off-diagonal updates by thread-per-row dot products (forward) or
-// coalesced column sweeps (backward), two FP64 FMAs per matrix element and no reductions.  A non-positive or non-finite pivot marks the
-// subproblem EDT_ENOTPD and zeroes its solution.
+// place of its truncated SVD.
 //
-// chol_solve applied to r - lam x, with r = Ahat^T (dhat - Ahat x) accumulated by the
-// refinement kernel, gives one step of iterative refinement on the normal equations.
+// Native FP64 (the FP64 path and chol_df = 2): one block per midpoint wavenumber m (two
+// resident per SM, so one problem's serial panel steps overlap another's trailing update on the
+// FP64 pipe): blocked right-looking Cholesky with 32-column panels, in place on the L2-resident
+// matrix -- the diagonal block factored by one warp in shared memory, the panel by
+// row-per-thread triangular solves, the trailing lower triangle by 4x4 FP64 register tiles.
+// Then forward and backward substitution for the two right-hand sides with each 32x32 diagonal
+// block staged in shared memory and solved by one warp with shuffles, and the off-diagonal
+// updates by thread-per-row dot products (forward) or coalesced column sweeps (backward).
+//
+// Streaming batches (per-request sizes): the blocked factorisation in double-float over many
+// launches, every launch covering all active requests (see the blocked-Cholesky section).
+//
+// A non-positive or non-finite pivot marks the subproblem EDT_ENOTPD and zeroes its solution.
+// The solve applied to r - lam x, with r = Ahat^T (dhat - Ahat x) accumulated by the refinement
+// kernel, gives one step of iterative refinement on the normal equations.
 #include "edt_internal.h"
 #include "cplx.cuh"
 #include "dfloat.cuh"

@@ -9,7 +9,7 @@
 
 namespace edt {
 
-constexpr int ST_MAX_NZ = 512;          // unknowns per request (FP64 panel of the Cholesky)
+constexpr int ST_MAX_NZ = 512;          // unknowns per request (shared memory of the substitutions)
 constexpr int ST_MAX_LAYERS = 64;       // layers of a request's reference
 constexpr int ST_TILE = 128;            // depth rows per tensor-core tile
 constexpr int ST_DROWS = 16;            // data rows after the depth rows (d_+, d_-, zeros)

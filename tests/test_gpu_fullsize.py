@@ -1,7 +1,7 @@
 """Parity at the full production size, in the launch configuration bench.py times.
 
 The 512 x 512 x 128-frequency x 256-depth workload (20 layers, alpha = 1e-2) is inverted
-on the GPU by the mixed path (split BF16x3 tensor-core Gram, FP64 Cholesky, one refinement
+on the GPU by the mixed path (split tensor-core Gram, FP64-class Cholesky, one refinement
 step, reciprocal folding) and by the plain FP64 path; the FP64 oracle solves a sample of
 midpoint wavenumbers (it cannot afford all 257 split systems in a test).  Sampled Vhat are
 compared one by one: 1e-5 relative for the mixed path, 1e-10 for the FP64 path.  Data are

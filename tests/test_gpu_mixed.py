@@ -1,4 +1,4 @@
-"""GPU parity of the mixed-precision path (tcgen05 Gram + FP64 Cholesky + refinement).
+"""GPU parity of the mixed-precision path (tcgen05 Gram + FP64-class Cholesky + refinement).
 
 The tensor-core normal matrices are compared with Ahat^T Ahat formed in FP64 from the
 oracle's own kernel rows (a matmul in the test; the oracle itself never forms a Gram);

@@ -1,7 +1,7 @@
 """GPU parity of the finite-aperture (window) geometry against the FP64 oracle (oracle/edt3d.py).
 
 The mixed path (FP32 kernel-row assembly and data transforms, split BF16x3 tensor-core
-Gram, FP64 Cholesky, one refinement step) is compared with the oracle's QR solution on
+Gram, FP64-class Cholesky, one refinement step) is compared with the oracle's QR solution on
 the same seeded inputs: V and Vhat to 1e-5 relative L2.  Cases: a 32 x 32 grid with a
 4 x 4 window, a 64-point line with a 16-sample aperture, a 64 x 64 grid with an 8 x 8
 window and odd depth count, the cut disabled, complex128 data; and the 128 x 128 grid with
