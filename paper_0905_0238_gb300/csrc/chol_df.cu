@@ -15,11 +15,13 @@
 // (one CTA per subproblem would leave the serial parts of each factorisation on its SM's
 // critical path and 257 systems unevenly spread over 152 SMs):
 //   * the Gram reduction has written the lower triangle of G + lam I in double-float;
-//   * per 32-column step: cdf_diag factors and inverts the step's 32 x 32 diagonal block of
-//     every subproblem (1024 threads, one element each); cdf_panel multiplies the panel rows
-//     by the inverse (x = a L_kk^-T, independent outputs); cdf_update subtracts P P^T from the
-//     trailing lower triangle in 64 x 64 tiles of every subproblem (the panel staged
-//     transposed in shared memory, each thread a 4 x 4 interleaved register tile);
+//   * cdf_diag factors and inverts the first 32 x 32 diagonal block of every subproblem
+//     (df_diag_block: 256 threads, one barrier per column); per 32-column step cdf_panel
+//     multiplies the panel rows by the inverse (x = a L_kk^-T, independent outputs) and
+//     cdf_update subtracts P P^T from the trailing lower triangle in 64 x 64 tiles of every
+//     subproblem (the panel staged transposed in shared memory, each thread a 4 x 4 interleaved
+//     register tile), its tile-(0, 0) CTAs, first in the launch, going on to factor and invert
+//     the next diagonal block;
 //   * look-ahead: the update of the tile column holding the next diagonal block and panel runs
 //     first, and the rest of the update runs on a second stream while the next diagonal block
 //     and panel proceed (the latency-bound small launches overlap the throughput-bound tiles);
@@ -41,75 +43,19 @@ constexpr int UT = 64, ULD = UT + 1;   // update tile and its padded shared row
 
 __device__ __forceinline__ bool has_rows(const Dev& d, int m) { return d.row_off[m + 1] > d.row_off[m]; }
 
-// Diagonal block of step k0 of every subproblem, factored and inverted in double-float by 1024
-// threads, thread (i, l) holding element (i, l): per column j the pivot's 1 / sqrt, the column
-// scale and the rank-1 update of the trailing block each take one step between barriers (the
-// column of L double-buffered in shared memory so that one step's readers and the next step's
-// writers never meet); then X = L_kk^-1 by the same right-looking sweep over the identity.
-// Writes L_kk (lower triangle), X (strict upper triangle, X_il at (l, i)) and the reciprocal
-// pivots (FP64) to dinv.  At k0 = 0 the status is set and the trace slot takes lam from here on.
-__global__ void __launch_bounds__(1024) cdf_diag_kernel(Dev d, int k0) {
-  __shared__ float2 sCol[2][FB], sInv[FB], sXr[2][FB];
-  __shared__ float2 sLf[FB * FLD];
-  __shared__ int fail;
+// First diagonal block of every subproblem, factored and inverted in double-float (see
+// df_diag_block); the later ones are factored by the update launches.  Sets the status and
+// the trace slot, which holds lam from here on.
+__global__ void __launch_bounds__(256) cdf_diag_kernel(Dev d) {
+  __shared__ DfDiagScratch sh;
   const int m = blockIdx.x, n = d.nz;
-  if (!has_rows(d, m) || (k0 > 0 && d.status[m] != EDT_OK)) return;
-  const int kb = min(FB, n - k0);
-  const int i = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const bool in = i < kb && l <= i;
+  if (!has_rows(d, m)) return;
   float2* A = reinterpret_cast<float2*>(d.G + size_t(m) * n * n);
-  float2 a = in ? A[size_t(k0 + i) * n + k0 + l] : make_float2(0.f, 0.f);
-  if (threadIdx.x == 0) fail = 0;
-  __syncthreads();
-  for (int j = 0; j < kb; ++j) {
-    float2* col = sCol[j & 1];
-    if (i == j && l == j) {
-      const float2 djj = df_norm(a);
-      if (!(djj.x > 0.f) || !isfinite(djj.x)) {
-        fail = 1;
-      } else {
-        const float2 inv = df_rsqrt(djj);
-        a = df_mul(djj, inv);
-        sInv[j] = inv;
-        col[j] = a;
-      }
-    }
-    __syncthreads();
-    if (fail) break;                                  // the same value in every thread
-    if (l == j && i > j && i < kb) { a = df_mul(df_norm(a), sInv[j]); col[i] = a; }
-    __syncthreads();
-    if (l > j && i >= l && i < kb) df_acc(a, df_neg(col[i]), col[l]);
-  }
-  if (fail) {
-    if (threadIdx.x == 0) d.status[m] = EDT_ENOTPD;
-    return;
-  }
-  a = df_norm(a);
-  if (in) {
-    A[size_t(k0 + i) * n + k0 + l] = a;
-    sLf[i * FLD + l] = a;
-    if (d.L32) d.L32[size_t(m) * n * n + size_t(k0 + i) * n + k0 + l] = a.x;   // FP32 copy
-  }
-  if (threadIdx.x < kb) d.dinv[size_t(m) * n + k0 + threadIdx.x] = df_val(sInv[threadIdx.x]);
-  __syncthreads();
-  // X = L^-1: right-looking forward substitution on the identity, row k final at step k
-  float2 x = make_float2(i == l ? 1.f : 0.f, 0.f);
-  for (int k = 0; k < kb; ++k) {
-    float2* xr = sXr[k & 1];
-    if (i == k) {
-      if (l <= k) x = df_mul(df_norm(x), sInv[k]);
-      xr[l] = l <= k ? x : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    if (i > k && i < kb && l <= k) df_acc(x, df_neg(sLf[i * FLD + k]), xr[l]);
-  }
-  if (i < kb && l < i) {
-    const float2 v = df_norm(x);
-    A[size_t(k0 + l) * n + k0 + i] = v;
-    if (d.L32) d.L32[size_t(m) * n * n + size_t(k0 + l) * n + k0 + i] = v.x;   // X in the FP32 copy too
-  }
-  if (threadIdx.x == 0) {
-    if (k0 == 0) { d.trace[m] = d.alpha * d.trace[m]; d.status[m] = EDT_OK; }
+  const bool ok = df_diag_block(A, d.L32 ? d.L32 + size_t(m) * n * n : nullptr, d.dinv + size_t(m) * n,
+                                d.dinv32 ? d.dinv32 + size_t(m) * n : nullptr, d.status + m, n, 0, sh);
+  if (ok && threadIdx.x == 0) {
+    d.trace[m] = d.alpha * d.trace[m];
+    d.status[m] = EDT_OK;
   }
 }
 
@@ -379,7 +325,7 @@ cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s, con
   cudaEvent_t prev_rest = nullptr;
   // The diagonal block of step 0 has a launch of its own; every later one is factored by the
   // previous step's update (parts 0 and 1) as soon as its tile is final.
-  cdf_diag_kernel<<<d.nsub, 1024, 0, s>>>(d, 0);
+  cdf_diag_kernel<<<d.nsub, 256, 0, s>>>(d);
   for (int step = 0, k0 = 0; k0 + FB < n; ++step, k0 += FB) {
     const int t = n - k0 - FB, nt = (t + UT - 1) / UT;
     cdf_panel_kernel<<<dim3((t + 31) / 32, d.nsub), 128, 0, s>>>(d, k0);
