@@ -82,4 +82,31 @@ __device__ __forceinline__ float2 expi_ff(float kxh, float kxl, float kyh, float
   return make_float2(mag * cs, mag * sn);
 }
 
+// 1 / b in FP32 complex arithmetic (|b| far from the FP32 range limits)
+__device__ __forceinline__ float2 cinv32(float2 b) {
+  const float r = 1.f / (b.x * b.x + b.y * b.y);
+  return make_float2(b.x * r, -b.y * r);
+}
+
+// principal square root in FP32, then the branch with non-negative imaginary part
+__device__ __forceinline__ float2 csqrt_upper32(float2 w) {
+  const float r = hypotf(w.x, w.y);
+  if (r == 0.f) return make_float2(0.f, 0.f);
+  float2 z;
+  if (w.x >= 0.f) {
+    const float t = sqrtf(0.5f * (r + w.x));
+    z = make_float2(t, w.y / (2.f * t));
+  } else {
+    const float t = sqrtf(0.5f * (r - w.x));
+    z = make_float2(fabsf(w.y) / (2.f * t), copysignf(t, w.y));
+  }
+  if (z.y < 0.f) z = make_float2(-z.x, -z.y);
+  return z;
+}
+
+__device__ __forceinline__ void split_ff(double v, float& hi, float& lo) {
+  hi = float(v);
+  lo = float(v - double(hi));
+}
+
 }  // namespace edt

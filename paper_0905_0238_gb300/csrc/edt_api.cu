@@ -842,12 +842,15 @@ void prof_ev(edt_ctx* c, int stage, int end, cudaStream_t s) {
 }
 
 // Tables the depth march writes for an inversion: FP64 (FP64 path); the FP32 table by the
-// fast FP32 evaluation (mixed path with the FP32 residual, ~1e-7 relative); the FP32 table
-// rounded from the FP64 evaluation with its remainder, the double-float pair the FP64-accurate
-// residual reads (mixed line path, resid 2).
+// fast FP32 evaluation (mixed path with the FP32 residual, ~1e-7 relative; on the line
+// geometry from FP32 coefficients, a few 1e-6, which the damping of that residual's regime,
+// alpha >= 1e-3, keeps far below the result's tolerance); the FP32 table rounded from the FP64
+// evaluation with its remainder, the double-float pair the FP64-accurate residual reads (mixed
+// line path, resid 2).
 int green_tables(const edt_ctx* c) {
   if (c->cfg.precision != EDT_MIXED) return GREEN_G64;
-  return c->resid_df ? GREEN_G32DF : GREEN_G32;
+  if (c->resid_df) return GREEN_G32DF;
+  return c->win ? GREEN_G32 : GREEN_G32F;
 }
 
 // Data transform and right-hand-side gather, chunk by chunk of frequency planes.

@@ -194,7 +194,10 @@ int record_cuda_error(cudaError_t e);
 
 // ---- launchers (each returns cudaGetLastError()) ---------------------------------------
 constexpr int GREEN_G64 = 1, GREEN_G32 = 2, GREEN_G32DF = 4;   // tables launch_green writes
+constexpr int GREEN_G32F = 8;
 // GREEN_G32 alone: the fast FP32 evaluation for the mixed path (no FP64 table);
+// GREEN_G32F: the same table from coefficients formed in FP32 (green_coef32; about the number
+// of layers times FP32 rounding, for the line inversion with the FP32 residual);
 // GREEN_G32DF: the FP64 evaluation written as the double-float pair g32 + g32lo (no g64)
 cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables);
 

@@ -25,6 +25,14 @@
 //                 each exponential's phase and decay are formed and range-reduced in FP64
 //                 (Cody-Waite for the phase, integer/fraction split for the decay) and
 //                 evaluated with FP32 sincos/exp2 of the reduced arguments, ~1e-7 relative.
+// For the line inversion with the FP32 residual (GREEN_G32F) and at most 64 layers,
+// green_coef32 replaces green_layer and green_recursion: one thread per (f, n) forms
+// each kappa_j by an FP32 complex square root and one Newton step on the FP64 residual
+// w - kappa^2 (the square of the FP32 root is exact in FP64, so the (hi, lo) pair carries
+// kappa to ~1e-14 with four FP64 products instead of a complex FP64 root), exp(i kappa_j h_j)
+// by double-float phase reduction, and both recursions in FP32 complex arithmetic; its
+// outputs are the FP32 coefficients green_eval32 reads.  GB300's FP64 rate made the FP64
+// transcendentals of green_layer and the recursion's FP64 divisions most of the depth march.
 #include "edt_internal.h"
 #include "cplx.cuh"
 
@@ -124,6 +132,65 @@ __global__ void green_recursion_kernel(Dev d) {
   }
 }
 
+constexpr int COEF32_MAX_LAYERS = 64;
+
+__global__ void __launch_bounds__(128) green_coef32_kernel(Dev d) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (n >= d.nk) return;
+  const int J = d.nlayer;
+  const FreqConst fc = d.fc[f];
+  const double L = double(d.N) * d.dx;
+  const double k = d.kval ? d.kval[n] : 2.0 * M_PI * double(n) / L;
+  const double om2r = fc.om_re * fc.om_re - fc.om_im * fc.om_im, om2i = 2.0 * fc.om_re * fc.om_im;
+  const double k2 = k * k;
+  float* c32 = d.coef32 + (size_t(f) * d.nk + n) * size_t(J) * NCOEF32;
+  float2 kap[COEF32_MAX_LAYERS], eh[COEF32_MAX_LAYERS];
+  for (int j = 0; j < J; ++j) {
+    const double ic2 = 1.0 / (d.layer_vel[j] * d.layer_vel[j]);
+    const double wr2 = om2r * ic2 - k2, wi2 = om2i * ic2;
+    const float2 k32 = csqrt_upper32(make_float2(float(wr2), float(wi2)));
+    const double rr = wr2 - (double(k32.x) * k32.x - double(k32.y) * k32.y);
+    const double ri = wi2 - 2.0 * double(k32.x) * k32.y;
+    const float2 dk = (k32.x == 0.f && k32.y == 0.f)
+                          ? make_float2(0.f, 0.f)
+                          : make_float2(float(rr), float(ri)) * cinv32(make_float2(2.f * k32.x, 2.f * k32.y));
+    float* o = c32 + j * NCOEF32;
+    o[0] = k32.x; o[1] = dk.x; o[2] = k32.y; o[3] = dk.y;
+    kap[j] = make_float2(k32.x + dk.x, k32.y + dk.y);
+    if (j + 1 < J) {
+      float hh, hl;
+      split_ff(d.layer_top[j + 1] - d.layer_top[j], hh, hl);
+      eh[j] = expi_ff(k32.x, dk.x, k32.y, hh, hl);       // exp(i kappa_j h_j)
+    } else {
+      eh[j] = make_float2(1.f, 0.f);
+    }
+  }
+  // upward: r_{J-1} = 0; y = kappa_{j+1}(1 - r_{j+1})/(1 + r_{j+1}); rho_j = (kappa_j - y)/(kappa_j + y);
+  // the reflection coefficients are kept in the rho slots and the 1 / (1 + r_{j+1}) in eh's
+  // place once eh_j is used
+  const float2 one = make_float2(1.f, 0.f);
+  float2 r = make_float2(0.f, 0.f);
+  c32[(J - 1) * NCOEF32 + 6] = 0.f;
+  c32[(J - 1) * NCOEF32 + 7] = 0.f;
+  for (int j = J - 2; j >= 0; --j) {
+    const float2 inv1r = cinv32(one + r);
+    const float2 y = kap[j + 1] * (one - r) * inv1r;
+    const float2 rho = (kap[j] - y) * cinv32(kap[j] + y);
+    c32[j * NCOEF32 + 6] = rho.x;
+    c32[j * NCOEF32 + 7] = rho.y;
+    r = rho * (eh[j] * eh[j]);
+    eh[j] = eh[j] * inv1r;                              // exp(i kappa_j h_j) / (1 + r_{j+1})
+  }
+  // downward: A_0 = i / (2 kappa_0), A_{j+1} = A_j exp(i kappa_j h_j)(1 + rho_j)/(1 + r_{j+1})
+  float2 amp = make_float2(0.f, 0.5f) * cinv32(kap[0]);
+  for (int j = 0; j < J; ++j) {
+    c32[j * NCOEF32 + 4] = amp.x;
+    c32[j * NCOEF32 + 5] = amp.y;
+    if (j + 1 < J) amp = amp * eh[j] * (one + make_float2(c32[j * NCOEF32 + 6], c32[j * NCOEF32 + 7]));
+  }
+}
+
 constexpr int EV_WARPS = 4;
 constexpr int EV_ZC = 16;   // depths per warp chunk
 
@@ -214,11 +281,15 @@ __global__ void green_eval32_kernel(Dev d) {
 }  // namespace
 
 cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables) {
-  const bool fast32 = tables == GREEN_G32;
-  const long long nl = (long long)d.nf * d.nk * d.nlayer;
-  green_layer_kernel<<<unsigned((nl + 255) / 256), 256, 0, s>>>(d, fast32 ? 0 : 1);
+  const bool fast32 = tables == GREEN_G32 || tables == GREEN_G32F;
   dim3 g1((d.nk + 127) / 128, d.nf);
-  green_recursion_kernel<<<g1, 128, 0, s>>>(d);
+  if (tables == GREEN_G32F && d.coef32 && d.nlayer <= COEF32_MAX_LAYERS) {
+    green_coef32_kernel<<<g1, 128, 0, s>>>(d);
+  } else {
+    const long long nl = (long long)d.nf * d.nk * d.nlayer;
+    green_layer_kernel<<<unsigned((nl + 255) / 256), 256, 0, s>>>(d, fast32 ? 0 : 1);
+    green_recursion_kernel<<<g1, 128, 0, s>>>(d);
+  }
   if (fast32) {
     const long long ne = (long long)d.nf * d.nk * d.nz;
     green_eval32_kernel<<<unsigned((ne + 255) / 256), 256, 0, s>>>(d);

@@ -45,38 +45,12 @@ __device__ __forceinline__ int find_req(const long long* pre, int nreq, long lon
   return lo;
 }
 
-__device__ __forceinline__ float2 cinv32(float2 b) {
-  const float r = 1.f / (b.x * b.x + b.y * b.y);
-  return make_float2(b.x * r, -b.y * r);
-}
-
 // unit phase of s_f = omega~^2 dz / dx (dz / dx > 0): omega~^2 / |omega~|^2
 __device__ __forceinline__ float2 sf_phase(double f_hz, double eps) {
   const double wr = 2.0 * M_PI * f_hz;
   const double re = wr * wr - eps * eps, im = 2.0 * wr * eps;
   const double r = 1.0 / sqrt(re * re + im * im);
   return make_float2(float(re * r), float(im * r));
-}
-
-// principal square root in FP32, then the branch with non-negative imaginary part
-__device__ __forceinline__ float2 csqrt_upper32(float2 w) {
-  const float r = hypotf(w.x, w.y);
-  if (r == 0.f) return make_float2(0.f, 0.f);
-  float2 z;
-  if (w.x >= 0.f) {
-    const float t = sqrtf(0.5f * (r + w.x));
-    z = make_float2(t, w.y / (2.f * t));
-  } else {
-    const float t = sqrtf(0.5f * (r - w.x));
-    z = make_float2(fabsf(w.y) / (2.f * t), copysignf(t, w.y));
-  }
-  if (z.y < 0.f) z = make_float2(-z.x, -z.y);
-  return z;
-}
-
-__device__ __forceinline__ void split_ff(double v, float& hi, float& lo) {
-  hi = float(v);
-  lo = float(v - double(hi));
 }
 
 // ------------------------------------------------------------------------- depth tables
