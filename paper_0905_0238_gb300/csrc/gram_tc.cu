@@ -434,29 +434,72 @@ __global__ void gram_scale_kernel(Dev d) {
 // Sum the partial tiles of each subproblem into the FP64 Gram (both triangles) and b.  With
 // df_out (the double-float factorisation follows) the lower triangle of G + lam I is written
 // instead, lam = alpha * trace, each value as a double-float pair (float2) in the same 8 bytes.
-// trace(G) of subproblem m: the per-warp partials of its segments, in slot and warp order
+// trace(G) of subproblem m: the per-warp partials of its segments, in slot and warp order.
 __device__ __forceinline__ double trace_of(const Dev& d, int sl0, int sl1) {
   double t = 0.0;
   for (int i = sl0 * PRODUCER_WARPS; i < sl1 * PRODUCER_WARPS; ++i) t += d.tpart[i];
   return t;
 }
 
-__global__ void gram_reduce_kernel(Dev d, int df_out) {
+// One CTA per 32 x 32 tile of G (the lower triangle with df_out, else the whole matrix),
+// 32 x 8 threads: the partial tiles are read with consecutive threads on consecutive TMEM
+// lanes (coalesced; a tile below the diagonal block TC_M x TC_M in its left part reads the
+// transposed tile, whose lanes run along its columns), summed over the subproblem's slots in
+// slot order, staged in shared memory and written as rows of G (coalesced).  CTA ntile of each
+// subproblem forms b and the trace.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(Dev d, int df_out) {
+  __shared__ double s64[32][33];
+  float2* sdf = reinterpret_cast<float2*>(&s64[0][0]);   // [32][33] pairs, same storage
   const int m = blockIdx.y;
   const int nz = d.nz, nzp = nzp_of(nz), ncols = cols_of(nzp);
   const int c1 = nzp + 16;
   const int sl0 = d.m_slot0[m], sl1 = d.m_slot0[m + 1];
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int T = (nz + 31) / 32;
+  const int ntile = df_out ? T * (T + 1) / 2 : T * T;
   const long long nG = (long long)nz * nz;
-  if (e == 0) d.trace[m] = trace_of(d, sl0, sl1);
-  if (e < nG) {
-    const int zi = int(e / nz), zj = int(e - (long long)zi * nz);
-    if (df_out && zj > zi) return;
-    int a = zi, b = zj;
-    if (a >= TC_M && b < TC_M) { a = zj; b = zi; }     // lower-left block from its transpose
+  if (int(blockIdx.x) == ntile) {                      // right-hand sides and the trace
+    if (threadIdx.x == 0) d.trace[m] = trace_of(d, sl0, sl1);
+    for (int e = threadIdx.x; e < 2 * nz; e += blockDim.x) {
+      const int zi = e >> 1, k = e & 1;
+      int lanei, col;
+      if (zi < TC_M) { lanei = zi; col = nzp + k; }
+      else { lanei = zi - TC_M; col = c1 + (nzp - TC_M) + k; }
+      double sacc = 0.0;
+      for (int sl = sl0; sl < sl1; ++sl) {
+        const double v = double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
+        sacc += d.gscale ? v * pow2d(-d.gscale[sl].x - d.gscale[sl].y) : v;
+      }
+      d.b[(size_t(m) * nz + zi) * 2 + k] = sacc;
+    }
+    return;
+  }
+  int ti, tj;
+  if (df_out) {
+    const int t = blockIdx.x;
+    ti = int((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while (ti * (ti + 1) / 2 > t) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    tj = t - ti * (ti + 1) / 2;
+  } else {
+    ti = blockIdx.x / T;
+    tj = blockIdx.x - ti * T;
+  }
+  const int i0 = 32 * ti, j0 = 32 * tj;
+  const bool lane_on_j = i0 >= TC_M && j0 < TC_M;     // TC_M is a multiple of 32: no tile straddles it
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  __shared__ double s_lam;
+  if (df_out && ti == tj) {                           // lam for the diagonal, formed once per CTA
+    if (threadIdx.x == 0) s_lam = d.alpha * trace_of(d, sl0, sl1);
+    __syncthreads();
+  }
+  for (int k = 0; k < 4; ++k) {
+    const int r = ty + 8 * k;
+    const int zi = lane_on_j ? i0 + r : i0 + tx, zj = lane_on_j ? j0 + tx : j0 + r;
+    if (zi >= nz || zj >= nz || (df_out && zj > zi)) continue;
     int lanei, col;
-    if (a < TC_M) { lanei = a; col = b; }
-    else { lanei = a - TC_M; col = c1 + (b - TC_M); }
+    if (zi < TC_M) { lanei = zi; col = zj; }
+    else if (zj < TC_M) { lanei = zj; col = zi; }
+    else { lanei = zi - TC_M; col = c1 + (zj - TC_M); }
     if (df_out) {
       // the partial tiles (FP32, exact power-of-two scales) summed as a double-float pair by
       // TwoSum on the FP32 pipes, then lam added on the diagonal
@@ -469,33 +512,29 @@ __global__ void gram_reduce_kernel(Dev d, int df_out) {
         sh = t;
       }
       if (zi == zj) {
-        const double lam = d.alpha * trace_of(d, sl0, sl1);
+        const double lam = s_lam;
         const float lh = __double2float_rn(lam), ll = __double2float_rn(lam - double(lh));
         const float t = __fadd_rn(sh, lh), bb = __fsub_rn(t, sh);
         sl_ = __fadd_rn(sl_, __fadd_rn(__fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(lh, bb)), ll));
         sh = t;
       }
       const float hs = __fadd_rn(sh, sl_);
-      reinterpret_cast<float2*>(d.G + size_t(m) * nG)[e] = make_float2(hs, __fsub_rn(sl_, __fsub_rn(hs, sh)));
+      sdf[(zi - i0) * 33 + (zj - j0)] = make_float2(hs, __fsub_rn(sl_, __fsub_rn(hs, sh)));
     } else {
-      double s = 0.0;
+      double sacc = 0.0;
       for (int sl = sl0; sl < sl1; ++sl) {
         const double v = double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
-        s += d.gscale ? v * pow2d(-2 * d.gscale[sl].x) : v;
+        sacc += d.gscale ? v * pow2d(-2 * d.gscale[sl].x) : v;
       }
-      d.G[size_t(m) * nG + e] = s;
+      s64[zi - i0][zj - j0] = sacc;
     }
-  } else if (e < nG + 2 * nz) {
-    const int zi = int((e - nG) >> 1), k = int((e - nG) & 1);
-    int lanei, col;
-    if (zi < TC_M) { lanei = zi; col = nzp + k; }
-    else { lanei = zi - TC_M; col = c1 + (nzp - TC_M) + k; }
-    double s = 0.0;
-    for (int sl = sl0; sl < sl1; ++sl) {
-      const double v = double(d.gpart[(size_t(sl) * ncols + col) * TC_M + lanei]);
-      s += d.gscale ? v * pow2d(-d.gscale[sl].x - d.gscale[sl].y) : v;
-    }
-    d.b[(size_t(m) * nz + zi) * 2 + k] = s;
+  }
+  __syncthreads();
+  for (int k = 0; k < 4; ++k) {
+    const int r = ty + 8 * k, zi = i0 + r, zj = j0 + tx;
+    if (zi >= nz || zj >= nz || (df_out && zj > zi)) continue;
+    if (df_out) reinterpret_cast<float2*>(d.G + size_t(m) * nG)[size_t(zi) * nz + zj] = sdf[r * 33 + tx];
+    else d.G[size_t(m) * nG + size_t(zi) * nz + zj] = s64[r][tx];
   }
 }
 
@@ -548,8 +587,8 @@ cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s) {
 }
 
 cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s, int df_out) {
-  const long long n = (long long)d.nz * d.nz + 2 * d.nz;
-  dim3 g(unsigned((n + 255) / 256), d.nsub);
+  const int T = (d.nz + 31) / 32;
+  dim3 g(unsigned((df_out ? T * (T + 1) / 2 : T * T) + 1), d.nsub);
   gram_reduce_kernel<<<g, 256, 0, s>>>(d, df_out);
   return cudaGetLastError();
 }
