@@ -3,10 +3,10 @@
 // accumulated over every row of every subproblem, matrix-free: each kernel row
 // a(z) = |s_f| g(k_p, z) g(k_q, z) is rebuilt from the FP32 table sqrt|s_f| g (rounded from
 // the FP64 depth march), the row's prediction sum_z a(z) x(z) and residual u = d~ - a.x are
-// formed in FP32, and w Re(conj(a(z)) u) is accumulated per lane in FP32 over the warp's 32
-// rows (partial sums of <= 32 terms), then summed across warps in FP64; each CTA stores its
-// partial and refine_sum adds the partials of a subproblem in CTA order, so repeated calls
-// give the same bits.  Table
+// formed in FP32, and w Re(conj(a(z)) u) is accumulated per lane in FP32 over the warp's
+// rows, then summed across the CTA's warps in FP32; each CTA stores its partial (FP64) and
+// refine_sum adds the partials of a subproblem in FP64 in CTA order, so repeated calls give the
+// same bits.  Table
 // rows are read with 16-byte loads (two depths per load) when nz is even, two rows at a time
 // per warp so that both rows' loads are in flight together.  Each warp walks its rows two at a time so that the table loads of
 // both rows are in flight together; rows p and -p sit side by side in the row order and
@@ -30,7 +30,7 @@ template <int Z4, bool FA, int RF_WARPS, int RF_ROWS_PER_WARP>
 __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
   constexpr int ZL = 64 * Z4;
   __shared__ float xs[2][ZL];
-  __shared__ double red[RF_WARPS][2][ZL];
+  __shared__ float red[RF_WARPS][2][ZL];
   const int m = blockIdx.y;
   const long long r0 = d.row_off[m], nr = d.row_off[m + 1] - r0;
   const long long c0 = (long long)blockIdx.x * RF_WARPS * RF_ROWS_PER_WARP;
@@ -120,13 +120,16 @@ __global__ void __launch_bounds__(RF_WARPS * 32) refine_kernel(Dev d) {
     red[warp][0][z + 1] = acc[t][1][0]; red[warp][1][z + 1] = acc[t][1][1];
   }
   __syncthreads();
+  // the warps' FP32 partials added in FP32, in warp order (a handful of terms, each already an
+  // FP32 sum); the CTA partials go to FP64 and are added across CTAs by refine_sum.  Every FP64
+  // operation runs on GB300's narrow FP64 unit, so the CTA keeps them to one per output.
   double* part = d.rpart + (size_t(m) * d.rf_stride + blockIdx.x) * nz * 2;
   for (int i = threadIdx.x; i < 2 * nz; i += blockDim.x) {
     const int z = i >> 1, k = i & 1;
-    double sacc = 0.0;
+    float sacc = 0.f;
 #pragma unroll
     for (int w = 0; w < RF_WARPS; ++w) sacc += red[w][k][z];
-    part[i] = sacc;
+    part[i] = double(sacc);
   }
 }
 
