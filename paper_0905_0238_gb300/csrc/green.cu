@@ -25,14 +25,15 @@
 //                 each exponential's phase and decay are formed and range-reduced in FP64
 //                 (Cody-Waite for the phase, integer/fraction split for the decay) and
 //                 evaluated with FP32 sincos/exp2 of the reduced arguments, ~1e-7 relative.
-// For the line inversion with the FP32 residual (GREEN_G32F) and at most 64 layers,
-// green_coef32 replaces green_layer and green_recursion: one thread per (f, n) forms
-// each kappa_j by an FP32 complex square root and one Newton step on the FP64 residual
-// w - kappa^2 (the square of the FP32 root is exact in FP64, so the (hi, lo) pair carries
-// kappa to ~1e-14 with four FP64 products instead of a complex FP64 root), exp(i kappa_j h_j)
-// by double-float phase reduction, and both recursions in FP32 complex arithmetic; its
-// outputs are the FP32 coefficients green_eval32 reads.  GB300's FP64 rate made the FP64
-// transcendentals of green_layer and the recursion's FP64 divisions most of the depth march.
+// For the line inversion with the FP32 residual (GREEN_G32F) and at most 32 layers,
+// green_kap32 (one thread per (f, n, layer)) and green_rec32 (one thread per (f, n)) replace
+// green_layer and green_recursion: each kappa_j by an FP32 complex square root and one Newton
+// step on the FP64 residual w - kappa^2 (the square of the FP32 root is exact in FP64, so the
+// (hi, lo) pair carries kappa to ~1e-14 with four FP64 products instead of a complex FP64
+// root), exp(i kappa_j h_j) by double-float phase reduction, and both recursions in FP32
+// complex arithmetic; the outputs are the FP32 coefficients green_eval32 reads.  GB300's FP64
+// rate made the FP64 transcendentals of green_layer and the recursion's FP64 divisions most of
+// the depth march.
 #include "edt_internal.h"
 #include "cplx.cuh"
 
@@ -132,62 +133,76 @@ __global__ void green_recursion_kernel(Dev d) {
   }
 }
 
-constexpr int COEF32_MAX_LAYERS = 64;
+// The FP32 recursion's rounding errors (and those of its FP32 exponentials) compound over the
+// layers, about a few FP32 ulps per layer in the amplitudes: deeper stacks keep the FP64 march.
+constexpr int COEF32_MAX_LAYERS = 32;
 
-__global__ void __launch_bounds__(128) green_coef32_kernel(Dev d) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  const int f = blockIdx.y;
-  if (n >= d.nk) return;
+// FP32 coefficients, pass 1: one thread per (f, n, layer) -- kappa_j (FP32 root, one Newton
+// step on the FP64 residual) and exp(i kappa_j h_j), the latter parked in the amplitude slots
+// until the recursion replaces it.
+__global__ void green_kap32_kernel(Dev d) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int J = d.nlayer;
+  const long long total = (long long)d.nf * d.nk * J;
+  if (gid >= total) return;
+  const int j = int(gid % J);
+  const long long fn = gid / J;
+  const int n = int(fn % d.nk), f = int(fn / d.nk);
   const FreqConst fc = d.fc[f];
   const double L = double(d.N) * d.dx;
   const double k = d.kval ? d.kval[n] : 2.0 * M_PI * double(n) / L;
   const double om2r = fc.om_re * fc.om_re - fc.om_im * fc.om_im, om2i = 2.0 * fc.om_re * fc.om_im;
-  const double k2 = k * k;
-  float* c32 = d.coef32 + (size_t(f) * d.nk + n) * size_t(J) * NCOEF32;
-  float2 kap[COEF32_MAX_LAYERS], eh[COEF32_MAX_LAYERS];
-  for (int j = 0; j < J; ++j) {
-    const double ic2 = 1.0 / (d.layer_vel[j] * d.layer_vel[j]);
-    const double wr2 = om2r * ic2 - k2, wi2 = om2i * ic2;
-    const float2 k32 = csqrt_upper32(make_float2(float(wr2), float(wi2)));
-    const double rr = wr2 - (double(k32.x) * k32.x - double(k32.y) * k32.y);
-    const double ri = wi2 - 2.0 * double(k32.x) * k32.y;
-    const float2 dk = (k32.x == 0.f && k32.y == 0.f)
-                          ? make_float2(0.f, 0.f)
-                          : make_float2(float(rr), float(ri)) * cinv32(make_float2(2.f * k32.x, 2.f * k32.y));
-    float* o = c32 + j * NCOEF32;
-    o[0] = k32.x; o[1] = dk.x; o[2] = k32.y; o[3] = dk.y;
-    kap[j] = make_float2(k32.x + dk.x, k32.y + dk.y);
-    if (j + 1 < J) {
-      float hh, hl;
-      split_ff(d.layer_top[j + 1] - d.layer_top[j], hh, hl);
-      eh[j] = expi_ff(k32.x, dk.x, k32.y, hh, hl);       // exp(i kappa_j h_j)
-    } else {
-      eh[j] = make_float2(1.f, 0.f);
-    }
+  const double ic2 = 1.0 / (d.layer_vel[j] * d.layer_vel[j]);
+  const double wr2 = om2r * ic2 - k * k, wi2 = om2i * ic2;
+  const float2 k32 = csqrt_upper32(make_float2(float(wr2), float(wi2)));
+  const double rr = wr2 - (double(k32.x) * k32.x - double(k32.y) * k32.y);
+  const double ri = wi2 - 2.0 * double(k32.x) * k32.y;
+  const float2 dk = (k32.x == 0.f && k32.y == 0.f)
+                        ? make_float2(0.f, 0.f)
+                        : make_float2(float(rr), float(ri)) * cinv32(make_float2(2.f * k32.x, 2.f * k32.y));
+  float2 eh = make_float2(1.f, 0.f);
+  if (j + 1 < J) {
+    float hh, hl;
+    split_ff(d.layer_top[j + 1] - d.layer_top[j], hh, hl);
+    eh = expi_ff(k32.x, dk.x, k32.y, hh, hl);            // exp(i kappa_j h_j)
   }
-  // upward: r_{J-1} = 0; y = kappa_{j+1}(1 - r_{j+1})/(1 + r_{j+1}); rho_j = (kappa_j - y)/(kappa_j + y);
-  // the reflection coefficients are kept in the rho slots and the 1 / (1 + r_{j+1}) in eh's
-  // place once eh_j is used
+  float4* o = reinterpret_cast<float4*>(d.coef32 + size_t(gid) * NCOEF32);
+  o[0] = make_float4(k32.x, dk.x, k32.y, dk.y);
+  o[1] = make_float4(eh.x, eh.y, 0.f, 0.f);
+}
+
+// Pass 2: one thread per (f, n) -- the upward recursion for rho_j (stored; the amplitude slot
+// takes exp(i kappa_j h_j) / (1 + r_{j+1})), then the downward one for the amplitudes, in FP32.
+__global__ void __launch_bounds__(128) green_rec32_kernel(Dev d) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (n >= d.nk) return;
+  const int J = d.nlayer;
+  float4* c4 = reinterpret_cast<float4*>(d.coef32 + (size_t(f) * d.nk + n) * size_t(J) * NCOEF32);
   const float2 one = make_float2(1.f, 0.f);
+  // upward: r_{J-1} = 0; y = kappa_{j+1}(1 - r_{j+1})/(1 + r_{j+1}); rho_j = (kappa_j - y)/(kappa_j + y)
   float2 r = make_float2(0.f, 0.f);
-  c32[(J - 1) * NCOEF32 + 6] = 0.f;
-  c32[(J - 1) * NCOEF32 + 7] = 0.f;
+  float4 kn4 = c4[2 * (J - 1)];
+  float2 kn = make_float2(kn4.x + kn4.y, kn4.z + kn4.w);
+  c4[2 * (J - 1) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);   // amplitude set below; rho_{J-1} = 0
   for (int j = J - 2; j >= 0; --j) {
+    const float4 kj4 = c4[2 * j], ah = c4[2 * j + 1];
+    const float2 kj = make_float2(kj4.x + kj4.y, kj4.z + kj4.w), eh = make_float2(ah.x, ah.y);
     const float2 inv1r = cinv32(one + r);
-    const float2 y = kap[j + 1] * (one - r) * inv1r;
-    const float2 rho = (kap[j] - y) * cinv32(kap[j] + y);
-    c32[j * NCOEF32 + 6] = rho.x;
-    c32[j * NCOEF32 + 7] = rho.y;
-    r = rho * (eh[j] * eh[j]);
-    eh[j] = eh[j] * inv1r;                              // exp(i kappa_j h_j) / (1 + r_{j+1})
+    const float2 y = kn * (one - r) * inv1r;
+    const float2 rho = (kj - y) * cinv32(kj + y);
+    r = rho * (eh * eh);
+    const float2 ehi = eh * inv1r;                            // exp(i kappa_j h_j) / (1 + r_{j+1})
+    c4[2 * j + 1] = make_float4(ehi.x, ehi.y, rho.x, rho.y);
+    kn = kj;
   }
   // downward: A_0 = i / (2 kappa_0), A_{j+1} = A_j exp(i kappa_j h_j)(1 + rho_j)/(1 + r_{j+1})
-  float2 amp = make_float2(0.f, 0.5f) * cinv32(kap[0]);
+  const float4 k04 = c4[0];
+  float2 amp = make_float2(0.f, 0.5f) * cinv32(make_float2(k04.x + k04.y, k04.z + k04.w));
   for (int j = 0; j < J; ++j) {
-    c32[j * NCOEF32 + 4] = amp.x;
-    c32[j * NCOEF32 + 5] = amp.y;
-    if (j + 1 < J) amp = amp * eh[j] * (one + make_float2(c32[j * NCOEF32 + 6], c32[j * NCOEF32 + 7]));
+    const float4 ah = c4[2 * j + 1];                          // (ehi, rho)
+    c4[2 * j + 1] = make_float4(amp.x, amp.y, ah.z, ah.w);
+    if (j + 1 < J) amp = amp * make_float2(ah.x, ah.y) * (one + make_float2(ah.z, ah.w));
   }
 }
 
@@ -284,7 +299,9 @@ cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables) {
   const bool fast32 = tables == GREEN_G32 || tables == GREEN_G32F;
   dim3 g1((d.nk + 127) / 128, d.nf);
   if (tables == GREEN_G32F && d.coef32 && d.nlayer <= COEF32_MAX_LAYERS) {
-    green_coef32_kernel<<<g1, 128, 0, s>>>(d);
+    const long long nl = (long long)d.nf * d.nk * d.nlayer;
+    green_kap32_kernel<<<unsigned((nl + 255) / 256), 256, 0, s>>>(d);
+    green_rec32_kernel<<<g1, 128, 0, s>>>(d);
   } else {
     const long long nl = (long long)d.nf * d.nk * d.nlayer;
     green_layer_kernel<<<unsigned((nl + 255) / 256), 256, 0, s>>>(d, fast32 ? 0 : 1);
