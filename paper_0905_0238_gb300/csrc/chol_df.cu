@@ -285,13 +285,11 @@ size_t cdf_final_smem(int n) { return size_t(3 * n + blk_solve_scratch<DfArith, 
 }  // namespace
 
 int chol_dfloat_launches(int n) {
-  int k = 1;                                        // the final solve
-  for (int k0 = 0; k0 < n; k0 += FB) {
-    ++k;                                            // diagonal block
-    if (k0 + FB >= n) break;
+  int k = 2;                                        // the first diagonal block, the final solve
+  for (int k0 = 0; k0 + FB < n; k0 += FB) {
     const int nt = (n - k0 - FB + UT - 1) / UT;
-    k += 1 + (nt < 2 ? 1 : 2);                      // panel, update (one or two parts)
-  }
+    k += 1 + (nt < 2 ? 1 : 2);                      // panel, update (one or two parts; the next
+  }                                                 // diagonal block inside the first)
   return k;
 }
 

@@ -914,7 +914,7 @@ int run_invert(edt_ctx* c, const void* D, int D_dtype, void* V, int V_dtype, cud
   prof_ev(c, 2, 1, s);
   if (ov) EDT_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   prof_ev(c, 3, 0, s);
-  if (mixed) EDT_TRY(launch_gram_scale(d, s));
+  if (mixed) EDT_TRY(launch_gram_scale(d, s, green_tables(c) != GREEN_G32DF));
   prof_ev(c, 3, 1, s);
   prof_ev(c, 4, 0, s);
   if (mixed) {
@@ -1471,7 +1471,7 @@ int edt_gram(edt_ctx* c, const void* D, int D_dtype, void* G, void* b, void* tr,
   EDT_TRYI(kernel_rows(c, s));
   EDT_TRYI(transform_rhs(c, D, D_dtype, s));
   if (mixed) {
-    EDT_TRY(launch_gram_scale(d, s));
+    EDT_TRY(launch_gram_scale(d, s, green_tables(c) != GREEN_G32DF));
     EDT_TRY(launch_gram_tc(d, s));
     EDT_TRY(launch_gram_reduce(d, s));
   } else {
@@ -1519,7 +1519,7 @@ int edt_get_stats(edt_ctx* c, edt_stats* o) {
   }
   const int chol_n = c->dev.chol_df ? chol_dfloat_launches(c->nz) : chol_launches(c->nz);
   o->launches_per_invert = (c->cfg.precision == EDT_MIXED ? 6 + 3 * c->cfg.refine : 5) + tr_launches +
-                           chol_n + gram_scale_launches(c->dev);
+                           chol_n + gram_scale_launches(c->dev, green_tables(c) != GREEN_G32DF);
   // solver variants replace the Cholesky launch: trace, two projections, the solve (Cholesky
   // or Jacobi), the back-projection with the disk; the Jacobi kernel alone without it
   if (c->variant) o->launches_per_invert += (c->kz_p.empty() ? 1 : 5) - chol_launches(c->nz);

@@ -227,9 +227,11 @@ cudaError_t fft2_f64(const Dev& d, double2* X, int planes, int ny, int sign, dou
 
 cudaError_t launch_gram_f64(const Dev& d, cudaStream_t s);
 cudaError_t launch_gram_tc(const Dev& d, cudaStream_t s);       // partial tiles + trace
-int gram_scale_launches(const Dev& d);                          // FP16 operand scales: 0 or 2 kernels
+int gram_scale_launches(const Dev& d, bool rowmax_ready);       // FP16 operand scales: 0, 1 or 2 kernels
 int gram_trace_parts();                                         // trace partials per Gram segment
-cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s);    // per-segment FP16 operand scales
+// per-segment FP16 operand scales; rowmax_ready: the FP32 table's evaluation (green_eval32)
+// has already written the row maxima
+cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s, bool rowmax_ready);
 // partials -> G, b (FP64); df_out: the lower triangle of G + lam I as double-float pairs
 cudaError_t launch_gram_reduce(const Dev& d, cudaStream_t s, int df_out = 0);
 cudaError_t launch_trace_diag(const Dev& d, cudaStream_t s);   // trace[m] = sum_z G[m][z][z]

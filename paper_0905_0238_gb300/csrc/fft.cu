@@ -290,7 +290,7 @@ cudaError_t fft2_f64(const Dev& d, double2* X, int planes, int ny, int sign, dou
 namespace {
 
 // ---- inverse transform ------------------------------------------------------------------
-constexpr int INV_ZT = 8;
+constexpr int INV_ZT = 2;   // depths per CTA: 128 CTAs for 256 depths (8 left most SMs idle)
 
 __global__ void inverse_kernel(Dev d, void* V, int V_dtype) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -560,12 +560,14 @@ cudaError_t prepare_gram_tc(const Dev& d) {
                        : cudaFuncSetAttribute(gram_tc_kernel<1, false>, attr, smem);
 }
 
-int gram_scale_launches(const Dev& d) { return d.f16 && d.ncta_gram > 0 ? 2 : 0; }
+int gram_scale_launches(const Dev& d, bool rowmax_ready) {
+  return d.f16 && d.ncta_gram > 0 ? (rowmax_ready ? 1 : 2) : 0;
+}
 
-cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s) {
+cudaError_t launch_gram_scale(const Dev& d, cudaStream_t s, bool rowmax_ready) {
   if (!d.f16 || d.ncta_gram <= 0) return cudaSuccess;
   const long long nrows = (long long)d.nf * d.nk;
-  table_rowmax_kernel<<<unsigned((nrows + 7) / 8), 256, 0, s>>>(d, nrows);
+  if (!rowmax_ready) table_rowmax_kernel<<<unsigned((nrows + 7) / 8), 256, 0, s>>>(d, nrows);
   gram_scale_kernel<<<d.nseg, 256, 0, s>>>(d);
   return cudaGetLastError();
 }

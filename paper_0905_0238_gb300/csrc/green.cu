@@ -271,26 +271,38 @@ __global__ void __launch_bounds__(EV_WARPS * 32) green_eval64_kernel(Dev d) {
   }
 }
 
-__global__ void green_eval32_kernel(Dev d) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)d.nf * d.nk * d.nz;
-  if (gid >= total) return;
-  const int z = int(gid % d.nz);
-  const long long fn = gid / d.nz;
+// One CTA per table row (f, n), threads over depth; the row's largest |value| goes to rowmax
+// (when present) for the FP16 operand scales of the Gram, so that no pass re-reads the table.
+__global__ void __launch_bounds__(256) green_eval32_kernel(Dev d) {
+  __shared__ float red[8];
+  const long long fn = blockIdx.x;
   const int J = d.nlayer;
-  const int l = d.z_layer[z];
-  const float4 zo = reinterpret_cast<const float4*>(d.z_off32)[z];   // off (hi, lo), 2h - off (hi, lo)
-  const float4* c4 = reinterpret_cast<const float4*>(d.coef32 + (fn * J + l) * NCOEF32);
-  const float4 k4 = c4[0], ar = c4[1];
-  float2 e = expi_ff(k4.x, k4.y, k4.z, zo.x, zo.y);
-  if (l < J - 1) {
-    const float2 e2 = expi_ff(k4.x, k4.y, k4.z, zo.z, zo.w);
-    e = e + make_float2(ar.z, ar.w) * e2;
-  }
   const int f = int(fn / d.nk);
   const float sq = d.fc32_sqrt_s[f];
-  const float2 g = make_float2(ar.x, ar.y) * e;
-  d.g32[size_t(fn) * d.nzs + z] = make_float2(sq * g.x, sq * g.y);
+  float mx = 0.f;
+  for (int z = threadIdx.x; z < d.nz; z += blockDim.x) {
+    const int l = d.z_layer[z];
+    const float4 zo = reinterpret_cast<const float4*>(d.z_off32)[z];   // off (hi, lo), 2h - off (hi, lo)
+    const float4* c4 = reinterpret_cast<const float4*>(d.coef32 + (fn * J + l) * NCOEF32);
+    const float4 k4 = c4[0], ar = c4[1];
+    float2 e = expi_ff(k4.x, k4.y, k4.z, zo.x, zo.y);
+    if (l < J - 1) {
+      const float2 e2 = expi_ff(k4.x, k4.y, k4.z, zo.z, zo.w);
+      e = e + make_float2(ar.z, ar.w) * e2;
+    }
+    const float2 g = make_float2(ar.x, ar.y) * e;
+    const float2 v = make_float2(sq * g.x, sq * g.y);
+    d.g32[size_t(fn) * d.nzs + z] = v;
+    mx = fmaxf(mx, sqrtf(v.x * v.x + v.y * v.y));
+  }
+  if (!d.rowmax) return;                           // the same in the whole CTA
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+    d.rowmax[fn] = mx;
+  }
 }
 
 }  // namespace
@@ -308,8 +320,7 @@ cudaError_t launch_green(const Dev& d, cudaStream_t s, int tables) {
     green_recursion_kernel<<<g1, 128, 0, s>>>(d);
   }
   if (fast32) {
-    const long long ne = (long long)d.nf * d.nk * d.nz;
-    green_eval32_kernel<<<unsigned((ne + 255) / 256), 256, 0, s>>>(d);
+    green_eval32_kernel<<<unsigned((long long)d.nf * d.nk), 256, 0, s>>>(d);
   } else {
     Dev e = d;
     if (!(tables & (GREEN_G32 | GREEN_G32DF))) e.g32 = nullptr;
