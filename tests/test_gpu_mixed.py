@@ -212,3 +212,26 @@ def test_shorter_gram_segments_reduce_the_accumulation_error():
         G = s.gram(dev(D))[0].cpu().numpy()
         err[cap] = max(rel_l2(G[m], refs[m]) for m in refs)
     assert err[32] < err[0] / 3 and err[32] < 5e-6, err
+
+
+@pytest.mark.parametrize("nlayer", [1, 5, 32])
+def test_few_layer_reference_with_fp32_march_coefficients(nlayer):
+    """A line reference of at most 32 layers with the FP32 residual (alpha >= 1e-3): the depth
+    march's coefficients are formed in FP32 (kappa refined by one Newton step on the FP64
+    residual, double-float phases, FP32 recursions), a few FP32 ulps per layer in the table.
+    The inversion meets the oracle's 1e-5 and stays within 2e-6 of the FP64 GPU path, whose
+    table comes from the FP64 march."""
+    from paper_0905_0238_gb300 import Config, Solver, EDT_FP64
+    nz, dz = 48, 8.0
+    tops = np.linspace(0.0, nz * dz, nlayer, endpoint=False)
+    vel = np.linspace(1500.0, 3000.0, nlayer)
+    wl = small_workload(nx=32, nz=nz, nf=6, alpha=1e-2, dz=dz, layers=(tops, vel))
+    D = born_data(wl, salt=8)
+    V_or, vh_or = edt2d.invert(wl, D.astype(np.complex128))
+    s = solver(wl)
+    V = s.invert(dev(D)).cpu().numpy()
+    vh = s.vhat().cpu().numpy()
+    V64 = Solver(Config.from_workload(wl, precision=EDT_FP64)).invert(dev(D.astype(np.complex128))).cpu().numpy()
+    assert rel_l2(vh, vh_or) < 1e-5
+    assert rel_l2(V, V_or) < 1e-5
+    assert rel_l2(V, V64) < 2e-6
