@@ -535,41 +535,46 @@ def main():
                    fp64_gpu_subproblems_per_sec=sub_per_step / (ms64 / 1e3),
                    speedup_vs_fp64_gpu=(ms64 / ms_step))
 
-    # ---- variant: the native FP64 Cholesky (a library option) beside the double-float one ----
+    # ---- variants: the native FP64 Cholesky and the double-float one with its trailing updates
+    # on the tensor cores (library options) beside the default double-float one ----
     variants = {}
-    if args.chol_df != 2:
-        dfs = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=args.passes,
-                                          refine=args.refine, chol_df=2), device=dev)
-        # the same launch shapes, so that only the factorisation differs (the shapes set FP32
-        # summation orders in the transform and the residual)
-        dfs.set_tuning(**{k: v for k, v in mixed.tuning().items() if k != "invert_ms"})
-        Vdf = torch.empty_like(Vout)
-        for _ in range(3):
-            dfs.invert(D, out=Vdf)
-        torch.cuda.synchronize()
-        barrier()
-        v0 = torch.cuda.Event(enable_timing=True)
-        v1 = torch.cuda.Event(enable_timing=True)
-        v0.record(stream)
-        for _ in range(args.steps):
-            dfs.invert(D, out=Vdf)
-        v1.record(stream)
-        torch.cuda.synchronize()
-        ms_df = max_over_ranks(v0.elapsed_time(v1), world)
-        Ldf = torch.tril(mixed.factor())
-        L64 = torch.tril(dfs.factor())
-        fac_err = float(torch.max(torch.linalg.norm(Ldf - L64, dim=(1, 2))
-                                  / torch.clamp(torch.linalg.norm(L64, dim=(1, 2)), min=1e-300)))
-        variants["chol_fp64"] = dict(
-            description="native FP64 Cholesky factorisation and solves (chol_df = 2)",
-            factor_rel_diff_max=fac_err,
-            value=job_throughput(world, sub_per_step, args.steps, ms_df), unit="subproblems/s",
-            ms_per_step=ms_df / args.steps,
-            rel_l2_V_vs_default=float(torch.linalg.norm(Vdf.double() - Vout.double())
-                                      / torch.linalg.norm(Vout.double())),
-            rel_l2_vhat_vs_default=float(torch.linalg.norm(dfs.vhat() - mixed.vhat())
-                                         / torch.linalg.norm(mixed.vhat())))
-        del dfs
+    if args.chol_df not in (2, 3):
+        for vname, vcd, vdesc in (
+                ("chol_fp64", 2, "native FP64 Cholesky factorisation and solves (chol_df = 2)"),
+                ("chol_tensor_slices", 3, "double-float Cholesky with the trailing updates on the tensor "
+                                          "cores, eight 7-bit BF16 slices per panel value (chol_df = 3)")):
+            dfs = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=args.passes,
+                                              refine=args.refine, chol_df=vcd), device=dev)
+            # the same launch shapes, so that only the factorisation differs (the shapes set FP32
+            # summation orders in the transform and the residual)
+            dfs.set_tuning(**{k: v for k, v in mixed.tuning().items() if k != "invert_ms"})
+            Vdf = torch.empty_like(Vout)
+            for _ in range(3):
+                dfs.invert(D, out=Vdf)
+            torch.cuda.synchronize()
+            barrier()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for _ in range(args.steps):
+                dfs.invert(D, out=Vdf)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            ms_df = max_over_ranks(v0.elapsed_time(v1), world)
+            Ldf = torch.tril(mixed.factor())
+            L64 = torch.tril(dfs.factor())
+            fac_err = float(torch.max(torch.linalg.norm(Ldf - L64, dim=(1, 2))
+                                      / torch.clamp(torch.linalg.norm(L64, dim=(1, 2)), min=1e-300)))
+            variants[vname] = dict(
+                description=vdesc,
+                factor_rel_diff_max=fac_err,
+                value=job_throughput(world, sub_per_step, args.steps, ms_df), unit="subproblems/s",
+                ms_per_step=ms_df / args.steps,
+                rel_l2_V_vs_default=float(torch.linalg.norm(Vdf.double() - Vout.double())
+                                          / torch.linalg.norm(Vout.double())),
+                rel_l2_vhat_vs_default=float(torch.linalg.norm(dfs.vhat() - mixed.vhat())
+                                             / torch.linalg.norm(mixed.vhat())))
+            del dfs
 
     if rank != 0:
         if world > 1:

@@ -128,8 +128,12 @@ typedef struct {
                                    solves in double-float (FP32 hi/lo pairs, ~48-bit,
                                    error-free products and sums) on the FP32 pipes with
                                    FP64 pivots (1, and 0 = automatic, the default), or
-                                   native FP64 throughout (2); the FP64 path always
-                                   factors in native FP64                               */
+                                   native FP64 throughout (2), or double-float with the
+                                   trailing updates on the tensor cores (3: each panel
+                                   value cut into eight 7-bit BF16 slices, every level of
+                                   slice products summed exactly in FP32 tensor memory;
+                                   the same factor to FP64 class, slower as built); the
+                                   FP64 path always factors in native FP64              */
   int freq_chunk;               /* frequency planes per chunk of the data transform and
                                    the forward model (the spectrum buffer holds one
                                    chunk); 0 = automatic: as many planes as fit in

@@ -33,6 +33,7 @@
 #include "edt_internal.h"
 #include "dfloat.cuh"
 #include "blksolve.cuh"
+#include "tc_ptx.cuh"
 
 namespace edt {
 
@@ -207,6 +208,207 @@ __global__ void __launch_bounds__(256) cdf_update_kernel(Dev d, int k0, int part
   }
 }
 
+// ---- trailing updates on the tensor cores: error-free BF16 slices (Ozaki scheme) ----------
+// Tile of 128 rows (I) x 64 columns (J) of the trailing lower triangle: C -= P_I P_J^T with the
+// step's double-float panel P (K = 32).  Each panel row r is scaled by 2^-E_r (|P_rk| < 2^E_r)
+// and cut into eight signed 7-bit integer slices s_0..s_7 (P_rk = 2^E_r sum_i s_i 2^-7(i+1),
+// to the double-float's precision), exact in BF16.  The slice products of one level
+// l = i + j, summed over K = 32 and over the level's at most eight pairs, are integers below
+// 2^22, so the FP32 accumulators in tensor memory hold them exactly: one accumulator of 64
+// columns per level (8 x 64 = 512 columns).  The operands pack two slices per 128-byte row
+// (K = 64): A tile u = [s_2u | s_2u+1], B tile c = [t_c | t_c-1], so one K = 64 product adds the
+// two pairs (2u, l - 2u) and (2u + 1, l - 2u - 1) of level l: 20 products of K = 64 in all.
+// The epilogue adds the levels from the smallest up in double-float, scales by
+// 2^(E_r + E_c - 14) and subtracts from C.
+constexpr int TCU_M = 128, TCU_N = 64, TCU_A = TCU_M * 128, TCU_B = TCU_N * 128;
+constexpr int TCU_SMEM = 1024 + 4 * TCU_A + 8 * TCU_B;
+
+__device__ __forceinline__ void tcu_tiles(int t, int& RT, int& CT) {
+  RT = (t + TCU_M - 1) / TCU_M;
+  CT = (t + TCU_N - 1) / TCU_N;
+}
+// number of tiles (I, J), J <= 2 I + 1, J < CT, of part 0 (all), 1 (J = 0) or 2 (J >= 1)
+__host__ __device__ inline int tcu_count(int t, int part) {
+  const int RT = (t + TCU_M - 1) / TCU_M, CT = (t + TCU_N - 1) / TCU_N;
+  if (part == 1) return RT;
+  int c = 0;
+  for (int I = 0; I < RT; ++I) c += min(2 * I + 2, CT) - (part == 2 ? 1 : 0);
+  return c;
+}
+
+__device__ __forceinline__ void tcu_put(unsigned char* tile, int row, int kk, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(tile + tcx::sw_off(row, kk >> 3) + (kk & 7) * 2) = __float2bfloat16_rn(v);
+}
+
+__global__ void __launch_bounds__(256) cdf_update_tc_kernel(Dev d, int k0, int part) {
+  using namespace tcx;
+  extern __shared__ __align__(1024) unsigned char tcu_raw[];
+  __shared__ int sEA[TCU_M], sEB[TCU_N];
+  __shared__ uint64_t done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ DfDiagScratch dg;
+  unsigned char* smA = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tcu_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* smB = smA + 4 * TCU_A;
+  const int n = d.nz, t = n - k0 - FB, t0 = k0 + FB;
+  int m, pt;
+  if (part == 2) {
+    m = blockIdx.y;
+    pt = blockIdx.x;
+  } else if (int(blockIdx.x) < d.nsub) {
+    m = blockIdx.x;
+    pt = 0;
+  } else {
+    m = (blockIdx.x - d.nsub) % d.nsub;
+    pt = 1 + (blockIdx.x - d.nsub) / d.nsub;
+  }
+  if (!has_rows(d, m) || d.status[m] != EDT_OK) return;
+  int I = 0, J = 0;
+  {
+    int RT, CT;
+    tcu_tiles(t, RT, CT);
+    if (part == 1) {
+      I = pt;
+    } else {
+      int rem = pt;
+      for (I = 0; I < RT; ++I) {
+        const int j0 = part == 2 ? 1 : 0, j1 = min(2 * I + 2, CT);
+        if (rem < j1 - j0) { J = j0 + rem; break; }
+        rem -= j1 - j0;
+      }
+    }
+  }
+  const int r0 = t0 + TCU_M * I, c0 = t0 + TCU_N * J;
+  float2* A = reinterpret_cast<float2*>(d.G + size_t(m) * n * n);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  // operands: every row's values loaded first (24 loads in flight per warp), then per row the
+  // exponent and eight slices
+  float2 va[TCU_M / 8], vb[TCU_N / 8];
+#pragma unroll
+  for (int q = 0; q < TCU_M / 8; ++q) {
+    const int rg = r0 + warp + 8 * q;
+    va[q] = rg < n ? A[size_t(rg) * n + k0 + lane] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < TCU_N / 8; ++q) {
+    const int cg = c0 + warp + 8 * q;
+    vb[q] = cg < n ? A[size_t(cg) * n + k0 + lane] : make_float2(0.f, 0.f);
+  }
+  auto slice_row = [&](float2 a, int& E, float* sl) {
+    float mx = fabsf(a.x);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    E = 0;
+    if (mx > 0.f) frexpf(mx, &E);                   // mx < 2^E
+    float vh = ldexpf(a.x, -E), vl = ldexpf(a.y, -E);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float th = vh * 128.f, tl = vl * 128.f;
+      const float si = rintf(th);
+      sl[i] = si;
+      const float2 r = two_sum(th - si, tl);
+      vh = r.x;
+      vl = r.y;
+    }
+  };
+#pragma unroll
+  for (int q = 0; q < TCU_M / 8; ++q) {
+    const int r = warp + 8 * q;
+    int E;
+    float sl[8];
+    slice_row(va[q], E, sl);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tcu_put(smA + (i >> 1) * TCU_A, r, 32 * (i & 1) + lane, sl[i]);
+    if (lane == 0) sEA[r] = E;
+  }
+#pragma unroll
+  for (int q = 0; q < TCU_N / 8; ++q) {
+    const int c = warp + 8 * q;
+    int E;
+    float sl[8];
+    slice_row(vb[q], E, sl);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      tcu_put(smB + i * TCU_B, c, lane, sl[i]);
+      if (i < 7) tcu_put(smB + (i + 1) * TCU_B, c, 32 + lane, sl[i]);
+    }
+    tcu_put(smB, c, 32 + lane, 0.f);
+    if (lane == 0) sEB[c] = E;
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = idesc_bf16(TCU_M, TCU_N);
+    const uint32_t a0 = smem_u32(smA), b0 = smem_u32(smB);
+    for (int l = 0; l < 8; ++l)
+      for (int u = 0; 2 * u <= l; ++u) {
+        const uint32_t aa = a0 + uint32_t(u) * TCU_A, bb = b0 + uint32_t(l - 2 * u) * TCU_B;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(tmem + uint32_t(64 * l), sw128_desc(aa + 32 * kk), sw128_desc(bb + 32 * kk), idesc,
+                   (u > 0 || kk > 0) ? 1u : 0u);
+      }
+    mma_commit(&done);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&done, 0u, &abort_flag);
+  tc_fence_after();
+  if (ok) {
+    const int qd = warp & 3, h = warp >> 2;
+    const int rr = 32 * qd + lane, rg = r0 + rr;
+    for (int g = 0; g < 2; ++g) {
+      const int cb = 32 * h + 16 * g;
+      uint32_t v[8][16];                           // the eight levels' loads in flight together
+#pragma unroll
+      for (int l = 0; l < 8; ++l) tmem_ld16_nowait(tmem + (uint32_t(32 * qd) << 16) + uint32_t(64 * l + cb), v[l]);
+      tmem_wait_ld();
+      float hi[16], lo[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) { hi[c] = ldexpf(__uint_as_float(v[7][c]), -49); lo[c] = 0.f; }
+#pragma unroll
+      for (int l = 6; l >= 0; --l) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float2 sm = two_sum(hi[c], ldexpf(__uint_as_float(v[l][c]), -7 * l));
+          hi[c] = sm.x;
+          lo[c] = __fadd_rn(lo[c], sm.y);
+        }
+      }
+      if (rg < n) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int cg = c0 + cb + c;
+          if (cg < n && cg <= rg) {
+            const int e = sEA[rr] + sEB[cb + c] - 14;
+            const float2 pv = df_norm(make_float2(ldexpf(hi[c], e), ldexpf(lo[c], e)));
+            float2* a = A + size_t(rg) * n + cg;
+            *a = df_add(*a, df_neg(pv));
+          }
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(d.flags, 1u);                         // a tensor-core wait expired
+    mbar_drain(&done, 0u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (ok && part <= 1 && pt == 0) {                // the same in every thread of the CTA
+    __syncthreads();
+    df_diag_block(A, d.L32 ? d.L32 + size_t(m) * n * n : nullptr, d.dinv + size_t(m) * n,
+                  d.dinv32 ? d.dinv32 + size_t(m) * n : nullptr, d.status + m, n, t0, dg);
+  }
+}
+
 // Both substitutions and the solution; the factor stays in double-float (its readers take
 // the pairs).  Its high parts, the FP32 copy for the refinement's correction solves, were
 // written by the diagonal-block and panel kernels as each element became final.
@@ -297,6 +499,8 @@ cudaError_t prepare_chol_dfloat(const Dev& d) {
   cudaError_t e = cudaFuncSetAttribute(cdf_final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(cdf_final_smem(d.nz)));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(cdf_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TCU_SMEM);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(cdf_resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(cdf_final_smem(d.nz)));
 }
@@ -327,6 +531,24 @@ cudaError_t launch_chol_dfloat(const Dev& d, int trace_mode, cudaStream_t s, con
   for (int step = 0, k0 = 0; k0 + FB < n; ++step, k0 += FB) {
     const int t = n - k0 - FB, nt = (t + UT - 1) / UT;
     cdf_panel_kernel<<<dim3((t + 31) / 32, d.nsub), 128, 0, s>>>(d, k0);
+    if (d.chol_tc) {                               // tensor-core updates: tiles of 128 x 64
+      const int ct = (t + TCU_N - 1) / TCU_N;
+      if (!ahead || ct < 2) {
+        if (prev_rest && (e = cudaStreamWaitEvent(s, prev_rest, 0)) != cudaSuccess) return e;
+        prev_rest = nullptr;
+        cdf_update_tc_kernel<<<unsigned(tcu_count(t, 0) * d.nsub), 256, TCU_SMEM, s>>>(d, k0, 0);
+        continue;
+      }
+      cudaEvent_t ev_panel = la->ev[2 * step], ev_rest = la->ev[2 * step + 1];
+      if ((e = cudaEventRecord(ev_panel, s)) != cudaSuccess) return e;
+      if (prev_rest && (e = cudaStreamWaitEvent(s, prev_rest, 0)) != cudaSuccess) return e;
+      cdf_update_tc_kernel<<<unsigned(tcu_count(t, 1) * d.nsub), 256, TCU_SMEM, s>>>(d, k0, 1);
+      if ((e = cudaStreamWaitEvent(la->side, ev_panel, 0)) != cudaSuccess) return e;
+      cdf_update_tc_kernel<<<dim3(tcu_count(t, 2), d.nsub), 256, TCU_SMEM, la->side>>>(d, k0, 2);
+      if ((e = cudaEventRecord(ev_rest, la->side)) != cudaSuccess) return e;
+      prev_rest = ev_rest;
+      continue;
+    }
     if (!ahead || nt < 2) {
       if (prev_rest && (e = cudaStreamWaitEvent(s, prev_rest, 0)) != cudaSuccess) return e;
       prev_rest = nullptr;

@@ -169,7 +169,7 @@ int validate(const edt_config* c) {
   if (!(c->alpha >= 0) || !std::isfinite(c->alpha)) return EDT_EINVAL;
   if (!std::isfinite(c->cutoff)) return EDT_EINVAL;
   if (c->fold != 0 && c->fold != 1) return EDT_EINVAL;
-  if (c->chol_df < 0 || c->chol_df > 2) return EDT_EINVAL;
+  if (c->chol_df < 0 || c->chol_df > 3) return EDT_EINVAL;
   if (c->freq_chunk < 0 || c->gram_seg_rows < 0) return EDT_EINVAL;
   if (c->resid < 0 || c->resid > 2) return EDT_EINVAL;
   if (c->sub_begin < 0 || c->sub_end < 0 || c->sub_begin > c->sub_end) return EDT_EINVAL;
@@ -728,6 +728,7 @@ void bind(edt_ctx* c) {
   d.precision = c->cfg.precision; d.passes = c->cfg.passes; d.fold = c->cfg.fold;
   // the mixed path factors in double-float unless native FP64 is asked for (chol_df = 2)
   d.chol_df = c->cfg.precision == EDT_MIXED && c->cfg.chol_df != 2 ? 1 : 0;
+  d.chol_tc = d.chol_df && c->cfg.chol_df == 3 ? 1 : 0;
   d.alpha = c->cfg.alpha; d.dx = c->cfg.dx; d.dz = c->cfg.dz;
   d.fc = at<const FreqConst*>(c, c->r_fc);
   d.layer_top = at<const double*>(c, c->r_ltop);

@@ -66,6 +66,7 @@ struct Dev {
   int N, nk, nz, nf, nsub, nlayer;
   int nzs;                      // row stride of the FP32 table: nz rounded up to even
   int precision, passes, fold, chol_df;
+  int chol_tc;                  // double-float factorisation with the sliced tensor-core updates
   // window geometry (geom == EDT_GEOM_WINDOW): ny x nx midpoints (nx == N), wy x wx
   // half-offsets, W = wx * wy, nxy = nx * ny
   int geom, ny, wx, wy, W, nxy;

@@ -235,3 +235,25 @@ def test_few_layer_reference_with_fp32_march_coefficients(nlayer):
     assert rel_l2(vh, vh_or) < 1e-5
     assert rel_l2(V, V_or) < 1e-5
     assert rel_l2(V, V64) < 2e-6
+
+
+@pytest.mark.parametrize("nz", [40, 130, 256])
+def test_tensor_core_sliced_updates_match_the_double_float_factor(nz):
+    """chol_df = 3: the trailing updates of the double-float Cholesky run on the tensor cores
+    (eight 7-bit BF16 slices per panel value, every level of slice products summed exactly in
+    FP32 tensor memory).  The factor matches the default double-float one to FP64 class and
+    the inversion the oracle's 1e-5."""
+    from paper_0905_0238_gb300 import Config, Solver, EDT_MIXED
+    wl = small_workload(nx=32, nz=nz, nf=4, alpha=1e-2, dz=8.0)
+    D = born_data(wl, salt=9)
+    V_or, _ = edt2d.invert(wl, D.astype(np.complex128))
+    out = {}
+    for cd in (0, 3):
+        s = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=3, refine=1, chol_df=cd))
+        V = s.invert(dev(D)).cpu().numpy()
+        st = s.stats()
+        assert st.n_notpd == 0 and st.n_nonfinite == 0 and st.gram_timeouts == 0
+        out[cd] = (V, np.tril(s.factor().cpu().numpy()))
+    L0, L3 = out[0][1], out[3][1]
+    assert np.abs(L3 - L0).max() <= 1e-12 * np.abs(L0).max()
+    assert rel_l2(out[3][0], V_or) < 1e-5
