@@ -6,9 +6,11 @@ Workload: 512 shots x 512 receivers (dx 12.5 m, periodic line), 128 frequencies 
 velocity field, complex64 Born data from the library's own forward model plus complex
 Gaussian noise at 20 dB SNR per frequency, damping alpha = 1e-2 (lam = alpha trace G).
 One step = one full inversion (all 257 split systems standing for the 512 midpoint
-wavenumbers): depth march, data transform, right-hand sides, tensor-core Gram, FP64
-Cholesky, one refinement step, inverse transform.  Subproblems counted = nx (512) per
-inversion, one per midpoint wavenumber.
+wavenumbers): depth march, data transform, right-hand sides, tensor-core Gram, double-float
+(FP64-class) Cholesky, one refinement step, inverse transform.  Subproblems counted = nx (512)
+per inversion, one per midpoint wavenumber.  Independent lines are inverted two at a time
+(--lines-in-flight), each with its own context and CUDA stream, consecutive steps alternating
+between them, so that one line's tensor-core Gram overlaps another's Cholesky and refinement.
 
 Multi-GPU: each rank inverts its own independent survey line (weak scaling, no
 data-path collective); time = max over ranks.
@@ -47,6 +49,9 @@ def parse():
                     help="Cholesky of the mixed path: 0/1 double-float on the FP32 pipes (default), "
                          "2 native FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lines-in-flight", type=int, default=2,
+                    help="production line: independent lines inverted concurrently, one context "
+                         "and CUDA stream each (the timed steps alternate between them)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--freq-stride", type=int, default=1,
                     help="profiling aid: keep every k-th frequency of the 2D line (a smaller case of "
@@ -449,12 +454,32 @@ def main():
     tuning = None
     if not args.no_autotune:
         tuning = mixed.autotune(D, out=Vout, reps=3)     # launch shapes (same arithmetic)
+    # independent lines in flight: one context (workspace, streams, tuned shapes) and one CUDA
+    # stream each; consecutive steps alternate between them, so one line's tensor-core Gram
+    # overlaps another's FP32-bound Cholesky and L1-bound refinement
+    lines = max(1, args.lines_in_flight)
+    ctxs, outs = [mixed], [Vout]
+    for _ in range(lines - 1):
+        c2 = Solver(Config.from_workload(wl, precision=EDT_MIXED, passes=args.passes,
+                                         refine=args.refine, chol_df=args.chol_df), device=dev)
+        c2.set_tuning(**{k: v for k, v in mixed.tuning().items() if k != "invert_ms"})
+        ctxs.append(c2)
+        outs.append(torch.empty_like(Vout))
+    lstreams = [torch.cuda.Stream(device=dev) for _ in range(lines)]
+
+    def run_lines(k_steps):
+        for k in range(k_steps):
+            i = k % lines
+            with torch.cuda.stream(lstreams[i]):
+                ctxs[i].invert(D, out=outs[i])
+
     for _ in range(max(3, args.warmup)):
-        mixed.invert(D, out=Vout)
+        run_lines(lines)
     torch.cuda.synchronize()
-    st = mixed.stats()
-    if st.n_notpd or st.n_nonfinite:
-        raise RuntimeError(f"mixed path: {st.n_notpd} not PD, {st.n_nonfinite} non-finite")
+    for c in ctxs:
+        st = c.stats()
+        if st.n_notpd or st.n_nonfinite:
+            raise RuntimeError(f"mixed path: {st.n_notpd} not PD, {st.n_nonfinite} non-finite")
 
     # ---- device-resident timed region ----------------------------------------------
     clocks = Clocks(local)
@@ -463,11 +488,17 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        mixed.invert(D, out=Vout)
-    e1.record(stream)
+    e0.record(lstreams[0])
+    for ls in lstreams[1:]:
+        ls.wait_event(e0)
+    run_lines(args.steps)
+    for ls in lstreams[1:]:
+        ej = torch.cuda.Event()
+        ej.record(ls)
+        lstreams[0].wait_event(ej)
+    e1.record(lstreams[0])
     torch.cuda.synchronize()
+    del ctxs[1:], outs[1:]
     barrier()
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
@@ -630,7 +661,7 @@ def main():
         config=dict(workload=workload_summary(wl), l2=f"inputs larger than L2 ({D.numel() * D.element_size() / 1e6:.0f} MB data per step)",
                     passes=args.passes, refine=args.refine, chol_df=args.chol_df, alpha=wl.alpha,
                     rows_total=int(st.rows_total), rows_solved=int(st.rows_solved),
-                    parallelism=f"replicas x{world} (independent lines)",
+                    parallelism=f"replicas x{world} (independent lines)", lines_in_flight=lines,
                     launch_shapes=(tuning or mixed.tuning()), autotuned=tuning is not None),
         model_pts_per_sec=world * wl.nx * wl.nz * args.steps / (ms_total / 1e3),
         e2e=dict(value=e2e_value, unit="subproblems/s",
