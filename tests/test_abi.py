@@ -56,7 +56,7 @@ def test_host_side_validation_without_gpu():
                       (dict(precision=7), edt.EDT_EINVAL), (dict(fold=3), edt.EDT_EINVAL),
                       (dict(precision=edt.EDT_MIXED, passes=2), edt.EDT_EINVAL),
                       (dict(precision=edt.EDT_MIXED, nz=300), edt.EDT_EUNSUPPORTED),
-                      (dict(chol_df=3), edt.EDT_EINVAL), (dict(freq_chunk=-1), edt.EDT_EINVAL)):
+                      (dict(chol_df=4), edt.EDT_EINVAL), (dict(freq_chunk=-1), edt.EDT_EINVAL)):
         with pytest.raises(edt.EdtError) as ei:
             edt.edt_create(cfg(**bad))
         assert ei.value.code == code
