@@ -498,7 +498,6 @@ def main():
         lstreams[0].wait_event(ej)
     e1.record(lstreams[0])
     torch.cuda.synchronize()
-    del ctxs[1:], outs[1:]
     barrier()
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
@@ -516,31 +515,45 @@ def main():
 
     # ---- end to end through the host-buffer entry point ----------------------------
     # every step copies its 268 MB of data in and V out inside the timed region; with the
-    # host pipeline on, step k+1's input copy overlaps step k's stages (the serial figure,
-    # every copy in line with the stages, is reported beside it)
+    # host pipeline on, a context's next input copy overlaps its current stages (the serial
+    # figure, one context with every copy in line with the stages, is reported beside it).
+    # The same lines in flight as the device-resident region, each context on its own stream.
     Dh = D.cpu().pin_memory()
-    Vh = torch.empty((wl.nx, wl.nz), dtype=torch.float32).pin_memory()
+    Vhs = [torch.empty((wl.nx, wl.nz), dtype=torch.float32).pin_memory() for _ in range(lines)]
 
-    def e2e_ms(pipe):
-        mixed.set_host_pipeline(pipe)
-        for _ in range(2):
-            mixed.invert_host(Dh, Vh)
+    def e2e_ms(pipe, nl):
+        for c in ctxs[:nl]:
+            c.set_host_pipeline(pipe)
+        for i in range(nl):
+            with torch.cuda.stream(lstreams[i]):
+                for _ in range(2):
+                    ctxs[i].invert_host(Dh, Vhs[i])
         torch.cuda.synchronize()
         barrier()
         h0 = torch.cuda.Event(enable_timing=True)
         h1 = torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        for _ in range(args.steps):
-            mixed.invert_host(Dh, Vh)
-        h1.record(stream)
+        h0.record(lstreams[0])
+        for ls in lstreams[1:nl]:
+            ls.wait_event(h0)
+        for k in range(args.steps):
+            i = k % nl
+            with torch.cuda.stream(lstreams[i]):
+                ctxs[i].invert_host(Dh, Vhs[i])
+        for ls in lstreams[1:nl]:
+            ej = torch.cuda.Event()
+            ej.record(ls)
+            lstreams[0].wait_event(ej)
+        h1.record(lstreams[0])
         torch.cuda.synchronize()
         barrier()
-        mixed.set_host_pipeline(False)
+        for c in ctxs[:nl]:
+            c.set_host_pipeline(False)
         return max_over_ranks(h0.elapsed_time(h1), world)
 
-    ms_e2e_serial = e2e_ms(False)
-    ms_e2e = e2e_ms(True)
+    ms_e2e_serial = e2e_ms(False, 1)
+    ms_e2e = e2e_ms(True, lines)
     e2e_value = job_throughput(world, sub_per_step, args.steps, ms_e2e)
+    del ctxs[1:], outs[1:]
 
     # ---- accuracy vs the FP64 GPU path, and the FP64 path's own throughput --------------
     acc = {}
@@ -666,8 +679,8 @@ def main():
         model_pts_per_sec=world * wl.nx * wl.nz * args.steps / (ms_total / 1e3),
         e2e=dict(value=e2e_value, unit="subproblems/s",
                  h2d_bytes_per_step=int(Dh.numel() * Dh.element_size()),
-                 d2h_bytes_per_step=int(Vh.numel() * Vh.element_size()),
-                 pipelined=True, ms_per_step=ms_e2e / args.steps,
+                 d2h_bytes_per_step=int(Vhs[0].numel() * Vhs[0].element_size()),
+                 pipelined=True, lines_in_flight=lines, ms_per_step=ms_e2e / args.steps,
                  serial_value=job_throughput(world, sub_per_step, args.steps, ms_e2e_serial),
                  serial_ms_per_step=ms_e2e_serial / args.steps),
         gpu_launches=int(st.launches_per_invert) * args.steps,
