@@ -118,14 +118,9 @@ __device__ void chol_solve_2rhs(const double* A, const double* dinv, int n, doub
 }
 
 // trace_mode 0: trace from the diagonal of G; 1: from d.trace (accumulated by the producer).
-// DF = true: the trailing updates (almost all of the n^3/3 flops) are accumulated in
-// double-float arithmetic on the FP32 pipes -- each panel entry split into an FP32 (hi, lo)
-// pair, products by the exact fma error transformation plus the two cross terms, sums by
-// TwoSum -- about 48-bit accurate, then subtracted from the FP64 matrix.  Diagonal blocks,
-// panels, pivots, storage and the solves stay FP64.
 // VAR = true: every subproblem m has its own size sub_n[m], its matrices at element offset
 // sub_goff[m] of G (and L32) and its vectors at sub_voff[m] (streaming batches).
-template <bool DF, bool VAR>
+template <bool VAR>
 __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
   extern __shared__ __align__(16) double sm[];
   const int m = VAR && d.sub_order ? d.sub_order[blockIdx.x] : blockIdx.x;
@@ -232,16 +227,6 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
     }
     __syncthreads();
     // trailing lower triangle: A[i][j] -= sum_l P[i][l] P[j][l], 4x4 tiles
-    if (DF) {   // split the panel in place into FP32 (hi, lo) pairs (same 8 bytes per entry)
-      __syncthreads();
-      for (int e = threadIdx.x; e < t * kb; e += blockDim.x) {
-        const int i = e / kb, j = e - i * kb;
-        const double x = sP[i * LDP + j];
-        const float hi = float(x);
-        reinterpret_cast<float2*>(sP)[i * LDP + j] = make_float2(hi, float(x - double(hi)));
-      }
-      __syncthreads();
-    }
     const int nbt = (t + 3) / 4;
     const int npair = nbt * (nbt + 1) / 2;
     for (int pt = threadIdx.x; pt < npair; pt += blockDim.x) {
@@ -249,62 +234,27 @@ __global__ void __launch_bounds__(256) chol_kernel(Dev d, int trace_mode) {
       while (bi * (bi + 1) / 2 > pt) --bi;
       while ((bi + 1) * (bi + 2) / 2 <= pt) ++bi;
       const int bj = pt - bi * (bi + 1) / 2;
-      if (DF) {
-        const float2* sP2 = reinterpret_cast<const float2*>(sP);
-        float sh[4][4] = {}, sl[4][4] = {};
-        for (int l = 0; l < kb; ++l) {
-          float2 pi[4], pj[4];
+      double acc[4][4] = {};
+      for (int l = 0; l < kb; ++l) {
+        double pi[4], pj[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int ii = bi * 4 + u, jj = bj * 4 + u;
-            pi[u] = ii < t ? sP2[ii * LDP + l] : make_float2(0.f, 0.f);
-            pj[u] = jj < t ? sP2[jj * LDP + l] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const float p = pi[u].x * pj[v].x;
-              const float e = fmaf(pi[u].x, pj[v].x, -p);                  // exact error of p
-              const float c = fmaf(pi[u].x, pj[v].y, pi[u].y * pj[v].x);   // cross terms
-              const float sv = sh[u][v] + p;                               // TwoSum(sh, p)
-              const float bv = sv - sh[u][v];
-              const float er = (sh[u][v] - (sv - bv)) + (p - bv);
-              sh[u][v] = sv;
-              sl[u][v] += er + (e + c);
-            }
+        for (int u = 0; u < 4; ++u) {
+          const int ii = bi * 4 + u, jj = bj * 4 + u;
+          pi[u] = ii < t ? sP[ii * LDP + l] : 0.0;
+          pj[u] = jj < t ? sP[jj * LDP + l] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int ii = bi * 4 + u, jj = bj * 4 + v;
-            if (ii < t && jj <= ii)
-              A[size_t(t0 + ii) * n + t0 + jj] -= double(sh[u][v]) + double(sl[u][v]);
-          }
-      } else {
-        double acc[4][4] = {};
-        for (int l = 0; l < kb; ++l) {
-          double pi[4], pj[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int ii = bi * 4 + u, jj = bj * 4 + u;
-            pi[u] = ii < t ? sP[ii * LDP + l] : 0.0;
-            pj[u] = jj < t ? sP[jj * LDP + l] : 0.0;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fma(pi[u], pj[v], acc[u][v]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int ii = bi * 4 + u, jj = bj * 4 + v;
-            if (ii < t && jj <= ii) A[size_t(t0 + ii) * n + t0 + jj] -= acc[u][v];
-          }
+          for (int v = 0; v < 4; ++v) acc[u][v] = fma(pi[u], pj[v], acc[u][v]);
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int ii = bi * 4 + u, jj = bj * 4 + v;
+          if (ii < t && jj <= ii) A[size_t(t0 + ii) * n + t0 + jj] -= acc[u][v];
+        }
     }
     __syncthreads();
   }
@@ -746,7 +696,7 @@ int chol_launches(int nz) { return 1; }
 static size_t chol_smem(int nz) { return (size_t(nz) * LDP + NB * LDP + 2 * nz + 40) * sizeof(double); }
 
 cudaError_t prepare_chol(const Dev& d) {
-  cudaError_t e = cudaFuncSetAttribute(chol_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(chol_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(chol_smem(d.nz)));
   if (e != cudaSuccess) return e;
   return prepare_chol_dfloat(d);
@@ -754,7 +704,7 @@ cudaError_t prepare_chol(const Dev& d) {
 
 cudaError_t launch_chol_solve(const Dev& d, int trace_mode, cudaStream_t s, const CholLookahead* la) {
   if (d.chol_df) return launch_chol_dfloat(d, trace_mode, s, la);
-  chol_kernel<false, false><<<d.nsub, 256, chol_smem(d.nz), s>>>(d, trace_mode);
+  chol_kernel<false><<<d.nsub, 256, chol_smem(d.nz), s>>>(d, trace_mode);
   return cudaGetLastError();
 }
 
@@ -776,14 +726,14 @@ cudaError_t launch_refine_update(const Dev& d, cudaStream_t s) {
 // Streaming batches: subproblem m has size sub_n[m] <= nmax; lam = trace[m] (trace_mode 1
 // with alpha = 1: the caller accumulates alpha * trace).
 cudaError_t prepare_chol_var(int nmax) {
-  return cudaFuncSetAttribute(chol_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(chol_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(chol_smem(nmax)));
 }
 
 int chol_block_cols() { return NB; }
 
 cudaError_t launch_chol_var(const Dev& d, int nmax, cudaStream_t s) {
-  chol_kernel<false, true><<<d.nsub, 256, chol_smem(nmax), s>>>(d, 1);
+  chol_kernel<true><<<d.nsub, 256, chol_smem(nmax), s>>>(d, 1);
   return cudaGetLastError();
 }
 
